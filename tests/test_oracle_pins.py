@@ -1,0 +1,508 @@
+"""Pins for the CPU oracle: each test checks the oracle against something other
+than itself -- closed forms, brute force, hand-worked values, invariants -- so
+that a dropped term, a wrong sign or index, or a transposed operand in the
+oracle fails at least one of them. CPU only."""
+from __future__ import annotations
+
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------
+# helpers written independently of the oracle
+# ----------------------------------------------------------------------------
+
+def kron_G(N):
+    """F^{(x)n} by numpy's Kronecker product (Def. II.1)."""
+    F = np.array([[1, 0], [1, 1]], dtype=np.int64)
+    G = np.array([[1]], dtype=np.int64)
+    while G.shape[0] < N:
+        G = np.kron(G, F)
+    return G
+
+
+def gf2_rank(A):
+    A = (np.array(A, dtype=np.uint8) & 1).copy()
+    rows, cols = A.shape
+    r = 0
+    for c in range(cols):
+        piv = np.nonzero(A[r:, c])[0]
+        if piv.size == 0:
+            continue
+        p = r + piv[0]
+        A[[r, p]] = A[[p, r]]
+        mask = A[:, c].astype(bool)
+        mask[r] = False
+        A[mask] ^= A[r]
+        r += 1
+        if r == rows:
+            break
+    return r
+
+
+def esp(ks):
+    """Coefficients of prod (1 + k x): the elementary symmetric polynomials."""
+    poly = [1]
+    for k in ks:
+        nxt = poly + [0]
+        for i in range(len(poly)):
+            nxt[i + 1] += k * poly[i]
+        poly = nxt
+    return poly
+
+
+def canonical_index(code, Sp):
+    """Closed-form canonical index of a TEP given by per-rank codes (2 bits per
+    rank, 0 = unchanged, 1 = h, 2 = v, 3 = diag)."""
+    digits = [(code >> (2 * r)) & 3 for r in range(Sp)]
+    P = [r for r in range(Sp) if digits[r]]
+    w = len(P)
+    off = sum(math.comb(Sp, v) * 3 ** v for v in range(w))
+    colex = sum(math.comb(p, j + 1) for j, p in enumerate(P))
+    alpha = sum((digits[p] - 1) * 3 ** j for j, p in enumerate(P))
+    return off + colex * 3 ** w + alpha
+
+
+def gray(l):
+    return l ^ (l >> 1)
+
+
+# ----------------------------------------------------------------------------
+# code construction (Def. II.1)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N", [2, 4, 8, 32, 128])
+def test_generator_is_kronecker_power_and_involution(oracle_lib, N):
+    G = oracle_lib.generator_G(N).astype(np.int64)
+    assert np.array_equal(G, kron_G(N))
+    assert np.array_equal((G @ G) % 2, np.eye(N, dtype=np.int64))
+
+
+def _bec_erasure_by_bruteforce(N, eps):
+    """Erasure probability of each synthetic channel of G_N on a BEC(eps) under
+    successive cancellation, by enumerating all 2^N erasure patterns: u_i is
+    lost iff some u with u_<i = 0 and u_i = 1 encodes to zeros on every
+    observed position."""
+    G = kron_G(N)
+    pe = np.zeros(N)
+    for mask in range(1 << N):
+        observed = [j for j in range(N) if not (mask >> j) & 1]
+        p = eps ** (N - len(observed)) * (1 - eps) ** len(observed)
+        for i in range(N):
+            # unknowns u_{i+1..N-1}; equations sum_k u_k G[k][j] = G[i][j]
+            A = np.array([[G[k][j] for k in range(i + 1, N)] + [G[i][j]] for j in observed],
+                         dtype=np.uint8).reshape(len(observed), N - i)
+            consistent = gf2_rank(A[:, :-1]) == gf2_rank(A) if A.size else True
+            if consistent:
+                pe[i] += p
+    return pe
+
+
+def test_bhattacharyya_matches_bec_bruteforce(oracle_lib):
+    """Arikan's recursion is exact on the BEC; the oracle's parameters must equal
+    the brute-force erasure probabilities (pins the index orientation)."""
+    for N in (4, 8):
+        eps = math.exp(-0.5)
+        z = oracle_lib.bhattacharyya(N, 0.5, 0.0)
+        assert np.allclose(z, _bec_erasure_by_bruteforce(N, eps), atol=1e-12, rtol=0)
+    # capacity is conserved on the BEC: the mean parameter equals the input one
+    z = oracle_lib.bhattacharyya(1024, 0.5, 0.0)
+    assert abs(z.mean() - math.exp(-0.5)) < 1e-12
+
+
+def test_frozen_set_n32(oracle_lib):
+    """Bhattacharyya at 0 dB, R = 1/2, the 16 largest parameters frozen."""
+    assert oracle_lib.frozen_set(32, 16).tolist() == [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 16, 17, 18, 20]
+    for N in (32, 64, 128, 256, 512, 1024):
+        f = oracle_lib.frozen_set(N, N // 2)
+        z = oracle_lib.bhattacharyya(N, 0.5, 0.0)
+        info = np.setdiff1d(np.arange(N), f)
+        assert f.size == N // 2 and np.all(np.diff(f) > 0)
+        assert z[f].min() >= z[info].max()
+
+
+@pytest.mark.parametrize("N", [32, 64, 128, 256, 512, 1024])
+def test_parity_matrix_annihilates_code(oracle_lib, N):
+    K = N // 2
+    H = oracle_lib.parity_H(N, K).astype(np.int64)
+    f = oracle_lib.frozen_set(N, K)
+    info = np.setdiff1d(np.arange(N), f)
+    G = kron_G(N)
+    assert not ((G[info] @ H.T) % 2).any()  # G_I H^T = 0
+    assert gf2_rank(H) == N - K
+    g = wl.rng(99, N)
+    c = wl.random_codewords(g, 2000, N, info).astype(np.int64)
+    assert not ((c @ H.T) % 2).any()
+
+
+# ----------------------------------------------------------------------------
+# demodulation (Def. II.2, Eq. 2, Def. III.1, Def. III.2)
+# ----------------------------------------------------------------------------
+
+def _read_hand_vectors():
+    rows = []
+    with open(os.path.join(GOLDEN, "demod_hand_vectors.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            t = line.split()
+            rows.append(t)
+    return rows
+
+
+def _pt(s):
+    return None if s == "none" else tuple(int(v) for v in s.split(","))
+
+
+def test_qam_d_is_eq2(oracle_lib):
+    for M, m in ((4, 1), (16, 2), (64, 3), (256, 4)):
+        assert oracle_lib.qam_d(M) == pytest.approx(math.sqrt(3 * m / (M - 1)), rel=1e-15)
+        # average symbol energy of the scaled odd-integer grid is 2m E_b
+        side = int(math.isqrt(M))
+        A = 2 * np.arange(side) - (side - 1)
+        es = 2 * np.mean(A.astype(float) ** 2) * oracle_lib.qam_d(M) ** 2
+        assert es == pytest.approx(2 * m, rel=1e-12)
+
+
+@pytest.mark.parametrize("literal", [False, True])
+def test_demod_hand_vectors(oracle_lib, literal):
+    for t in _read_hand_vectors():
+        M = int(t[0])
+        rI, rQ = float(t[1]), float(t[2])
+        AI, AQ = int(t[3]), int(t[4])
+        Lx = float(t[15]) if literal else float(t[7])
+        key = int(t[14]) if literal else int(t[8])
+        nmask, hard = int(t[9]), int(t[10])
+        h, v, dg = _pt(t[11]), _pt(t[12]), _pt(t[13])
+        d = math.sqrt(3 * (math.log2(M) / 2) / (M - 1))
+        sym = np.array([[complex(rI * d, rQ * d)]], dtype=np.complex64)
+        N = 32
+        out = oracle_lib.demod(np.repeat(sym, 1, axis=1), M, N, literal=literal)
+        side = int(math.isqrt(M))
+        lI, lQ = int(out["hard_idx"][0, 0]) >> 8, int(out["hard_idx"][0, 0]) & 0xFF
+        assert (2 * lI - (side - 1), 2 * lQ - (side - 1)) == (AI, AQ)
+        assert out["hard_idx"][0, 0] == hard
+        assert out["key"][0, 0] == key
+        assert out["nmask"][0, 0] == nmask
+        assert out["rel"][0, 0] == pytest.approx(Lx, abs=2e-6)
+        # neighbours from the mask
+        nm = out["nmask"][0, 0]
+        dI = 1 if nm & 8 else -1
+        dQ = 1 if nm & 16 else -1
+        got_h = (AI + 2 * dI, AQ) if nm & 1 else None
+        got_v = (AI, AQ + 2 * dQ) if nm & 2 else None
+        got_d = (AI + 2 * dI, AQ + 2 * dQ) if nm & 4 else None
+        assert (got_h, got_v, got_d) == (h, v, dg)
+
+
+@pytest.mark.parametrize("M", [4, 16, 64, 256])
+def test_demod_hard_point_is_nearest_point(oracle_lib, M):
+    """Brute force: the hard point is the nearest of the M points on the
+    quantised grid; exactly on a threshold the upper level is taken."""
+    side = int(math.isqrt(M))
+    g = np.random.default_rng(M)
+    d = math.sqrt(3 * (math.log2(M) / 2) / (M - 1))
+    r = g.uniform(-side - 2, side + 2, size=(4000, 2))
+    # include exact thresholds and exact points
+    r[:200, 0] = 2 * g.integers(-side // 2, side // 2 + 1, size=200)
+    r[200:400, 1] = 2 * g.integers(-side // 2, side // 2 + 1, size=200) - 1
+    sym = (r[:, 0] * d + 1j * r[:, 1] * d).astype(np.complex64).reshape(-1, 1)
+    out = oracle_lib.demod(sym, M, 32)
+    q = np.float32(256.0 / d)
+    A = 2 * np.arange(side) - (side - 1)
+    for axis, comp in ((0, sym.real), (1, sym.imag)):
+        aq = np.clip(np.rint(comp.astype(np.float32) * q), -32768, 32767).astype(np.int64)[:, 0]
+        dist = np.abs(256 * A[None, :] - aq[:, None])
+        best = dist.min(axis=1, keepdims=True)
+        cand = np.where(dist == best, np.arange(side)[None, :], -1)
+        want = cand.max(axis=1)  # tie (threshold) -> upper level
+        got = (out["hard_idx"][:, 0] >> 8) if axis == 0 else (out["hard_idx"][:, 0] & 0xFF)
+        assert np.array_equal(got.astype(np.int64), want)
+
+
+def test_demod_invariants(oracle_lib):
+    M = 64
+    side = 8
+    g = np.random.default_rng(5)
+    d = math.sqrt(3 * 3 / 63)
+    r = g.uniform(-side - 3, side + 3, size=(5000, 2))
+    sym = (r[:, 0] * d + 1j * r[:, 1] * d).astype(np.complex64).reshape(-1, 1)
+    out = oracle_lib.demod(sym, M, 32)
+    nm = out["nmask"][:, 0]
+    k = ((nm & 1) > 0).astype(int) + ((nm & 2) > 0) + ((nm & 4) > 0)
+    assert set(np.unique(k)) <= {0, 1, 3}
+    # diag exists iff both h and v exist
+    assert np.array_equal((nm & 4) > 0, ((nm & 1) > 0) & ((nm & 2) > 0))
+    # inside the constellation square every axis has a neighbour
+    inside = (np.abs(r[:, 0]) < side - 1) & (np.abs(r[:, 1]) < side - 1)
+    assert np.all(k[inside] == 3)
+    # the FP64 likelihood is sqrt(dI^2 + dQ^2) with d <= 1 inside
+    assert np.all(out["rel"][inside, 0] <= math.sqrt(2) + 1e-9)
+
+
+def test_demod_packs_gray_labels(oracle_lib):
+    """Noise-free symbols demodulate to the transmitted coded bits."""
+    for M in (4, 16, 64, 256):
+        for N in (32, 128):
+            info = oracle_lib.info_set(N, N // 2)
+            g = wl.rng(7, M + N)
+            c = wl.random_codewords(g, 50, N, info)
+            tx = wl.qam_modulate(c, M).astype(np.complex64)
+            out = oracle_lib.demod(tx, M, N)
+            assert np.array_equal(out["y"], wl.pack_bits(c))
+
+
+# ----------------------------------------------------------------------------
+# TEP order (Alg. 2 Steps 2-4, Cor. III.1)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("Sp", [0, 1, 2, 3, 5, 8])
+def test_tep_order_all_neighbours(oracle_lib, Sp):
+    exists = np.full(Sp, 7, dtype=np.uint8)
+    codes, total = oracle_lib.tep_order(exists)
+    assert total == 4 ** Sp  # Cor. III.1 / Prop. III.1: 4^S patterns
+    idx = [canonical_index(int(c), Sp) for c in codes]
+    assert idx == list(range(4 ** Sp))
+    w = np.array([sum(1 for r in range(Sp) if (int(c) >> 2 * r) & 3) for c in codes])
+    for k in range(Sp + 1):
+        assert np.sum(w == k) == math.comb(Sp, k) * 3 ** k
+    # bit weight of the pattern: h and v flip one Gray bit, diag two
+    bw = np.array([sum({0: 0, 1: 1, 2: 1, 3: 2}[(int(c) >> 2 * r) & 3] for r in range(Sp)) for c in codes])
+    for b in range(2 * Sp + 1):
+        assert np.sum(bw == b) == math.comb(2 * Sp, b)
+
+
+def test_tep_order_partial_neighbours(oracle_lib):
+    g = np.random.default_rng(11)
+    for trial in range(30):
+        Sp = int(g.integers(1, 9))
+        exists = g.choice(np.array([0, 1, 2, 7], dtype=np.uint8), size=Sp)
+        codes, total = oracle_lib.tep_order(exists)
+        ks = [{0: 0, 1: 1, 2: 1, 7: 3}[int(e)] for e in exists]
+        assert total == int(np.prod([1 + k for k in ks]))
+        idx = [canonical_index(int(c), Sp) for c in codes]
+        assert all(a < b for a, b in zip(idx, idx[1:]))  # canonical order
+        # every valid pattern appears exactly once
+        allowed = [[0] + [a for a in (1, 2, 3) if (int(exists[r]) >> (a - 1)) & 1] for r in range(Sp)]
+        want = sorted(canonical_index(sum(d << 2 * r for r, d in enumerate(ds)), Sp)
+                      for ds in itertools.product(*allowed))
+        assert idx == want
+        w = [sum(1 for r in range(Sp) if (int(c) >> 2 * r) & 3) for c in codes]
+        assert [w.count(k) for k in range(Sp + 1)] == esp(ks)
+
+
+def test_select_is_stable_sort(oracle_lib):
+    g = np.random.default_rng(3)
+    for _ in range(50):
+        L = int(g.integers(1, 80))
+        key = g.integers(0, 6, size=L).astype(np.uint32)  # many ties
+        S = int(g.integers(0, 14))
+        got = oracle_lib.select(key, S)
+        want = np.lexsort((np.arange(L), key))[: min(S, L)]
+        assert np.array_equal(got, want)
+
+
+# ----------------------------------------------------------------------------
+# decoding (Alg. 2 and GRAND-AB)
+# ----------------------------------------------------------------------------
+
+def _codebook(oracle_lib, N):
+    K = N // 2
+    info = oracle_lib.info_set(N, K)
+    u = np.zeros((1 << K, N), dtype=np.uint8)
+    ids = np.arange(1 << K)
+    for b, pos in enumerate(info):
+        u[:, pos] = (ids >> b) & 1
+    return wl.polar_encode(u)
+
+
+def test_decode_noise_free(oracle_lib):
+    for M, N in ((4, 32), (16, 128), (64, 256), (256, 128)):
+        info = oracle_lib.info_set(N, N // 2)
+        H = oracle_lib.parity_H(N, N // 2)
+        g = wl.rng(1, M)
+        c = wl.random_codewords(g, 20, N, info)
+        tx = wl.qam_modulate(c, M).astype(np.complex64)
+        r = oracle_lib.decode_qam(H, tx, M, S=8, cap=1 << 16)
+        assert np.all(r["queries"] == 1) and np.all(r["abandon"] == 0)
+        assert np.array_equal(r["cw"], wl.pack_bits(c))
+
+
+def test_grand_ab_is_ml_within_radius(oracle_lib):
+    """GRAND-AB at N=32 against brute-force ML over all 2^16 codewords: with a
+    codeword within Hamming distance 3 the decision is the first such codeword
+    in (weight, colex) order of the error pattern; otherwise abandon."""
+    N = 32
+    book = _codebook(oracle_lib, N)
+    H = oracle_lib.parity_H(N, 16)
+    info = oracle_lib.info_set(N, 16)
+    d = wl.bpsk_frames(1, 0, 300, N, info, 1.0)
+    r = oracle_lib.decode_ab(H, d["symbols"], 3, 5489)
+    y = (d["symbols"] < 0).astype(np.uint8)
+    for f in range(300):
+        e = book ^ y[f]
+        wt = e.sum(axis=1)
+        dmin = wt.min()
+        if dmin <= 3:
+            cands = e[wt == dmin]
+            pos = [np.nonzero(x)[0].tolist() for x in cands]
+            ranks = [sum(math.comb(p, j + 1) for j, p in enumerate(P)) for P in pos]
+            best = cands[int(np.argmin(ranks))]
+            want_cw = wl.pack_bits((y[f] ^ best)[None, :])[0]
+            q = sum(math.comb(N, v) for v in range(dmin)) + min(ranks) + 1
+            assert r["abandon"][f] == 0
+            assert np.array_equal(r["cw"][f], want_cw)
+            assert r["queries"][f] == q
+        else:
+            assert r["abandon"][f] == 1 and r["queries"][f] == 5489
+            assert np.array_equal(r["cw"][f], wl.pack_bits(y[f][None, :])[0])
+
+
+def _expected_symbol_level(book_ints, sym_frame, M, N, S, cap, literal=False):
+    """Brute force for one frame, independent of the oracle's search: order the
+    symbols by the quantised key, enumerate every valid TEP by the closed-form
+    canonical index, build each candidate word from the Gray labels and look
+    it up in the codebook (membership by lookup, not by syndrome)."""
+    import oracle as orc
+    dm = orc.demod(sym_frame[None, :], M, N, literal=literal)
+    L = sym_frame.size
+    m = int(math.log2(M)) // 2
+    lI = (dm["hard_idx"][0] >> 8).astype(int)
+    lQ = (dm["hard_idx"][0] & 0xFF).astype(int)
+    nm = dm["nmask"][0].astype(int)
+    order = np.lexsort((np.arange(L), dm["key"][0]))
+    Sp = min(S, L)
+    sel = order[:Sp]
+
+    def labels_to_bits(lab_I, lab_Q):
+        bits = np.zeros(2 * m * L, dtype=np.uint8)
+        for i in range(L):
+            lab = (gray(lab_I[i]) << m) | gray(lab_Q[i])
+            for k in range(2 * m):
+                bits[2 * m * i + k] = (lab >> (2 * m - 1 - k)) & 1
+        return bits[:N]
+
+    alts = []
+    for r in range(Sp):
+        i = sel[r]
+        dI = 1 if nm[i] & 8 else -1
+        dQ = 1 if nm[i] & 16 else -1
+        opts = [0]
+        if nm[i] & 1:
+            opts.append(1)
+        if nm[i] & 2:
+            opts.append(2)
+        if nm[i] & 4:
+            opts.append(3)
+        alts.append((i, dI, dQ, opts))
+    combos = []
+    for ds in itertools.product(*[a[3] for a in alts]):
+        code = sum(d_ << 2 * r for r, d_ in enumerate(ds))
+        combos.append((canonical_index(code, Sp), ds))
+    combos.sort()
+    n_valid = len(combos)
+    for pos, (t, ds) in enumerate(combos, start=1):
+        if pos > cap:
+            break
+        II, QQ = lI.copy(), lQ.copy()
+        for (i, dI, dQ, _), dd in zip(alts, ds):
+            if dd in (1, 3):
+                II[i] += dI
+            if dd in (2, 3):
+                QQ[i] += dQ
+        x = labels_to_bits(II, QQ)
+        xi = int(wl.pack_bits(x[None, :])[0].astype(np.uint64)[0]) if N == 32 else None
+        if xi in book_ints:
+            return wl.pack_bits(x[None, :])[0], pos, 0
+    y = labels_to_bits(lI, lQ)
+    return wl.pack_bits(y[None, :])[0], min(cap, n_valid), 1
+
+
+@pytest.mark.parametrize("M,snr,S", [(4, 2.0, 8), (16, 6.0, 5), (64, 10.0, 4), (256, 14.0, 3)])
+def test_symbol_level_matches_codebook_bruteforce(oracle_lib, M, snr, S):
+    N = 32
+    book = _codebook(oracle_lib, N)
+    book_ints = set(wl.pack_bits(book)[:, 0].astype(np.uint64).tolist())
+    H = oracle_lib.parity_H(N, 16)
+    info = oracle_lib.info_set(N, 16)
+    d = wl.qam_frames(3, M, 40, N, info, M, snr)
+    cap = 4 ** S
+    r = oracle_lib.decode_qam(H, d["symbols"], M, S, cap)
+    n_ab = 0
+    for f in range(40):
+        cw, q, ab = _expected_symbol_level(book_ints, d["symbols"][f], M, N, S, cap)
+        assert (int(r["abandon"][f]), int(r["queries"][f])) == (ab, q), f
+        assert np.array_equal(r["cw"][f], cw)
+        n_ab += ab
+    assert 0 < n_ab < 40  # both outcomes exercised
+
+
+def test_cap_boundary(oracle_lib):
+    """A hit at exactly query = cap decodes; with cap one less it abandons."""
+    N, M = 128, 16
+    H = oracle_lib.parity_H(N, 64)
+    info = oracle_lib.info_set(N, 64)
+    d = wl.qam_frames(4, 0, 60, N, info, M, 8.0)
+    r = oracle_lib.decode_qam(H, d["symbols"], M, 8, 1 << 16)
+    f = int(np.nonzero((r["abandon"] == 0) & (r["queries"] > 3))[0][0])
+    q = int(r["queries"][f])
+    s = d["symbols"][f:f + 1]
+    a = oracle_lib.decode_qam(H, s, M, 8, q)
+    assert (a["abandon"][0], a["queries"][0]) == (0, q)
+    assert np.array_equal(a["cw"][0], r["cw"][f])
+    b = oracle_lib.decode_qam(H, s, M, 8, q - 1)
+    y = oracle_lib.demod(s, M, N)["y"][0]
+    assert (b["abandon"][0], b["queries"][0]) == (1, q - 1)
+    assert np.array_equal(b["cw"][0], y)
+
+
+def test_injected_error_at_least_reliable_symbol(oracle_lib):
+    """Move the least reliable symbol of a noise-free-like frame to a
+    neighbouring point: the search finds it within 1 + k_0 queries."""
+    N, M = 128, 16
+    H = oracle_lib.parity_H(N, 64)
+    info = oracle_lib.info_set(N, 64)
+    g = wl.rng(5, 0)
+    c = wl.random_codewords(g, 30, N, info)
+    tx = wl.qam_modulate(c, M)
+    d = oracle_lib.qam_d(M)
+    tx = tx + d * 0.05 * (g.standard_normal(tx.shape) + 1j * g.standard_normal(tx.shape))
+    # push symbol 5 of each frame just across its nearest threshold toward 0
+    for f in range(30):
+        z = tx[f, 5] / d
+        re = z.real - np.sign(z.real) * (abs(z.real) - abs(z.real) // 2 * 2 + 0.1) if abs(z.real) > 1 else -0.1 * np.sign(z.real)
+        tx[f, 5] = d * complex(re, z.imag)
+    sym = tx.astype(np.complex64)
+    r = oracle_lib.decode_qam(H, sym, M, 8, 1 << 16)
+    dm = oracle_lib.demod(sym, M, N)
+    for f in range(30):
+        sel = oracle_lib.select(dm["key"][f], 8)
+        assert sel[0] == 5
+        nm = int(dm["nmask"][f, 5])
+        k0 = (nm & 1 > 0) + (nm & 2 > 0) + (nm & 4 > 0)
+        assert r["abandon"][f] == 0
+        assert np.array_equal(r["cw"][f], wl.pack_bits(c[f][None, :])[0])
+        assert 1 < r["queries"][f] <= 1 + k0
+
+
+def test_nonfinite_frame_is_not_searched(oracle_lib):
+    N, M = 128, 16
+    H = oracle_lib.parity_H(N, 64)
+    info = oracle_lib.info_set(N, 64)
+    d = wl.qam_frames(6, 0, 3, N, info, M, 8.0)
+    s = d["symbols"].copy()
+    s[1, 7] = np.complex64(complex(np.nan, 0.0))
+    s[2, 0] = np.complex64(complex(0.5, np.inf))
+    r = oracle_lib.decode_qam(H, s, M, 8, 1 << 16)
+    assert r["abandon"].tolist()[1:] == [2, 2] and r["queries"].tolist()[1:] == [0, 0]
+    ra = oracle_lib.decode_ab(oracle_lib.parity_H(32, 16), np.array([[np.nan] + [1.0] * 31], np.float32), 3, 5489)
+    assert (ra["abandon"][0], ra["queries"][0]) == (2, 0)
