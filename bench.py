@@ -1,0 +1,433 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 GRAND decoder (arXiv 2405.01808, Alg. 2 on a GPU).
+
+Default workload: polar code N=128 K=64 (Bhattacharyya frozen set at 0 dB), Gray
+16-QAM over AWGN at Eb/N0 = 6, 8 and 10 dB, 100,000 frames per SNR (300,000
+frames per step), cut-off S = 10, query cap 2^20, symbol-level TEP order of the
+paper's likelihood function. One step decodes the whole batch through the
+fused demodulate-and-decode call (grand_decode_symbols): demodulation,
+likelihood and neighbours, selection, syndrome deltas, TEP enumeration and
+membership tests, and the decoded words.
+
+Metric: useful TEP syndrome checks per second (the sum of the query counts,
+i.e. valid TEPs up to the first codeword or the cap), with frames/s and the
+per-step latency beside it. Inputs are resident in HBM; L2 is flushed (256 MiB
+write) before every timed step. `e2e` repeats the measurement through the same
+public call with pinned host buffers (copies in the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--config c1|c2|c3a|c3b|c4]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+# -------------------------------------------------------------------------
+# workloads
+# -------------------------------------------------------------------------
+CONFIGS = {
+    "c1": dict(kind="ab", N=32, K=16, M=2, snrs=(4.0,), frames=10000, max_weight=3, cap=5489,
+               desc="polar N=32 K=16, BPSK, Eb/N0 4 dB, GRAND-AB weight<=3 (cap 5489), 10000 frames"),
+    "c2": dict(kind="qam", N=128, K=64, M=16, snrs=(6.0, 8.0, 10.0), frames=100000, S=10, cap=1 << 20,
+               desc="polar N=128 K=64, 16-QAM Gray, Eb/N0 6/8/10 dB x 100000 frames, S=10, cap 2^20"),
+    "c3a": dict(kind="qam", N=512, K=256, M=64, snrs=(10.0, 12.0, 14.0, 16.0), frames=20000, S=12, cap=1 << 24,
+                desc="polar N=512 K=256, 64-QAM Gray, Eb/N0 10/12/14/16 dB x 20000 frames, S=12, cap 2^24"),
+    "c3b": dict(kind="qam", N=1024, K=512, M=256, snrs=(10.0, 12.0, 14.0, 16.0), frames=20000, S=12, cap=1 << 24,
+                desc="polar N=1024 K=512, 256-QAM Gray, Eb/N0 10/12/14/16 dB x 20000 frames, S=12, cap 2^24"),
+    "c4": dict(kind="mixed", frames=1000000, S=10, cap=1 << 20,
+               desc="uneven mix: N in {32..1024}, M in {4,16,64,256}, Eb/N0 U(4,14) dB, 1000000 frames, "
+                    "S=min(L,10), cap 2^20, one call"),
+}
+METRIC = "TEP syndrome checks/s & frames/s per GB300; p50/p99 decode latency"
+CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5}
+# ALU roofline: 152 SMs x 64 integer-ALU lanes per clock (LOP3/ISETP class)
+# x 2.07 GHz maximum SM clock.
+SMS, ALU_LANES, MAX_CLOCK_GHZ = 152, 64, 2.07
+ALU_PEAK_TOPS = SMS * ALU_LANES * MAX_CLOCK_GHZ / 1000.0
+
+
+def make_inputs(cfg, rank, info_by_N):
+    """Host arrays of one step's batch (seeded; rank selects the stream)."""
+    cid = CONFIG_IDS[cfg["name"]]
+    if cfg["kind"] == "mixed":
+        return wl.mixed_frames(cid, 1000 + rank, cfg["frames"], info_by_N)
+    parts = []
+    for i, snr in enumerate(cfg["snrs"]):
+        if cfg["kind"] == "ab":
+            parts.append(wl.bpsk_frames(cid, 100 * rank + i, cfg["frames"], cfg["N"], info_by_N[cfg["N"]], snr))
+        else:
+            parts.append(wl.qam_frames(cid, 100 * rank + i, cfg["frames"], cfg["N"], info_by_N[cfg["N"]], cfg["M"],
+                                       snr))
+    return {"symbols": np.concatenate([p["symbols"] for p in parts]),
+            "codewords_packed": np.concatenate([p["codewords_packed"] for p in parts]),
+            "snr": np.concatenate([np.full(len(p["symbols"]), p["ebn0_db"]) for p in parts])}
+
+
+# -------------------------------------------------------------------------
+# clocks during the timed region
+# -------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                t = [x.strip() for x in line.split(",")]
+                if len(t) >= 9:
+                    rows.append(t)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------------------------
+# oracle (CPU baseline and the reference arm)
+# -------------------------------------------------------------------------
+def oracle_sample(cfg, inputs, per_snr, offset=0):
+    """A bounded, SNR-stratified sample of the step's frames."""
+    if cfg["kind"] == "mixed":
+        idx = np.arange(offset, offset + per_snr * 3) % len(inputs["N"])
+        return idx
+    n_snr = len(cfg["snrs"])
+    F = cfg["frames"]
+    return np.concatenate([s * F + (offset + np.arange(per_snr)) % F for s in range(n_snr)])
+
+
+def oracle_run(cfg, inputs, idx, threads):
+    """Decode the sampled frames with the oracle; returns (useful checks, frames, seconds)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    useful = 0
+    if cfg["kind"] == "mixed":
+        for n in np.unique(inputs["N"][idx]):
+            H = oracle.parity_H(int(n), int(n) // 2)
+            for M in np.unique(inputs["M"][idx]):
+                sel = idx[(inputs["N"][idx] == n) & (inputs["M"][idx] == M)]
+                if sel.size == 0:
+                    continue
+                L = wl.symbols_per_frame(int(n), int(M))
+                sym = np.stack([inputs["symbols"][inputs["sym_offset"][f]:inputs["sym_offset"][f] + L] for f in sel])
+                r = oracle.decode_qam(H, sym, int(M), min(cfg["S"], L), cfg["cap"], threads=threads)
+                useful += int(r["queries"].sum())
+    else:
+        H = oracle.parity_H(cfg["N"], cfg["K"])
+        if cfg["kind"] == "ab":
+            r = oracle.decode_ab(H, inputs["symbols"][idx], cfg["max_weight"], cfg["cap"], threads=threads)
+        else:
+            r = oracle.decode_qam(H, inputs["symbols"][idx], cfg["M"], cfg["S"], cfg["cap"], threads=threads)
+        useful = int(r["queries"].sum())
+    return useful, len(idx), time.perf_counter() - t0
+
+
+def info_sets(cfg, source):
+    Ns = wl.MIXED_N if cfg["kind"] == "mixed" else (cfg["N"],)
+    out = {}
+    for n in Ns:
+        if source == "oracle":
+            import oracle
+
+            out[n] = oracle.info_set(n, n // 2)
+        else:
+            import paper_2405_01808_gb300 as g
+
+            _, frozen = g.polar_H(n, n // 2)
+            out[n] = np.setdiff1d(np.arange(n), frozen)
+    return out
+
+
+def run_reference(args, cfg):
+    """The oracle as the reference arm: each step decodes a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    inputs = make_inputs(cfg, 0, info_sets(cfg, "oracle"))
+    threads = os.cpu_count() or 1
+    per = {"ab": 2000, "qam": 24, "mixed": 24}[cfg["kind"]]
+    for w in range(args.warmup):
+        oracle_run(cfg, inputs, oracle_sample(cfg, inputs, max(1, per // 8), offset=7 * w), threads)
+    useful = frames = 0
+    secs = 0.0
+    for k in range(args.steps):
+        u, f, s = oracle_run(cfg, inputs, oracle_sample(cfg, inputs, per, offset=per * k), threads)
+        useful += u
+        frames += f
+        secs += s
+    value = useful / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "checks/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded random polar codewords over AWGN)",
+        "config": {"workload": cfg["desc"], "sample_frames_per_step": frames // args.steps},
+        "frames_per_s": frames / secs,
+        "cpu_baseline": {"value": value, "unit": "checks/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{frames // args.steps} frames per step, SNR-stratified, of the workload"},
+        "e2e": {"value": value, "unit": "checks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------------
+# GPU arm
+# -------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=("gpu", "reference"))
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=0, help="override frames per SNR (for quick runs)")
+    args = ap.parse_args()
+    cfg = dict(CONFIGS[args.config])
+    cfg["name"] = args.config
+    if args.frames:
+        cfg["frames"] = args.frames
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import paper_2405_01808_gb300 as g
+
+    if rank == 0:
+        g.build()
+    if dist:
+        dist.barrier()
+    g.lib()
+
+    info = info_sets(cfg, "library")
+    inputs = make_inputs(cfg, rank, info)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    # ---- code objects and device buffers
+    if cfg["kind"] == "mixed":
+        codes = [g.Code.polar(n, n // 2) for n in wl.MIXED_N]
+        desc = g.frame_desc(np.searchsorted(np.array(wl.MIXED_N), inputs["N"]), inputs["M"], inputs["sym_offset"],
+                            inputs["cw_offset"])
+        d_desc = torch.from_numpy(desc.view(np.uint8)).to(dev)
+        n_frames = len(inputs["N"])
+        n_cw = inputs["n_cw_words"]
+        p = g.Params.make(M=0, S=cfg["S"], query_cap=cfg["cap"])
+        alg_words = None
+    else:
+        codes = [g.Code.polar(cfg["N"], cfg["K"])]
+        n_frames = len(inputs["symbols"])
+        n_cw = n_frames * cfg["N"] // 32
+        if cfg["kind"] == "ab":
+            p = g.Params.make(order=g.ORDER_HAMMING, M=2, max_weight=cfg["max_weight"], query_cap=cfg["cap"])
+        else:
+            p = g.Params.make(M=cfg["M"], S=cfg["S"], query_cap=cfg["cap"])
+        alg_words = (cfg["N"] - cfg["K"]) / 32.0
+    h_sym = torch.from_numpy(inputs["symbols"]).pin_memory()
+    d_sym = h_sym.to(dev)
+    d_cw = torch.empty(n_cw, dtype=torch.int32, device=dev)
+    d_q = torch.empty(n_frames, dtype=torch.int32, device=dev)
+    d_ab = torch.empty(n_frames, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(sym, stats=True):
+        if cfg["kind"] == "mixed":
+            return g.decode_mixed(codes, p, d_desc, sym, n_cw, cw=d_cw, queries=d_q, abandon=d_ab, stats=stats)
+        cw2 = d_cw.view(n_frames, -1)
+        return g.decode_symbols(codes[0], p, sym, cw=cw2, queries=d_q, abandon=d_ab, stats=stats)
+
+    for _ in range(args.warmup):
+        step(d_sym)
+    torch.cuda.synchronize()
+
+    # ---- timed steps (device-resident inputs)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, search_ms, prep_ms = [], [], []
+    useful_total = 0
+    search_useful = 0
+    evaluated = 0
+    hard = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = step(d_sym, stats=True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        search_ms.append(r["search_ms"])
+        prep_ms.append(r["prep_ms"])
+        search_useful += r["search_useful"]
+        evaluated += r["evaluated_checks"]
+        hard += r["hard_frames"]
+        useful_total += int(d_q.to(torch.int64).sum().item())  # outside the events
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    units = torch.tensor([float(useful_total), float(n_frames * args.steps), total_ms], dtype=torch.float64,
+                         device=dev)
+    if dist:
+        tmax = units[2].clone()
+        dist.all_reduce(units[:2], op=dist.ReduceOp.SUM)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        units[2] = tmax
+        dist.barrier()
+    useful_all, frames_all, tmax_ms = units.tolist()
+    value = useful_all / (tmax_ms / 1e3)
+    frames_per_s = frames_all / (tmax_ms / 1e3)
+
+    # ---- correctness of the timed output (decoded words vs transmitted)
+    cw_host = d_cw.cpu().numpy().view(np.uint32)
+    ab_host = d_ab.cpu().numpy()
+    if cfg["kind"] == "mixed":
+        sent = inputs["codewords_packed"]
+        errs = 0
+        for f in range(0, n_frames, max(1, n_frames // 20000)):
+            o, n = inputs["cw_offset"][f], inputs["N"][f] // 32
+            errs += int(not np.array_equal(cw_host[o:o + n], sent[o:o + n]))
+        bler = errs / len(range(0, n_frames, max(1, n_frames // 20000)))
+    else:
+        bler = float(np.mean((cw_host.reshape(n_frames, -1) != inputs["codewords_packed"]).any(axis=1)))
+
+    # ---- e2e: same call with host buffers, copies in the timed region
+    h_cw = torch.empty(n_cw, dtype=torch.int32).pin_memory()
+    h_q = torch.empty(n_frames, dtype=torch.int32).pin_memory()
+    h_ab = torch.empty(n_frames, dtype=torch.uint8).pin_memory()
+    d_sym2 = torch.empty_like(d_sym)
+    e2e_ms = []
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d_sym2.copy_(h_sym, non_blocking=True)
+        step(d_sym2, stats=False)
+        h_cw.copy_(d_cw, non_blocking=True)
+        h_q.copy_(d_q, non_blocking=True)
+        h_ab.copy_(d_ab, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = (useful_total / args.steps) / (statistics.mean(e2e_ms) / 1e3)
+
+    # ---- roofline of the dominant kernel (the TEP search)
+    roofline = None
+    if alg_words is not None and sum(search_ms) > 0:
+        ops = search_useful / args.steps * alg_words
+        achieved = ops / (statistics.mean(search_ms) / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                    "frac": achieved / ALU_PEAK_TOPS, "traffic": None, "kernel": "k_search",
+                    "ops_per_check": alg_words,
+                    "peak_source": f"derived: {SMS} SMs x {ALU_LANES} ALU lanes/clk x {MAX_CLOCK_GHZ} GHz"}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per = {"ab": 3000, "qam": 48, "mixed": 40}[cfg["kind"]]
+        idx = oracle_sample(cfg, inputs, per)
+        threads = os.cpu_count() or 1
+        u, f, s = oracle_run(cfg, inputs, idx, threads)
+        cpu = {"value": u / s, "unit": "checks/s", "cores": threads, "kind": "oracle",
+               "sample": f"{f} frames ({per} per SNR point) of the same workload", "frames_per_s": f / s,
+               "seconds": s}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "checks/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded random polar codewords over AWGN)",
+            "config": {"workload": cfg["desc"], "frames_per_step_per_gpu": n_frames,
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "parallelism": f"frames sharded, {world} replica(s)"},
+            "frames_per_s": frames_per_s,
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                           "what": "whole-batch decode time per step"},
+            "bler": bler,
+            "evaluated_checks_per_step": evaluated / args.steps,
+            "useful_checks_per_step": useful_total / args.steps,
+            "hard_frames_per_step": hard / args.steps,
+            "kernel_ms": {"prep": statistics.mean(prep_ms), "search": statistics.mean(search_ms)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "checks/s", "h2d_bytes_per_step": int(h_sym.numel() * h_sym.element_size()),
+                    "d2h_bytes_per_step": int(n_cw * 4 + n_frames * 5), "ms_per_step": statistics.mean(e2e_ms)},
+            "gpu_launches": 2 * args.steps if cfg["kind"] != "ab" else args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

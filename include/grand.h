@@ -1,0 +1,233 @@
+/*
+ * grand.h -- C ABI of the GB300 GRAND decoder (arXiv 2405.01808, "GRAND Massive
+ * Parallel Decoding Framework for Low Latency in Beyond 5G").
+ *
+ * The library decodes binary linear codes given by a parity-check matrix H
+ * (Def. II.1) from square M-QAM received symbols (Def. II.2). Each frame is
+ * demodulated with the paper's likelihood function and its three near-neighbour
+ * alternatives per symbol (Def. III.1, III.2), the S' = min(S, L) least
+ * reliable symbols are kept (Alg. 2 Steps 2-3), and the test error patterns
+ * (TEPs) over them are queried in a fixed canonical order until the first one
+ * whose candidate word has a zero syndrome H (y xor e) = 0 (Alg. 2 Steps 4-5),
+ * or until a query cap (abandonment, Sec. II). A bit-level GRAND-AB variant
+ * (hard decision, TEPs in ascending Hamming weight, Sec. I) is also provided.
+ *
+ * Canonical order (the paper leaves the order inside the 4^S set open): by the
+ * number w of altered symbols, then the colex order of the set of altered
+ * reliability ranks (rank 0 = least reliable), then the alternatives read as a
+ * base-3 number (h < v < diag) whose least significant digit belongs to the
+ * smallest altered rank. A TEP is valid when every chosen alternative exists;
+ * invalid TEPs are skipped and not counted. `queries` is the 1-based position
+ * of the decoded TEP among valid TEPs, or min(cap, number of valid TEPs) when
+ * the frame is abandoned.
+ *
+ * Conventions for every call:
+ *   - Return value 0 (GRAND_OK) or a negative grand_status. No exception
+ *     crosses the ABI. Argument errors are detected before any GPU work.
+ *   - "device" pointers are CUDA global memory owned by the caller; the
+ *     library never frees them. "host" pointers are ordinary CPU memory.
+ *     With n_frames == 0 the data pointers may be NULL (nothing is launched).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Calls that
+ *     take a stream enqueue asynchronous work on it and return; the caller
+ *     synchronises the stream before reading outputs and keeps every buffer
+ *     alive until then. Internal scratch is stream-ordered (cudaMallocAsync).
+ *   - Bit packing: a word of N bits is stored in N/32 uint32 words, bit j at
+ *     word j >> 5, bit position j & 31 (LSB first).
+ *   - A code object is immutable after creation; decodes on different streams
+ *     may share it. Destroying it while work on it is in flight is undefined.
+ */
+#ifndef GRAND_H
+#define GRAND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRAND_VERSION 10000 /* 1.0.0 */
+
+typedef enum grand_status {
+  GRAND_OK = 0,
+  GRAND_E_INVALID = -1,     /* an argument is out of range or NULL */
+  GRAND_E_RANK = -2,        /* H does not have full row rank N-K */
+  GRAND_E_NOMEM = -3,       /* host or device allocation failed */
+  GRAND_E_CUDA = -4,        /* a CUDA runtime call failed */
+  GRAND_E_TIMEOUT = -5,     /* a bounded device wait ran out */
+  GRAND_E_BUSY = -6,        /* the server cannot admit the request now */
+  GRAND_E_UNSUPPORTED = -7, /* valid request outside the built limits */
+} grand_status;
+
+/* TEP orders. */
+typedef enum grand_order {
+  GRAND_ORDER_HAMMING = 0, /* bit-level GRAND-AB: ascending Hamming weight, colex (Sec. I) */
+  GRAND_ORDER_QAM_NNE = 1, /* symbol-level, likelihood order of Def. III.1/III.2 (Alg. 2) */
+} grand_order;
+
+/* Readings of Def. III.1 for a received value beyond the outermost level. */
+typedef enum grand_lik {
+  GRAND_LIK_THRESHOLD = 0, /* d = distance to the nearest decision threshold (1 + |A - a|) */
+  GRAND_LIK_LITERAL = 1,   /* d = 1 - |A - a| as printed, clamped at 0 */
+} grand_lik;
+
+/* Built limits. */
+#define GRAND_N_MIN 32
+#define GRAND_N_MAX 1024
+#define GRAND_S_MAX 12
+#define GRAND_AB_WEIGHT_MAX 4
+
+/* Decode parameters.
+ *   order       GRAND_ORDER_*.
+ *   M           constellation: 2 (BPSK, HAMMING order only), 4, 16, 64, 256.
+ *   S           cut-off (Alg. 2 Step 3), 0..GRAND_S_MAX; S' = min(S, L).
+ *   max_weight  HAMMING order: largest number of flipped bits (0..4).
+ *   query_cap   abandonment threshold, >= 1 valid queries.
+ *   lik_variant GRAND_LIK_*.
+ *   tiles       launch shape, 0 = automatic: [0] warps per search CTA (1..16),
+ *               [1] A-side ranks of the search split (1..6), [2] number of
+ *               TEP weights tested by the per-frame preparation (0..3),
+ *               [3] reserved (0). Results do not depend on tiles. */
+typedef struct grand_params {
+  int32_t order;
+  int32_t M;
+  int32_t S;
+  int32_t max_weight;
+  int64_t query_cap;
+  int32_t lik_variant;
+  int32_t tiles[4];
+} grand_params;
+
+typedef struct grand_code grand_code;
+
+/* One frame of an uneven batch (grand_decode_mixed). Device memory.
+ *   code        index into the `codes` array of the call.
+ *   M           constellation of this frame (4, 16, 64, 256); L = ceil(N / log2 M).
+ *   sym_offset  first received symbol of the frame in the flat symbol array.
+ *   cw_offset   first output word of the frame in the flat codeword array. */
+typedef struct grand_frame_desc {
+  int32_t code;
+  int32_t M;
+  int64_t sym_offset;
+  int64_t cw_offset;
+} grand_frame_desc;
+
+/* Per-call counters (optional output of the decode calls; host memory).
+ * Requesting them makes the call synchronise its stream before returning.
+ *   evaluated_checks  TEP syndrome checks executed on the GPU, including
+ *                     speculative ones beyond the first hit.
+ *   hard_frames       frames that needed the parallel search stage.
+ *   search_useful     valid TEP queries (positions <= the reported query
+ *                     count) that fell to the search stage.
+ *   prep_ms, search_ms  device time of the preparation and search kernels,
+ *                     from CUDA events recorded on the call's stream. */
+typedef struct grand_stats {
+  uint64_t evaluated_checks;
+  uint64_t hard_frames;
+  uint64_t search_useful;
+  float prep_ms;
+  float search_ms;
+} grand_stats;
+
+/* Library version (GRAND_VERSION) and a static description of a status. */
+int grand_version(void);
+const char* grand_status_string(int status);
+
+/* Polar code helper (Def. II.1, Sec. II): G_N = F^{(x)n}; frozen set = the N-K
+ * synthetic channels with the largest Bhattacharyya parameter at design SNR
+ * `design_snr_db` (E_b/N0, rate-scaled: z0 = exp(-K/N * 10^(snr/10)); ties go
+ * to the lower index); H row r = column frozen[r] of G_N, so G_I H^T = 0.
+ *   H_out       host, (N-K) rows x (N/32) words, row-major, bit-packed.
+ *   frozen_out  host, N-K ascending indices, or NULL.
+ * Errors: GRAND_E_INVALID if N is not a power of two in [32, 1024], K < 1,
+ * K >= N, or H_out is NULL. Pure host computation. */
+int grand_polar_H(int N, int K, double design_snr_db, uint32_t* H_out, int32_t* frozen_out);
+
+/* Create a code from its parity-check matrix (Def. II.1; the membership test
+ * of Alg. 2 Step 5 is H x = 0).
+ *   H    host, (N-K) x (N/32) words, same layout as grand_polar_H; copied, not
+ *        retained. The object keeps a column-packed device copy.
+ *   out  receives the new object (host pointer).
+ * Errors: GRAND_E_INVALID (N not a power of two in [32, 1024], K < 1,
+ * N-K > 512, K >= N, NULL pointers), GRAND_E_RANK (rank H != N-K),
+ * GRAND_E_NOMEM, GRAND_E_CUDA. Synchronous on the current device. */
+int grand_code_create(const uint32_t* H, int N, int K, grand_code** out);
+
+/* Destroy a code (NULL is a no-op). The caller synchronises first. */
+int grand_code_destroy(grand_code* code);
+
+/* N and K of a code (host outputs, either may be NULL). */
+int grand_code_info(const grand_code* code, int* N, int* K);
+
+/* Demodulation (Def. III.1, III.2; Alg. 2 Step 1) of n_frames frames of L
+ * symbols each.
+ *   symbols   device. M >= 4: complex64 (interleaved float32 I, Q) [n_frames][L],
+ *             in transmitted units with E_b = 1 per coded bit, d = sqrt(3m/(M-1))
+ *             (Eq. 2). M = 2: float32 [n_frames][N] BPSK samples (bit 1 <-> -1).
+ *   M         2, 4, 16, 64 or 256; L must equal ceil(N / log2 M).
+ *   N0        noise spectral density; validated (> 0, finite) but the
+ *             likelihood is geometric and does not use it.
+ *   lik_variant GRAND_LIK_*.
+ *   Outputs (device, any may be NULL; only y is written for M = 2):
+ *   hard_idx  uint16 [n_frames][L] = (I level << 8) | Q level, level l has
+ *             odd amplitude 2l - (sqrt(M) - 1).
+ *   key       uint32 [n_frames][L] = dI^2 + dQ^2 with d the Q8.8 distance of
+ *             the received value to its nearest decision threshold (the
+ *             fixed-point likelihood; small = unreliable).
+ *   nmask     uint8 [n_frames][L]: bit0 h exists, bit1 v exists, bit2 diag
+ *             exists, bit3 I direction is +1, bit4 Q direction is +1, bit7
+ *             a coordinate was not finite (read as 0).
+ *   rel       float [n_frames][L] = sqrt(d1^2 + d2^2), Def. III.1, FP32.
+ *   y         uint32 [n_frames][N/32] packed hard word: symbol i carries bits
+ *             [2m i, 2m i + 2m), I Gray label then Q Gray label, MSB first;
+ *             bits >= N are dropped. For M = 2, bit j = [r_j < 0].
+ * Errors: GRAND_E_INVALID. Asynchronous on `stream`. */
+int grand_demod(const void* symbols, int64_t n_frames, int L, int M, float N0, int lik_variant,
+                uint16_t* hard_idx, uint32_t* key, uint8_t* nmask, float* rel, uint32_t* y, int N,
+                void* stream);
+
+/* Decode demodulated frames (Alg. 2 Steps 2-5 and Return).
+ *   For GRAND_ORDER_QAM_NNE: hard_idx, key, nmask, y as written by
+ *   grand_demod with the same M and lik_variant (device).
+ *   For GRAND_ORDER_HAMMING: only y is read (others may be NULL).
+ *   Outputs (device): cw uint32 [n_frames][N/32] decoded word (the hard word
+ *   when abandoned); queries uint32 [n_frames]; abandon uint8 [n_frames]:
+ *   0 decoded, 1 abandoned (cap reached or TEPs exhausted), 2 not searched
+ *   because a received value was not finite.
+ *   stats (host, may be NULL): filled after an internal stream synchronise;
+ *   pass NULL to keep the call asynchronous.
+ * Errors: GRAND_E_INVALID, GRAND_E_UNSUPPORTED, GRAND_E_NOMEM, GRAND_E_CUDA. */
+int grand_decode_batch(const grand_code* code, const grand_params* params, const uint16_t* hard_idx,
+                       const uint32_t* key, const uint8_t* nmask, const uint32_t* y, int64_t n_frames,
+                       uint32_t* cw, uint32_t* queries, uint8_t* abandon, grand_stats* stats, void* stream);
+
+/* Demodulate and decode in one pass: the per-symbol arrays are not written
+ * to memory. symbols as for grand_demod (M = params->M); outputs as for
+ * grand_decode_batch. */
+int grand_decode_symbols(const grand_code* code, const grand_params* params, const void* symbols,
+                         int64_t n_frames, float N0, uint32_t* cw, uint32_t* queries, uint8_t* abandon,
+                         grand_stats* stats, void* stream);
+
+/* Decode an uneven batch: frames of different codes and constellations in
+ * one launch sequence (persistent search kernel with a per-frame work queue).
+ *   codes      host array of n_codes code pointers.
+ *   desc       device array of n_frames grand_frame_desc.
+ *   symbols    device complex64, flat, n_symbols entries; frame f starts at
+ *              desc[f].sym_offset.
+ *   cw         device uint32, flat, n_cw_words entries; frame f starts at
+ *              desc[f].cw_offset.
+ *   params     order must be GRAND_ORDER_QAM_NNE; params->M is ignored (each
+ *              frame has its own); S' = min(params->S, L) per frame.
+ * Errors as for grand_decode_batch. A descriptor with an unknown code, an
+ * unsupported M or a range outside the arrays is not decoded: its abandon
+ * flag is 3 and its queries 0 (checked on the device). */
+int grand_decode_mixed(const grand_code* const* codes, int n_codes, const grand_params* params,
+                       const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
+                       float N0, uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon,
+                       grand_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAND_H */

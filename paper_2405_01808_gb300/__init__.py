@@ -1,0 +1,293 @@
+"""GB300 GRAND decoder: Python binding of the C ABI in include/grand.h.
+
+This module only marshals arguments: every step of the decoding path runs in
+the library's CUDA kernels (libgrand.so, built in-tree for sm_103a). PyTorch
+supplies device memory and streams. If the library is missing the calls raise:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "GrandError", "lib", "build", "polar_H", "Code", "Params", "demod", "decode_batch",
+    "decode_symbols", "decode_mixed", "frame_desc", "ORDER_HAMMING", "ORDER_QAM_NNE",
+    "LIK_THRESHOLD", "LIK_LITERAL",
+]
+
+ORDER_HAMMING = 0
+ORDER_QAM_NNE = 1
+LIK_THRESHOLD = 0
+LIK_LITERAL = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GrandError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().grand_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} ({status})")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("order", ctypes.c_int32), ("M", ctypes.c_int32), ("S", ctypes.c_int32),
+        ("max_weight", ctypes.c_int32), ("query_cap", ctypes.c_int64), ("lik_variant", ctypes.c_int32),
+        ("tiles", ctypes.c_int32 * 4),
+    ]
+
+    @classmethod
+    def make(cls, order=ORDER_QAM_NNE, M=16, S=10, max_weight=3, query_cap=1 << 20, lik_variant=LIK_THRESHOLD,
+             tiles=(0, 0, 0, 0)):
+        p = cls()
+        p.order, p.M, p.S, p.max_weight = int(order), int(M), int(S), int(max_weight)
+        p.query_cap, p.lik_variant = int(query_cap), int(lik_variant)
+        for i, t in enumerate(tiles):
+            p.tiles[i] = int(t)
+        return p
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("evaluated_checks", ctypes.c_uint64), ("hard_frames", ctypes.c_uint64),
+                ("search_useful", ctypes.c_uint64), ("prep_ms", ctypes.c_float), ("search_ms", ctypes.c_float)]
+
+
+FRAME_DESC_DTYPE = np.dtype([("code", "<i4"), ("M", "<i4"), ("sym_offset", "<i8"), ("cw_offset", "<i8")])
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    return _build.build(force=force, verbose=verbose)
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgrand.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libgrand.so is missing and could not be built")
+            L = ctypes.CDLL(_build.LIB)
+            P, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+            L.grand_version.restype = i32
+            L.grand_status_string.argtypes = [i32]
+            L.grand_status_string.restype = ctypes.c_char_p
+            L.grand_polar_H.argtypes = [i32, i32, ctypes.c_double, P, P]
+            L.grand_code_create.argtypes = [P, i32, i32, ctypes.POINTER(P)]
+            L.grand_code_destroy.argtypes = [P]
+            L.grand_code_info.argtypes = [P, P, P]
+            L.grand_demod.argtypes = [P, i64, i32, i32, ctypes.c_float, i32, P, P, P, P, P, i32, P]
+            L.grand_decode_batch.argtypes = [P, P, P, P, P, P, i64, P, P, P, P, P]
+            L.grand_decode_symbols.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, P, P]
+            L.grand_decode_mixed.argtypes = [P, i32, P, P, i64, P, i64, ctypes.c_float, P, i64, P, P, P, P]
+            for name in ("grand_polar_H", "grand_code_create", "grand_code_destroy", "grand_code_info",
+                         "grand_demod", "grand_decode_batch", "grand_decode_symbols", "grand_decode_mixed"):
+                getattr(L, name).restype = i32
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise GrandError(rc, where)
+
+
+def polar_H(N: int, K: int, design_snr_db: float = 0.0):
+    """Parity-check matrix (N-K, N/32) uint32 and frozen set of the polar code."""
+    H = np.zeros((N - K, N // 32), dtype=np.uint32)
+    frozen = np.zeros(N - K, dtype=np.int32)
+    _check(lib().grand_polar_H(N, K, float(design_snr_db), H.ctypes.data, frozen.ctypes.data), "grand_polar_H")
+    return H, frozen
+
+
+def H_from_dense(H: np.ndarray) -> np.ndarray:
+    """(R, N) 0/1 matrix -> (R, N/32) packed rows."""
+    H = np.asarray(H, dtype=np.uint64)
+    R, N = H.shape
+    sh = np.arange(32, dtype=np.uint64)
+    return (H.reshape(R, N // 32, 32) << sh).sum(axis=2).astype(np.uint32)
+
+
+class Code:
+    """A code object (column-packed H on the current CUDA device)."""
+
+    def __init__(self, H_packed: np.ndarray, N: int, K: int):
+        H_packed = np.ascontiguousarray(H_packed, dtype=np.uint32)
+        if H_packed.shape != (N - K, N // 32):
+            raise ValueError("H must be (N-K, N/32) packed rows")
+        h = ctypes.c_void_p()
+        _check(lib().grand_code_create(H_packed.ctypes.data, N, K, ctypes.byref(h)), "grand_code_create")
+        self._h = h
+        self.N, self.K = N, K
+
+    @classmethod
+    def polar(cls, N: int, K: int, design_snr_db: float = 0.0) -> "Code":
+        H, _ = polar_H(N, K, design_snr_db)
+        return cls(H, N, K)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("code was closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().grand_code_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("tensors must live on the CUDA device")
+        if t is not None and not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+
+
+def demod(symbols, M: int, N: int, N0: float = 1.0, lik_variant: int = LIK_THRESHOLD, outputs=None, stream=None):
+    """grand_demod. symbols: complex64 (F, L) for QAM, float32 (F, N) for BPSK."""
+    import torch
+
+    _require_cuda(symbols)
+    F = symbols.shape[0]
+    if M == 2:
+        L = N
+        sym = symbols
+    else:
+        L = symbols.shape[1]
+        sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
+    dev = symbols.device
+    if outputs is None:
+        outputs = {"y": torch.empty((F, N // 32), dtype=torch.int32, device=dev)}
+        if M == 2:
+            outputs["nmask"] = torch.empty((F, N), dtype=torch.uint8, device=dev)
+        else:
+            outputs.update({
+                "hard_idx": torch.empty((F, L), dtype=torch.int16, device=dev),
+                "key": torch.empty((F, L), dtype=torch.int32, device=dev),
+                "nmask": torch.empty((F, L), dtype=torch.uint8, device=dev),
+                "rel": torch.empty((F, L), dtype=torch.float32, device=dev),
+            })
+    o = outputs
+    _require_cuda(*o.values())
+    rc = lib().grand_demod(_ptr(sym), F, L, M, float(N0), int(lik_variant), _ptr(o.get("hard_idx")), _ptr(o.get("key")),
+                           _ptr(o.get("nmask")), _ptr(o.get("rel")), _ptr(o.get("y")), N, _stream(stream))
+    _check(rc, "grand_demod")
+    return o
+
+
+def _outputs(F, N, dev, cw=None, queries=None, abandon=None):
+    import torch
+
+    if cw is None:
+        cw = torch.empty((F, N // 32), dtype=torch.int32, device=dev)
+    if queries is None:
+        queries = torch.empty(F, dtype=torch.int32, device=dev)
+    if abandon is None:
+        abandon = torch.empty(F, dtype=torch.uint8, device=dev)
+    return cw, queries, abandon
+
+
+def _result(cw, queries, abandon, st, want_stats):
+    r = {"cw": cw, "queries": queries, "abandon": abandon}
+    if want_stats:
+        r["evaluated_checks"] = int(st.evaluated_checks)
+        r["hard_frames"] = int(st.hard_frames)
+        r["search_useful"] = int(st.search_useful)
+        r["prep_ms"] = float(st.prep_ms)
+        r["search_ms"] = float(st.search_ms)
+    return r
+
+
+def decode_batch(code: Code, params: Params, y, hard_idx=None, key=None, nmask=None, cw=None, queries=None,
+                 abandon=None, stats: bool = False, stream=None):
+    """grand_decode_batch on demodulated frames (outputs of `demod`)."""
+    _require_cuda(y, hard_idx, key, nmask)
+    F = y.shape[0]
+    cw, queries, abandon = _outputs(F, code.N, y.device, cw, queries, abandon)
+    st = Stats()
+    rc = lib().grand_decode_batch(code.handle, ctypes.byref(params), _ptr(hard_idx), _ptr(key), _ptr(nmask), _ptr(y), F,
+                                  _ptr(cw), _ptr(queries), _ptr(abandon), ctypes.byref(st) if stats else None,
+                                  _stream(stream))
+    _check(rc, "grand_decode_batch")
+    return _result(cw, queries, abandon, st, stats)
+
+
+def decode_symbols(code: Code, params: Params, symbols, N0: float = 1.0, cw=None, queries=None, abandon=None,
+                   stats: bool = False, stream=None):
+    """grand_decode_symbols: demodulate and decode in one pass."""
+    import torch
+
+    _require_cuda(symbols)
+    F = symbols.shape[0]
+    sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
+    cw, queries, abandon = _outputs(F, code.N, symbols.device, cw, queries, abandon)
+    st = Stats()
+    rc = lib().grand_decode_symbols(code.handle, ctypes.byref(params), _ptr(sym), F, float(N0), _ptr(cw),
+                                    _ptr(queries), _ptr(abandon), ctypes.byref(st) if stats else None, _stream(stream))
+    _check(rc, "grand_decode_symbols")
+    return _result(cw, queries, abandon, st, stats)
+
+
+def frame_desc(code_idx, M, sym_offset, cw_offset) -> np.ndarray:
+    d = np.zeros(len(code_idx), dtype=FRAME_DESC_DTYPE)
+    d["code"], d["M"], d["sym_offset"], d["cw_offset"] = code_idx, M, sym_offset, cw_offset
+    return d
+
+
+def decode_mixed(codes, params: Params, desc, symbols, n_cw_words: int, N0: float = 1.0, cw=None, queries=None,
+                 abandon=None, stats: bool = False, stream=None):
+    """grand_decode_mixed. desc: device uint8 tensor holding FRAME_DESC_DTYPE records."""
+    import torch
+
+    _require_cuda(desc, symbols)
+    F = desc.numel() // FRAME_DESC_DTYPE.itemsize
+    sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
+    n_sym = symbols.numel() if symbols.is_complex() else symbols.numel() // 2
+    dev = symbols.device
+    if cw is None:
+        cw = torch.empty(n_cw_words, dtype=torch.int32, device=dev)
+    if queries is None:
+        queries = torch.empty(F, dtype=torch.int32, device=dev)
+    if abandon is None:
+        abandon = torch.empty(F, dtype=torch.uint8, device=dev)
+    arr = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
+    st = Stats()
+    rc = lib().grand_decode_mixed(arr, len(codes), ctypes.byref(params), _ptr(desc), F, _ptr(sym), n_sym, float(N0),
+                                  _ptr(cw), n_cw_words, _ptr(queries), _ptr(abandon),
+                                  ctypes.byref(st) if stats else None, _stream(stream))
+    _check(rc, "grand_decode_mixed")
+    return _result(cw, queries, abandon, st, stats)

@@ -1,0 +1,1314 @@
+// GRAND decoder kernels for sm_103a and the C ABI entry points.
+//
+// Stages of one decode call (Alg. 2 of the paper):
+//   k_prep    one warp per frame: demodulation + likelihood + neighbours
+//             (Step 1), hard word y and base syndrome s0 = H y, selection of
+//             the S' least reliable symbols (Steps 2-3), the syndrome deltas
+//             of their alternatives (Step 4), and the first TEP weights in
+//             canonical order (Step 5). Most frames finish here.
+//   k_search  persistent CTAs pull the unfinished frames from a work queue
+//             and test the rest of the TEP space in parallel (Step 5): the S'
+//             ranks are split into a low group A and a high group B, every
+//             valid alternative assignment of each group gets its partial
+//             syndrome, and a TEP (a, b) is a codeword iff
+//                 s0 ^ D_A(a) == D_B(b)            (all syndrome words).
+//             Lanes hold A entries in registers, B entries are broadcast from
+//             shared memory, and the first syndrome word is compared with one
+//             integer compare per TEP; equal first words are verified on all
+//             words. Tiles are visited in order of their lightest TEP so a
+//             frame stops after the weight of its first hit.
+//   k_ab      bit-level GRAND-AB (Sec. I), one warp per frame.
+//   k_demod   the public demodulation call (per-symbol outputs).
+#include <stdio.h>
+
+#include <vector>
+
+#include "device_common.cuh"
+
+namespace grand {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------
+// Launch-wide parameters
+// ---------------------------------------------------------------------------
+struct QamConst {
+  float q[5];      // 256/d rounded to float, index m = log2(M)/2
+  float inv_d[5];  // 1/d rounded to float
+};
+
+struct PrepArgs {
+  // fused path: received symbols; else the demodulated arrays
+  const float2* symbols;
+  const uint16_t* hard_idx;
+  const uint32_t* key;
+  const uint8_t* nmask;
+  const uint32_t* y_in;
+  const grand_frame_desc* desc;  // NULL: uniform batch
+  int64_t n_symbols;             // mixed: length of the flat symbol array
+  int64_t n_cw_words;            // mixed: length of the flat output array
+  const CodeDev* codes;          // device table
+  int n_codes;
+  int64_t n_frames;
+  int M;                         // uniform batch
+  int S;
+  int lik;
+  int w0;
+  int Lmax;
+  int Wmax;
+  int64_t cap;
+  QamConst qc;
+  uint32_t* cw;
+  uint32_t* queries;
+  uint8_t* abandon;
+  FrameRec* recs;
+  Scratch* scr;
+};
+
+struct SearchArgs {
+  const FrameRec* recs;
+  const CodeDev* codes;
+  Scratch* scr;
+  int64_t cap;
+  int split;       // 0 = automatic (S'/2)
+  int tabA, tabB;  // table capacities
+  int max_tiles;
+  int Wmax;
+  uint32_t* cw;
+  uint32_t* queries;
+  uint8_t* abandon;
+};
+
+// ---------------------------------------------------------------------------
+// Per-frame preparation (one warp per frame)
+// ---------------------------------------------------------------------------
+struct PrepSmem {
+  uint32_t* key;    // [Lmax]
+  uint32_t* info;   // [Lmax]
+  uint32_t* y;      // [32]
+  uint32_t* delta;  // [kSMax][3][Wmax]
+  uint32_t* E;      // [kEStride^2]
+  uint8_t* ex;      // [kSMax]
+  uint16_t* pos;    // [kSMax][2]
+};
+
+__host__ __device__ inline size_t prep_warp_bytes(int Lmax, int Wmax) {
+  size_t words = 2 * (size_t)Lmax + 32 + (size_t)kSMax * 3 * Wmax + kEStride * kEStride + kSMax / 4 + 1 + kSMax;
+  return ((words * 4) + 15) & ~(size_t)15;
+}
+
+__device__ inline PrepSmem prep_smem(char* base, int Lmax, int Wmax) {
+  PrepSmem s;
+  uint32_t* p = reinterpret_cast<uint32_t*>(base);
+  s.key = p; p += Lmax;
+  s.info = p; p += Lmax;
+  s.y = p; p += 32;
+  s.delta = p; p += kSMax * 3 * Wmax;
+  s.E = p; p += kEStride * kEStride;
+  s.pos = reinterpret_cast<uint16_t*>(p); p += kSMax;
+  s.ex = reinterpret_cast<uint8_t*>(p);
+  return s;
+}
+
+// Word 0..W-1 syndrome of the TEP given by `code` (ranks with nonzero digit),
+// XORed into acc.
+__device__ __forceinline__ void xor_delta(uint32_t* acc, const uint32_t* delta, int W, int Sp, uint32_t code) {
+  for (int r = 0; r < Sp; ++r) {
+    const uint32_t c = (code >> (2 * r)) & 3u;
+    if (c) {
+      const uint32_t* d = delta + ((size_t)r * 3 + (c - 1)) * W;
+      for (int w = 0; w < W; ++w) acc[w] ^= d[w];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_prep(PrepArgs a) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp_in_block = threadIdx.x >> 5;
+  const int warps_per_block = blockDim.x >> 5;
+  PrepSmem sm = prep_smem(smem_raw + warp_in_block * prep_warp_bytes(a.Lmax, a.Wmax), a.Lmax, a.Wmax);
+  const int64_t gwarp = (int64_t)blockIdx.x * warps_per_block + warp_in_block;
+  const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
+  unsigned long long evaluated = 0;
+
+  for (int64_t f = gwarp; f < a.n_frames; f += nwarps) {
+    // --- frame parameters -------------------------------------------------
+    int code_id = 0, M = a.M;
+    int64_t sym_off, cw_off;
+    bool bad_desc = false;
+    if (a.desc) {
+      const grand_frame_desc d = a.desc[f];
+      code_id = d.code;
+      M = d.M;
+      sym_off = d.sym_offset;
+      cw_off = d.cw_offset;
+      bad_desc = code_id < 0 || code_id >= a.n_codes || !(M == 4 || M == 16 || M == 64 || M == 256) ||
+                 sym_off < 0 || cw_off < 0;
+      if (!bad_desc) {
+        const int mm = (31 - __clz(M)) >> 1;
+        const int NN = a.codes[code_id].N;
+        const int LL = (NN + 2 * mm - 1) / (2 * mm);
+        bad_desc = sym_off + LL > a.n_symbols || cw_off + (NN >> 5) > a.n_cw_words;
+      }
+    }
+    if (bad_desc) {
+      if (lane == 0) {
+        a.queries[f] = 0;
+        a.abandon[f] = 3;
+      }
+      continue;
+    }
+    const CodeDev code = a.codes[code_id];
+    const int N = code.N, W = code.W, NW = N >> 5;
+    const int m = (31 - __clz(M)) >> 1;
+    const int side = 1 << m;
+    const int L = (N + 2 * m - 1) / (2 * m);
+    if (!a.desc) {
+      sym_off = f * (int64_t)L;
+      cw_off = f * (int64_t)NW;
+    }
+    const int Sp = a.S < L ? a.S : L;
+
+    // --- Step 1: demodulation, hard word -----------------------------------
+    if (lane < NW) sm.y[lane] = a.y_in && !a.symbols ? a.y_in[f * (int64_t)NW + lane] : 0u;
+    __syncwarp();
+    bool nonfinite = false;
+    for (int i = lane; i < L; i += 32) {
+      uint32_t key, info;
+      if (a.symbols) {
+        float2 s = a.symbols[sym_off + i];
+        const bool nf = !(isfinite(s.x) && isfinite(s.y));
+        if (nf) s = make_float2(0.0f, 0.0f);
+        nonfinite |= nf;
+        const AxisDemod I = demod_axis_q(s.x, a.qc.q[m], side, a.lik);
+        const AxisDemod Q = demod_axis_q(s.y, a.qc.q[m], side, a.lik);
+        key = (uint32_t)I.dq * (uint32_t)I.dq + (uint32_t)Q.dq * (uint32_t)Q.dq;
+        info = pack_info(I.level, Q.level, make_nmask(I, Q, nf));
+        // Gray label, MSB first, into the packed hard word
+        const uint32_t label = ((uint32_t)gray_code(I.level) << m) | (uint32_t)gray_code(Q.level);
+        const uint32_t rl = __brev(label) >> (32 - 2 * m);  // bit k = label bit (2m-1-k)
+        const int p0 = 2 * m * i;
+        const int wd = p0 >> 5, sh = p0 & 31;
+        const uint32_t lo = rl << sh;
+        const uint32_t hi = sh ? (rl >> (32 - sh)) : 0u;
+        if (wd < NW) atomicOr(&sm.y[wd], lo);
+        if (hi && wd + 1 < NW) atomicOr(&sm.y[wd + 1], hi);
+      } else {
+        const int64_t o = f * (int64_t)L + i;
+        key = a.key[o];
+        const uint32_t hidx = a.hard_idx[o];
+        const uint32_t nm = a.nmask[o];
+        nonfinite |= (nm & 128u) != 0;
+        info = pack_info(hidx >> 8, hidx & 0xFF, nm);
+      }
+      sm.key[i] = key;
+      sm.info[i] = info;
+    }
+    nonfinite = __any_sync(kFull, nonfinite);
+    __syncwarp();
+    // bits beyond N never set: padding positions were dropped above
+    if (nonfinite) {
+      if (lane < NW) a.cw[cw_off + lane] = sm.y[lane];
+      if (lane == 0) {
+        a.queries[f] = 0;
+        a.abandon[f] = 2;
+      }
+      __syncwarp();
+      continue;
+    }
+
+    // --- base syndrome s0 = H y (XOR of the columns where y_j = 1) --------
+    uint32_t s0[kWMax];
+#pragma unroll
+    for (int w = 0; w < kWMax; ++w) s0[w] = 0;
+    for (int j = lane; j < N; j += 32) {
+      if ((sm.y[j >> 5] >> (j & 31)) & 1u) {
+        const uint32_t* col = code.hcol + (size_t)j * W;
+#pragma unroll
+        for (int w = 0; w < kWMax; ++w)
+          if (w < W) s0[w] ^= __ldg(col + w);
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < kWMax; ++w) {
+      if (w < W) {
+        uint32_t v = s0[w];
+        for (int o = 16; o; o >>= 1) v ^= __shfl_xor_sync(kFull, v, o);
+        s0[w] = v;
+      }
+    }
+
+    // --- Steps 2-3: the S' least reliable symbols, by (key, index) ---------
+    int my_sel = -1;
+    for (int r = 0; r < Sp; ++r) {
+      uint32_t best_k = 0xFFFFFFFFu, best_i = 0xFFFFFFFFu;
+      for (int i = lane; i < L; i += 32) {
+        const uint32_t k = sm.key[i];
+        if (k < best_k) { best_k = k; best_i = (uint32_t)i; }
+      }
+      const uint32_t kmin = __reduce_min_sync(kFull, best_k);
+      const uint32_t imin = __reduce_min_sync(kFull, best_k == kmin ? best_i : 0xFFFFFFFFu);
+      if (lane == (int)(imin & 31u)) sm.key[imin] = 0xFFFFFFFFu;  // keys are < 2^31
+      if (lane == r) my_sel = (int)imin;
+      __syncwarp();
+    }
+
+    // --- Step 4: alternatives and their syndrome deltas --------------------
+    if (lane < Sp) {
+      const int i = my_sel;
+      const uint32_t info = sm.info[i];
+      const int lI = info & 0xFF, lQ = (info >> 8) & 0xFF;
+      const uint32_t nm = (info >> 16) & 0xFF;
+      const bool exI = nm & 1u, exQ = nm & 2u;
+      const int dI = (nm & 8u) ? 1 : -1, dQ = (nm & 16u) ? 1 : -1;
+      const uint16_t pI = exI ? flip_pos_I(i, m, lI, dI, N) : kNoPos;
+      const uint16_t pQ = exQ ? flip_pos_Q(i, m, lQ, dQ, N) : kNoPos;
+      sm.pos[2 * lane] = pI;
+      sm.pos[2 * lane + 1] = pQ;
+      sm.ex[lane] = (uint8_t)((exI ? 1 : 0) | (exQ ? 2 : 0) | (exI && exQ ? 4 : 0));
+      uint32_t* dh = sm.delta + ((size_t)lane * 3 + 0) * W;
+      uint32_t* dv = sm.delta + ((size_t)lane * 3 + 1) * W;
+      uint32_t* dd = sm.delta + ((size_t)lane * 3 + 2) * W;
+      for (int w = 0; w < W; ++w) {
+        const uint32_t h = pI != kNoPos ? __ldg(code.hcol + (size_t)pI * W + w) : 0u;
+        const uint32_t v = pQ != kNoPos ? __ldg(code.hcol + (size_t)pQ * W + w) : 0u;
+        dh[w] = h;
+        dv[w] = v;
+        dd[w] = h ^ v;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) esp_table(sm.ex, Sp, sm.E);
+    __syncwarp();
+    const uint32_t total = esp_total(sm.E, Sp);
+
+    // --- Step 5 (first part): small spaces completely, else light weights --
+    uint32_t best_rank = 0xFFFFFFFFu, best_code = 0;
+    int w_done = -1;
+    if (Sp <= 6) {
+      // the whole product space, every lane a stride of assignments
+      const uint32_t n_all = 1u << (2 * Sp);
+      for (uint32_t c = lane; c < n_all; c += 32) {
+        bool valid = true;
+        for (int r = 0; r < Sp; ++r) {
+          const uint32_t d = (c >> (2 * r)) & 3u;
+          if (d && !((sm.ex[r] >> (d - 1)) & 1u)) valid = false;
+        }
+        if (!valid) continue;
+        ++evaluated;
+        uint32_t z[kWMax];
+        for (int w = 0; w < W; ++w) z[w] = s0[w];
+        xor_delta(z, sm.delta, W, Sp, c);
+        uint32_t orr = 0;
+        for (int w = 0; w < W; ++w) orr |= z[w];
+        if (orr == 0) {
+          const uint32_t rk = tep_rank(sm.E, Sp, sm.ex, c);
+          if (rk < best_rank) { best_rank = rk; best_code = c; }
+        }
+      }
+      w_done = Sp;
+    } else {
+      const int wmax = a.w0 < Sp ? a.w0 : Sp;
+      for (int w = 0; w <= wmax && best_rank == 0xFFFFFFFFu; ++w) {
+        const uint32_t nsets = binom16(Sp, w);
+        for (uint32_t base = 0; base < nsets; base += 32) {
+          const uint32_t cidx = base + lane;
+          uint32_t hit_code = 0;
+          bool hit = false;
+          if (cidx < nsets) {
+            // colex unranking of the altered rank set
+            int P[kSMax];
+            uint32_t rem = cidx;
+            int p = Sp - 1;
+            for (int j = w; j >= 1; --j) {
+              while (binom16(p, j) > rem) --p;
+              P[j - 1] = p;
+              rem -= binom16(p, j);
+              --p;
+            }
+            // alternatives in base-3 order, least significant digit first
+            int dig[kSMax];
+            for (int j = 0; j < w; ++j) dig[j] = 0;
+            uint32_t n_alpha = 1;
+            for (int j = 0; j < w; ++j) n_alpha *= 3;
+            for (uint32_t al = 0; al < n_alpha; ++al) {
+              bool valid = true;
+              uint32_t code = 0;
+              for (int j = 0; j < w; ++j) {
+                if (!((sm.ex[P[j]] >> dig[j]) & 1u)) valid = false;
+                code |= (uint32_t)(dig[j] + 1) << (2 * P[j]);
+              }
+              if (valid) {
+                ++evaluated;
+                uint32_t z0 = s0[0];
+                for (int j = 0; j < w; ++j) z0 ^= sm.delta[((size_t)P[j] * 3 + dig[j]) * W];
+                if (z0 == 0) {
+                  uint32_t z[kWMax];
+                  for (int ww = 0; ww < W; ++ww) z[ww] = s0[ww];
+                  xor_delta(z, sm.delta, W, Sp, code);
+                  uint32_t orr = 0;
+                  for (int ww = 0; ww < W; ++ww) orr |= z[ww];
+                  if (orr == 0) {
+                    hit = true;
+                    hit_code = code;
+                    break;
+                  }
+                }
+              }
+              for (int j = 0; j < w; ++j) {  // odometer
+                if (++dig[j] < 3) break;
+                dig[j] = 0;
+              }
+            }
+          }
+          const unsigned hb = __ballot_sync(kFull, hit);
+          if (hb) {
+            const int src = __ffs(hb) - 1;
+            best_code = __shfl_sync(kFull, hit_code, src);
+            best_rank = tep_rank(sm.E, Sp, sm.ex, best_code);
+            break;
+          }
+        }
+        w_done = w;
+      }
+    }
+    // warp-wide best (only the full-space branch leaves lane-local values)
+    {
+      const uint32_t br = __reduce_min_sync(kFull, best_rank);
+      const unsigned who = __ballot_sync(kFull, best_rank == br);
+      best_code = __shfl_sync(kFull, best_code, __ffs(who) - 1);
+      best_rank = br;
+    }
+    uint32_t done_count = 0;  // valid TEPs with at most w_done altered ranks
+    for (int v = 0; v <= w_done; ++v) done_count += sm.E[Sp * kEStride + v];
+
+    const bool resolved = best_rank != 0xFFFFFFFFu || w_done >= Sp || (uint64_t)done_count >= (uint64_t)a.cap;
+    if (resolved) {
+      uint32_t q;
+      uint8_t ab;
+      bool flip = false;
+      if (best_rank != 0xFFFFFFFFu && (uint64_t)best_rank <= (uint64_t)a.cap) {
+        q = best_rank;
+        ab = 0;
+        flip = true;
+      } else {
+        q = (uint32_t)((uint64_t)total < (uint64_t)a.cap ? total : a.cap);
+        ab = 1;
+      }
+      if (flip && lane == 0) {
+        for (int r = 0; r < Sp; ++r) {
+          const uint32_t c = (best_code >> (2 * r)) & 3u;
+          if (c & 1u) { const uint16_t p = sm.pos[2 * r]; if (p != kNoPos) sm.y[p >> 5] ^= 1u << (p & 31); }
+          if (c & 2u) { const uint16_t p = sm.pos[2 * r + 1]; if (p != kNoPos) sm.y[p >> 5] ^= 1u << (p & 31); }
+        }
+      }
+      __syncwarp();
+      if (lane < NW) a.cw[cw_off + lane] = sm.y[lane];
+      if (lane == 0) {
+        a.queries[f] = q;
+        a.abandon[f] = ab;
+      }
+    } else {
+      // hand the frame to the search stage
+      unsigned slot = 0;
+      if (lane == 0) slot = atomicAdd(&a.scr->n_hard, 1u);
+      slot = __shfl_sync(kFull, slot, 0);
+      FrameRec* rec = a.recs + slot;
+      if (lane < NW) a.cw[cw_off + lane] = sm.y[lane];
+      if (lane < W) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int w = 0; w < kWMax; ++w)
+          if (w == lane) v = s0[w];
+        rec->s0[lane] = v;
+      }
+      if (lane < Sp) {
+        rec->pos[lane][0] = sm.pos[2 * lane];
+        rec->pos[lane][1] = sm.pos[2 * lane + 1];
+        rec->ex[lane] = sm.ex[lane];
+      }
+      if (lane == 0) {
+        rec->frame = (uint32_t)f;
+        rec->code = (uint16_t)code_id;
+        rec->sp = (uint8_t)Sp;
+        rec->w_done = (uint8_t)w_done;
+        rec->cw_off = cw_off;
+      }
+    }
+    __syncwarp();
+  }
+  // stats
+  for (int o = 16; o; o >>= 1) evaluated += __shfl_xor_sync(kFull, evaluated, o);
+  if (lane == 0 && evaluated) atomicAdd(&a.scr->evaluated, evaluated);
+}
+
+// ---------------------------------------------------------------------------
+// Parallel search over the remaining TEP space (persistent CTAs)
+// ---------------------------------------------------------------------------
+constexpr int kRowsPerLane = 8;                 // A entries held per lane
+constexpr int kTileRows = 32 * kRowsPerLane;    // A entries per tile
+constexpr int kTileCols = 64;                   // B entries per tile
+constexpr uint32_t kPadA = 0xA5A5A5A5u;
+constexpr uint32_t kPadB = 0x5A5A5A5Au;
+
+// 64 first-word compares: lane-held q[0..7] against 8 broadcast B words.
+// One predicate-accumulating integer compare per pair; returns nonzero if any
+// pair is equal.
+__device__ __forceinline__ uint32_t any_equal_8x8(const uint32_t (&q)[kRowsPerLane], const uint4& z0,
+                                                   const uint4& z1) {
+  uint32_t f;
+#define G_SETP(p, a, b) "setp.eq.u32 " p ", " a ", " b ";\n\t"
+#define G_SETO(p, a, b) "setp.eq.or.u32 " p ", " a ", " b ", " p ";\n\t"
+#define G_ROW_OR(b) G_SETO("p0", "%1", b) G_SETO("p1", "%2", b) G_SETO("p2", "%3", b) G_SETO("p3", "%4", b) \
+  G_SETO("p0", "%5", b) G_SETO("p1", "%6", b) G_SETO("p2", "%7", b) G_SETO("p3", "%8", b)
+  asm("{\n\t.reg .pred p0, p1, p2, p3;\n\t"
+      G_SETP("p0", "%1", "%9") G_SETP("p1", "%2", "%9") G_SETP("p2", "%3", "%9") G_SETP("p3", "%4", "%9")
+      G_SETO("p0", "%5", "%9") G_SETO("p1", "%6", "%9") G_SETO("p2", "%7", "%9") G_SETO("p3", "%8", "%9")
+      G_ROW_OR("%10") G_ROW_OR("%11") G_ROW_OR("%12") G_ROW_OR("%13") G_ROW_OR("%14") G_ROW_OR("%15")
+      G_ROW_OR("%16")
+      "or.pred p0, p0, p1;\n\t"
+      "or.pred p2, p2, p3;\n\t"
+      "or.pred p0, p0, p2;\n\t"
+      "selp.u32 %0, 1, 0, p0;\n\t}"
+      : "=r"(f)
+      : "r"(q[0]), "r"(q[1]), "r"(q[2]), "r"(q[3]), "r"(q[4]), "r"(q[5]), "r"(q[6]), "r"(q[7]), "r"(z0.x),
+        "r"(z0.y), "r"(z0.z), "r"(z0.w), "r"(z1.x), "r"(z1.y), "r"(z1.z), "r"(z1.w));
+#undef G_ROW_OR
+#undef G_SETO
+#undef G_SETP
+  return f;
+}
+
+struct SearchSmem {
+  uint32_t* Aq;      // [tabA + kTileRows] first word of s0 ^ D_A
+  uint32_t* Bz;      // [tabB + kTileCols] first word of D_B
+  uint16_t* Acode;   // [tabA]
+  uint16_t* Bcode;   // [tabB]
+  uint16_t* tiles;   // [max_tiles]
+  uint32_t* delta;   // [kSMax][3][Wmax]
+  uint32_t* E;       // [kEStride^2]
+  uint32_t* s0;      // [Wmax]
+};
+
+__host__ __device__ inline size_t search_smem_bytes(int tabA, int tabB, int max_tiles, int Wmax) {
+  size_t b = 0;
+  b += 4 * (size_t)(tabA + kTileRows);
+  b += 4 * (size_t)(tabB + kTileCols);
+  b += 2 * (size_t)tabA + 2 * (size_t)tabB;
+  b += 2 * (size_t)max_tiles;
+  b = (b + 15) & ~(size_t)15;
+  b += 4 * (size_t)kSMax * 3 * Wmax + 4 * kEStride * kEStride + 4 * (size_t)Wmax;
+  return (b + 15) & ~(size_t)15;
+}
+
+__device__ inline SearchSmem search_smem(char* base, int tabA, int tabB, int max_tiles, int Wmax) {
+  SearchSmem s;
+  char* p = base;
+  s.Aq = reinterpret_cast<uint32_t*>(p); p += 4 * (size_t)(tabA + kTileRows);
+  s.Bz = reinterpret_cast<uint32_t*>(p); p += 4 * (size_t)(tabB + kTileCols);
+  s.Acode = reinterpret_cast<uint16_t*>(p); p += 2 * (size_t)tabA;
+  s.Bcode = reinterpret_cast<uint16_t*>(p); p += 2 * (size_t)tabB;
+  s.tiles = reinterpret_cast<uint16_t*>(p); p += 2 * (size_t)max_tiles;
+  p = base + (((size_t)(p - base) + 15) & ~(size_t)15);
+  s.delta = reinterpret_cast<uint32_t*>(p); p += 4 * (size_t)kSMax * 3 * Wmax;
+  s.E = reinterpret_cast<uint32_t*>(p); p += 4 * kEStride * kEStride;
+  s.s0 = reinterpret_cast<uint32_t*>(p);
+  return s;
+}
+
+// Build one side's table: every valid alternative assignment of ranks
+// [r0, r0 + n) with its first syndrome word (XOR of the deltas, plus `seed`),
+// bucketed by the number of altered ranks. cnt/off are [kSideMax + 2] smem.
+__device__ void build_side(const uint32_t* delta, int W, const uint8_t* ex, int r0, int n, uint32_t seed,
+                           uint32_t* outq, uint16_t* outcode, unsigned* cnt, unsigned* off, int total) {
+  // radix of rank r: 1 + k_r, choices 0, then the existing alternatives
+  for (int i = threadIdx.x; i <= kSideMax + 1; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      int rem = e, wgt = 0;
+      uint32_t q = seed;
+      uint32_t code = 0;
+      for (int j = 0; j < n; ++j) {
+        const uint32_t exj = ex[r0 + j] & 7u;
+        const int radix = 1 + __popc(exj);
+        const int dgt = rem % radix;
+        rem /= radix;
+        if (dgt) {
+          // dgt-th existing alternative (1-based) -> its code 1..3
+          uint32_t bits = exj;
+          for (int t = 1; t < dgt; ++t) bits &= bits - 1;
+          const uint32_t c = (uint32_t)__ffs(bits);
+          code |= c << (2 * j);
+          q ^= delta[((size_t)(r0 + j) * 3 + (c - 1)) * W];
+          ++wgt;
+        }
+      }
+      if (pass == 0) {
+        atomicAdd(&cnt[wgt], 1u);
+      } else {
+        const unsigned slot = atomicAdd(&off[wgt], 1u);
+        outq[slot] = q;
+        outcode[slot] = (uint16_t)code;
+      }
+    }
+    __syncthreads();
+    if (pass == 0) {
+      if (threadIdx.x == 0) {
+        unsigned acc = 0;
+        for (int w = 0; w <= kSideMax + 1; ++w) {
+          off[w] = acc;
+          acc += cnt[w];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// weight (number of altered ranks) of table entry i from the bucket counts
+__device__ __forceinline__ int side_weight(const unsigned* cnt, unsigned i) {
+  int w = 0;
+  unsigned acc = cnt[0];
+  while (i >= acc && w < kSideMax) acc += cnt[++w];
+  return w;
+}
+
+__global__ void __launch_bounds__(256) k_search(SearchArgs a) {
+  extern __shared__ __align__(16) char smem_raw[];
+  SearchSmem sm = search_smem(smem_raw, a.tabA, a.tabB, a.max_tiles, a.Wmax);
+  __shared__ unsigned s_frame;
+  __shared__ unsigned cntA[kSideMax + 2], offA[kSideMax + 2], cntB[kSideMax + 2], offB[kSideMax + 2];
+  __shared__ unsigned s_tile_cnt[2 * kSMax + 2];
+  __shared__ unsigned s_n_tiles, s_tile_next;
+  __shared__ unsigned long long s_best;  // (rank << 32) | code
+  __shared__ int s_best_w;
+  __shared__ FrameRec s_rec;
+  __shared__ unsigned long long s_eval;
+  const int lane = threadIdx.x & 31;
+  const int n_hard = (int)*(volatile unsigned*)&a.scr->n_hard;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_frame = atomicAdd(&a.scr->next, 1u);
+    __syncthreads();
+    const unsigned fi = s_frame;
+    if (fi >= (unsigned)n_hard) break;
+    // --- load the frame ----------------------------------------------------
+    if (threadIdx.x < sizeof(FrameRec) / 8)
+      reinterpret_cast<unsigned long long*>(&s_rec)[threadIdx.x] =
+          reinterpret_cast<const unsigned long long*>(a.recs + fi)[threadIdx.x];
+    __syncthreads();
+    const CodeDev code = a.codes[s_rec.code];
+    const int W = code.W;
+    const int Sp = s_rec.sp;
+    const int split = (a.split > 0) ? max(Sp - kSideMax, min(a.split, kSideMax)) : (Sp >> 1);
+    const int nAr = split, nBr = Sp - split;
+    for (int t = threadIdx.x; t < Sp * 3 * W; t += blockDim.x) {
+      const int r = t / (3 * W), rem = t % (3 * W), alt = rem / W, w = rem % W;
+      const uint16_t pI = s_rec.pos[r][0], pQ = s_rec.pos[r][1];
+      const uint32_t h = (alt != 1 && pI != kNoPos) ? __ldg(code.hcol + (size_t)pI * W + w) : 0u;
+      const uint32_t v = (alt != 0 && pQ != kNoPos) ? __ldg(code.hcol + (size_t)pQ * W + w) : 0u;
+      sm.delta[t] = h ^ v;  // alt 0: h, 1: v, 2: h ^ v
+    }
+    if (threadIdx.x < W) sm.s0[threadIdx.x] = s_rec.s0[threadIdx.x];
+    if (threadIdx.x == 0) {
+      esp_table(s_rec.ex, Sp, sm.E);
+      s_best = ~0ull;
+      s_best_w = 127;
+      s_tile_next = 0;
+      s_eval = 0;
+    }
+    __syncthreads();
+    const uint32_t total = esp_total(sm.E, Sp);
+    // heaviest weight class that still holds a position <= cap
+    int w_cap = Sp;
+    {
+      uint64_t acc = 0;
+      for (int v = 0; v <= Sp; ++v) {
+        acc += sm.E[Sp * kEStride + v];
+        if (acc >= (uint64_t)a.cap) { w_cap = v; break; }
+      }
+    }
+    unsigned nA = 1, nB = 1;
+    for (int r = 0; r < nAr; ++r) nA *= 1u + __popc(s_rec.ex[r] & 7u);
+    for (int r = nAr; r < Sp; ++r) nB *= 1u + __popc(s_rec.ex[r] & 7u);
+    build_side(sm.delta, W, s_rec.ex, 0, nAr, sm.s0[0], sm.Aq, sm.Acode, cntA, offA, (int)nA);
+    build_side(sm.delta, W, s_rec.ex, nAr, nBr, 0u, sm.Bz, sm.Bcode, cntB, offB, (int)nB);
+    // pads (never a real entry): rows to a full tile, columns to a full tile
+    const unsigned nRB = (nA + kTileRows - 1) / kTileRows, nCB = (nB + kTileCols - 1) / kTileCols;
+    for (unsigned i = nA + threadIdx.x; i < nRB * kTileRows; i += blockDim.x) sm.Aq[i] = kPadA;
+    for (unsigned i = nB + threadIdx.x; i < nCB * kTileCols; i += blockDim.x) sm.Bz[i] = kPadB;
+    // --- tile list ordered by the lightest TEP of each tile ----------------
+    if (threadIdx.x < 2 * kSMax + 2) s_tile_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int w_done = s_rec.w_done;
+    const unsigned n_tiles_all = nRB * nCB;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (unsigned t = threadIdx.x; t < n_tiles_all; t += blockDim.x) {
+        const unsigned rb = t / nCB, cb = t % nCB;
+        const int minw = side_weight(cntA, rb * kTileRows) + side_weight(cntB, cb * kTileCols);
+        const int maxw = side_weight(cntA, min(nA, (rb + 1) * kTileRows) - 1) +
+                         side_weight(cntB, min(nB, (cb + 1) * kTileCols) - 1);
+        if (maxw <= w_done || minw > w_cap) continue;
+        if (pass == 0) {
+          atomicAdd(&s_tile_cnt[minw], 1u);
+        } else {
+          const unsigned slot = atomicAdd(&s_tile_cnt[minw], 1u);
+          sm.tiles[slot] = (uint16_t)((rb << 8) | cb);
+        }
+      }
+      __syncthreads();
+      if (pass == 0) {
+        if (threadIdx.x == 0) {
+          unsigned acc = 0;
+          for (int w = 0; w < 2 * kSMax + 2; ++w) {
+            const unsigned c = s_tile_cnt[w];
+            s_tile_cnt[w] = acc;
+            acc += c;
+          }
+          s_n_tiles = acc;
+        }
+        __syncthreads();
+      }
+    }
+    const unsigned n_tiles = s_n_tiles;
+
+    // --- the tile loop (one warp per tile) ---------------------------------
+    unsigned long long my_eval = 0;
+    for (;;) {
+      unsigned ti = 0;
+      if (lane == 0) ti = atomicAdd(&s_tile_next, 1u);
+      ti = __shfl_sync(kFull, ti, 0);
+      if (ti >= n_tiles) break;
+      const unsigned tile = sm.tiles[ti];
+      const unsigned rb = tile >> 8, cb = tile & 0xFF;
+      const unsigned row0 = rb * kTileRows, col0 = cb * kTileCols;
+      const int minw = side_weight(cntA, row0) + side_weight(cntB, col0);
+      if (minw > *(volatile int*)&s_best_w) break;  // tiles are sorted by minw
+      uint32_t q[kRowsPerLane];
+#pragma unroll
+      for (int t = 0; t < kRowsPerLane; ++t) q[t] = sm.Aq[row0 + lane + 32 * t];
+      const uint4* zb = reinterpret_cast<const uint4*>(sm.Bz + col0);
+      uint32_t any = 0;
+#pragma unroll 2
+      for (int g = 0; g < kTileCols / 8; ++g) any |= any_equal_8x8(q, zb[2 * g], zb[2 * g + 1]);
+      if (lane == 0) my_eval += (unsigned long long)(min(nA - row0, (unsigned)kTileRows)) *
+                                (unsigned long long)(min(nB - col0, (unsigned)kTileCols));
+      if (__any_sync(kFull, any)) {
+        // rare: locate the equal first words and verify every syndrome word
+        if (any) {
+          for (int t = 0; t < kRowsPerLane; ++t) {
+            const unsigned row = row0 + lane + 32 * t;
+            if (row >= nA) continue;
+            for (int j = 0; j < kTileCols; ++j) {
+              const unsigned col = col0 + j;
+              if (col >= nB || sm.Bz[col] != q[t]) continue;
+              const uint32_t c = (uint32_t)sm.Acode[row] | ((uint32_t)sm.Bcode[col] << (2 * nAr));
+              uint32_t orr = 0;
+              for (int w = 0; w < W; ++w) {
+                uint32_t z = sm.s0[w];
+                for (int r = 0; r < Sp; ++r) {
+                  const uint32_t d = (c >> (2 * r)) & 3u;
+                  if (d) z ^= sm.delta[((size_t)r * 3 + (d - 1)) * W + w];
+                }
+                orr |= z;
+              }
+              if (orr == 0) {
+                const uint32_t rk = tep_rank(sm.E, Sp, s_rec.ex, c);
+                atomicMin(&s_best, ((unsigned long long)rk << 32) | c);
+                atomicMin(&s_best_w, code_weight(c));
+              }
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    if (lane == 0 && my_eval) atomicAdd(&s_eval, my_eval);
+    __syncthreads();
+    // --- result ------------------------------------------------------------
+    if (threadIdx.x == 0) {
+      const unsigned f = s_rec.frame;
+      const unsigned long long best = s_best;
+      const uint32_t rk = (uint32_t)(best >> 32), c = (uint32_t)best;
+      if (best != ~0ull && (uint64_t)rk <= (uint64_t)a.cap) {
+        uint32_t* cw = a.cw + s_rec.cw_off;
+        for (int r = 0; r < Sp; ++r) {
+          const uint32_t d = (c >> (2 * r)) & 3u;
+          if (d & 1u) { const uint16_t p = s_rec.pos[r][0]; if (p != kNoPos) cw[p >> 5] ^= 1u << (p & 31); }
+          if (d & 2u) { const uint16_t p = s_rec.pos[r][1]; if (p != kNoPos) cw[p >> 5] ^= 1u << (p & 31); }
+        }
+        a.queries[f] = rk;
+        a.abandon[f] = 0;
+      } else {
+        a.queries[f] = (uint32_t)((uint64_t)total < (uint64_t)a.cap ? total : (uint64_t)a.cap);
+        a.abandon[f] = 1;
+      }
+      uint32_t done = 0;  // valid TEPs the preparation already tested
+      for (int v = 0; v <= w_done; ++v) done += sm.E[Sp * kEStride + v];
+      atomicAdd(&a.scr->evaluated, s_eval);
+      atomicAdd(&a.scr->search_useful, (unsigned long long)(a.queries[f] - done));
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Bit-level GRAND-AB: TEPs of 0..max_weight flipped bits in colex order
+// ---------------------------------------------------------------------------
+struct AbArgs {
+  const float* samples;   // fused: [n_frames][N] BPSK samples
+  const uint32_t* y_in;   // else: packed hard words
+  const uint8_t* nmask;   // optional: bit7 = non-finite sample
+  CodeDev code;
+  int64_t n_frames;
+  int max_weight;
+  int64_t cap;
+  uint32_t* cw;
+  uint32_t* queries;
+  uint8_t* abandon;
+  Scratch* scr;
+};
+
+__global__ void __launch_bounds__(128) k_ab(AbArgs a) {
+  __shared__ uint32_t s_y[4][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int N = a.code.N, W = a.code.W, NW = N >> 5;
+  uint32_t* y = s_y[wib];
+  unsigned long long evaluated = 0;
+  for (int64_t f = gwarp; f < a.n_frames; f += nwarps) {
+    bool nonfinite = false;
+    if (a.samples) {
+      for (int w = 0; w < NW; ++w) {
+        float v = a.samples[f * N + 32 * w + lane];
+        const bool nf = !isfinite(v);
+        nonfinite |= nf;
+        if (nf) v = 0.0f;
+        const unsigned b = __ballot_sync(kFull, v < 0.0f);
+        if (lane == 0) y[w] = b;
+      }
+    } else {
+      if (lane < NW) y[lane] = a.y_in[f * NW + lane];
+      if (a.nmask)
+        for (int j = lane; j < N; j += 32) nonfinite |= (a.nmask[f * N + j] & 128u) != 0;
+    }
+    nonfinite = __any_sync(kFull, nonfinite);
+    __syncwarp();
+    if (nonfinite) {
+      if (lane < NW) a.cw[f * NW + lane] = y[lane];
+      if (lane == 0) { a.queries[f] = 0; a.abandon[f] = 2; }
+      __syncwarp();
+      continue;
+    }
+    uint32_t s0[kWMax];
+#pragma unroll
+    for (int w = 0; w < kWMax; ++w) s0[w] = 0;
+    for (int j = lane; j < N; j += 32)
+      if ((y[j >> 5] >> (j & 31)) & 1u) {
+#pragma unroll
+        for (int w = 0; w < kWMax; ++w)
+          if (w < W) s0[w] ^= __ldg(a.code.hcol + (size_t)j * W + w);
+      }
+#pragma unroll
+    for (int w = 0; w < kWMax; ++w)
+      if (w < W) {
+        uint32_t v = s0[w];
+        for (int o = 16; o; o >>= 1) v ^= __shfl_xor_sync(kFull, v, o);
+        s0[w] = v;
+      }
+    // classes in order; position within the order = start(w) + colex + 1
+    uint64_t start = 0;
+    bool found = false;
+    uint64_t hit_q = 0;
+    int hit_p[GRAND_AB_WEIGHT_MAX] = {0, 0, 0, 0};
+    int hit_w = 0;
+    for (int w = 0; w <= a.max_weight && !found && start < (uint64_t)a.cap; ++w) {
+      const uint64_t nsets = binom_big(N, w);
+      const uint64_t limit = min(nsets, (uint64_t)a.cap - start);
+      for (uint64_t base = 0; base < limit && !found; base += 32) {
+        const uint64_t c = base + lane;
+        bool hit = false;
+        int P[GRAND_AB_WEIGHT_MAX] = {0, 0, 0, 0};
+        if (c < limit) {
+          ++evaluated;
+          uint64_t rem = c;
+          int hiP = N - 1;
+          for (int j = w; j >= 1; --j) {
+            // largest p <= hiP with C(p, j) <= rem (binary search)
+            int lo = j - 1, hi = hiP;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (binom_big(mid, j) <= rem) lo = mid; else hi = mid - 1;
+            }
+            P[j - 1] = lo;
+            rem -= binom_big(lo, j);
+            hiP = lo - 1;
+          }
+          uint32_t z0 = s0[0];
+          for (int j = 0; j < w; ++j) z0 ^= __ldg(a.code.hcol + (size_t)P[j] * W);
+          if (z0 == 0) {
+            uint32_t orr = 0;
+            for (int ww = 0; ww < W; ++ww) {
+              uint32_t z = s0[ww];
+              for (int j = 0; j < w; ++j) z ^= __ldg(a.code.hcol + (size_t)P[j] * W + ww);
+              orr |= z;
+            }
+            hit = orr == 0;
+          }
+        }
+        const unsigned hb = __ballot_sync(kFull, hit);
+        if (hb) {
+          const int src = __ffs(hb) - 1;
+          found = true;
+          hit_w = w;
+          hit_q = start + base + src + 1;
+          for (int j = 0; j < GRAND_AB_WEIGHT_MAX; ++j) hit_p[j] = __shfl_sync(kFull, P[j], src);
+        }
+      }
+      start += nsets;
+    }
+    if (found && lane == 0)
+      for (int j = 0; j < hit_w; ++j) y[hit_p[j] >> 5] ^= 1u << (hit_p[j] & 31);
+    __syncwarp();
+    if (lane < NW) a.cw[f * NW + lane] = y[lane];
+    if (lane == 0) {
+      uint64_t total = 0;
+      for (int w = 0; w <= a.max_weight; ++w) total += binom_big(N, w);
+      a.queries[f] = (uint32_t)(found ? hit_q : min(total, (uint64_t)a.cap));
+      a.abandon[f] = found ? 0 : 1;
+    }
+    __syncwarp();
+  }
+  for (int o = 16; o; o >>= 1) evaluated += __shfl_xor_sync(kFull, evaluated, o);
+  if (lane == 0 && evaluated && a.scr) atomicAdd(&a.scr->evaluated, evaluated);
+}
+
+// ---------------------------------------------------------------------------
+// Public demodulation: one thread per symbol
+// ---------------------------------------------------------------------------
+struct DemodArgs {
+  const float2* symbols;
+  int64_t n_sym;
+  int L, m, side, N, NW, lik;
+  float q, inv_d;
+  uint16_t* hard_idx;
+  uint32_t* key;
+  uint8_t* nmask;
+  float* rel;
+  uint32_t* y;
+};
+
+__global__ void __launch_bounds__(256) k_demod(DemodArgs a) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_sym; s += (int64_t)gridDim.x * blockDim.x) {
+    float2 v = a.symbols[s];
+    const bool nf = !(isfinite(v.x) && isfinite(v.y));
+    if (nf) v = make_float2(0.0f, 0.0f);
+    const AxisDemod I = demod_axis_q(v.x, a.q, a.side, a.lik);
+    const AxisDemod Q = demod_axis_q(v.y, a.q, a.side, a.lik);
+    if (a.hard_idx) a.hard_idx[s] = (uint16_t)((I.level << 8) | Q.level);
+    if (a.key) a.key[s] = (uint32_t)I.dq * (uint32_t)I.dq + (uint32_t)Q.dq * (uint32_t)Q.dq;
+    if (a.nmask) a.nmask[s] = (uint8_t)make_nmask(I, Q, nf);
+    if (a.rel) {
+      const float dI = axis_dist_f32(v.x, a.inv_d, I.amp, I.outside, a.lik);
+      const float dQ = axis_dist_f32(v.y, a.inv_d, Q.amp, Q.outside, a.lik);
+      a.rel[s] = sqrtf(dI * dI + dQ * dQ);
+    }
+    if (a.y) {
+      const int64_t f = s / a.L;
+      const int i = (int)(s - f * a.L);
+      const uint32_t label = ((uint32_t)gray_code(I.level) << a.m) | (uint32_t)gray_code(Q.level);
+      const uint32_t rl = __brev(label) >> (32 - 2 * a.m);
+      const int p0 = 2 * a.m * i;
+      const int wd = p0 >> 5, sh = p0 & 31;
+      const uint32_t lo = rl << sh, hi = sh ? (rl >> (32 - sh)) : 0u;
+      uint32_t* yf = a.y + f * a.NW;
+      if (wd < a.NW && lo) atomicOr(yf + wd, lo);
+      if (hi && wd + 1 < a.NW) atomicOr(yf + wd + 1, hi);
+    }
+  }
+}
+
+// BPSK hard decisions: one warp per 32 samples
+__global__ void __launch_bounds__(256) k_demod_bpsk(const float* r, int64_t n_words, uint32_t* y, uint8_t* nmask) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_words;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    float v = r[32 * w + lane];
+    const bool nf = !isfinite(v);
+    if (nf) v = 0.0f;
+    const unsigned b = __ballot_sync(kFull, v < 0.0f);
+    if (lane == 0 && y) y[w] = b;
+    if (nmask) nmask[32 * w + lane] = nf ? 128 : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static int m_of(int M) {
+  switch (M) {
+    case 4: return 1;
+    case 16: return 2;
+    case 64: return 3;
+    case 256: return 4;
+    default: return 0;
+  }
+}
+
+static QamConst make_qam_const() {
+  QamConst c{};
+  for (int m = 1; m <= 4; ++m) {
+    const int M = 1 << (2 * m);
+    const double d = sqrt(3.0 * m / (double)(M - 1));
+    c.q[m] = (float)(256.0 / d);
+    c.inv_d[m] = (float)(1.0 / d);
+  }
+  return c;
+}
+
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+#define CU(x)                                   \
+  do {                                          \
+    if ((x) != cudaSuccess) return GRAND_E_CUDA; \
+  } while (0)
+
+// Common body of the symbol-level decode calls.
+static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, const grand_params* p,
+                   const PrepArgs& proto, int64_t n_frames, grand_stats* stats, cudaStream_t st) {
+  if (n_frames == 0) {
+    if (stats) *stats = grand_stats{};
+    return GRAND_OK;
+  }
+  // scratch: header + one record per frame (worst case: every frame hard)
+  const size_t rec_bytes = sizeof(FrameRec) * (size_t)n_frames;
+  char* scratch = nullptr;
+  if (cudaMallocAsync((void**)&scratch, 256 + rec_bytes, st) != cudaSuccess) return GRAND_E_NOMEM;
+  Scratch* scr = reinterpret_cast<Scratch*>(scratch);
+  FrameRec* recs = reinterpret_cast<FrameRec*>(scratch + 256);
+  int rc = GRAND_OK;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  do {
+    if (cudaMemsetAsync(scr, 0, sizeof(Scratch), st) != cudaSuccess) { rc = GRAND_E_CUDA; break; }
+    PrepArgs a = proto;
+    a.recs = recs;
+    a.scr = scr;
+    a.Lmax = Lmax;
+    a.Wmax = Wmax;
+    a.w0 = p->tiles[2] > 0 ? (p->tiles[2] > 3 ? 3 : p->tiles[2]) : 2;
+    const int warps = 4;
+    const size_t prep_smem = prep_warp_bytes(Lmax, Wmax) * warps;
+    if (prep_smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem) != cudaSuccess) {
+      rc = GRAND_E_CUDA;
+      break;
+    }
+    const int64_t want = (n_frames + warps - 1) / warps;
+    const int grid = (int)(want < (int64_t)sm_count() * 64 ? want : (int64_t)sm_count() * 64);
+    if (stats) {
+      for (int i = 0; i < 3; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) { rc = GRAND_E_CUDA; break; }
+      if (rc) break;
+      cudaEventRecord(ev[0], st);
+    }
+    k_prep<<<grid, 32 * warps, prep_smem, st>>>(a);
+    if (stats) cudaEventRecord(ev[1], st);
+    if (cudaGetLastError() != cudaSuccess) { rc = GRAND_E_CUDA; break; }
+
+    const int Smax = p->S < Lmax ? p->S : Lmax;
+    if (Smax > 6) {
+      SearchArgs s{};
+      s.recs = recs;
+      s.codes = d_codes;
+      s.scr = scr;
+      s.cap = p->query_cap;
+      s.split = p->tiles[1];
+      // table capacities for the largest split the call can produce
+      s.tabA = kTableMax;
+      s.tabB = kTableMax;
+      if (s.split <= 0) {
+        s.tabA = 1 << (2 * (Smax / 2));
+        s.tabB = 1 << (2 * (Smax - Smax / 2));
+      }
+      s.max_tiles = ((s.tabA + kTileRows - 1) / kTileRows) * ((s.tabB + kTileCols - 1) / kTileCols);
+      s.Wmax = Wmax;
+      s.cw = proto.cw;
+      s.queries = proto.queries;
+      s.abandon = proto.abandon;
+      const int threads = p->tiles[0] > 0 ? 32 * (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 256;
+      const size_t smem = search_smem_bytes(s.tabA, s.tabB, s.max_tiles, Wmax);
+      if (cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        rc = GRAND_E_CUDA;
+        break;
+      }
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search, threads, smem);
+      if (per_sm < 1) per_sm = 1;
+      k_search<<<sm_count() * per_sm, threads, smem, st>>>(s);
+      if (cudaGetLastError() != cudaSuccess) { rc = GRAND_E_CUDA; break; }
+    }
+    if (stats) {
+      cudaEventRecord(ev[2], st);
+      Scratch h{};
+      if (cudaMemcpyAsync(&h, scr, sizeof(Scratch), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        rc = GRAND_E_CUDA;
+        break;
+      }
+      stats->evaluated_checks = h.evaluated;
+      stats->hard_frames = h.n_hard;
+      stats->search_useful = h.search_useful;
+      cudaEventElapsedTime(&stats->prep_ms, ev[0], ev[1]);
+      cudaEventElapsedTime(&stats->search_ms, ev[1], ev[2]);
+    }
+  } while (0);
+  for (int i = 0; i < 3; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  cudaFreeAsync(scratch, st);
+  return rc;
+}
+
+static int check_params(const grand_params* p) {
+  if (!p) return GRAND_E_INVALID;
+  if (p->query_cap < 1) return GRAND_E_INVALID;
+  if (p->lik_variant != GRAND_LIK_THRESHOLD && p->lik_variant != GRAND_LIK_LITERAL) return GRAND_E_INVALID;
+  if (p->order == GRAND_ORDER_QAM_NNE) {
+    if (p->S < 0) return GRAND_E_INVALID;
+    if (p->S > kSMax) return GRAND_E_UNSUPPORTED;
+  } else if (p->order == GRAND_ORDER_HAMMING) {
+    if (p->max_weight < 0) return GRAND_E_INVALID;
+    if (p->max_weight > GRAND_AB_WEIGHT_MAX) return GRAND_E_UNSUPPORTED;
+  } else {
+    return GRAND_E_INVALID;
+  }
+  for (int i = 0; i < 4; ++i)
+    if (p->tiles[i] < 0) return GRAND_E_INVALID;
+  return GRAND_OK;
+}
+
+static int run_ab(const grand_code* c, const grand_params* p, const float* samples, const uint32_t* y,
+                  const uint8_t* nmask, int64_t n_frames, uint32_t* cw, uint32_t* queries, uint8_t* abandon,
+                  grand_stats* stats, cudaStream_t st) {
+  // positions must fit the 32-bit query counter
+  uint64_t total = 0;
+  for (int w = 0; w <= p->max_weight; ++w) {
+    uint64_t b = 1;
+    for (int i = 1; i <= w; ++i) b = b * (uint64_t)(c->N - w + i) / (uint64_t)i;
+    total += b;
+  }
+  if ((total < (uint64_t)p->query_cap ? total : (uint64_t)p->query_cap) > 0xFFFFFFFFull) return GRAND_E_UNSUPPORTED;
+  if (n_frames == 0) {
+    if (stats) *stats = grand_stats{};
+    return GRAND_OK;
+  }
+  Scratch* scr = nullptr;
+  if (cudaMallocAsync((void**)&scr, sizeof(Scratch), st) != cudaSuccess) return GRAND_E_NOMEM;
+  int rc = GRAND_OK;
+  do {
+    if (cudaMemsetAsync(scr, 0, sizeof(Scratch), st) != cudaSuccess) { rc = GRAND_E_CUDA; break; }
+    AbArgs a{};
+    a.samples = samples;
+    a.y_in = y;
+    a.nmask = nmask;
+    a.code = c->dev;
+    a.n_frames = n_frames;
+    a.max_weight = p->max_weight;
+    a.cap = p->query_cap;
+    a.cw = cw;
+    a.queries = queries;
+    a.abandon = abandon;
+    a.scr = scr;
+    const int64_t want = (n_frames + 3) / 4;
+    const int grid = (int)(want < (int64_t)sm_count() * 64 ? want : (int64_t)sm_count() * 64);
+    k_ab<<<grid, 128, 0, st>>>(a);
+    if (cudaGetLastError() != cudaSuccess) { rc = GRAND_E_CUDA; break; }
+    if (stats) {
+      Scratch h{};
+      if (cudaMemcpyAsync(&h, scr, sizeof(Scratch), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        rc = GRAND_E_CUDA;
+        break;
+      }
+      stats->evaluated_checks = h.evaluated;
+      stats->hard_frames = 0;
+      stats->search_useful = 0;
+      stats->prep_ms = stats->search_ms = 0.0f;
+    }
+  } while (0);
+  cudaFreeAsync(scr, st);
+  return rc;
+}
+
+}  // namespace grand
+
+using namespace grand;
+
+extern "C" int grand_demod(const void* symbols, int64_t n_frames, int L, int M, float N0, int lik_variant,
+                           uint16_t* hard_idx, uint32_t* key, uint8_t* nmask, float* rel, uint32_t* y, int N,
+                           void* stream) {
+  if ((!symbols && n_frames > 0) || n_frames < 0 || !(N0 > 0.0f) || !isfinite(N0)) return GRAND_E_INVALID;
+  if (N < GRAND_N_MIN || N > GRAND_N_MAX || (N & (N - 1))) return GRAND_E_INVALID;
+  if (lik_variant != GRAND_LIK_THRESHOLD && lik_variant != GRAND_LIK_LITERAL) return GRAND_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (M == 2) {
+    if (L != N) return GRAND_E_INVALID;
+    if (n_frames == 0) return GRAND_OK;
+    const int64_t n_words = n_frames * (N / 32);
+    const int64_t blocks = (n_words * 32 + 255) / 256;
+    k_demod_bpsk<<<(int)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, st>>>((const float*)symbols, n_words, y,
+                                                                                  nmask);
+    return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
+  }
+  const int m = m_of(M);
+  if (!m || L != (N + 2 * m - 1) / (2 * m)) return GRAND_E_INVALID;
+  if (n_frames == 0) return GRAND_OK;
+  const QamConst qc = make_qam_const();
+  DemodArgs a{};
+  a.symbols = (const float2*)symbols;
+  a.n_sym = n_frames * L;
+  a.L = L;
+  a.m = m;
+  a.side = 1 << m;
+  a.N = N;
+  a.NW = N / 32;
+  a.lik = lik_variant;
+  a.q = qc.q[m];
+  a.inv_d = qc.inv_d[m];
+  a.hard_idx = hard_idx;
+  a.key = key;
+  a.nmask = nmask;
+  a.rel = rel;
+  a.y = y;
+  if (y && cudaMemsetAsync(y, 0, sizeof(uint32_t) * (size_t)n_frames * (N / 32), st) != cudaSuccess)
+    return GRAND_E_CUDA;
+  const int64_t blocks = (a.n_sym + 255) / 256;
+  const int grid = (int)(blocks < (int64_t)sm_count() * 32 ? blocks : (int64_t)sm_count() * 32);
+  k_demod<<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
+}
+
+extern "C" int grand_decode_batch(const grand_code* c, const grand_params* p, const uint16_t* hard_idx,
+                                  const uint32_t* key, const uint8_t* nmask, const uint32_t* y, int64_t n_frames,
+                                  uint32_t* cw, uint32_t* queries, uint8_t* abandon, grand_stats* stats,
+                                  void* stream) {
+  if (!c || n_frames < 0 || (n_frames > 0 && (!cw || !queries || !abandon || !y))) return GRAND_E_INVALID;
+  int rc = check_params(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p->order == GRAND_ORDER_HAMMING) return run_ab(c, p, nullptr, y, nmask, n_frames, cw, queries, abandon, stats, st);
+  const int m = m_of(p->M);
+  if (!m || (n_frames > 0 && (!hard_idx || !key || !nmask))) return GRAND_E_INVALID;
+  if (n_frames > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
+  const int L = (c->N + 2 * m - 1) / (2 * m);
+  PrepArgs a{};
+  a.hard_idx = hard_idx;
+  a.key = key;
+  a.nmask = nmask;
+  a.y_in = y;
+  a.codes = c->d_dev;
+  a.n_codes = 1;
+  a.n_frames = n_frames;
+  a.M = p->M;
+  a.S = p->S;
+  a.lik = p->lik_variant;
+  a.cap = p->query_cap;
+  a.qc = make_qam_const();
+  a.cw = cw;
+  a.queries = queries;
+  a.abandon = abandon;
+  return run_qam(c->d_dev, 1, L, c->W, p, a, n_frames, stats, st);
+}
+
+extern "C" int grand_decode_symbols(const grand_code* c, const grand_params* p, const void* symbols, int64_t n_frames,
+                                    float N0, uint32_t* cw, uint32_t* queries, uint8_t* abandon, grand_stats* stats,
+                                    void* stream) {
+  if (!c || n_frames < 0 || (n_frames > 0 && (!symbols || !cw || !queries || !abandon))) return GRAND_E_INVALID;
+  if (!(N0 > 0.0f) || !isfinite(N0)) return GRAND_E_INVALID;
+  int rc = check_params(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p->order == GRAND_ORDER_HAMMING) {
+    if (p->M != 2) return GRAND_E_INVALID;
+    return run_ab(c, p, (const float*)symbols, nullptr, nullptr, n_frames, cw, queries, abandon, stats, st);
+  }
+  const int m = m_of(p->M);
+  if (!m) return GRAND_E_INVALID;
+  if (n_frames > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
+  const int L = (c->N + 2 * m - 1) / (2 * m);
+  PrepArgs a{};
+  a.symbols = (const float2*)symbols;
+  a.codes = c->d_dev;
+  a.n_codes = 1;
+  a.n_frames = n_frames;
+  a.M = p->M;
+  a.S = p->S;
+  a.lik = p->lik_variant;
+  a.cap = p->query_cap;
+  a.qc = make_qam_const();
+  a.cw = cw;
+  a.queries = queries;
+  a.abandon = abandon;
+  return run_qam(c->d_dev, 1, L, c->W, p, a, n_frames, stats, st);
+}
+
+extern "C" int grand_decode_mixed(const grand_code* const* codes, int n_codes, const grand_params* p,
+                                  const grand_frame_desc* desc, int64_t n_frames, const void* symbols,
+                                  int64_t n_symbols, float N0, uint32_t* cw, int64_t n_cw_words, uint32_t* queries,
+                                  uint8_t* abandon, grand_stats* stats, void* stream) {
+  if (!codes || n_codes < 1 || n_codes > 65535 || n_frames < 0 || n_symbols < 0 || n_cw_words < 0 ||
+      (n_frames > 0 && (!desc || !symbols || !cw || !queries || !abandon)))
+    return GRAND_E_INVALID;
+  if (!(N0 > 0.0f) || !isfinite(N0)) return GRAND_E_INVALID;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p->order != GRAND_ORDER_QAM_NNE) return GRAND_E_INVALID;
+  if (n_frames > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  int Wmax = 1, Lmax = 1;
+  std::vector<CodeDev> table(n_codes);
+  for (int i = 0; i < n_codes; ++i) {
+    if (!codes[i]) return GRAND_E_INVALID;
+    table[i] = codes[i]->dev;
+    Wmax = table[i].W > Wmax ? table[i].W : Wmax;
+    const int L = (table[i].N + 1) / 2;  // QPSK bound
+    Lmax = L > Lmax ? L : Lmax;
+  }
+  CodeDev* d_table = nullptr;
+  if (cudaMallocAsync((void**)&d_table, sizeof(CodeDev) * n_codes, st) != cudaSuccess) return GRAND_E_NOMEM;
+  if (cudaMemcpyAsync(d_table, table.data(), sizeof(CodeDev) * n_codes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cudaFreeAsync(d_table, st);
+    return GRAND_E_CUDA;
+  }
+  PrepArgs a{};
+  a.symbols = (const float2*)symbols;
+  a.desc = desc;
+  a.n_symbols = n_symbols;
+  a.n_cw_words = n_cw_words;
+  a.codes = d_table;
+  a.n_codes = n_codes;
+  a.n_frames = n_frames;
+  a.M = 0;
+  a.S = p->S;
+  a.lik = p->lik_variant;
+  a.cap = p->query_cap;
+  a.qc = make_qam_const();
+  a.cw = cw;
+  a.queries = queries;
+  a.abandon = abandon;
+  rc = run_qam(d_table, n_codes, Lmax, Wmax, p, a, n_frames, stats, st);
+  // the table must outlive the kernels: stream-ordered free
+  cudaFreeAsync(d_table, st);
+  return rc;
+}

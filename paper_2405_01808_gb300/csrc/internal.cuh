@@ -1,0 +1,58 @@
+// Internal definitions of the GB300 GRAND decoder library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "grand.h"
+
+namespace grand {
+
+constexpr int kSMax = GRAND_S_MAX;   // cut-off limit: 4^12 TEPs per frame
+constexpr int kWMax = 16;            // syndrome words: N - K <= 512
+constexpr int kNMax = GRAND_N_MAX;
+constexpr int kLMax = 512;           // symbols per frame (N = 1024 with QPSK)
+constexpr int kSideMax = 6;          // ranks per side of the search split (4^6 table entries)
+constexpr int kTableMax = 4096;      // 4^kSideMax
+constexpr uint16_t kNoPos = 0xFFFF;  // alternative bit beyond N (padding): no syndrome change
+
+// Device view of one code: column-packed parity-check matrix.
+//   hcol[j * W + w] bit b = H[32 w + b][j]   (column j of H, W words)
+struct CodeDev {
+  const uint32_t* hcol;
+  int32_t N, K, R, W;
+};
+
+// Per-frame state handed from the preparation kernel to the search kernel
+// for frames the preparation could not finish.
+struct FrameRec {
+  uint32_t frame;            // frame index in the batch
+  uint16_t code;             // index into the code table
+  uint8_t sp;                // S' = min(S, L)
+  uint8_t w_done;            // every TEP with at most w_done altered symbols was tested
+  int64_t cw_off;            // first output word of the frame
+  uint32_t s0[kWMax];        // base syndrome H y
+  uint16_t pos[kSMax][2];    // bit position flipped by the I / Q alternative of rank r
+  uint8_t ex[kSMax];         // bit0 h exists, bit1 v exists, bit2 diag exists
+  uint8_t pad[4];
+};
+static_assert(sizeof(FrameRec) % 8 == 0, "FrameRec alignment");
+
+// Scratch shared by the kernels of one decode call (device memory).
+struct Scratch {
+  unsigned int n_hard;              // frames appended by the preparation kernel
+  unsigned int next;                // search work-queue head
+  unsigned long long evaluated;     // TEP checks executed
+  unsigned long long search_useful; // valid queries answered by the search stage
+};
+
+}  // namespace grand
+
+// Opaque code object of the ABI.
+struct grand_code {
+  int N, K, R, W;
+  uint32_t* d_hcol;                 // device, N * W words
+  grand::CodeDev* d_dev;            // device copy of the CodeDev (for code tables)
+  grand::CodeDev dev;               // host copy of the device view
+  int device;                       // CUDA device the object lives on
+};
