@@ -226,6 +226,29 @@ int grand_decode_mixed(const grand_code* const* codes, int n_codes, const grand_
                        float N0, uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon,
                        grand_stats* stats, void* stream);
 
+/* grand_decode_symbols without any allocation (the paper has no counterpart:
+ * this is a deployment convenience). For callers that are not allowed to
+ * allocate device memory once they are running -- for example a real-time
+ * receiver pipeline that reserves all memory at start-up, or code running
+ * where the stream-ordered allocator is unavailable or would break a latency
+ * budget. Same inputs, outputs and results as grand_decode_symbols with the
+ * same params; the caller still provides every input and output buffer.
+ *   - Internal scratch is a fixed array of about 2.4 MB in the library's
+ *     device memory, present on every GPU that loads the library until the
+ *     process exits. It holds at most GRAND_NOALLOC_MAX_FRAMES frames: larger
+ *     n_frames is rejected with GRAND_E_UNSUPPORTED before any GPU work.
+ *   - Only GRAND_ORDER_QAM_NNE; no statistics output.
+ *   - The first call on a device looks up the array's device address (a
+ *     one-time set-up); make that first call before any stream capture.
+ *   - Every call on a device shares the one array and resets its counters
+ *     first: calls whose GPU work overlaps in time (different streams, or
+ *     different host threads) race and give wrong results. Serialise them.
+ * Errors: GRAND_E_INVALID, GRAND_E_UNSUPPORTED, GRAND_E_CUDA. */
+#define GRAND_NOALLOC_MAX_FRAMES 16384
+int grand_decode_symbols_noalloc(const grand_code* code, const grand_params* params, const void* symbols,
+                                 int64_t n_frames, float N0, uint32_t* cw, uint32_t* queries, uint8_t* abandon,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

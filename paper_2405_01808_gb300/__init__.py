@@ -89,8 +89,10 @@ def lib() -> ctypes.CDLL:
             L.grand_decode_batch.argtypes = [P, P, P, P, P, P, i64, P, P, P, P, P]
             L.grand_decode_symbols.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, P, P]
             L.grand_decode_mixed.argtypes = [P, i32, P, P, i64, P, i64, ctypes.c_float, P, i64, P, P, P, P]
+            L.grand_decode_symbols_noalloc.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, P]
             for name in ("grand_polar_H", "grand_code_create", "grand_code_destroy", "grand_code_info",
-                         "grand_demod", "grand_decode_batch", "grand_decode_symbols", "grand_decode_mixed"):
+                         "grand_demod", "grand_decode_batch", "grand_decode_symbols", "grand_decode_mixed",
+                         "grand_decode_symbols_noalloc"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -291,3 +293,22 @@ def decode_mixed(codes, params: Params, desc, symbols, n_cw_words: int, N0: floa
                                   ctypes.byref(st) if stats else None, _stream(stream))
     _check(rc, "grand_decode_mixed")
     return _result(cw, queries, abandon, st, stats)
+
+
+NOALLOC_MAX_FRAMES = 16384
+
+
+def decode_symbols_noalloc(code: Code, params: Params, symbols, cw, queries, abandon, N0: float = 1.0, stream=None):
+    """grand_decode_symbols_noalloc: the decode of `decode_symbols` for callers
+    that may not allocate device memory while running. The caller passes every
+    output buffer; at most NOALLOC_MAX_FRAMES frames per call; calls on one
+    device must not overlap in time (they share one fixed scratch array)."""
+    import torch
+
+    _require_cuda(symbols, cw, queries, abandon)
+    F = symbols.shape[0]
+    sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
+    rc = lib().grand_decode_symbols_noalloc(code.handle, ctypes.byref(params), _ptr(sym), F, float(N0), _ptr(cw),
+                                            _ptr(queries), _ptr(abandon), _stream(stream))
+    _check(rc, "grand_decode_symbols_noalloc")
+    return {"cw": cw, "queries": queries, "abandon": abandon}

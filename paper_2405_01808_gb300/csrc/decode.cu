@@ -21,6 +21,7 @@
 //   k_demod   the public demodulation call (per-symbol outputs).
 #include <stdio.h>
 
+#include <mutex>
 #include <vector>
 
 #include "device_common.cuh"
@@ -1311,4 +1312,125 @@ extern "C" int grand_decode_mixed(const grand_code* const* codes, int n_codes, c
   // the table must outlive the kernels: stream-ordered free
   cudaFreeAsync(d_table, st);
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of grand_decode_symbols.
+//
+// The regular call takes its scratch (a header plus one hand-off record per
+// frame between the preparation and the search kernel) from cudaMallocAsync.
+// This variant takes it from one fixed array in device memory instead, so a
+// caller that must not allocate after start-up can still decode. The array is
+// part of the library's device code: every GPU that loads the library holds
+// it (kNoAllocScratchBytes, about 2.4 MB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace grand {
+
+constexpr int64_t kNoAllocMaxFrames = GRAND_NOALLOC_MAX_FRAMES;
+constexpr size_t kNoAllocHeader = 256;
+constexpr size_t kNoAllocScratchBytes = kNoAllocHeader + sizeof(FrameRec) * (size_t)kNoAllocMaxFrames;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[kNoAllocMaxDevices];
+
+// Device address of the array on the current device. In host code the name
+// g_noalloc_scratch is only a host-side handle, so the address is looked up
+// once per device (with that device current) and cached.
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GRAND_E_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return GRAND_E_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GRAND_E_CUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return GRAND_OK;
+}
+
+}  // namespace grand
+
+extern "C" int grand_decode_symbols_noalloc(const grand_code* c, const grand_params* p, const void* symbols,
+                                            int64_t n_frames, float N0, uint32_t* cw, uint32_t* queries,
+                                            uint8_t* abandon, void* stream) {
+  if (!c || n_frames < 0 || (n_frames > 0 && (!symbols || !cw || !queries || !abandon))) return GRAND_E_INVALID;
+  if (!(N0 > 0.0f) || !isfinite(N0)) return GRAND_E_INVALID;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p->order != GRAND_ORDER_QAM_NNE) return GRAND_E_INVALID;
+  const int m = m_of(p->M);
+  if (!m) return GRAND_E_INVALID;
+  if (n_frames > kNoAllocMaxFrames) return GRAND_E_UNSUPPORTED;
+  void* base = nullptr;
+  rc = noalloc_scratch(&base);  // first call on a device: symbol lookup
+  if (rc) return rc;
+  if (n_frames == 0) return GRAND_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch* scr = reinterpret_cast<Scratch*>(base);
+  FrameRec* recs = reinterpret_cast<FrameRec*>(static_cast<char*>(base) + kNoAllocHeader);
+  // the array keeps the previous call's contents: reset the counters
+  if (cudaMemsetAsync(scr, 0, sizeof(Scratch), st) != cudaSuccess) return GRAND_E_CUDA;
+  const int L = (c->N + 2 * m - 1) / (2 * m);
+  PrepArgs a{};
+  a.symbols = (const float2*)symbols;
+  a.codes = c->d_dev;
+  a.n_codes = 1;
+  a.n_frames = n_frames;
+  a.M = p->M;
+  a.S = p->S;
+  a.lik = p->lik_variant;
+  a.cap = p->query_cap;
+  a.qc = make_qam_const();
+  a.cw = cw;
+  a.queries = queries;
+  a.abandon = abandon;
+  a.recs = recs;
+  a.scr = scr;
+  a.Lmax = L;
+  a.Wmax = c->W;
+  a.w0 = p->tiles[2] > 0 ? (p->tiles[2] > 3 ? 3 : p->tiles[2]) : 2;
+  const int warps = 4;
+  const size_t prep_smem = prep_warp_bytes(L, c->W) * warps;
+  if (prep_smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem) != cudaSuccess)
+    return GRAND_E_CUDA;
+  const int64_t want = (n_frames + warps - 1) / warps;
+  const int grid = (int)(want < (int64_t)sm_count() * 64 ? want : (int64_t)sm_count() * 64);
+  k_prep<<<grid, 32 * warps, prep_smem, st>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return GRAND_E_CUDA;
+  const int Smax = p->S < L ? p->S : L;
+  if (Smax > 6) {
+    SearchArgs s{};
+    s.recs = recs;
+    s.codes = c->d_dev;
+    s.scr = scr;
+    s.cap = p->query_cap;
+    s.split = p->tiles[1];
+    s.tabA = kTableMax;
+    s.tabB = kTableMax;
+    if (s.split <= 0) {
+      s.tabA = 1 << (2 * (Smax / 2));
+      s.tabB = 1 << (2 * (Smax - Smax / 2));
+    }
+    s.max_tiles = ((s.tabA + kTileRows - 1) / kTileRows) * ((s.tabB + kTileCols - 1) / kTileCols);
+    s.Wmax = c->W;
+    s.cw = cw;
+    s.queries = queries;
+    s.abandon = abandon;
+    const int threads = p->tiles[0] > 0 ? 32 * (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 256;
+    const size_t smem = search_smem_bytes(s.tabA, s.tabB, s.max_tiles, c->W);
+    if (cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return GRAND_E_CUDA;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    k_search<<<sm_count() * per_sm, threads, smem, st>>>(s);
+    if (cudaGetLastError() != cudaSuccess) return GRAND_E_CUDA;
+  }
+  return GRAND_OK;
 }
