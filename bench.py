@@ -235,11 +235,13 @@ def main():
     ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=0, help="override frames per SNR (for quick runs)")
+    ap.add_argument("--tiles", default="0,0,0,0", help="launch shape (grand_params.tiles), 0 = automatic")
     args = ap.parse_args()
     cfg = dict(CONFIGS[args.config])
     cfg["name"] = args.config
     if args.frames:
         cfg["frames"] = args.frames
+    tiles = tuple(int(t) for t in args.tiles.split(","))
     if args.impl == "reference":
         return run_reference(args, cfg)
 
@@ -275,7 +277,7 @@ def main():
         d_desc = torch.from_numpy(desc.view(np.uint8)).to(dev)
         n_frames = len(inputs["N"])
         n_cw = inputs["n_cw_words"]
-        p = g.Params.make(M=0, S=cfg["S"], query_cap=cfg["cap"])
+        p = g.Params.make(M=0, S=cfg["S"], query_cap=cfg["cap"], tiles=tiles)
         alg_words = None
     else:
         codes = [g.Code.polar(cfg["N"], cfg["K"])]
@@ -284,7 +286,7 @@ def main():
         if cfg["kind"] == "ab":
             p = g.Params.make(order=g.ORDER_HAMMING, M=2, max_weight=cfg["max_weight"], query_cap=cfg["cap"])
         else:
-            p = g.Params.make(M=cfg["M"], S=cfg["S"], query_cap=cfg["cap"])
+            p = g.Params.make(M=cfg["M"], S=cfg["S"], query_cap=cfg["cap"], tiles=tiles)
         alg_words = (cfg["N"] - cfg["K"]) / 32.0
     h_sym = torch.from_numpy(inputs["symbols"]).pin_memory()
     d_sym = h_sym.to(dev)
@@ -405,7 +407,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": tmax_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic (seeded random polar codewords over AWGN)",
-            "config": {"workload": cfg["desc"], "frames_per_step_per_gpu": n_frames,
+            "config": {"workload": cfg["desc"], "frames_per_step_per_gpu": n_frames, "tiles": list(tiles),
                        "l2": "flushed before every timed step (256 MiB write)",
                        "parallelism": f"frames sharded, {world} replica(s)"},
             "frames_per_s": frames_per_s,

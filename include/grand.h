@@ -84,10 +84,11 @@ typedef enum grand_lik {
  *   max_weight  HAMMING order: largest number of flipped bits (0..4).
  *   query_cap   abandonment threshold, >= 1 valid queries.
  *   lik_variant GRAND_LIK_*.
- *   tiles       launch shape, 0 = automatic: [0] warps per search CTA (1..16),
+ *   tiles       launch shape, 0 = automatic: [0] warps per search CTA (1..8),
  *               [1] A-side ranks of the search split (1..6), [2] number of
  *               TEP weights tested by the per-frame preparation (0..3),
- *               [3] reserved (0). Results do not depend on tiles. */
+ *               [3] register budget of the search kernel as resident CTAs
+ *               per SM (4, 6 or 8). Results do not depend on tiles. */
 typedef struct grand_params {
   int32_t order;
   int32_t M;

@@ -90,11 +90,23 @@ extern "C" int grand_code_create(const uint32_t* H, int N, int K, grand_code** o
   const int R = N - K;
   if (gf2_row_rank(H, R, N) != R) return GRAND_E_RANK;
   const int W = (R + 31) / 32;
-  // column-packed copy: word w of column j holds rows 32w .. 32w+31
-  std::vector<uint32_t> hcol((size_t)N * W, 0);
-  for (int r = 0; r < R; ++r)
+  // column-packed copy: word w of column j holds rows 32w .. 32w+31; then the
+  // per-column projections hf[j] (a fixed pseudo-random 32-bit word per row,
+  // from the splitmix64 finaliser of the row index)
+  std::vector<uint32_t> hcol((size_t)N * W + N, 0);
+  uint32_t* hf = hcol.data() + (size_t)N * W;
+  for (int r = 0; r < R; ++r) {
+    uint64_t z = 0x9E3779B97F4A7C15ull * (uint64_t)(r + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const uint32_t pr = (uint32_t)z ^ (uint32_t)(z >> 32);
     for (int j = 0; j < N; ++j)
-      if ((H[(size_t)r * (N / 32) + (j >> 5)] >> (j & 31)) & 1u) hcol[(size_t)j * W + r / 32] |= 1u << (r % 32);
+      if ((H[(size_t)r * (N / 32) + (j >> 5)] >> (j & 31)) & 1u) {
+        hcol[(size_t)j * W + r / 32] |= 1u << (r % 32);
+        hf[j] ^= pr;
+      }
+  }
   grand_code* c = (grand_code*)calloc(1, sizeof(grand_code));
   if (!c) return GRAND_E_NOMEM;
   c->N = N; c->K = K; c->R = R; c->W = W;
@@ -109,6 +121,7 @@ extern "C" int grand_code_create(const uint32_t* H, int N, int K, grand_code** o
     return GRAND_E_NOMEM;
   }
   c->dev.hcol = c->d_hcol;
+  c->dev.hf = c->d_hcol + (size_t)N * W;
   c->dev.N = N; c->dev.K = K; c->dev.R = R; c->dev.W = W;
   if (cudaMemcpy(c->d_hcol, hcol.data(), hcol.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->d_dev, &c->dev, sizeof(grand::CodeDev), cudaMemcpyHostToDevice) != cudaSuccess) {

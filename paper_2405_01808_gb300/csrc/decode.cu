@@ -75,6 +75,7 @@ struct SearchArgs {
   int tabA, tabB;  // table capacities
   int max_tiles;
   int Wmax;
+  int warp_kernel;  // 1: warp-per-frame kernel (S' <= 10, automatic split)
   uint32_t* cw;
   uint32_t* queries;
   uint8_t* abandon;
@@ -88,13 +89,16 @@ struct PrepSmem {
   uint32_t* info;   // [Lmax]
   uint32_t* y;      // [32]
   uint32_t* delta;  // [kSMax][3][Wmax]
+  uint32_t* dflt;   // [kSMax][3] projections of the deltas
   uint32_t* E;      // [kEStride^2]
+  uint32_t* s0;     // [Wmax] base syndrome
   uint8_t* ex;      // [kSMax]
   uint16_t* pos;    // [kSMax][2]
 };
 
 __host__ __device__ inline size_t prep_warp_bytes(int Lmax, int Wmax) {
-  size_t words = 2 * (size_t)Lmax + 32 + (size_t)kSMax * 3 * Wmax + kEStride * kEStride + kSMax / 4 + 1 + kSMax;
+  size_t words = 2 * (size_t)Lmax + 32 + (size_t)kSMax * 3 * Wmax + kSMax * 3 + kEStride * kEStride + Wmax +
+                 kSMax / 4 + 1 + kSMax;
   return ((words * 4) + 15) & ~(size_t)15;
 }
 
@@ -105,25 +109,44 @@ __device__ inline PrepSmem prep_smem(char* base, int Lmax, int Wmax) {
   s.info = p; p += Lmax;
   s.y = p; p += 32;
   s.delta = p; p += kSMax * 3 * Wmax;
+  s.dflt = p; p += kSMax * 3;
   s.E = p; p += kEStride * kEStride;
+  s.s0 = p; p += Wmax;
   s.pos = reinterpret_cast<uint16_t*>(p); p += kSMax;
   s.ex = reinterpret_cast<uint8_t*>(p);
   return s;
 }
 
-// Word 0..W-1 syndrome of the TEP given by `code` (ranks with nonzero digit),
-// XORed into acc.
-__device__ __forceinline__ void xor_delta(uint32_t* acc, const uint32_t* delta, int W, int Sp, uint32_t code) {
-  for (int r = 0; r < Sp; ++r) {
-    const uint32_t c = (code >> (2 * r)) & 3u;
-    if (c) {
-      const uint32_t* d = delta + ((size_t)r * 3 + (c - 1)) * W;
-      for (int w = 0; w < W; ++w) acc[w] ^= d[w];
+
+// Full syndrome of the candidate `code` (2 bits per rank) is zero.
+__device__ __forceinline__ bool syndrome_zero(const uint32_t* s0, const uint32_t* delta, int W, int Sp, uint32_t code) {
+  uint32_t orr = 0;
+  for (int w = 0; w < W; ++w) {
+    uint32_t z = s0[w];
+    for (int r = 0; r < Sp; ++r) {
+      const uint32_t c = (code >> (2 * r)) & 3u;
+      if (c) z ^= delta[((size_t)r * 3 + (c - 1)) * W + w];
     }
+    orr |= z;
   }
+  return orr == 0;
 }
 
-__global__ void __launch_bounds__(128) k_prep(PrepArgs a) {
+// Projection (see CodeDev::hf) of the candidate's syndrome.
+__device__ __forceinline__ uint32_t projection(uint32_t f0, const uint32_t* dflt, int Sp, uint32_t code) {
+  uint32_t z = f0;
+  for (int r = 0; r < Sp; ++r) {
+    const uint32_t c = (code >> (2 * r)) & 3u;
+    if (c) z ^= dflt[r * 3 + (c - 1)];
+  }
+  return z;
+}
+
+constexpr int kPrepMaxW0 = 3;  // TEP weights the preparation can test in canonical order
+
+// WM: compile-time bound on the syndrome words (registers of the base syndrome).
+template <int WM>
+__global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp_in_block = threadIdx.x >> 5;
@@ -136,7 +159,7 @@ __global__ void __launch_bounds__(128) k_prep(PrepArgs a) {
   for (int64_t f = gwarp; f < a.n_frames; f += nwarps) {
     // --- frame parameters -------------------------------------------------
     int code_id = 0, M = a.M;
-    int64_t sym_off, cw_off;
+    int64_t sym_off = 0, cw_off = 0;
     bool bad_desc = false;
     if (a.desc) {
       const grand_frame_desc d = a.desc[f];
@@ -178,12 +201,12 @@ __global__ void __launch_bounds__(128) k_prep(PrepArgs a) {
     for (int i = lane; i < L; i += 32) {
       uint32_t key, info;
       if (a.symbols) {
-        float2 s = a.symbols[sym_off + i];
-        const bool nf = !(isfinite(s.x) && isfinite(s.y));
-        if (nf) s = make_float2(0.0f, 0.0f);
+        float2 sy = a.symbols[sym_off + i];
+        const bool nf = !(isfinite(sy.x) && isfinite(sy.y));
+        if (nf) sy = make_float2(0.0f, 0.0f);
         nonfinite |= nf;
-        const AxisDemod I = demod_axis_q(s.x, a.qc.q[m], side, a.lik);
-        const AxisDemod Q = demod_axis_q(s.y, a.qc.q[m], side, a.lik);
+        const AxisDemod I = demod_axis_q(sy.x, a.qc.q[m], side, a.lik);
+        const AxisDemod Q = demod_axis_q(sy.y, a.qc.q[m], side, a.lik);
         key = (uint32_t)I.dq * (uint32_t)I.dq + (uint32_t)Q.dq * (uint32_t)Q.dq;
         info = pack_info(I.level, Q.level, make_nmask(I, Q, nf));
         // Gray label, MSB first, into the packed hard word
@@ -208,7 +231,6 @@ __global__ void __launch_bounds__(128) k_prep(PrepArgs a) {
     }
     nonfinite = __any_sync(kFull, nonfinite);
     __syncwarp();
-    // bits beyond N never set: padding positions were dropped above
     if (nonfinite) {
       if (lane < NW) a.cw[cw_off + lane] = sm.y[lane];
       if (lane == 0) {
@@ -220,24 +242,26 @@ __global__ void __launch_bounds__(128) k_prep(PrepArgs a) {
     }
 
     // --- base syndrome s0 = H y (XOR of the columns where y_j = 1) --------
-    uint32_t s0[kWMax];
+    uint32_t s0[WM];
+    uint32_t f0 = 0;  // projection of s0
 #pragma unroll
-    for (int w = 0; w < kWMax; ++w) s0[w] = 0;
+    for (int w = 0; w < WM; ++w) s0[w] = 0;
     for (int j = lane; j < N; j += 32) {
       if ((sm.y[j >> 5] >> (j & 31)) & 1u) {
         const uint32_t* col = code.hcol + (size_t)j * W;
 #pragma unroll
-        for (int w = 0; w < kWMax; ++w)
+        for (int w = 0; w < WM; ++w)
           if (w < W) s0[w] ^= __ldg(col + w);
+        f0 ^= __ldg(code.hf + j);
       }
     }
+    for (int o = 16; o; o >>= 1) f0 ^= __shfl_xor_sync(kFull, f0, o);
 #pragma unroll
-    for (int w = 0; w < kWMax; ++w) {
-      if (w < W) {
-        uint32_t v = s0[w];
-        for (int o = 16; o; o >>= 1) v ^= __shfl_xor_sync(kFull, v, o);
-        s0[w] = v;
-      }
+    for (int w = 0; w < WM; ++w) {
+      uint32_t v = s0[w];
+      for (int o = 16; o; o >>= 1) v ^= __shfl_xor_sync(kFull, v, o);
+      s0[w] = v;
+      if (lane == w && w < W) sm.s0[w] = v;
     }
 
     // --- Steps 2-3: the S' least reliable symbols, by (key, index) ---------
@@ -269,18 +293,21 @@ __global__ void __launch_bounds__(128) k_prep(PrepArgs a) {
       sm.pos[2 * lane + 1] = pQ;
       sm.ex[lane] = (uint8_t)((exI ? 1 : 0) | (exQ ? 2 : 0) | (exI && exQ ? 4 : 0));
       uint32_t* dh = sm.delta + ((size_t)lane * 3 + 0) * W;
-      uint32_t* dv = sm.delta + ((size_t)lane * 3 + 1) * W;
-      uint32_t* dd = sm.delta + ((size_t)lane * 3 + 2) * W;
       for (int w = 0; w < W; ++w) {
         const uint32_t h = pI != kNoPos ? __ldg(code.hcol + (size_t)pI * W + w) : 0u;
         const uint32_t v = pQ != kNoPos ? __ldg(code.hcol + (size_t)pQ * W + w) : 0u;
         dh[w] = h;
-        dv[w] = v;
-        dd[w] = h ^ v;
+        dh[W + w] = v;
+        dh[2 * W + w] = h ^ v;
       }
+      const uint32_t fh = pI != kNoPos ? __ldg(code.hf + pI) : 0u;
+      const uint32_t fv = pQ != kNoPos ? __ldg(code.hf + pQ) : 0u;
+      sm.dflt[3 * lane + 0] = fh;
+      sm.dflt[3 * lane + 1] = fv;
+      sm.dflt[3 * lane + 2] = fh ^ fv;
     }
     __syncwarp();
-    if (lane == 0) esp_table(sm.ex, Sp, sm.E);
+    esp_table_warp(sm.ex, Sp, sm.E);
     __syncwarp();
     const uint32_t total = esp_total(sm.E, Sp);
 
@@ -298,19 +325,14 @@ __global__ void __launch_bounds__(128) k_prep(PrepArgs a) {
         }
         if (!valid) continue;
         ++evaluated;
-        uint32_t z[kWMax];
-        for (int w = 0; w < W; ++w) z[w] = s0[w];
-        xor_delta(z, sm.delta, W, Sp, c);
-        uint32_t orr = 0;
-        for (int w = 0; w < W; ++w) orr |= z[w];
-        if (orr == 0) {
+        if (projection(f0, sm.dflt, Sp, c) == 0 && syndrome_zero(sm.s0, sm.delta, W, Sp, c)) {
           const uint32_t rk = tep_rank(sm.E, Sp, sm.ex, c);
           if (rk < best_rank) { best_rank = rk; best_code = c; }
         }
       }
       w_done = Sp;
     } else {
-      const int wmax = a.w0 < Sp ? a.w0 : Sp;
+      const int wmax = min(min(a.w0, kPrepMaxW0), Sp);
       for (int w = 0; w <= wmax && best_rank == 0xFFFFFFFFu; ++w) {
         const uint32_t nsets = binom16(Sp, w);
         for (uint32_t base = 0; base < nsets; base += 32) {
@@ -318,46 +340,45 @@ __global__ void __launch_bounds__(128) k_prep(PrepArgs a) {
           uint32_t hit_code = 0;
           bool hit = false;
           if (cidx < nsets) {
-            // colex unranking of the altered rank set
-            int P[kSMax];
+            // colex unranking of the altered rank set P[0] < ... < P[w-1]
+            int P[kPrepMaxW0] = {0, 0, 0};
             uint32_t rem = cidx;
             int p = Sp - 1;
-            for (int j = w; j >= 1; --j) {
-              while (binom16(p, j) > rem) --p;
-              P[j - 1] = p;
-              rem -= binom16(p, j);
+#pragma unroll
+            for (int jj = kPrepMaxW0; jj >= 1; --jj) {
+              if (jj > w) continue;
+              while (binom16(p, jj) > rem) --p;
+              P[jj - 1] = p;
+              rem -= binom16(p, jj);
               --p;
             }
             // alternatives in base-3 order, least significant digit first
-            int dig[kSMax];
-            for (int j = 0; j < w; ++j) dig[j] = 0;
+            int dig[kPrepMaxW0] = {0, 0, 0};
             uint32_t n_alpha = 1;
-            for (int j = 0; j < w; ++j) n_alpha *= 3;
+#pragma unroll
+            for (int j = 0; j < kPrepMaxW0; ++j)
+              if (j < w) n_alpha *= 3;
             for (uint32_t al = 0; al < n_alpha; ++al) {
               bool valid = true;
-              uint32_t code = 0;
-              for (int j = 0; j < w; ++j) {
+              uint32_t code_c = 0, z0 = f0;
+#pragma unroll
+              for (int j = 0; j < kPrepMaxW0; ++j) {
+                if (j >= w) continue;
                 if (!((sm.ex[P[j]] >> dig[j]) & 1u)) valid = false;
-                code |= (uint32_t)(dig[j] + 1) << (2 * P[j]);
+                code_c |= (uint32_t)(dig[j] + 1) << (2 * P[j]);
+                z0 ^= sm.dflt[P[j] * 3 + dig[j]];
               }
               if (valid) {
                 ++evaluated;
-                uint32_t z0 = s0[0];
-                for (int j = 0; j < w; ++j) z0 ^= sm.delta[((size_t)P[j] * 3 + dig[j]) * W];
-                if (z0 == 0) {
-                  uint32_t z[kWMax];
-                  for (int ww = 0; ww < W; ++ww) z[ww] = s0[ww];
-                  xor_delta(z, sm.delta, W, Sp, code);
-                  uint32_t orr = 0;
-                  for (int ww = 0; ww < W; ++ww) orr |= z[ww];
-                  if (orr == 0) {
-                    hit = true;
-                    hit_code = code;
-                    break;
-                  }
+                if (z0 == 0 && syndrome_zero(sm.s0, sm.delta, W, Sp, code_c)) {
+                  hit = true;
+                  hit_code = code_c;
+                  break;
                 }
               }
-              for (int j = 0; j < w; ++j) {  // odometer
+#pragma unroll
+              for (int j = 0; j < kPrepMaxW0; ++j) {  // odometer
+                if (j >= w) break;
                 if (++dig[j] < 3) break;
                 dig[j] = 0;
               }
@@ -417,19 +438,14 @@ __global__ void __launch_bounds__(128) k_prep(PrepArgs a) {
       slot = __shfl_sync(kFull, slot, 0);
       FrameRec* rec = a.recs + slot;
       if (lane < NW) a.cw[cw_off + lane] = sm.y[lane];
-      if (lane < W) {
-        uint32_t v = 0;
-#pragma unroll
-        for (int w = 0; w < kWMax; ++w)
-          if (w == lane) v = s0[w];
-        rec->s0[lane] = v;
-      }
+      if (lane < W) rec->s0[lane] = sm.s0[lane];
       if (lane < Sp) {
         rec->pos[lane][0] = sm.pos[2 * lane];
         rec->pos[lane][1] = sm.pos[2 * lane + 1];
         rec->ex[lane] = sm.ex[lane];
       }
       if (lane == 0) {
+        rec->f0 = f0;
         rec->frame = (uint32_t)f;
         rec->code = (uint16_t)code_id;
         rec->sp = (uint8_t)Sp;
@@ -449,7 +465,7 @@ __global__ void __launch_bounds__(128) k_prep(PrepArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int kRowsPerLane = 8;                 // A entries held per lane
 constexpr int kTileRows = 32 * kRowsPerLane;    // A entries per tile
-constexpr int kTileCols = 64;                   // B entries per tile
+constexpr int kTileCols = 128;                  // B entries per tile
 constexpr uint32_t kPadA = 0xA5A5A5A5u;
 constexpr uint32_t kPadB = 0x5A5A5A5Au;
 
@@ -486,8 +502,9 @@ struct SearchSmem {
   uint32_t* Bz;      // [tabB + kTileCols] first word of D_B
   uint16_t* Acode;   // [tabA]
   uint16_t* Bcode;   // [tabB]
-  uint16_t* tiles;   // [max_tiles]
+  uint32_t* tiles;   // [max_tiles] (minw << 16) | (row block << 8) | column block
   uint32_t* delta;   // [kSMax][3][Wmax]
+  uint32_t* dflt;    // [kSMax][3] projections of the deltas
   uint32_t* E;       // [kEStride^2]
   uint32_t* s0;      // [Wmax]
 };
@@ -497,9 +514,10 @@ __host__ __device__ inline size_t search_smem_bytes(int tabA, int tabB, int max_
   b += 4 * (size_t)(tabA + kTileRows);
   b += 4 * (size_t)(tabB + kTileCols);
   b += 2 * (size_t)tabA + 2 * (size_t)tabB;
-  b += 2 * (size_t)max_tiles;
+  b = (b + 3) & ~(size_t)3;
+  b += 4 * (size_t)max_tiles;
   b = (b + 15) & ~(size_t)15;
-  b += 4 * (size_t)kSMax * 3 * Wmax + 4 * kEStride * kEStride + 4 * (size_t)Wmax;
+  b += 4 * (size_t)kSMax * 3 * Wmax + 4 * kSMax * 3 + 4 * kEStride * kEStride + 4 * (size_t)Wmax;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -510,62 +528,76 @@ __device__ inline SearchSmem search_smem(char* base, int tabA, int tabB, int max
   s.Bz = reinterpret_cast<uint32_t*>(p); p += 4 * (size_t)(tabB + kTileCols);
   s.Acode = reinterpret_cast<uint16_t*>(p); p += 2 * (size_t)tabA;
   s.Bcode = reinterpret_cast<uint16_t*>(p); p += 2 * (size_t)tabB;
-  s.tiles = reinterpret_cast<uint16_t*>(p); p += 2 * (size_t)max_tiles;
+  p = base + (((size_t)(p - base) + 3) & ~(size_t)3);
+  s.tiles = reinterpret_cast<uint32_t*>(p); p += 4 * (size_t)max_tiles;
   p = base + (((size_t)(p - base) + 15) & ~(size_t)15);
   s.delta = reinterpret_cast<uint32_t*>(p); p += 4 * (size_t)kSMax * 3 * Wmax;
+  s.dflt = reinterpret_cast<uint32_t*>(p); p += 4 * kSMax * 3;
   s.E = reinterpret_cast<uint32_t*>(p); p += 4 * kEStride * kEStride;
   s.s0 = reinterpret_cast<uint32_t*>(p);
   return s;
 }
 
-// Build one side's table: every valid alternative assignment of ranks
-// [r0, r0 + n) with its first syndrome word (XOR of the deltas, plus `seed`),
-// bucketed by the number of altered ranks. cnt/off are [kSideMax + 2] smem.
-__device__ void build_side(const uint32_t* delta, int W, const uint8_t* ex, int r0, int n, uint32_t seed,
-                           uint32_t* outq, uint16_t* outcode, unsigned* cnt, unsigned* off, int total) {
-  // radix of rank r: 1 + k_r, choices 0, then the existing alternatives
-  for (int i = threadIdx.x; i <= kSideMax + 1; i += blockDim.x) cnt[i] = 0;
+// Build one side's table: every valid alternative assignment of the ranks
+// [r0, r0 + n) (n <= 6) with the projection of its syndrome delta (XOR of the
+// projected deltas, plus `seed`). Entries are grouped by the subset of
+// altered ranks; subsets are ordered by size (the TEP weight), so the table
+// is sorted by weight. A subset whose ranks have k_r existing alternatives
+// contributes prod k_r entries (k_r is 1 or 3), decoded in base 3.
+//   sub_off [2^n + 1]: first entry of each subset; cnt [n + 2]: entries per weight.
+__device__ void build_side(const uint32_t* dflt, const uint8_t* ex, int r0, int n, uint32_t seed, uint32_t* outq,
+                           uint16_t* outcode, unsigned* sub_off, unsigned* sub_size, unsigned* cnt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int nsub = 1 << n;
+  // subset sizes (prod k over its ranks), then each subset's offset in
+  // (weight, subset) order: one thread per subset, no serial chain
+  for (int sb = threadIdx.x; sb < nsub; sb += blockDim.x) {
+    unsigned size = 1;
+    for (int j = 0; j < n; ++j)
+      if ((sb >> j) & 1) size *= (unsigned)__popc(ex[r0 + j] & 7u);
+    sub_size[sb] = size;
+  }
   __syncthreads();
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-      int rem = e, wgt = 0;
-      uint32_t q = seed;
-      uint32_t code = 0;
-      for (int j = 0; j < n; ++j) {
-        const uint32_t exj = ex[r0 + j] & 7u;
-        const int radix = 1 + __popc(exj);
-        const int dgt = rem % radix;
-        rem /= radix;
-        if (dgt) {
-          // dgt-th existing alternative (1-based) -> its code 1..3
-          uint32_t bits = exj;
-          for (int t = 1; t < dgt; ++t) bits &= bits - 1;
-          const uint32_t c = (uint32_t)__ffs(bits);
-          code |= c << (2 * j);
-          q ^= delta[((size_t)(r0 + j) * 3 + (c - 1)) * W];
-          ++wgt;
-        }
-      }
-      if (pass == 0) {
-        atomicAdd(&cnt[wgt], 1u);
-      } else {
-        const unsigned slot = atomicAdd(&off[wgt], 1u);
-        outq[slot] = q;
-        outcode[slot] = (uint16_t)code;
-      }
+  for (int sb = threadIdx.x; sb < nsub; sb += blockDim.x) {
+    const int w = __popc(sb);
+    unsigned off = 0;
+    for (int t = 0; t < nsub; ++t) {
+      const int wt = __popc(t);
+      if (wt < w || (wt == w && t < sb)) off += sub_size[t];
     }
-    __syncthreads();
-    if (pass == 0) {
-      if (threadIdx.x == 0) {
-        unsigned acc = 0;
-        for (int w = 0; w <= kSideMax + 1; ++w) {
-          off[w] = acc;
-          acc += cnt[w];
+    sub_off[sb] = off;
+  }
+  for (int w = threadIdx.x; w <= kSideMax + 1; w += blockDim.x) {
+    unsigned c = 0;
+    for (int t = 0; t < nsub; ++t)
+      if (__popc(t) == w) c += sub_size[t];
+    cnt[w] = c;
+  }
+  __syncthreads();
+  for (int sb = warp; sb < nsub; sb += nwarps) {
+    const unsigned base = sub_off[sb];
+    const unsigned size = sub_size[sb];
+    for (unsigned c = lane; c < size; c += 32) {
+      unsigned rem = c;
+      uint32_t q = seed, code = 0;
+      for (int j = 0; j < n; ++j) {
+        if (!((sb >> j) & 1)) continue;
+        const uint32_t exj = ex[r0 + j] & 7u;
+        uint32_t alt;  // 1 h, 2 v, 3 diag
+        if (exj == 7u) {
+          alt = rem % 3u + 1u;
+          rem /= 3u;
+        } else {
+          alt = (uint32_t)__ffs(exj);  // the single existing alternative
         }
+        code |= alt << (2 * j);
+        q ^= dflt[(r0 + j) * 3 + (alt - 1)];
       }
-      __syncthreads();
+      outq[base + c] = q;
+      outcode[base + c] = (uint16_t)code;
     }
   }
+  __syncthreads();
 }
 
 // weight (number of altered ranks) of table entry i from the bucket counts
@@ -576,17 +608,44 @@ __device__ __forceinline__ int side_weight(const unsigned* cnt, unsigned i) {
   return w;
 }
 
-__global__ void __launch_bounds__(256) k_search(SearchArgs a) {
+// Full-syndrome check of a first-word match; records the canonical position.
+__device__ __noinline__ void verify_hit(const SearchSmem& sm, const uint8_t* ex, int Sp, int W, int nAr, uint32_t acode,
+                                        uint32_t bcode, unsigned long long* best, int* best_w) {
+  const uint32_t c = acode | (bcode << (2 * nAr));
+  uint32_t orr = 0;
+  for (int w = 0; w < W; ++w) {
+    uint32_t z = sm.s0[w];
+    for (int r = 0; r < Sp; ++r) {
+      const uint32_t d = (c >> (2 * r)) & 3u;
+      if (d) z ^= sm.delta[((size_t)r * 3 + (d - 1)) * W + w];
+    }
+    orr |= z;
+  }
+  if (orr == 0) {
+    const uint32_t rk = tep_rank(sm.E, Sp, ex, c);
+    atomicMin(best, ((unsigned long long)rk << 32) | c);
+    atomicMin(best_w, code_weight(c));
+  }
+}
+
+// kMinBlocks sets the register budget (65536 / (256 * kMinBlocks) per thread).
+template <int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks) k_search(SearchArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
-  SearchSmem sm = search_smem(smem_raw, a.tabA, a.tabB, a.max_tiles, a.Wmax);
+  __shared__ SearchSmem s_layout;  // pointers kept in shared memory, not registers
+  if (threadIdx.x == 0) s_layout = search_smem(smem_raw, a.tabA, a.tabB, a.max_tiles, a.Wmax);
+  __syncthreads();
+  const SearchSmem& sm = s_layout;
   __shared__ unsigned s_frame;
-  __shared__ unsigned cntA[kSideMax + 2], offA[kSideMax + 2], cntB[kSideMax + 2], offB[kSideMax + 2];
+  __shared__ unsigned cntA[kSideMax + 2], cntB[kSideMax + 2];
+  __shared__ unsigned subA[1 << kSideMax], subB[1 << kSideMax], sizeA[1 << kSideMax], sizeB[1 << kSideMax];
   __shared__ unsigned s_tile_cnt[2 * kSMax + 2];
   __shared__ unsigned s_n_tiles, s_tile_next;
   __shared__ unsigned long long s_best;  // (rank << 32) | code
   __shared__ int s_best_w;
   __shared__ FrameRec s_rec;
   __shared__ unsigned long long s_eval;
+  __shared__ uint32_t s_qbuf[8][kTileRows];  // slow-path stash, one per warp (<= 8 warps)
   const int lane = threadIdx.x & 31;
   const int n_hard = (int)*(volatile unsigned*)&a.scr->n_hard;
 
@@ -613,8 +672,15 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a) {
       sm.delta[t] = h ^ v;  // alt 0: h, 1: v, 2: h ^ v
     }
     if (threadIdx.x < W) sm.s0[threadIdx.x] = s_rec.s0[threadIdx.x];
+    if (threadIdx.x < 3 * Sp) {
+      const int r = threadIdx.x / 3, alt = threadIdx.x % 3;
+      const uint16_t pI = s_rec.pos[r][0], pQ = s_rec.pos[r][1];
+      const uint32_t h = (alt != 1 && pI != kNoPos) ? __ldg(code.hf + pI) : 0u;
+      const uint32_t v = (alt != 0 && pQ != kNoPos) ? __ldg(code.hf + pQ) : 0u;
+      sm.dflt[threadIdx.x] = h ^ v;
+    }
+    if (threadIdx.x < 32) esp_table_warp(s_rec.ex, Sp, sm.E);
     if (threadIdx.x == 0) {
-      esp_table(s_rec.ex, Sp, sm.E);
       s_best = ~0ull;
       s_best_w = 127;
       s_tile_next = 0;
@@ -634,8 +700,8 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a) {
     unsigned nA = 1, nB = 1;
     for (int r = 0; r < nAr; ++r) nA *= 1u + __popc(s_rec.ex[r] & 7u);
     for (int r = nAr; r < Sp; ++r) nB *= 1u + __popc(s_rec.ex[r] & 7u);
-    build_side(sm.delta, W, s_rec.ex, 0, nAr, sm.s0[0], sm.Aq, sm.Acode, cntA, offA, (int)nA);
-    build_side(sm.delta, W, s_rec.ex, nAr, nBr, 0u, sm.Bz, sm.Bcode, cntB, offB, (int)nB);
+    build_side(sm.dflt, s_rec.ex, 0, nAr, s_rec.f0, sm.Aq, sm.Acode, subA, sizeA, cntA);
+    build_side(sm.dflt, s_rec.ex, nAr, nBr, 0u, sm.Bz, sm.Bcode, subB, sizeB, cntB);
     // pads (never a real entry): rows to a full tile, columns to a full tile
     const unsigned nRB = (nA + kTileRows - 1) / kTileRows, nCB = (nB + kTileCols - 1) / kTileCols;
     for (unsigned i = nA + threadIdx.x; i < nRB * kTileRows; i += blockDim.x) sm.Aq[i] = kPadA;
@@ -656,19 +722,20 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a) {
           atomicAdd(&s_tile_cnt[minw], 1u);
         } else {
           const unsigned slot = atomicAdd(&s_tile_cnt[minw], 1u);
-          sm.tiles[slot] = (uint16_t)((rb << 8) | cb);
+          sm.tiles[slot] = ((unsigned)minw << 16) | (rb << 8) | cb;
         }
       }
       __syncthreads();
       if (pass == 0) {
-        if (threadIdx.x == 0) {
-          unsigned acc = 0;
-          for (int w = 0; w < 2 * kSMax + 2; ++w) {
-            const unsigned c = s_tile_cnt[w];
-            s_tile_cnt[w] = acc;
-            acc += c;
+        if (threadIdx.x < 32) {  // exclusive scan of the per-weight tile counts
+          const unsigned c = threadIdx.x < 2 * kSMax + 2 ? s_tile_cnt[threadIdx.x] : 0u;
+          unsigned incl = c;
+          for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(kFull, incl, o);
+            if ((int)threadIdx.x >= o) incl += t;
           }
-          s_n_tiles = acc;
+          if (threadIdx.x < 2 * kSMax + 2) s_tile_cnt[threadIdx.x] = incl - c;
+          if (threadIdx.x == 31) s_n_tiles = incl;
         }
         __syncthreads();
       }
@@ -683,10 +750,9 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a) {
       ti = __shfl_sync(kFull, ti, 0);
       if (ti >= n_tiles) break;
       const unsigned tile = sm.tiles[ti];
-      const unsigned rb = tile >> 8, cb = tile & 0xFF;
+      const unsigned rb = (tile >> 8) & 0xFF, cb = tile & 0xFF;
       const unsigned row0 = rb * kTileRows, col0 = cb * kTileCols;
-      const int minw = side_weight(cntA, row0) + side_weight(cntB, col0);
-      if (minw > *(volatile int*)&s_best_w) break;  // tiles are sorted by minw
+      if ((int)(tile >> 16) > *(volatile int*)&s_best_w) break;  // tiles are sorted by minw
       uint32_t q[kRowsPerLane];
 #pragma unroll
       for (int t = 0; t < kRowsPerLane; ++t) q[t] = sm.Aq[row0 + lane + 32 * t];
@@ -697,30 +763,19 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a) {
       if (lane == 0) my_eval += (unsigned long long)(min(nA - row0, (unsigned)kTileRows)) *
                                 (unsigned long long)(min(nB - col0, (unsigned)kTileCols));
       if (__any_sync(kFull, any)) {
-        // rare: locate the equal first words and verify every syndrome word
+        // rare: locate the equal projections and verify every syndrome word
+        uint32_t* qs = s_qbuf[threadIdx.x >> 5];
+#pragma unroll
+        for (int t = 0; t < kRowsPerLane; ++t) qs[lane + 32 * t] = q[t];
+        __syncwarp();
         if (any) {
           for (int t = 0; t < kRowsPerLane; ++t) {
             const unsigned row = row0 + lane + 32 * t;
+            const uint32_t qt = qs[lane + 32 * t];
             if (row >= nA) continue;
-            for (int j = 0; j < kTileCols; ++j) {
-              const unsigned col = col0 + j;
-              if (col >= nB || sm.Bz[col] != q[t]) continue;
-              const uint32_t c = (uint32_t)sm.Acode[row] | ((uint32_t)sm.Bcode[col] << (2 * nAr));
-              uint32_t orr = 0;
-              for (int w = 0; w < W; ++w) {
-                uint32_t z = sm.s0[w];
-                for (int r = 0; r < Sp; ++r) {
-                  const uint32_t d = (c >> (2 * r)) & 3u;
-                  if (d) z ^= sm.delta[((size_t)r * 3 + (d - 1)) * W + w];
-                }
-                orr |= z;
-              }
-              if (orr == 0) {
-                const uint32_t rk = tep_rank(sm.E, Sp, s_rec.ex, c);
-                atomicMin(&s_best, ((unsigned long long)rk << 32) | c);
-                atomicMin(&s_best_w, code_weight(c));
-              }
-            }
+            for (int j = 0; j < kTileCols; ++j)
+              if (sm.Bz[col0 + j] == qt && col0 + j < nB)
+                verify_hit(sm, s_rec.ex, Sp, W, nAr, sm.Acode[row], sm.Bcode[col0 + j], &s_best, &s_best_w);
           }
         }
         __syncwarp();
@@ -752,6 +807,363 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a) {
       atomicAdd(&a.scr->search_useful, (unsigned long long)(a.queries[f] - done));
     }
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-per-frame, bit-sliced search for S' <= 10 (at most 4^5 = 1024 entries
+// per side).
+//
+// Every warp owns one frame at a time; its tables live in the warp's own slice
+// of shared memory and the whole set-up runs on warp shuffles, so no
+// block-wide barrier exists and the set-up of one warp overlaps the compares of
+// the others.
+//
+// The compare is bit-sliced. The A side (s0 ^ D_A, weight-sorted) is cut into
+// groups of 32 entries and each group is stored as kPlanes bit-planes: plane b
+// holds bit b of the projections of the group's 32 entries. A lane holds one B
+// entry and expands its projection z into kPlanes masks (all-ones where the bit
+// is 1). For one group,
+//     acc = OR_b (plane_b XOR mask_b)
+// has a zero bit exactly at the entries whose low kPlanes projection bits equal
+// z's: kPlanes 3-input logic ops test 32 TEPs (0.66 integer ops per TEP with
+// the candidate fold). Candidates (false rate 2^-kPlanes) are verified on every
+// syndrome word.
+// ---------------------------------------------------------------------------
+constexpr int kWarpSideMax = 5;
+constexpr int kWarpTab = 1 << (2 * kWarpSideMax);   // 1024 entries per side
+constexpr int kPlanes = 20;                          // projection bits compared per TEP
+constexpr int kGroups = kWarpTab / 32;               // A groups of 32 entries
+constexpr int kGroupUnroll = 4;                      // groups per candidate check
+
+struct WarpSlice {
+  uint32_t* planes;  // [kGroups][kPlanes] bit-planes of the A side
+  uint32_t* Bz;      // [kWarpTab] projection of D_B, weight-sorted
+  uint32_t* delta;   // [10][3][Wmax] full syndrome deltas
+  uint32_t* dflt;    // [10][3] projections of the deltas
+  uint32_t* E;       // [kEStride^2]
+  uint32_t* s0;      // [Wmax]
+  uint32_t* startA;  // [33] first entry of the k-th subset of A in table order
+  uint32_t* startB;  // [33]
+  uint32_t* cumA;    // [8] A entries of weight <= v
+  uint32_t* cumB;    // [8]
+  uint8_t* ordA;     // [32] subset at table position k
+  uint8_t* ordB;     // [32]
+  uint8_t* ex;       // [16]
+  uint16_t* pos;     // [10][2]
+};
+
+__host__ __device__ inline size_t warp_slice_bytes(int Wmax) {
+  size_t words = (size_t)kGroups * kPlanes + kWarpTab + 30 * (size_t)Wmax + 30 + kEStride * kEStride + Wmax + 33 +
+                 33 + 8 + 8 + 8 + 8 + 4 + 10;
+  return (words * 4 + 15) & ~(size_t)15;
+}
+
+__device__ inline WarpSlice warp_slice(char* base, int Wmax) {
+  WarpSlice w;
+  uint32_t* p = reinterpret_cast<uint32_t*>(base);
+  w.planes = p; p += kGroups * kPlanes;
+  w.Bz = p; p += kWarpTab;
+  w.delta = p; p += 30 * Wmax;
+  w.dflt = p; p += 30;
+  w.E = p; p += kEStride * kEStride;
+  w.s0 = p; p += Wmax;
+  w.startA = p; p += 33;
+  w.startB = p; p += 33;
+  w.cumA = p; p += 8;
+  w.cumB = p; p += 8;
+  w.ordA = reinterpret_cast<uint8_t*>(p); p += 8;
+  w.ordB = reinterpret_cast<uint8_t*>(p); p += 8;
+  w.ex = reinterpret_cast<uint8_t*>(p); p += 4;
+  w.pos = reinterpret_cast<uint16_t*>(p);
+  return w;
+}
+
+// Layout of one side's table, computed by one warp. Subsets of the side's n
+// ranks are laid out by (size, colex order), i.e. by TEP weight; the k-th
+// subset's entries start at start[k]; cum[v] = entries of weight <= v.
+// Returns the number of entries.
+__device__ inline unsigned warp_side_layout(const WarpSlice& sl, int r0, int n, uint32_t* start, uint8_t* ord,
+                                            uint32_t* cum) {
+  const int lane = threadIdx.x & 31;
+  const int nsub = 1 << n;
+  unsigned size = 0;
+  int posk = 0, w = 0;
+  if (lane < nsub) {
+    size = 1;
+    int colex = 0;
+    for (int j = 0; j < n; ++j)
+      if ((lane >> j) & 1) {
+        size *= (unsigned)__popc(sl.ex[r0 + j] & 7u);
+        ++w;
+        colex += (int)binom16(j, w);
+      }
+    int before = 0;
+    for (int v = 0; v < w; ++v) before += (int)binom16(n, v);
+    posk = before + colex;
+    ord[posk] = (uint8_t)lane;
+  }
+  __syncwarp();
+  const int src = lane < nsub ? (int)ord[lane] : 0;
+  const unsigned gathered = __shfl_sync(kFull, size, src);
+  const unsigned size_k = lane < nsub ? gathered : 0u;
+  unsigned incl = size_k;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane < nsub) start[lane] = incl - size_k;
+  const unsigned total = __shfl_sync(kFull, incl, 31);
+  if (lane == 0) start[nsub] = total;
+  // cumulative count per weight: subsets of weight <= v end at position sum_{u<=v} C(n,u)
+  if (lane <= n) {
+    int endk = 0;
+    for (int u = 0; u <= lane; ++u) endk += (int)binom16(n, u);
+    cum[lane] = 0;  // filled below
+    (void)endk;
+  }
+  __syncwarp();
+  if (lane <= n) {
+    int endk = 0;
+    for (int u = 0; u <= lane; ++u) endk += (int)binom16(n, u);
+    cum[lane] = start[endk];
+  }
+  for (int v = n + 1 + lane; v < 8; v += 32) cum[v] = total;
+  __syncwarp();
+  return total;
+}
+
+// Table entry e of a side: projection (seed ^ XOR of projected deltas) and the
+// alternative code (2 bits per rank of the side).
+__device__ __forceinline__ void warp_side_entry(const WarpSlice& sl, int r0, int n, const uint32_t* start,
+                                                const uint8_t* ord, uint32_t seed, unsigned e, uint32_t& q,
+                                                uint32_t& code) {
+  const int nsub = 1 << n;
+  int lo = 0, hi = nsub - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  const int sb = ord[lo];
+  unsigned rem = e - start[lo];
+  q = seed;
+  code = 0;
+  for (int j = 0; j < n; ++j) {
+    if (!((sb >> j) & 1)) continue;
+    const uint32_t exj = sl.ex[r0 + j] & 7u;
+    uint32_t alt;
+    if (exj == 7u) {
+      alt = rem % 3u + 1u;
+      rem /= 3u;
+    } else {
+      alt = (uint32_t)__ffs(exj);  // the single existing alternative
+    }
+    code |= alt << (2 * j);
+    q ^= sl.dflt[(r0 + j) * 3 + (alt - 1)];
+  }
+}
+
+// weight of entry e: the number of weights whose cumulative count is <= e
+__device__ __forceinline__ int side_entry_weight(const uint32_t* cum, int n, unsigned e) {
+  int w = 0;
+  while (w < n && cum[w] <= e) ++w;
+  return w;
+}
+
+// OR over the planes of group g of (plane XOR mask): zero bits mark candidates.
+__device__ __forceinline__ uint32_t group_acc(const uint32_t* planes, int g, const uint32_t (&m)[kPlanes]) {
+  const uint4* pl = reinterpret_cast<const uint4*>(planes + g * kPlanes);
+  uint32_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < kPlanes / 4; ++j) {
+    const uint4 p = pl[j];
+    acc |= p.x ^ m[4 * j + 0];
+    acc |= p.y ^ m[4 * j + 1];
+    acc |= p.z ^ m[4 * j + 2];
+    acc |= p.w ^ m[4 * j + 3];
+  }
+  return acc;
+}
+
+template <int kMinBlocks>
+__global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const WarpSlice sl = warp_slice(smem_raw + (threadIdx.x >> 5) * warp_slice_bytes(a.Wmax), a.Wmax);
+  const unsigned n_hard = *(volatile unsigned*)&a.scr->n_hard;
+  unsigned long long my_eval = 0, my_useful = 0;
+
+  for (;;) {
+    unsigned fi = 0;
+    if (lane == 0) fi = atomicAdd(&a.scr->next, 1u);
+    fi = __shfl_sync(kFull, fi, 0);
+    if (fi >= n_hard) break;
+    const FrameRec* rec = a.recs + fi;
+    const int Sp = rec->sp;
+    const int w_done = rec->w_done;
+    const CodeDev code = a.codes[rec->code];
+    const int W = code.W;
+    if (lane < Sp) {
+      sl.ex[lane] = rec->ex[lane];
+      sl.pos[2 * lane] = rec->pos[lane][0];
+      sl.pos[2 * lane + 1] = rec->pos[lane][1];
+    }
+    if (lane < W) sl.s0[lane] = rec->s0[lane];
+    const uint32_t f0 = rec->f0;
+    __syncwarp();
+    for (int t = lane; t < Sp * 3 * W; t += 32) {
+      const int r = t / (3 * W), rem = t % (3 * W), alt = rem / W, w = rem % W;
+      const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
+      const uint32_t h = (alt != 1 && pI != kNoPos) ? __ldg(code.hcol + (size_t)pI * W + w) : 0u;
+      const uint32_t v = (alt != 0 && pQ != kNoPos) ? __ldg(code.hcol + (size_t)pQ * W + w) : 0u;
+      sl.delta[t] = h ^ v;
+    }
+    if (lane < 3 * Sp) {
+      const int r = lane / 3, alt = lane % 3;
+      const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
+      const uint32_t h = (alt != 1 && pI != kNoPos) ? __ldg(code.hf + pI) : 0u;
+      const uint32_t v = (alt != 0 && pQ != kNoPos) ? __ldg(code.hf + pQ) : 0u;
+      sl.dflt[lane] = h ^ v;
+    }
+    esp_table_warp(sl.ex, Sp, sl.E);
+    __syncwarp();
+    const uint32_t total = esp_total(sl.E, Sp);
+    int w_cap = Sp;
+    {
+      uint64_t acc = 0;
+      for (int v = 0; v <= Sp; ++v) {
+        acc += sl.E[Sp * kEStride + v];
+        if (acc >= (uint64_t)a.cap) { w_cap = v; break; }
+      }
+    }
+    const int nAr = Sp >> 1, nBr = Sp - nAr;
+    const unsigned nA = warp_side_layout(sl, 0, nAr, sl.startA, sl.ordA, sl.cumA);
+    const unsigned nB = warp_side_layout(sl, nAr, nBr, sl.startB, sl.ordB, sl.cumB);
+    const int nG = (int)((nA + 31) / 32);
+    // A side as bit-planes (one group of 32 entries per round of ballots)
+    for (int g = 0; g < kGroups; ++g) {
+      uint32_t q = kPadA, cdummy;
+      const unsigned e = 32u * g + lane;
+      if (g < nG) {
+        if (e < nA) warp_side_entry(sl, 0, nAr, sl.startA, sl.ordA, f0, e, q, cdummy);
+        uint32_t mine = 0;
+#pragma unroll
+        for (int b = 0; b < kPlanes; ++b) {
+          const uint32_t pb = __ballot_sync(kFull, (q >> b) & 1u);
+          if (lane == b) mine = pb;
+        }
+        if (lane < kPlanes) sl.planes[g * kPlanes + lane] = mine;
+      } else if (lane < kPlanes) {
+        sl.planes[g * kPlanes + lane] = 0u;
+      }
+    }
+    // B side, scalar projections
+    for (unsigned e = lane; e < nB; e += 32) {
+      uint32_t q, cdummy;
+      warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, e, q, cdummy);
+      sl.Bz[e] = q;
+    }
+    __syncwarp();
+
+    // --- chunks of 32 B entries in weight order, A groups in weight order ----
+    uint32_t best_rank = 0xFFFFFFFFu, best_code = 0;
+    int best_w = 127;
+    const int nCh = (int)((nB + 31) / 32);
+    const int w_lim = w_cap;  // no TEP heavier than the cap's class matters
+    for (int ch = 0; ch < nCh; ++ch) {
+      const int wb = side_entry_weight(sl.cumB, nBr, 32u * ch);
+      const int budget = min(best_w, w_lim) - wb;  // heaviest A weight still worth testing
+      if (budget < 0) break;
+      const unsigned col = 32u * ch + lane;
+      const uint32_t z = col < nB ? sl.Bz[col] : kPadB;
+      uint32_t m[kPlanes];
+#pragma unroll
+      for (int b = 0; b < kPlanes; ++b) m[b] = 0u - ((z >> b) & 1u);
+      // groups holding an A entry of weight <= budget; skip what the
+      // preparation already tested (every TEP of weight <= w_done)
+      int g_end = (int)((sl.cumA[min(budget, nAr)] + 31) / 32);
+      // chunk max weight: if it cannot exceed w_done with the heaviest group, skip
+      const int wb_hi = side_entry_weight(sl.cumB, nBr, min(nB, 32u * ch + 32u) - 1u);
+      if (wb_hi + nAr <= w_done) continue;
+      for (int g0 = 0; g0 < g_end; g0 += kGroupUnroll) {
+        uint32_t cand = 0;
+#pragma unroll
+        for (int u = 0; u < kGroupUnroll; ++u) cand |= ~group_acc(sl.planes, g0 + u, m);
+        if (lane == 0) {
+          const unsigned rows = min(nA, 32u * (g0 + kGroupUnroll)) - min(nA, 32u * g0);
+          my_eval += (unsigned long long)rows * (unsigned long long)min(32u, nB - 32u * ch);
+        }
+        if (__any_sync(kFull, cand)) {
+          // rare: locate candidates of this lane and verify every syndrome word
+          uint32_t lr = 0xFFFFFFFFu, lc = 0;
+          if (cand && col < nB) {
+            uint32_t bcode, bq;
+            warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, bq, bcode);
+            for (int u = 0; u < kGroupUnroll; ++u) {
+              uint32_t c = ~group_acc(sl.planes, g0 + u, m);
+              while (c) {
+                const int i = __ffs(c) - 1;
+                c &= c - 1;
+                const unsigned row = 32u * (g0 + u) + i;
+                if (row >= nA) continue;
+                uint32_t aq, acode;
+                warp_side_entry(sl, 0, nAr, sl.startA, sl.ordA, f0, row, aq, acode);
+                const uint32_t cc = acode | (bcode << (2 * nAr));
+                uint32_t orr = 0;
+                for (int w = 0; w < W; ++w) {
+                  uint32_t zz = sl.s0[w];
+                  for (int r = 0; r < Sp; ++r) {
+                    const uint32_t d = (cc >> (2 * r)) & 3u;
+                    if (d) zz ^= sl.delta[((size_t)r * 3 + (d - 1)) * W + w];
+                  }
+                  orr |= zz;
+                }
+                if (orr == 0) {
+                  const uint32_t rk = tep_rank(sl.E, Sp, sl.ex, cc);
+                  if (rk < lr) { lr = rk; lc = cc; }
+                }
+              }
+            }
+          }
+          const uint32_t wr = __reduce_min_sync(kFull, lr);
+          if (wr < best_rank) {
+            const unsigned who = __ballot_sync(kFull, lr == wr);
+            best_code = __shfl_sync(kFull, lc, __ffs(who) - 1);
+            best_rank = wr;
+            best_w = code_weight(best_code);
+            const int nb = min(best_w, w_lim) - wb;
+            g_end = nb < 0 ? 0 : min(g_end, (int)((sl.cumA[min(nb, nAr)] + 31) / 32));
+          }
+        }
+      }
+    }
+    // --- result -------------------------------------------------------------
+    if (lane == 0) {
+      const unsigned f = rec->frame;
+      uint32_t q_out;
+      if (best_rank != 0xFFFFFFFFu && (uint64_t)best_rank <= (uint64_t)a.cap) {
+        uint32_t* cw = a.cw + rec->cw_off;
+        for (int r = 0; r < Sp; ++r) {
+          const uint32_t d = (best_code >> (2 * r)) & 3u;
+          if (d & 1u) { const uint16_t p = sl.pos[2 * r]; if (p != kNoPos) cw[p >> 5] ^= 1u << (p & 31); }
+          if (d & 2u) { const uint16_t p = sl.pos[2 * r + 1]; if (p != kNoPos) cw[p >> 5] ^= 1u << (p & 31); }
+        }
+        q_out = best_rank;
+        a.abandon[f] = 0;
+      } else {
+        q_out = (uint32_t)((uint64_t)total < (uint64_t)a.cap ? total : (uint64_t)a.cap);
+        a.abandon[f] = 1;
+      }
+      a.queries[f] = q_out;
+      uint32_t done = 0;
+      for (int v = 0; v <= w_done; ++v) done += sl.E[Sp * kEStride + v];
+      my_useful += q_out - done;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (my_eval) atomicAdd(&a.scr->evaluated, my_eval);
+    if (my_useful) atomicAdd(&a.scr->search_useful, my_useful);
   }
 }
 
@@ -805,6 +1217,7 @@ __global__ void __launch_bounds__(128) k_ab(AbArgs a) {
       continue;
     }
     uint32_t s0[kWMax];
+    uint32_t f0 = 0;
 #pragma unroll
     for (int w = 0; w < kWMax; ++w) s0[w] = 0;
     for (int j = lane; j < N; j += 32)
@@ -812,7 +1225,9 @@ __global__ void __launch_bounds__(128) k_ab(AbArgs a) {
 #pragma unroll
         for (int w = 0; w < kWMax; ++w)
           if (w < W) s0[w] ^= __ldg(a.code.hcol + (size_t)j * W + w);
+        f0 ^= __ldg(a.code.hf + j);
       }
+    for (int o = 16; o; o >>= 1) f0 ^= __shfl_xor_sync(kFull, f0, o);
 #pragma unroll
     for (int w = 0; w < kWMax; ++w)
       if (w < W) {
@@ -848,8 +1263,8 @@ __global__ void __launch_bounds__(128) k_ab(AbArgs a) {
             rem -= binom_big(lo, j);
             hiP = lo - 1;
           }
-          uint32_t z0 = s0[0];
-          for (int j = 0; j < w; ++j) z0 ^= __ldg(a.code.hcol + (size_t)P[j] * W);
+          uint32_t z0 = f0;
+          for (int j = 0; j < w; ++j) z0 ^= __ldg(a.code.hf + P[j]);
           if (z0 == 0) {
             uint32_t orr = 0;
             for (int ww = 0; ww < W; ++ww) {
@@ -959,6 +1374,15 @@ static int m_of(int M) {
   }
 }
 
+typedef void (*PrepKernel)(PrepArgs);
+static PrepKernel prep_kernel_for(int Wmax) {
+  if (Wmax <= 1) return k_prep<1>;
+  if (Wmax <= 2) return k_prep<2>;
+  if (Wmax <= 4) return k_prep<4>;
+  if (Wmax <= 8) return k_prep<8>;
+  return k_prep<16>;
+}
+
 static QamConst make_qam_const() {
   QamConst c{};
   for (int m = 1; m <= 4; ++m) {
@@ -979,6 +1403,47 @@ static int sm_count() {
     if (n <= 0) n = 1;
   }
   return n;
+}
+
+// Persistent launch of the search kernel: one wave of CTAs (as many as fit
+// on every SM) pulling frames from the work queue. variant: register budget
+// (4, 6 or 8 CTAs of 256 threads per SM; 0 = 4).
+template <int B>
+static int launch_search_t(const SearchArgs& s, int threads, size_t smem, cudaStream_t st) {
+  if (cudaFuncSetAttribute(k_search<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GRAND_E_CUDA;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search<B>, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  k_search<B><<<sm_count() * per_sm, threads, smem, st>>>(s);
+  return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
+}
+
+template <int B>
+static int launch_search_warp_t(const SearchArgs& s, cudaStream_t st) {
+  const size_t smem = warp_slice_bytes(s.Wmax) * 4;
+  if (cudaFuncSetAttribute(k_search_warp<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GRAND_E_CUDA;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_warp<B>, 128, smem);
+  if (per_sm < 1) per_sm = 1;
+  k_search_warp<B><<<sm_count() * per_sm, 128, smem, st>>>(s);
+  return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
+}
+
+static int launch_search(const SearchArgs& s, int threads, size_t smem, int variant, cudaStream_t st) {
+  if (s.warp_kernel) {
+    switch (variant) {
+      case 4: return launch_search_warp_t<4>(s, st);
+      case 8: return launch_search_warp_t<8>(s, st);
+      default: return launch_search_warp_t<6>(s, st);
+    }
+  }
+  switch (variant) {
+    case 6: return launch_search_t<6>(s, threads, smem, st);
+    case 8: return launch_search_t<8>(s, threads, smem, st);
+    default: return launch_search_t<4>(s, threads, smem, st);
+  }
 }
 
 #define CU(x)                                   \
@@ -1011,20 +1476,21 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     a.w0 = p->tiles[2] > 0 ? (p->tiles[2] > 3 ? 3 : p->tiles[2]) : 2;
     const int warps = 4;
     const size_t prep_smem = prep_warp_bytes(Lmax, Wmax) * warps;
+    const int64_t want = (n_frames + warps - 1) / warps;
+    const int grid = (int)(want < (int64_t)sm_count() * 64 ? want : (int64_t)sm_count() * 64);
+    auto kp = prep_kernel_for(Wmax);
     if (prep_smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem) != cudaSuccess) {
+        cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem) != cudaSuccess) {
       rc = GRAND_E_CUDA;
       break;
     }
-    const int64_t want = (n_frames + warps - 1) / warps;
-    const int grid = (int)(want < (int64_t)sm_count() * 64 ? want : (int64_t)sm_count() * 64);
     if (stats) {
       for (int i = 0; i < 3; ++i)
         if (cudaEventCreate(&ev[i]) != cudaSuccess) { rc = GRAND_E_CUDA; break; }
       if (rc) break;
       cudaEventRecord(ev[0], st);
     }
-    k_prep<<<grid, 32 * warps, prep_smem, st>>>(a);
+    kp<<<grid, 32 * warps, prep_smem, st>>>(a);
     if (stats) cudaEventRecord(ev[1], st);
     if (cudaGetLastError() != cudaSuccess) { rc = GRAND_E_CUDA; break; }
 
@@ -1045,20 +1511,16 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
       }
       s.max_tiles = ((s.tabA + kTileRows - 1) / kTileRows) * ((s.tabB + kTileCols - 1) / kTileCols);
       s.Wmax = Wmax;
+      s.warp_kernel = (Smax <= 2 * kWarpSideMax && s.split <= 0) ? 1 : 0;
       s.cw = proto.cw;
       s.queries = proto.queries;
       s.abandon = proto.abandon;
       const int threads = p->tiles[0] > 0 ? 32 * (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 256;
       const size_t smem = search_smem_bytes(s.tabA, s.tabB, s.max_tiles, Wmax);
-      if (cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      if (launch_search(s, threads, smem, p->tiles[3], st) != GRAND_OK) {
         rc = GRAND_E_CUDA;
         break;
       }
-      int per_sm = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search, threads, smem);
-      if (per_sm < 1) per_sm = 1;
-      k_search<<<sm_count() * per_sm, threads, smem, st>>>(s);
-      if (cudaGetLastError() != cudaSuccess) { rc = GRAND_E_CUDA; break; }
     }
     if (stats) {
       cudaEventRecord(ev[2], st);
@@ -1396,12 +1858,13 @@ extern "C" int grand_decode_symbols_noalloc(const grand_code* c, const grand_par
   a.w0 = p->tiles[2] > 0 ? (p->tiles[2] > 3 ? 3 : p->tiles[2]) : 2;
   const int warps = 4;
   const size_t prep_smem = prep_warp_bytes(L, c->W) * warps;
+  auto kp = prep_kernel_for(c->W);
   if (prep_smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem) != cudaSuccess)
+      cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem) != cudaSuccess)
     return GRAND_E_CUDA;
   const int64_t want = (n_frames + warps - 1) / warps;
   const int grid = (int)(want < (int64_t)sm_count() * 64 ? want : (int64_t)sm_count() * 64);
-  k_prep<<<grid, 32 * warps, prep_smem, st>>>(a);
+  kp<<<grid, 32 * warps, prep_smem, st>>>(a);
   if (cudaGetLastError() != cudaSuccess) return GRAND_E_CUDA;
   const int Smax = p->S < L ? p->S : L;
   if (Smax > 6) {
@@ -1419,18 +1882,13 @@ extern "C" int grand_decode_symbols_noalloc(const grand_code* c, const grand_par
     }
     s.max_tiles = ((s.tabA + kTileRows - 1) / kTileRows) * ((s.tabB + kTileCols - 1) / kTileCols);
     s.Wmax = c->W;
+    s.warp_kernel = (Smax <= 2 * kWarpSideMax && s.split <= 0) ? 1 : 0;
     s.cw = cw;
     s.queries = queries;
     s.abandon = abandon;
     const int threads = p->tiles[0] > 0 ? 32 * (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 256;
     const size_t smem = search_smem_bytes(s.tabA, s.tabB, s.max_tiles, c->W);
-    if (cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return GRAND_E_CUDA;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search, threads, smem);
-    if (per_sm < 1) per_sm = 1;
-    k_search<<<sm_count() * per_sm, threads, smem, st>>>(s);
-    if (cudaGetLastError() != cudaSuccess) return GRAND_E_CUDA;
+    if (launch_search(s, threads, smem, p->tiles[3], st) != GRAND_OK) return GRAND_E_CUDA;
   }
   return GRAND_OK;
 }

@@ -134,12 +134,17 @@ __device__ __forceinline__ uint16_t flip_pos_Q(int i, int m, int l, int dir, int
 // ---------------------------------------------------------------------------
 constexpr int kEStride = kSMax + 1;
 
-__device__ inline void esp_table(const uint8_t* ex, int Sp, uint32_t* E) {
-  for (int v = 0; v <= Sp; ++v) E[v] = (v == 0) ? 1u : 0u;
+// One full warp: lane v carries e_v along x (E[x+1][v] = E[x][v] + k_x E[x][v-1]).
+__device__ inline void esp_table_warp(const uint8_t* ex, int Sp, uint32_t* E) {
+  const int v = threadIdx.x & 31;
+  uint32_t e = (v == 0) ? 1u : 0u;
+  if (v <= Sp) E[v] = e;
   for (int x = 0; x < Sp; ++x) {
     const uint32_t k = __popc(ex[x] & 7u);
-    for (int v = 0; v <= Sp; ++v)
-      E[(x + 1) * kEStride + v] = E[x * kEStride + v] + (v ? k * E[x * kEStride + v - 1] : 0u);
+    uint32_t up = __shfl_up_sync(0xFFFFFFFFu, e, 1);
+    if (v == 0) up = 0;
+    e += k * up;
+    if (v <= Sp) E[(x + 1) * kEStride + v] = e;
   }
 }
 

@@ -18,8 +18,14 @@ constexpr uint16_t kNoPos = 0xFFFF;  // alternative bit beyond N (padding): no s
 
 // Device view of one code: column-packed parity-check matrix.
 //   hcol[j * W + w] bit b = H[32 w + b][j]   (column j of H, W words)
+//   hf[j] = XOR of p_r over the rows r with H[r][j] = 1, for fixed
+//           pseudo-random 32-bit words p_r: a random linear projection of
+//           column j. The projection of a syndrome is the XOR of hf over the
+//           flipped positions; a zero syndrome has a zero projection, so it
+//           is a filter in front of the full test (false matches ~ 2^-32).
 struct CodeDev {
   const uint32_t* hcol;
+  const uint32_t* hf;
   int32_t N, K, R, W;
 };
 
@@ -34,7 +40,7 @@ struct FrameRec {
   uint32_t s0[kWMax];        // base syndrome H y
   uint16_t pos[kSMax][2];    // bit position flipped by the I / Q alternative of rank r
   uint8_t ex[kSMax];         // bit0 h exists, bit1 v exists, bit2 diag exists
-  uint8_t pad[4];
+  uint32_t f0;               // projection of s0 (see CodeDev::hf)
 };
 static_assert(sizeof(FrameRec) % 8 == 0, "FrameRec alignment");
 
@@ -51,7 +57,7 @@ struct Scratch {
 // Opaque code object of the ABI.
 struct grand_code {
   int N, K, R, W;
-  uint32_t* d_hcol;                 // device, N * W words
+  uint32_t* d_hcol;                 // device, N * W words, then the N projections hf
   grand::CodeDev* d_dev;            // device copy of the CodeDev (for code tables)
   grand::CodeDev dev;               // host copy of the device view
   int device;                       // CUDA device the object lives on
