@@ -93,12 +93,13 @@ struct PrepSmem {
   uint32_t* E;      // [kEStride^2]
   uint32_t* s0;     // [Wmax] base syndrome
   uint8_t* ex;      // [kSMax]
+  uint8_t* sel;     // [kSMax] symbol of each reliability rank (L <= 32)
   uint16_t* pos;    // [kSMax][2]
 };
 
 __host__ __device__ inline size_t prep_warp_bytes(int Lmax, int Wmax) {
   size_t words = 2 * (size_t)Lmax + 32 + (size_t)kSMax * 3 * Wmax + kSMax * 3 + kEStride * kEStride + Wmax +
-                 kSMax / 4 + 1 + kSMax;
+                 kSMax / 4 + 1 + kSMax / 4 + 1 + kSMax;
   return ((words * 4) + 15) & ~(size_t)15;
 }
 
@@ -113,7 +114,8 @@ __device__ inline PrepSmem prep_smem(char* base, int Lmax, int Wmax) {
   s.E = p; p += kEStride * kEStride;
   s.s0 = p; p += Wmax;
   s.pos = reinterpret_cast<uint16_t*>(p); p += kSMax;
-  s.ex = reinterpret_cast<uint8_t*>(p);
+  s.ex = reinterpret_cast<uint8_t*>(p); p += kSMax / 4 + 1;
+  s.sel = reinterpret_cast<uint8_t*>(p);
   return s;
 }
 
@@ -266,6 +268,19 @@ __global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
 
     // --- Steps 2-3: the S' least reliable symbols, by (key, index) ---------
     int my_sel = -1;
+    if (L <= 32) {
+      // one symbol per lane: its rank is the number of (key, index) pairs below it
+      const uint32_t k_i = lane < L ? sm.key[lane] : 0xFFFFFFFFu;
+      int rank = 0;
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) {
+        const uint32_t k_j = __shfl_sync(kFull, k_i, j);
+        rank += (k_j < k_i || (k_j == k_i && j < lane)) ? 1 : 0;
+      }
+      if (lane < L && rank < Sp) sm.sel[rank] = (uint8_t)lane;
+      __syncwarp();
+      if (lane < Sp) my_sel = sm.sel[lane];
+    } else
     for (int r = 0; r < Sp; ++r) {
       uint32_t best_k = 0xFFFFFFFFu, best_i = 0xFFFFFFFFu;
       for (int i = lane; i < L; i += 32) {
@@ -834,7 +849,7 @@ constexpr int kWarpSideMax = 5;
 constexpr int kWarpTab = 1 << (2 * kWarpSideMax);   // 1024 entries per side
 constexpr int kPlanes = 20;                          // projection bits compared per TEP
 constexpr int kGroups = kWarpTab / 32;               // A groups of 32 entries
-constexpr int kGroupUnroll = 4;                      // groups per candidate check
+constexpr int kGroupUnroll = 8;                      // groups per candidate check
 
 struct WarpSlice {
   uint32_t* planes;  // [kGroups][kPlanes] bit-planes of the A side
@@ -849,13 +864,15 @@ struct WarpSlice {
   uint32_t* cumB;    // [8]
   uint8_t* ordA;     // [32] subset at table position k
   uint8_t* ordB;     // [32]
+  uint8_t* invA;     // [32] table position of subset sb
+  uint8_t* invB;     // [32]
   uint8_t* ex;       // [16]
   uint16_t* pos;     // [10][2]
 };
 
 __host__ __device__ inline size_t warp_slice_bytes(int Wmax) {
   size_t words = (size_t)kGroups * kPlanes + kWarpTab + 30 * (size_t)Wmax + 30 + kEStride * kEStride + Wmax + 33 +
-                 33 + 8 + 8 + 8 + 8 + 4 + 10;
+                 33 + 8 + 8 + 8 + 8 + 8 + 8 + 4 + 10;
   return (words * 4 + 15) & ~(size_t)15;
 }
 
@@ -874,6 +891,8 @@ __device__ inline WarpSlice warp_slice(char* base, int Wmax) {
   w.cumB = p; p += 8;
   w.ordA = reinterpret_cast<uint8_t*>(p); p += 8;
   w.ordB = reinterpret_cast<uint8_t*>(p); p += 8;
+  w.invA = reinterpret_cast<uint8_t*>(p); p += 8;
+  w.invB = reinterpret_cast<uint8_t*>(p); p += 8;
   w.ex = reinterpret_cast<uint8_t*>(p); p += 4;
   w.pos = reinterpret_cast<uint16_t*>(p);
   return w;
@@ -884,7 +903,7 @@ __device__ inline WarpSlice warp_slice(char* base, int Wmax) {
 // subset's entries start at start[k]; cum[v] = entries of weight <= v.
 // Returns the number of entries.
 __device__ inline unsigned warp_side_layout(const WarpSlice& sl, int r0, int n, uint32_t* start, uint8_t* ord,
-                                            uint32_t* cum) {
+                                            uint8_t* inv, uint32_t* cum) {
   const int lane = threadIdx.x & 31;
   const int nsub = 1 << n;
   unsigned size = 0;
@@ -902,6 +921,7 @@ __device__ inline unsigned warp_side_layout(const WarpSlice& sl, int r0, int n, 
     for (int v = 0; v < w; ++v) before += (int)binom16(n, v);
     posk = before + colex;
     ord[posk] = (uint8_t)lane;
+    inv[lane] = (uint8_t)posk;
   }
   __syncwarp();
   const int src = lane < nsub ? (int)ord[lane] : 0;
@@ -934,7 +954,9 @@ __device__ inline unsigned warp_side_layout(const WarpSlice& sl, int r0, int n, 
 }
 
 // Table entry e of a side: projection (seed ^ XOR of projected deltas) and the
-// alternative code (2 bits per rank of the side).
+// alternative code (2 bits per rank of the side). Within a subset's block the
+// entries follow the doubling order of warp_fill_side: the highest rank's
+// alternative is the least significant base-k digit.
 __device__ __forceinline__ void warp_side_entry(const WarpSlice& sl, int r0, int n, const uint32_t* start,
                                                 const uint8_t* ord, uint32_t seed, unsigned e, uint32_t& q,
                                                 uint32_t& code) {
@@ -948,7 +970,7 @@ __device__ __forceinline__ void warp_side_entry(const WarpSlice& sl, int r0, int
   unsigned rem = e - start[lo];
   q = seed;
   code = 0;
-  for (int j = 0; j < n; ++j) {
+  for (int j = n - 1; j >= 0; --j) {
     if (!((sb >> j) & 1)) continue;
     const uint32_t exj = sl.ex[r0 + j] & 7u;
     uint32_t alt;
@@ -961,6 +983,44 @@ __device__ __forceinline__ void warp_side_entry(const WarpSlice& sl, int r0, int
     code |= alt << (2 * j);
     q ^= sl.dflt[(r0 + j) * 3 + (alt - 1)];
   }
+}
+
+// Fill one side's weight-sorted table by doubling: the block of subset S is
+// the block of S minus its highest rank j, each entry XORed with one of j's
+// projected deltas (entry c = parent entry c / k_j, alternative c % k_j).
+// Blocks are visited in table order, so parents (one rank lighter) are ready.
+__device__ inline void warp_fill_side(const WarpSlice& sl, int r0, int n, const uint32_t* start, const uint8_t* ord,
+                                      const uint8_t* inv, uint32_t seed, uint32_t* out) {
+  const int lane = threadIdx.x & 31;
+  const int nsub = 1 << n;
+  if (lane == 0) out[0] = seed;  // the empty subset is first
+  __syncwarp();
+  int prev_w = 0;
+  for (int k = 1; k < nsub; ++k) {
+    const int sb = ord[k];
+    const int w = __popc(sb);
+    if (w != prev_w) {  // the parents of this weight are complete
+      __syncwarp();
+      prev_w = w;
+    }
+    const unsigned base = start[k], size = start[k + 1] - base;
+    if (size == 0) continue;
+    const int j = 31 - __clz(sb);
+    const int pk = inv[sb & ~(1 << j)];
+    const unsigned pbase = start[pk];
+    const uint32_t exj = sl.ex[r0 + j] & 7u;
+    const uint32_t* dj = sl.dflt + (r0 + j) * 3;
+    if (exj == 7u) {
+      for (unsigned c = lane; c < size; c += 32) {
+        const unsigned pi = c / 3u, ai = c - 3u * pi;
+        out[base + c] = out[pbase + pi] ^ dj[ai];
+      }
+    } else {
+      const uint32_t d = dj[__ffs(exj) - 1];
+      for (unsigned c = lane; c < size; c += 32) out[base + c] = out[pbase + c] ^ d;
+    }
+  }
+  __syncwarp();
 }
 
 // weight of entry e: the number of weights whose cumulative count is <= e
@@ -1037,15 +1097,16 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
       }
     }
     const int nAr = Sp >> 1, nBr = Sp - nAr;
-    const unsigned nA = warp_side_layout(sl, 0, nAr, sl.startA, sl.ordA, sl.cumA);
-    const unsigned nB = warp_side_layout(sl, nAr, nBr, sl.startB, sl.ordB, sl.cumB);
+    const unsigned nA = warp_side_layout(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, sl.cumA);
+    const unsigned nB = warp_side_layout(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, sl.cumB);
     const int nG = (int)((nA + 31) / 32);
-    // A side as bit-planes (one group of 32 entries per round of ballots)
+    // A side: scalar projections into the B buffer, then bit-planes (one group
+    // of 32 entries per round of ballots)
+    warp_fill_side(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, f0, sl.Bz);
     for (int g = 0; g < kGroups; ++g) {
-      uint32_t q = kPadA, cdummy;
-      const unsigned e = 32u * g + lane;
       if (g < nG) {
-        if (e < nA) warp_side_entry(sl, 0, nAr, sl.startA, sl.ordA, f0, e, q, cdummy);
+        const unsigned e = 32u * g + lane;
+        const uint32_t q = e < nA ? sl.Bz[e] : kPadA;
         uint32_t mine = 0;
 #pragma unroll
         for (int b = 0; b < kPlanes; ++b) {
@@ -1057,13 +1118,9 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
         sl.planes[g * kPlanes + lane] = 0u;
       }
     }
-    // B side, scalar projections
-    for (unsigned e = lane; e < nB; e += 32) {
-      uint32_t q, cdummy;
-      warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, e, q, cdummy);
-      sl.Bz[e] = q;
-    }
     __syncwarp();
+    // B side, scalar projections
+    warp_fill_side(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, 0u, sl.Bz);
 
     // --- chunks of 32 B entries in weight order, A groups in weight order ----
     uint32_t best_rank = 0xFFFFFFFFu, best_code = 0;
@@ -1085,14 +1142,11 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
       // chunk max weight: if it cannot exceed w_done with the heaviest group, skip
       const int wb_hi = side_entry_weight(sl.cumB, nBr, min(nB, 32u * ch + 32u) - 1u);
       if (wb_hi + nAr <= w_done) continue;
-      for (int g0 = 0; g0 < g_end; g0 += kGroupUnroll) {
+      int g0 = 0;
+      for (; g0 < g_end; g0 += kGroupUnroll) {
         uint32_t cand = 0;
 #pragma unroll
         for (int u = 0; u < kGroupUnroll; ++u) cand |= ~group_acc(sl.planes, g0 + u, m);
-        if (lane == 0) {
-          const unsigned rows = min(nA, 32u * (g0 + kGroupUnroll)) - min(nA, 32u * g0);
-          my_eval += (unsigned long long)rows * (unsigned long long)min(32u, nB - 32u * ch);
-        }
         if (__any_sync(kFull, cand)) {
           // rare: locate candidates of this lane and verify every syndrome word
           uint32_t lr = 0xFFFFFFFFu, lc = 0;
@@ -1136,6 +1190,8 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
           }
         }
       }
+      if (lane == 0)
+        my_eval += (unsigned long long)min(nA, 32u * (unsigned)g0) * (unsigned long long)min(32u, nB - 32u * ch);
     }
     // --- result -------------------------------------------------------------
     if (lane == 0) {
