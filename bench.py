@@ -60,6 +60,10 @@ CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5}
 # x 2.07 GHz maximum SM clock.
 SMS, ALU_LANES, MAX_CLOCK_GHZ = 152, 64, 2.07
 ALU_PEAK_TOPS = SMS * ALU_LANES * MAX_CLOCK_GHZ / 1000.0
+# Counters of the search kernel from one ncu capture (profiles/k_search_warp_c2_small.md),
+# valid only while csrc/decode.cu is the captured source (sha256 prefix).
+NCU_SEARCH = {"sha": "1c0b187066c9008a", "dram_bytes_per_hard_frame": 1551872 / 9596,
+              "alu_pipe_active": 0.770, "alu_ops_per_check": 0.98}
 
 
 def make_inputs(cfg, rank, info_by_N):
@@ -97,7 +101,7 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
@@ -229,7 +233,7 @@ def run_reference(args, cfg):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=("gpu", "reference"))
     ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
@@ -383,11 +387,22 @@ def main():
     # ---- roofline of the dominant kernel (the TEP search)
     roofline = None
     if alg_words is not None and sum(search_ms) > 0:
+        import hashlib
+
         ops = search_useful / args.steps * alg_words
         achieved = ops / (statistics.mean(search_ms) / 1e3) / 1e12
+        src = os.path.join(ROOT, "paper_2405_01808_gb300", "csrc", "decode.cu")
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        fresh = sha == NCU_SEARCH["sha"] and cfg["name"] == "c2"
+        kernel = "k_search_warp" if cfg["S"] <= 10 else "k_search"
         roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                    "frac": achieved / ALU_PEAK_TOPS, "traffic": None, "kernel": "k_search",
-                    "ops_per_check": alg_words,
+                    "frac": achieved / ALU_PEAK_TOPS,
+                    "traffic": NCU_SEARCH["dram_bytes_per_hard_frame"] * hard / args.steps if fresh else None,
+                    "kernel": kernel, "ops_per_check": alg_words,
+                    "ops_per_check_note": "survey model: (N-K)/32 LOP3 per useful check; the kernel compares a "
+                                          "20-bit projection bit-sliced (21 ops per 32 checks) and verifies matches",
+                    "ncu_alu_pipe_active": NCU_SEARCH["alu_pipe_active"] if fresh else None,
+                    "ncu_alu_ops_per_evaluated_check": NCU_SEARCH["alu_ops_per_check"] if fresh else None,
                     "peak_source": f"derived: {SMS} SMs x {ALU_LANES} ALU lanes/clk x {MAX_CLOCK_GHZ} GHz"}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
