@@ -299,8 +299,20 @@ def main():
     d_ab = torch.empty(n_frames, dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    tune = None
+    plan = None
+    if cfg["kind"] == "mixed":
+        # tiles from the autotuner on a 100,000-frame sample, then the whole
+        # batch captured once into a CUDA graph (one replay per step)
+        n_tune = min(n_frames, 100000)
+        tune = g.autotune_mixed(codes, p, d_desc[: n_tune * g.FRAME_DESC_DTYPE.itemsize], d_sym, n_cw)
+        plan = g.plan_mixed(codes, p, d_desc, d_sym, d_cw, d_q, d_ab)
+
     def step(sym, stats=True):
         if cfg["kind"] == "mixed":
+            if sym is d_sym and not stats:
+                plan.launch()
+                return None
             return g.decode_mixed(codes, p, d_desc, sym, n_cw, cw=d_cw, queries=d_q, abandon=d_ab, stats=stats)
         cw2 = d_cw.view(n_frames, -1)
         return g.decode_symbols(codes[0], p, sym, cw=cw2, queries=d_q, abandon=d_ab, stats=stats)
@@ -320,21 +332,28 @@ def main():
     search_useful = 0
     evaluated = 0
     hard = 0
+    graph_steps = cfg["kind"] == "mixed"
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r = step(d_sym, stats=True)
+        r = step(d_sym, stats=not graph_steps)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        search_ms.append(r["search_ms"])
-        prep_ms.append(r["prep_ms"])
-        search_useful += r["search_useful"]
-        evaluated += r["evaluated_checks"]
-        hard += r["hard_frames"]
+        if r is not None:
+            search_ms.append(r["search_ms"])
+            prep_ms.append(r["prep_ms"])
+            search_useful += r["search_useful"]
+            evaluated += r["evaluated_checks"]
+            hard += r["hard_frames"]
         useful_total += int(d_q.to(torch.int64).sum().item())  # outside the events
+    if graph_steps:  # kernel split and counters from one direct call of the same batch
+        r = step(d_sym, stats=True)
+        search_ms, prep_ms = [r["search_ms"]], [r["prep_ms"]]
+        search_useful, evaluated, hard = (r["search_useful"] * args.steps, r["evaluated_checks"] * args.steps,
+                                          r["hard_frames"] * args.steps)
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = sum(step_ms)
@@ -383,6 +402,29 @@ def main():
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_value = (useful_total / args.steps) / (statistics.mean(e2e_ms) / 1e3)
+
+    # ---- the plain one-frame-per-launch GPU path on a sample (same frames, same results)
+    one = None
+    if cfg["kind"] in ("qam", "mixed"):
+        n_one = min(2000, n_frames)
+        idx = np.linspace(0, n_frames - 1, n_one).astype(np.int64)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for f in idx.tolist():
+            if cfg["kind"] == "mixed":
+                dsz = g.FRAME_DESC_DTYPE.itemsize
+                g.decode_mixed(codes, p, d_desc[f * dsz:(f + 1) * dsz], d_sym, n_cw, cw=d_cw, queries=d_q[f:f + 1],
+                               abandon=d_ab[f:f + 1])
+            else:
+                g.decode_symbols(codes[0], p, d_sym[f:f + 1], cw=d_cw.view(n_frames, -1)[f:f + 1],
+                                 queries=d_q[f:f + 1], abandon=d_ab[f:f + 1])
+        e1.record(stream)
+        e1.synchronize()
+        one_ms = e0.elapsed_time(e1)
+        one = {"frames_per_s": n_one / (one_ms / 1e3), "ms_per_frame": one_ms / n_one,
+               "sample": f"{n_one} frames evenly spread over the batch, one decode call each"}
 
     # ---- roofline of the dominant kernel (the TEP search)
     roofline = None
@@ -434,10 +476,13 @@ def main():
             "hard_frames_per_step": hard / args.steps,
             "kernel_ms": {"prep": statistics.mean(prep_ms), "search": statistics.mean(search_ms)},
             "roofline": roofline,
+            "one_frame_per_launch": one,
+            "autotune": tune,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "checks/s", "h2d_bytes_per_step": int(h_sym.numel() * h_sym.element_size()),
                     "d2h_bytes_per_step": int(n_cw * 4 + n_frames * 5), "ms_per_step": statistics.mean(e2e_ms)},
             "gpu_launches": 2 * args.steps if cfg["kind"] != "ab" else args.steps,
+            "graph": bool(graph_steps),
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -227,6 +227,51 @@ int grand_decode_mixed(const grand_code* const* codes, int n_codes, const grand_
                        float N0, uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon,
                        grand_stats* stats, void* stream);
 
+/* Plans: one decode call captured into a CUDA graph, replayed by
+ * grand_plan_launch on any stream with the buffers given at creation (the
+ * caller refills the inputs between launches; outputs are overwritten). The
+ * captured sequence is the same as the direct call's (counter reset,
+ * preparation kernel, persistent search kernel with its work queue, scratch as
+ * graph memory nodes), so results are identical. Creation runs the call once
+ * eagerly on a private stream and synchronises it; it must not be called
+ * while the calling thread captures a stream. A plan's launches must not
+ * overlap each other in time (they share the buffers); the caller orders them.
+ *   grand_plan_symbols: arguments as grand_decode_symbols (n_frames >= 1).
+ *   grand_plan_mixed:   arguments as grand_decode_mixed; the code table is
+ *                       copied into the plan (codes must outlive the plan).
+ * Errors: as the direct calls, plus GRAND_E_CUDA if capture fails. */
+typedef struct grand_plan grand_plan;
+int grand_plan_symbols(const grand_code* code, const grand_params* params, const void* symbols, int64_t n_frames,
+                       float N0, uint32_t* cw, uint32_t* queries, uint8_t* abandon, grand_plan** out);
+int grand_plan_mixed(const grand_code* const* codes, int n_codes, const grand_params* params,
+                     const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
+                     float N0, uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon,
+                     grand_plan** out);
+int grand_plan_launch(grand_plan* plan, void* stream);
+int grand_plan_destroy(grand_plan* plan);
+
+/* Launch-shape autotuner. Times every candidate `tiles` setting (preparation
+ * weights, search register budget, and for S' > 10 the CTA width) on the
+ * given sample with CUDA events (median of 3 runs after one untimed run) and
+ * writes the fastest into params->tiles. Results never depend on the tiles.
+ *   cache_path  host path of a text cache (NULL: no cache). Lines are
+ *               "key t0 t1 t2 t3 ms"; the key holds the GPU name and the
+ *               workload (N, K, M, S, cap, likelihood variant; the codes of a
+ *               mixed batch). A cached key is used without timing.
+ *   out         host, may be NULL: best time, candidates tried, cache hit.
+ * The sample buffers are device memory; the tuner allocates its own outputs
+ * (cudaMalloc) and synchronises `stream`. Errors: as the decode calls. */
+typedef struct grand_tune_result {
+  float best_ms;
+  int32_t candidates;
+  int32_t from_cache;
+} grand_tune_result;
+int grand_autotune(const grand_code* code, grand_params* params, const void* symbols, int64_t n_frames, float N0,
+                   const char* cache_path, void* stream, grand_tune_result* out);
+int grand_autotune_mixed(const grand_code* const* codes, int n_codes, grand_params* params,
+                         const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
+                         float N0, int64_t n_cw_words, const char* cache_path, void* stream, grand_tune_result* out);
+
 /* grand_decode_symbols without any allocation (the paper has no counterpart:
  * this is a deployment convenience). For callers that are not allowed to
  * allocate device memory once they are running -- for example a real-time

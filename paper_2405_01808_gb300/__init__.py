@@ -90,9 +90,16 @@ def lib() -> ctypes.CDLL:
             L.grand_decode_symbols.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, P, P]
             L.grand_decode_mixed.argtypes = [P, i32, P, P, i64, P, i64, ctypes.c_float, P, i64, P, P, P, P]
             L.grand_decode_symbols_noalloc.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, P]
+            L.grand_plan_symbols.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, ctypes.POINTER(P)]
+            L.grand_plan_mixed.argtypes = [P, i32, P, P, i64, P, i64, ctypes.c_float, P, i64, P, P, ctypes.POINTER(P)]
+            L.grand_plan_launch.argtypes = [P, P]
+            L.grand_plan_destroy.argtypes = [P]
+            L.grand_autotune.argtypes = [P, P, P, i64, ctypes.c_float, ctypes.c_char_p, P, P]
+            L.grand_autotune_mixed.argtypes = [P, i32, P, P, i64, P, i64, ctypes.c_float, i64, ctypes.c_char_p, P, P]
             for name in ("grand_polar_H", "grand_code_create", "grand_code_destroy", "grand_code_info",
                          "grand_demod", "grand_decode_batch", "grand_decode_symbols", "grand_decode_mixed",
-                         "grand_decode_symbols_noalloc"):
+                         "grand_decode_symbols_noalloc", "grand_plan_symbols", "grand_plan_mixed",
+                         "grand_plan_launch", "grand_plan_destroy", "grand_autotune", "grand_autotune_mixed"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -312,3 +319,92 @@ def decode_symbols_noalloc(code: Code, params: Params, symbols, cw, queries, aba
                                             _ptr(queries), _ptr(abandon), _stream(stream))
     _check(rc, "grand_decode_symbols_noalloc")
     return {"cw": cw, "queries": queries, "abandon": abandon}
+
+
+class Plan:
+    """A decode call captured into a CUDA graph (grand_plan_*): launch() replays
+    it on the buffers given at creation. Keep those tensors alive."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        _check(lib().grand_plan_launch(self._h, _stream(stream)), "grand_plan_launch")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().grand_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_symbols(code: Code, params: Params, symbols, cw, queries, abandon, N0: float = 1.0) -> Plan:
+    import torch
+
+    _require_cuda(symbols, cw, queries, abandon)
+    sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
+    h = ctypes.c_void_p()
+    rc = lib().grand_plan_symbols(code.handle, ctypes.byref(params), _ptr(sym), symbols.shape[0], float(N0), _ptr(cw),
+                                  _ptr(queries), _ptr(abandon), ctypes.byref(h))
+    _check(rc, "grand_plan_symbols")
+    return Plan(h, (code, params, symbols, cw, queries, abandon))
+
+
+def plan_mixed(codes, params: Params, desc, symbols, cw, queries, abandon, N0: float = 1.0) -> Plan:
+    import torch
+
+    _require_cuda(desc, symbols, cw, queries, abandon)
+    F = desc.numel() // FRAME_DESC_DTYPE.itemsize
+    sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
+    n_sym = symbols.numel() if symbols.is_complex() else symbols.numel() // 2
+    arr = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
+    h = ctypes.c_void_p()
+    rc = lib().grand_plan_mixed(arr, len(codes), ctypes.byref(params), _ptr(desc), F, _ptr(sym), n_sym, float(N0),
+                                _ptr(cw), cw.numel(), _ptr(queries), _ptr(abandon), ctypes.byref(h))
+    _check(rc, "grand_plan_mixed")
+    return Plan(h, (codes, params, desc, symbols, cw, queries, abandon))
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("best_ms", ctypes.c_float), ("candidates", ctypes.c_int32), ("from_cache", ctypes.c_int32)]
+
+
+def _tune_dict(p, r):
+    return {"tiles": tuple(p.tiles), "best_ms": float(r.best_ms), "candidates": int(r.candidates),
+            "from_cache": bool(r.from_cache)}
+
+
+def autotune(code: Code, params: Params, symbols, N0: float = 1.0, cache_path: str | None = None, stream=None):
+    """grand_autotune: picks params.tiles on a sample batch (in place)."""
+    import torch
+
+    _require_cuda(symbols)
+    sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
+    r = TuneResult()
+    rc = lib().grand_autotune(code.handle, ctypes.byref(params), _ptr(sym), symbols.shape[0], float(N0),
+                              cache_path.encode() if cache_path else None, _stream(stream), ctypes.byref(r))
+    _check(rc, "grand_autotune")
+    return _tune_dict(params, r)
+
+
+def autotune_mixed(codes, params: Params, desc, symbols, n_cw_words: int, N0: float = 1.0,
+                   cache_path: str | None = None, stream=None):
+    import torch
+
+    _require_cuda(desc, symbols)
+    F = desc.numel() // FRAME_DESC_DTYPE.itemsize
+    sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
+    n_sym = symbols.numel() if symbols.is_complex() else symbols.numel() // 2
+    arr = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
+    r = TuneResult()
+    rc = lib().grand_autotune_mixed(arr, len(codes), ctypes.byref(params), _ptr(desc), F, _ptr(sym), n_sym, float(N0),
+                                    n_cw_words, cache_path.encode() if cache_path else None, _stream(stream),
+                                    ctypes.byref(r))
+    _check(rc, "grand_autotune_mixed")
+    return _tune_dict(params, r)

@@ -1782,10 +1782,26 @@ extern "C" int grand_decode_symbols(const grand_code* c, const grand_params* p, 
   return run_qam(c->d_dev, 1, L, c->W, p, a, n_frames, stats, st);
 }
 
-extern "C" int grand_decode_mixed(const grand_code* const* codes, int n_codes, const grand_params* p,
-                                  const grand_frame_desc* desc, int64_t n_frames, const void* symbols,
-                                  int64_t n_symbols, float N0, uint32_t* cw, int64_t n_cw_words, uint32_t* queries,
-                                  uint8_t* abandon, grand_stats* stats, void* stream) {
+namespace grand {
+
+// Code table of an uneven batch: device views plus the batch-wide bounds.
+static int code_table(const grand_code* const* codes, int n_codes, std::vector<CodeDev>& table, int& Lmax, int& Wmax) {
+  Wmax = 1;
+  Lmax = 1;
+  table.resize(n_codes);
+  for (int i = 0; i < n_codes; ++i) {
+    if (!codes[i]) return GRAND_E_INVALID;
+    table[i] = codes[i]->dev;
+    Wmax = table[i].W > Wmax ? table[i].W : Wmax;
+    const int L = (table[i].N + 1) / 2;  // QPSK bound
+    Lmax = L > Lmax ? L : Lmax;
+  }
+  return GRAND_OK;
+}
+
+static int check_mixed_args(const grand_code* const* codes, int n_codes, const grand_params* p,
+                            const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
+                            float N0, uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon) {
   if (!codes || n_codes < 1 || n_codes > 65535 || n_frames < 0 || n_symbols < 0 || n_cw_words < 0 ||
       (n_frames > 0 && (!desc || !symbols || !cw || !queries || !abandon)))
     return GRAND_E_INVALID;
@@ -1794,22 +1810,14 @@ extern "C" int grand_decode_mixed(const grand_code* const* codes, int n_codes, c
   if (rc) return rc;
   if (p->order != GRAND_ORDER_QAM_NNE) return GRAND_E_INVALID;
   if (n_frames > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
-  cudaStream_t st = (cudaStream_t)stream;
-  int Wmax = 1, Lmax = 1;
-  std::vector<CodeDev> table(n_codes);
-  for (int i = 0; i < n_codes; ++i) {
-    if (!codes[i]) return GRAND_E_INVALID;
-    table[i] = codes[i]->dev;
-    Wmax = table[i].W > Wmax ? table[i].W : Wmax;
-    const int L = (table[i].N + 1) / 2;  // QPSK bound
-    Lmax = L > Lmax ? L : Lmax;
-  }
-  CodeDev* d_table = nullptr;
-  if (cudaMallocAsync((void**)&d_table, sizeof(CodeDev) * n_codes, st) != cudaSuccess) return GRAND_E_NOMEM;
-  if (cudaMemcpyAsync(d_table, table.data(), sizeof(CodeDev) * n_codes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-    cudaFreeAsync(d_table, st);
-    return GRAND_E_CUDA;
-  }
+  return GRAND_OK;
+}
+
+// The uneven-batch launch sequence on a device-resident code table.
+static int mixed_impl(const CodeDev* d_table, int n_codes, int Lmax, int Wmax, const grand_params* p,
+                      const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
+                      uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon, grand_stats* stats,
+                      cudaStream_t st) {
   PrepArgs a{};
   a.symbols = (const float2*)symbols;
   a.desc = desc;
@@ -1826,10 +1834,149 @@ extern "C" int grand_decode_mixed(const grand_code* const* codes, int n_codes, c
   a.cw = cw;
   a.queries = queries;
   a.abandon = abandon;
-  rc = run_qam(d_table, n_codes, Lmax, Wmax, p, a, n_frames, stats, st);
+  return run_qam(d_table, n_codes, Lmax, Wmax, p, a, n_frames, stats, st);
+}
+
+}  // namespace grand
+
+extern "C" int grand_decode_mixed(const grand_code* const* codes, int n_codes, const grand_params* p,
+                                  const grand_frame_desc* desc, int64_t n_frames, const void* symbols,
+                                  int64_t n_symbols, float N0, uint32_t* cw, int64_t n_cw_words, uint32_t* queries,
+                                  uint8_t* abandon, grand_stats* stats, void* stream) {
+  int rc = check_mixed_args(codes, n_codes, p, desc, n_frames, symbols, n_symbols, N0, cw, n_cw_words, queries,
+                            abandon);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int Wmax = 1, Lmax = 1;
+  std::vector<CodeDev> table;
+  rc = code_table(codes, n_codes, table, Lmax, Wmax);
+  if (rc) return rc;
+  CodeDev* d_table = nullptr;
+  if (cudaMallocAsync((void**)&d_table, sizeof(CodeDev) * n_codes, st) != cudaSuccess) return GRAND_E_NOMEM;
+  // pageable source: the copy is staged before the call returns
+  if (cudaMemcpyAsync(d_table, table.data(), sizeof(CodeDev) * n_codes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cudaFreeAsync(d_table, st);
+    return GRAND_E_CUDA;
+  }
+  rc = mixed_impl(d_table, n_codes, Lmax, Wmax, p, desc, n_frames, symbols, n_symbols, cw, n_cw_words, queries,
+                  abandon, stats, st);
   // the table must outlive the kernels: stream-ordered free
   cudaFreeAsync(d_table, st);
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Plans: one decode call captured into a CUDA graph for repeated launches on
+// fixed buffers (the launch sequence -- counter reset, preparation, search,
+// with the stream-ordered scratch as graph memory nodes -- replays with one
+// cudaGraphLaunch).
+// ---------------------------------------------------------------------------
+struct grand_plan {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  grand::CodeDev* d_table;  // uneven batches: code table owned by the plan
+};
+
+namespace grand {
+
+template <typename F>
+static int capture_plan(F&& body, grand_plan** out) {
+  cudaStream_t cap = nullptr;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return GRAND_E_CUDA;
+  int rc = body(cap);  // one eager run: module load, attributes, pool warm-up
+  if (rc == GRAND_OK && cudaStreamSynchronize(cap) != cudaSuccess) rc = GRAND_E_CUDA;
+  grand_plan* plan = nullptr;
+  if (rc == GRAND_OK) {
+    plan = (grand_plan*)calloc(1, sizeof(grand_plan));
+    if (!plan) rc = GRAND_E_NOMEM;
+  }
+  if (rc == GRAND_OK) {
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = GRAND_E_CUDA;
+    } else {
+      const int brc = body(cap);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(cap, &g);
+      if (brc != GRAND_OK || e != cudaSuccess || !g) {
+        rc = brc != GRAND_OK ? brc : GRAND_E_CUDA;
+        if (g) cudaGraphDestroy(g);
+      } else {
+        plan->graph = g;
+        if (cudaGraphInstantiate(&plan->exec, g, 0) != cudaSuccess) rc = GRAND_E_CUDA;
+      }
+    }
+  }
+  cudaStreamDestroy(cap);
+  if (rc != GRAND_OK) {
+    if (plan) {
+      if (plan->exec) cudaGraphExecDestroy(plan->exec);
+      if (plan->graph) cudaGraphDestroy(plan->graph);
+      free(plan);
+    }
+    return rc;
+  }
+  *out = plan;
+  return GRAND_OK;
+}
+
+}  // namespace grand
+
+extern "C" int grand_plan_symbols(const grand_code* c, const grand_params* p, const void* symbols, int64_t n_frames,
+                                  float N0, uint32_t* cw, uint32_t* queries, uint8_t* abandon, grand_plan** out) {
+  if (!out || n_frames < 1) return GRAND_E_INVALID;
+  *out = nullptr;
+  return capture_plan(
+      [&](cudaStream_t st) {
+        return grand_decode_symbols(c, p, symbols, n_frames, N0, cw, queries, abandon, nullptr, st);
+      },
+      out);
+}
+
+extern "C" int grand_plan_mixed(const grand_code* const* codes, int n_codes, const grand_params* p,
+                                const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
+                                float N0, uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon,
+                                grand_plan** out) {
+  if (!out || n_frames < 1) return GRAND_E_INVALID;
+  *out = nullptr;
+  int rc = check_mixed_args(codes, n_codes, p, desc, n_frames, symbols, n_symbols, N0, cw, n_cw_words, queries,
+                            abandon);
+  if (rc) return rc;
+  int Wmax = 1, Lmax = 1;
+  std::vector<CodeDev> table;
+  rc = code_table(codes, n_codes, table, Lmax, Wmax);
+  if (rc) return rc;
+  CodeDev* d_table = nullptr;
+  if (cudaMalloc((void**)&d_table, sizeof(CodeDev) * n_codes) != cudaSuccess) return GRAND_E_NOMEM;
+  if (cudaMemcpy(d_table, table.data(), sizeof(CodeDev) * n_codes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d_table);
+    return GRAND_E_CUDA;
+  }
+  rc = capture_plan(
+      [&](cudaStream_t st) {
+        return mixed_impl(d_table, n_codes, Lmax, Wmax, p, desc, n_frames, symbols, n_symbols, cw, n_cw_words,
+                          queries, abandon, nullptr, st);
+      },
+      out);
+  if (rc != GRAND_OK) {
+    cudaFree(d_table);
+    return rc;
+  }
+  (*out)->d_table = d_table;
+  return GRAND_OK;
+}
+
+extern "C" int grand_plan_launch(grand_plan* plan, void* stream) {
+  if (!plan || !plan->exec) return GRAND_E_INVALID;
+  return cudaGraphLaunch(plan->exec, (cudaStream_t)stream) == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
+}
+
+extern "C" int grand_plan_destroy(grand_plan* plan) {
+  if (!plan) return GRAND_OK;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  if (plan->d_table) cudaFree(plan->d_table);
+  free(plan);
+  return GRAND_OK;
 }
 
 // ---------------------------------------------------------------------------
