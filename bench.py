@@ -53,9 +53,12 @@ CONFIGS = {
     "c4": dict(kind="mixed", frames=1000000, S=10, cap=1 << 20,
                desc="uneven mix: N in {32..1024}, M in {4,16,64,256}, Eb/N0 U(4,14) dB, 1000000 frames, "
                     "S=min(L,10), cap 2^20, one call"),
+    "c5": dict(kind="serve", frames=1000000, S=10, cap=1 << 20, rates=(0.5e6, 1e6, 2e6, 5e6),
+               desc="serving: Poisson arrivals at 0.5/1/2/5 M frames/s of the uneven mix (N 32..1024, "
+                    "M 4..256, Eb/N0 U(4,14) dB), 1000000 requests per rate, S=min(L,10), cap 2^20"),
 }
 METRIC = "TEP syndrome checks/s & frames/s per GB300; p50/p99 decode latency"
-CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5}
+CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5, "c5": 6}
 # ALU roofline: 152 SMs x 64 integer-ALU lanes per clock (LOP3/ISETP class)
 # x 2.07 GHz maximum SM clock.
 SMS, ALU_LANES, MAX_CLOCK_GHZ = 152, 64, 2.07
@@ -69,7 +72,7 @@ NCU_SEARCH = {"sha": "1c0b187066c9008a", "dram_bytes_per_hard_frame": 1551872 / 
 def make_inputs(cfg, rank, info_by_N):
     """Host arrays of one step's batch (seeded; rank selects the stream)."""
     cid = CONFIG_IDS[cfg["name"]]
-    if cfg["kind"] == "mixed":
+    if cfg["kind"] in ("mixed", "serve"):
         return wl.mixed_frames(cid, 1000 + rank, cfg["frames"], info_by_N)
     parts = []
     for i, snr in enumerate(cfg["snrs"]):
@@ -179,7 +182,7 @@ def oracle_run(cfg, inputs, idx, threads):
 
 
 def info_sets(cfg, source):
-    Ns = wl.MIXED_N if cfg["kind"] == "mixed" else (cfg["N"],)
+    Ns = wl.MIXED_N if cfg["kind"] in ("mixed", "serve") else (cfg["N"],)
     out = {}
     for n in Ns:
         if source == "oracle":
@@ -228,6 +231,68 @@ def run_reference(args, cfg):
 
 
 # -------------------------------------------------------------------------
+# serving (continuous batching server, Poisson arrivals)
+# -------------------------------------------------------------------------
+def run_serving(args, cfg, g, inputs):
+    """Offer the requests at each Poisson rate; latency = completion - arrival."""
+    import torch
+
+    codes = [g.Code.polar(n, n // 2) for n in wl.MIXED_N]
+    code_of_N = {n: i for i, n in enumerate(wl.MIXED_N)}
+    F = len(inputs["N"])
+    sym = np.ascontiguousarray(inputs["symbols"])
+    reqs = np.zeros(F, dtype=g.REQUEST_DTYPE)
+    reqs["code"] = [code_of_N[int(n)] for n in inputs["N"]]
+    reqs["M"] = inputs["M"]
+    reqs["symbols"] = sym.ctypes.data + 8 * inputs["sym_offset"].astype(np.uint64)
+    reqs["tag"] = np.arange(F, dtype=np.uint64)
+    p = g.Params.make(M=0, S=cfg["S"], query_cap=cfg["cap"])
+    rows = []
+    g_rng = np.random.default_rng(CONFIG_IDS["c5"])
+    for rate in cfg["rates"]:
+        srv = g.Server(codes, p, max_slots=1 << 18, max_device_bytes=1 << 30, max_batch=1 << 16, n_streams=4)
+        # warm-up: a short burst (module load, pools)
+        w = srv.submit(reqs[:2000])
+        srv.drain(60.0)
+        while len(srv.poll(1 << 16)):
+            pass
+        gaps = g_rng.exponential(1.0 / rate, size=F)
+        t0 = g.clock_ns() + 2_000_000
+        arrival = t0 + np.cumsum(gaps * 1e9).astype(np.int64)
+        reqs["arrival_ns"] = arrival
+        i = 0
+        got = []
+        t_start = time.perf_counter()
+        while i < F:
+            now = g.clock_ns()
+            j = int(np.searchsorted(arrival, now, side="right"))
+            if j > i:
+                i += srv.submit(reqs[i:j])
+            got.append(srv.poll(1 << 16))
+            if time.perf_counter() - t_start > 120:
+                break
+        srv.drain(120.0)
+        while True:
+            tail = srv.poll(1 << 16)
+            if not len(tail):
+                break
+            got.append(tail)
+        st = srv.stats()
+        srv.close()
+        res = np.concatenate(got)
+        lat_us = (res["done_ns"] - res["arrival_ns"]) / 1e3
+        span = (res["done_ns"].max() - arrival[0]) / 1e9
+        rows.append({"offered_frames_per_s": rate, "completed": int(len(res)),
+                     "frames_per_s": len(res) / span, "checks_per_s": float(res["queries"].sum()) / span,
+                     "latency_us": {"p50": float(np.percentile(lat_us, 50)), "p99": float(np.percentile(lat_us, 99)),
+                                    "max": float(lat_us.max())},
+                     "batches": st["batches"], "mean_batch": st["batched_frames"] / max(1, st["batches"]),
+                     "max_inflight_batches": st["max_inflight_batches"], "rejected_submits": st["rejected"],
+                     "errors": st["errors"]})
+    return rows
+
+
+# -------------------------------------------------------------------------
 # GPU arm
 # -------------------------------------------------------------------------
 def main():
@@ -272,6 +337,26 @@ def main():
     inputs = make_inputs(cfg, rank, info)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    if cfg["kind"] == "serve":
+        clocks = ClockSampler(local)
+        clocks.start()
+        rows = run_serving(args, cfg, g, inputs)
+        clk = clocks.stop()
+        if rank == 0:
+            head = rows[-1]
+            line = {"metric": METRIC, "value": head["frames_per_s"], "unit": "frames/s", "n_gpus": world,
+                    "steps": len(rows), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                    "data": "synthetic (seeded random polar codewords over AWGN)",
+                    "config": {"workload": cfg["desc"], "server": "max_slots 262144, budget 1 GiB, max_batch 65536, "
+                                                                   "4 streams"},
+                    "latency_us": head["latency_us"], "rates": rows, "clocks": clk,
+                    "e2e": {"value": head["frames_per_s"], "unit": "frames/s",
+                            "h2d_bytes_per_step": int(inputs["symbols"].nbytes),
+                            "d2h_bytes_per_step": int(len(inputs["N"]) * 160)},
+                    "gpu_launches": int(sum(r["batches"] for r in rows) * 2)}
+            print(json.dumps(line), flush=True)
+        return 0
 
     # ---- code objects and device buffers
     if cfg["kind"] == "mixed":

@@ -272,6 +272,85 @@ int grand_autotune_mixed(const grand_code* const* codes, int n_codes, grand_para
                          const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
                          float N0, int64_t n_cw_words, const char* cache_path, void* stream, grand_tune_result* out);
 
+/* Serving loop (continuous batching of decode requests, spec pattern
+ * "serving"). A request is one frame of any of the server's codes and any
+ * constellation. Submit admits requests while a slot is free and the device
+ * memory budget allows (bytes per request: 8 L received symbols + 144 hand-off
+ * record + N/8 + 5 outputs); admitted requests keep their received word
+ * resident on the device (a device ring mirrored from pinned host memory)
+ * until they complete. A worker thread launches all admitted, not yet launched
+ * requests as one uneven batch on the first idle stream (grand_decode_mixed),
+ * so requests arriving while batches run are decoded concurrently on other
+ * streams. Results are exactly those of grand_decode_mixed / grand_decode_symbols
+ * for the same frame, whatever the batch it landed in.
+ *   codes             host array of n_codes code pointers (borrowed; they must
+ *                     outlive the server).
+ *   params            order GRAND_ORDER_QAM_NNE; M comes with each request.
+ *   max_slots         admitted requests resident at once.
+ *   max_device_bytes  memory budget of the resident request state; the
+ *                     symbol ring holds max_device_bytes / 8 symbols.
+ *   max_batch         frames per launch (0: max_slots).
+ *   n_streams         batches in flight at once (1..16). */
+typedef struct grand_server_cfg {
+  const grand_code* const* codes;
+  int32_t n_codes;
+  grand_params params;
+  float N0;
+  int32_t max_slots;
+  int64_t max_device_bytes;
+  int32_t max_batch;
+  int32_t n_streams;
+} grand_server_cfg;
+
+/* One decode request. symbols: host complex64 [L], L = ceil(N / log2 M) of the
+ * request's code, copied during submit. arrival_ns: arrival time on the
+ * grand_clock_ns() clock (0: the submit time); latency = done - arrival. */
+typedef struct grand_request {
+  int32_t code;
+  int32_t M;
+  const void* symbols;
+  uint64_t tag;
+  int64_t arrival_ns;
+} grand_request;
+
+/* One completed request: decoded word (first N/32 words of cw), query count,
+ * abandon flag (as grand_decode_batch; 4 = the batch failed on the device). */
+typedef struct grand_result {
+  uint64_t tag;
+  int64_t arrival_ns;
+  int64_t done_ns;
+  uint32_t queries;
+  uint8_t abandon;
+  uint8_t pad[3];
+  uint32_t cw[GRAND_N_MAX / 32];
+} grand_result;
+
+typedef struct grand_server_stats {
+  int64_t admitted, rejected, completed, batches, batched_frames, max_inflight_batches, errors;
+  int64_t live_slots, live_bytes, pending, inflight_batches;
+} grand_server_stats;
+
+typedef struct grand_server grand_server;
+
+/* Host monotonic clock of the server, nanoseconds. */
+int64_t grand_clock_ns(void);
+/* Create a server on the current device (allocates the ring, per-stream
+ * buffers, streams, and starts the worker thread). */
+int grand_server_create(const grand_server_cfg* cfg, grand_server** out);
+/* Admit requests in order until one does not fit; *n_admitted of them were
+ * taken. Returns GRAND_OK if at least one was admitted (or n == 0),
+ * GRAND_E_BUSY if none fits now, GRAND_E_INVALID on a malformed request
+ * (the requests before it stay admitted). Thread-safe. */
+int grand_server_submit(grand_server* srv, const grand_request* reqs, int n, int* n_admitted);
+/* Move up to max completed results into out (host); *n of them. Thread-safe. */
+int grand_server_poll(grand_server* srv, grand_result* out, int max, int* n);
+/* Wait until every admitted request completed; GRAND_E_TIMEOUT after
+ * timeout_ns (results stay queued for poll). */
+int grand_server_drain(grand_server* srv, int64_t timeout_ns);
+int grand_server_get_stats(grand_server* srv, grand_server_stats* out);
+/* Drain (bounded: 10 s), stop the worker and free everything. */
+int grand_server_destroy(grand_server* srv);
+
 /* grand_decode_symbols without any allocation (the paper has no counterpart:
  * this is a deployment convenience). For callers that are not allowed to
  * allocate device memory once they are running -- for example a real-time

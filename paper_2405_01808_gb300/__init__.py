@@ -96,10 +96,19 @@ def lib() -> ctypes.CDLL:
             L.grand_plan_destroy.argtypes = [P]
             L.grand_autotune.argtypes = [P, P, P, i64, ctypes.c_float, ctypes.c_char_p, P, P]
             L.grand_autotune_mixed.argtypes = [P, i32, P, P, i64, P, i64, ctypes.c_float, i64, ctypes.c_char_p, P, P]
+            L.grand_clock_ns.restype = i64
+            L.grand_server_create.argtypes = [P, ctypes.POINTER(P)]
+            L.grand_server_submit.argtypes = [P, P, i32, P]
+            L.grand_server_poll.argtypes = [P, P, i32, P]
+            L.grand_server_drain.argtypes = [P, i64]
+            L.grand_server_get_stats.argtypes = [P, P]
+            L.grand_server_destroy.argtypes = [P]
             for name in ("grand_polar_H", "grand_code_create", "grand_code_destroy", "grand_code_info",
                          "grand_demod", "grand_decode_batch", "grand_decode_symbols", "grand_decode_mixed",
                          "grand_decode_symbols_noalloc", "grand_plan_symbols", "grand_plan_mixed",
-                         "grand_plan_launch", "grand_plan_destroy", "grand_autotune", "grand_autotune_mixed"):
+                         "grand_plan_launch", "grand_plan_destroy", "grand_autotune", "grand_autotune_mixed",
+                         "grand_server_create", "grand_server_submit", "grand_server_poll", "grand_server_drain",
+                         "grand_server_get_stats", "grand_server_destroy"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -408,3 +417,84 @@ def autotune_mixed(codes, params: Params, desc, symbols, n_cw_words: int, N0: fl
                                     ctypes.byref(r))
     _check(rc, "grand_autotune_mixed")
     return _tune_dict(params, r)
+
+
+# --------------------------------------------------------------------------
+# serving loop
+# --------------------------------------------------------------------------
+REQUEST_DTYPE = np.dtype([("code", "<i4"), ("M", "<i4"), ("symbols", "<u8"), ("tag", "<u8"), ("arrival_ns", "<i8")])
+RESULT_DTYPE = np.dtype([("tag", "<u8"), ("arrival_ns", "<i8"), ("done_ns", "<i8"), ("queries", "<u4"),
+                         ("abandon", "u1"), ("pad", "u1", (3,)), ("cw", "<u4", (32,))])
+
+
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("codes", ctypes.c_void_p), ("n_codes", ctypes.c_int32), ("params", Params), ("N0", ctypes.c_float),
+                ("max_slots", ctypes.c_int32), ("max_device_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32),
+                ("n_streams", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("admitted", "rejected", "completed", "batches", "batched_frames",
+                                              "max_inflight_batches", "errors", "live_slots", "live_bytes",
+                                              "pending", "inflight_batches")]
+
+
+def clock_ns() -> int:
+    return int(lib().grand_clock_ns())
+
+
+class Server:
+    """grand_server_*: continuous-batching decode server on the current device."""
+
+    def __init__(self, codes, params: Params, max_slots=65536, max_device_bytes=256 << 20, max_batch=0,
+                 n_streams=4, N0=1.0):
+        self._codes = list(codes)
+        self._arr = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
+        cfg = ServerCfg()
+        cfg.codes = ctypes.cast(self._arr, ctypes.c_void_p)
+        cfg.n_codes = len(codes)
+        cfg.params = params
+        cfg.N0 = float(N0)
+        cfg.max_slots, cfg.max_device_bytes = int(max_slots), int(max_device_bytes)
+        cfg.max_batch, cfg.n_streams = int(max_batch), int(n_streams)
+        h = ctypes.c_void_p()
+        _check(lib().grand_server_create(ctypes.byref(cfg), ctypes.byref(h)), "grand_server_create")
+        self._h = h
+
+    def submit(self, reqs: np.ndarray) -> int:
+        """Submit a REQUEST_DTYPE array (symbols = host addresses); returns how
+        many (a prefix) were admitted; 0 when the server is full."""
+        reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
+        n = ctypes.c_int(0)
+        rc = lib().grand_server_submit(self._h, reqs.ctypes.data, len(reqs), ctypes.byref(n))
+        if rc not in (0, -6):
+            _check(rc, "grand_server_submit")
+        return n.value
+
+    def poll(self, max_results: int = 65536) -> np.ndarray:
+        """Completed results (RESULT_DTYPE), at most max_results per call."""
+        buf = getattr(self, "_buf", None)
+        if buf is None or len(buf) < max_results:
+            buf = self._buf = np.zeros(max_results, dtype=RESULT_DTYPE)
+        n = ctypes.c_int(0)
+        _check(lib().grand_server_poll(self._h, buf.ctypes.data, max_results, ctypes.byref(n)), "grand_server_poll")
+        return buf[: n.value].copy()
+
+    def drain(self, timeout_s: float = 10.0):
+        _check(lib().grand_server_drain(self._h, int(timeout_s * 1e9)), "grand_server_drain")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().grand_server_get_stats(self._h, ctypes.byref(st)), "grand_server_get_stats")
+        return {n: int(getattr(st, n)) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().grand_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

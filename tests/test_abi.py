@@ -83,3 +83,13 @@ def test_argument_validation_without_gpu(glib):
                                   None) == -1
     assert L.grand_demod(None, 1, 32, 16, ctypes.c_float(1.0), 0, None, None, None, None, None, 128, None) == -1
     assert L.grand_code_destroy(None) == 0
+
+
+def test_server_and_plan_validation_without_gpu(glib):
+    L = glib.lib()
+    h = ctypes.c_void_p()
+    assert L.grand_server_create(None, ctypes.byref(h)) == -1
+    assert L.grand_plan_launch(None, None) == -1
+    assert L.grand_plan_destroy(None) == 0
+    assert L.grand_server_destroy(None) == 0
+    assert L.grand_clock_ns() > 0

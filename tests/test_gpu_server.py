@@ -1,0 +1,160 @@
+"""GPU tests of the serving loop: every result equals the same frame decoded
+alone; admission by slots and by memory budget; concurrent submitters."""
+from __future__ import annotations
+
+import threading
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+NS = (32, 64, 128, 256, 512, 1024)
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2405_01808_gb300 as g
+
+    g.build()
+    codes = [g.Code.polar(n, n // 2) for n in NS]
+    info = {}
+    for n in NS:
+        _, frozen = g.polar_H(n, n // 2)
+        info[n] = np.setdiff1d(np.arange(n), frozen)
+    return g, codes, info
+
+
+def make_requests(g, mx, code_of_N):
+    F = len(mx["N"])
+    reqs = np.zeros(F, dtype=g.REQUEST_DTYPE)
+    base = mx["symbols"].ctypes.data
+    reqs["code"] = [code_of_N[int(n)] for n in mx["N"]]
+    reqs["M"] = mx["M"]
+    reqs["symbols"] = base + 8 * mx["sym_offset"].astype(np.uint64)
+    reqs["tag"] = np.arange(F, dtype=np.uint64)
+    return reqs
+
+
+def alone(g, codes, code_of_N, mx, f, p):
+    """The frame decoded by itself (one-frame call)."""
+    import torch
+
+    n, M = int(mx["N"][f]), int(mx["M"][f])
+    L = wl.symbols_per_frame(n, M)
+    o = mx["sym_offset"][f]
+    sym = torch.from_numpy(np.ascontiguousarray(mx["symbols"][o:o + L]).reshape(1, L)).cuda()
+    pp = g.Params.make(M=M, S=p.S, query_cap=p.query_cap)
+    r = g.decode_symbols(codes[code_of_N[n]], pp, sym)
+    torch.cuda.synchronize()
+    return r["cw"].cpu().numpy().view(np.uint32)[0], int(r["queries"][0]), int(r["abandon"][0])
+
+
+def run_all(srv, reqs, timeout_s=30.0):
+    import time
+
+    got = []
+    i = 0
+    t0 = time.time()
+    while i < len(reqs):
+        i += srv.submit(reqs[i:])
+        got.append(srv.poll())
+        assert time.time() - t0 < timeout_s
+    srv.drain(timeout_s)
+    got.append(srv.poll())
+    return np.concatenate(got)
+
+
+def test_results_equal_alone(env):
+    g, codes, info = env
+    code_of_N = {n: i for i, n in enumerate(NS)}
+    mx = wl.mixed_frames(60, 0, 3000, info, ebn0_range=(6.0, 14.0))
+    p = g.Params.make(M=0, S=10, query_cap=1 << 20)
+    srv = g.Server(codes, p, max_slots=4096, max_device_bytes=64 << 20, max_batch=512, n_streams=4)
+    reqs = make_requests(g, mx, code_of_N)
+    res = run_all(srv, reqs)
+    st = srv.stats()
+    srv.close()
+    assert len(res) == 3000 and sorted(res["tag"].tolist()) == list(range(3000))
+    assert st["completed"] == 3000 and st["errors"] == 0 and st["batches"] >= 2
+    assert np.all(res["done_ns"] >= res["arrival_ns"])
+    # every result equals the frame decoded alone (sampled: 300 frames, all kinds)
+    by_tag = {int(r["tag"]): r for r in res}
+    for f in np.linspace(0, 2999, 300).astype(int):
+        cw, q, ab = alone(g, codes, code_of_N, mx, f, p)
+        r = by_tag[int(f)]
+        nw = int(mx["N"][f]) // 32
+        assert (int(r["queries"]), int(r["abandon"])) == (q, ab), f
+        assert np.array_equal(r["cw"][:nw], cw), f
+
+
+def test_admission_by_slots(env):
+    g, codes, info = env
+    code_of_N = {n: i for i, n in enumerate(NS)}
+    mx = wl.mixed_frames(61, 0, 64, info, ebn0_range=(12.0, 14.0))
+    p = g.Params.make(M=0, S=8, query_cap=1 << 16)
+    srv = g.Server(codes, p, max_slots=8, max_device_bytes=16 << 20, n_streams=2)
+    reqs = make_requests(g, mx, code_of_N)
+    first = srv.submit(reqs)
+    assert 1 <= first <= 8
+    res = run_all(srv, reqs[first:])
+    res = np.concatenate([res, srv.poll()])
+    st = srv.stats()
+    srv.close()
+    assert st["rejected"] > 0 and st["admitted"] == 64
+    assert st["live_slots"] == 0 and st["live_bytes"] == 0
+
+
+def test_admission_by_memory(env):
+    g, codes, info = env
+    code_of_N = {n: i for i, n in enumerate(NS)}
+    # N=1024 with QPSK: 512 symbols (4 KB) + record + outputs per request
+    mx = wl.mixed_frames(62, 0, 40, info, ebn0_range=(12.0, 14.0), n_choices=(1024,), m_choices=(4,))
+    p = g.Params.make(M=0, S=8, query_cap=1 << 16)
+    budget = 5 * (8 * 512 + 144 + 128 + 5)
+    srv = g.Server(codes, p, max_slots=1000, max_device_bytes=budget, n_streams=1)
+    reqs = make_requests(g, mx, code_of_N)
+    first = srv.submit(reqs)
+    assert first == 5
+    res = run_all(srv, reqs[first:])
+    srv.close()
+
+
+def test_concurrent_submitters(env):
+    g, codes, info = env
+    code_of_N = {n: i for i, n in enumerate(NS)}
+    mx = wl.mixed_frames(63, 0, 4000, info, ebn0_range=(8.0, 14.0))
+    p = g.Params.make(M=0, S=10, query_cap=1 << 20)
+    srv = g.Server(codes, p, max_slots=2048, max_device_bytes=32 << 20, max_batch=256, n_streams=4)
+    reqs = make_requests(g, mx, code_of_N)
+    parts = np.array_split(np.arange(4000), 4)
+    errors = []
+
+    def feed(idx):
+        try:
+            i = 0
+            while i < len(idx):
+                i += srv.submit(reqs[idx[i:]])
+        except Exception as e:  # pragma: no cover - reported below
+            errors.append(e)
+
+    ths = [threading.Thread(target=feed, args=(part,)) for part in parts]
+    for t in ths:
+        t.start()
+    got = []
+    while any(t.is_alive() for t in ths):
+        got.append(srv.poll())
+    for t in ths:
+        t.join()
+    srv.drain(30.0)
+    got.append(srv.poll())
+    res = np.concatenate(got)
+    srv.close()
+    assert not errors
+    assert sorted(res["tag"].tolist()) == list(range(4000))
