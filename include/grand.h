@@ -27,6 +27,10 @@
  *   - "device" pointers are CUDA global memory owned by the caller; the
  *     library never frees them. "host" pointers are ordinary CPU memory.
  *     With n_frames == 0 the data pointers may be NULL (nothing is launched).
+ *   - The first decode call on a device raises the release threshold of that
+ *     device's default stream-ordered memory pool (cudaMemPoolAttrRelease-
+ *     Threshold = UINT64_MAX), so scratch stays cached between calls instead
+ *     of being returned to the system at each synchronisation.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream). Calls that
  *     take a stream enqueue asynchronous work on it and return; the caller
  *     synchronises the stream before reading outputs and keeps every buffer
@@ -325,9 +329,13 @@ typedef struct grand_result {
   uint32_t cw[GRAND_N_MAX / 32];
 } grand_result;
 
+/* Counters of a server. batch_service_ns: sum over batches of (completion seen
+ * - launch start); launch_ns: host time spent issuing batches (copies, decode
+ * call, event). */
 typedef struct grand_server_stats {
   int64_t admitted, rejected, completed, batches, batched_frames, max_inflight_batches, errors;
   int64_t live_slots, live_bytes, pending, inflight_batches;
+  int64_t batch_service_ns, max_batch_service_ns, launch_ns, max_launch_ns;
 } grand_server_stats;
 
 typedef struct grand_server grand_server;

@@ -436,7 +436,8 @@ class ServerCfg(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("admitted", "rejected", "completed", "batches", "batched_frames",
                                               "max_inflight_batches", "errors", "live_slots", "live_bytes",
-                                              "pending", "inflight_batches")]
+                                              "pending", "inflight_batches", "batch_service_ns",
+                                              "max_batch_service_ns", "launch_ns", "max_launch_ns")]
 
 
 def clock_ns() -> int:

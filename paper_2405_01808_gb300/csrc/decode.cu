@@ -1450,6 +1450,24 @@ static QamConst make_qam_const() {
   return c;
 }
 
+// Keep the scratch of repeated calls cached: the default stream-ordered pool
+// of the device otherwise returns its memory to the system at every
+// synchronisation and the next call maps it again. Once per device.
+static void keep_pool_cached() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  done[dev] = true;
+}
+
 static int sm_count() {
   static int n = 0;
   if (!n) {
@@ -1514,6 +1532,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     if (stats) *stats = grand_stats{};
     return GRAND_OK;
   }
+  keep_pool_cached();
   // scratch: header + one record per frame (worst case: every frame hard)
   const size_t rec_bytes = sizeof(FrameRec) * (size_t)n_frames;
   char* scratch = nullptr;

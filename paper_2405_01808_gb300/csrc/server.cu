@@ -71,6 +71,7 @@ struct StreamBuf {
 
 struct Batch {
   int stream;
+  int64_t launch_ns;
   std::vector<Req> reqs;
   int64_t vend;   // ring released up to here once this and all earlier batches are done
   int64_t bytes;
@@ -200,6 +201,8 @@ void worker_main(grand_server* s) {
           s->done.push_back(r);
         }
         s->st.completed += b.reqs.size();
+        s->st.batch_service_ns += t - b.launch_ns;
+        if (t - b.launch_ns > s->st.max_batch_service_ns) s->st.max_batch_service_ns = t - b.launch_ns;
         if (b.status != GRAND_OK) s->st.errors += 1;
         buf.busy = false;
         progressed = true;
@@ -242,10 +245,14 @@ void worker_main(grand_server* s) {
         s->st.batched_frames += b.reqs.size();
       }
       cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
+      b.launch_ns = now_ns();
       b.status = launch_batch(s, si, b);
+      const int64_t issued = now_ns() - b.launch_ns;
       if (b.status != GRAND_OK) cudaEventRecord(b.ev, s->sb[si].stream);
       {
         std::unique_lock<std::mutex> lk(s->mu);
+        s->st.launch_ns += issued;
+        if (issued > s->st.max_launch_ns) s->st.max_launch_ns = issued;
         s->inflight.push_back(std::move(b));
         const int64_t inflight = (int64_t)s->inflight.size();
         if (inflight > s->st.max_inflight_batches) s->st.max_inflight_batches = inflight;
