@@ -250,7 +250,7 @@ def run_serving(args, cfg, g, inputs):
     rows = []
     g_rng = np.random.default_rng(CONFIG_IDS["c5"])
     for rate in cfg["rates"]:
-        srv = g.Server(codes, p, max_slots=1 << 18, max_device_bytes=1 << 30, max_batch=1 << 16, n_streams=4)
+        srv = g.Server(codes, p, max_slots=1 << 18, max_device_bytes=1 << 30, max_batch=args.serve_batch, n_streams=args.serve_streams)
         # warm-up: a short burst (module load, pools)
         w = srv.submit(reqs[:2000])
         srv.drain(60.0)
@@ -311,6 +311,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=0, help="override frames per SNR (for quick runs)")
     ap.add_argument("--tiles", default="0,0,0,0", help="launch shape (grand_params.tiles), 0 = automatic")
+    ap.add_argument("--serve-batch", type=int, default=65536, help="serving: frames per launch")
+    ap.add_argument("--serve-streams", type=int, default=4, help="serving: batches in flight")
     args = ap.parse_args()
     cfg = dict(CONFIGS[args.config])
     cfg["name"] = args.config
@@ -354,8 +356,9 @@ def main():
                     "steps": len(rows), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
                     "scaling": "weak", "vs_baseline": None, "dtype": "u32",
                     "data": "synthetic (seeded random polar codewords over AWGN)",
-                    "config": {"workload": cfg["desc"], "server": "max_slots 262144, budget 1 GiB, max_batch 65536, "
-                                                                   "4 streams"},
+                    "config": {"workload": cfg["desc"],
+                               "server": f"max_slots 262144, budget 1 GiB, max_batch {args.serve_batch}, "
+                                         f"{args.serve_streams} streams"},
                     "latency_us": head["latency_us"], "rates": rows, "clocks": clk,
                     "e2e": {"value": head["frames_per_s"], "unit": "frames/s",
                             "h2d_bytes_per_step": int(inputs["symbols"].nbytes),
