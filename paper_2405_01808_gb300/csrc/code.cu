@@ -93,19 +93,37 @@ extern "C" int grand_code_create(const uint32_t* H, int N, int K, grand_code** o
   // column-packed copy: word w of column j holds rows 32w .. 32w+31; then the
   // per-column projections hf[j] (a fixed pseudo-random 32-bit word per row,
   // from the splitmix64 finaliser of the row index)
-  std::vector<uint32_t> hcol((size_t)N * W + N, 0);
+  // layout of the device copy: hcol [N*W], hf [N], prow [R], frozen [R] (u16, packed 2 per word)
+  const size_t words = (size_t)N * W + N + R + (R + 1) / 2;
+  std::vector<uint32_t> hcol(words, 0);
   uint32_t* hf = hcol.data() + (size_t)N * W;
+  uint32_t* prow = hf + N;
+  uint16_t* frozen = reinterpret_cast<uint16_t*>(prow + R);
+  bool polar = true;
   for (int r = 0; r < R; ++r) {
     uint64_t z = 0x9E3779B97F4A7C15ull * (uint64_t)(r + 1);
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
     const uint32_t pr = (uint32_t)z ^ (uint32_t)(z >> 32);
+    prow[r] = pr;
+    int first = -1;
     for (int j = 0; j < N; ++j)
       if ((H[(size_t)r * (N / 32) + (j >> 5)] >> (j & 31)) & 1u) {
+        if (first < 0) first = j;
         hcol[(size_t)j * W + r / 32] |= 1u << (r % 32);
         hf[j] ^= pr;
       }
+    // polar row: exactly the indices j that contain its first index f
+    if (first < 0) {
+      polar = false;
+    } else {
+      frozen[r] = (uint16_t)first;
+      for (int j = 0; j < N && polar; ++j) {
+        const bool bit = (H[(size_t)r * (N / 32) + (j >> 5)] >> (j & 31)) & 1u;
+        if (bit != ((j & first) == first)) polar = false;
+      }
+    }
   }
   grand_code* c = (grand_code*)calloc(1, sizeof(grand_code));
   if (!c) return GRAND_E_NOMEM;
@@ -122,7 +140,10 @@ extern "C" int grand_code_create(const uint32_t* H, int N, int K, grand_code** o
   }
   c->dev.hcol = c->d_hcol;
   c->dev.hf = c->d_hcol + (size_t)N * W;
+  c->dev.prow = c->dev.hf + N;
+  c->dev.frozen = reinterpret_cast<const uint16_t*>(c->dev.prow + R);
   c->dev.N = N; c->dev.K = K; c->dev.R = R; c->dev.W = W;
+  c->dev.polar = polar ? 1 : 0;
   if (cudaMemcpy(c->d_hcol, hcol.data(), hcol.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->d_dev, &c->dev, sizeof(grand::CodeDev), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(c->d_hcol);

@@ -243,28 +243,57 @@ __global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
       continue;
     }
 
-    // --- base syndrome s0 = H y (XOR of the columns where y_j = 1) --------
-    uint32_t s0[WM];
+    // --- base syndrome s0 = H y ---------------------------------------------
     uint32_t f0 = 0;  // projection of s0
+    if (code.polar) {
+      // H y = (y G_N) restricted to the frozen rows: superset sums of y by
+      // butterfly stages (bits inside a word, then words across lanes)
+      uint32_t x = lane < NW ? sm.y[lane] : 0u;
+      x ^= (x >> 1) & 0x55555555u;
+      x ^= (x >> 2) & 0x33333333u;
+      x ^= (x >> 4) & 0x0F0F0F0Fu;
+      x ^= (x >> 8) & 0x00FF00FFu;
+      x ^= (x >> 16) & 0x0000FFFFu;
+      for (int dw = 1; dw < 32; dw <<= 1) {
+        const uint32_t o = __shfl_down_sync(kFull, x, dw);
+        if (dw < NW && (lane & dw) == 0) x ^= o;
+      }
 #pragma unroll
-    for (int w = 0; w < WM; ++w) s0[w] = 0;
-    for (int j = lane; j < N; j += 32) {
-      if ((sm.y[j >> 5] >> (j & 31)) & 1u) {
-        const uint32_t* col = code.hcol + (size_t)j * W;
+      for (int w = 0; w < WM; ++w) {
+        if (w < W) {
+          const int r = 32 * w + lane;
+          const int fr = r < code.R ? (int)__ldg(code.frozen + r) : 0;
+          const uint32_t src = __shfl_sync(kFull, x, fr >> 5);
+          const bool bit = r < code.R && ((src >> (fr & 31)) & 1u);
+          const uint32_t word = __ballot_sync(kFull, bit);
+          if (bit) f0 ^= __ldg(code.prow + r);
+          if (lane == w) sm.s0[w] = word;
+        }
+      }
+      for (int o = 16; o; o >>= 1) f0 ^= __shfl_xor_sync(kFull, f0, o);
+    } else {
+      // XOR of the H columns where y_j = 1
+      uint32_t s0[WM];
 #pragma unroll
-        for (int w = 0; w < WM; ++w)
-          if (w < W) s0[w] ^= __ldg(col + w);
-        f0 ^= __ldg(code.hf + j);
+      for (int w = 0; w < WM; ++w) s0[w] = 0;
+      for (int j = lane; j < N; j += 32) {
+        if ((sm.y[j >> 5] >> (j & 31)) & 1u) {
+          const uint32_t* col = code.hcol + (size_t)j * W;
+#pragma unroll
+          for (int w = 0; w < WM; ++w)
+            if (w < W) s0[w] ^= __ldg(col + w);
+          f0 ^= __ldg(code.hf + j);
+        }
+      }
+      for (int o = 16; o; o >>= 1) f0 ^= __shfl_xor_sync(kFull, f0, o);
+#pragma unroll
+      for (int w = 0; w < WM; ++w) {
+        uint32_t v = s0[w];
+        for (int o = 16; o; o >>= 1) v ^= __shfl_xor_sync(kFull, v, o);
+        if (lane == w && w < W) sm.s0[w] = v;
       }
     }
-    for (int o = 16; o; o >>= 1) f0 ^= __shfl_xor_sync(kFull, f0, o);
-#pragma unroll
-    for (int w = 0; w < WM; ++w) {
-      uint32_t v = s0[w];
-      for (int o = 16; o; o >>= 1) v ^= __shfl_xor_sync(kFull, v, o);
-      s0[w] = v;
-      if (lane == w && w < W) sm.s0[w] = v;
-    }
+    __syncwarp();
 
     // --- Steps 2-3: the S' least reliable symbols, by (key, index) ---------
     int my_sel = -1;
@@ -329,24 +358,8 @@ __global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
     // --- Step 5 (first part): small spaces completely, else light weights --
     uint32_t best_rank = 0xFFFFFFFFu, best_code = 0;
     int w_done = -1;
-    if (Sp <= 6) {
-      // the whole product space, every lane a stride of assignments
-      const uint32_t n_all = 1u << (2 * Sp);
-      for (uint32_t c = lane; c < n_all; c += 32) {
-        bool valid = true;
-        for (int r = 0; r < Sp; ++r) {
-          const uint32_t d = (c >> (2 * r)) & 3u;
-          if (d && !((sm.ex[r] >> (d - 1)) & 1u)) valid = false;
-        }
-        if (!valid) continue;
-        ++evaluated;
-        if (projection(f0, sm.dflt, Sp, c) == 0 && syndrome_zero(sm.s0, sm.delta, W, Sp, c)) {
-          const uint32_t rk = tep_rank(sm.E, Sp, sm.ex, c);
-          if (rk < best_rank) { best_rank = rk; best_code = c; }
-        }
-      }
-      w_done = Sp;
-    } else {
+    {
+      // every TEP of weight <= w0 in canonical order (all of them when S' <= w0)
       const int wmax = min(min(a.w0, kPrepMaxW0), Sp);
       for (int w = 0; w <= wmax && best_rank == 0xFFFFFFFFu; ++w) {
         const uint32_t nsets = binom16(Sp, w);
@@ -677,7 +690,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_search(SearchArgs a) {
     const CodeDev code = a.codes[s_rec.code];
     const int W = code.W;
     const int Sp = s_rec.sp;
-    const int split = (a.split > 0) ? max(Sp - kSideMax, min(a.split, kSideMax)) : (Sp >> 1);
+    const int split = (a.split > 0) ? min(Sp, max(Sp - kSideMax, min(a.split, kSideMax))) : (Sp >> 1);
     const int nAr = split, nBr = Sp - split;
     for (int t = threadIdx.x; t < Sp * 3 * W; t += blockDim.x) {
       const int r = t / (3 * W), rem = t % (3 * W), alt = rem / W, w = rem % W;
@@ -1570,7 +1583,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     if (cudaGetLastError() != cudaSuccess) { rc = GRAND_E_CUDA; break; }
 
     const int Smax = p->S < Lmax ? p->S : Lmax;
-    if (Smax > 6) {
+    if (Smax > a.w0) {
       SearchArgs s{};
       s.recs = recs;
       s.codes = d_codes;
@@ -2089,7 +2102,7 @@ extern "C" int grand_decode_symbols_noalloc(const grand_code* c, const grand_par
   kp<<<grid, 32 * warps, prep_smem, st>>>(a);
   if (cudaGetLastError() != cudaSuccess) return GRAND_E_CUDA;
   const int Smax = p->S < L ? p->S : L;
-  if (Smax > 6) {
+  if (Smax > a.w0) {
     SearchArgs s{};
     s.recs = recs;
     s.codes = c->d_dev;

@@ -23,10 +23,17 @@ constexpr uint16_t kNoPos = 0xFFFF;  // alternative bit beyond N (padding): no s
 //           column j. The projection of a syndrome is the XOR of hf over the
 //           flipped positions; a zero syndrome has a zero projection, so it
 //           is a filter in front of the full test (false matches ~ 2^-32).
+//   polar: every row r of H is column frozen[r] of G_N = F^{(x)n} (Def. II.1),
+//          so H y is the frozen part of the polar transform y G_N and the
+//          preparation computes it with log2 N butterfly stages instead of
+//          column loads; prow[r] = p_r (the projection word of row r).
 struct CodeDev {
   const uint32_t* hcol;
   const uint32_t* hf;
+  const uint16_t* frozen;
+  const uint32_t* prow;
   int32_t N, K, R, W;
+  int32_t polar;
 };
 
 // Per-frame state handed from the preparation kernel to the search kernel

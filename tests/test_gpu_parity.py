@@ -310,3 +310,27 @@ def test_mixed_rejects_bad_descriptors(g, oracle_lib):
     torch.cuda.synchronize()
     ab = r["abandon"].cpu().tolist()
     assert ab[1:] == [3, 3, 3] and ab[0] in (0, 1)
+
+
+@pytest.mark.parametrize("N,M,S", [(128, 16, 10), (512, 64, 8), (1024, 256, 12)])
+def test_general_H_path_matches_polar_path(g, oracle_lib, N, M, S):
+    """The same code given by a parity-check matrix that is not in polar form
+    (row 0 replaced by row 0 xor row 1: same null space) takes the general
+    column path; its decisions must equal those of the polar-form matrix."""
+    import torch
+
+    code, H, info = code_pair(g, oracle_lib, N)
+    Hp, _ = g.polar_H(N, N // 2)
+    Hg = Hp.copy()
+    Hg[0] ^= Hg[1]
+    code_g = g.Code(Hg, N, N // 2)
+    d = wl.qam_frames(41, N + M, 300, N, info, M, 10.0 if M < 256 else 16.0)
+    cap = 1 << 16
+    a = gpu_decode(g, code, d["symbols"], M, S, cap)
+    b = gpu_decode(g, code_g, d["symbols"], M, S, cap)
+    assert_same(b, a, "general vs polar H")
+    Hd = H.copy()
+    Hd[0] ^= Hd[1]
+    want = oracle_lib.decode_qam(Hd, d["symbols"][:60], M, S, cap, threads=THREADS)
+    assert_same({k: v[:60] for k, v in b.items()}, want, "general H vs oracle")
+    code_g.close()
