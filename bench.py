@@ -71,16 +71,18 @@ NCU_SEARCH = {"sha": "1c0b187066c9008a", "dram_bytes_per_hard_frame": 1551872 / 
 
 def make_inputs(cfg, rank, info_by_N):
     """Host arrays of one step's batch (seeded; rank selects the stream)."""
+    from paper_2405_01808_gb300.dist import shard_stream
+
     cid = CONFIG_IDS[cfg["name"]]
     if cfg["kind"] in ("mixed", "serve"):
         return wl.mixed_frames(cid, 1000 + rank, cfg["frames"], info_by_N)
     parts = []
     for i, snr in enumerate(cfg["snrs"]):
         if cfg["kind"] == "ab":
-            parts.append(wl.bpsk_frames(cid, 100 * rank + i, cfg["frames"], cfg["N"], info_by_N[cfg["N"]], snr))
+            parts.append(wl.bpsk_frames(cid, shard_stream(rank, i), cfg["frames"], cfg["N"], info_by_N[cfg["N"]], snr))
         else:
-            parts.append(wl.qam_frames(cid, 100 * rank + i, cfg["frames"], cfg["N"], info_by_N[cfg["N"]], cfg["M"],
-                                       snr))
+            parts.append(wl.qam_frames(cid, shard_stream(rank, i), cfg["frames"], cfg["N"], info_by_N[cfg["N"]],
+                                       cfg["M"], snr))
     return {"symbols": np.concatenate([p["symbols"] for p in parts]),
             "codewords_packed": np.concatenate([p["codewords_packed"] for p in parts]),
             "snr": np.concatenate([np.full(len(p["symbols"]), p["ebn0_db"]) for p in parts])}
@@ -451,15 +453,12 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = sum(step_ms)
-    units = torch.tensor([float(useful_total), float(n_frames * args.steps), total_ms], dtype=torch.float64,
-                         device=dev)
+    from paper_2405_01808_gb300 import dist as gdist
+
+    (useful_all, frames_all), tmax_ms = gdist.aggregate([useful_total, n_frames * args.steps], total_ms,
+                                                        dist, device=dev)
     if dist:
-        tmax = units[2].clone()
-        dist.all_reduce(units[:2], op=dist.ReduceOp.SUM)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        units[2] = tmax
         dist.barrier()
-    useful_all, frames_all, tmax_ms = units.tolist()
     value = useful_all / (tmax_ms / 1e3)
     frames_per_s = frames_all / (tmax_ms / 1e3)
 
