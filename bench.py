@@ -65,8 +65,8 @@ SMS, ALU_LANES, MAX_CLOCK_GHZ = 152, 64, 2.07
 ALU_PEAK_TOPS = SMS * ALU_LANES * MAX_CLOCK_GHZ / 1000.0
 # Counters of the search kernel from one ncu capture (profiles/k_search_warp_c2_small.md),
 # valid only while csrc/decode.cu is the captured source (sha256 prefix).
-NCU_SEARCH = {"sha": "1c0b187066c9008a", "dram_bytes_per_hard_frame": 1551872 / 9596,
-              "alu_pipe_active": 0.770, "alu_ops_per_check": 0.98}
+NCU_SEARCH = {"sha": "11153b3aa3d1fbc6", "dram_bytes_per_hard_frame": 1550592 / 9596,
+              "alu_pipe_active": 0.771, "alu_ops_per_check": 0.99}
 
 
 def make_inputs(cfg, rank, info_by_N):

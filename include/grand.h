@@ -83,7 +83,8 @@ typedef enum grand_lik {
 
 /* Decode parameters.
  *   order       GRAND_ORDER_*.
- *   M           constellation: 2 (BPSK, HAMMING order only), 4, 16, 64, 256.
+ *   M           constellation: 2 (BPSK, HAMMING order only), 4, 16, 64, 256, 1024,
+ *               4096 (the paper's set, Sec. I contributions and Fig. 4).
  *   S           cut-off (Alg. 2 Step 3), 0..GRAND_S_MAX; S' = min(S, L).
  *   max_weight  HAMMING order: largest number of flipped bits (0..4).
  *   query_cap   abandonment threshold, >= 1 valid queries.
@@ -107,7 +108,7 @@ typedef struct grand_code grand_code;
 
 /* One frame of an uneven batch (grand_decode_mixed). Device memory.
  *   code        index into the `codes` array of the call.
- *   M           constellation of this frame (4, 16, 64, 256); L = ceil(N / log2 M).
+ *   M           constellation of this frame (4 .. 4096); L = ceil(N / log2 M).
  *   sym_offset  first received symbol of the frame in the flat symbol array.
  *   cw_offset   first output word of the frame in the flat codeword array. */
 typedef struct grand_frame_desc {
@@ -169,7 +170,7 @@ int grand_code_info(const grand_code* code, int* N, int* K);
  *   symbols   device. M >= 4: complex64 (interleaved float32 I, Q) [n_frames][L],
  *             in transmitted units with E_b = 1 per coded bit, d = sqrt(3m/(M-1))
  *             (Eq. 2). M = 2: float32 [n_frames][N] BPSK samples (bit 1 <-> -1).
- *   M         2, 4, 16, 64 or 256; L must equal ceil(N / log2 M).
+ *   M         2, 4, 16, 64, 256, 1024 or 4096; L must equal ceil(N / log2 M).
  *   N0        noise spectral density; validated (> 0, finite) but the
  *             likelihood is geometric and does not use it.
  *   lik_variant GRAND_LIK_*.

@@ -34,8 +34,8 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 // Launch-wide parameters
 // ---------------------------------------------------------------------------
 struct QamConst {
-  float q[5];      // 256/d rounded to float, index m = log2(M)/2
-  float inv_d[5];  // 1/d rounded to float
+  float q[7];      // 256/d rounded to float, index m = log2(M)/2 (M = 4 .. 4096)
+  float inv_d[7];  // 1/d rounded to float
 };
 
 struct PrepArgs {
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
       M = d.M;
       sym_off = d.sym_offset;
       cw_off = d.cw_offset;
-      bad_desc = code_id < 0 || code_id >= a.n_codes || !(M == 4 || M == 16 || M == 64 || M == 256) ||
+      bad_desc = code_id < 0 || code_id >= a.n_codes || !(M == 4 || M == 16 || M == 64 || M == 256 || M == 1024 || M == 4096) ||
                  sym_off < 0 || cw_off < 0;
       if (!bad_desc) {
         const int mm = (31 - __clz(M)) >> 1;
@@ -1439,6 +1439,8 @@ static int m_of(int M) {
     case 16: return 2;
     case 64: return 3;
     case 256: return 4;
+    case 1024: return 5;
+    case 4096: return 6;
     default: return 0;
   }
 }
@@ -1454,7 +1456,7 @@ static PrepKernel prep_kernel_for(int Wmax) {
 
 static QamConst make_qam_const() {
   QamConst c{};
-  for (int m = 1; m <= 4; ++m) {
+  for (int m = 1; m <= 6; ++m) {
     const int M = 1 << (2 * m);
     const double d = sqrt(3.0 * m / (double)(M - 1));
     c.q[m] = (float)(256.0 / d);

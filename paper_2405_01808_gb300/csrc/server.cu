@@ -44,6 +44,8 @@ int m_of(int M) {
     case 16: return 2;
     case 64: return 3;
     case 256: return 4;
+    case 1024: return 5;
+    case 4096: return 6;
     default: return 0;
   }
 }

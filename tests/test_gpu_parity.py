@@ -96,7 +96,7 @@ def adversarial_symbols(M, F, L, seed):
     return s
 
 
-@pytest.mark.parametrize("M", [4, 16, 64, 256])
+@pytest.mark.parametrize("M", [4, 16, 64, 256, 1024, 4096])
 @pytest.mark.parametrize("lik", [0, 1])
 def test_demod_parity(g, oracle_lib, M, lik):
     import torch
@@ -161,6 +161,9 @@ CASES = [
     (128, 16, 1, 8.0, 100, 300, 0),          # S = 1
     (128, 16, 0, 8.0, 100, 100, 0),          # S = 0: only the hard word
     (1024, 256, 12, 17.0, 1 << 14, 60, 0),   # largest code, cap binds early
+    (128, 1024, 8, 20.0, 1 << 16, 200, 0),   # 1024-QAM, L = 13
+    (256, 4096, 10, 24.0, 1 << 20, 120, 0),  # 4096-QAM, L = 22 (4 padding bits)
+    (32, 4096, 8, 24.0, 1 << 16, 200, 0),    # L = 3 < S
 ]
 
 

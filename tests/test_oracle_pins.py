@@ -164,7 +164,7 @@ def _pt(s):
 
 
 def test_qam_d_is_eq2(oracle_lib):
-    for M, m in ((4, 1), (16, 2), (64, 3), (256, 4)):
+    for M, m in ((4, 1), (16, 2), (64, 3), (256, 4), (1024, 5), (4096, 6)):
         assert oracle_lib.qam_d(M) == pytest.approx(math.sqrt(3 * m / (M - 1)), rel=1e-15)
         # average symbol energy of the scaled odd-integer grid is 2m E_b
         side = int(math.isqrt(M))
@@ -204,7 +204,7 @@ def test_demod_hand_vectors(oracle_lib, literal):
         assert (got_h, got_v, got_d) == (h, v, dg)
 
 
-@pytest.mark.parametrize("M", [4, 16, 64, 256])
+@pytest.mark.parametrize("M", [4, 16, 64, 256, 1024, 4096])
 def test_demod_hard_point_is_nearest_point(oracle_lib, M):
     """Brute force: the hard point is the nearest of the M points on the
     quantised grid; exactly on a threshold the upper level is taken."""
@@ -251,7 +251,7 @@ def test_demod_invariants(oracle_lib):
 
 def test_demod_packs_gray_labels(oracle_lib):
     """Noise-free symbols demodulate to the transmitted coded bits."""
-    for M in (4, 16, 64, 256):
+    for M in (4, 16, 64, 256, 1024, 4096):
         for N in (32, 128):
             info = oracle_lib.info_set(N, N // 2)
             g = wl.rng(7, M + N)
@@ -427,7 +427,8 @@ def _expected_symbol_level(book_ints, sym_frame, M, N, S, cap, literal=False):
     return wl.pack_bits(y[None, :])[0], min(cap, n_valid), 1
 
 
-@pytest.mark.parametrize("M,snr,S", [(4, 2.0, 8), (16, 6.0, 5), (64, 10.0, 4), (256, 14.0, 3)])
+@pytest.mark.parametrize("M,snr,S", [(4, 2.0, 8), (16, 6.0, 5), (64, 10.0, 4), (256, 14.0, 3), (1024, 19.0, 3),
+                                     (4096, 23.0, 2)])
 def test_symbol_level_matches_codebook_bruteforce(oracle_lib, M, snr, S):
     N = 32
     book = _codebook(oracle_lib, N)
