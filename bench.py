@@ -66,7 +66,7 @@ ALU_PEAK_TOPS = SMS * ALU_LANES * MAX_CLOCK_GHZ / 1000.0
 # Counters of the search kernel from one ncu capture (profiles/k_search_warp_c2_small.md),
 # valid only while csrc/decode.cu is the captured source (sha256 prefix).
 NCU_SEARCH = {"sha": "11153b3aa3d1fbc6", "dram_bytes_per_hard_frame": 1550592 / 9596,
-              "alu_pipe_active": 0.771, "alu_ops_per_check": 0.99}
+              "alu_pipe_active": 0.771, "alu_ops_per_check": 0.98}
 
 
 def make_inputs(cfg, rank, info_by_N):
