@@ -44,6 +44,53 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def _setup(lib):
+    P = ctypes.c_void_p
+    i32, i64, dbl, flt = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_float
+    lib.oracle_polar_G.argtypes = [i32, P]
+    lib.oracle_bhattacharyya.argtypes = [i32, dbl, dbl, P]
+    lib.oracle_frozen_set.argtypes = [i32, i32, dbl, P]
+    lib.oracle_frozen_set.restype = i32
+    lib.oracle_parity_H.argtypes = [i32, i32, P, P]
+    lib.oracle_qam_d.argtypes = [i32]
+    lib.oracle_qam_d.restype = dbl
+    lib.oracle_qam_qscale.argtypes = [i32]
+    lib.oracle_qam_qscale.restype = flt
+    lib.oracle_demod.argtypes = [P, i64, i32, i32, i32, i32, P, P, P, P, P]
+    lib.oracle_decode_qam.argtypes = [P, i32, i32, P, i64, i32, i32, i32, i64, i32, i32, P, P, P]
+    lib.oracle_decode_qam.restype = i32
+    lib.oracle_decode_ab.argtypes = [P, i32, i32, P, i64, i32, i64, i32, P, P, P]
+    lib.oracle_decode_ab.restype = i32
+    lib.oracle_tep_order.argtypes = [i32, P, P, i64]
+    lib.oracle_tep_order.restype = i64
+    lib.oracle_select.argtypes = [P, i32, i32, P]
+    lib.oracle_select.restype = i32
+    return lib
+
+
+def build_variant(source_text: str, so_path: str) -> str:
+    """Compile a modified copy of the oracle source (used by the tests that
+    check that the pins catch planted mistakes)."""
+    src = so_path + ".c"
+    with open(src, "w") as fh:
+        fh.write(source_text)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-ffp-contract=off",
+                    "-fno-fast-math", "-pthread", src, "-o", so_path, "-lm"], check=True)
+    return so_path
+
+
+def source_text() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
+
+
+def use_library(so_path: str | None):
+    """Route every call to the library at so_path (None: the built oracle)."""
+    global _lib
+    with _lock:
+        _lib = None if so_path is None else _setup(ctypes.CDLL(so_path))
+
+
 def _load():
     global _lib
     with _lock:

@@ -507,3 +507,28 @@ def test_nonfinite_frame_is_not_searched(oracle_lib):
     assert r["abandon"].tolist()[1:] == [2, 2] and r["queries"].tolist()[1:] == [0, 0]
     ra = oracle_lib.decode_ab(oracle_lib.parity_H(32, 16), np.array([[np.nan] + [1.0] * 31], np.float32), 3, 5489)
     assert (ra["abandon"][0], ra["queries"][0]) == (2, 0)
+
+
+def test_selection_ties_break_by_index(oracle_lib):
+    """All 32 symbols of a 16-QAM frame sit 0.25 units from their point toward
+    the centre (equal keys, exact in Q8.8, all k = 3); symbol 3 is received at
+    the neighbouring point on the I axis. Ties must go to the lower index, so
+    symbol 3 is rank 3 and its horizontal alternative is TEP t = 10: query 11."""
+    N, M = 128, 16
+    H = oracle_lib.parity_H(N, 64)
+    info = oracle_lib.info_set(N, 64)
+    g = wl.rng(8, 0)
+    c = wl.random_codewords(g, 1, N, info)
+    d = oracle_lib.qam_d(M)
+    tx = np.round(wl.qam_modulate(c, M)[0] / d)  # odd-integer units
+    rx = tx - 0.25 * np.sign(tx.real) - 0.25j * np.sign(tx.imag)
+    # symbol 3 across the threshold toward the centre, 0.25 from the wrong point
+    A = tx[3].real
+    wrong = A - 2 * np.sign(A) if abs(A) == 3 else -A
+    rx[3] = complex(wrong + 0.25 * np.sign(A), rx[3].imag)
+    sym = (rx * d).astype(np.complex64)[None, :]
+    keys = oracle_lib.demod(sym, M, N)["key"][0]
+    assert len(set(keys.tolist())) == 1
+    r = oracle_lib.decode_qam(H, sym, M, 10, 1 << 20)
+    assert (int(r["abandon"][0]), int(r["queries"][0])) == (0, 11)
+    assert np.array_equal(r["cw"][0], wl.pack_bits(c)[0])
