@@ -53,12 +53,15 @@ CONFIGS = {
     "c4": dict(kind="mixed", frames=1000000, S=10, cap=1 << 20,
                desc="uneven mix: N in {32..1024}, M in {4,16,64,256}, Eb/N0 U(4,14) dB, 1000000 frames, "
                     "S=min(L,10), cap 2^20, one call"),
+    "bler": dict(kind="bler", frames=100000, S=8,
+                 desc="BLER vs Eb/N0 at S=8 (the paper's cut-off), cap 4^8: N in {32..1024} x M in {4..4096}, "
+                      "Eb/N0 grid of 9 points per M, frames per point as given"),
     "c5": dict(kind="serve", frames=1000000, S=10, cap=1 << 20, rates=(0.5e6, 1e6, 2e6, 5e6),
                desc="serving: Poisson arrivals at 0.5/1/2/5 M frames/s of the uneven mix (N 32..1024, "
                     "M 4..256, Eb/N0 U(4,14) dB), 1000000 requests per rate, S=min(L,10), cap 2^20"),
 }
 METRIC = "TEP syndrome checks/s & frames/s per GB300; p50/p99 decode latency"
-CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5, "c5": 6}
+CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5, "c5": 6, "bler": 7}
 # ALU roofline: 152 SMs x 64 integer-ALU lanes per clock (LOP3/ISETP class)
 # x 2.07 GHz maximum SM clock.
 SMS, ALU_LANES, MAX_CLOCK_GHZ = 152, 64, 2.07
@@ -73,6 +76,8 @@ def make_inputs(cfg, rank, info_by_N):
     """Host arrays of one step's batch (seeded; rank selects the stream)."""
     from paper_2405_01808_gb300.dist import shard_stream
 
+    if cfg["kind"] == "bler":
+        return None
     cid = CONFIG_IDS[cfg["name"]]
     if cfg["kind"] in ("mixed", "serve"):
         return wl.mixed_frames(cid, 1000 + rank, cfg["frames"], info_by_N)
@@ -184,6 +189,8 @@ def oracle_run(cfg, inputs, idx, threads):
 
 
 def info_sets(cfg, source):
+    if cfg["kind"] == "bler":
+        return {}
     Ns = wl.MIXED_N if cfg["kind"] in ("mixed", "serve") else (cfg["N"],)
     out = {}
     for n in Ns:
@@ -301,6 +308,47 @@ def run_serving(args, cfg, g, inputs):
 
 
 # -------------------------------------------------------------------------
+# BLER sweep (the paper's experiment, Sec. IV / Fig. 4, with this decoder)
+# -------------------------------------------------------------------------
+BLER_GRID = {4: range(0, 9), 16: range(4, 13), 64: range(8, 17), 256: range(12, 21), 1024: range(16, 25),
+             4096: range(20, 29)}
+
+
+def run_bler(args, cfg, g):
+    import torch
+
+    rows = []
+    frames = cfg["frames"]
+    dec_s = 0.0
+    n_total = 0
+    for N in wl.MIXED_N:
+        H, frozen = g.polar_H(N, N // 2)
+        info = np.setdiff1d(np.arange(N), frozen)
+        code = g.Code(H, N, N // 2)
+        for M, grid in BLER_GRID.items():
+            p = g.Params.make(M=M, S=cfg["S"], query_cap=4 ** cfg["S"])
+            curve = []
+            for snr in grid:
+                d = wl.qam_frames(CONFIG_IDS["bler"], N * 10007 + M * 31 + snr, frames, N, info, M, float(snr))
+                sym = torch.from_numpy(d["symbols"]).cuda()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = g.decode_symbols(code, p, sym)
+                torch.cuda.synchronize()
+                dec_s += time.perf_counter() - t0
+                n_total += frames
+                cw = r["cw"].cpu().numpy().view(np.uint32)
+                err = (cw != d["codewords_packed"]).any(axis=1)
+                ab = r["abandon"].cpu().numpy()
+                curve.append({"ebn0_db": snr, "bler": float(err.mean()), "abandon": float((ab == 1).mean()),
+                              "undetected": float((err & (ab == 0)).mean()),
+                              "mean_queries": float(r["queries"].to(torch.float64).mean().item())})
+            rows.append({"N": N, "M": M, "L": wl.symbols_per_frame(N, M), "curve": curve})
+        code.close()
+    return rows, n_total / dec_s
+
+
+# -------------------------------------------------------------------------
 # GPU arm
 # -------------------------------------------------------------------------
 def main():
@@ -347,6 +395,16 @@ def main():
     inputs = make_inputs(cfg, rank, info)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    if cfg["kind"] == "bler":
+        rows, fps = run_bler(args, cfg, g)
+        if rank == 0:
+            print(json.dumps({"metric": "BLER vs Eb/N0 (own curves; the paper's Fig. 4 values are not in its text)",
+                              "value": fps, "unit": "frames/s (decode calls of the sweep)", "n_gpus": world,
+                              "steps": len(rows), "warmup": 0, "higher_is_better": True, "dtype": "u32",
+                              "data": "synthetic (seeded random polar codewords over AWGN)",
+                              "config": {"workload": cfg["desc"], "frames_per_point": cfg["frames"]},
+                              "bler": rows}), flush=True)
+        return 0
     if cfg["kind"] == "serve":
         clocks = ClockSampler(local)
         clocks.start()
