@@ -862,7 +862,8 @@ constexpr int kWarpSideMax = 5;
 constexpr int kWarpTab = 1 << (2 * kWarpSideMax);   // 1024 entries per side
 constexpr int kPlanes = 20;                          // projection bits compared per TEP
 constexpr int kGroups = kWarpTab / 32;               // A groups of 32 entries
-constexpr int kGroupUnroll = 8;                      // groups per candidate check
+constexpr int kGroupUnroll = 4;                      // groups per candidate check
+constexpr int kPlanesL1 = 16;                        // first-level planes (the rest only on a match)
 
 struct WarpSlice {
   uint32_t* planes;  // [kGroups][kPlanes] bit-planes of the A side
@@ -1058,6 +1059,22 @@ __device__ __forceinline__ uint32_t group_acc(const uint32_t* planes, int g, con
   return acc;
 }
 
+// The same OR over a range of planes [B0, B1) (multiples of 4).
+template <int B0, int B1>
+__device__ __forceinline__ uint32_t group_acc_part(const uint32_t* planes, int g, const uint32_t (&m)[kPlanes]) {
+  const uint4* pl = reinterpret_cast<const uint4*>(planes + g * kPlanes);
+  uint32_t acc = 0;
+#pragma unroll
+  for (int j = B0 / 4; j < B1 / 4; ++j) {
+    const uint4 p = pl[j];
+    acc |= p.x ^ m[4 * j + 0];
+    acc |= p.y ^ m[4 * j + 1];
+    acc |= p.z ^ m[4 * j + 2];
+    acc |= p.w ^ m[4 * j + 3];
+  }
+  return acc;
+}
+
 template <int kMinBlocks>
 __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
@@ -1157,9 +1174,20 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
       if (wb_hi + nAr <= w_done) continue;
       int g0 = 0;
       for (; g0 < g_end; g0 += kGroupUnroll) {
+        // first level: kPlanesL1 projection bits of kGroupUnroll groups
+        uint32_t acc[kGroupUnroll];
+        uint32_t all = 0xFFFFFFFFu;
+#pragma unroll
+        for (int u = 0; u < kGroupUnroll; ++u) {
+          acc[u] = group_acc_part<0, kPlanesL1>(sl.planes, g0 + u, m);
+          all &= acc[u];
+        }
+        if (!__any_sync(kFull, all != 0xFFFFFFFFu)) continue;
+        // a first-level match somewhere in the warp: the remaining planes
         uint32_t cand = 0;
 #pragma unroll
-        for (int u = 0; u < kGroupUnroll; ++u) cand |= ~group_acc(sl.planes, g0 + u, m);
+        for (int u = 0; u < kGroupUnroll; ++u)
+          cand |= ~(acc[u] | group_acc_part<kPlanesL1, kPlanes>(sl.planes, g0 + u, m));
         if (__any_sync(kFull, cand)) {
           // rare: locate candidates of this lane and verify every syndrome word
           uint32_t lr = 0xFFFFFFFFu, lc = 0;
