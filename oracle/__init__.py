@@ -10,7 +10,9 @@ Functions and the passages they follow:
   qam_d / qscale                                      -- Def. II.2, Eq. 2
   demod                                               -- Def. III.1, III.2, Alg. 2 Step 1
   tep_order / select                                  -- Alg. 2 Steps 2-4, Cor. III.1
-  decode_qam                                          -- Alg. 2 (Steps 0-5, Return)
+  decode_qam                                          -- Alg. 2 (Steps 0-5, Return); order
+                                                         variants: nearer axis first,
+                                                         five-point NNE (Sec. II)
   decode_ab                                           -- GRAND-AB, Sec. I
 """
 from __future__ import annotations
@@ -59,10 +61,14 @@ def _setup(lib):
     lib.oracle_demod.argtypes = [P, i64, i32, i32, i32, i32, P, P, P, P, P]
     lib.oracle_decode_qam.argtypes = [P, i32, i32, P, i64, i32, i32, i32, i64, i32, i32, P, P, P]
     lib.oracle_decode_qam.restype = i32
+    lib.oracle_decode_qam_order.argtypes = [P, i32, i32, P, i64, i32, i32, i32, i64, i32, i32, i32, P, P, P]
+    lib.oracle_decode_qam_order.restype = i32
     lib.oracle_decode_ab.argtypes = [P, i32, i32, P, i64, i32, i64, i32, P, P, P]
     lib.oracle_decode_ab.restype = i32
     lib.oracle_tep_order.argtypes = [i32, P, P, i64]
     lib.oracle_tep_order.restype = i64
+    lib.oracle_tep_order_n.argtypes = [i32, i32, P, P, i64]
+    lib.oracle_tep_order_n.restype = i64
     lib.oracle_select.argtypes = [P, i32, i32, P]
     lib.oracle_select.restype = i32
     return lib
@@ -96,27 +102,7 @@ def _load():
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_SO)
-            P = ctypes.c_void_p
-            i32, i64, dbl, flt = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_float
-            lib.oracle_polar_G.argtypes = [i32, P]
-            lib.oracle_bhattacharyya.argtypes = [i32, dbl, dbl, P]
-            lib.oracle_frozen_set.argtypes = [i32, i32, dbl, P]
-            lib.oracle_frozen_set.restype = i32
-            lib.oracle_parity_H.argtypes = [i32, i32, P, P]
-            lib.oracle_qam_d.argtypes = [i32]
-            lib.oracle_qam_d.restype = dbl
-            lib.oracle_qam_qscale.argtypes = [i32]
-            lib.oracle_qam_qscale.restype = flt
-            lib.oracle_demod.argtypes = [P, i64, i32, i32, i32, i32, P, P, P, P, P]
-            lib.oracle_decode_qam.argtypes = [P, i32, i32, P, i64, i32, i32, i32, i64, i32, i32, P, P, P]
-            lib.oracle_decode_qam.restype = i32
-            lib.oracle_decode_ab.argtypes = [P, i32, i32, P, i64, i32, i64, i32, P, P, P]
-            lib.oracle_decode_ab.restype = i32
-            lib.oracle_tep_order.argtypes = [i32, P, P, i64]
-            lib.oracle_tep_order.restype = i64
-            lib.oracle_select.argtypes = [P, i32, i32, P]
-            lib.oracle_select.restype = i32
+            lib = _setup(ctypes.CDLL(_SO))
             _lib = lib
     return _lib
 
@@ -182,8 +168,11 @@ def demod(symbols: np.ndarray, M: int, N: int, literal: bool = False) -> dict:
     return out
 
 
+ORDER_NNE, ORDER_NNE_DSORT, ORDER_NNE5 = 1, 2, 3
+
+
 def decode_qam(H: np.ndarray, symbols: np.ndarray, M: int, S: int, cap: int, literal: bool = False,
-               threads: int = 1) -> dict:
+               threads: int = 1, order: int = ORDER_NNE) -> dict:
     H = np.ascontiguousarray(H, dtype=np.uint8)
     R, N = H.shape
     s = np.ascontiguousarray(symbols, dtype=np.complex64)
@@ -191,8 +180,8 @@ def decode_qam(H: np.ndarray, symbols: np.ndarray, M: int, S: int, cap: int, lit
     cw = np.zeros((F, N // 32), np.uint32)
     q = np.zeros(F, np.int64)
     ab = np.zeros(F, np.uint8)
-    rc = _load().oracle_decode_qam(_ptr(H), N, N - R, _ptr(s), F, L, M, S, int(cap), int(literal),
-                                   int(threads), _ptr(cw), _ptr(q), _ptr(ab))
+    rc = _load().oracle_decode_qam_order(_ptr(H), N, N - R, _ptr(s), F, L, M, S, int(cap), int(literal),
+                                         int(order), int(threads), _ptr(cw), _ptr(q), _ptr(ab))
     if rc != 0:
         raise ValueError("oracle_decode_qam: invalid arguments")
     return {"cw": cw, "queries": q, "abandon": ab}
@@ -219,6 +208,17 @@ def tep_order(exists: np.ndarray, max_out: int = 1 << 20) -> tuple[np.ndarray, i
     e = np.ascontiguousarray(exists, dtype=np.uint8)
     out = np.zeros(max_out, dtype=np.uint32)
     total = int(_load().oracle_tep_order(int(e.size), _ptr(e), _ptr(out), int(max_out)))
+    return out[: min(total, max_out)].copy(), total
+
+
+def tep_order_n(exists: np.ndarray, n_alt: int, max_out: int = 1 << 20) -> tuple[np.ndarray, int]:
+    """As tep_order for n_alt alternatives per rank (bit c-1 of exists[r]:
+    alternative c allowed), codes packed with 3 bits per rank."""
+    e = np.ascontiguousarray(exists, dtype=np.uint8)
+    out = np.zeros(max_out, dtype=np.uint32)
+    total = int(_load().oracle_tep_order_n(int(e.size), int(n_alt), _ptr(e), _ptr(out), int(max_out)))
+    if total < 0:
+        raise ValueError("tep_order_n: invalid arguments")
     return out[: min(total, max_out)].copy(), total
 
 

@@ -40,6 +40,17 @@
  *      coordinates read as 0).
  *   R5 bit-level GRAND-AB (Sec. I): hard bit = [r < 0]; TEPs are the bit sets
  *      of weight 0..max_weight in (weight, colex) order over bit indices.
+ *   R6 order variant "nearer axis first": as R3, but the horizontal and
+ *      vertical alternatives of a symbol swap places when the vertical
+ *      distance to the threshold is strictly smaller (d_Q < d_I), so the
+ *      single-axis alternative of the less reliable axis is queried first.
+ *   R7 order variant "five-point NNE" (the nearest-neighbour error channel
+ *      the paper compares against in Sec. II): up to four alternatives per
+ *      symbol, the neighbouring levels on either side of each axis (toward
+ *      the received point on I, toward it on Q, away from it on I, away on
+ *      Q, in that order), no diagonal; a neighbour exists iff its level is
+ *      on the constellation. Symbols are sorted by the same key, and the
+ *      TEPs follow R3 with base-4 alternative digits.
  */
 #include <math.h>
 #include <pthread.h>
@@ -214,6 +225,7 @@ static sym_t demod_symbol(float a, float b, float q, double dscale, int sqrtM, i
  *   hard_idx = (I level << 8) | Q level
  *   nmask bit0 = horizontal neighbour exists, bit1 = vertical, bit2 = diagonal,
  *         bit3 = I direction is +1, bit4 = Q direction is +1,
+ *         bit5 = d_Q < d_I (the vertical alternative is the nearer one),
  *         bit7 = non-finite received value. */
 static uint8_t pack_nmask(const sym_t* s) {
   uint8_t m = 0;
@@ -222,6 +234,7 @@ static uint8_t pack_nmask(const sym_t* s) {
   if (s->I.exists && s->Q.exists) m |= 4;
   if (s->I.dir > 0) m |= 8;
   if (s->Q.dir > 0) m |= 16;
+  if (s->Q.dq < s->I.dq) m |= 32; /* vertical alternative nearer (R6) */
   if (s->nonfinite) m |= 128;
   return m;
 }
@@ -312,14 +325,15 @@ static void pack64(const uint8_t* bits, int N, uint64_t* x) {
     if (bits[j]) x[j / 64] |= (uint64_t)1 << (j % 64);
 }
 
-/* Visit the valid TEPs over S' ranks in canonical order (R3). exists[r] has
- * bit0 = h, bit1 = v, bit2 = diag allowed for rank r. For each valid TEP
+/* Visit the valid TEPs over S' ranks in canonical order (R3), with n_alt
+ * alternatives per symbol (3 for the paper's order, 4 for R7). Bit c-1 of
+ * exists[r] says whether alternative c of rank r exists. For each valid TEP
  * the callback gets its per-rank alternative codes alt[r] in {0 = unchanged,
- * 1 = h, 2 = v, 3 = diag}; it returns nonzero to stop. Returns the number of
- * valid TEPs visited (including the one that stopped the walk). */
+ * 1 .. n_alt}; it returns nonzero to stop. Returns the number of valid TEPs
+ * visited (including the one that stopped the walk). */
 typedef int (*tep_visit_fn)(void* ctx, const int* alt, int64_t count);
 
-static int64_t walk_teps(int Sp, const uint8_t* exists, tep_visit_fn visit, void* ctx) {
+static int64_t walk_teps(int Sp, int n_alt, const uint8_t* exists, tep_visit_fn visit, void* ctx) {
   int64_t count = 0;
   int p[ORACLE_MAX_S];
   int alt[ORACLE_MAX_S];
@@ -328,14 +342,14 @@ static int64_t walk_teps(int Sp, const uint8_t* exists, tep_visit_fn visit, void
     int more = 1;
     while (more) {
       int64_t n_alpha = 1;
-      for (int i = 0; i < w; ++i) n_alpha *= 3;
+      for (int i = 0; i < w; ++i) n_alpha *= n_alt;
       for (int64_t alpha = 0; alpha < n_alpha; ++alpha) {
         for (int r = 0; r < Sp; ++r) alt[r] = 0;
         int valid = 1;
         int64_t rest = alpha;
         for (int j = 0; j < w; ++j) { /* digit j belongs to the j-th smallest rank */
-          int code = (int)(rest % 3) + 1; /* 1 = h, 2 = v, 3 = diag */
-          rest /= 3;
+          int code = (int)(rest % n_alt) + 1; /* e.g. 1 = h, 2 = v, 3 = diag */
+          rest /= n_alt;
           alt[p[j]] = code;
           if (!((exists[p[j]] >> (code - 1)) & 1)) valid = 0;
         }
@@ -361,7 +375,7 @@ typedef struct {
   int m;
   int Sp;
   int sym_of_rank[ORACLE_MAX_S];
-  int alt_label[ORACLE_MAX_S][4]; /* label after alternative code c (c=0: hard) */
+  int alt_label[ORACLE_MAX_S][5]; /* label after alternative code c (c=0: hard) */
   const uint8_t* ybits;
   int64_t cap;
   /* result */
@@ -402,9 +416,13 @@ static int list_visit(void* vctx, const int* alt, int64_t count) {
 
 /* Decode one frame. H is (R x N) bytes. Writes cw_words (N/32), queries,
  * abandon. Returns the number of valid TEPs of the frame (Prod (1+k_i)). */
+#define ORDER_NNE 1       /* Def. III.2: h, v, diag */
+#define ORDER_NNE_DSORT 2 /* R6 */
+#define ORDER_NNE5 3      /* R7 */
+
 static void decode_qam_frame(const uint64_t* Hrows, int N, int R, const float* sym, int L, int M,
-                             int S, int64_t cap, int literal, uint32_t* cw_words, int64_t* queries,
-                             uint8_t* abandon) {
+                             int S, int64_t cap, int literal, int order, uint32_t* cw_words,
+                             int64_t* queries, uint8_t* abandon) {
   int sqrtM = 1 << (log2i(M) / 2);
   int m = log2i(M) / 2;
   float q = oracle_qam_qscale(M);
@@ -450,12 +468,29 @@ static void decode_qam_frame(const uint64_t* Hrows, int N, int R, const float* s
     int lI = t->I.level, lQ = t->Q.level;
     int nI = lI + t->I.dir, nQ = lQ + t->Q.dir;
     /* Def. III.2: horizontal s_d1, vertical s_d2, diagonal s_d1d2 */
+    int lab_h = t->I.exists ? ((gray(nI) << m) | gray(lQ)) : 0;
+    int lab_v = t->Q.exists ? ((gray(lI) << m) | gray(nQ)) : 0;
+    int ex_h = t->I.exists, ex_v = t->Q.exists;
     c.alt_label[r][0] = (gray(lI) << m) | gray(lQ);
-    c.alt_label[r][1] = t->I.exists ? ((gray(nI) << m) | gray(lQ)) : 0;
-    c.alt_label[r][2] = t->Q.exists ? ((gray(lI) << m) | gray(nQ)) : 0;
+    if (order == ORDER_NNE5) {
+      /* R7: the other neighbouring level of each axis, away from r */
+      int aI = lI - t->I.dir, aQ = lQ - t->Q.dir;
+      int ex_aI = aI >= 0 && aI < sqrtM, ex_aQ = aQ >= 0 && aQ < sqrtM;
+      c.alt_label[r][1] = lab_h;
+      c.alt_label[r][2] = lab_v;
+      c.alt_label[r][3] = ex_aI ? ((gray(aI) << m) | gray(lQ)) : 0;
+      c.alt_label[r][4] = ex_aQ ? ((gray(lI) << m) | gray(aQ)) : 0;
+      exists[r] = (uint8_t)(ex_h | (ex_v << 1) | (ex_aI << 2) | (ex_aQ << 3));
+      continue;
+    }
+    if (order == ORDER_NNE_DSORT && t->Q.dq < t->I.dq) { /* R6: nearer axis first */
+      int tl = lab_h; lab_h = lab_v; lab_v = tl;
+      int te = ex_h; ex_h = ex_v; ex_v = te;
+    }
+    c.alt_label[r][1] = lab_h;
+    c.alt_label[r][2] = lab_v;
     c.alt_label[r][3] = (t->I.exists && t->Q.exists) ? ((gray(nI) << m) | gray(nQ)) : 0;
-    exists[r] = (uint8_t)((t->I.exists ? 1 : 0) | (t->Q.exists ? 2 : 0) |
-                          ((t->I.exists && t->Q.exists) ? 4 : 0));
+    exists[r] = (uint8_t)((ex_h ? 1 : 0) | (ex_v ? 2 : 0) | ((ex_h && ex_v) ? 4 : 0));
   }
   free(used);
   c.Hrows = Hrows;
@@ -467,7 +502,7 @@ static void decode_qam_frame(const uint64_t* Hrows, int N, int R, const float* s
   c.ybits = ybits;
   c.cap = cap;
   /* Alg. 2 Steps 4-5: query the TEPs in canonical order until a codeword */
-  int64_t n = walk_teps(Sp, exists, qam_visit, &c);
+  int64_t n = walk_teps(Sp, order == ORDER_NNE5 ? 4 : 3, exists, qam_visit, &c);
   const uint8_t* out = c.hit ? c.xbits : ybits;
   for (int w = 0; w < W; ++w) {
     uint32_t v = 0;
@@ -538,7 +573,7 @@ static uint64_t* pack_H_rows(const uint8_t* H, int R, int N) {
 
 typedef struct {
   const uint64_t* Hrows;
-  int N, R, L, M, S, max_weight, literal, bit_level;
+  int N, R, L, M, S, max_weight, literal, order, bit_level;
   int64_t cap;
   const float* sym;
   int64_t F;
@@ -557,7 +592,7 @@ static void* run_job(void* vjob) {
                       j->cw + (size_t)f * W, &j->queries[f], &j->abandon[f]);
     else
       decode_qam_frame(j->Hrows, j->N, j->R, j->sym + 2 * (size_t)f * j->L, j->L, j->M, j->S, j->cap,
-                       j->literal, j->cw + (size_t)f * W, &j->queries[f], &j->abandon[f]);
+                       j->literal, j->order, j->cw + (size_t)f * W, &j->queries[f], &j->abandon[f]);
   }
   return NULL;
 }
@@ -581,20 +616,31 @@ static int run_batch(job_t proto, int nthreads) {
   return 0;
 }
 
-/* Symbol-level decode of F frames of L complex symbols (float pairs). */
-int oracle_decode_qam(const uint8_t* H, int N, int K, const float* sym, int64_t F, int L, int M, int S,
-                      int64_t cap, int literal, int nthreads, uint32_t* cw, int64_t* queries,
-                      uint8_t* abandon) {
+/* Symbol-level decode of F frames of L complex symbols (float pairs), with
+ * the TEP order `order` (ORDER_NNE, ORDER_NNE_DSORT or ORDER_NNE5). */
+int oracle_decode_qam_order(const uint8_t* H, int N, int K, const float* sym, int64_t F, int L, int M,
+                            int S, int64_t cap, int literal, int order, int nthreads, uint32_t* cw,
+                            int64_t* queries, uint8_t* abandon) {
   if (S < 0 || S > ORACLE_MAX_S || cap < 1 || N > ORACLE_MAX_N || N % 32) return -1;
+  if (order != ORDER_NNE && order != ORDER_NNE_DSORT && order != ORDER_NNE5) return -1;
   job_t p;
   memset(&p, 0, sizeof p);
   p.R = N - K;
   p.Hrows = pack_H_rows(H, p.R, N);
-  p.N = N; p.L = L; p.M = M; p.S = S; p.cap = cap; p.literal = literal; p.bit_level = 0;
+  p.N = N; p.L = L; p.M = M; p.S = S; p.cap = cap; p.literal = literal; p.order = order;
+  p.bit_level = 0;
   p.sym = sym; p.F = F; p.cw = cw; p.queries = queries; p.abandon = abandon;
   run_batch(p, nthreads);
   free((void*)p.Hrows);
   return 0;
+}
+
+/* The same with the paper's order (Def. III.2). */
+int oracle_decode_qam(const uint8_t* H, int N, int K, const float* sym, int64_t F, int L, int M, int S,
+                      int64_t cap, int literal, int nthreads, uint32_t* cw, int64_t* queries,
+                      uint8_t* abandon) {
+  return oracle_decode_qam_order(H, N, K, sym, F, L, M, S, cap, literal, ORDER_NNE, nthreads, cw,
+                                 queries, abandon);
 }
 
 /* Bit-level GRAND-AB decode of F frames of N real BPSK samples. */
@@ -618,6 +664,7 @@ int oracle_decode_ab(const uint8_t* H, int N, int K, const float* r, int64_t F, 
 
 typedef struct {
   int Sp;
+  int bits; /* bits per rank in the packed code */
   uint32_t* out;
   int64_t max;
 } codes_ctx;
@@ -626,7 +673,7 @@ static int codes_visit(void* vctx, const int* alt, int64_t count) {
   codes_ctx* c = (codes_ctx*)vctx;
   if (count > c->max) return 1;
   uint32_t code = 0;
-  for (int r = 0; r < c->Sp; ++r) code |= (uint32_t)alt[r] << (2 * r);
+  for (int r = 0; r < c->Sp; ++r) code |= (uint32_t)alt[r] << (c->bits * r);
   c->out[count - 1] = code;
   return 0;
 }
@@ -636,12 +683,25 @@ static int codes_visit(void* vctx, const int* alt, int64_t count) {
  * Returns the total number of valid TEPs (even if larger than max_out). */
 int64_t oracle_tep_order(int Sp, const uint8_t* exists, uint32_t* out, int64_t max_out) {
   if (Sp < 0 || Sp > ORACLE_MAX_S) return -1;
-  codes_ctx c = {Sp, out, max_out};
-  int64_t total = walk_teps(Sp, exists, codes_visit, &c);
+  codes_ctx c = {Sp, 2, out, max_out};
+  int64_t total = walk_teps(Sp, 3, exists, codes_visit, &c);
   if (total > max_out) {
     /* the walk stopped early; count the rest without recording */
     list_ctx l = {exists, NULL, INT64_MAX};
-    total = walk_teps(Sp, exists, list_visit, &l);
+    total = walk_teps(Sp, 3, exists, list_visit, &l);
+  }
+  return total;
+}
+
+/* The same for n_alt alternatives per symbol (3 or 4), packed with 3 bits
+ * per rank (Sp <= 10). */
+int64_t oracle_tep_order_n(int Sp, int n_alt, const uint8_t* exists, uint32_t* out, int64_t max_out) {
+  if (Sp < 0 || Sp > 10 || n_alt < 1 || n_alt > 4) return -1;
+  codes_ctx c = {Sp, 3, out, max_out};
+  int64_t total = walk_teps(Sp, n_alt, exists, codes_visit, &c);
+  if (total > max_out) {
+    list_ctx l = {exists, NULL, INT64_MAX};
+    total = walk_teps(Sp, n_alt, exists, list_visit, &l);
   }
   return total;
 }

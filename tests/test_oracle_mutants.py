@@ -69,6 +69,22 @@ MUTANTS = {
         "if (best < 0 || s[i].key < s[best].key) best = i; /* ties: lower index first */",
         "if (best < 0 || s[i].key <= s[best].key) best = i; /* ties: lower index first */",
         ["test_symbol_level_matches_codebook_bruteforce", "test_selection_ties_break_by_index"]),
+    "nearer_axis_tie_counts_as_vertical": (
+        "if (s->Q.dq < s->I.dq) m |= 32;",
+        "if (s->Q.dq <= s->I.dq) m |= 32;",
+        ["test_demod_hand_vectors"]),
+    "nearer_axis_order_reversed": (
+        "if (order == ORDER_NNE_DSORT && t->Q.dq < t->I.dq) {",
+        "if (order == ORDER_NNE_DSORT && t->Q.dq > t->I.dq) {",
+        ["test_nearer_axis_first_single_error", "test_order_variants_match_codebook_bruteforce"]),
+    "five_point_away_on_the_near_side": (
+        "int aI = lI - t->I.dir, aQ = lQ - t->Q.dir;",
+        "int aI = lI + t->I.dir, aQ = lQ - t->Q.dir;",
+        ["test_order_variants_match_codebook_bruteforce"]),
+    "five_point_walk_in_base_3": (
+        "walk_teps(Sp, order == ORDER_NNE5 ? 4 : 3, exists, qam_visit, &c);",
+        "walk_teps(Sp, order == ORDER_NNE5 ? 3 : 3, exists, qam_visit, &c);",
+        ["test_five_point_away_error", "test_order_variants_match_codebook_bruteforce"]),
 }
 
 

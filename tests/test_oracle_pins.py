@@ -59,16 +59,17 @@ def esp(ks):
     return poly
 
 
-def canonical_index(code, Sp):
-    """Closed-form canonical index of a TEP given by per-rank codes (2 bits per
-    rank, 0 = unchanged, 1 = h, 2 = v, 3 = diag)."""
-    digits = [(code >> (2 * r)) & 3 for r in range(Sp)]
+def canonical_index(code, Sp, base=3, bits=2):
+    """Closed-form canonical index of a TEP given by per-rank codes (`bits` bits
+    per rank, 0 = unchanged, 1..base = the alternative; for the paper's order
+    1 = h, 2 = v, 3 = diag)."""
+    digits = [(code >> (bits * r)) & ((1 << bits) - 1) for r in range(Sp)]
     P = [r for r in range(Sp) if digits[r]]
     w = len(P)
-    off = sum(math.comb(Sp, v) * 3 ** v for v in range(w))
+    off = sum(math.comb(Sp, v) * base ** v for v in range(w))
     colex = sum(math.comb(p, j + 1) for j, p in enumerate(P))
-    alpha = sum((digits[p] - 1) * 3 ** j for j, p in enumerate(P))
-    return off + colex * 3 ** w + alpha
+    alpha = sum((digits[p] - 1) * base ** j for j, p in enumerate(P))
+    return off + colex * base ** w + alpha
 
 
 def gray(l):
@@ -182,6 +183,7 @@ def test_demod_hand_vectors(oracle_lib, literal):
         Lx = float(t[15]) if literal else float(t[7])
         key = int(t[14]) if literal else int(t[8])
         nmask, hard = int(t[9]), int(t[10])
+        nmask |= 32 * int(t[17] if literal else t[16])  # nearer alternative is vertical
         h, v, dg = _pt(t[11]), _pt(t[12]), _pt(t[13])
         d = math.sqrt(3 * (math.log2(M) / 2) / (M - 1))
         sym = np.array([[complex(rI * d, rQ * d)]], dtype=np.complex64)
@@ -300,6 +302,37 @@ def test_tep_order_partial_neighbours(oracle_lib):
         assert [w.count(k) for k in range(Sp + 1)] == esp(ks)
 
 
+@pytest.mark.parametrize("Sp", [0, 1, 2, 4, 7])
+def test_tep_order_five_point_all_neighbours(oracle_lib, Sp):
+    """Four alternatives per symbol (the five-point NNE model of Sec. II):
+    5^S' patterns, C(S', w) 4^w of them with w altered symbols."""
+    codes, total = oracle_lib.tep_order_n(np.full(Sp, 15, np.uint8), 4)
+    assert total == 5 ** Sp
+    idx = [canonical_index(int(c), Sp, base=4, bits=3) for c in codes]
+    assert idx == list(range(5 ** Sp))
+    w = np.array([sum(1 for r in range(Sp) if (int(c) >> 3 * r) & 7) for c in codes])
+    for k in range(Sp + 1):
+        assert np.sum(w == k) == math.comb(Sp, k) * 4 ** k
+
+
+def test_tep_order_five_point_partial_neighbours(oracle_lib):
+    """Edge and corner symbols (2 or 3 alternatives): the valid patterns are
+    exactly the allowed products, in canonical order, counted by e_w(k)."""
+    g = np.random.default_rng(12)
+    for trial in range(30):
+        Sp = int(g.integers(1, 7))
+        exists = g.choice(np.array([15, 7, 11, 13, 14, 5, 10, 3, 12], dtype=np.uint8), size=Sp)
+        codes, total = oracle_lib.tep_order_n(exists, 4)
+        ks = [bin(int(e)).count("1") for e in exists]
+        assert total == int(np.prod([1 + k for k in ks]))
+        allowed = [[0] + [a for a in (1, 2, 3, 4) if (int(exists[r]) >> (a - 1)) & 1] for r in range(Sp)]
+        want = sorted(canonical_index(sum(d << 3 * r for r, d in enumerate(ds)), Sp, base=4, bits=3)
+                      for ds in itertools.product(*allowed))
+        assert [canonical_index(int(c), Sp, base=4, bits=3) for c in codes] == want
+        w = [sum(1 for r in range(Sp) if (int(c) >> 3 * r) & 7) for c in codes]
+        assert [w.count(k) for k in range(Sp + 1)] == esp(ks)
+
+
 def test_select_is_stable_sort(oracle_lib):
     g = np.random.default_rng(3)
     for _ in range(50):
@@ -367,11 +400,14 @@ def test_grand_ab_is_ml_within_radius(oracle_lib):
             assert np.array_equal(r["cw"][f], wl.pack_bits(y[f][None, :])[0])
 
 
-def _expected_symbol_level(book_ints, sym_frame, M, N, S, cap, literal=False):
+def _expected_symbol_level(book_ints, sym_frame, M, N, S, cap, literal=False, order=1):
     """Brute force for one frame, independent of the oracle's search: order the
     symbols by the quantised key, enumerate every valid TEP by the closed-form
     canonical index, build each candidate word from the Gray labels and look
-    it up in the codebook (membership by lookup, not by syndrome)."""
+    it up in the codebook (membership by lookup, not by syndrome).
+    order 1: h, v, diag; 2: the single-axis alternative of the nearer axis
+    first (nmask bit 32 = vertical nearer); 3: the four axis neighbours
+    (toward on I, toward on Q, away on I, away on Q), base-4 digits."""
     import oracle as orc
     dm = orc.demod(sym_frame[None, :], M, N, literal=literal)
     L = sym_frame.size
@@ -379,9 +415,9 @@ def _expected_symbol_level(book_ints, sym_frame, M, N, S, cap, literal=False):
     lI = (dm["hard_idx"][0] >> 8).astype(int)
     lQ = (dm["hard_idx"][0] & 0xFF).astype(int)
     nm = dm["nmask"][0].astype(int)
-    order = np.lexsort((np.arange(L), dm["key"][0]))
+    by_key = np.lexsort((np.arange(L), dm["key"][0]))
     Sp = min(S, L)
-    sel = order[:Sp]
+    sel = by_key[:Sp]
 
     def labels_to_bits(lab_I, lab_Q):
         bits = np.zeros(2 * m * L, dtype=np.uint8)
@@ -391,34 +427,38 @@ def _expected_symbol_level(book_ints, sym_frame, M, N, S, cap, literal=False):
                 bits[2 * m * i + k] = (lab >> (2 * m - 1 - k)) & 1
         return bits[:N]
 
+    side = 1 << m
     alts = []
     for r in range(Sp):
         i = sel[r]
         dI = 1 if nm[i] & 8 else -1
         dQ = 1 if nm[i] & 16 else -1
-        opts = [0]
-        if nm[i] & 1:
-            opts.append(1)
-        if nm[i] & 2:
-            opts.append(2)
-        if nm[i] & 4:
-            opts.append(3)
-        alts.append((i, dI, dQ, opts))
+        # each alternative as a level move (move_I, move_Q)
+        moves = {1: (dI, 0), 2: (0, dQ), 3: (dI, dQ)}
+        ok = {1: bool(nm[i] & 1), 2: bool(nm[i] & 2), 3: bool(nm[i] & 4)}
+        if order == 2 and nm[i] & 32:
+            moves[1], moves[2] = moves[2], moves[1]
+            ok[1], ok[2] = ok[2], ok[1]
+        if order == 3:
+            moves = {1: (dI, 0), 2: (0, dQ), 3: (-dI, 0), 4: (0, -dQ)}
+            ok = {1: bool(nm[i] & 1), 2: bool(nm[i] & 2), 3: 0 <= lI[i] - dI < side, 4: 0 <= lQ[i] - dQ < side}
+        opts = [0] + [a for a in sorted(moves) if ok[a]]
+        alts.append((i, moves, opts))
+    base, bits = (4, 3) if order == 3 else (3, 2)
     combos = []
-    for ds in itertools.product(*[a[3] for a in alts]):
-        code = sum(d_ << 2 * r for r, d_ in enumerate(ds))
-        combos.append((canonical_index(code, Sp), ds))
+    for ds in itertools.product(*[a[2] for a in alts]):
+        code = sum(d_ << bits * r for r, d_ in enumerate(ds))
+        combos.append((canonical_index(code, Sp, base=base, bits=bits), ds))
     combos.sort()
     n_valid = len(combos)
     for pos, (t, ds) in enumerate(combos, start=1):
         if pos > cap:
             break
         II, QQ = lI.copy(), lQ.copy()
-        for (i, dI, dQ, _), dd in zip(alts, ds):
-            if dd in (1, 3):
-                II[i] += dI
-            if dd in (2, 3):
-                QQ[i] += dQ
+        for (i, moves, _), dd in zip(alts, ds):
+            if dd:
+                II[i] += moves[dd][0]
+                QQ[i] += moves[dd][1]
         x = labels_to_bits(II, QQ)
         xi = int(wl.pack_bits(x[None, :])[0].astype(np.uint64)[0]) if N == 32 else None
         if xi in book_ints:
@@ -445,6 +485,86 @@ def test_symbol_level_matches_codebook_bruteforce(oracle_lib, M, snr, S):
         assert np.array_equal(r["cw"][f], cw)
         n_ab += ab
     assert 0 < n_ab < 40  # both outcomes exercised
+
+
+@pytest.mark.parametrize("order,M,snr,S", [(2, 4, 2.0, 8), (2, 16, 6.0, 5), (2, 64, 9.0, 4),
+                                           (3, 4, 2.0, 6), (3, 16, 6.0, 4), (3, 64, 9.0, 3)])
+def test_order_variants_match_codebook_bruteforce(oracle_lib, order, M, snr, S):
+    """The two order variants (nearer axis first; five-point NNE) against the
+    codebook brute force at N=32, the whole TEP space within the cap."""
+    N = 32
+    book = _codebook(oracle_lib, N)
+    book_ints = set(wl.pack_bits(book)[:, 0].astype(np.uint64).tolist())
+    H = oracle_lib.parity_H(N, 16)
+    info = oracle_lib.info_set(N, 16)
+    d = wl.qam_frames(3, 100 * order + M, 40, N, info, M, snr)
+    cap = (5 if order == 3 else 4) ** S
+    r = oracle_lib.decode_qam(H, d["symbols"], M, S, cap, order=order)
+    n_ab = 0
+    for f in range(40):
+        cw, q, ab = _expected_symbol_level(book_ints, d["symbols"][f], M, N, S, cap, order=order)
+        assert (int(r["abandon"][f]), int(r["queries"][f])) == (ab, q), f
+        assert np.array_equal(r["cw"][f], cw)
+        n_ab += ab
+    assert 0 < n_ab < 40
+
+
+def _frame_with_moved_symbol(oracle_lib, want, place):
+    """A 16-QAM N=128 frame received exactly on its points except one symbol:
+    the first symbol whose transmitted amplitudes (A_I, A_Q) satisfy `want`
+    is received at place(A_I, A_Q) (odd-integer units). Returns the
+    codeword, the symbols and that symbol's index."""
+    N, M = 128, 16
+    info = oracle_lib.info_set(N, 64)
+    c = wl.random_codewords(wl.rng(9, 0), 1, N, info)
+    d = oracle_lib.qam_d(M)
+    tx = np.round(wl.qam_modulate(c, M)[0] / d)
+    i = next(j for j in range(tx.size) if want(int(tx[j].real), int(tx[j].imag)))
+    rx = tx.copy()
+    rx[i] = place(int(tx[i].real), int(tx[i].imag))
+    return c, (rx * d).astype(np.complex64)[None, :], i
+
+
+def test_nearer_axis_first_single_error(oracle_lib):
+    """One symbol is received 0.2 past its Q threshold toward the centre
+    (d_Q = 0.2, so the hard point is wrong on Q only) and 0.6 from its point
+    toward the centre on I (d_I = 0.4). The transmitted point is then the
+    vertical alternative of the least reliable symbol: query 3 in the
+    paper's order (after h), query 2 when the nearer axis goes first."""
+    N, M = 128, 16
+    H = oracle_lib.parity_H(N, 64)
+    c, s, i = _frame_with_moved_symbol(
+        oracle_lib, lambda aI, aQ: True,
+        lambda aI, aQ: complex(aI - 0.6 * np.sign(aI), aQ - 1.2 * np.sign(aQ)))
+    dm = oracle_lib.demod(s, M, N)
+    assert oracle_lib.select(dm["key"][0], 8)[0] == i
+    assert dm["nmask"][0, i] & 32 and dm["nmask"][0, i] & 7 == 7
+    a = oracle_lib.decode_qam(H, s, M, 8, 1 << 16, order=1)
+    b = oracle_lib.decode_qam(H, s, M, 8, 1 << 16, order=2)
+    for r in (a, b):
+        assert r["abandon"][0] == 0 and np.array_equal(r["cw"][0], wl.pack_bits(c)[0])
+    assert (int(a["queries"][0]), int(b["queries"][0])) == (3, 2)
+
+
+def test_five_point_away_error(oracle_lib):
+    """A symbol sent at (+-1, +-3) is received at (+-0.5, +-0.7): its hard
+    point is (+-1, +-1) and the transmitted point is the neighbour on the Q
+    axis away from the received value. With four alternatives per symbol
+    (toward I, toward Q, away I, away Q, all present) it is the fourth
+    alternative of rank 0: query 5."""
+    N, M = 128, 16
+    H = oracle_lib.parity_H(N, 64)
+    c, s, i = _frame_with_moved_symbol(
+        oracle_lib, lambda aI, aQ: abs(aI) == 1 and abs(aQ) == 3,
+        lambda aI, aQ: complex(aI - 0.5 * np.sign(aI), 0.7 * np.sign(aQ)))
+    dm = oracle_lib.demod(s, M, N)
+    assert oracle_lib.select(dm["key"][0], 8)[0] == i
+    r = oracle_lib.decode_qam(H, s, M, 8, 1 << 16, order=3)
+    assert r["abandon"][0] == 0 and int(r["queries"][0]) == 5
+    assert np.array_equal(r["cw"][0], wl.pack_bits(c)[0])
+    # the paper's order cannot reach it at rank 0: its first hit, if any, is later
+    p = oracle_lib.decode_qam(H, s, M, 8, 1 << 16, order=1)
+    assert p["abandon"][0] == 1 or int(p["queries"][0]) > 4
 
 
 def test_cap_boundary(oracle_lib):
