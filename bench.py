@@ -56,12 +56,21 @@ CONFIGS = {
     "bler": dict(kind="bler", frames=100000, S=8,
                  desc="BLER vs Eb/N0 at S=8 (the paper's cut-off), cap 4^8: N in {32..1024} x M in {4..4096}, "
                       "Eb/N0 grid of 9 points per M, frames per point as given"),
+    "orders": dict(kind="orders", N=128, K=64, M=16, snrs=(6.0, 8.0, 10.0), frames=20000,
+                   desc="TEP order comparison on polar N=128 K=64, 16-QAM, Eb/N0 6/8/10 dB x 20000 frames: the "
+                        "paper's order, its literal Def. III.1 reading, nearer axis first, five-point NNE; S=8 "
+                        "with the whole space (4^8 / 5^8) and S=10 with cap 2^20"),
+    "membership": dict(kind="membership", N=128, K=64, M=16, snrs=(6.0, 8.0, 10.0), frames=2000, S=10,
+                       cap=1 << 20,
+                       desc="membership-test ablation on polar N=128 K=64, 16-QAM, Eb/N0 6/8/10 dB x 2000 "
+                            "frames, S=10, cap 2^20: split search (syndrome deltas, bit-sliced), per-TEP "
+                            "syndrome deltas, per-TEP row parity (Alg. 1's product)"),
     "c5": dict(kind="serve", frames=1000000, S=10, cap=1 << 20, rates=(0.5e6, 1e6, 2e6, 5e6),
                desc="serving: Poisson arrivals at 0.5/1/2/5 M frames/s of the uneven mix (N 32..1024, "
                     "M 4..256, Eb/N0 U(4,14) dB), 1000000 requests per rate, S=min(L,10), cap 2^20"),
 }
 METRIC = "TEP syndrome checks/s & frames/s per GB300; p50/p99 decode latency"
-CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5, "c5": 6, "bler": 7}
+CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5, "c5": 6, "bler": 7, "orders": 2, "membership": 2}
 # ALU roofline: 152 SMs x 64 integer-ALU lanes per clock (LOP3/ISETP class)
 # x 2.07 GHz maximum SM clock.
 SMS, ALU_LANES, MAX_CLOCK_GHZ = 152, 64, 2.07
@@ -76,7 +85,7 @@ def make_inputs(cfg, rank, info_by_N):
     """Host arrays of one step's batch (seeded; rank selects the stream)."""
     from paper_2405_01808_gb300.dist import shard_stream
 
-    if cfg["kind"] == "bler":
+    if cfg["kind"] in ("bler", "orders", "membership"):
         return None
     cid = CONFIG_IDS[cfg["name"]]
     if cfg["kind"] in ("mixed", "serve"):
@@ -348,6 +357,89 @@ def run_bler(args, cfg, g):
     return rows, n_total / dec_s
 
 
+def _c2_like_batch(cfg, g):
+    """The N=128 16-QAM frames of the default workload (same seeds), on the device."""
+    import torch
+
+    H, frozen = g.polar_H(cfg["N"], cfg["K"])
+    info = np.setdiff1d(np.arange(cfg["N"]), frozen)
+    parts = [wl.qam_frames(CONFIG_IDS[cfg["name"]], i, cfg["frames"], cfg["N"], info, cfg["M"], snr)
+             for i, snr in enumerate(cfg["snrs"])]
+    sym = torch.from_numpy(np.concatenate([p["symbols"] for p in parts])).cuda()
+    cwt = np.concatenate([p["codewords_packed"] for p in parts])
+    return g.Code(H, cfg["N"], cfg["K"]), sym, cwt
+
+
+def _timed_decode(g, code, p, sym):
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = g.decode_symbols(code, p, sym, stats=True)
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
+
+
+def run_orders(args, cfg, g):
+    """Query counts and BLER of the TEP orders on the same frames (one decode
+    per order and setting, after a warm-up call)."""
+    code, sym, cwt = _c2_like_batch(cfg, g)
+    F = cfg["frames"]
+    variants = [("paper (Def. III.1/III.2)", g.ORDER_QAM_NNE, g.LIK_THRESHOLD),
+                ("paper, literal Def. III.1 edge distance", g.ORDER_QAM_NNE, g.LIK_LITERAL),
+                ("nearer axis first", g.ORDER_QAM_NEARER, g.LIK_THRESHOLD),
+                ("five-point NNE (4 alternatives, no diagonal)", g.ORDER_QAM_NNE5, g.LIK_THRESHOLD)]
+    rows = []
+    for S, cap_of in ((8, lambda o: (5 if o == g.ORDER_QAM_NNE5 else 4) ** 8), (10, lambda o: 1 << 20)):
+        for name, order, lik in variants:
+            p = g.Params.make(order=order, M=cfg["M"], S=S, query_cap=cap_of(order), lik_variant=lik)
+            _timed_decode(g, code, p, sym[:1000])
+            r, secs = _timed_decode(g, code, p, sym)
+            cw = r["cw"].cpu().numpy().view(np.uint32)
+            q = r["queries"].cpu().numpy().view(np.uint32).astype(np.int64)
+            ab = r["abandon"].cpu().numpy()
+            per_snr = []
+            for i, snr in enumerate(cfg["snrs"]):
+                sl = slice(i * F, (i + 1) * F)
+                err = (cw[sl] != cwt[sl]).any(axis=1)
+                dec = ab[sl] == 0
+                per_snr.append({"ebn0_db": snr, "bler": float(err.mean()), "abandon": float((ab[sl] == 1).mean()),
+                                "undetected": float((err & dec).mean()), "mean_queries": float(q[sl].mean()),
+                                "mean_queries_decoded": float(q[sl][dec].mean()) if dec.any() else None,
+                                "median_queries_correct": float(np.median(q[sl][dec & ~err])) if (dec & ~err).any()
+                                else None})
+            rows.append({"order": name, "S": S, "cap": cap_of(order), "seconds": secs,
+                         "frames_per_s": len(q) / secs, "useful_checks_per_s": float(q.sum()) / secs,
+                         "per_snr": per_snr})
+    code.close()
+    return rows
+
+
+def run_membership(args, cfg, g):
+    """Device time of the three membership tests on the same frames."""
+    code, sym, cwt = _c2_like_batch(cfg, g)
+    rows = []
+    ref = None
+    for name, mem in (("split search, syndrome deltas (bit-sliced)", g.MEMBERSHIP_AUTO),
+                      ("per-TEP syndrome deltas", g.MEMBERSHIP_DELTA),
+                      ("per-TEP row parity (Alg. 1 product)", g.MEMBERSHIP_ROW_PARITY)):
+        p = g.Params.make(M=cfg["M"], S=cfg["S"], query_cap=cfg["cap"], membership=mem)
+        _timed_decode(g, code, p, sym[:2000])
+        r, secs = _timed_decode(g, code, p, sym)
+        q = r["queries"].cpu().numpy().view(np.uint32).astype(np.int64)
+        out = (r["cw"].cpu().numpy(), q, r["abandon"].cpu().numpy())
+        same = True if ref is None else all(np.array_equal(a, b) for a, b in zip(out, ref))
+        ref = ref or out
+        kern_ms = float(r["prep_ms"] + r["search_ms"])
+        rows.append({"membership": name, "seconds": secs, "kernel_ms": kern_ms,
+                     "useful_checks_per_s": float(q.sum()) / (kern_ms / 1e3),
+                     "evaluated_checks": int(r["evaluated_checks"]),
+                     "evaluated_checks_per_s": r["evaluated_checks"] / (kern_ms / 1e3),
+                     "results_equal_split_search": bool(same)})
+    code.close()
+    return rows
+
+
 # -------------------------------------------------------------------------
 # GPU arm
 # -------------------------------------------------------------------------
@@ -404,6 +496,19 @@ def main():
                               "data": "synthetic (seeded random polar codewords over AWGN)",
                               "config": {"workload": cfg["desc"], "frames_per_point": cfg["frames"]},
                               "bler": rows}), flush=True)
+        return 0
+    if cfg["kind"] in ("orders", "membership"):
+        clocks = ClockSampler(local)
+        clocks.start()
+        rows = run_orders(args, cfg, g) if cfg["kind"] == "orders" else run_membership(args, cfg, g)
+        clk = clocks.stop()
+        if rank == 0:
+            print(json.dumps({"metric": "TEP order comparison (queries, BLER)" if cfg["kind"] == "orders"
+                              else "membership-test ablation (checks/s)",
+                              "value": rows[0]["useful_checks_per_s"], "unit": "checks/s (first row)",
+                              "n_gpus": world, "steps": 1, "warmup": 1, "higher_is_better": True, "dtype": "u32",
+                              "data": "synthetic (seeded random polar codewords over AWGN)",
+                              "config": {"workload": cfg["desc"]}, "clocks": clk, "rows": rows}), flush=True)
         return 0
     if cfg["kind"] == "serve":
         clocks = ClockSampler(local)

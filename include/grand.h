@@ -67,7 +67,36 @@ typedef enum grand_status {
 typedef enum grand_order {
   GRAND_ORDER_HAMMING = 0, /* bit-level GRAND-AB: ascending Hamming weight, colex (Sec. I) */
   GRAND_ORDER_QAM_NNE = 1, /* symbol-level, likelihood order of Def. III.1/III.2 (Alg. 2) */
+  /* Order variants for comparison with the paper's order:
+   * QAM_NEARER  as QAM_NNE, but the horizontal and vertical alternatives of
+   *             a symbol swap places when its Q distance to the threshold is
+   *             strictly smaller than its I distance (the less reliable axis
+   *             is queried first; the diagonal stays last).
+   * QAM_NNE5    the five-point nearest-neighbour error model the paper
+   *             contrasts with its own (Sec. II, before Cor. III.1): up to
+   *             four alternatives per symbol, the neighbouring level on each
+   *             side of each axis, in the order toward the received value on
+   *             I, toward it on Q, away on I, away on Q; no diagonal. Symbols
+   *             are sorted by the same key; O(5^S') patterns. S <= 10. */
+  GRAND_ORDER_QAM_NEARER = 2,
+  GRAND_ORDER_QAM_NNE5 = 3,
 } grand_order;
+
+/* How a TEP's membership H (y ^ e) = 0 is tested (results do not depend on it).
+ *   AUTO        syndrome deltas (Alg. 2 Step 4: s(y) xor the H columns a TEP
+ *               flips) in the split search of the fused kernels; QAM_NNE5
+ *               runs DELTA.
+ *   DELTA       syndrome deltas, one TEP per lane and step in canonical
+ *               order (no split search); grand_decode_symbols only.
+ *   ROW_PARITY  the candidate word y ^ e multiplied by H row by row, each
+ *               syndrome bit the parity of (row AND word) -- the product of
+ *               Alg. 1 (pMult) evaluated per TEP, stopping at the first odd
+ *               row; one TEP per lane; grand_decode_symbols only. */
+typedef enum grand_membership {
+  GRAND_MEMBERSHIP_AUTO = 0,
+  GRAND_MEMBERSHIP_DELTA = 1,
+  GRAND_MEMBERSHIP_ROW_PARITY = 2,
+} grand_membership;
 
 /* Readings of Def. III.1 for a received value beyond the outermost level. */
 typedef enum grand_lik {
@@ -79,6 +108,7 @@ typedef enum grand_lik {
 #define GRAND_N_MIN 32
 #define GRAND_N_MAX 1024
 #define GRAND_S_MAX 12
+#define GRAND_S_MAX_NNE5 10
 #define GRAND_AB_WEIGHT_MAX 4
 
 /* Decode parameters.
@@ -93,7 +123,8 @@ typedef enum grand_lik {
  *               [1] A-side ranks of the search split (1..6), [2] number of
  *               TEP weights tested by the per-frame preparation (0..3),
  *               [3] register budget of the search kernel as resident CTAs
- *               per SM (4, 6 or 8). Results do not depend on tiles. */
+ *               per SM (4, 6 or 8). Results do not depend on tiles.
+ *   membership  GRAND_MEMBERSHIP_*. */
 typedef struct grand_params {
   int32_t order;
   int32_t M;
@@ -102,6 +133,7 @@ typedef struct grand_params {
   int64_t query_cap;
   int32_t lik_variant;
   int32_t tiles[4];
+  int32_t membership;
 } grand_params;
 
 typedef struct grand_code grand_code;
@@ -181,8 +213,10 @@ int grand_code_info(const grand_code* code, int* N, int* K);
  *             the received value to its nearest decision threshold (the
  *             fixed-point likelihood; small = unreliable).
  *   nmask     uint8 [n_frames][L]: bit0 h exists, bit1 v exists, bit2 diag
- *             exists, bit3 I direction is +1, bit4 Q direction is +1, bit7
- *             a coordinate was not finite (read as 0).
+ *             exists, bit3 I direction is +1, bit4 Q direction is +1, bit5
+ *             the Q distance is strictly smaller than the I distance (the
+ *             vertical alternative is the nearer one), bit7 a coordinate was
+ *             not finite (read as 0).
  *   rel       float [n_frames][L] = sqrt(d1^2 + d2^2), Def. III.1, FP32.
  *   y         uint32 [n_frames][N/32] packed hard word: symbol i carries bits
  *             [2m i, 2m i + 2m), I Gray label then Q Gray label, MSB first;
@@ -193,8 +227,9 @@ int grand_demod(const void* symbols, int64_t n_frames, int L, int M, float N0, i
                 void* stream);
 
 /* Decode demodulated frames (Alg. 2 Steps 2-5 and Return).
- *   For GRAND_ORDER_QAM_NNE: hard_idx, key, nmask, y as written by
- *   grand_demod with the same M and lik_variant (device).
+ *   For GRAND_ORDER_QAM_NNE / QAM_NEARER: hard_idx, key, nmask, y as written
+ *   by grand_demod with the same M and lik_variant (device). QAM_NNE5 and a
+ *   membership other than AUTO: GRAND_E_UNSUPPORTED (use grand_decode_symbols).
  *   For GRAND_ORDER_HAMMING: only y is read (others may be NULL).
  *   Outputs (device): cw uint32 [n_frames][N/32] decoded word (the hard word
  *   when abandoned); queries uint32 [n_frames]; abandon uint8 [n_frames]:
@@ -209,7 +244,11 @@ int grand_decode_batch(const grand_code* code, const grand_params* params, const
 
 /* Demodulate and decode in one pass: the per-symbol arrays are not written
  * to memory. symbols as for grand_demod (M = params->M); outputs as for
- * grand_decode_batch. */
+ * grand_decode_batch. Every QAM order and membership test is accepted here;
+ * QAM_NNE5 and membership DELTA / ROW_PARITY run the per-TEP kernel (one
+ * warp per frame: demodulation, selection and the canonical walk), whose
+ * stats report prep_ms = 0, the walk in search_ms, hard_frames = frames
+ * whose first query failed and search_useful = their queries. */
 int grand_decode_symbols(const grand_code* code, const grand_params* params, const void* symbols,
                          int64_t n_frames, float N0, uint32_t* cw, uint32_t* queries, uint8_t* abandon,
                          grand_stats* stats, void* stream);
@@ -222,8 +261,9 @@ int grand_decode_symbols(const grand_code* code, const grand_params* params, con
  *              desc[f].sym_offset.
  *   cw         device uint32, flat, n_cw_words entries; frame f starts at
  *              desc[f].cw_offset.
- *   params     order must be GRAND_ORDER_QAM_NNE; params->M is ignored (each
- *              frame has its own); S' = min(params->S, L) per frame.
+ *   params     order GRAND_ORDER_QAM_NNE or QAM_NEARER with membership
+ *              AUTO; params->M is ignored (each frame has its own);
+ *              S' = min(params->S, L) per frame.
  * Errors as for grand_decode_batch. A descriptor with an unknown code, an
  * unsupported M or a range outside the arrays is not decoded: its abandon
  * flag is 3 and its queries 0 (checked on the device). */
@@ -290,7 +330,8 @@ int grand_autotune_mixed(const grand_code* const* codes, int n_codes, grand_para
  * for the same frame, whatever the batch it landed in.
  *   codes             host array of n_codes code pointers (borrowed; they must
  *                     outlive the server).
- *   params            order GRAND_ORDER_QAM_NNE; M comes with each request.
+ *   params            order GRAND_ORDER_QAM_NNE or QAM_NEARER, membership
+ *                     AUTO; M comes with each request.
  *   max_slots         admitted requests resident at once.
  *   max_device_bytes  memory budget of the resident request state; the
  *                     symbol ring holds max_device_bytes / 8 symbols.
@@ -371,7 +412,7 @@ int grand_server_destroy(grand_server* srv);
  *     device memory, present on every GPU that loads the library until the
  *     process exits. It holds at most GRAND_NOALLOC_MAX_FRAMES frames: larger
  *     n_frames is rejected with GRAND_E_UNSUPPORTED before any GPU work.
- *   - Only GRAND_ORDER_QAM_NNE; no statistics output.
+ *   - Only GRAND_ORDER_QAM_NNE with membership AUTO; no statistics output.
  *   - The first call on a device looks up the array's device address (a
  *     one-time set-up); make that first call before any stream capture.
  *   - Every call on a device shares the one array and resets its counters

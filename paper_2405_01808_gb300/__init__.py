@@ -18,11 +18,17 @@ from . import _build
 __all__ = [
     "GrandError", "lib", "build", "polar_H", "Code", "Params", "demod", "decode_batch",
     "decode_symbols", "decode_mixed", "frame_desc", "ORDER_HAMMING", "ORDER_QAM_NNE",
+    "ORDER_QAM_NEARER", "ORDER_QAM_NNE5", "MEMBERSHIP_AUTO", "MEMBERSHIP_DELTA", "MEMBERSHIP_ROW_PARITY",
     "LIK_THRESHOLD", "LIK_LITERAL",
 ]
 
 ORDER_HAMMING = 0
 ORDER_QAM_NNE = 1
+ORDER_QAM_NEARER = 2
+ORDER_QAM_NNE5 = 3
+MEMBERSHIP_AUTO = 0
+MEMBERSHIP_DELTA = 1
+MEMBERSHIP_ROW_PARITY = 2
 LIK_THRESHOLD = 0
 LIK_LITERAL = 1
 
@@ -41,13 +47,14 @@ class Params(ctypes.Structure):
     _fields_ = [
         ("order", ctypes.c_int32), ("M", ctypes.c_int32), ("S", ctypes.c_int32),
         ("max_weight", ctypes.c_int32), ("query_cap", ctypes.c_int64), ("lik_variant", ctypes.c_int32),
-        ("tiles", ctypes.c_int32 * 4),
+        ("tiles", ctypes.c_int32 * 4), ("membership", ctypes.c_int32),
     ]
 
     @classmethod
     def make(cls, order=ORDER_QAM_NNE, M=16, S=10, max_weight=3, query_cap=1 << 20, lik_variant=LIK_THRESHOLD,
-             tiles=(0, 0, 0, 0)):
+             tiles=(0, 0, 0, 0), membership=MEMBERSHIP_AUTO):
         p = cls()
+        p.membership = int(membership)
         p.order, p.M, p.S, p.max_weight = int(order), int(M), int(S), int(max_weight)
         p.query_cap, p.lik_variant = int(query_cap), int(lik_variant)
         for i, t in enumerate(tiles):

@@ -93,12 +93,15 @@ extern "C" int grand_code_create(const uint32_t* H, int N, int K, grand_code** o
   // column-packed copy: word w of column j holds rows 32w .. 32w+31; then the
   // per-column projections hf[j] (a fixed pseudo-random 32-bit word per row,
   // from the splitmix64 finaliser of the row index)
-  // layout of the device copy: hcol [N*W], hf [N], prow [R], frozen [R] (u16, packed 2 per word)
-  const size_t words = (size_t)N * W + N + R + (R + 1) / 2;
+  // layout of the device copy: hcol [N*W], hf [N], prow [R], frozen [R] (u16, packed 2 per word),
+  // hrow [R * N/32] (the rows as given)
+  const size_t words = (size_t)N * W + N + R + (R + 1) / 2 + (size_t)R * (N / 32);
   std::vector<uint32_t> hcol(words, 0);
   uint32_t* hf = hcol.data() + (size_t)N * W;
   uint32_t* prow = hf + N;
   uint16_t* frozen = reinterpret_cast<uint16_t*>(prow + R);
+  uint32_t* hrow = prow + R + (R + 1) / 2;
+  memcpy(hrow, H, sizeof(uint32_t) * (size_t)R * (N / 32));
   bool polar = true;
   for (int r = 0; r < R; ++r) {
     uint64_t z = 0x9E3779B97F4A7C15ull * (uint64_t)(r + 1);
@@ -142,6 +145,7 @@ extern "C" int grand_code_create(const uint32_t* H, int N, int K, grand_code** o
   c->dev.hf = c->d_hcol + (size_t)N * W;
   c->dev.prow = c->dev.hf + N;
   c->dev.frozen = reinterpret_cast<const uint16_t*>(c->dev.prow + R);
+  c->dev.hrow = c->dev.prow + R + (R + 1) / 2;
   c->dev.N = N; c->dev.K = K; c->dev.R = R; c->dev.W = W;
   c->dev.polar = polar ? 1 : 0;
   if (cudaMemcpy(c->d_hcol, hcol.data(), hcol.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "device_common.cuh"
+#include "host_util.cuh"
 
 namespace grand {
 
@@ -33,10 +34,6 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 // ---------------------------------------------------------------------------
 // Launch-wide parameters
 // ---------------------------------------------------------------------------
-struct QamConst {
-  float q[7];      // 256/d rounded to float, index m = log2(M)/2 (M = 4 .. 4096)
-  float inv_d[7];  // 1/d rounded to float
-};
 
 struct PrepArgs {
   // fused path: received symbols; else the demodulated arrays
@@ -54,6 +51,7 @@ struct PrepArgs {
   int M;                         // uniform batch
   int S;
   int lik;
+  int nearer;                    // GRAND_ORDER_QAM_NEARER: swap h / v where d_Q < d_I
   int w0;
   int Lmax;
   int Wmax;
@@ -329,10 +327,16 @@ __global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
       const uint32_t info = sm.info[i];
       const int lI = info & 0xFF, lQ = (info >> 8) & 0xFF;
       const uint32_t nm = (info >> 16) & 0xFF;
-      const bool exI = nm & 1u, exQ = nm & 2u;
+      bool exI = nm & 1u, exQ = nm & 2u;
       const int dI = (nm & 8u) ? 1 : -1, dQ = (nm & 16u) ? 1 : -1;
-      const uint16_t pI = exI ? flip_pos_I(i, m, lI, dI, N) : kNoPos;
-      const uint16_t pQ = exQ ? flip_pos_Q(i, m, lQ, dQ, N) : kNoPos;
+      uint16_t pI = exI ? flip_pos_I(i, m, lI, dI, N) : kNoPos;
+      uint16_t pQ = exQ ? flip_pos_Q(i, m, lQ, dQ, N) : kNoPos;
+      if (a.nearer && (nm & 32u)) {
+        // nearer axis first: the first single-axis slot takes the vertical
+        // alternative (every later stage reads slots, not axes)
+        const uint16_t tp = pI; pI = pQ; pQ = tp;
+        const bool te = exI; exI = exQ; exQ = te;
+      }
       sm.pos[2 * lane] = pI;
       sm.pos[2 * lane + 1] = pQ;
       sm.ex[lane] = (uint8_t)((exI ? 1 : 0) | (exQ ? 2 : 0) | (exI && exQ ? 4 : 0));
@@ -862,7 +866,7 @@ constexpr int kWarpSideMax = 5;
 constexpr int kWarpTab = 1 << (2 * kWarpSideMax);   // 1024 entries per side
 constexpr int kPlanes = 20;                          // projection bits compared per TEP
 constexpr int kGroups = kWarpTab / 32;               // A groups of 32 entries
-constexpr int kGroupUnroll = 4;                      // groups per candidate check
+constexpr int kGroupUnroll = 8;                      // groups per candidate check
 constexpr int kPlanesL1 = 16;                        // first-level planes (the rest only on a match)
 
 struct WarpSlice {
@@ -1461,17 +1465,6 @@ __global__ void __launch_bounds__(256) k_demod_bpsk(const float* r, int64_t n_wo
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-static int m_of(int M) {
-  switch (M) {
-    case 4: return 1;
-    case 16: return 2;
-    case 64: return 3;
-    case 256: return 4;
-    case 1024: return 5;
-    case 4096: return 6;
-    default: return 0;
-  }
-}
 
 typedef void (*PrepKernel)(PrepArgs);
 static PrepKernel prep_kernel_for(int Wmax) {
@@ -1482,45 +1475,8 @@ static PrepKernel prep_kernel_for(int Wmax) {
   return k_prep<16>;
 }
 
-static QamConst make_qam_const() {
-  QamConst c{};
-  for (int m = 1; m <= 6; ++m) {
-    const int M = 1 << (2 * m);
-    const double d = sqrt(3.0 * m / (double)(M - 1));
-    c.q[m] = (float)(256.0 / d);
-    c.inv_d[m] = (float)(1.0 / d);
-  }
-  return c;
-}
 
-// Keep the scratch of repeated calls cached: the default stream-ordered pool
-// of the device otherwise returns its memory to the system at every
-// synchronisation and the next call maps it again. Once per device.
-static void keep_pool_cached() {
-  static std::mutex mu;
-  static bool done[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
-  std::lock_guard<std::mutex> lock(mu);
-  if (done[dev]) return;
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-    uint64_t keep = UINT64_MAX;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-  }
-  done[dev] = true;
-}
 
-static int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
 
 // Persistent launch of the search kernel: one wave of CTAs (as many as fit
 // on every SM) pulling frames from the work queue. variant: register budget
@@ -1587,6 +1543,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
   do {
     if (cudaMemsetAsync(scr, 0, sizeof(Scratch), st) != cudaSuccess) { rc = GRAND_E_CUDA; break; }
     PrepArgs a = proto;
+    a.nearer = p->order == GRAND_ORDER_QAM_NEARER ? 1 : 0;
     a.recs = recs;
     a.scr = scr;
     a.Lmax = Lmax;
@@ -1665,9 +1622,10 @@ static int check_params(const grand_params* p) {
   if (!p) return GRAND_E_INVALID;
   if (p->query_cap < 1) return GRAND_E_INVALID;
   if (p->lik_variant != GRAND_LIK_THRESHOLD && p->lik_variant != GRAND_LIK_LITERAL) return GRAND_E_INVALID;
-  if (p->order == GRAND_ORDER_QAM_NNE) {
+  if (p->membership < GRAND_MEMBERSHIP_AUTO || p->membership > GRAND_MEMBERSHIP_ROW_PARITY) return GRAND_E_INVALID;
+  if (p->order == GRAND_ORDER_QAM_NNE || p->order == GRAND_ORDER_QAM_NEARER || p->order == GRAND_ORDER_QAM_NNE5) {
     if (p->S < 0) return GRAND_E_INVALID;
-    if (p->S > kSMax) return GRAND_E_UNSUPPORTED;
+    if (p->S > (p->order == GRAND_ORDER_QAM_NNE5 ? GRAND_S_MAX_NNE5 : kSMax)) return GRAND_E_UNSUPPORTED;
   } else if (p->order == GRAND_ORDER_HAMMING) {
     if (p->max_weight < 0) return GRAND_E_INVALID;
     if (p->max_weight > GRAND_AB_WEIGHT_MAX) return GRAND_E_UNSUPPORTED;
@@ -1789,6 +1747,7 @@ extern "C" int grand_decode_batch(const grand_code* c, const grand_params* p, co
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if (p->order == GRAND_ORDER_HAMMING) return run_ab(c, p, nullptr, y, nmask, n_frames, cw, queries, abandon, stats, st);
+  if (p->order == GRAND_ORDER_QAM_NNE5 || p->membership != GRAND_MEMBERSHIP_AUTO) return GRAND_E_UNSUPPORTED;
   const int m = m_of(p->M);
   if (!m || (n_frames > 0 && (!hard_idx || !key || !nmask))) return GRAND_E_INVALID;
   if (n_frames > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
@@ -1827,6 +1786,8 @@ extern "C" int grand_decode_symbols(const grand_code* c, const grand_params* p, 
   const int m = m_of(p->M);
   if (!m) return GRAND_E_INVALID;
   if (n_frames > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
+  if (p->order == GRAND_ORDER_QAM_NNE5 || p->membership != GRAND_MEMBERSHIP_AUTO)
+    return run_per_tep(c, p, symbols, n_frames, cw, queries, abandon, stats, st);
   const int L = (c->N + 2 * m - 1) / (2 * m);
   PrepArgs a{};
   a.symbols = (const float2*)symbols;
@@ -1870,7 +1831,9 @@ static int check_mixed_args(const grand_code* const* codes, int n_codes, const g
   if (!(N0 > 0.0f) || !isfinite(N0)) return GRAND_E_INVALID;
   int rc = check_params(p);
   if (rc) return rc;
-  if (p->order != GRAND_ORDER_QAM_NNE) return GRAND_E_INVALID;
+  if ((p->order != GRAND_ORDER_QAM_NNE && p->order != GRAND_ORDER_QAM_NEARER) ||
+      p->membership != GRAND_MEMBERSHIP_AUTO)
+    return GRAND_E_INVALID;
   if (n_frames > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
   return GRAND_OK;
 }
@@ -2089,7 +2052,7 @@ extern "C" int grand_decode_symbols_noalloc(const grand_code* c, const grand_par
   if (!(N0 > 0.0f) || !isfinite(N0)) return GRAND_E_INVALID;
   int rc = check_params(p);
   if (rc) return rc;
-  if (p->order != GRAND_ORDER_QAM_NNE) return GRAND_E_INVALID;
+  if (p->order != GRAND_ORDER_QAM_NNE || p->membership != GRAND_MEMBERSHIP_AUTO) return GRAND_E_INVALID;
   const int m = m_of(p->M);
   if (!m) return GRAND_E_INVALID;
   if (n_frames > kNoAllocMaxFrames) return GRAND_E_UNSUPPORTED;

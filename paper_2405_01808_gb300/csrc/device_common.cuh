@@ -104,6 +104,7 @@ __device__ __forceinline__ uint32_t make_nmask(const AxisDemod& I, const AxisDem
   if (I.exists && Q.exists) m |= 4u;
   if (I.dir > 0) m |= 8u;
   if (Q.dir > 0) m |= 16u;
+  if (Q.dq < I.dq) m |= 32u;  // the vertical alternative is the nearer one
   if (nonfinite) m |= 128u;
   return m;
 }

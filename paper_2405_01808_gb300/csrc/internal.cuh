@@ -27,11 +27,14 @@ constexpr uint16_t kNoPos = 0xFFFF;  // alternative bit beyond N (padding): no s
 //          so H y is the frozen part of the polar transform y G_N and the
 //          preparation computes it with log2 N butterfly stages instead of
 //          column loads; prow[r] = p_r (the projection word of row r).
+//   hrow[r * (N/32) + w] bit b = H[r][32 w + b]   (row r of H, as given to
+//          grand_code_create): the row-parity membership test.
 struct CodeDev {
   const uint32_t* hcol;
   const uint32_t* hf;
   const uint16_t* frozen;
   const uint32_t* prow;
+  const uint32_t* hrow;
   int32_t N, K, R, W;
   int32_t polar;
 };
@@ -58,6 +61,12 @@ struct Scratch {
   unsigned long long evaluated;     // TEP checks executed
   unsigned long long search_useful; // valid queries answered by the search stage
 };
+
+// Per-TEP decode (five-point NNE order, or a membership test other than the
+// split search): defined in per_tep.cu, called by grand_decode_symbols after
+// its argument checks.
+int run_per_tep(const grand_code* c, const grand_params* p, const void* symbols, int64_t n_frames, uint32_t* cw,
+                uint32_t* queries, uint8_t* abandon, grand_stats* stats, cudaStream_t st);
 
 }  // namespace grand
 
