@@ -77,8 +77,8 @@ SMS, ALU_LANES, MAX_CLOCK_GHZ = 152, 64, 2.07
 ALU_PEAK_TOPS = SMS * ALU_LANES * MAX_CLOCK_GHZ / 1000.0
 # Counters of the search kernel from one ncu capture (profiles/k_search_warp_c2_small.md),
 # valid only while csrc/decode.cu is the captured source (sha256 prefix).
-NCU_SEARCH = {"sha": "11153b3aa3d1fbc6", "dram_bytes_per_hard_frame": 1550592 / 9596,
-              "alu_pipe_active": 0.771, "alu_ops_per_check": 0.98}
+NCU_SEARCH = {"sha": "db4f27971124f605", "dram_bytes_per_hard_frame": 1549056 / 9596,
+              "alu_pipe_active": 0.762, "alu_ops_per_check": 0.87}
 
 
 def make_inputs(cfg, rank, info_by_N):
@@ -698,7 +698,8 @@ def main():
                     "traffic": NCU_SEARCH["dram_bytes_per_hard_frame"] * hard / args.steps if fresh else None,
                     "kernel": kernel, "ops_per_check": alg_words,
                     "ops_per_check_note": "survey model: (N-K)/32 LOP3 per useful check; the kernel compares a "
-                                          "20-bit projection bit-sliced (21 ops per 32 checks) and verifies matches",
+                                          "16-bit projection bit-sliced (16 ops per 32 checks), 4 more bits on a "
+                                          "match, and verifies matches on the full syndrome",
                     "ncu_alu_pipe_active": NCU_SEARCH["alu_pipe_active"] if fresh else None,
                     "ncu_alu_ops_per_evaluated_check": NCU_SEARCH["alu_ops_per_check"] if fresh else None,
                     "peak_source": f"derived: {SMS} SMs x {ALU_LANES} ALU lanes/clk x {MAX_CLOCK_GHZ} GHz"}
