@@ -1007,38 +1007,73 @@ __device__ __forceinline__ void warp_side_entry(const WarpSlice& sl, int r0, int
 // the block of S minus its highest rank j, each entry XORed with one of j's
 // projected deltas (entry c = parent entry c / k_j, alternative c % k_j).
 // Blocks are visited in table order, so parents (one rank lighter) are ready.
+// Lane k first gathers the description of the k-th block (offsets, parent,
+// neighbour mask, the three projected deltas of j); the walk over the blocks
+// then reads it by shuffles instead of chains of shared-memory loads.
 __device__ inline void warp_fill_side(const WarpSlice& sl, int r0, int n, const uint32_t* start, const uint8_t* ord,
                                       const uint8_t* inv, uint32_t seed, uint32_t* out) {
   const int lane = threadIdx.x & 31;
   const int nsub = 1 << n;
+  uint32_t m_info = 0, m_off = 0, m_d0 = 0, m_d1 = 0, m_d2 = 0;
+  if (lane < nsub) {
+    const int sb = ord[lane];
+    const unsigned base = start[lane], size = start[lane + 1] - base;
+    uint32_t exj = 0;
+    unsigned pbase = 0;
+    if (sb) {
+      const int j = 31 - __clz(sb);
+      pbase = start[inv[sb & ~(1 << j)]];
+      exj = sl.ex[r0 + j] & 7u;
+      const uint32_t* dj = sl.dflt + (r0 + j) * 3;
+      m_d0 = dj[0];
+      m_d1 = dj[1];
+      m_d2 = dj[2];
+      if (exj != 7u && exj) m_d0 = dj[__ffs(exj) - 1];  // the single existing alternative
+    }
+    m_info = size | ((uint32_t)__popc(sb) << 16) | (exj << 24);
+    m_off = base | (pbase << 16);
+  }
   if (lane == 0) out[0] = seed;  // the empty subset is first
   __syncwarp();
   int prev_w = 0;
   for (int k = 1; k < nsub; ++k) {
-    const int sb = ord[k];
-    const int w = __popc(sb);
+    const uint32_t info = __shfl_sync(kFull, m_info, k);
+    const uint32_t off = __shfl_sync(kFull, m_off, k);
+    const uint32_t d0 = __shfl_sync(kFull, m_d0, k);
+    const uint32_t d1 = __shfl_sync(kFull, m_d1, k);
+    const uint32_t d2 = __shfl_sync(kFull, m_d2, k);
+    const int w = (info >> 16) & 0xFF;
     if (w != prev_w) {  // the parents of this weight are complete
       __syncwarp();
       prev_w = w;
     }
-    const unsigned base = start[k], size = start[k + 1] - base;
+    const unsigned size = info & 0xFFFFu;
     if (size == 0) continue;
-    const int j = 31 - __clz(sb);
-    const int pk = inv[sb & ~(1 << j)];
-    const unsigned pbase = start[pk];
-    const uint32_t exj = sl.ex[r0 + j] & 7u;
-    const uint32_t* dj = sl.dflt + (r0 + j) * 3;
-    if (exj == 7u) {
+    const unsigned base = off & 0xFFFFu, pbase = off >> 16;
+    if ((info >> 24) == 7u) {
       for (unsigned c = lane; c < size; c += 32) {
         const unsigned pi = c / 3u, ai = c - 3u * pi;
-        out[base + c] = out[pbase + pi] ^ dj[ai];
+        out[base + c] = out[pbase + pi] ^ (ai == 0 ? d0 : (ai == 1 ? d1 : d2));
       }
     } else {
-      const uint32_t d = dj[__ffs(exj) - 1];
-      for (unsigned c = lane; c < size; c += 32) out[base + c] = out[pbase + c] ^ d;
+      for (unsigned c = lane; c < size; c += 32) out[base + c] = out[pbase + c] ^ d0;
     }
   }
   __syncwarp();
+}
+
+// 32 x 32 bit transpose across the warp: on return lane b holds the word whose
+// bit i is bit b of lane i's input (five butterfly exchange stages).
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const uint32_t m = s == 16 ? 0x0000FFFFu : (s == 8 ? 0x00FF00FFu : (s == 4 ? 0x0F0F0F0Fu : (s == 2 ? 0x33333333u
+                                                                                                      : 0x55555555u)));
+    const uint32_t y = __shfl_xor_sync(kFull, x, s);
+    x = (lane & s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y << s) & ~m));
+  }
+  return x;
 }
 
 // weight of entry e: the number of weights whose cumulative count is <= e
@@ -1141,12 +1176,7 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
       if (g < nG) {
         const unsigned e = 32u * g + lane;
         const uint32_t q = e < nA ? sl.Bz[e] : kPadA;
-        uint32_t mine = 0;
-#pragma unroll
-        for (int b = 0; b < kPlanes; ++b) {
-          const uint32_t pb = __ballot_sync(kFull, (q >> b) & 1u);
-          if (lane == b) mine = pb;
-        }
+        const uint32_t mine = warp_transpose32(q);  // lane b: bit-plane b of the group
         if (lane < kPlanes) sl.planes[g * kPlanes + lane] = mine;
       } else if (lane < kPlanes) {
         sl.planes[g * kPlanes + lane] = 0u;
