@@ -21,6 +21,7 @@ public call with pinned host buffers (copies in the timed region).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -275,12 +276,16 @@ def run_serving(args, cfg, g, inputs):
         while len(srv.poll(1 << 16)):
             pass
         gaps = g_rng.exponential(1.0 / rate, size=F)
-        t0 = g.clock_ns() + 2_000_000
-        arrival = t0 + np.cumsum(gaps * 1e9).astype(np.int64)
+        offsets = np.cumsum(gaps * 1e9).astype(np.int64)
+        # the first arrival lies 50 ms ahead: filling the arrival times of the
+        # request table takes a few ms and must not start the stream late
+        t0 = g.clock_ns() + 50_000_000
+        arrival = t0 + offsets
         reqs["arrival_ns"] = arrival
         i = 0
         got = []
         t_start = time.perf_counter()
+        gc.disable()  # the driver loop stands in for a native client: no collector pauses inside it
         while i < F:
             now = g.clock_ns()
             j = int(np.searchsorted(arrival, now, side="right"))
@@ -289,6 +294,7 @@ def run_serving(args, cfg, g, inputs):
             got.append(srv.poll(1 << 16))
             if time.perf_counter() - t_start > 120:
                 break
+        gc.enable()
         srv.drain(120.0)
         while True:
             tail = srv.poll(1 << 16)

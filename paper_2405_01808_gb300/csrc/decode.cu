@@ -1892,6 +1892,13 @@ static int mixed_impl(const CodeDev* d_table, int n_codes, int Lmax, int Wmax, c
   return run_qam(d_table, n_codes, Lmax, Wmax, p, a, n_frames, stats, st);
 }
 
+int decode_mixed_resident(const CodeDev* d_table, int n_codes, int Lmax, int Wmax, const grand_params* p,
+                          const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
+                          uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon, cudaStream_t st) {
+  return mixed_impl(d_table, n_codes, Lmax, Wmax, p, desc, n_frames, symbols, n_symbols, cw, n_cw_words, queries,
+                    abandon, nullptr, st);
+}
+
 }  // namespace grand
 
 extern "C" int grand_decode_mixed(const grand_code* const* codes, int n_codes, const grand_params* p,

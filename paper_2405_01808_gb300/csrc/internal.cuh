@@ -68,6 +68,13 @@ struct Scratch {
 int run_per_tep(const grand_code* c, const grand_params* p, const void* symbols, int64_t n_frames, uint32_t* cw,
                 uint32_t* queries, uint8_t* abandon, grand_stats* stats, cudaStream_t st);
 
+// grand_decode_mixed on a code table already resident on the device (the
+// serving loop keeps one for its lifetime). The caller has validated params
+// (QAM order, membership AUTO); Lmax / Wmax bound L and W over the table.
+int decode_mixed_resident(const CodeDev* d_table, int n_codes, int Lmax, int Wmax, const grand_params* p,
+                          const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
+                          uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon, cudaStream_t st);
+
 }  // namespace grand
 
 // Opaque code object of the ABI.

@@ -4,13 +4,19 @@
 // Admission: a request is admitted when a slot is free and its device bytes
 // (received symbols, hand-off record, outputs) fit the memory budget; its
 // symbols go into a pinned host ring whose device mirror keeps every admitted
-// request's received word resident until it completes. A worker thread
-// launches the admitted requests as one uneven batch (grand_decode_mixed) on
-// the first idle stream as soon as one is idle, so batches that arrive while
-// others run overlap on the device. Completed batches are harvested by event
-// query; results carry the arrival and completion times (CLOCK_MONOTONIC).
-// Ring space is reclaimed in launch order; results are delivered in
-// completion order. Every wait is bounded.
+// request's received word resident until it completes. Submit reserves ring
+// space under the lock and copies the symbols outside it; a request becomes
+// launchable once its copy is done (launches take the ready prefix, so the
+// ring stays contiguous in launch order).
+//
+// Two threads run the loop. The launcher takes the ready requests as one
+// uneven batch as soon as a stream is idle and issues it (symbols to the
+// device ring, descriptors, the decode on the server's resident code table,
+// results back to pinned buffers, an event). The harvester polls the events
+// of running batches, turns a finished batch into result records outside the
+// lock and hands the stream back. Results carry the arrival and completion
+// times (CLOCK_MONOTONIC). Ring space is reclaimed in launch order; results
+// are delivered in completion order. Every wait is bounded.
 #include <errno.h>
 #include <stdlib.h>
 #include <string.h>
@@ -25,6 +31,7 @@
 #include <thread>
 #include <vector>
 
+#include "host_util.cuh"
 #include "internal.cuh"
 
 namespace {
@@ -38,24 +45,14 @@ int64_t now_ns() {
   return (int64_t)ts.tv_sec * 1000000000ll + ts.tv_nsec;
 }
 
-int m_of(int M) {
-  switch (M) {
-    case 4: return 1;
-    case 16: return 2;
-    case 64: return 3;
-    case 256: return 4;
-    case 1024: return 5;
-    case 4096: return 6;
-    default: return 0;
-  }
-}
-
 struct Req {
   uint64_t tag;
   int64_t arrival_ns;
   int32_t code, M, L, nw;
   int64_t vpos;   // virtual ring position of the first symbol
   int64_t bytes;  // device bytes charged to the budget
+  uint64_t seq;   // admission order
+  bool ready;     // symbols copied into the ring
 };
 
 struct StreamBuf {
@@ -82,12 +79,20 @@ struct Batch {
   int status;
 };
 
+// Completed results waiting for poll, in completion order.
+struct Chunk {
+  std::vector<grand_result> v;
+  size_t off = 0;
+};
+
 }  // namespace
 
 struct grand_server {
   grand_server_cfg cfg;
   std::vector<const grand_code*> codes;
   int device = 0;
+  grand::CodeDev* d_table = nullptr;  // device copy of the codes' views
+  int Lmax = 1, Wmax = 1;
   // ring of received symbols (complex64 as float2), virtual positions
   float2* h_ring = nullptr;
   float2* d_ring = nullptr;
@@ -96,13 +101,16 @@ struct grand_server {
   int64_t vtail = 0;      // oldest live virtual position
   int64_t live_bytes = 0;
   int32_t live_slots = 0;
+  uint64_t next_seq = 0;
+  int running = 0;        // launched batches not yet harvested
   std::vector<StreamBuf> sb;
-  std::deque<Req> pending;
-  std::deque<Batch> inflight;
-  std::deque<grand_result> done;
+  std::deque<Req> pending;     // admitted, not launched (ring order)
+  std::deque<Batch> inflight;  // launch order
+  std::deque<Chunk> done;
   std::mutex mu;
-  std::condition_variable cv;
-  std::thread worker;
+  std::condition_variable cv_launch;   // ready requests, an idle stream, or stop
+  std::condition_variable cv_harvest;  // a launched batch, or stop
+  std::thread launcher, harvester;
   std::atomic<bool> stop{false};
   grand_server_stats st{};
 };
@@ -125,13 +133,13 @@ void free_server(grand_server* s) {
     if (b.stream) cudaStreamDestroy(b.stream);
   }
   for (Batch& b : s->inflight) cudaEventDestroy(b.ev);
+  cudaFree(s->d_table);
   cudaFree(s->d_ring);
   cudaFreeHost(s->h_ring);
   delete s;
 }
 
-// Launch the pending requests (at most max_batch) on stream `si`.
-// Called by the worker without the lock held; `reqs` was taken under it.
+// Issue batch b on stream si (no lock held; b.reqs was taken under it).
 int launch_batch(grand_server* s, int si, Batch& b) {
   StreamBuf& buf = s->sb[si];
   const int n = (int)b.reqs.size();
@@ -158,9 +166,9 @@ int launch_batch(grand_server* s, int si, Batch& b) {
   if (cudaMemcpyAsync(buf.d_desc, buf.h_desc, sizeof(grand_frame_desc) * n, cudaMemcpyHostToDevice, buf.stream) !=
       cudaSuccess)
     return GRAND_E_CUDA;
-  int rc = grand_decode_mixed(s->codes.data(), (int)s->codes.size(), &s->cfg.params, buf.d_desc, n, s->d_ring,
-                              s->ring_cap, s->cfg.N0, buf.d_cw, (int64_t)n * kResultWords, buf.d_q, buf.d_ab, nullptr,
-                              buf.stream);
+  int rc = grand::decode_mixed_resident(s->d_table, (int)s->codes.size(), s->Lmax, s->Wmax, &s->cfg.params,
+                                        buf.d_desc, n, s->d_ring, s->ring_cap, buf.d_cw, (int64_t)n * kResultWords,
+                                        buf.d_q, buf.d_ab, buf.stream);
   if (rc != GRAND_OK) return rc;
   if (cudaMemcpyAsync(buf.h_cw, buf.d_cw, sizeof(uint32_t) * n * kResultWords, cudaMemcpyDeviceToHost, buf.stream) !=
           cudaSuccess ||
@@ -171,101 +179,118 @@ int launch_batch(grand_server* s, int si, Batch& b) {
   return GRAND_OK;
 }
 
-void worker_main(grand_server* s) {
+void launcher_main(grand_server* s) {
   cudaSetDevice(s->device);
-  while (!s->stop.load(std::memory_order_acquire)) {
-    bool progressed = false;
-    // 1. harvest completed batches (any order)
-    std::vector<grand_result> out;
+  for (;;) {
+    Batch b;
+    int si = -1;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      for (Batch& b : s->inflight) {
-        if (b.done) continue;
-        const cudaError_t q = cudaEventQuery(b.ev);
-        if (q == cudaErrorNotReady) continue;
-        b.done = true;
-        b.status = q == cudaSuccess ? b.status : GRAND_E_CUDA;
-        StreamBuf& buf = s->sb[b.stream];
-        const int64_t t = now_ns();
-        for (size_t i = 0; i < b.reqs.size(); ++i) {
-          grand_result r;
-          memset(&r, 0, sizeof r);
-          r.tag = b.reqs[i].tag;
-          r.arrival_ns = b.reqs[i].arrival_ns;
-          r.done_ns = t;
-          if (b.status == GRAND_OK) {
-            r.queries = buf.h_q[i];
-            r.abandon = buf.h_ab[i];
-            memcpy(r.cw, buf.h_cw + i * kResultWords, sizeof(uint32_t) * b.reqs[i].nw);
-          } else {
-            r.abandon = 4;  // the batch failed on the device
-          }
-          s->done.push_back(r);
+      while (!s->stop.load(std::memory_order_acquire)) {
+        if (!s->pending.empty() && s->pending.front().ready) {
+          for (int i = 0; i < (int)s->sb.size(); ++i)
+            if (!s->sb[i].busy) { si = i; break; }
+          if (si >= 0) break;
         }
-        s->st.completed += b.reqs.size();
-        s->st.batch_service_ns += t - b.launch_ns;
-        if (t - b.launch_ns > s->st.max_batch_service_ns) s->st.max_batch_service_ns = t - b.launch_ns;
-        if (b.status != GRAND_OK) s->st.errors += 1;
-        buf.busy = false;
-        progressed = true;
+        s->cv_launch.wait_for(lk, std::chrono::milliseconds(1));  // bounded: re-check
       }
-      // reclaim ring space and budget in launch order
-      while (!s->inflight.empty() && s->inflight.front().done) {
-        Batch& f = s->inflight.front();
-        s->vtail = f.vend;
-        s->live_bytes -= f.bytes;
-        s->live_slots -= (int)f.reqs.size();
-        cudaEventDestroy(f.ev);
-        s->inflight.pop_front();
+      if (si < 0) return;  // stop
+      const int maxb = s->cfg.max_batch;
+      int64_t bytes = 0;
+      while (!s->pending.empty() && s->pending.front().ready && (int)b.reqs.size() < maxb) {
+        bytes += s->pending.front().bytes;
+        b.reqs.push_back(s->pending.front());
+        s->pending.pop_front();
       }
+      b.stream = si;
+      b.vend = b.reqs.back().vpos + b.reqs.back().L;
+      b.bytes = bytes;
+      b.done = false;
+      b.status = GRAND_OK;
+      s->sb[si].busy = true;
+      s->st.batches += 1;
+      s->st.batched_frames += b.reqs.size();
     }
-    (void)out;
-    // 2. launch the pending requests on an idle stream
-    for (;;) {
-      Batch b;
-      int si = -1;
-      {
-        std::unique_lock<std::mutex> lk(s->mu);
-        if (s->pending.empty()) break;
-        for (int i = 0; i < (int)s->sb.size(); ++i)
-          if (!s->sb[i].busy) { si = i; break; }
-        if (si < 0) break;
-        const int maxb = s->cfg.max_batch;
-        int64_t bytes = 0;
-        while (!s->pending.empty() && (int)b.reqs.size() < maxb) {
-          bytes += s->pending.front().bytes;
-          b.reqs.push_back(s->pending.front());
-          s->pending.pop_front();
-        }
-        b.stream = si;
-        b.vend = b.reqs.back().vpos + b.reqs.back().L;
-        b.bytes = bytes;
-        b.done = false;
-        b.status = GRAND_OK;
-        s->sb[si].busy = true;
-        s->st.batches += 1;
-        s->st.batched_frames += b.reqs.size();
-      }
-      cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
-      b.launch_ns = now_ns();
-      b.status = launch_batch(s, si, b);
-      const int64_t issued = now_ns() - b.launch_ns;
-      if (b.status != GRAND_OK) cudaEventRecord(b.ev, s->sb[si].stream);
-      {
-        std::unique_lock<std::mutex> lk(s->mu);
-        s->st.launch_ns += issued;
-        if (issued > s->st.max_launch_ns) s->st.max_launch_ns = issued;
-        s->inflight.push_back(std::move(b));
-        const int64_t inflight = (int64_t)s->inflight.size();
-        if (inflight > s->st.max_inflight_batches) s->st.max_inflight_batches = inflight;
-      }
-      progressed = true;
-    }
-    if (!progressed) {
+    cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
+    b.launch_ns = now_ns();
+    b.status = launch_batch(s, si, b);
+    const int64_t issued = now_ns() - b.launch_ns;
+    if (b.status != GRAND_OK) cudaEventRecord(b.ev, s->sb[si].stream);
+    {
       std::unique_lock<std::mutex> lk(s->mu);
-      // nothing new: wait briefly for a submit, then poll the events again
-      s->cv.wait_for(lk, std::chrono::microseconds(20));
+      s->st.launch_ns += issued;
+      if (issued > s->st.max_launch_ns) s->st.max_launch_ns = issued;
+      s->inflight.push_back(std::move(b));
+      s->running += 1;
+      const int64_t inflight = (int64_t)s->inflight.size();
+      if (inflight > s->st.max_inflight_batches) s->st.max_inflight_batches = inflight;
     }
+    s->cv_harvest.notify_one();
+  }
+}
+
+void harvester_main(grand_server* s) {
+  cudaSetDevice(s->device);
+  std::vector<Batch*> running;
+  for (;;) {
+    running.clear();
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      while (!s->stop.load(std::memory_order_acquire) && s->running == 0)
+        s->cv_harvest.wait_for(lk, std::chrono::milliseconds(1));  // bounded: re-check
+      if (s->stop.load(std::memory_order_acquire)) return;
+      // references into the deque stay valid: only finished batches are popped
+      for (Batch& b : s->inflight)
+        if (!b.done) running.push_back(&b);
+    }
+    bool any = false;
+    for (Batch* b : running) {
+      const cudaError_t q = cudaEventQuery(b->ev);
+      if (q == cudaErrorNotReady) continue;
+      any = true;
+      const int64_t t = now_ns();
+      const int status = q == cudaSuccess ? b->status : GRAND_E_CUDA;
+      const StreamBuf& buf = s->sb[b->stream];
+      Chunk c;
+      c.v.resize(b->reqs.size());
+      for (size_t i = 0; i < b->reqs.size(); ++i) {
+        grand_result& r = c.v[i];
+        memset(&r, 0, sizeof r);
+        r.tag = b->reqs[i].tag;
+        r.arrival_ns = b->reqs[i].arrival_ns;
+        r.done_ns = t;
+        if (status == GRAND_OK) {
+          r.queries = buf.h_q[i];
+          r.abandon = buf.h_ab[i];
+          memcpy(r.cw, buf.h_cw + i * kResultWords, sizeof(uint32_t) * b->reqs[i].nw);
+        } else {
+          r.abandon = 4;  // the batch failed on the device
+        }
+      }
+      {
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->done.push_back(std::move(c));
+        b->done = true;
+        b->status = status;
+        s->running -= 1;
+        s->st.completed += b->reqs.size();
+        s->st.batch_service_ns += t - b->launch_ns;
+        if (t - b->launch_ns > s->st.max_batch_service_ns) s->st.max_batch_service_ns = t - b->launch_ns;
+        if (status != GRAND_OK) s->st.errors += 1;
+        s->sb[b->stream].busy = false;
+        // reclaim ring space and budget in launch order
+        while (!s->inflight.empty() && s->inflight.front().done) {
+          Batch& f = s->inflight.front();
+          s->vtail = f.vend;
+          s->live_bytes -= f.bytes;
+          s->live_slots -= (int)f.reqs.size();
+          cudaEventDestroy(f.ev);
+          s->inflight.pop_front();
+        }
+      }
+      s->cv_launch.notify_one();
+    }
+    if (!any) std::this_thread::sleep_for(std::chrono::microseconds(5));
   }
 }
 
@@ -293,6 +318,23 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
     delete s;
     return GRAND_E_CUDA;
   }
+  {
+    std::vector<grand::CodeDev> table(cfg->n_codes);
+    for (int i = 0; i < cfg->n_codes; ++i) {
+      table[i] = cfg->codes[i]->dev;
+      s->Wmax = std::max(s->Wmax, table[i].W);
+      s->Lmax = std::max(s->Lmax, (table[i].N + 1) / 2);  // QPSK bound
+    }
+    if (cudaMalloc((void**)&s->d_table, sizeof(grand::CodeDev) * cfg->n_codes) != cudaSuccess) {
+      free_server(s);
+      return GRAND_E_NOMEM;
+    }
+    if (cudaMemcpy(s->d_table, table.data(), sizeof(grand::CodeDev) * cfg->n_codes, cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      free_server(s);
+      return GRAND_E_CUDA;
+    }
+  }
   s->ring_cap = cfg->max_device_bytes / 8;
   if (cudaMallocHost((void**)&s->h_ring, sizeof(float2) * s->ring_cap) != cudaSuccess ||
       cudaMalloc((void**)&s->d_ring, sizeof(float2) * s->ring_cap) != cudaSuccess) {
@@ -315,7 +357,19 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
       return GRAND_E_NOMEM;
     }
   }
-  s->worker = std::thread(worker_main, s);
+  // Grow the device's stream-ordered pool to the decode scratch of n_streams
+  // full batches now, so that no batch waits on the pool growing later (the
+  // library keeps freed pool memory cached).
+  {
+    grand::keep_pool_cached();
+    const size_t per_batch = 256 + sizeof(grand::FrameRec) * mb + 4096;
+    void* warm = nullptr;
+    if (cudaMallocAsync(&warm, per_batch * s->sb.size(), s->sb[0].stream) == cudaSuccess)
+      cudaFreeAsync(warm, s->sb[0].stream);
+    cudaStreamSynchronize(s->sb[0].stream);
+  }
+  s->launcher = std::thread(launcher_main, s);
+  s->harvester = std::thread(harvester_main, s);
   *out = s;
   return GRAND_OK;
 }
@@ -327,11 +381,16 @@ extern "C" int grand_server_submit(grand_server* s, const grand_request* reqs, i
   const int64_t t = now_ns();
   int admitted = 0;
   int rc = GRAND_OK;
+  uint64_t seq0 = 0;
+  std::vector<int64_t> at;  // ring slot of each admitted request
+  at.reserve(n);
+  // 1. reserve ring space and budget (under the lock)
   {
     std::unique_lock<std::mutex> lk(s->mu);
+    seq0 = s->next_seq;
     for (int i = 0; i < n; ++i) {
       const grand_request& q = reqs[i];
-      const int m = m_of(q.M);
+      const int m = grand::m_of(q.M);
       if (q.code < 0 || q.code >= (int)s->codes.size() || !m || !q.symbols) {
         rc = GRAND_E_INVALID;
         break;
@@ -353,7 +412,6 @@ extern "C" int grand_server_submit(grand_server* s, const grand_request* reqs, i
         s->st.rejected += n - i;
         break;
       }
-      memcpy(s->h_ring + v % s->ring_cap, q.symbols, sizeof(float2) * L);
       Req r;
       r.tag = q.tag;
       r.arrival_ns = q.arrival_ns ? q.arrival_ns : t;
@@ -363,7 +421,10 @@ extern "C" int grand_server_submit(grand_server* s, const grand_request* reqs, i
       r.nw = N / 32;
       r.vpos = v;
       r.bytes = bytes;
+      r.seq = s->next_seq++;
+      r.ready = false;
       s->pending.push_back(r);
+      at.push_back(v % s->ring_cap);
       s->vhead = v + L;
       s->live_bytes += bytes;
       s->live_slots += 1;
@@ -371,18 +432,53 @@ extern "C" int grand_server_submit(grand_server* s, const grand_request* reqs, i
     }
     s->st.admitted += admitted;
   }
-  s->cv.notify_one();
+  // 2. copy the received symbols into the reserved slots (no lock: the slots
+  //    are not launchable and cannot be reclaimed before they are marked ready)
+  for (int i = 0; i < admitted; ++i) {
+    const grand_request& q = reqs[i];
+    const int m = grand::m_of(q.M);
+    const int L = (s->codes[q.code]->N + 2 * m - 1) / (2 * m);
+    memcpy(s->h_ring + at[i], q.symbols, sizeof(float2) * L);
+  }
+  // 3. mark them launchable
+  if (admitted) {
+    std::unique_lock<std::mutex> lk(s->mu);
+    const uint64_t front = s->pending.front().seq;  // ours are still pending (not ready)
+    for (int i = 0; i < admitted; ++i) s->pending[(size_t)(seq0 + i - front)].ready = true;
+  }
+  s->cv_launch.notify_one();
   *n_admitted = admitted;
   return rc;
 }
 
 extern "C" int grand_server_poll(grand_server* s, grand_result* out, int max, int* n) {
   if (!s || !n || max < 0 || (max > 0 && !out)) return GRAND_E_INVALID;
-  std::unique_lock<std::mutex> lk(s->mu);
+  // whole chunks are moved out under the lock and copied after it
+  std::vector<Chunk> taken;
   int k = 0;
-  while (k < max && !s->done.empty()) {
-    out[k++] = s->done.front();
-    s->done.pop_front();
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (k < max && !s->done.empty()) {
+      Chunk& c = s->done.front();
+      const size_t left = c.v.size() - c.off;
+      if (left <= (size_t)(max - k)) {
+        k += (int)left;
+        taken.push_back(std::move(c));
+        s->done.pop_front();
+      } else {
+        // the last, partial chunk: its prefix goes after the whole chunks
+        memcpy(out + k, c.v.data() + c.off, sizeof(grand_result) * (size_t)(max - k));
+        c.off += (size_t)(max - k);
+        k = max;
+      }
+    }
+  }
+  // the whole chunks, in order, before the partial prefix
+  int pos = 0;
+  for (Chunk& c : taken) {
+    const size_t left = c.v.size() - c.off;
+    memcpy(out + pos, c.v.data() + c.off, sizeof(grand_result) * left);
+    pos += (int)left;
   }
   *n = k;
   return GRAND_OK;
@@ -416,8 +512,13 @@ extern "C" int grand_server_destroy(grand_server* s) {
   if (!s) return GRAND_OK;
   grand_server_drain(s, 10ll * 1000000000ll);  // bounded: 10 s
   s->stop.store(true, std::memory_order_release);
-  s->cv.notify_all();
-  if (s->worker.joinable()) s->worker.join();
+  {
+    std::unique_lock<std::mutex> lk(s->mu);  // no waiter can miss the flag
+  }
+  s->cv_launch.notify_all();
+  s->cv_harvest.notify_all();
+  if (s->launcher.joinable()) s->launcher.join();
+  if (s->harvester.joinable()) s->harvester.join();
   free_server(s);
   return GRAND_OK;
 }
