@@ -26,10 +26,11 @@ std::vector<Candidate> candidates(int S) {
     for (int w0 : {1, 2, 3})
       for (int regs : {4, 6, 8}) out.push_back({{0, 0, w0, regs}});
   } else {
-    // CTA-per-frame search: warps per CTA x prep weights x register budget
-    for (int warps : {4, 8})
+    // warp-per-frame search with 6-rank sides: warps per CTA x prep weights x
+    // register budget
+    for (int warps : {1, 2, 4})
       for (int w0 : {2, 3})
-        for (int regs : {4, 8}) out.push_back({{warps, 0, w0, regs}});
+        for (int regs : {4, 6}) out.push_back({{warps, 0, w0, regs}});
   }
   return out;
 }

@@ -73,7 +73,8 @@ struct SearchArgs {
   int tabA, tabB;  // table capacities
   int max_tiles;
   int Wmax;
-  int warp_kernel;  // 1: warp-per-frame kernel (S' <= 10, automatic split)
+  int warp_kernel;  // 1 / 2: warp-per-frame kernel with 5- / 6-rank sides (automatic split); 0: CTA kernel
+  int warps;        // warps per CTA of the 6-rank warp kernel (0: 2)
   uint32_t* cw;
   uint32_t* queries;
   uint8_t* abandon;
@@ -843,8 +844,8 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_search(SearchArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Warp-per-frame, bit-sliced search for S' <= 10 (at most 4^5 = 1024 entries
-// per side).
+// Warp-per-frame, bit-sliced search: sides of at most kSide ranks, 4^kSide
+// table entries per side (kSide = 5: S' <= 10; kSide = 6: S' <= 12).
 //
 // Every warp owns one frame at a time; its tables live in the warp's own slice
 // of shared memory and the whole set-up runs on warp shuffles, so no
@@ -862,55 +863,67 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_search(SearchArgs a) {
 // the candidate fold). Candidates (false rate 2^-kPlanes) are verified on every
 // syndrome word.
 // ---------------------------------------------------------------------------
-constexpr int kWarpSideMax = 5;
-constexpr int kWarpTab = 1 << (2 * kWarpSideMax);   // 1024 entries per side
+constexpr int kWarpSideMax = 5;                      // the small-table variant (S' <= 10)
 constexpr int kPlanes = 20;                          // projection bits compared per TEP
-constexpr int kGroups = kWarpTab / 32;               // A groups of 32 entries
 constexpr int kGroupUnroll = 8;                      // groups per candidate check
 constexpr int kPlanesL1 = 16;                        // first-level planes (the rest only on a match)
 
-struct WarpSlice {
-  uint32_t* planes;  // [kGroups][kPlanes] bit-planes of the A side
-  uint32_t* Bz;      // [kWarpTab] projection of D_B, weight-sorted
-  uint32_t* delta;   // [10][3][Wmax] full syndrome deltas
-  uint32_t* dflt;    // [10][3] projections of the deltas
-  uint32_t* E;       // [kEStride^2]
-  uint32_t* s0;      // [Wmax]
-  uint32_t* startA;  // [33] first entry of the k-th subset of A in table order
-  uint32_t* startB;  // [33]
-  uint32_t* cumA;    // [8] A entries of weight <= v
-  uint32_t* cumB;    // [8]
-  uint8_t* ordA;     // [32] subset at table position k
-  uint8_t* ordB;     // [32]
-  uint8_t* invA;     // [32] table position of subset sb
-  uint8_t* invB;     // [32]
-  uint8_t* ex;       // [16]
-  uint16_t* pos;     // [10][2]
+// Table sizes of one side for the kSide variant.
+template <int kSide>
+struct WarpDims {
+  static constexpr int kTab = 1 << (2 * kSide);  // entries per side
+  static constexpr int kGroups = kTab / 32;      // A groups of 32 entries
+  static constexpr int kSub = 1 << kSide;        // rank subsets per side
+  static constexpr int kRanks = 2 * kSide;       // S' bound
 };
 
+struct WarpSlice {
+  uint32_t* planes;  // [kGroups][kPlanes] bit-planes of the A side
+  uint32_t* Bz;      // [kTab] projection of D_A, then of D_B, weight-sorted (kSide = 5 only)
+  uint32_t* delta;   // [kRanks][3][Wmax] full syndrome deltas
+  uint32_t* dflt;    // [kRanks][3] projections of the deltas
+  uint32_t* E;       // [kEStride^2]
+  uint32_t* s0;      // [Wmax]
+  uint32_t* startA;  // [kSub + 1] first entry of the k-th subset of A in table order
+  uint32_t* startB;  // [kSub + 1]
+  uint32_t* cumA;    // [8] A entries of weight <= v
+  uint32_t* cumB;    // [8]
+  uint8_t* ordA;     // [kSub] subset at table position k
+  uint8_t* ordB;     // [kSub]
+  uint8_t* invA;     // [kSub] table position of subset sb
+  uint8_t* invB;     // [kSub]
+  uint8_t* ex;       // [16]
+  uint16_t* pos;     // [kRanks][2]
+};
+
+template <int kSide>
 __host__ __device__ inline size_t warp_slice_bytes(int Wmax) {
-  size_t words = (size_t)kGroups * kPlanes + kWarpTab + 30 * (size_t)Wmax + 30 + kEStride * kEStride + Wmax + 33 +
-                 33 + 8 + 8 + 8 + 8 + 8 + 8 + 4 + 10;
+  using D = WarpDims<kSide>;
+  const size_t bz = kSide == kWarpSideMax ? D::kTab : 0;
+  size_t words = (size_t)D::kGroups * kPlanes + bz + 3 * D::kRanks * (size_t)Wmax + 3 * D::kRanks +
+                 kEStride * kEStride + Wmax + 2 * (D::kSub + 1) + 8 + 8 + D::kSub + 4 + D::kRanks;
   return (words * 4 + 15) & ~(size_t)15;
 }
 
+template <int kSide>
 __device__ inline WarpSlice warp_slice(char* base, int Wmax) {
+  using D = WarpDims<kSide>;
   WarpSlice w;
   uint32_t* p = reinterpret_cast<uint32_t*>(base);
-  w.planes = p; p += kGroups * kPlanes;
-  w.Bz = p; p += kWarpTab;
-  w.delta = p; p += 30 * Wmax;
-  w.dflt = p; p += 30;
+  w.planes = p; p += D::kGroups * kPlanes;
+  w.Bz = p; p += kSide == kWarpSideMax ? D::kTab : 0;
+  w.delta = p; p += 3 * D::kRanks * Wmax;
+  w.dflt = p; p += 3 * D::kRanks;
   w.E = p; p += kEStride * kEStride;
   w.s0 = p; p += Wmax;
-  w.startA = p; p += 33;
-  w.startB = p; p += 33;
+  w.startA = p; p += D::kSub + 1;
+  w.startB = p; p += D::kSub + 1;
   w.cumA = p; p += 8;
   w.cumB = p; p += 8;
-  w.ordA = reinterpret_cast<uint8_t*>(p); p += 8;
-  w.ordB = reinterpret_cast<uint8_t*>(p); p += 8;
-  w.invA = reinterpret_cast<uint8_t*>(p); p += 8;
-  w.invB = reinterpret_cast<uint8_t*>(p); p += 8;
+  w.ordA = reinterpret_cast<uint8_t*>(p); p += D::kSub / 4;
+  w.ordB = reinterpret_cast<uint8_t*>(p); p += D::kSub / 4;
+  w.invA = reinterpret_cast<uint8_t*>(p); p += D::kSub / 4;
+  w.invB = reinterpret_cast<uint8_t*>(p); p += D::kSub / 4;
   w.ex = reinterpret_cast<uint8_t*>(p); p += 4;
   w.pos = reinterpret_cast<uint16_t*>(p);
   return w;
@@ -923,44 +936,44 @@ __device__ inline WarpSlice warp_slice(char* base, int Wmax) {
 __device__ inline unsigned warp_side_layout(const WarpSlice& sl, int r0, int n, uint32_t* start, uint8_t* ord,
                                             uint8_t* inv, uint32_t* cum) {
   const int lane = threadIdx.x & 31;
-  const int nsub = 1 << n;
-  unsigned size = 0;
-  int posk = 0, w = 0;
-  if (lane < nsub) {
-    size = 1;
-    int colex = 0;
+  const int nsub = 1 << n;  // <= 64: two subsets per lane
+  for (int sb = lane; sb < nsub; sb += 32) {
+    int w = 0, colex = 0;
     for (int j = 0; j < n; ++j)
-      if ((lane >> j) & 1) {
-        size *= (unsigned)__popc(sl.ex[r0 + j] & 7u);
+      if ((sb >> j) & 1) {
         ++w;
         colex += (int)binom16(j, w);
       }
     int before = 0;
     for (int v = 0; v < w; ++v) before += (int)binom16(n, v);
-    posk = before + colex;
-    ord[posk] = (uint8_t)lane;
-    inv[lane] = (uint8_t)posk;
+    const int posk = before + colex;
+    ord[posk] = (uint8_t)sb;
+    inv[sb] = (uint8_t)posk;
   }
   __syncwarp();
-  const int src = lane < nsub ? (int)ord[lane] : 0;
-  const unsigned gathered = __shfl_sync(kFull, size, src);
-  const unsigned size_k = lane < nsub ? gathered : 0u;
-  unsigned incl = size_k;
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned t = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += t;
+  // entries of the subset at table position k, then an exclusive scan
+  unsigned carry = 0;
+  for (int k0 = 0; k0 < nsub; k0 += 32) {
+    const int k = k0 + lane;
+    unsigned size_k = 0;
+    if (k < nsub) {
+      const int sb = ord[k];
+      size_k = 1;
+      for (int j = 0; j < n; ++j)
+        if ((sb >> j) & 1) size_k *= (unsigned)__popc(sl.ex[r0 + j] & 7u);
+    }
+    unsigned incl = size_k;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (k < nsub) start[k] = carry + incl - size_k;
+    carry += __shfl_sync(kFull, incl, 31);
   }
-  if (lane < nsub) start[lane] = incl - size_k;
-  const unsigned total = __shfl_sync(kFull, incl, 31);
+  const unsigned total = carry;
   if (lane == 0) start[nsub] = total;
-  // cumulative count per weight: subsets of weight <= v end at position sum_{u<=v} C(n,u)
-  if (lane <= n) {
-    int endk = 0;
-    for (int u = 0; u <= lane; ++u) endk += (int)binom16(n, u);
-    cum[lane] = 0;  // filled below
-    (void)endk;
-  }
   __syncwarp();
+  // cumulative count per weight: subsets of weight <= v end at position sum_{u<=v} C(n,u)
   if (lane <= n) {
     int endk = 0;
     for (int u = 0; u <= lane; ++u) endk += (int)binom16(n, u);
@@ -1114,11 +1127,13 @@ __device__ __forceinline__ uint32_t group_acc_part(const uint32_t* planes, int g
   return acc;
 }
 
-template <int kMinBlocks>
+template <int kMinBlocks, int kSide>
 __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
+  using D = WarpDims<kSide>;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31;
-  const WarpSlice sl = warp_slice(smem_raw + (threadIdx.x >> 5) * warp_slice_bytes(a.Wmax), a.Wmax);
+  const WarpSlice sl =
+      warp_slice<kSide>(smem_raw + (threadIdx.x >> 5) * warp_slice_bytes<kSide>(a.Wmax), a.Wmax);
   const unsigned n_hard = *(volatile unsigned*)&a.scr->n_hard;
   unsigned long long my_eval = 0, my_useful = 0;
 
@@ -1147,12 +1162,12 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
       const uint32_t v = (alt != 0 && pQ != kNoPos) ? __ldg(code.hcol + (size_t)pQ * W + w) : 0u;
       sl.delta[t] = h ^ v;
     }
-    if (lane < 3 * Sp) {
-      const int r = lane / 3, alt = lane % 3;
+    for (int t = lane; t < 3 * Sp; t += 32) {
+      const int r = t / 3, alt = t % 3;
       const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
       const uint32_t h = (alt != 1 && pI != kNoPos) ? __ldg(code.hf + pI) : 0u;
       const uint32_t v = (alt != 0 && pQ != kNoPos) ? __ldg(code.hf + pQ) : 0u;
-      sl.dflt[lane] = h ^ v;
+      sl.dflt[t] = h ^ v;
     }
     esp_table_warp(sl.ex, Sp, sl.E);
     __syncwarp();
@@ -1169,22 +1184,39 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
     const unsigned nA = warp_side_layout(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, sl.cumA);
     const unsigned nB = warp_side_layout(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, sl.cumB);
     const int nG = (int)((nA + 31) / 32);
-    // A side: scalar projections into the B buffer, then bit-planes (one group
-    // of 32 entries per round of ballots)
-    warp_fill_side(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, f0, sl.Bz);
-    for (int g = 0; g < kGroups; ++g) {
-      if (g < nG) {
-        const unsigned e = 32u * g + lane;
-        const uint32_t q = e < nA ? sl.Bz[e] : kPadA;
-        const uint32_t mine = warp_transpose32(q);  // lane b: bit-plane b of the group
-        if (lane < kPlanes) sl.planes[g * kPlanes + lane] = mine;
-      } else if (lane < kPlanes) {
-        sl.planes[g * kPlanes + lane] = 0u;
+    // the bit-plane pattern of a padding entry (never a candidate in practice;
+    // candidates beyond nA are skipped at verification)
+    const uint32_t pad_plane = (kPadA >> (lane < kPlanes ? lane : 0)) & 1u ? 0xFFFFFFFFu : 0u;
+    if constexpr (kSide == kWarpSideMax) {
+      // A side: scalar projections into the B buffer (doubling), then
+      // bit-planes (one group of 32 entries per warp transpose)
+      warp_fill_side(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, f0, sl.Bz);
+      for (int g = 0; g < D::kGroups; ++g) {
+        if (g < nG) {
+          const unsigned e = 32u * g + lane;
+          const uint32_t q = e < nA ? sl.Bz[e] : kPadA;
+          const uint32_t mine = warp_transpose32(q);  // lane b: bit-plane b of the group
+          if (lane < kPlanes) sl.planes[g * kPlanes + lane] = mine;
+        } else if (lane < kPlanes) {
+          sl.planes[g * kPlanes + lane] = pad_plane;
+        }
       }
+      __syncwarp();
+      // B side, scalar projections
+      warp_fill_side(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, 0u, sl.Bz);
+    } else {
+      // large sides: no scalar tables; each lane derives its A entry from the
+      // table layout, one group of 32 per warp transpose
+      const int nG8 = (nG + kGroupUnroll - 1) / kGroupUnroll * kGroupUnroll;
+      for (int g = 0; g < nG8; ++g) {
+        const unsigned e = 32u * g + lane;
+        uint32_t q = kPadA, acode;
+        if (e < nA) warp_side_entry(sl, 0, nAr, sl.startA, sl.ordA, f0, e, q, acode);
+        const uint32_t mine = warp_transpose32(q);
+        if (lane < kPlanes) sl.planes[g * kPlanes + lane] = g < nG ? mine : pad_plane;
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    // B side, scalar projections
-    warp_fill_side(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, 0u, sl.Bz);
 
     // --- chunks of 32 B entries in weight order, A groups in weight order ----
     uint32_t best_rank = 0xFFFFFFFFu, best_code = 0;
@@ -1196,7 +1228,13 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
       const int budget = min(best_w, w_lim) - wb;  // heaviest A weight still worth testing
       if (budget < 0) break;
       const unsigned col = 32u * ch + lane;
-      const uint32_t z = col < nB ? sl.Bz[col] : kPadB;
+      uint32_t z = kPadB;
+      if constexpr (kSide == kWarpSideMax) {
+        if (col < nB) z = sl.Bz[col];
+      } else {
+        uint32_t bcode0;
+        if (col < nB) warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, z, bcode0);
+      }
       uint32_t m[kPlanes];
 #pragma unroll
       for (int b = 0; b < kPlanes; ++b) m[b] = 0u - ((z >> b) & 1u);
@@ -1522,24 +1560,34 @@ static int launch_search_t(const SearchArgs& s, int threads, size_t smem, cudaSt
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
-template <int B>
-static int launch_search_warp_t(const SearchArgs& s, cudaStream_t st) {
-  const size_t smem = warp_slice_bytes(s.Wmax) * 4;
-  if (cudaFuncSetAttribute(k_search_warp<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+template <int B, int Side>
+static int launch_search_warp_t(const SearchArgs& s, int warps, cudaStream_t st) {
+  constexpr int kSide = Side;
+  const size_t smem = warp_slice_bytes<kSide>(s.Wmax) * warps;
+  auto kern = k_search_warp<B, kSide>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return GRAND_E_CUDA;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_warp<B>, 128, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem);
   if (per_sm < 1) per_sm = 1;
-  k_search_warp<B><<<sm_count() * per_sm, 128, smem, st>>>(s);
+  kern<<<sm_count() * per_sm, 32 * warps, smem, st>>>(s);
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
 static int launch_search(const SearchArgs& s, int threads, size_t smem, int variant, cudaStream_t st) {
-  if (s.warp_kernel) {
+  if (s.warp_kernel == 1) {
     switch (variant) {
-      case 4: return launch_search_warp_t<4>(s, st);
-      case 8: return launch_search_warp_t<8>(s, st);
-      default: return launch_search_warp_t<6>(s, st);
+      case 4: return launch_search_warp_t<4, kWarpSideMax>(s, 4, st);
+      case 8: return launch_search_warp_t<8, kWarpSideMax>(s, 4, st);
+      default: return launch_search_warp_t<6, kWarpSideMax>(s, 4, st);
+    }
+  }
+  if (s.warp_kernel == 2) {  // sides of 6 ranks; warps per CTA from the tiles (default 2)
+    const int warps = s.warps > 0 ? s.warps : 2;
+    switch (variant) {
+      case 6: return launch_search_warp_t<6, kWarpSideMax + 1>(s, warps, st);
+      case 8: return launch_search_warp_t<8, kWarpSideMax + 1>(s, warps, st);
+      default: return launch_search_warp_t<4, kWarpSideMax + 1>(s, warps, st);
     }
   }
   switch (variant) {
@@ -1616,7 +1664,10 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
       }
       s.max_tiles = ((s.tabA + kTileRows - 1) / kTileRows) * ((s.tabB + kTileCols - 1) / kTileCols);
       s.Wmax = Wmax;
-      s.warp_kernel = (Smax <= 2 * kWarpSideMax && s.split <= 0) ? 1 : 0;
+      // warp-per-frame bit-sliced search with 5- or 6-rank sides; an explicit
+      // split selects the CTA kernel
+      s.warp_kernel = s.split > 0 ? 0 : (Smax <= 2 * kWarpSideMax ? 1 : 2);
+      s.warps = p->tiles[0] > 0 ? (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 0;
       s.cw = proto.cw;
       s.queries = proto.queries;
       s.abandon = proto.abandon;

@@ -31,12 +31,23 @@ __device__ __forceinline__ uint32_t binom16(int n, int k) {
   return (k < 0 || n < 0 || k > n) ? 0u : c_binom.v[n][k];
 }
 
-// C(n, k) for n up to 1024, k up to 4 (bit-level orders), 64-bit.
+// C(n, k) for n up to 1024, k up to 4 (bit-level orders), 64-bit: the falling
+// factorial over k!, with constant divisors (no division loop).
 __device__ __forceinline__ uint64_t binom_big(int n, int k) {
   if (k < 0 || n < k) return 0;
-  uint64_t r = 1;
-  for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
-  return r;
+  const uint64_t m = (uint64_t)n;
+  switch (k) {
+    case 0: return 1;
+    case 1: return m;
+    case 2: return m * (m - 1) / 2;
+    case 3: return m * (m - 1) * (m - 2) / 6;
+    case 4: return m * (m - 1) * (m - 2) * (m - 3) / 24;
+    default: {
+      uint64_t r = 1;
+      for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
+      return r;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -202,6 +202,21 @@ def test_tiles_do_not_change_results(g, oracle_lib, tiles):
     assert_same(other, base, f"tiles={tiles}")
 
 
+@pytest.mark.parametrize("tiles", [(4, 6, 2, 0), (1, 0, 3, 6), (4, 0, 2, 8), (8, 5, 2, 0)])
+def test_tiles_do_not_change_results_s12(g, oracle_lib, tiles):
+    """S' = 12: the warp-per-frame search with 6-rank sides (automatic split,
+    any warps per CTA and register budget) and the CTA search (explicit
+    split) decide identically."""
+    N, M, S = 512, 64, 12
+    code, H, info = code_pair(g, oracle_lib, N)
+    d = wl.qam_frames(35, 0, 200, N, info, M, 12.0)
+    base = gpu_decode(g, code, d["symbols"], M, S, 1 << 22)
+    other = gpu_decode(g, code, d["symbols"], M, S, 1 << 22, tiles=tiles)
+    assert_same(other, base, f"tiles={tiles}")
+    want = oracle_lib.decode_qam(H, d["symbols"][:40], M, S, 1 << 22, threads=THREADS)
+    assert_same({k: v[:40] for k, v in base.items()}, want, "S=12 vs oracle")
+
+
 def test_empty_batch(g, oracle_lib):
     import torch
 
