@@ -119,11 +119,14 @@ typedef enum grand_lik {
  *   max_weight  HAMMING order: largest number of flipped bits (0..4).
  *   query_cap   abandonment threshold, >= 1 valid queries.
  *   lik_variant GRAND_LIK_*.
- *   tiles       launch shape, 0 = automatic: [0] warps per search CTA (1..8),
- *               [1] A-side ranks of the search split (1..6), [2] number of
- *               TEP weights tested by the per-frame preparation (0..3),
- *               [3] register budget of the search kernel as resident CTAs
- *               per SM (4, 6 or 8). Results do not depend on tiles.
+ *   tiles       launch shape, 0 = automatic: [0] warps per search CTA (1..8;
+ *               S' = 11, 12 and explicit splits), [1] A-side ranks of the
+ *               search split (1..6; a nonzero value selects the CTA-per-frame
+ *               search, 0 the warp-per-frame search with S'/2 ranks on the A
+ *               side), [2] number of TEP weights tested by the per-frame
+ *               preparation (0..3), [3] register budget of the search kernel
+ *               as resident CTAs per SM (4, 6 or 8). Results do not depend on
+ *               tiles.
  *   membership  GRAND_MEMBERSHIP_*. */
 typedef struct grand_params {
   int32_t order;
@@ -296,7 +299,7 @@ int grand_plan_launch(grand_plan* plan, void* stream);
 int grand_plan_destroy(grand_plan* plan);
 
 /* Launch-shape autotuner. Times every candidate `tiles` setting (preparation
- * weights, search register budget, and for S' > 10 the CTA width) on the
+ * weights, search register budget, and for S' > 10 the warps per CTA) on the
  * given sample with CUDA events (median of 3 runs after one untimed run) and
  * writes the fastest into params->tiles. Results never depend on the tiles.
  *   cache_path  host path of a text cache (NULL: no cache). Lines are
