@@ -80,13 +80,15 @@ __device__ bool row_parity_zero(const uint32_t* __restrict__ hrow, int R, int NW
   return zero;
 }
 
-// Full syndrome of the TEP (P, dig) is zero: s0 xor the flipped H columns.
-__device__ bool delta_zero(const CodeDev& code, const uint32_t* s0, const uint32_t* apos, const int* P,
-                           const int* dig, int w) {
+// Full syndrome of the TEP is zero: s0 xor the flipped H columns. The TEP is
+// held packed: rank of position j in bits [4j, 4j+4) of pp, its alternative
+// index in bits [2j, 2j+2) of dg.
+__device__ bool delta_zero(const CodeDev& code, const uint32_t* s0, const uint32_t* apos, uint64_t pp, uint32_t dg,
+                           int w) {
   for (int k = 0; k < code.W; ++k) {
     uint32_t v = s0[k];
     for (int j = 0; j < w; ++j) {
-      const uint32_t ap = apos[P[j] * kAltMax + dig[j]];
+      const uint32_t ap = apos[(int)((pp >> (4 * j)) & 15u) * kAltMax + ((dg >> (2 * j)) & 3u)];
       const uint32_t p0 = ap & 0xFFFFu, p1 = ap >> 16;
       if (p0 != kNoPos) v ^= __ldg(code.hcol + (size_t)p0 * code.W + k);
       if (p1 != kNoPos) v ^= __ldg(code.hcol + (size_t)p1 * code.W + k);
@@ -242,42 +244,71 @@ __global__ void __launch_bounds__(32 * kTepWarps) k_per_tep(TepArgs a) {
     bool found = false;
     uint32_t hit_rank = 0;
     int hit_lane = -1, w_hit = 0;
-    int P[kSMax], dig[kSMax];
+    // the lane's TEP, packed: pp = ranks (4 bits per position, ascending),
+    // dg = alternative indices (2 bits), km = alternatives - 1 (2 bits)
+    uint64_t pp = 0;
+    uint32_t dg = 0, km = 0;
     for (int w = 0; w <= Sp && !found && cum < cap; ++w) {
       const uint32_t nsets = binom16(Sp, w);
-      for (uint32_t b0 = 0; b0 < nsets && !found && cum < cap; b0 += 32) {
-        const uint32_t si = b0 + lane;
+      for (uint32_t b0 = 0; b0 < nsets && !found && cum < cap;) {
+        // m sets in this batch, P lanes per set: lane l takes part l % P of
+        // set b0 + l / P (parts split the set's alternatives in order, so
+        // lane order stays canonical order)
+        const uint32_t m = min(32u, nsets - b0);
+        const uint32_t P = 32u / m;
+        const uint32_t si = b0 + (uint32_t)lane / P;
+        const uint32_t part = (uint32_t)lane % P;
+        const bool has_set = (uint32_t)lane < m * P;
+        b0 += m;
         uint32_t nalpha = 0;
-        if (si < nsets) {
+        pp = 0;
+        km = 0;
+        if (has_set) {
           // colex unranking: the largest rank first
           uint32_t t = si;
+          nalpha = 1;
           for (int j = w; j >= 1; --j) {
             int p = j - 1;
             while (binom16(p + 1, j) <= t) ++p;
-            P[j - 1] = p;
             t -= binom16(p, j);
+            pp |= (uint64_t)p << (4 * (j - 1));
+            const uint32_t k = kk[p];
+            nalpha *= k;
+            km |= ((k ? k : 1u) - 1u) << (2 * (j - 1));
           }
-          nalpha = 1;
-          for (int j = 0; j < w; ++j) nalpha *= kk[P[j]];
         }
-        uint32_t incl = nalpha;
+        // this lane's part of the set's alternatives: [a0, a0 + n_lane)
+        const uint32_t chunk = (nalpha + P - 1) / P;
+        const uint32_t a0 = part * chunk;
+        const uint32_t n_lane = a0 < nalpha ? min(chunk, nalpha - a0) : 0u;
+        uint32_t incl = n_lane;
         for (int o = 1; o < 32; o <<= 1) {
           const uint32_t v = __shfl_up_sync(kAll, incl, o);
           if (lane >= o) incl += v;
         }
         const uint32_t batch = __shfl_sync(kAll, incl, 31);
-        const uint32_t first = cum + (incl - nalpha) + 1;  // 1-based position of the lane's first TEP
+        const uint32_t first = cum + (incl - n_lane) + 1;  // 1-based position of the lane's first TEP
         uint32_t n_here = 0;
-        if (nalpha && first <= cap) n_here = min(nalpha, cap - first + 1);
-        // every altered rank at its first alternative
+        if (n_lane && first <= cap) n_here = min(n_lane, cap - first + 1);
+        // alternative indices of the part's first TEP: a0 in mixed radix,
+        // the smallest rank the least significant digit
         uint32_t z = f0;
-        for (int j = 0; j < w; ++j) dig[j] = 0;
-        if (n_here)
-          for (int j = 0; j < w; ++j) z ^= aproj[P[j] * kAltMax];
+        dg = 0;
+        if (n_here) {
+          uint32_t rest = a0;
+          for (int j = 0; j < w; ++j) {
+            const uint32_t k = ((km >> (2 * j)) & 3u) + 1u;
+            const uint32_t d = rest % k;
+            rest /= k;
+            dg |= d << (2 * j);
+            z ^= aproj[(int)((pp >> (4 * j)) & 15u) * kAltMax + d];
+          }
+        }
         if (a.rowparity) {
           for (int k = 0; k < NW; ++k) xs[k * 32 + lane] = y[k];
           if (n_here)
-            for (int j = 0; j < w; ++j) flip_lane(xs, lane, apos[P[j] * kAltMax]);
+            for (int j = 0; j < w; ++j)
+              flip_lane(xs, lane, apos[(int)((pp >> (4 * j)) & 15u) * kAltMax + ((dg >> (2 * j)) & 3u)]);
         }
         bool live = n_here > 0, hit = false;
         uint32_t ai = 0;
@@ -286,7 +317,7 @@ __global__ void __launch_bounds__(32 * kTepWarps) k_per_tep(TepArgs a) {
           if (a.rowparity)
             h = row_parity_zero(code.hrow, code.R, NW, xs, lane, live);
           else
-            h = live && z == 0u && delta_zero(code, s0, apos, P, dig, w);
+            h = live && z == 0u && delta_zero(code, s0, apos, pp, dg, w);
           n_eval += live ? 1u : 0u;
           if (h) {
             hit = true;
@@ -298,15 +329,16 @@ __global__ void __launch_bounds__(32 * kTepWarps) k_per_tep(TepArgs a) {
             } else {
               // next alternative tuple: mixed-radix increment, smallest rank fastest
               for (int j = 0; j < w; ++j) {
-                const int r = P[j];
-                const int d = dig[j];
-                const int nd = d + 1 == kk[r] ? 0 : d + 1;
+                const int sh = 2 * j;
+                const int r = (int)((pp >> (4 * j)) & 15u);
+                const uint32_t d = (dg >> sh) & 3u;
+                const uint32_t nd = d == ((km >> sh) & 3u) ? 0u : d + 1u;
                 z ^= aproj[r * kAltMax + d] ^ aproj[r * kAltMax + nd];
                 if (a.rowparity) {
                   flip_lane(xs, lane, apos[r * kAltMax + d]);
                   flip_lane(xs, lane, apos[r * kAltMax + nd]);
                 }
-                dig[j] = nd;
+                dg = (dg & ~(3u << sh)) | (nd << sh);
                 if (nd) break;
               }
             }
@@ -330,7 +362,7 @@ __global__ void __launch_bounds__(32 * kTepWarps) k_per_tep(TepArgs a) {
     // --- Return: x = y xor e of the first hit, else y ---------------------
     if (found && lane == hit_lane) {
       for (int j = 0; j < w_hit; ++j) {
-        const uint32_t ap = apos[P[j] * kAltMax + dig[j]];
+        const uint32_t ap = apos[(int)((pp >> (4 * j)) & 15u) * kAltMax + ((dg >> (2 * j)) & 3u)];
         const uint32_t p0 = ap & 0xFFFFu, p1 = ap >> 16;
         if (p0 != kNoPos) y[p0 >> 5] ^= 1u << (p0 & 31);
         if (p1 != kNoPos) y[p1 >> 5] ^= 1u << (p1 & 31);
