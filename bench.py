@@ -721,6 +721,11 @@ def main():
         cpu = {"value": u / s, "unit": "checks/s", "cores": threads, "kind": "oracle",
                "sample": f"{f} frames ({per} per SNR point) of the same workload", "frames_per_s": f / s,
                "seconds": s}
+        # the same oracle on one core, on a quarter of that sample
+        idx1 = oracle_sample(cfg, inputs, max(1, per // 4))
+        u1, f1, s1 = oracle_run(cfg, inputs, idx1, 1)
+        cpu["single_core"] = {"value": u1 / s1, "unit": "checks/s", "frames": f1, "seconds": s1,
+                              "frames_per_s": f1 / s1}
 
     if rank == 0:
         line = {
