@@ -54,7 +54,7 @@ CONFIGS = {
     "c4": dict(kind="mixed", frames=1000000, S=10, cap=1 << 20,
                desc="uneven mix: N in {32..1024}, M in {4,16,64,256}, Eb/N0 U(4,14) dB, 1000000 frames, "
                     "S=min(L,10), cap 2^20, one call"),
-    "bler": dict(kind="bler", frames=100000, S=8,
+    "bler": dict(kind="bler", frames=1000000, S=8,
                  desc="BLER vs Eb/N0 at S=8 (the paper's cut-off), cap 4^8: N in {32..1024} x M in {4..4096}, "
                       "Eb/N0 grid of 9 points per M, frames per point as given"),
     "orders": dict(kind="orders", N=128, K=64, M=16, snrs=(6.0, 8.0, 10.0), frames=20000,
@@ -330,12 +330,17 @@ BLER_GRID = {4: range(0, 9), 16: range(4, 13), 64: range(8, 17), 256: range(12, 
 
 
 def run_bler(args, cfg, g):
+    """BLER per (N, M, Eb/N0) at S=8: frames generated on the device in chunks
+    (torch transmitter of `workloads`, seeded per point), decoded by the fused
+    call, compared with the sent codewords on the device."""
     import torch
 
     rows = []
     frames = cfg["frames"]
+    chunk = min(frames, 250000)
     dec_s = 0.0
     n_total = 0
+    dev = torch.device("cuda", torch.cuda.current_device())
     for N in wl.MIXED_N:
         H, frozen = g.polar_H(N, N // 2)
         info = np.setdiff1d(np.arange(N), frozen)
@@ -344,20 +349,26 @@ def run_bler(args, cfg, g):
             p = g.Params.make(M=M, S=cfg["S"], query_cap=4 ** cfg["S"])
             curve = []
             for snr in grid:
-                d = wl.qam_frames(CONFIG_IDS["bler"], N * 10007 + M * 31 + snr, frames, N, info, M, float(snr))
-                sym = torch.from_numpy(d["symbols"]).cuda()
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                r = g.decode_symbols(code, p, sym)
-                torch.cuda.synchronize()
-                dec_s += time.perf_counter() - t0
-                n_total += frames
-                cw = r["cw"].cpu().numpy().view(np.uint32)
-                err = (cw != d["codewords_packed"]).any(axis=1)
-                ab = r["abandon"].cpu().numpy()
-                curve.append({"ebn0_db": snr, "bler": float(err.mean()), "abandon": float((ab == 1).mean()),
-                              "undetected": float((err & (ab == 0)).mean()),
-                              "mean_queries": float(r["queries"].to(torch.float64).mean().item())})
+                n_err = n_ab = n_und = 0
+                q_sum = 0.0
+                for c0 in range(0, frames, chunk):
+                    F = min(chunk, frames - c0)
+                    seed = (CONFIG_IDS["bler"] << 40) ^ (N << 28) ^ (M << 12) ^ (int(snr) << 6) ^ (c0 // chunk)
+                    d = wl.torch_qam_frames(seed, F, N, info, M, float(snr), dev)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    r = g.decode_symbols(code, p, d["symbols"])
+                    torch.cuda.synchronize()
+                    dec_s += time.perf_counter() - t0
+                    n_total += F
+                    err = (r["cw"] != d["codewords_packed"].view(r["cw"].dtype)).any(dim=1)
+                    ab = r["abandon"] == 1
+                    n_err += int(err.sum().item())
+                    n_ab += int(ab.sum().item())
+                    n_und += int((err & ~ab).sum().item())
+                    q_sum += float(r["queries"].to(torch.float64).sum().item())
+                curve.append({"ebn0_db": snr, "bler": n_err / frames, "abandon": n_ab / frames,
+                              "undetected": n_und / frames, "mean_queries": q_sum / frames})
             rows.append({"N": N, "M": M, "L": wl.symbols_per_frame(N, M), "curve": curve})
         code.close()
     return rows, n_total / dec_s

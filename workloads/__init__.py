@@ -199,3 +199,67 @@ def mixed_frames(config_id: int, stream: int, n_frames: int, info_by_N: dict,
         "ebn0_db": snr, "codewords_packed": cw_packed, "n_sym": int(sym_off[-1]),
         "n_cw_words": int(cw_off[-1]),
     }
+
+
+# ---------------------------------------------------------------------------
+# The same transmitter and channel in torch, on any device, for sweeps whose
+# frame counts make host generation the bottleneck (10^6 frames per point).
+# It follows the conventions above step by step; the noise comes from a
+# seeded torch generator (not numpy's Philox stream), so its draws differ
+# from qam_frames for the same seed while the distribution is the same.
+# ---------------------------------------------------------------------------
+def torch_encode_modulate(u, M: int):
+    """Information-position bits u (F, N) uint8 tensor -> (tx complex128 (F, L),
+    codeword bits (F, N) uint8): polar transform, padding, Gray QAM map."""
+    import torch
+
+    c = u.clone()
+    F, N = c.shape
+    half = 1
+    while half < N:
+        v = c.view(F, N // (2 * half), 2, half)
+        v[:, :, 0, :] ^= v[:, :, 1, :]
+        half *= 2
+    b = bits_per_symbol(M)
+    m = b // 2
+    L = -(-N // b)
+    bits = torch.zeros((F, L * b), dtype=torch.int32, device=c.device)
+    bits[:, :N] = c.to(torch.int32)
+    bits = bits.view(F, L, b)
+    weights = (1 << torch.arange(m - 1, -1, -1, device=c.device, dtype=torch.int32))
+    gI = (bits[:, :, :m] * weights).sum(dim=2)
+    gQ = (bits[:, :, m:] * weights).sum(dim=2)
+    side = 1 << m
+    levels = torch.arange(side, device=c.device, dtype=torch.int64)
+    level_of = torch.empty(side, dtype=torch.int64, device=c.device)
+    level_of[levels ^ (levels >> 1)] = levels
+    aI = (2 * level_of[gI.long()] - (side - 1)).to(torch.float64)
+    aQ = (2 * level_of[gQ.long()] - (side - 1)).to(torch.float64)
+    d = math.sqrt(3.0 * m / (M - 1))
+    return torch.complex(d * aI, d * aQ), c
+
+
+def torch_pack_bits(bits):
+    """(F, N) 0/1 tensor, N a multiple of 32 -> (F, N/32) int32 words (bit j at word j>>5, bit j&31)."""
+    import torch
+
+    F, N = bits.shape
+    w = bits.to(torch.int64).view(F, N // 32, 32) << torch.arange(32, device=bits.device, dtype=torch.int64)
+    return ((w.sum(dim=2) + (1 << 31)) % (1 << 32) - (1 << 31)).to(torch.int32)  # two's complement
+
+
+def torch_qam_frames(seed: int, n_frames: int, N: int, info_positions, M: int, ebn0_db: float, device):
+    """A uniform batch generated on `device`: received complex64 symbols (F, L)
+    and the sent codewords packed (F, N/32) int32."""
+    import torch
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    info = torch.as_tensor(np.asarray(info_positions, dtype=np.int64), device=device)
+    u = torch.zeros((n_frames, N), dtype=torch.uint8, device=device)
+    u[:, info] = torch.randint(0, 2, (n_frames, info.numel()), generator=gen, device=device, dtype=torch.uint8)
+    tx, c = torch_encode_modulate(u, M)
+    sigma = math.sqrt(float(ebn0_to_n0(ebn0_db)) / 2.0)
+    noise = torch.randn(tx.shape + (2,), generator=gen, device=device, dtype=torch.float64) * sigma
+    rx = torch.complex(tx.real + noise[..., 0], tx.imag + noise[..., 1]).to(torch.complex64)
+    return {"symbols": rx, "codewords_packed": torch_pack_bits(c)}
