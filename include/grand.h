@@ -91,11 +91,21 @@ typedef enum grand_order {
  *   ROW_PARITY  the candidate word y ^ e multiplied by H row by row, each
  *               syndrome bit the parity of (row AND word) -- the product of
  *               Alg. 1 (pMult) evaluated per TEP, stopping at the first odd
- *               row; one TEP per lane; grand_decode_symbols only. */
+ *               row; one TEP per lane; grand_decode_symbols only.
+ *   HASH        a decision procedure rather than a test per TEP: the split's A
+ *               side (s(y) xor the A deltas) goes into a hash table keyed by
+ *               its 32-bit syndrome projection, every B delta is looked up,
+ *               and each pair with equal projections is confirmed on the full
+ *               syndrome and ranked; the smallest rank is the first hit.
+ *               Same outputs as the TEP-by-TEP search (every codeword of the
+ *               space is found), O(|A| + |B|) work per frame; stats count only
+ *               the confirmed pairs as checks. QAM_NNE / QAM_NEARER with
+ *               S' <= 10 (larger S' use AUTO); not for QAM_NNE5. */
 typedef enum grand_membership {
   GRAND_MEMBERSHIP_AUTO = 0,
   GRAND_MEMBERSHIP_DELTA = 1,
   GRAND_MEMBERSHIP_ROW_PARITY = 2,
+  GRAND_MEMBERSHIP_HASH = 3,
 } grand_membership;
 
 /* Readings of Def. III.1 for a received value beyond the outermost level. */
@@ -231,8 +241,9 @@ int grand_demod(const void* symbols, int64_t n_frames, int L, int M, float N0, i
 
 /* Decode demodulated frames (Alg. 2 Steps 2-5 and Return).
  *   For GRAND_ORDER_QAM_NNE / QAM_NEARER: hard_idx, key, nmask, y as written
- *   by grand_demod with the same M and lik_variant (device). QAM_NNE5 and a
- *   membership other than AUTO: GRAND_E_UNSUPPORTED (use grand_decode_symbols).
+ *   by grand_demod with the same M and lik_variant (device). QAM_NNE5 and the
+ *   membership tests DELTA / ROW_PARITY: GRAND_E_UNSUPPORTED (use
+ *   grand_decode_symbols).
  *   For GRAND_ORDER_HAMMING: only y is read (others may be NULL).
  *   Outputs (device): cw uint32 [n_frames][N/32] decoded word (the hard word
  *   when abandoned); queries uint32 [n_frames]; abandon uint8 [n_frames]:
@@ -265,7 +276,7 @@ int grand_decode_symbols(const grand_code* code, const grand_params* params, con
  *   cw         device uint32, flat, n_cw_words entries; frame f starts at
  *              desc[f].cw_offset.
  *   params     order GRAND_ORDER_QAM_NNE or QAM_NEARER with membership
- *              AUTO; params->M is ignored (each frame has its own);
+ *              AUTO or HASH; params->M is ignored (each frame has its own);
  *              S' = min(params->S, L) per frame.
  * Errors as for grand_decode_batch. A descriptor with an unknown code, an
  * unsupported M or a range outside the arrays is not decoded: its abandon
@@ -334,7 +345,7 @@ int grand_autotune_mixed(const grand_code* const* codes, int n_codes, grand_para
  *   codes             host array of n_codes code pointers (borrowed; they must
  *                     outlive the server).
  *   params            order GRAND_ORDER_QAM_NNE or QAM_NEARER, membership
- *                     AUTO; M comes with each request.
+ *                     AUTO or HASH; M comes with each request.
  *   max_slots         admitted requests resident at once.
  *   max_device_bytes  memory budget of the resident request state; the
  *                     symbol ring holds max_device_bytes / 8 symbols.

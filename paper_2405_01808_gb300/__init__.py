@@ -18,7 +18,7 @@ from . import _build
 __all__ = [
     "GrandError", "lib", "build", "polar_H", "Code", "Params", "demod", "decode_batch",
     "decode_symbols", "decode_mixed", "frame_desc", "ORDER_HAMMING", "ORDER_QAM_NNE",
-    "ORDER_QAM_NEARER", "ORDER_QAM_NNE5", "MEMBERSHIP_AUTO", "MEMBERSHIP_DELTA", "MEMBERSHIP_ROW_PARITY",
+    "ORDER_QAM_NEARER", "ORDER_QAM_NNE5", "MEMBERSHIP_AUTO", "MEMBERSHIP_DELTA", "MEMBERSHIP_ROW_PARITY", "MEMBERSHIP_HASH",
     "LIK_THRESHOLD", "LIK_LITERAL",
 ]
 
@@ -29,6 +29,7 @@ ORDER_QAM_NNE5 = 3
 MEMBERSHIP_AUTO = 0
 MEMBERSHIP_DELTA = 1
 MEMBERSHIP_ROW_PARITY = 2
+MEMBERSHIP_HASH = 3
 LIK_THRESHOLD = 0
 LIK_LITERAL = 1
 

@@ -141,7 +141,7 @@ extern "C" int grand_autotune(const grand_code* c, grand_params* p, const void* 
                               const char* cache_path, void* stream, grand_tune_result* res) {
   if (!c || !p || !symbols || n_frames < 1 ||
       (p->order != GRAND_ORDER_QAM_NNE && p->order != GRAND_ORDER_QAM_NEARER) ||
-      p->membership != GRAND_MEMBERSHIP_AUTO)
+      (p->membership != GRAND_MEMBERSHIP_AUTO && p->membership != GRAND_MEMBERSHIP_HASH))
     return GRAND_E_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   const int N = c->N, W = c->N / 32;
@@ -155,8 +155,8 @@ extern "C" int grand_autotune(const grand_code* c, grand_params* p, const void* 
     return GRAND_E_NOMEM;
   }
   char key[384];
-  snprintf(key, sizeof key, "%s|sym|N=%d|K=%d|M=%d|S=%d|cap=%lld|lik=%d|ord=%d", device_name().c_str(), N, c->K,
-           p->M, p->S, (long long)p->query_cap, p->lik_variant, p->order);
+  snprintf(key, sizeof key, "%s|sym|N=%d|K=%d|M=%d|S=%d|cap=%lld|lik=%d|ord=%d|mem=%d", device_name().c_str(), N,
+           c->K, p->M, p->S, (long long)p->query_cap, p->lik_variant, p->order, p->membership);
   const int rc = tune(
       key, p, cache_path, st,
       [&](const grand_params* pp, cudaStream_t s) {
@@ -195,7 +195,8 @@ extern "C" int grand_autotune_mixed(const grand_code* const* codes, int n_codes,
     key += std::to_string(codes[i]->N) + "/" + std::to_string(codes[i]->K) + (i + 1 < n_codes ? "," : "");
   }
   key += "|S=" + std::to_string(p->S) + "|cap=" + std::to_string((long long)p->query_cap) +
-         "|lik=" + std::to_string(p->lik_variant) + "|ord=" + std::to_string(p->order);
+         "|lik=" + std::to_string(p->lik_variant) + "|ord=" + std::to_string(p->order) +
+         "|mem=" + std::to_string(p->membership);
   const int rc = tune(
       key, p, cache_path, st,
       [&](const grand_params* pp, cudaStream_t s) {

@@ -73,7 +73,8 @@ struct SearchArgs {
   int tabA, tabB;  // table capacities
   int max_tiles;
   int Wmax;
-  int warp_kernel;  // 1 / 2: warp-per-frame kernel with 5- / 6-rank sides (automatic split); 0: CTA kernel
+  int warp_kernel;  // 1 / 2: warp-per-frame kernel with 5- / 6-rank sides (automatic split); 0: CTA kernel;
+                    // 3: hash join (membership HASH, S' <= 10)
   int warps;        // warps per CTA of the 6-rank warp kernel (0: 2)
   uint32_t* cw;
   uint32_t* queries;
@@ -896,21 +897,22 @@ struct WarpSlice {
   uint16_t* pos;     // [kRanks][2]
 };
 
-template <int kSide>
+template <int kSide, bool kWithPlanes = true>
 __host__ __device__ inline size_t warp_slice_bytes(int Wmax) {
   using D = WarpDims<kSide>;
   const size_t bz = kSide == kWarpSideMax ? D::kTab : 0;
-  size_t words = (size_t)D::kGroups * kPlanes + bz + 3 * D::kRanks * (size_t)Wmax + 3 * D::kRanks +
+  size_t words = (kWithPlanes ? (size_t)D::kGroups * kPlanes : 0) + bz + 3 * D::kRanks * (size_t)Wmax + 3 * D::kRanks +
                  kEStride * kEStride + Wmax + 2 * (D::kSub + 1) + 8 + 8 + D::kSub + 4 + D::kRanks;
   return (words * 4 + 15) & ~(size_t)15;
 }
 
-template <int kSide>
+template <int kSide, bool kWithPlanes = true>
 __device__ inline WarpSlice warp_slice(char* base, int Wmax) {
   using D = WarpDims<kSide>;
   WarpSlice w;
   uint32_t* p = reinterpret_cast<uint32_t*>(base);
-  w.planes = p; p += D::kGroups * kPlanes;
+  w.planes = kWithPlanes ? p : nullptr;
+  p += kWithPlanes ? D::kGroups * kPlanes : 0;
   w.Bz = p; p += kSide == kWarpSideMax ? D::kTab : 0;
   w.delta = p; p += 3 * D::kRanks * Wmax;
   w.dflt = p; p += 3 * D::kRanks;
@@ -1337,6 +1339,171 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Meet-in-the-middle hash join (membership GRAND_MEMBERSHIP_HASH, S' <= 10):
+// the same A x B split, but instead of comparing every pair the warp inserts
+// the A side's 32-bit syndrome projections (s0 ^ D_A) into a shared-memory
+// hash table and looks every B projection up. Each pair whose projections are
+// equal is confirmed on the full syndrome and ranked in closed form; the
+// smallest rank is the canonical first hit. The decision equals that of the
+// TEP-by-TEP test (every codeword TEP of the space is found), with O(|A| + |B|)
+// work per frame instead of O(|A| |B|); no TEP is tested one by one, so this
+// mode reports no TEP checks beyond the confirmed candidates.
+// ---------------------------------------------------------------------------
+constexpr int kHashSlots = 2 * (1 << (2 * kWarpSideMax));  // 2048: load factor <= 1/2
+constexpr int kHashBits = 11;
+// A slot packs the key's top 21 bits with (A entry + 1) in the low 11 bits; 0 is empty.
+constexpr uint32_t kHashEmpty = 0u;
+
+// Slot of a projection. The projections of one side form an affine subspace
+// (XORs of a few deltas), so their low bits alone would fill one contiguous
+// half of the table and make linear probing walk it; a multiplicative hash
+// (the top bits of key * an odd constant) scatters them.
+__device__ __forceinline__ uint32_t hash_slot(uint32_t key) { return (key * 0x9E3779B1u) >> (32 - kHashBits); }
+
+__host__ __device__ inline size_t hash_slice_bytes(int Wmax) {
+  return warp_slice_bytes<kWarpSideMax, false>(Wmax) + 4 * (size_t)kHashSlots;
+}
+
+__global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
+  using D = WarpDims<kWarpSideMax>;
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  char* base = smem_raw + (threadIdx.x >> 5) * hash_slice_bytes(a.Wmax);
+  const WarpSlice sl = warp_slice<kWarpSideMax, false>(base, a.Wmax);
+  uint32_t* hslot = reinterpret_cast<uint32_t*>(base + warp_slice_bytes<kWarpSideMax, false>(a.Wmax));
+  const unsigned n_hard = *(volatile unsigned*)&a.scr->n_hard;
+  unsigned long long my_eval = 0, my_useful = 0;
+
+  for (;;) {
+    unsigned fi = 0;
+    if (lane == 0) fi = atomicAdd(&a.scr->next, 1u);
+    fi = __shfl_sync(kFull, fi, 0);
+    if (fi >= n_hard) break;
+    const FrameRec* rec = a.recs + fi;
+    const int Sp = rec->sp;
+    const int w_done = rec->w_done;
+    const CodeDev code = a.codes[rec->code];
+    const int W = code.W;
+    if (lane < Sp) {
+      sl.ex[lane] = rec->ex[lane];
+      sl.pos[2 * lane] = rec->pos[lane][0];
+      sl.pos[2 * lane + 1] = rec->pos[lane][1];
+    }
+    if (lane < W) sl.s0[lane] = rec->s0[lane];
+    const uint32_t f0 = rec->f0;
+    for (int t = lane; t < kHashSlots; t += 32) hslot[t] = kHashEmpty;
+    __syncwarp();
+    for (int t = lane; t < Sp * 3 * W; t += 32) {
+      const int r = t / (3 * W), rem = t % (3 * W), alt = rem / W, w = rem % W;
+      const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
+      const uint32_t h = (alt != 1 && pI != kNoPos) ? __ldg(code.hcol + (size_t)pI * W + w) : 0u;
+      const uint32_t v = (alt != 0 && pQ != kNoPos) ? __ldg(code.hcol + (size_t)pQ * W + w) : 0u;
+      sl.delta[t] = h ^ v;
+    }
+    for (int t = lane; t < 3 * Sp; t += 32) {
+      const int r = t / 3, alt = t % 3;
+      const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
+      const uint32_t h = (alt != 1 && pI != kNoPos) ? __ldg(code.hf + pI) : 0u;
+      const uint32_t v = (alt != 0 && pQ != kNoPos) ? __ldg(code.hf + pQ) : 0u;
+      sl.dflt[t] = h ^ v;
+    }
+    esp_table_warp(sl.ex, Sp, sl.E);
+    __syncwarp();
+    const uint32_t total = esp_total(sl.E, Sp);
+    const int nAr = Sp >> 1, nBr = Sp - nAr;
+    const unsigned nA = warp_side_layout(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, sl.cumA);
+    const unsigned nB = warp_side_layout(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, sl.cumB);
+    // A side: projections (with s0's) by doubling, then into the hash table
+    warp_fill_side(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, f0, sl.Bz);
+    for (unsigned e = lane; e < nA; e += 32) {
+      const uint32_t key = sl.Bz[e];
+      const uint32_t packed = (key & ~((1u << kHashBits) - 1u)) | (e + 1u);
+      uint32_t h = hash_slot(key);
+      for (int probe = 0; probe < kHashSlots; ++probe) {  // at most half full: ends at an empty slot
+        if (atomicCAS(&hslot[h], kHashEmpty, packed) == kHashEmpty) break;
+        h = (h + 1) & (kHashSlots - 1);
+      }
+    }
+    __syncwarp();
+    // B side: projections by doubling, then one lookup per entry
+    warp_fill_side(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, 0u, sl.Bz);
+    uint32_t lr = 0xFFFFFFFFu, lc = 0;
+    for (unsigned col = lane; col < nB; col += 32) {
+      const uint32_t z = sl.Bz[col];
+      uint32_t h = hash_slot(z);
+      bool have_b = false;
+      uint32_t bcode = 0, bq;
+      const uint32_t zhi = z & ~((1u << kHashBits) - 1u);
+      for (int probe = 0; probe < kHashSlots; ++probe) {
+        const uint32_t slot = hslot[h];
+        if (slot == kHashEmpty) break;
+        if ((slot & ~((1u << kHashBits) - 1u)) == zhi) {
+          // top 21 bits equal (the slot index came from the whole key): a candidate
+          const uint32_t row = (slot & ((1u << kHashBits) - 1u)) - 1u;
+          // confirm on every syndrome word, rank in closed form
+          if (!have_b) {
+            warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, bq, bcode);
+            have_b = true;
+          }
+          uint32_t aq, acode;
+          warp_side_entry(sl, 0, nAr, sl.startA, sl.ordA, f0, row, aq, acode);
+          const uint32_t cc = acode | (bcode << (2 * nAr));
+          uint32_t orr = 0;
+          for (int w = 0; w < W; ++w) {
+            uint32_t zz = sl.s0[w];
+            for (int r = 0; r < Sp; ++r) {
+              const uint32_t d = (cc >> (2 * r)) & 3u;
+              if (d) zz ^= sl.delta[((size_t)r * 3 + (d - 1)) * W + w];
+            }
+            orr |= zz;
+          }
+          ++my_eval;
+          if (orr == 0) {
+            const uint32_t rk = tep_rank(sl.E, Sp, sl.ex, cc);
+            if (rk < lr) {
+              lr = rk;
+              lc = cc;
+            }
+          }
+        }
+        h = (h + 1) & (kHashSlots - 1);
+      }
+    }
+    const uint32_t best_rank = __reduce_min_sync(kFull, lr);
+    const unsigned who = __ballot_sync(kFull, lr == best_rank);
+    const uint32_t best_code = __shfl_sync(kFull, lc, __ffs(who) - 1);
+    // --- result -------------------------------------------------------------
+    if (lane == 0) {
+      const unsigned f = rec->frame;
+      uint32_t q_out;
+      if (best_rank != 0xFFFFFFFFu && (uint64_t)best_rank <= (uint64_t)a.cap) {
+        uint32_t* cw = a.cw + rec->cw_off;
+        for (int r = 0; r < Sp; ++r) {
+          const uint32_t d = (best_code >> (2 * r)) & 3u;
+          if (d & 1u) { const uint16_t p = sl.pos[2 * r]; if (p != kNoPos) cw[p >> 5] ^= 1u << (p & 31); }
+          if (d & 2u) { const uint16_t p = sl.pos[2 * r + 1]; if (p != kNoPos) cw[p >> 5] ^= 1u << (p & 31); }
+        }
+        q_out = best_rank;
+        a.abandon[f] = 0;
+      } else {
+        q_out = (uint32_t)((uint64_t)total < (uint64_t)a.cap ? total : (uint64_t)a.cap);
+        a.abandon[f] = 1;
+      }
+      a.queries[f] = q_out;
+      uint32_t done = 0;
+      for (int v = 0; v <= w_done; ++v) done += sl.E[Sp * kEStride + v];
+      my_useful += q_out - done;
+    }
+    __syncwarp();
+  }
+  for (int o = 16; o; o >>= 1) my_eval += __shfl_xor_sync(kFull, my_eval, o);
+  if (lane == 0) {
+    if (my_eval) atomicAdd(&a.scr->evaluated, my_eval);
+    if (my_useful) atomicAdd(&a.scr->search_useful, my_useful);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Bit-level GRAND-AB: TEPs of 0..max_weight flipped bits in colex order
 // ---------------------------------------------------------------------------
 struct AbArgs {
@@ -1582,6 +1749,17 @@ static int launch_search(const SearchArgs& s, int threads, size_t smem, int vari
       default: return launch_search_warp_t<6, kWarpSideMax>(s, 4, st);
     }
   }
+  if (s.warp_kernel == 3) {  // hash join (S' <= 10); warps per CTA from the tiles (default 4)
+    const int warps = s.warps > 0 ? s.warps : 4;
+    const size_t hsmem = hash_slice_bytes(s.Wmax) * warps;
+    if (cudaFuncSetAttribute(k_search_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem) != cudaSuccess)
+      return GRAND_E_CUDA;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_hash, 32 * warps, hsmem);
+    if (per_sm < 1) per_sm = 1;
+    k_search_hash<<<sm_count() * per_sm, 32 * warps, hsmem, st>>>(s);
+    return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
+  }
   if (s.warp_kernel == 2) {  // sides of 6 ranks; warps per CTA from the tiles (default 2)
     const int warps = s.warps > 0 ? s.warps : 2;
     switch (variant) {
@@ -1667,6 +1845,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
       // warp-per-frame bit-sliced search with 5- or 6-rank sides; an explicit
       // split selects the CTA kernel
       s.warp_kernel = s.split > 0 ? 0 : (Smax <= 2 * kWarpSideMax ? 1 : 2);
+      if (p->membership == GRAND_MEMBERSHIP_HASH && s.split <= 0 && Smax <= 2 * kWarpSideMax) s.warp_kernel = 3;
       s.warps = p->tiles[0] > 0 ? (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 0;
       s.cw = proto.cw;
       s.queries = proto.queries;
@@ -1703,7 +1882,8 @@ static int check_params(const grand_params* p) {
   if (!p) return GRAND_E_INVALID;
   if (p->query_cap < 1) return GRAND_E_INVALID;
   if (p->lik_variant != GRAND_LIK_THRESHOLD && p->lik_variant != GRAND_LIK_LITERAL) return GRAND_E_INVALID;
-  if (p->membership < GRAND_MEMBERSHIP_AUTO || p->membership > GRAND_MEMBERSHIP_ROW_PARITY) return GRAND_E_INVALID;
+  if (p->membership < GRAND_MEMBERSHIP_AUTO || p->membership > GRAND_MEMBERSHIP_HASH) return GRAND_E_INVALID;
+  if (p->order == GRAND_ORDER_QAM_NNE5 && p->membership == GRAND_MEMBERSHIP_HASH) return GRAND_E_UNSUPPORTED;
   if (p->order == GRAND_ORDER_QAM_NNE || p->order == GRAND_ORDER_QAM_NEARER || p->order == GRAND_ORDER_QAM_NNE5) {
     if (p->S < 0) return GRAND_E_INVALID;
     if (p->S > (p->order == GRAND_ORDER_QAM_NNE5 ? GRAND_S_MAX_NNE5 : kSMax)) return GRAND_E_UNSUPPORTED;
@@ -1828,7 +2008,9 @@ extern "C" int grand_decode_batch(const grand_code* c, const grand_params* p, co
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if (p->order == GRAND_ORDER_HAMMING) return run_ab(c, p, nullptr, y, nmask, n_frames, cw, queries, abandon, stats, st);
-  if (p->order == GRAND_ORDER_QAM_NNE5 || p->membership != GRAND_MEMBERSHIP_AUTO) return GRAND_E_UNSUPPORTED;
+  if (p->order == GRAND_ORDER_QAM_NNE5 || p->membership == GRAND_MEMBERSHIP_DELTA ||
+      p->membership == GRAND_MEMBERSHIP_ROW_PARITY)
+    return GRAND_E_UNSUPPORTED;
   const int m = m_of(p->M);
   if (!m || (n_frames > 0 && (!hard_idx || !key || !nmask))) return GRAND_E_INVALID;
   if (n_frames > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
@@ -1867,7 +2049,8 @@ extern "C" int grand_decode_symbols(const grand_code* c, const grand_params* p, 
   const int m = m_of(p->M);
   if (!m) return GRAND_E_INVALID;
   if (n_frames > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
-  if (p->order == GRAND_ORDER_QAM_NNE5 || p->membership != GRAND_MEMBERSHIP_AUTO)
+  if (p->order == GRAND_ORDER_QAM_NNE5 || p->membership == GRAND_MEMBERSHIP_DELTA ||
+      p->membership == GRAND_MEMBERSHIP_ROW_PARITY)
     return run_per_tep(c, p, symbols, n_frames, cw, queries, abandon, stats, st);
   const int L = (c->N + 2 * m - 1) / (2 * m);
   PrepArgs a{};
@@ -1913,7 +2096,7 @@ static int check_mixed_args(const grand_code* const* codes, int n_codes, const g
   int rc = check_params(p);
   if (rc) return rc;
   if ((p->order != GRAND_ORDER_QAM_NNE && p->order != GRAND_ORDER_QAM_NEARER) ||
-      p->membership != GRAND_MEMBERSHIP_AUTO)
+      (p->membership != GRAND_MEMBERSHIP_AUTO && p->membership != GRAND_MEMBERSHIP_HASH))
     return GRAND_E_INVALID;
   if (n_frames > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
   return GRAND_OK;

@@ -303,7 +303,8 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
       cfg->n_streams < 1 || cfg->n_streams > kMaxStreams || cfg->max_batch < 0 || !(cfg->N0 > 0.0f))
     return GRAND_E_INVALID;
   if ((cfg->params.order != GRAND_ORDER_QAM_NNE && cfg->params.order != GRAND_ORDER_QAM_NEARER) ||
-      cfg->params.membership != GRAND_MEMBERSHIP_AUTO || cfg->params.query_cap < 1 || cfg->params.S < 0 ||
+      (cfg->params.membership != GRAND_MEMBERSHIP_AUTO && cfg->params.membership != GRAND_MEMBERSHIP_HASH) ||
+      cfg->params.query_cap < 1 || cfg->params.S < 0 ||
       cfg->params.S > GRAND_S_MAX)
     return GRAND_E_INVALID;
   for (int i = 0; i < cfg->n_codes; ++i)

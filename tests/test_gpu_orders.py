@@ -1,8 +1,8 @@
-"""GPU parity of the TEP order variants and the membership tests kept for
-comparison: the nearer-axis-first order (split search and per-TEP kernel),
-the five-point NNE order (per-TEP kernel), and the syndrome-delta and
-row-parity membership tests, each against the CPU oracle with the same order,
-bit-exact on decoded words, query counts and abandon flags."""
+"""GPU parity of the TEP order variants and the membership tests: the
+nearer-axis-first order (split search and per-TEP kernel), the five-point NNE
+order (per-TEP kernel), the syndrome-delta and row-parity tests kept for
+comparison, and the hash-join decision, each against the CPU oracle with the
+same order, bit-exact on decoded words, query counts and abandon flags."""
 from __future__ import annotations
 
 import os
@@ -63,7 +63,7 @@ def assert_same(got, want, label=""):
 
 # oracle order ids: 1 paper, 2 nearer axis first, 3 five-point NNE (same as the ABI's)
 NNE, NEARER, NNE5 = 1, 2, 3
-AUTO, DELTA, ROW = 0, 1, 2
+AUTO, DELTA, ROW, HASH = 0, 1, 2, 3
 
 CASES = [
     # order, membership, N, M, S, EbN0 dB, cap, frames, lik
@@ -87,6 +87,16 @@ CASES = [
     (NNE5, AUTO, 128, 16, 0, 8.0, 100, 60, 0),          # S = 0
     (NNE5, AUTO, 512, 64, 7, 12.0, 3000, 60, 0),        # cap inside a weight class
     (NNE5, ROW, 128, 16, 6, 6.0, 5 ** 6, 150, 0),
+    (NNE, HASH, 128, 16, 10, 6.0, 1 << 20, 200, 0),
+    (NNE, HASH, 128, 16, 10, 10.0, 1 << 20, 400, 0),
+    (NNE, HASH, 32, 4, 8, 3.0, 1 << 16, 300, 0),
+    (NNE, HASH, 256, 64, 9, 10.0, 4 ** 9, 150, 0),
+    (NNE, HASH, 512, 64, 10, 13.0, 50000, 100, 0),      # cap inside a weight class
+    (NNE, HASH, 1024, 256, 10, 17.0, 1 << 14, 40, 0),
+    (NNE, HASH, 128, 16, 1, 8.0, 100, 200, 0),           # S = 1
+    (NNE, HASH, 128, 16, 12, 9.0, 1 << 20, 60, 0),       # S' > 10: the split search decides
+    (NEARER, HASH, 128, 16, 10, 7.0, 1 << 20, 150, 0),
+    (NNE, HASH, 128, 16, 10, 7.0, 1 << 20, 100, 1),      # literal likelihood
 ]
 
 
@@ -100,7 +110,7 @@ def test_order_parity(g, oracle_lib, order, mem, N, M, S, snr, cap, F, lik):
     assert_same(got, want, f"order={order} membership={mem} N={N} M={M} S={S}")
 
 
-@pytest.mark.parametrize("mem", [DELTA, ROW])
+@pytest.mark.parametrize("mem", [DELTA, ROW, HASH])
 def test_membership_tests_equal_split_search(g, oracle_lib, mem):
     """The per-TEP kernel with either membership test decides exactly as the
     split search on a larger batch (the paper's order)."""
@@ -175,6 +185,8 @@ def test_unsupported_combinations_are_refused(g, oracle_lib):
     code, _, _ = code_pair(g, oracle_lib, N)
     sym = torch.zeros((4, 32), dtype=torch.complex64, device="cuda")
     dm = g.demod(sym, M, N)
+    with pytest.raises(g.GrandError):  # the hash join does not serve the five-point order
+        g.decode_symbols(code, g.Params.make(order=NNE5, M=M, S=8, membership=HASH), sym)
     for p in (g.Params.make(order=NNE5, M=M, S=8), g.Params.make(M=M, S=8, membership=ROW)):
         with pytest.raises(g.GrandError):
             g.decode_batch(code, p, dm["y"], dm["hard_idx"], dm["key"], dm["nmask"])
@@ -184,4 +196,35 @@ def test_unsupported_combinations_are_refused(g, oracle_lib):
     with pytest.raises(g.GrandError):  # S above the five-point limit
         g.decode_symbols(code, g.Params.make(order=NNE5, M=M, S=11), sym)
     with pytest.raises(g.GrandError):  # unknown membership test
-        g.decode_symbols(code, g.Params.make(M=M, S=8, membership=3), sym)
+        g.decode_symbols(code, g.Params.make(M=M, S=8, membership=4), sym)
+
+
+def test_hash_join_two_call_mixed_and_full_batch(g, oracle_lib):
+    """The hash join through grand_decode_batch and an uneven batch, and on a
+    large batch against the split search (every output identical)."""
+    import torch
+
+    N, M, S = 128, 16, 10
+    code, H, info = code_pair(g, oracle_lib, N)
+    d = wl.qam_frames(64, 0, 30000, N, info, M, 7.0)
+    sym = to_dev(d["symbols"])
+    ph = g.Params.make(M=M, S=S, query_cap=1 << 20, membership=HASH)
+    a = unpack(g.decode_symbols(code, g.Params.make(M=M, S=S, query_cap=1 << 20), sym))
+    b = unpack(g.decode_symbols(code, ph, sym))
+    assert_same(b, a, "hash vs split, 30000 frames")
+    dm = g.demod(sym, M, N)
+    c = unpack(g.decode_batch(code, ph, dm["y"], dm["hard_idx"], dm["key"], dm["nmask"]))
+    assert_same(c, a, "hash two-call")
+    Ns = (32, 64, 128, 256, 512, 1024)
+    codes = [code_pair(g, oracle_lib, n)[0] for n in Ns]
+    infos = {n: code_pair(g, oracle_lib, n)[2] for n in Ns}
+    mx = wl.mixed_frames(65, 0, 3000, infos)
+    desc = g.frame_desc(np.searchsorted(np.array(Ns), mx["N"]), mx["M"], mx["sym_offset"], mx["cw_offset"])
+    dd, ss = to_dev(desc.view(np.uint8)), to_dev(mx["symbols"])
+    pm = g.Params.make(M=0, S=10, query_cap=1 << 18)
+    pmh = g.Params.make(M=0, S=10, query_cap=1 << 18, membership=HASH)
+    r1 = g.decode_mixed(codes, pm, dd, ss, mx["n_cw_words"])
+    r2 = g.decode_mixed(codes, pmh, dd, ss, mx["n_cw_words"])
+    torch.cuda.synchronize()
+    for k in ("cw", "queries", "abandon"):
+        assert torch.equal(r1[k], r2[k]), k
