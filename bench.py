@@ -491,6 +491,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=0, help="override frames per SNR (for quick runs)")
     ap.add_argument("--tiles", default="0,0,0,0", help="launch shape (grand_params.tiles), 0 = automatic")
+    ap.add_argument("--membership", default="auto", choices=("auto", "hash"),
+                    help="membership test of the search (the headline uses the TEP-by-TEP search)")
     ap.add_argument("--serve-batch", type=int, default=65536, help="serving: frames per launch")
     ap.add_argument("--serve-streams", type=int, default=4, help="serving: batches in flight")
     args = ap.parse_args()
@@ -499,6 +501,7 @@ def main():
     if args.frames:
         cfg["frames"] = args.frames
     tiles = tuple(int(t) for t in args.tiles.split(","))
+    membership = {"auto": 0, "hash": 3}[args.membership]
     if args.impl == "reference":
         return run_reference(args, cfg)
 
@@ -578,7 +581,7 @@ def main():
         d_desc = torch.from_numpy(desc.view(np.uint8)).to(dev)
         n_frames = len(inputs["N"])
         n_cw = inputs["n_cw_words"]
-        p = g.Params.make(M=0, S=cfg["S"], query_cap=cfg["cap"], tiles=tiles)
+        p = g.Params.make(M=0, S=cfg["S"], query_cap=cfg["cap"], tiles=tiles, membership=membership)
         alg_words = None
     else:
         codes = [g.Code.polar(cfg["N"], cfg["K"])]
@@ -587,7 +590,7 @@ def main():
         if cfg["kind"] == "ab":
             p = g.Params.make(order=g.ORDER_HAMMING, M=2, max_weight=cfg["max_weight"], query_cap=cfg["cap"])
         else:
-            p = g.Params.make(M=cfg["M"], S=cfg["S"], query_cap=cfg["cap"], tiles=tiles)
+            p = g.Params.make(M=cfg["M"], S=cfg["S"], query_cap=cfg["cap"], tiles=tiles, membership=membership)
         alg_words = (cfg["N"] - cfg["K"]) / 32.0
     h_sym = torch.from_numpy(inputs["symbols"]).pin_memory()
     d_sym = h_sym.to(dev)
@@ -677,6 +680,37 @@ def main():
     else:
         bler = float(np.mean((cw_host.reshape(n_frames, -1) != inputs["codewords_packed"]).any(axis=1)))
 
+    # ---- the same batch decided by the hash join of the split (same outputs,
+    #      membership not tested TEP by TEP): reported beside the headline
+    hash_join = None
+    if cfg["kind"] in ("qam", "mixed") and args.membership == "auto":
+        ref_out = (d_cw.clone(), d_q.clone(), d_ab.clone())
+        ph = g.Params.make(order=p.order, M=p.M, S=p.S, query_cap=p.query_cap, tiles=tiles,
+                           membership=g.MEMBERSHIP_HASH)
+
+        def hstep():
+            if cfg["kind"] == "mixed":
+                return g.decode_mixed(codes, ph, d_desc, d_sym, n_cw, cw=d_cw, queries=d_q, abandon=d_ab)
+            return g.decode_symbols(codes[0], ph, d_sym, cw=d_cw.view(n_frames, -1), queries=d_q, abandon=d_ab)
+
+        for _ in range(args.warmup):
+            hstep()
+        h_ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hstep()
+            e1.record(stream)
+            e1.synchronize()
+            h_ms.append(e0.elapsed_time(e1))
+        same = all(torch.equal(x, y) for x, y in zip((d_cw, d_q, d_ab), ref_out))
+        hash_join = {"ms_per_step": statistics.mean(h_ms), "frames_per_s": n_frames / (statistics.mean(h_ms) / 1e3),
+                     "outputs_equal": bool(same),
+                     "what": "membership decided by a hash join of the split (GRAND_MEMBERSHIP_HASH): same outputs, "
+                             "not a per-TEP test, so not counted as checks"}
+
     # ---- e2e: same call with host buffers, copies in the timed region
     h_cw = torch.empty(n_cw, dtype=torch.int32).pin_memory()
     h_q = torch.empty(n_frames, dtype=torch.int32).pin_memory()
@@ -723,7 +757,7 @@ def main():
 
     # ---- roofline of the dominant kernel (the TEP search)
     roofline = None
-    if alg_words is not None and sum(search_ms) > 0:
+    if alg_words is not None and sum(search_ms) > 0 and args.membership == "auto":  # TEPs tested one by one
         import hashlib
 
         ops = search_useful / args.steps * alg_words
@@ -767,6 +801,7 @@ def main():
             "data": "synthetic (seeded random polar codewords over AWGN)",
             "config": {"workload": cfg["desc"], "frames_per_step_per_gpu": n_frames, "tiles": list(tiles),
                        "l2": "flushed before every timed step (256 MiB write)",
+                       "membership": args.membership,
                        "parallelism": f"frames sharded, {world} replica(s)"},
             "frames_per_s": frames_per_s,
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -778,6 +813,7 @@ def main():
             "kernel_ms": ({"prep": statistics.mean(prep_ms), "search": statistics.mean(search_ms)} if search_ms
                           else None),
             "roofline": roofline,
+            "hash_join": hash_join,
             "one_frame_per_launch": one,
             "autotune": tune,
             "cpu_baseline": cpu,

@@ -99,8 +99,8 @@ typedef enum grand_order {
  *               syndrome and ranked; the smallest rank is the first hit.
  *               Same outputs as the TEP-by-TEP search (every codeword of the
  *               space is found), O(|A| + |B|) work per frame; stats count only
- *               the confirmed pairs as checks. QAM_NNE / QAM_NEARER with
- *               S' <= 10 (larger S' use AUTO); not for QAM_NNE5. */
+ *               the confirmed pairs as checks. QAM_NNE / QAM_NEARER, S' <= 12;
+ *               not for QAM_NNE5. */
 typedef enum grand_membership {
   GRAND_MEMBERSHIP_AUTO = 0,
   GRAND_MEMBERSHIP_DELTA = 1,

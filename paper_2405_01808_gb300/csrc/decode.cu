@@ -74,7 +74,7 @@ struct SearchArgs {
   int max_tiles;
   int Wmax;
   int warp_kernel;  // 1 / 2: warp-per-frame kernel with 5- / 6-rank sides (automatic split); 0: CTA kernel;
-                    // 3: hash join (membership HASH, S' <= 10)
+                    // 3 / 4: hash join (membership HASH) with 5- / 6-rank sides
   int warps;        // warps per CTA of the 6-rank warp kernel (0: 2)
   uint32_t* cw;
   uint32_t* queries;
@@ -1339,7 +1339,8 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Meet-in-the-middle hash join (membership GRAND_MEMBERSHIP_HASH, S' <= 10):
+// Meet-in-the-middle hash join (membership GRAND_MEMBERSHIP_HASH; sides of 5
+// ranks, S' <= 10, or 6 ranks, S' = 11, 12):
 // the same A x B split, but instead of comparing every pair the warp inserts
 // the A side's 32-bit syndrome projections (s0 ^ D_A) into a shared-memory
 // hash table and looks every B projection up. Each pair whose projections are
@@ -1349,28 +1350,39 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
 // work per frame instead of O(|A| |B|); no TEP is tested one by one, so this
 // mode reports no TEP checks beyond the confirmed candidates.
 // ---------------------------------------------------------------------------
-constexpr int kHashSlots = 2 * (1 << (2 * kWarpSideMax));  // 2048: load factor <= 1/2
-constexpr int kHashBits = 11;
-// A slot packs the key's top 21 bits with (A entry + 1) in the low 11 bits; 0 is empty.
+// Table of one side of kSide ranks: 2 x 4^kSide slots (load factor <= 1/2).
+// A slot packs the key's top (32 - kBits) bits with (A entry + 1) in the low
+// kBits bits; 0 is empty.
+template <int kSide>
+struct HashDims {
+  static constexpr int kBits = 2 * kSide + 1;
+  static constexpr int kSlots = 1 << kBits;
+  static constexpr uint32_t kLow = (1u << kBits) - 1u;
+};
 constexpr uint32_t kHashEmpty = 0u;
 
 // Slot of a projection. The projections of one side form an affine subspace
 // (XORs of a few deltas), so their low bits alone would fill one contiguous
 // half of the table and make linear probing walk it; a multiplicative hash
 // (the top bits of key * an odd constant) scatters them.
-__device__ __forceinline__ uint32_t hash_slot(uint32_t key) { return (key * 0x9E3779B1u) >> (32 - kHashBits); }
-
-__host__ __device__ inline size_t hash_slice_bytes(int Wmax) {
-  return warp_slice_bytes<kWarpSideMax, false>(Wmax) + 4 * (size_t)kHashSlots;
+template <int kSide>
+__device__ __forceinline__ uint32_t hash_slot(uint32_t key) {
+  return (key * 0x9E3779B1u) >> (32 - HashDims<kSide>::kBits);
 }
 
+template <int kSide>
+__host__ __device__ inline size_t hash_slice_bytes(int Wmax) {
+  return warp_slice_bytes<kSide, false>(Wmax) + 4 * (size_t)HashDims<kSide>::kSlots;
+}
+
+template <int kSide>
 __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
-  using D = WarpDims<kWarpSideMax>;
+  using HD = HashDims<kSide>;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31;
-  char* base = smem_raw + (threadIdx.x >> 5) * hash_slice_bytes(a.Wmax);
-  const WarpSlice sl = warp_slice<kWarpSideMax, false>(base, a.Wmax);
-  uint32_t* hslot = reinterpret_cast<uint32_t*>(base + warp_slice_bytes<kWarpSideMax, false>(a.Wmax));
+  char* base = smem_raw + (threadIdx.x >> 5) * hash_slice_bytes<kSide>(a.Wmax);
+  const WarpSlice sl = warp_slice<kSide, false>(base, a.Wmax);
+  uint32_t* hslot = reinterpret_cast<uint32_t*>(base + warp_slice_bytes<kSide, false>(a.Wmax));
   const unsigned n_hard = *(volatile unsigned*)&a.scr->n_hard;
   unsigned long long my_eval = 0, my_useful = 0;
 
@@ -1391,7 +1403,7 @@ __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
     }
     if (lane < W) sl.s0[lane] = rec->s0[lane];
     const uint32_t f0 = rec->f0;
-    for (int t = lane; t < kHashSlots; t += 32) hslot[t] = kHashEmpty;
+    for (int t = lane; t < HD::kSlots; t += 32) hslot[t] = kHashEmpty;
     __syncwarp();
     for (int t = lane; t < Sp * 3 * W; t += 32) {
       const int r = t / (3 * W), rem = t % (3 * W), alt = rem / W, w = rem % W;
@@ -1413,35 +1425,48 @@ __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
     const int nAr = Sp >> 1, nBr = Sp - nAr;
     const unsigned nA = warp_side_layout(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, sl.cumA);
     const unsigned nB = warp_side_layout(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, sl.cumB);
-    // A side: projections (with s0's) by doubling, then into the hash table
-    warp_fill_side(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, f0, sl.Bz);
+    // A side: projections (with s0's) into the hash table -- by doubling into
+    // the scalar buffer for 5-rank sides, from the table layout otherwise
+    if constexpr (kSide == kWarpSideMax) warp_fill_side(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, f0, sl.Bz);
     for (unsigned e = lane; e < nA; e += 32) {
-      const uint32_t key = sl.Bz[e];
-      const uint32_t packed = (key & ~((1u << kHashBits) - 1u)) | (e + 1u);
-      uint32_t h = hash_slot(key);
-      for (int probe = 0; probe < kHashSlots; ++probe) {  // at most half full: ends at an empty slot
+      uint32_t key;
+      if constexpr (kSide == kWarpSideMax) {
+        key = sl.Bz[e];
+      } else {
+        uint32_t acode;
+        warp_side_entry(sl, 0, nAr, sl.startA, sl.ordA, f0, e, key, acode);
+      }
+      const uint32_t packed = (key & ~HD::kLow) | (e + 1u);
+      uint32_t h = hash_slot<kSide>(key);
+      for (int probe = 0; probe < HD::kSlots; ++probe) {  // at most half full: ends at an empty slot
         if (atomicCAS(&hslot[h], kHashEmpty, packed) == kHashEmpty) break;
-        h = (h + 1) & (kHashSlots - 1);
+        h = (h + 1) & (HD::kSlots - 1);
       }
     }
     __syncwarp();
-    // B side: projections by doubling, then one lookup per entry
-    warp_fill_side(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, 0u, sl.Bz);
+    // B side: one lookup per entry
+    if constexpr (kSide == kWarpSideMax) warp_fill_side(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, 0u, sl.Bz);
     uint32_t lr = 0xFFFFFFFFu, lc = 0;
     for (unsigned col = lane; col < nB; col += 32) {
-      const uint32_t z = sl.Bz[col];
-      uint32_t h = hash_slot(z);
+      uint32_t z, bcode = 0;
       bool have_b = false;
-      uint32_t bcode = 0, bq;
-      const uint32_t zhi = z & ~((1u << kHashBits) - 1u);
-      for (int probe = 0; probe < kHashSlots; ++probe) {
+      if constexpr (kSide == kWarpSideMax) {
+        z = sl.Bz[col];
+      } else {
+        warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, z, bcode);
+        have_b = true;
+      }
+      uint32_t h = hash_slot<kSide>(z);
+      const uint32_t zhi = z & ~HD::kLow;
+      for (int probe = 0; probe < HD::kSlots; ++probe) {
         const uint32_t slot = hslot[h];
         if (slot == kHashEmpty) break;
-        if ((slot & ~((1u << kHashBits) - 1u)) == zhi) {
-          // top 21 bits equal (the slot index came from the whole key): a candidate
-          const uint32_t row = (slot & ((1u << kHashBits) - 1u)) - 1u;
+        if ((slot & ~HD::kLow) == zhi) {
+          // top bits equal (the slot index came from the whole key): a candidate;
           // confirm on every syndrome word, rank in closed form
+          const uint32_t row = (slot & HD::kLow) - 1u;
           if (!have_b) {
+            uint32_t bq;
             warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, bq, bcode);
             have_b = true;
           }
@@ -1466,7 +1491,7 @@ __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
             }
           }
         }
-        h = (h + 1) & (kHashSlots - 1);
+        h = (h + 1) & (HD::kSlots - 1);
       }
     }
     const uint32_t best_rank = __reduce_min_sync(kFull, lr);
@@ -1741,6 +1766,19 @@ static int launch_search_warp_t(const SearchArgs& s, int warps, cudaStream_t st)
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
+template <int kSide>
+static int launch_search_hash_t(const SearchArgs& s, int warps, cudaStream_t st) {
+  const size_t hsmem = hash_slice_bytes<kSide>(s.Wmax) * warps;
+  auto kern = k_search_hash<kSide>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem) != cudaSuccess)
+    return GRAND_E_CUDA;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, hsmem);
+  if (per_sm < 1) per_sm = 1;
+  kern<<<sm_count() * per_sm, 32 * warps, hsmem, st>>>(s);
+  return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
+}
+
 static int launch_search(const SearchArgs& s, int threads, size_t smem, int variant, cudaStream_t st) {
   if (s.warp_kernel == 1) {
     switch (variant) {
@@ -1749,16 +1787,9 @@ static int launch_search(const SearchArgs& s, int threads, size_t smem, int vari
       default: return launch_search_warp_t<6, kWarpSideMax>(s, 4, st);
     }
   }
-  if (s.warp_kernel == 3) {  // hash join (S' <= 10); warps per CTA from the tiles (default 4)
-    const int warps = s.warps > 0 ? s.warps : 4;
-    const size_t hsmem = hash_slice_bytes(s.Wmax) * warps;
-    if (cudaFuncSetAttribute(k_search_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem) != cudaSuccess)
-      return GRAND_E_CUDA;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_hash, 32 * warps, hsmem);
-    if (per_sm < 1) per_sm = 1;
-    k_search_hash<<<sm_count() * per_sm, 32 * warps, hsmem, st>>>(s);
-    return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
+  if (s.warp_kernel == 3 || s.warp_kernel == 4) {  // hash join; warps per CTA from the tiles
+    return s.warp_kernel == 3 ? launch_search_hash_t<kWarpSideMax>(s, s.warps > 0 ? s.warps : 4, st)
+                              : launch_search_hash_t<kWarpSideMax + 1>(s, s.warps > 0 ? s.warps : 1, st);
   }
   if (s.warp_kernel == 2) {  // sides of 6 ranks; warps per CTA from the tiles (default 2)
     const int warps = s.warps > 0 ? s.warps : 2;
@@ -1845,7 +1876,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
       // warp-per-frame bit-sliced search with 5- or 6-rank sides; an explicit
       // split selects the CTA kernel
       s.warp_kernel = s.split > 0 ? 0 : (Smax <= 2 * kWarpSideMax ? 1 : 2);
-      if (p->membership == GRAND_MEMBERSHIP_HASH && s.split <= 0 && Smax <= 2 * kWarpSideMax) s.warp_kernel = 3;
+      if (p->membership == GRAND_MEMBERSHIP_HASH && s.split <= 0) s.warp_kernel = Smax <= 2 * kWarpSideMax ? 3 : 4;
       s.warps = p->tiles[0] > 0 ? (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 0;
       s.cw = proto.cw;
       s.queries = proto.queries;

@@ -94,7 +94,9 @@ CASES = [
     (NNE, HASH, 512, 64, 10, 13.0, 50000, 100, 0),      # cap inside a weight class
     (NNE, HASH, 1024, 256, 10, 17.0, 1 << 14, 40, 0),
     (NNE, HASH, 128, 16, 1, 8.0, 100, 200, 0),           # S = 1
-    (NNE, HASH, 128, 16, 12, 9.0, 1 << 20, 60, 0),       # S' > 10: the split search decides
+    (NNE, HASH, 128, 16, 12, 9.0, 1 << 20, 60, 0),       # S' = 12: 6-rank sides
+    (NNE, HASH, 512, 64, 12, 13.0, 1 << 22, 40, 0),
+    (NNE, HASH, 1024, 256, 11, 17.0, 1 << 20, 30, 0),    # S' = 11: 5 + 6 ranks
     (NEARER, HASH, 128, 16, 10, 7.0, 1 << 20, 150, 0),
     (NNE, HASH, 128, 16, 10, 7.0, 1 << 20, 100, 1),      # literal likelihood
 ]
