@@ -146,19 +146,15 @@ __device__ __forceinline__ uint32_t projection(uint32_t f0, const uint32_t* dflt
 
 constexpr int kPrepMaxW0 = 3;  // TEP weights the preparation can test in canonical order
 
-// WM: compile-time bound on the syndrome words (registers of the base syndrome).
+// One frame of the preparation (one warp). Returns true when the frame needs
+// the search stage; its hand-off record then went to a fresh slot of the
+// batch's record array. WM: compile-time bound on the syndrome words
+// (registers of the base syndrome).
 template <int WM>
-__global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
-  extern __shared__ __align__(16) char smem_raw[];
+__device__ __forceinline__ bool prep_frame(const PrepArgs& a, const int64_t f, const PrepSmem& sm,
+                                           unsigned long long& evaluated) {
   const int lane = threadIdx.x & 31;
-  const int warp_in_block = threadIdx.x >> 5;
-  const int warps_per_block = blockDim.x >> 5;
-  PrepSmem sm = prep_smem(smem_raw + warp_in_block * prep_warp_bytes(a.Lmax, a.Wmax), a.Lmax, a.Wmax);
-  const int64_t gwarp = (int64_t)blockIdx.x * warps_per_block + warp_in_block;
-  const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
-  unsigned long long evaluated = 0;
-
-  for (int64_t f = gwarp; f < a.n_frames; f += nwarps) {
+  {
     // --- frame parameters -------------------------------------------------
     int code_id = 0, M = a.M;
     int64_t sym_off = 0, cw_off = 0;
@@ -183,7 +179,7 @@ __global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
         a.queries[f] = 0;
         a.abandon[f] = 3;
       }
-      continue;
+      return false;
     }
     const CodeDev code = a.codes[code_id];
     const int N = code.N, W = code.W, NW = N >> 5;
@@ -240,7 +236,7 @@ __global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
         a.abandon[f] = 2;
       }
       __syncwarp();
-      continue;
+      return false;
     }
 
     // --- base syndrome s0 = H y ---------------------------------------------
@@ -486,9 +482,25 @@ __global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
         rec->w_done = (uint8_t)w_done;
         rec->cw_off = cw_off;
       }
+      __syncwarp();
+      return true;
     }
     __syncwarp();
   }
+  return false;
+}
+
+template <int WM>
+__global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp_in_block = threadIdx.x >> 5;
+  const int warps_per_block = blockDim.x >> 5;
+  PrepSmem sm = prep_smem(smem_raw + warp_in_block * prep_warp_bytes(a.Lmax, a.Wmax), a.Lmax, a.Wmax);
+  const int64_t gwarp = (int64_t)blockIdx.x * warps_per_block + warp_in_block;
+  const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
+  unsigned long long evaluated = 0;
+  for (int64_t f = gwarp; f < a.n_frames; f += nwarps) prep_frame<WM>(a, f, sm, evaluated);
   // stats
   for (int o = 16; o; o >>= 1) evaluated += __shfl_xor_sync(kFull, evaluated, o);
   if (lane == 0 && evaluated) atomicAdd(&a.scr->evaluated, evaluated);
@@ -1129,22 +1141,14 @@ __device__ __forceinline__ uint32_t group_acc_part(const uint32_t* planes, int g
   return acc;
 }
 
-template <int kMinBlocks, int kSide>
-__global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
+// The search of one frame from its hand-off record (one warp; `rec` may live in
+// global or shared memory). Lane 0 accumulates the evaluated and useful checks.
+template <int kSide>
+__device__ __forceinline__ void search_frame(const SearchArgs& a, const FrameRec* rec, const WarpSlice& sl,
+                                             unsigned long long& my_eval, unsigned long long& my_useful) {
   using D = WarpDims<kSide>;
-  extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31;
-  const WarpSlice sl =
-      warp_slice<kSide>(smem_raw + (threadIdx.x >> 5) * warp_slice_bytes<kSide>(a.Wmax), a.Wmax);
-  const unsigned n_hard = *(volatile unsigned*)&a.scr->n_hard;
-  unsigned long long my_eval = 0, my_useful = 0;
-
-  for (;;) {
-    unsigned fi = 0;
-    if (lane == 0) fi = atomicAdd(&a.scr->next, 1u);
-    fi = __shfl_sync(kFull, fi, 0);
-    if (fi >= n_hard) break;
-    const FrameRec* rec = a.recs + fi;
+  {
     const int Sp = rec->sp;
     const int w_done = rec->w_done;
     const CodeDev code = a.codes[rec->code];
@@ -1331,6 +1335,23 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
       my_useful += q_out - done;
     }
     __syncwarp();
+  }
+}
+
+template <int kMinBlocks, int kSide>
+__global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const WarpSlice sl =
+      warp_slice<kSide>(smem_raw + (threadIdx.x >> 5) * warp_slice_bytes<kSide>(a.Wmax), a.Wmax);
+  const unsigned n_hard = *(volatile unsigned*)&a.scr->n_hard;
+  unsigned long long my_eval = 0, my_useful = 0;
+  for (;;) {
+    unsigned fi = 0;
+    if (lane == 0) fi = atomicAdd(&a.scr->next, 1u);
+    fi = __shfl_sync(kFull, fi, 0);
+    if (fi >= n_hard) break;
+    search_frame<kSide>(a, a.recs + fi, sl, my_eval, my_useful);
   }
   if (lane == 0) {
     if (my_eval) atomicAdd(&a.scr->evaluated, my_eval);
@@ -1819,6 +1840,8 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     return GRAND_OK;
   }
   keep_pool_cached();
+  const int w0 = p->tiles[2] > 0 ? (p->tiles[2] > 3 ? 3 : p->tiles[2]) : 2;
+  const int Smax = p->S < Lmax ? p->S : Lmax;
   // scratch: header + one record per frame (worst case: every frame hard)
   const size_t rec_bytes = sizeof(FrameRec) * (size_t)n_frames;
   char* scratch = nullptr;
@@ -1835,7 +1858,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     a.scr = scr;
     a.Lmax = Lmax;
     a.Wmax = Wmax;
-    a.w0 = p->tiles[2] > 0 ? (p->tiles[2] > 3 ? 3 : p->tiles[2]) : 2;
+    a.w0 = w0;
     const int warps = 4;
     const size_t prep_smem = prep_warp_bytes(Lmax, Wmax) * warps;
     const int64_t want = (n_frames + warps - 1) / warps;
@@ -1856,7 +1879,6 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     if (stats) cudaEventRecord(ev[1], st);
     if (cudaGetLastError() != cudaSuccess) { rc = GRAND_E_CUDA; break; }
 
-    const int Smax = p->S < Lmax ? p->S : Lmax;
     if (Smax > a.w0) {
       SearchArgs s{};
       s.recs = recs;
