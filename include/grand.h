@@ -129,8 +129,9 @@ typedef enum grand_lik {
  *   max_weight  HAMMING order: largest number of flipped bits (0..4).
  *   query_cap   abandonment threshold, >= 1 valid queries.
  *   lik_variant GRAND_LIK_*.
- *   tiles       launch shape, 0 = automatic: [0] warps per search CTA (1..8;
- *               S' = 11, 12 and explicit splits), [1] A-side ranks of the
+ *   tiles       launch shape, 0 = automatic: [0] warps per search CTA (1..8
+ *               for explicit splits, 1..4 for the warp-per-frame kernels of
+ *               S' = 11, 12 and the hash join), [1] A-side ranks of the
  *               search split (1..6; a nonzero value selects the CTA-per-frame
  *               search, 0 the warp-per-frame search with S'/2 ranks on the A
  *               side), [2] number of TEP weights tested by the per-frame

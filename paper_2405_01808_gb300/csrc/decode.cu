@@ -1808,12 +1808,14 @@ static int launch_search(const SearchArgs& s, int threads, size_t smem, int vari
       default: return launch_search_warp_t<6, kWarpSideMax>(s, 4, st);
     }
   }
+  // the warp-per-frame kernels are compiled for CTAs of at most 4 warps
+  const int req_warps = s.warps > 4 ? 4 : s.warps;
   if (s.warp_kernel == 3 || s.warp_kernel == 4) {  // hash join; warps per CTA from the tiles
-    return s.warp_kernel == 3 ? launch_search_hash_t<kWarpSideMax>(s, s.warps > 0 ? s.warps : 4, st)
-                              : launch_search_hash_t<kWarpSideMax + 1>(s, s.warps > 0 ? s.warps : 1, st);
+    return s.warp_kernel == 3 ? launch_search_hash_t<kWarpSideMax>(s, req_warps > 0 ? req_warps : 4, st)
+                              : launch_search_hash_t<kWarpSideMax + 1>(s, req_warps > 0 ? req_warps : 1, st);
   }
   if (s.warp_kernel == 2) {  // sides of 6 ranks; warps per CTA from the tiles (default 2)
-    const int warps = s.warps > 0 ? s.warps : 2;
+    const int warps = req_warps > 0 ? req_warps : 2;
     switch (variant) {
       case 6: return launch_search_warp_t<6, kWarpSideMax + 1>(s, warps, st);
       case 8: return launch_search_warp_t<8, kWarpSideMax + 1>(s, warps, st);

@@ -202,7 +202,7 @@ def test_tiles_do_not_change_results(g, oracle_lib, tiles):
     assert_same(other, base, f"tiles={tiles}")
 
 
-@pytest.mark.parametrize("tiles", [(4, 6, 2, 0), (1, 0, 3, 6), (4, 0, 2, 8), (8, 5, 2, 0)])
+@pytest.mark.parametrize("tiles", [(4, 6, 2, 0), (1, 0, 3, 6), (4, 0, 2, 8), (8, 5, 2, 0), (8, 0, 2, 0)])
 def test_tiles_do_not_change_results_s12(g, oracle_lib, tiles):
     """S' = 12: the warp-per-frame search with 6-rank sides (automatic split,
     any warps per CTA and register budget) and the CTA search (explicit
