@@ -93,3 +93,22 @@ def test_server_and_plan_validation_without_gpu(glib):
     assert L.grand_plan_destroy(None) == 0
     assert L.grand_server_destroy(None) == 0
     assert L.grand_clock_ns() > 0
+
+
+def test_params_layout_matches_header(glib):
+    """grand_params as the binding lays it out: the header's field order,
+    natural alignment, 48 bytes (membership fills the tail padding)."""
+    P = glib.Params
+    assert ctypes.sizeof(P) == 48
+    offsets = {name: getattr(P, name).offset for name, _ in P._fields_}
+    assert offsets == {"order": 0, "M": 4, "S": 8, "max_weight": 12, "query_cap": 16, "lik_variant": 24,
+                       "tiles": 28, "membership": 44}
+    text = open(os.path.join(ROOT, "include", "grand.h")).read()
+    body = text[text.index("typedef struct grand_params {"):text.index("} grand_params;")]
+    fields = re.findall(r"^\s*\w+\s+(\w+)(?:\[\d+\])?;", body, flags=re.M)
+    assert fields == [n for n, _ in P._fields_]
+    for name, value in (("GRAND_ORDER_QAM_NEARER", glib.ORDER_QAM_NEARER), ("GRAND_ORDER_QAM_NNE5", glib.ORDER_QAM_NNE5),
+                        ("GRAND_MEMBERSHIP_DELTA", glib.MEMBERSHIP_DELTA),
+                        ("GRAND_MEMBERSHIP_ROW_PARITY", glib.MEMBERSHIP_ROW_PARITY),
+                        ("GRAND_MEMBERSHIP_HASH", glib.MEMBERSHIP_HASH)):
+        assert re.search(rf"{name}\s*=\s*{value}\b", text), name
