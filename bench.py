@@ -265,7 +265,7 @@ def run_serving(args, cfg, g, inputs):
     reqs["M"] = inputs["M"]
     reqs["symbols"] = sym.ctypes.data + 8 * inputs["sym_offset"].astype(np.uint64)
     reqs["tag"] = np.arange(F, dtype=np.uint64)
-    p = g.Params.make(M=0, S=cfg["S"], query_cap=cfg["cap"])
+    p = g.Params.make(M=0, S=cfg["S"], query_cap=cfg["cap"], membership={"auto": 0, "hash": 3}[args.membership])
     rows = []
     g_rng = np.random.default_rng(CONFIG_IDS["c5"])
     for rate in cfg["rates"]:
@@ -284,13 +284,16 @@ def run_serving(args, cfg, g, inputs):
         reqs["arrival_ns"] = arrival
         i = 0
         got = []
+        submit_ns = np.zeros(F, dtype=np.int64)  # when the driver handed each request over
         t_start = time.perf_counter()
         gc.disable()  # the driver loop stands in for a native client: no collector pauses inside it
         while i < F:
             now = g.clock_ns()
             j = int(np.searchsorted(arrival, now, side="right"))
             if j > i:
-                i += srv.submit(reqs[i:j])
+                k = srv.submit(reqs[i:j])
+                submit_ns[i:i + k] = now
+                i += k
             got.append(srv.poll(1 << 16))
             if time.perf_counter() - t_start > 120:
                 break
@@ -306,6 +309,8 @@ def run_serving(args, cfg, g, inputs):
         res = np.concatenate(got)
         res = res[res["tag"] >= 50000]  # the first 50,000 requests warm the server at this rate
         lat_us = (res["done_ns"] - res["arrival_ns"]) / 1e3
+        lag_us = (submit_ns[res["tag"].astype(np.int64)] - res["arrival_ns"]) / 1e3
+        srv_us = lat_us - lag_us
         span = (res["done_ns"].max() - arrival[50000]) / 1e9
         rows.append({"offered_frames_per_s": rate, "completed": int(len(res)),
                      "frames_per_s": len(res) / span, "checks_per_s": float(res["queries"].sum()) / span,
@@ -318,6 +323,11 @@ def run_serving(args, cfg, g, inputs):
                      "launch_us": {"mean": st["launch_ns"] / max(1, st["batches"]) / 1e3,
                                    "max": st["max_launch_ns"] / 1e3},
                      "latency_us_hist": np.percentile(lat_us, [10, 25, 50, 75, 90, 95, 99, 99.9]).round(1).tolist(),
+                     # the two parts: the driver's delay in handing requests over, and the server's time
+                     "driver_lag_us": {"p50": float(np.percentile(lag_us, 50)), "p99": float(np.percentile(lag_us, 99)),
+                                       "max": float(lag_us.max())},
+                     "server_latency_us": {"p50": float(np.percentile(srv_us, 50)),
+                                           "p99": float(np.percentile(srv_us, 99)), "max": float(srv_us.max())},
                      "errors": st["errors"]})
     return rows
 
