@@ -78,8 +78,8 @@ SMS, ALU_LANES, MAX_CLOCK_GHZ = 152, 64, 2.07
 ALU_PEAK_TOPS = SMS * ALU_LANES * MAX_CLOCK_GHZ / 1000.0
 # Counters of the search kernel from one ncu capture (profiles/k_search_warp_c2_small.md),
 # valid only while csrc/decode.cu is the captured source (sha256 prefix).
-NCU_SEARCH = {"sha": "5346236dbcb87ab7", "dram_bytes_per_hard_frame": 1551872 / 9596,
-              "alu_pipe_active": 0.737, "alu_ops_per_check": 0.75}
+NCU_SEARCH = {"sha": "3b0a968ccd49bed6", "dram_bytes_per_hard_frame": 1548544 / 9596,
+              "alu_pipe_active": 0.737, "alu_ops_per_check": 0.77}
 
 
 def make_inputs(cfg, rank, info_by_N):
