@@ -71,11 +71,12 @@ def run_all(srv, reqs, timeout_s=30.0):
     return np.concatenate(got)
 
 
-def test_results_equal_alone(env):
+@pytest.mark.parametrize("membership", [0, 3])  # TEP-by-TEP search; hash join
+def test_results_equal_alone(env, membership):
     g, codes, info = env
     code_of_N = {n: i for i, n in enumerate(NS)}
     mx = wl.mixed_frames(60, 0, 3000, info, ebn0_range=(6.0, 14.0))
-    p = g.Params.make(M=0, S=10, query_cap=1 << 20)
+    p = g.Params.make(M=0, S=10, query_cap=1 << 20, membership=membership)
     srv = g.Server(codes, p, max_slots=4096, max_device_bytes=64 << 20, max_batch=512, n_streams=4)
     reqs = make_requests(g, mx, code_of_N)
     res = run_all(srv, reqs)
