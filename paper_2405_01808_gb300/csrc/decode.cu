@@ -1697,34 +1697,83 @@ struct DemodArgs {
   uint8_t* nmask;
   float* rel;
   uint32_t* y;
+  uint64_t Lmagic;  // ceil(2^64 / L): frame of symbol s = high word of s * Lmagic (exact for s < 2^64 / L)
 };
 
+// One symbol of the public demodulation call (outputs that are NULL are skipped).
+__device__ __forceinline__ void demod_one(const DemodArgs& a, int64_t s, float2 v, uint16_t& hidx, uint32_t& key,
+                                          uint8_t& nmask, float& rel) {
+  const bool nf = !(isfinite(v.x) && isfinite(v.y));
+  if (nf) v = make_float2(0.0f, 0.0f);
+  const AxisDemod I = demod_axis_q(v.x, a.q, a.side, a.lik);
+  const AxisDemod Q = demod_axis_q(v.y, a.q, a.side, a.lik);
+  hidx = (uint16_t)((I.level << 8) | Q.level);
+  key = (uint32_t)I.dq * (uint32_t)I.dq + (uint32_t)Q.dq * (uint32_t)Q.dq;
+  nmask = (uint8_t)make_nmask(I, Q, nf);
+  if (a.rel) {
+    const float dI = axis_dist_f32(v.x, a.inv_d, I.amp, I.outside, a.lik);
+    const float dQ = axis_dist_f32(v.y, a.inv_d, Q.amp, Q.outside, a.lik);
+    rel = sqrtf(dI * dI + dQ * dQ);
+  }
+  if (a.y) {
+    const int64_t f = (int64_t)__umul64hi((uint64_t)s, a.Lmagic);
+    const int i = (int)(s - f * a.L);
+    const uint32_t label = ((uint32_t)gray_code(I.level) << a.m) | (uint32_t)gray_code(Q.level);
+    const uint32_t rl = __brev(label) >> (32 - 2 * a.m);
+    const int p0 = 2 * a.m * i;
+    const int wd = p0 >> 5, sh = p0 & 31;
+    const uint32_t lo = rl << sh, hi = sh ? (rl >> (32 - sh)) : 0u;
+    uint32_t* yf = a.y + f * a.NW;
+    if (wd < a.NW && lo) atomicOr(yf + wd, lo);
+    if (hi && wd + 1 < a.NW) atomicOr(yf + wd + 1, hi);
+  }
+}
+
+// Two symbols per thread: 16-byte loads, paired stores (every pointer aligned
+// for its pair type, checked by the host); otherwise one symbol per thread.
+template <bool kPaired>
 __global__ void __launch_bounds__(256) k_demod(DemodArgs a) {
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_sym; s += (int64_t)gridDim.x * blockDim.x) {
-    float2 v = a.symbols[s];
-    const bool nf = !(isfinite(v.x) && isfinite(v.y));
-    if (nf) v = make_float2(0.0f, 0.0f);
-    const AxisDemod I = demod_axis_q(v.x, a.q, a.side, a.lik);
-    const AxisDemod Q = demod_axis_q(v.y, a.q, a.side, a.lik);
-    if (a.hard_idx) a.hard_idx[s] = (uint16_t)((I.level << 8) | Q.level);
-    if (a.key) a.key[s] = (uint32_t)I.dq * (uint32_t)I.dq + (uint32_t)Q.dq * (uint32_t)Q.dq;
-    if (a.nmask) a.nmask[s] = (uint8_t)make_nmask(I, Q, nf);
-    if (a.rel) {
-      const float dI = axis_dist_f32(v.x, a.inv_d, I.amp, I.outside, a.lik);
-      const float dQ = axis_dist_f32(v.y, a.inv_d, Q.amp, Q.outside, a.lik);
-      a.rel[s] = sqrtf(dI * dI + dQ * dQ);
+  if constexpr (!kPaired) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_sym;
+         s += (int64_t)gridDim.x * blockDim.x) {
+      uint16_t h0;
+      uint32_t k0;
+      uint8_t m0;
+      float r0 = 0.0f;
+      demod_one(a, s, a.symbols[s], h0, k0, m0, r0);
+      if (a.hard_idx) a.hard_idx[s] = h0;
+      if (a.key) a.key[s] = k0;
+      if (a.nmask) a.nmask[s] = m0;
+      if (a.rel) a.rel[s] = r0;
     }
-    if (a.y) {
-      const int64_t f = s / a.L;
-      const int i = (int)(s - f * a.L);
-      const uint32_t label = ((uint32_t)gray_code(I.level) << a.m) | (uint32_t)gray_code(Q.level);
-      const uint32_t rl = __brev(label) >> (32 - 2 * a.m);
-      const int p0 = 2 * a.m * i;
-      const int wd = p0 >> 5, sh = p0 & 31;
-      const uint32_t lo = rl << sh, hi = sh ? (rl >> (32 - sh)) : 0u;
-      uint32_t* yf = a.y + f * a.NW;
-      if (wd < a.NW && lo) atomicOr(yf + wd, lo);
-      if (hi && wd + 1 < a.NW) atomicOr(yf + wd + 1, hi);
+    return;
+  }
+  const int64_t n_pairs = a.n_sym >> 1;
+  const float4* sym4 = reinterpret_cast<const float4*>(a.symbols);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= n_pairs; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = 2 * t;
+    if (t < n_pairs) {
+      const float4 v = sym4[t];
+      uint16_t h0, h1;
+      uint32_t k0, k1;
+      uint8_t m0, m1;
+      float r0 = 0.0f, r1 = 0.0f;
+      demod_one(a, s, make_float2(v.x, v.y), h0, k0, m0, r0);
+      demod_one(a, s + 1, make_float2(v.z, v.w), h1, k1, m1, r1);
+      if (a.hard_idx) reinterpret_cast<ushort2*>(a.hard_idx)[t] = make_ushort2(h0, h1);
+      if (a.key) reinterpret_cast<uint2*>(a.key)[t] = make_uint2(k0, k1);
+      if (a.nmask) reinterpret_cast<uchar2*>(a.nmask)[t] = make_uchar2(m0, m1);
+      if (a.rel) reinterpret_cast<float2*>(a.rel)[t] = make_float2(r0, r1);
+    } else if (s < a.n_sym) {  // odd count: the last symbol
+      uint16_t h0;
+      uint32_t k0;
+      uint8_t m0;
+      float r0 = 0.0f;
+      demod_one(a, s, a.symbols[s], h0, k0, m0, r0);
+      if (a.hard_idx) a.hard_idx[s] = h0;
+      if (a.key) a.key[s] = k0;
+      if (a.nmask) a.nmask[s] = m0;
+      if (a.rel) a.rel[s] = r0;
     }
   }
 }
@@ -2046,11 +2095,19 @@ extern "C" int grand_demod(const void* symbols, int64_t n_frames, int L, int M, 
   a.nmask = nmask;
   a.rel = rel;
   a.y = y;
+  a.Lmagic = UINT64_MAX / (uint64_t)L + 1;  // L >= 3 for the supported N and M
   if (y && cudaMemsetAsync(y, 0, sizeof(uint32_t) * (size_t)n_frames * (N / 32), st) != cudaSuccess)
     return GRAND_E_CUDA;
-  const int64_t blocks = (a.n_sym + 255) / 256;
+  auto aligned = [](const void* p, uintptr_t b) { return ((uintptr_t)p % b) == 0; };
+  const bool paired = aligned(a.symbols, 16) && aligned(a.hard_idx, 4) && aligned(a.key, 8) &&
+                      aligned(a.nmask, 2) && aligned(a.rel, 8);
+  const int64_t per_thread = paired ? 2 : 1;
+  const int64_t blocks = ((a.n_sym + per_thread - 1) / per_thread + 255) / 256;
   const int grid = (int)(blocks < (int64_t)sm_count() * 32 ? blocks : (int64_t)sm_count() * 32);
-  k_demod<<<grid, 256, 0, st>>>(a);
+  if (paired)
+    k_demod<true><<<grid, 256, 0, st>>>(a);
+  else
+    k_demod<false><<<grid, 256, 0, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
