@@ -817,7 +817,7 @@ def main():
                     "frac": achieved / ALU_PEAK_TOPS,
                     "traffic": NCU_SEARCH["dram_bytes_per_hard_frame"] * hard / args.steps if fresh else None,
                     "kernel": kernel, "ops_per_check": alg_words,
-                    "ops_per_check_note": "survey model: (N-K)/32 LOP3 per useful check; the kernel compares a "
+                    "ops_per_check_note": "model: (N-K)/32 LOP3 per useful check (one per syndrome word); the kernel compares a "
                                           "16-bit projection bit-sliced (16 ops per 32 checks), 4 more bits on a "
                                           "match, and verifies matches on the full syndrome",
                     "ncu_alu_pipe_active": NCU_SEARCH["alu_pipe_active"] if fresh else None,

@@ -332,9 +332,8 @@ int grand_autotune_mixed(const grand_code* const* codes, int n_codes, grand_para
                          const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
                          float N0, int64_t n_cw_words, const char* cache_path, void* stream, grand_tune_result* out);
 
-/* Serving loop (continuous batching of decode requests, spec pattern
- * "serving"). A request is one frame of any of the server's codes and any
- * constellation. Submit admits requests while a slot is free and the device
+/* Serving loop (continuous batching of decode requests). A request is one
+ * frame of any of the server's codes and any constellation. Submit admits requests while a slot is free and the device
  * memory budget allows (bytes per request: 8 L received symbols + 144 hand-off
  * record + N/8 + 5 outputs); admitted requests keep their received word
  * resident on the device (a device ring mirrored from pinned host memory)
