@@ -333,15 +333,17 @@ int grand_autotune_mixed(const grand_code* const* codes, int n_codes, grand_para
                          float N0, int64_t n_cw_words, const char* cache_path, void* stream, grand_tune_result* out);
 
 /* Serving loop (continuous batching of decode requests). A request is one
- * frame of any of the server's codes and any constellation. Submit admits requests while a slot is free and the device
- * memory budget allows (bytes per request: 8 L received symbols + 144 hand-off
- * record + N/8 + 5 outputs); admitted requests keep their received word
- * resident on the device (a device ring mirrored from pinned host memory)
- * until they complete. A worker thread launches all admitted, not yet launched
- * requests as one uneven batch on the first idle stream (grand_decode_mixed),
- * so requests arriving while batches run are decoded concurrently on other
- * streams. Results are exactly those of grand_decode_mixed / grand_decode_symbols
- * for the same frame, whatever the batch it landed in.
+ * frame of any of the server's codes and any constellation. Submit admits
+ * requests while a slot is free and the device memory budget allows (bytes
+ * per request: 8 L received symbols + 144 hand-off record + N/8 + 5
+ * outputs); admitted requests keep their received word resident on the
+ * device (a device ring mirrored from pinned host memory) until they
+ * complete. A launcher thread issues all admitted, not yet launched requests
+ * as one uneven batch on the first idle stream (the grand_decode_mixed
+ * sequence), so requests arriving while batches run are decoded concurrently
+ * on other streams; a harvester thread collects finished batches. Results
+ * are exactly those of grand_decode_mixed / grand_decode_symbols for the same
+ * frame, whatever the batch it landed in.
  *   codes             host array of n_codes code pointers (borrowed; they must
  *                     outlive the server).
  *   params            order GRAND_ORDER_QAM_NNE or QAM_NEARER, membership
