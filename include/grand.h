@@ -401,7 +401,7 @@ typedef struct grand_server grand_server;
 /* Host monotonic clock of the server, nanoseconds. */
 int64_t grand_clock_ns(void);
 /* Create a server on the current device (allocates the ring, per-stream
- * buffers, streams, and starts the worker thread). */
+ * buffers, streams, and starts the launcher and harvester threads). */
 int grand_server_create(const grand_server_cfg* cfg, grand_server** out);
 /* Admit requests in order until one does not fit; *n_admitted of them were
  * taken. Returns GRAND_OK if at least one was admitted (or n == 0),
@@ -414,7 +414,7 @@ int grand_server_poll(grand_server* srv, grand_result* out, int max, int* n);
  * timeout_ns (results stay queued for poll). */
 int grand_server_drain(grand_server* srv, int64_t timeout_ns);
 int grand_server_get_stats(grand_server* srv, grand_server_stats* out);
-/* Drain (bounded: 10 s), stop the worker and free everything. */
+/* Drain (bounded: 10 s), stop the threads and free everything. */
 int grand_server_destroy(grand_server* srv);
 
 /* grand_decode_symbols without any allocation (the paper has no counterpart:
