@@ -1,24 +1,29 @@
 // GRAND decoder kernels for sm_103a and the C ABI entry points.
 //
 // Stages of one decode call (Alg. 2 of the paper):
-//   k_prep    one warp per frame: demodulation + likelihood + neighbours
-//             (Step 1), hard word y and base syndrome s0 = H y, selection of
-//             the S' least reliable symbols (Steps 2-3), the syndrome deltas
-//             of their alternatives (Step 4), and the first TEP weights in
-//             canonical order (Step 5). Most frames finish here.
-//   k_search  persistent CTAs pull the unfinished frames from a work queue
-//             and test the rest of the TEP space in parallel (Step 5): the S'
-//             ranks are split into a low group A and a high group B, every
-//             valid alternative assignment of each group gets its partial
-//             syndrome, and a TEP (a, b) is a codeword iff
-//                 s0 ^ D_A(a) == D_B(b)            (all syndrome words).
-//             Lanes hold A entries in registers, B entries are broadcast from
-//             shared memory, and the first syndrome word is compared with one
-//             integer compare per TEP; equal first words are verified on all
-//             words. Tiles are visited in order of their lightest TEP so a
-//             frame stops after the weight of its first hit.
-//   k_ab      bit-level GRAND-AB (Sec. I), one warp per frame.
-//   k_demod   the public demodulation call (per-symbol outputs).
+//   k_prep         one warp per frame: demodulation + likelihood + neighbours
+//                  (Step 1), hard word y and base syndrome s0 = H y, selection
+//                  of the S' least reliable symbols (Steps 2-3), the syndrome
+//                  deltas of their alternatives (Step 4), and the first TEP
+//                  weights in canonical order (Step 5). Most frames finish
+//                  here; the others leave a hand-off record.
+//   k_search_warp  the search of the rest of the TEP space (Step 5), one warp
+//                  per frame from a work queue: the S' ranks are split into a
+//                  low group A and a high group B, every valid alternative
+//                  assignment of each group gets its partial syndrome, and a
+//                  TEP (a, b) is a codeword iff
+//                      s0 ^ D_A(a) == D_B(b)            (all syndrome words).
+//                  The comparison is bit-sliced on a syndrome projection (32
+//                  TEPs per 3-input logic op per projection bit), candidates
+//                  are confirmed on every word and ranked in closed form.
+//                  Sides of 5 ranks (S' <= 10) or 6 ranks (S' = 11, 12).
+//   k_search_hash  the same decision by a hash join of the two sides
+//                  (membership GRAND_MEMBERSHIP_HASH).
+//   k_search       the split with one CTA per frame (explicit split in the
+//                  launch shape): one projection compare per TEP.
+//   k_ab           bit-level GRAND-AB (Sec. I), one warp per frame.
+//   k_demod        the public demodulation call (per-symbol outputs).
+// The five-point NNE order and the per-TEP membership tests are in per_tep.cu.
 #include <stdio.h>
 
 #include <mutex>
