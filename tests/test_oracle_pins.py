@@ -140,7 +140,7 @@ def test_parity_matrix_annihilates_code(oracle_lib, N):
     assert not ((G[info] @ H.T) % 2).any()  # G_I H^T = 0
     assert gf2_rank(H) == N - K
     g = wl.rng(99, N)
-    c = wl.random_codewords(g, 2000, N, info).astype(np.int64)
+    c = wl.random_codewords(g, 10000, N, info).astype(np.int64)
     assert not ((c @ H.T) % 2).any()
 
 
