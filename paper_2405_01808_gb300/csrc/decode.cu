@@ -1896,6 +1896,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     return GRAND_OK;
   }
   keep_pool_cached();
+  NvtxRange range("grand.decode");
   const int w0 = p->tiles[2] > 0 ? (p->tiles[2] > 3 ? 3 : p->tiles[2]) : 2;
   const int Smax = p->S < Lmax ? p->S : Lmax;
   // scratch: header + one record per frame (worst case: every frame hard)
@@ -1931,7 +1932,10 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
       if (rc) break;
       cudaEventRecord(ev[0], st);
     }
-    kp<<<grid, 32 * warps, prep_smem, st>>>(a);
+    {
+      NvtxRange r_prep("grand.prep");
+      kp<<<grid, 32 * warps, prep_smem, st>>>(a);
+    }
     if (stats) cudaEventRecord(ev[1], st);
     if (cudaGetLastError() != cudaSuccess) { rc = GRAND_E_CUDA; break; }
 
@@ -1961,6 +1965,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
       s.abandon = proto.abandon;
       const int threads = p->tiles[0] > 0 ? 32 * (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 256;
       const size_t smem = search_smem_bytes(s.tabA, s.tabB, s.max_tiles, Wmax);
+      NvtxRange r_search("grand.search");
       if (launch_search(s, threads, smem, p->tiles[3], st) != GRAND_OK) {
         rc = GRAND_E_CUDA;
         break;

@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace grand {
 
@@ -70,5 +71,15 @@ inline int sm_count() {
   }
   return n;
 }
+
+// NVTX range over a host scope (enqueue of one stage), for profilers that
+// group launches by range (ncu --nvtx, Nsight Systems). Costs nothing when no
+// profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace grand

@@ -400,6 +400,7 @@ int run_per_tep(const grand_code* c, const grand_params* p, const void* symbols,
     return GRAND_OK;
   }
   keep_pool_cached();
+  NvtxRange range("grand.per_tep");
   const int m = m_of(p->M);
   TepArgs a{};
   a.code = c->dev;

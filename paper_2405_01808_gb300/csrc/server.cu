@@ -141,6 +141,7 @@ void free_server(grand_server* s) {
 
 // Issue batch b on stream si (no lock held; b.reqs was taken under it).
 int launch_batch(grand_server* s, int si, Batch& b) {
+  grand::NvtxRange range("grand.server.batch");
   StreamBuf& buf = s->sb[si];
   const int n = (int)b.reqs.size();
   for (int i = 0; i < n; ++i) {
