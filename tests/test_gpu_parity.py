@@ -317,6 +317,35 @@ def test_mixed_batch_parity(g, oracle_lib):
             assert_same(got, want, f"mixed N={n} M={M}")
 
 
+@pytest.mark.parametrize("membership", [0, 3])
+def test_mixed_batch_s12(g, oracle_lib, membership):
+    """S = 12 over an uneven batch: frames of every S' from 3 to 12 go through
+    the search for 6-rank sides (or its hash join) in one launch."""
+    import torch
+
+    Ns = (32, 64, 128, 256)
+    codes = [code_pair(g, oracle_lib, n)[0] for n in Ns]
+    info = {n: code_pair(g, oracle_lib, n)[2] for n in Ns}
+    mx = wl.mixed_frames(42, membership, 400, info, ebn0_range=(9.0, 14.0), n_choices=Ns)
+    code_idx = np.searchsorted(np.array(Ns), mx["N"])
+    desc = g.frame_desc(code_idx, mx["M"], mx["sym_offset"], mx["cw_offset"])
+    p = g.Params.make(M=0, S=12, query_cap=1 << 18, membership=membership)
+    r = g.decode_mixed(codes, p, to_dev(desc.view(np.uint8)), to_dev(mx["symbols"]), mx["n_cw_words"])
+    torch.cuda.synchronize()
+    cw, q, ab = u32(r["cw"]), u32(r["queries"]).astype(np.int64), r["abandon"].cpu().numpy()
+    for n in Ns:
+        for M in wl.QAM_ORDERS:
+            idx = np.nonzero((mx["N"] == n) & (mx["M"] == M))[0][:12]
+            if idx.size == 0:
+                continue
+            L = wl.symbols_per_frame(n, M)
+            sym = np.stack([mx["symbols"][mx["sym_offset"][f]:mx["sym_offset"][f] + L] for f in idx])
+            want = oracle_lib.decode_qam(code_pair(g, oracle_lib, n)[1], sym, M, 12, 1 << 18, threads=THREADS)
+            got = {"cw": np.stack([cw[mx["cw_offset"][f]:mx["cw_offset"][f] + n // 32] for f in idx]),
+                   "queries": q[idx], "abandon": ab[idx]}
+            assert_same(got, want, f"mixed S=12 N={n} M={M}")
+
+
 def test_mixed_rejects_bad_descriptors(g, oracle_lib):
     import torch
 
