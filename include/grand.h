@@ -58,7 +58,7 @@ typedef enum grand_status {
   GRAND_E_RANK = -2,        /* H does not have full row rank N-K */
   GRAND_E_NOMEM = -3,       /* host or device allocation failed */
   GRAND_E_CUDA = -4,        /* a CUDA runtime call failed */
-  GRAND_E_TIMEOUT = -5,     /* a bounded device wait ran out */
+  GRAND_E_TIMEOUT = -5,     /* a decode's deadline ran out (grand_stream_status) */
   GRAND_E_BUSY = -6,        /* the server cannot admit the request now */
   GRAND_E_UNSUPPORTED = -7, /* valid request outside the built limits */
 } grand_status;
@@ -138,7 +138,20 @@ typedef enum grand_lik {
  *               preparation (0..3), [3] register budget of the search kernel
  *               as resident CTAs per SM (4, 6 or 8). Results do not depend on
  *               tiles.
- *   membership  GRAND_MEMBERSHIP_*. */
+ *   membership  GRAND_MEMBERSHIP_*.
+ *   deadline_ns device-time budget of the call in nanoseconds, 0 = none
+ *               (the watchdog). The budget runs from the first look at the
+ *               device clock (%globaltimer) by any warp of the call. A search
+ *               warp that fetches a frame after the budget ran out does not
+ *               search it: the frame gets abandon = 5, cw = the hard word and
+ *               queries = the number of leading valid TEPs already tested
+ *               without a hit (those of the preparation stage; 0 for
+ *               HAMMING, QAM_NNE5 and the DELTA / ROW_PARITY tests), and the
+ *               code's status word is set for grand_stream_status. A frame
+ *               whose search has started finishes (at most one frame's search
+ *               per warp beyond the budget); frames the preparation resolves
+ *               are always decoded. Every other frame's outputs are those of
+ *               a call without deadline. */
 typedef struct grand_params {
   int32_t order;
   int32_t M;
@@ -148,6 +161,7 @@ typedef struct grand_params {
   int32_t lik_variant;
   int32_t tiles[4];
   int32_t membership;
+  int64_t deadline_ns;
 } grand_params;
 
 typedef struct grand_code grand_code;
@@ -211,6 +225,17 @@ int grand_code_destroy(grand_code* code);
 /* N and K of a code (host outputs, either may be NULL). */
 int grand_code_info(const grand_code* code, int* N, int* K);
 
+/* Status of the decodes on `code` (the watchdog's read-back): synchronises
+ * `stream`, then takes and clears the code's device status word, which every
+ * decode call on this code (any stream) sets when a frame was cut by its
+ * grand_params.deadline_ns. Returns GRAND_E_TIMEOUT if it was set,
+ * GRAND_E_CUDA if the stream reports an error, GRAND_OK otherwise. The word
+ * is taken by an atomic exchange on the device, so a flag raised by a
+ * concurrent decode on another stream is reported by exactly one read-back;
+ * grand_stream_status itself is not called concurrently on one code.
+ * Errors: GRAND_E_INVALID (NULL code). */
+int grand_stream_status(const grand_code* code, void* stream);
+
 /* Demodulation (Def. III.1, III.2; Alg. 2 Step 1) of n_frames frames of L
  * symbols each.
  *   symbols   device. M >= 4: complex64 (interleaved float32 I, Q) [n_frames][L],
@@ -249,7 +274,8 @@ int grand_demod(const void* symbols, int64_t n_frames, int L, int M, float N0, i
  *   Outputs (device): cw uint32 [n_frames][N/32] decoded word (the hard word
  *   when abandoned); queries uint32 [n_frames]; abandon uint8 [n_frames]:
  *   0 decoded, 1 abandoned (cap reached or TEPs exhausted), 2 not searched
- *   because a received value was not finite.
+ *   because a received value was not finite, 5 not searched because the
+ *   call's deadline (params->deadline_ns) had passed.
  *   stats (host, may be NULL): filled after an internal stream synchronise;
  *   pass NULL to keep the call asynchronous.
  * Errors: GRAND_E_INVALID, GRAND_E_UNSUPPORTED, GRAND_E_NOMEM, GRAND_E_CUDA. */
@@ -352,7 +378,8 @@ int grand_autotune_mixed(const grand_code* const* codes, int n_codes, grand_para
  *   max_device_bytes  memory budget of the resident request state; the
  *                     symbol ring holds max_device_bytes / 8 symbols.
  *   max_batch         frames per launch (0: max_slots).
- *   n_streams         batches in flight at once (1..16). */
+ *   n_streams         batches in flight at once (1..16).
+ *   params.deadline_ns, when nonzero, is the budget of each batch launch. */
 typedef struct grand_server_cfg {
   const grand_code* const* codes;
   int32_t n_codes;

@@ -19,7 +19,7 @@ __all__ = [
     "GrandError", "lib", "build", "polar_H", "Code", "Params", "demod", "decode_batch",
     "decode_symbols", "decode_mixed", "frame_desc", "ORDER_HAMMING", "ORDER_QAM_NNE",
     "ORDER_QAM_NEARER", "ORDER_QAM_NNE5", "MEMBERSHIP_AUTO", "MEMBERSHIP_DELTA", "MEMBERSHIP_ROW_PARITY", "MEMBERSHIP_HASH",
-    "LIK_THRESHOLD", "LIK_LITERAL",
+    "LIK_THRESHOLD", "LIK_LITERAL", "stream_status", "E_TIMEOUT", "ABANDON_DEADLINE",
 ]
 
 ORDER_HAMMING = 0
@@ -32,6 +32,8 @@ MEMBERSHIP_ROW_PARITY = 2
 MEMBERSHIP_HASH = 3
 LIK_THRESHOLD = 0
 LIK_LITERAL = 1
+E_TIMEOUT = -5         # grand_status GRAND_E_TIMEOUT
+ABANDON_DEADLINE = 5   # abandon flag of a frame cut at grand_params.deadline_ns
 
 _lock = threading.Lock()
 _lib = None
@@ -48,14 +50,15 @@ class Params(ctypes.Structure):
     _fields_ = [
         ("order", ctypes.c_int32), ("M", ctypes.c_int32), ("S", ctypes.c_int32),
         ("max_weight", ctypes.c_int32), ("query_cap", ctypes.c_int64), ("lik_variant", ctypes.c_int32),
-        ("tiles", ctypes.c_int32 * 4), ("membership", ctypes.c_int32),
+        ("tiles", ctypes.c_int32 * 4), ("membership", ctypes.c_int32), ("deadline_ns", ctypes.c_int64),
     ]
 
     @classmethod
     def make(cls, order=ORDER_QAM_NNE, M=16, S=10, max_weight=3, query_cap=1 << 20, lik_variant=LIK_THRESHOLD,
-             tiles=(0, 0, 0, 0), membership=MEMBERSHIP_AUTO):
+             tiles=(0, 0, 0, 0), membership=MEMBERSHIP_AUTO, deadline_ns=0):
         p = cls()
         p.membership = int(membership)
+        p.deadline_ns = int(deadline_ns)
         p.order, p.M, p.S, p.max_weight = int(order), int(M), int(S), int(max_weight)
         p.query_cap, p.lik_variant = int(query_cap), int(lik_variant)
         for i, t in enumerate(tiles):
@@ -93,6 +96,7 @@ def lib() -> ctypes.CDLL:
             L.grand_code_create.argtypes = [P, i32, i32, ctypes.POINTER(P)]
             L.grand_code_destroy.argtypes = [P]
             L.grand_code_info.argtypes = [P, P, P]
+            L.grand_stream_status.argtypes = [P, P]
             L.grand_demod.argtypes = [P, i64, i32, i32, ctypes.c_float, i32, P, P, P, P, P, i32, P]
             L.grand_decode_batch.argtypes = [P, P, P, P, P, P, i64, P, P, P, P, P]
             L.grand_decode_symbols.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, P, P]
@@ -112,6 +116,7 @@ def lib() -> ctypes.CDLL:
             L.grand_server_get_stats.argtypes = [P, P]
             L.grand_server_destroy.argtypes = [P]
             for name in ("grand_polar_H", "grand_code_create", "grand_code_destroy", "grand_code_info",
+                         "grand_stream_status",
                          "grand_demod", "grand_decode_batch", "grand_decode_symbols", "grand_decode_mixed",
                          "grand_decode_symbols_noalloc", "grand_plan_symbols", "grand_plan_mixed",
                          "grand_plan_launch", "grand_plan_destroy", "grand_autotune", "grand_autotune_mixed",
@@ -182,6 +187,17 @@ class Code:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def stream_status(code: Code, stream=None) -> int:
+    """grand_stream_status: synchronise the stream, then take and clear the
+    code's deadline flag. Returns 0, or E_TIMEOUT when a frame of a decode on
+    this code was cut at its deadline since the last call; raises on other
+    errors."""
+    rc = lib().grand_stream_status(code.handle, _stream(stream))
+    if rc not in (0, E_TIMEOUT):
+        _check(rc, "grand_stream_status")
+    return rc
 
 
 def _ptr(t):

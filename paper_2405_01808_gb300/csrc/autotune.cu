@@ -116,6 +116,7 @@ int tune(const std::string& key, grand_params* p, const char* cache_path, cudaSt
   for (const Candidate& c : candidates(p->S)) {
     grand_params q = *p;
     for (int i = 0; i < 4; ++i) q.tiles[i] = c.tiles[i];
+    q.deadline_ns = 0;  // time every candidate in full
     float ms = 0;
     const int rc = time_runs([&](cudaStream_t s) { return run(&q, s); }, st, 3, &ms);
     if (rc != GRAND_OK) return rc;

@@ -1,5 +1,6 @@
 // Host side of the library: version, status strings, the polar code helper
-// (Def. II.1) and the code object (column-packed H on the device).
+// (Def. II.1), the code object (column-packed H on the device) and the
+// read-back of its deadline status word.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -141,17 +142,26 @@ extern "C" int grand_code_create(const uint32_t* H, int N, int K, grand_code** o
     free(c);
     return GRAND_E_NOMEM;
   }
+  if (cudaMalloc(&c->d_status, 2 * sizeof(uint32_t)) != cudaSuccess) {
+    cudaFree(c->d_hcol);
+    cudaFree(c->d_dev);
+    free(c);
+    return GRAND_E_NOMEM;
+  }
   c->dev.hcol = c->d_hcol;
   c->dev.hf = c->d_hcol + (size_t)N * W;
   c->dev.prow = c->dev.hf + N;
   c->dev.frozen = reinterpret_cast<const uint16_t*>(c->dev.prow + R);
   c->dev.hrow = c->dev.prow + R + (R + 1) / 2;
+  c->dev.status = c->d_status;
   c->dev.N = N; c->dev.K = K; c->dev.R = R; c->dev.W = W;
   c->dev.polar = polar ? 1 : 0;
   if (cudaMemcpy(c->d_hcol, hcol.data(), hcol.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(c->d_dev, &c->dev, sizeof(grand::CodeDev), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaMemcpy(c->d_dev, &c->dev, sizeof(grand::CodeDev), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->d_status, 0, 2 * sizeof(uint32_t)) != cudaSuccess) {
     cudaFree(c->d_hcol);
     cudaFree(c->d_dev);
+    cudaFree(c->d_status);
     free(c);
     return GRAND_E_CUDA;
   }
@@ -163,6 +173,7 @@ extern "C" int grand_code_destroy(grand_code* c) {
   if (!c) return GRAND_OK;
   cudaFree(c->d_hcol);
   cudaFree(c->d_dev);
+  cudaFree(c->d_status);
   free(c);
   return GRAND_OK;
 }
@@ -172,4 +183,25 @@ extern "C" int grand_code_info(const grand_code* c, int* N, int* K) {
   if (N) *N = c->N;
   if (K) *K = c->K;
   return GRAND_OK;
+}
+
+namespace {
+// Take the code's status word with one atomic exchange (decodes on other
+// streams may set it at any time) and leave the taken value in status[1].
+__global__ void k_take_status(uint32_t* status) { status[1] = atomicExch(status, 0u); }
+}  // namespace
+
+// The watchdog's read-back: was a frame of a decode on this code cut at its
+// deadline (grand_params.deadline_ns) since the last call?
+extern "C" int grand_stream_status(const grand_code* c, void* stream) {
+  if (!c) return GRAND_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return GRAND_E_CUDA;
+  k_take_status<<<1, 1, 0, st>>>(c->d_status);
+  uint32_t h = 0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&h, c->d_status + 1, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GRAND_E_CUDA;
+  return h ? GRAND_E_TIMEOUT : GRAND_OK;
 }

@@ -67,6 +67,7 @@ struct PrepArgs {
   uint8_t* abandon;
   FrameRec* recs;
   Scratch* scr;
+  long long deadline;            // grand_params.deadline_ns (0: none)
 };
 
 struct SearchArgs {
@@ -84,7 +85,18 @@ struct SearchArgs {
   uint32_t* cw;
   uint32_t* queries;
   uint8_t* abandon;
+  long long deadline;  // grand_params.deadline_ns (0: none)
 };
+
+// A hard frame fetched after the call's deadline (lane 0): it keeps what the
+// preparation wrote (cw = the hard word, queries = the valid TEPs it tested
+// without a hit) and is marked abandon 5; the code's status word records it.
+__device__ __forceinline__ bool cut_at_deadline(const SearchArgs& a, const FrameRec* rec) {
+  if (!past_deadline(&a.scr->t0, a.deadline)) return false;
+  a.abandon[rec->frame] = 5;
+  atomicOr(a.codes[rec->code].status, 1u);
+  return true;
+}
 
 // ---------------------------------------------------------------------------
 // Per-frame preparation (one warp per frame)
@@ -480,6 +492,7 @@ __device__ __forceinline__ bool prep_frame(const PrepArgs& a, const int64_t f, c
         rec->ex[lane] = sm.ex[lane];
       }
       if (lane == 0) {
+        a.queries[f] = done_count;  // what a frame cut at the deadline reports
         rec->f0 = f0;
         rec->frame = (uint32_t)f;
         rec->code = (uint16_t)code_id;
@@ -505,6 +518,7 @@ __global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
   const int64_t gwarp = (int64_t)blockIdx.x * warps_per_block + warp_in_block;
   const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
   unsigned long long evaluated = 0;
+  if (a.deadline > 0 && lane == 0) past_deadline(&a.scr->t0, a.deadline);  // start the call's clock
   for (int64_t f = gwarp; f < a.n_frames; f += nwarps) prep_frame<WM>(a, f, sm, evaluated);
   // stats
   for (int o = 16; o; o >>= 1) evaluated += __shfl_xor_sync(kFull, evaluated, o);
@@ -688,6 +702,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_search(SearchArgs a) {
   __syncthreads();
   const SearchSmem& sm = s_layout;
   __shared__ unsigned s_frame;
+  __shared__ int s_cut;
   __shared__ unsigned cntA[kSideMax + 2], cntB[kSideMax + 2];
   __shared__ unsigned subA[1 << kSideMax], subB[1 << kSideMax], sizeA[1 << kSideMax], sizeB[1 << kSideMax];
   __shared__ unsigned s_tile_cnt[2 * kSMax + 2];
@@ -701,10 +716,18 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_search(SearchArgs a) {
   const int n_hard = (int)*(volatile unsigned*)&a.scr->n_hard;
 
   for (;;) {
-    if (threadIdx.x == 0) s_frame = atomicAdd(&a.scr->next, 1u);
+    if (threadIdx.x == 0) {
+      const unsigned f = atomicAdd(&a.scr->next, 1u);
+      s_frame = f;
+      s_cut = a.deadline > 0 && f < (unsigned)n_hard && cut_at_deadline(a, a.recs + f);
+    }
     __syncthreads();
     const unsigned fi = s_frame;
     if (fi >= (unsigned)n_hard) break;
+    if (s_cut) {
+      __syncthreads();  // everyone has read s_frame / s_cut before thread 0 rewrites them
+      continue;
+    }
     // --- load the frame ----------------------------------------------------
     if (threadIdx.x < sizeof(FrameRec) / 8)
       reinterpret_cast<unsigned long long*>(&s_rec)[threadIdx.x] =
@@ -1356,6 +1379,11 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
     if (lane == 0) fi = atomicAdd(&a.scr->next, 1u);
     fi = __shfl_sync(kFull, fi, 0);
     if (fi >= n_hard) break;
+    if (a.deadline > 0) {
+      int cut = 0;
+      if (lane == 0) cut = cut_at_deadline(a, a.recs + fi);
+      if (__shfl_sync(kFull, cut, 0)) continue;
+    }
     search_frame<kSide>(a, a.recs + fi, sl, my_eval, my_useful);
   }
   if (lane == 0) {
@@ -1417,6 +1445,11 @@ __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
     if (lane == 0) fi = atomicAdd(&a.scr->next, 1u);
     fi = __shfl_sync(kFull, fi, 0);
     if (fi >= n_hard) break;
+    if (a.deadline > 0) {
+      int cut = 0;
+      if (lane == 0) cut = cut_at_deadline(a, a.recs + fi);
+      if (__shfl_sync(kFull, cut, 0)) continue;
+    }
     const FrameRec* rec = a.recs + fi;
     const int Sp = rec->sp;
     const int w_done = rec->w_done;
@@ -1569,6 +1602,7 @@ struct AbArgs {
   uint32_t* queries;
   uint8_t* abandon;
   Scratch* scr;
+  long long deadline;  // grand_params.deadline_ns (0: none)
 };
 
 __global__ void __launch_bounds__(128) k_ab(AbArgs a) {
@@ -1602,6 +1636,16 @@ __global__ void __launch_bounds__(128) k_ab(AbArgs a) {
       if (lane == 0) { a.queries[f] = 0; a.abandon[f] = 2; }
       __syncwarp();
       continue;
+    }
+    if (a.deadline > 0) {
+      int cut = 0;
+      if (lane == 0) cut = past_deadline(&a.scr->t0, a.deadline);
+      if (__shfl_sync(kFull, cut, 0)) {  // not searched: the hard word, marked 5
+        if (lane < NW) a.cw[f * NW + lane] = y[lane];
+        if (lane == 0) { a.queries[f] = 0; a.abandon[f] = 5; atomicOr(a.code.status, 1u); }
+        __syncwarp();
+        continue;
+      }
     }
     uint32_t s0[kWMax];
     uint32_t f0 = 0;
@@ -1913,6 +1957,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     a.nearer = p->order == GRAND_ORDER_QAM_NEARER ? 1 : 0;
     a.recs = recs;
     a.scr = scr;
+    a.deadline = p->deadline_ns;
     a.Lmax = Lmax;
     a.Wmax = Wmax;
     a.w0 = w0;
@@ -1963,6 +2008,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
       s.cw = proto.cw;
       s.queries = proto.queries;
       s.abandon = proto.abandon;
+      s.deadline = p->deadline_ns;
       const int threads = p->tiles[0] > 0 ? 32 * (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 256;
       const size_t smem = search_smem_bytes(s.tabA, s.tabB, s.max_tiles, Wmax);
       NvtxRange r_search("grand.search");
@@ -1994,7 +2040,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
 
 static int check_params(const grand_params* p) {
   if (!p) return GRAND_E_INVALID;
-  if (p->query_cap < 1) return GRAND_E_INVALID;
+  if (p->query_cap < 1 || p->deadline_ns < 0) return GRAND_E_INVALID;
   if (p->lik_variant != GRAND_LIK_THRESHOLD && p->lik_variant != GRAND_LIK_LITERAL) return GRAND_E_INVALID;
   if (p->membership < GRAND_MEMBERSHIP_AUTO || p->membership > GRAND_MEMBERSHIP_HASH) return GRAND_E_INVALID;
   if (p->order == GRAND_ORDER_QAM_NNE5 && p->membership == GRAND_MEMBERSHIP_HASH) return GRAND_E_UNSUPPORTED;
@@ -2044,6 +2090,7 @@ static int run_ab(const grand_code* c, const grand_params* p, const float* sampl
     a.queries = queries;
     a.abandon = abandon;
     a.scr = scr;
+    a.deadline = p->deadline_ns;
     const int64_t want = (n_frames + 3) / 4;
     const int grid = (int)(want < (int64_t)sm_count() * 64 ? want : (int64_t)sm_count() * 64);
     k_ab<<<grid, 128, 0, st>>>(a);
@@ -2474,6 +2521,7 @@ extern "C" int grand_decode_symbols_noalloc(const grand_code* c, const grand_par
   a.abandon = abandon;
   a.recs = recs;
   a.scr = scr;
+  a.deadline = p->deadline_ns;
   a.Lmax = L;
   a.Wmax = c->W;
   a.w0 = p->tiles[2] > 0 ? (p->tiles[2] > 3 ? 3 : p->tiles[2]) : 2;
@@ -2507,6 +2555,7 @@ extern "C" int grand_decode_symbols_noalloc(const grand_code* c, const grand_par
     s.cw = cw;
     s.queries = queries;
     s.abandon = abandon;
+    s.deadline = p->deadline_ns;
     const int threads = p->tiles[0] > 0 ? 32 * (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 256;
     const size_t smem = search_smem_bytes(s.tabA, s.tabB, s.max_tiles, c->W);
     if (launch_search(s, threads, smem, p->tiles[3], st) != GRAND_OK) return GRAND_E_CUDA;

@@ -31,6 +31,30 @@ __device__ __forceinline__ uint32_t binom16(int n, int k) {
   return (k < 0 || n < 0 || k > n) ? 0u : c_binom.v[n][k];
 }
 
+// ---------------------------------------------------------------------------
+// The call's deadline (grand_params.deadline_ns). The budget runs from the
+// first look at the device clock by any warp of the call (stored in *t0, zero
+// before the call); a warp that looks after budget nanoseconds sees true.
+// Called by one lane; the caller broadcasts the answer to its warp.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool past_deadline(unsigned long long* t0, long long budget) {
+  if (budget <= 0 || !t0) return false;
+  const unsigned long long now = global_ns();
+  unsigned long long start = *(volatile unsigned long long*)t0;
+  if (start == 0) {
+    start = atomicCAS(t0, 0ull, now);
+    if (start == 0) start = now;
+  }
+  // another warp may have stamped a later time than this warp's reading
+  return now > start && now - start > (unsigned long long)budget;
+}
+
 // C(n, k) for n up to 1024, k up to 4 (bit-level orders), 64-bit: the falling
 // factorial over k!, with constant divisors (no division loop).
 __device__ __forceinline__ uint64_t binom_big(int n, int k) {

@@ -29,12 +29,15 @@ constexpr uint16_t kNoPos = 0xFFFF;  // alternative bit beyond N (padding): no s
 //          column loads; prow[r] = p_r (the projection word of row r).
 //   hrow[r * (N/32) + w] bit b = H[r][32 w + b]   (row r of H, as given to
 //          grand_code_create): the row-parity membership test.
+//   status[0]: set (atomicOr 1) by a kernel that cut a frame at the call's
+//          deadline; status[1]: where grand_stream_status takes it to.
 struct CodeDev {
   const uint32_t* hcol;
   const uint32_t* hf;
   const uint16_t* frozen;
   const uint32_t* prow;
   const uint32_t* hrow;
+  uint32_t* status;
   int32_t N, K, R, W;
   int32_t polar;
 };
@@ -60,6 +63,7 @@ struct Scratch {
   unsigned int next;                // search work-queue head
   unsigned long long evaluated;     // TEP checks executed
   unsigned long long search_useful; // valid queries answered by the search stage
+  unsigned long long t0;            // %globaltimer at the call's first look at the clock (deadline)
 };
 
 // Per-TEP decode (five-point NNE order, or a membership test other than the
@@ -82,6 +86,7 @@ struct grand_code {
   int N, K, R, W;
   uint32_t* d_hcol;                 // device, N * W words, then the N projections hf
   grand::CodeDev* d_dev;            // device copy of the CodeDev (for code tables)
+  uint32_t* d_status;               // device, 2 words (CodeDev::status)
   grand::CodeDev dev;               // host copy of the device view
   int device;                       // CUDA device the object lives on
 };

@@ -42,6 +42,8 @@ struct TepArgs {
   uint8_t* abandon;
   unsigned int* next;            // frame work queue
   unsigned long long* counters;  // [0] TEPs tested, [1] frames past query 1, [2] their queries
+  unsigned long long* t0;        // the call's clock start (deadline)
+  long long deadline;            // grand_params.deadline_ns (0: none)
 };
 
 // Shared memory of one warp (words):
@@ -155,6 +157,20 @@ __global__ void __launch_bounds__(32 * kTepWarps) k_per_tep(TepArgs a) {
       }
       __syncwarp();
       continue;
+    }
+    if (a.deadline > 0) {
+      int cut = 0;
+      if (lane == 0) cut = past_deadline(a.t0, a.deadline);
+      if (__shfl_sync(kAll, cut, 0)) {  // fetched after the deadline: the hard word, marked 5
+        if (lane < NW) a.cw[f * NW + lane] = y[lane];
+        if (lane == 0) {
+          a.queries[f] = 0;
+          a.abandon[f] = 5;
+          atomicOr(code.status, 1u);
+        }
+        __syncwarp();
+        continue;
+      }
     }
 
     // --- base syndrome s0 = H y and its projection (delta test) ----------
@@ -422,6 +438,8 @@ int run_per_tep(const grand_code* c, const grand_params* p, const void* symbols,
   if (cudaMallocAsync((void**)&scratch, 64, st) != cudaSuccess) return GRAND_E_NOMEM;
   a.next = reinterpret_cast<unsigned int*>(scratch);
   a.counters = reinterpret_cast<unsigned long long*>(scratch + 8);
+  a.t0 = reinterpret_cast<unsigned long long*>(scratch + 32);
+  a.deadline = p->deadline_ns;
   int rc = GRAND_OK;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   do {

@@ -305,7 +305,7 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
     return GRAND_E_INVALID;
   if ((cfg->params.order != GRAND_ORDER_QAM_NNE && cfg->params.order != GRAND_ORDER_QAM_NEARER) ||
       (cfg->params.membership != GRAND_MEMBERSHIP_AUTO && cfg->params.membership != GRAND_MEMBERSHIP_HASH) ||
-      cfg->params.query_cap < 1 || cfg->params.S < 0 ||
+      cfg->params.query_cap < 1 || cfg->params.deadline_ns < 0 || cfg->params.S < 0 ||
       cfg->params.S > GRAND_S_MAX)
     return GRAND_E_INVALID;
   for (int i = 0; i < cfg->n_codes; ++i)

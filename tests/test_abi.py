@@ -97,12 +97,13 @@ def test_server_and_plan_validation_without_gpu(glib):
 
 def test_params_layout_matches_header(glib):
     """grand_params as the binding lays it out: the header's field order,
-    natural alignment, 48 bytes (membership fills the tail padding)."""
+    natural alignment, 56 bytes (membership fills the slot before the 8-byte
+    deadline)."""
     P = glib.Params
-    assert ctypes.sizeof(P) == 48
+    assert ctypes.sizeof(P) == 56
     offsets = {name: getattr(P, name).offset for name, _ in P._fields_}
     assert offsets == {"order": 0, "M": 4, "S": 8, "max_weight": 12, "query_cap": 16, "lik_variant": 24,
-                       "tiles": 28, "membership": 44}
+                       "tiles": 28, "membership": 44, "deadline_ns": 48}
     text = open(os.path.join(ROOT, "include", "grand.h")).read()
     body = text[text.index("typedef struct grand_params {"):text.index("} grand_params;")]
     fields = re.findall(r"^\s*\w+\s+(\w+)(?:\[\d+\])?;", body, flags=re.M)
