@@ -724,7 +724,7 @@ def main():
         ach = dm_bytes / (statistics.mean(dm_ms) / 1e3) / 1e9
         demod = {"kernel": "k_demod", "bound": "hbm", "ms": statistics.mean(dm_ms), "bytes": dm_bytes,
                  "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": src,
-                 "note": "about 178 instructions per symbol keep the ALU pipe 79% busy (ncu): the "
+                 "note": "about 158 instructions per symbol keep the ALU pipe 81% busy (ncu): the "
                          "demodulation is issue-bound before it is HBM-bound"}
 
     # ---- the same batch decided by the hash join of the split (same outputs,

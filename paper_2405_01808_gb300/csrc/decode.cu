@@ -1749,9 +1749,11 @@ struct DemodArgs {
   uint64_t Lmagic;  // ceil(2^64 / L): frame of symbol s = high word of s * Lmagic (exact for s < 2^64 / L)
 };
 
-// One symbol of the public demodulation call (outputs that are NULL are skipped).
-__device__ __forceinline__ void demod_one(const DemodArgs& a, int64_t s, float2 v, uint16_t& hidx, uint32_t& key,
-                                          uint8_t& nmask, float& rel) {
+// One symbol of the public demodulation call (outputs that are NULL are
+// skipped); rl = the symbol's Gray label bits in transmission order (bit k =
+// label bit 2m-1-k), for the hard word.
+__device__ __forceinline__ void demod_one(const DemodArgs& a, float2 v, uint16_t& hidx, uint32_t& key, uint8_t& nmask,
+                                          float& rel, uint32_t& rl) {
   const bool nf = !(isfinite(v.x) && isfinite(v.y));
   if (nf) v = make_float2(0.0f, 0.0f);
   const AxisDemod I = demod_axis_q(v.x, a.q, a.side, a.lik);
@@ -1764,36 +1766,43 @@ __device__ __forceinline__ void demod_one(const DemodArgs& a, int64_t s, float2 
     const float dQ = axis_dist_f32(v.y, a.inv_d, Q.amp, Q.outside, a.lik);
     rel = sqrtf(dI * dI + dQ * dQ);
   }
-  if (a.y) {
-    const int64_t f = (int64_t)__umul64hi((uint64_t)s, a.Lmagic);
-    const int i = (int)(s - f * a.L);
-    const uint32_t label = ((uint32_t)gray_code(I.level) << a.m) | (uint32_t)gray_code(Q.level);
-    const uint32_t rl = __brev(label) >> (32 - 2 * a.m);
-    const int p0 = 2 * a.m * i;
-    const int wd = p0 >> 5, sh = p0 & 31;
-    const uint32_t lo = rl << sh, hi = sh ? (rl >> (32 - sh)) : 0u;
-    uint32_t* yf = a.y + f * a.NW;
-    if (wd < a.NW && lo) atomicOr(yf + wd, lo);
-    if (hi && wd + 1 < a.NW) atomicOr(yf + wd + 1, hi);
-  }
+  const uint32_t label = ((uint32_t)gray_code(I.level) << a.m) | (uint32_t)gray_code(Q.level);
+  rl = __brev(label) >> (32 - 2 * a.m);
+}
+
+// OR `bits` (at most 24) into the packed hard word yf at bit position p0;
+// words at or beyond NW (bits >= N: padding) are dropped.
+__device__ __forceinline__ void or_bits(uint32_t* yf, int NW, int p0, uint32_t bits) {
+  const int wd = p0 >> 5, sh = p0 & 31;
+  const uint32_t lo = bits << sh, hi = sh ? (bits >> (32 - sh)) : 0u;
+  if (wd < NW && lo) atomicOr(yf + wd, lo);
+  if (hi && wd + 1 < NW) atomicOr(yf + wd + 1, hi);
 }
 
 // Two symbols per thread: 16-byte loads, paired stores (every pointer aligned
 // for its pair type, checked by the host); otherwise one symbol per thread.
+// The frame of a symbol is found once per pair; the pair's label bits go into
+// the hard word with one OR when both symbols belong to the same frame.
 template <bool kPaired>
 __global__ void __launch_bounds__(256) k_demod(DemodArgs a) {
+  const int b2 = 2 * a.m;
   if constexpr (!kPaired) {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_sym;
          s += (int64_t)gridDim.x * blockDim.x) {
       uint16_t h0;
-      uint32_t k0;
+      uint32_t k0, rl0;
       uint8_t m0;
       float r0 = 0.0f;
-      demod_one(a, s, a.symbols[s], h0, k0, m0, r0);
+      demod_one(a, a.symbols[s], h0, k0, m0, r0, rl0);
       if (a.hard_idx) a.hard_idx[s] = h0;
       if (a.key) a.key[s] = k0;
       if (a.nmask) a.nmask[s] = m0;
       if (a.rel) a.rel[s] = r0;
+      if (a.y) {
+        const int64_t f = (int64_t)__umul64hi((uint64_t)s, a.Lmagic);
+        const int i = (int)(s - f * a.L);
+        or_bits(a.y + f * a.NW, a.NW, b2 * i, rl0);
+      }
     }
     return;
   }
@@ -1804,25 +1813,41 @@ __global__ void __launch_bounds__(256) k_demod(DemodArgs a) {
     if (t < n_pairs) {
       const float4 v = sym4[t];
       uint16_t h0, h1;
-      uint32_t k0, k1;
+      uint32_t k0, k1, rl0, rl1;
       uint8_t m0, m1;
       float r0 = 0.0f, r1 = 0.0f;
-      demod_one(a, s, make_float2(v.x, v.y), h0, k0, m0, r0);
-      demod_one(a, s + 1, make_float2(v.z, v.w), h1, k1, m1, r1);
+      demod_one(a, make_float2(v.x, v.y), h0, k0, m0, r0, rl0);
+      demod_one(a, make_float2(v.z, v.w), h1, k1, m1, r1, rl1);
       if (a.hard_idx) reinterpret_cast<ushort2*>(a.hard_idx)[t] = make_ushort2(h0, h1);
       if (a.key) reinterpret_cast<uint2*>(a.key)[t] = make_uint2(k0, k1);
       if (a.nmask) reinterpret_cast<uchar2*>(a.nmask)[t] = make_uchar2(m0, m1);
       if (a.rel) reinterpret_cast<float2*>(a.rel)[t] = make_float2(r0, r1);
+      if (a.y) {
+        const int64_t f = (int64_t)__umul64hi((uint64_t)s, a.Lmagic);
+        const int i = (int)(s - f * a.L);
+        uint32_t* yf = a.y + f * a.NW;
+        if (i + 1 < a.L) {
+          or_bits(yf, a.NW, b2 * i, rl0 | (rl1 << b2));
+        } else {  // the pair straddles two frames
+          or_bits(yf, a.NW, b2 * i, rl0);
+          or_bits(yf + a.NW, a.NW, 0, rl1);
+        }
+      }
     } else if (s < a.n_sym) {  // odd count: the last symbol
       uint16_t h0;
-      uint32_t k0;
+      uint32_t k0, rl0;
       uint8_t m0;
       float r0 = 0.0f;
-      demod_one(a, s, a.symbols[s], h0, k0, m0, r0);
+      demod_one(a, a.symbols[s], h0, k0, m0, r0, rl0);
       if (a.hard_idx) a.hard_idx[s] = h0;
       if (a.key) a.key[s] = k0;
       if (a.nmask) a.nmask[s] = m0;
       if (a.rel) a.rel[s] = r0;
+      if (a.y) {
+        const int64_t f = (int64_t)__umul64hi((uint64_t)s, a.Lmagic);
+        const int i = (int)(s - f * a.L);
+        or_bits(a.y + f * a.NW, a.NW, b2 * i, rl0);
+      }
     }
   }
 }

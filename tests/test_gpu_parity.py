@@ -116,6 +116,28 @@ def test_demod_parity(g, oracle_lib, M, lik):
     assert err.max() <= 1e-5
 
 
+@pytest.mark.parametrize("M", [64, 4096])
+def test_demod_unaligned_symbols(g, oracle_lib, M):
+    """Symbols starting 8 bytes past a 16-byte boundary take the one-symbol-
+    per-thread path; outputs equal the oracle's, as on the paired path."""
+    import torch
+
+    N = 512
+    L = wl.symbols_per_frame(N, M)
+    s = adversarial_symbols(M, 31, L, 7 * M)
+    flat = torch.zeros(s.size + 1, dtype=torch.complex64, device="cuda")
+    flat[1:] = torch.from_numpy(s.reshape(-1)).cuda()
+    x = flat[1:].view(31, L)
+    assert x.data_ptr() % 16 == 8
+    o = oracle_lib.demod(s, M, N)
+    r = g.demod(x, M, N)
+    torch.cuda.synchronize()
+    assert np.array_equal(r["hard_idx"].cpu().numpy().view(np.uint16), o["hard_idx"])
+    assert np.array_equal(u32(r["key"]), o["key"])
+    assert np.array_equal(r["nmask"].cpu().numpy(), o["nmask"])
+    assert np.array_equal(u32(r["y"]), o["y"])
+
+
 def test_demod_bpsk(g):
     import torch
 
