@@ -78,8 +78,8 @@ SMS, ALU_LANES, MAX_CLOCK_GHZ = 152, 64, 2.07
 ALU_PEAK_TOPS = SMS * ALU_LANES * MAX_CLOCK_GHZ / 1000.0
 # Counters of the search kernel from one ncu capture (profiles/k_search_warp_c2_small.md),
 # valid only while csrc/decode.cu is the captured source (sha256 prefix).
-NCU_SEARCH = {"sha": "454e0d1df310d358", "dram_bytes_per_hard_frame": 1547008 / 9596,
-              "alu_pipe_active": 0.735, "alu_ops_per_check": 0.75}
+NCU_SEARCH = {"sha": "d6b05f6cc03e0dae", "dram_bytes_per_hard_frame": 1552384 / 9596,
+              "alu_pipe_active": 0.732, "alu_ops_per_check": 0.77}
 
 
 def hbm_peak():
@@ -724,7 +724,7 @@ def main():
         ach = dm_bytes / (statistics.mean(dm_ms) / 1e3) / 1e9
         demod = {"kernel": "k_demod", "bound": "hbm", "ms": statistics.mean(dm_ms), "bytes": dm_bytes,
                  "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": src,
-                 "note": "about 158 instructions per symbol keep the ALU pipe 81% busy (ncu): the "
+                 "note": "about 159 instructions per symbol keep the ALU pipe 82% busy (ncu): the "
                          "demodulation is issue-bound before it is HBM-bound"}
 
     # ---- the same batch decided by the hash join of the split (same outputs,

@@ -1751,13 +1751,15 @@ struct DemodArgs {
 
 // One symbol of the public demodulation call (outputs that are NULL are
 // skipped); rl = the symbol's Gray label bits in transmission order (bit k =
-// label bit 2m-1-k), for the hard word.
+// label bit 2m-1-k), for the hard word. kM = log2(sqrt(M)) is a template
+// argument so that the level arithmetic folds into constants.
+template <int kM>
 __device__ __forceinline__ void demod_one(const DemodArgs& a, float2 v, uint16_t& hidx, uint32_t& key, uint8_t& nmask,
                                           float& rel, uint32_t& rl) {
   const bool nf = !(isfinite(v.x) && isfinite(v.y));
   if (nf) v = make_float2(0.0f, 0.0f);
-  const AxisDemod I = demod_axis_q(v.x, a.q, a.side, a.lik);
-  const AxisDemod Q = demod_axis_q(v.y, a.q, a.side, a.lik);
+  const AxisDemod I = demod_axis_q(v.x, a.q, 1 << kM, a.lik);
+  const AxisDemod Q = demod_axis_q(v.y, a.q, 1 << kM, a.lik);
   hidx = (uint16_t)((I.level << 8) | Q.level);
   key = (uint32_t)I.dq * (uint32_t)I.dq + (uint32_t)Q.dq * (uint32_t)Q.dq;
   nmask = (uint8_t)make_nmask(I, Q, nf);
@@ -1766,8 +1768,8 @@ __device__ __forceinline__ void demod_one(const DemodArgs& a, float2 v, uint16_t
     const float dQ = axis_dist_f32(v.y, a.inv_d, Q.amp, Q.outside, a.lik);
     rel = sqrtf(dI * dI + dQ * dQ);
   }
-  const uint32_t label = ((uint32_t)gray_code(I.level) << a.m) | (uint32_t)gray_code(Q.level);
-  rl = __brev(label) >> (32 - 2 * a.m);
+  const uint32_t label = ((uint32_t)gray_code(I.level) << kM) | (uint32_t)gray_code(Q.level);
+  rl = __brev(label) >> (32 - 2 * kM);
 }
 
 // OR `bits` (at most 24) into the packed hard word yf at bit position p0;
@@ -1783,9 +1785,9 @@ __device__ __forceinline__ void or_bits(uint32_t* yf, int NW, int p0, uint32_t b
 // for its pair type, checked by the host); otherwise one symbol per thread.
 // The frame of a symbol is found once per pair; the pair's label bits go into
 // the hard word with one OR when both symbols belong to the same frame.
-template <bool kPaired>
+template <bool kPaired, int kM>
 __global__ void __launch_bounds__(256) k_demod(DemodArgs a) {
-  const int b2 = 2 * a.m;
+  constexpr int b2 = 2 * kM;
   if constexpr (!kPaired) {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_sym;
          s += (int64_t)gridDim.x * blockDim.x) {
@@ -1793,7 +1795,7 @@ __global__ void __launch_bounds__(256) k_demod(DemodArgs a) {
       uint32_t k0, rl0;
       uint8_t m0;
       float r0 = 0.0f;
-      demod_one(a, a.symbols[s], h0, k0, m0, r0, rl0);
+      demod_one<kM>(a, a.symbols[s], h0, k0, m0, r0, rl0);
       if (a.hard_idx) a.hard_idx[s] = h0;
       if (a.key) a.key[s] = k0;
       if (a.nmask) a.nmask[s] = m0;
@@ -1816,8 +1818,8 @@ __global__ void __launch_bounds__(256) k_demod(DemodArgs a) {
       uint32_t k0, k1, rl0, rl1;
       uint8_t m0, m1;
       float r0 = 0.0f, r1 = 0.0f;
-      demod_one(a, make_float2(v.x, v.y), h0, k0, m0, r0, rl0);
-      demod_one(a, make_float2(v.z, v.w), h1, k1, m1, r1, rl1);
+      demod_one<kM>(a, make_float2(v.x, v.y), h0, k0, m0, r0, rl0);
+      demod_one<kM>(a, make_float2(v.z, v.w), h1, k1, m1, r1, rl1);
       if (a.hard_idx) reinterpret_cast<ushort2*>(a.hard_idx)[t] = make_ushort2(h0, h1);
       if (a.key) reinterpret_cast<uint2*>(a.key)[t] = make_uint2(k0, k1);
       if (a.nmask) reinterpret_cast<uchar2*>(a.nmask)[t] = make_uchar2(m0, m1);
@@ -1838,7 +1840,7 @@ __global__ void __launch_bounds__(256) k_demod(DemodArgs a) {
       uint32_t k0, rl0;
       uint8_t m0;
       float r0 = 0.0f;
-      demod_one(a, a.symbols[s], h0, k0, m0, r0, rl0);
+      demod_one<kM>(a, a.symbols[s], h0, k0, m0, r0, rl0);
       if (a.hard_idx) a.hard_idx[s] = h0;
       if (a.key) a.key[s] = k0;
       if (a.nmask) a.nmask[s] = m0;
@@ -1869,6 +1871,26 @@ __global__ void __launch_bounds__(256) k_demod_bpsk(const float* r, int64_t n_wo
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+
+template <int kM>
+static void launch_demod_m(const DemodArgs& a, bool paired, int grid, cudaStream_t st) {
+  if (paired)
+    k_demod<true, kM><<<grid, 256, 0, st>>>(a);
+  else
+    k_demod<false, kM><<<grid, 256, 0, st>>>(a);
+}
+
+// m = log2(sqrt(M)) in 1..6 (validated by the caller).
+static void launch_demod(const DemodArgs& a, bool paired, int grid, cudaStream_t st) {
+  switch (a.m) {
+    case 1: launch_demod_m<1>(a, paired, grid, st); break;
+    case 2: launch_demod_m<2>(a, paired, grid, st); break;
+    case 3: launch_demod_m<3>(a, paired, grid, st); break;
+    case 4: launch_demod_m<4>(a, paired, grid, st); break;
+    case 5: launch_demod_m<5>(a, paired, grid, st); break;
+    default: launch_demod_m<6>(a, paired, grid, st); break;
+  }
+}
 
 typedef void (*PrepKernel)(PrepArgs);
 static PrepKernel prep_kernel_for(int Wmax) {
@@ -2186,10 +2208,7 @@ extern "C" int grand_demod(const void* symbols, int64_t n_frames, int L, int M, 
   const int64_t per_thread = paired ? 2 : 1;
   const int64_t blocks = ((a.n_sym + per_thread - 1) / per_thread + 255) / 256;
   const int grid = (int)(blocks < (int64_t)sm_count() * 32 ? blocks : (int64_t)sm_count() * 32);
-  if (paired)
-    k_demod<true><<<grid, 256, 0, st>>>(a);
-  else
-    k_demod<false><<<grid, 256, 0, st>>>(a);
+  launch_demod(a, paired, grid, st);
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
