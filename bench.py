@@ -281,7 +281,7 @@ def run_serving(args, cfg, g, inputs):
     for rate in cfg["rates"]:
         srv = g.Server(codes, p, max_slots=1 << 18, max_device_bytes=1 << 30, max_batch=args.serve_batch, n_streams=args.serve_streams)
         # warm-up: a short burst (module load, pools)
-        w = srv.submit(reqs[:2000])
+        w = srv.submit(reqs[:20000])
         srv.drain(60.0)
         while len(srv.poll(1 << 16)):
             pass
@@ -339,7 +339,45 @@ def run_serving(args, cfg, g, inputs):
                      "server_latency_us": {"p50": float(np.percentile(srv_us, 50)),
                                            "p99": float(np.percentile(srv_us, 99)), "max": float(srv_us.max())},
                      "errors": st["errors"]})
-    return rows
+    last = res
+    # the plain one-frame-per-launch GPU path on a sample of the same requests:
+    # per request the host->device copy of its symbols, one decode call and the
+    # read-back of its result, one request after another (no batching); its
+    # outputs must equal the server's for the same requests (same BLER)
+    n_one = min(2000, F)
+    pick = np.linspace(min(50000, F - 1), F - 1, n_one).astype(np.int64)
+    pos = np.full(F, -1, dtype=np.int64)
+    pos[last["tag"].astype(np.int64)] = np.arange(len(last))
+    params_of_M = {}
+    lat_one = np.zeros(n_one)
+    equal = True
+    torch.cuda.synchronize()
+    t_all = time.perf_counter()
+    for k, f in enumerate(pick.tolist()):
+        n, M = int(inputs["N"][f]), int(inputs["M"][f])
+        L = wl.symbols_per_frame(n, M)
+        o = int(inputs["sym_offset"][f])
+        if M not in params_of_M:
+            params_of_M[M] = g.Params.make(M=M, S=cfg["S"], query_cap=cfg["cap"], membership=p.membership)
+        t1 = time.perf_counter()
+        x = torch.from_numpy(sym[o:o + L].reshape(1, L)).cuda()
+        r = g.decode_symbols(codes[code_of_N[n]], params_of_M[M], x)
+        cw_h, q_h, ab_h = r["cw"].cpu().numpy().view(np.uint32), r["queries"].cpu().numpy(), r["abandon"].cpu().numpy()
+        lat_one[k] = time.perf_counter() - t1
+        j = pos[f]
+        if j >= 0:
+            row = last[j]
+            equal &= bool(int(row["queries"]) == int(q_h[0]) and int(row["abandon"]) == int(ab_h[0])
+                          and np.array_equal(row["cw"][:n // 32], cw_h[0]))
+    span_one = time.perf_counter() - t_all
+    for c in codes:
+        c.close()
+    one = {"frames_per_s": n_one / span_one,
+           "latency_us": {"p50": float(np.percentile(lat_one, 50) * 1e6), "p99": float(np.percentile(lat_one, 99) * 1e6)},
+           "outputs_equal_server": equal,
+           "sample": f"{n_one} requests spread over the stream, each copied in, decoded by its own call and read back",
+           "note": "its frames/s is the most the plain path can serve; an offered rate above it queues without bound"}
+    return rows, one
 
 
 # -------------------------------------------------------------------------
@@ -574,7 +612,7 @@ def main():
     if cfg["kind"] == "serve":
         clocks = ClockSampler(local)
         clocks.start()
-        rows = run_serving(args, cfg, g, inputs)
+        rows, one = run_serving(args, cfg, g, inputs)
         clk = clocks.stop()
         if rank == 0:
             head = rows[-1]
@@ -585,7 +623,7 @@ def main():
                     "config": {"workload": cfg["desc"],
                                "server": f"max_slots 262144, budget 1 GiB, max_batch {args.serve_batch}, "
                                          f"{args.serve_streams} streams"},
-                    "latency_us": head["latency_us"], "rates": rows, "clocks": clk,
+                    "latency_us": head["latency_us"], "rates": rows, "one_frame_per_launch": one, "clocks": clk,
                     "e2e": {"value": head["frames_per_s"], "unit": "frames/s",
                             "h2d_bytes_per_step": int(inputs["symbols"].nbytes),
                             "d2h_bytes_per_step": int(len(inputs["N"]) * 160)},

@@ -1974,6 +1974,25 @@ static int launch_search(const SearchArgs& s, int threads, size_t smem, int vari
   }
 }
 
+// Load every kernel the symbol-level decode can launch (with lazy module
+// loading a kernel is otherwise loaded at its first launch, which puts a
+// one-time stall of milliseconds into the first batch that needs it).
+int preload_qam_kernels() {
+  const void* kernels[] = {
+      (const void*)k_prep<1>, (const void*)k_prep<2>, (const void*)k_prep<4>, (const void*)k_prep<8>,
+      (const void*)k_prep<16>,
+      (const void*)k_search_warp<4, kWarpSideMax>, (const void*)k_search_warp<6, kWarpSideMax>,
+      (const void*)k_search_warp<8, kWarpSideMax>, (const void*)k_search_warp<4, kWarpSideMax + 1>,
+      (const void*)k_search_warp<6, kWarpSideMax + 1>, (const void*)k_search_warp<8, kWarpSideMax + 1>,
+      (const void*)k_search_hash<kWarpSideMax>, (const void*)k_search_hash<kWarpSideMax + 1>,
+      (const void*)k_search<4>, (const void*)k_search<6>, (const void*)k_search<8>};
+  for (const void* k : kernels) {
+    cudaFuncAttributes attr;
+    if (cudaFuncGetAttributes(&attr, k) != cudaSuccess) return GRAND_E_CUDA;
+  }
+  return GRAND_OK;
+}
+
 #define CU(x)                                   \
   do {                                          \
     if ((x) != cudaSuccess) return GRAND_E_CUDA; \

@@ -72,6 +72,10 @@ struct Scratch {
 int run_per_tep(const grand_code* c, const grand_params* p, const void* symbols, int64_t n_frames, uint32_t* cw,
                 uint32_t* queries, uint8_t* abandon, grand_stats* stats, cudaStream_t st);
 
+// Load every kernel of the symbol-level decode now (the serving loop calls it
+// at creation so that no batch pays a lazy module load).
+int preload_qam_kernels();
+
 // grand_decode_mixed on a code table already resident on the device (the
 // serving loop keeps one for its lifetime). The caller has validated params
 // (QAM order, membership AUTO); Lmax / Wmax bound L and W over the table.

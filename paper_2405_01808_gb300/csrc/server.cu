@@ -370,6 +370,10 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
       cudaFreeAsync(warm, s->sb[0].stream);
     cudaStreamSynchronize(s->sb[0].stream);
   }
+  if (grand::preload_qam_kernels() != GRAND_OK) {
+    free_server(s);
+    return GRAND_E_CUDA;
+  }
   s->launcher = std::thread(launcher_main, s);
   s->harvester = std::thread(harvester_main, s);
   *out = s;
