@@ -16,7 +16,7 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "GrandError", "lib", "build", "polar_H", "Code", "Params", "demod", "decode_batch",
+    "GrandError", "GrandArgumentError", "lib", "build", "polar_H", "Code", "Params", "demod", "decode_batch",
     "decode_symbols", "decode_mixed", "frame_desc", "ORDER_HAMMING", "ORDER_QAM_NNE",
     "ORDER_QAM_NEARER", "ORDER_QAM_NNE5", "MEMBERSHIP_AUTO", "MEMBERSHIP_DELTA", "MEMBERSHIP_ROW_PARITY", "MEMBERSHIP_HASH",
     "LIK_THRESHOLD", "LIK_LITERAL", "stream_status", "E_TIMEOUT", "ABANDON_DEADLINE",
@@ -44,6 +44,15 @@ class GrandError(RuntimeError):
         msg = lib().grand_status_string(status).decode() if _lib is not None else str(status)
         super().__init__(f"{where}: {msg} ({status})")
         self.status = status
+
+
+class GrandArgumentError(GrandError, ValueError):
+    """An argument the binding rejects before it calls the library (a tensor
+    of the wrong type, size or device): status GRAND_E_INVALID."""
+
+    def __init__(self, msg: str):
+        RuntimeError.__init__(self, msg)
+        self.status = -1
 
 
 class Params(ctypes.Structure):
@@ -214,23 +223,69 @@ def _stream(stream):
 def _require_cuda(*ts):
     for t in ts:
         if t is not None and not t.is_cuda:
-            raise ValueError("tensors must live on the CUDA device")
+            raise GrandArgumentError("tensors must live on the CUDA device")
         if t is not None and not t.is_contiguous():
-            raise ValueError("tensors must be contiguous")
+            raise GrandArgumentError("tensors must be contiguous")
+
+
+# The library receives bare device pointers and trusts their sizes, so the
+# binding checks every tensor's element type and element count against what
+# the call will read or write (before any library call).
+def _symbols_per_frame(N: int, M: int) -> int:
+    if M == 2:
+        return N
+    m = (int(M).bit_length() - 1) >> 1
+    if M < 4 or (1 << (2 * m)) != M:
+        raise GrandArgumentError(f"M = {M} is not a square constellation 4^m (or 2 for BPSK)")
+    return -(-N // (2 * m))
+
+
+def _dtypes(*names):
+    import torch
+
+    return tuple(getattr(torch, n) for n in names if hasattr(torch, n))
+
+
+def _need(t, name, dtypes, numel, exact=False):
+    if t is None:
+        return
+    if t.dtype not in dtypes:
+        raise GrandArgumentError(f"{name}: dtype {t.dtype}; expected {', '.join(str(d) for d in dtypes)}")
+    if (t.numel() != numel) if exact else (t.numel() < numel):
+        raise GrandArgumentError(f"{name}: {t.numel()} elements; {'exactly' if exact else 'at least'} {numel} expected")
+
+
+def _check_symbols(symbols, M: int, L: int):
+    """Received symbols of F frames: complex64 [F][L] (or float32 [F][L][2]);
+    BPSK float32 [F][N]. Returns F."""
+    F = symbols.shape[0] if symbols.dim() > 0 else 0
+    if M == 2:
+        _need(symbols, "symbols", _dtypes("float32"), F * L, exact=True)
+    elif symbols.is_complex():
+        _need(symbols, "symbols", _dtypes("complex64"), F * L, exact=True)
+    else:
+        _need(symbols, "symbols", _dtypes("float32", "complex64"), 2 * F * L, exact=True)
+    return F
+
+
+def _check_outputs(F, N, cw, queries, abandon):
+    _need(cw, "cw", _dtypes("int32", "uint32"), F * (N // 32))
+    _need(queries, "queries", _dtypes("int32", "uint32"), F)
+    _need(abandon, "abandon", _dtypes("uint8"), F)
+
+
+def _params_M(params) -> int:
+    return 2 if params.order == ORDER_HAMMING else int(params.M)
 
 
 def demod(symbols, M: int, N: int, N0: float = 1.0, lik_variant: int = LIK_THRESHOLD, outputs=None, stream=None):
     """grand_demod. symbols: complex64 (F, L) for QAM, float32 (F, N) for BPSK."""
     import torch
 
+    L = _symbols_per_frame(N, M)
+    F = _check_symbols(symbols, M, L)
     _require_cuda(symbols)
-    F = symbols.shape[0]
-    if M == 2:
-        L = N
-        sym = symbols
-    else:
-        L = symbols.shape[1]
-        sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
+    sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
     dev = symbols.device
     if outputs is None:
         outputs = {"y": torch.empty((F, N // 32), dtype=torch.int32, device=dev)}
@@ -245,6 +300,12 @@ def demod(symbols, M: int, N: int, N0: float = 1.0, lik_variant: int = LIK_THRES
             })
     o = outputs
     _require_cuda(*o.values())
+    _need(o.get("y"), "y", _dtypes("int32", "uint32"), F * (N // 32))
+    n_per = F * (N if M == 2 else L)
+    _need(o.get("nmask"), "nmask", _dtypes("uint8"), n_per)
+    _need(o.get("hard_idx"), "hard_idx", _dtypes("int16", "uint16"), F * L)
+    _need(o.get("key"), "key", _dtypes("int32", "uint32"), F * L)
+    _need(o.get("rel"), "rel", _dtypes("float32"), F * L)
     rc = lib().grand_demod(_ptr(sym), F, L, M, float(N0), int(lik_variant), _ptr(o.get("hard_idx")), _ptr(o.get("key")),
                            _ptr(o.get("nmask")), _ptr(o.get("rel")), _ptr(o.get("y")), N, _stream(stream))
     _check(rc, "grand_demod")
@@ -277,8 +338,21 @@ def _result(cw, queries, abandon, st, want_stats):
 def decode_batch(code: Code, params: Params, y, hard_idx=None, key=None, nmask=None, cw=None, queries=None,
                  abandon=None, stats: bool = False, stream=None):
     """grand_decode_batch on demodulated frames (outputs of `demod`)."""
-    _require_cuda(y, hard_idx, key, nmask)
     F = y.shape[0]
+    M = _params_M(params)
+    L = _symbols_per_frame(code.N, M)
+    _need(y, "y", _dtypes("int32", "uint32"), F * (code.N // 32), exact=True)
+    if M == 2:
+        _need(nmask, "nmask", _dtypes("uint8"), F * code.N)
+    else:
+        for t, name in ((hard_idx, "hard_idx"), (key, "key"), (nmask, "nmask")):
+            if t is None:
+                raise GrandArgumentError(f"{name} is required for the symbol-level orders")
+        _need(hard_idx, "hard_idx", _dtypes("int16", "uint16"), F * L)
+        _need(key, "key", _dtypes("int32", "uint32"), F * L)
+        _need(nmask, "nmask", _dtypes("uint8"), F * L)
+    _check_outputs(F, code.N, cw, queries, abandon)
+    _require_cuda(y, hard_idx, key, nmask, cw, queries, abandon)
     cw, queries, abandon = _outputs(F, code.N, y.device, cw, queries, abandon)
     st = Stats()
     rc = lib().grand_decode_batch(code.handle, ctypes.byref(params), _ptr(hard_idx), _ptr(key), _ptr(nmask), _ptr(y), F,
@@ -293,8 +367,9 @@ def decode_symbols(code: Code, params: Params, symbols, N0: float = 1.0, cw=None
     """grand_decode_symbols: demodulate and decode in one pass."""
     import torch
 
-    _require_cuda(symbols)
-    F = symbols.shape[0]
+    F = _check_symbols(symbols, _params_M(params), _symbols_per_frame(code.N, _params_M(params)))
+    _check_outputs(F, code.N, cw, queries, abandon)
+    _require_cuda(symbols, cw, queries, abandon)
     sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
     cw, queries, abandon = _outputs(F, code.N, symbols.device, cw, queries, abandon)
     st = Stats()
@@ -310,15 +385,35 @@ def frame_desc(code_idx, M, sym_offset, cw_offset) -> np.ndarray:
     return d
 
 
+def _check_mixed(desc, symbols):
+    """Descriptor bytes (a whole number of FRAME_DESC_DTYPE records) and flat
+    complex64 symbols (or float32 pairs); returns (frames, symbols)."""
+    _need(desc, "desc", _dtypes("uint8"), desc.numel())
+    if desc.numel() % FRAME_DESC_DTYPE.itemsize:
+        raise GrandArgumentError(f"desc: {desc.numel()} bytes is not a whole number of "
+                                 f"{FRAME_DESC_DTYPE.itemsize}-byte records")
+    if symbols.is_complex():
+        _need(symbols, "symbols", _dtypes("complex64"), 0)
+        n_sym = symbols.numel()
+    else:
+        _need(symbols, "symbols", _dtypes("float32"), 0)
+        if symbols.numel() % 2:
+            raise GrandArgumentError("symbols: float32 pairs expected (an even number of elements)")
+        n_sym = symbols.numel() // 2
+    return desc.numel() // FRAME_DESC_DTYPE.itemsize, n_sym
+
+
 def decode_mixed(codes, params: Params, desc, symbols, n_cw_words: int, N0: float = 1.0, cw=None, queries=None,
                  abandon=None, stats: bool = False, stream=None):
     """grand_decode_mixed. desc: device uint8 tensor holding FRAME_DESC_DTYPE records."""
     import torch
 
-    _require_cuda(desc, symbols)
-    F = desc.numel() // FRAME_DESC_DTYPE.itemsize
+    F, n_sym = _check_mixed(desc, symbols)
+    _need(cw, "cw", _dtypes("int32", "uint32"), n_cw_words)
+    _need(queries, "queries", _dtypes("int32", "uint32"), F)
+    _need(abandon, "abandon", _dtypes("uint8"), F)
+    _require_cuda(desc, symbols, cw, queries, abandon)
     sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
-    n_sym = symbols.numel() if symbols.is_complex() else symbols.numel() // 2
     dev = symbols.device
     if cw is None:
         cw = torch.empty(n_cw_words, dtype=torch.int32, device=dev)
@@ -345,8 +440,12 @@ def decode_symbols_noalloc(code: Code, params: Params, symbols, cw, queries, aba
     device must not overlap in time (they share one fixed scratch array)."""
     import torch
 
+    F = _check_symbols(symbols, _params_M(params), _symbols_per_frame(code.N, _params_M(params)))
+    for t, name in ((cw, "cw"), (queries, "queries"), (abandon, "abandon")):
+        if t is None:
+            raise GrandArgumentError(f"{name} is required")
+    _check_outputs(F, code.N, cw, queries, abandon)
     _require_cuda(symbols, cw, queries, abandon)
-    F = symbols.shape[0]
     sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
     rc = lib().grand_decode_symbols_noalloc(code.handle, ctypes.byref(params), _ptr(sym), F, float(N0), _ptr(cw),
                                             _ptr(queries), _ptr(abandon), _stream(stream))
@@ -380,6 +479,11 @@ class Plan:
 def plan_symbols(code: Code, params: Params, symbols, cw, queries, abandon, N0: float = 1.0) -> Plan:
     import torch
 
+    F = _check_symbols(symbols, _params_M(params), _symbols_per_frame(code.N, _params_M(params)))
+    for t, name in ((cw, "cw"), (queries, "queries"), (abandon, "abandon")):
+        if t is None:
+            raise GrandArgumentError(f"{name} is required")
+    _check_outputs(F, code.N, cw, queries, abandon)
     _require_cuda(symbols, cw, queries, abandon)
     sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
     h = ctypes.c_void_p()
@@ -392,10 +496,12 @@ def plan_symbols(code: Code, params: Params, symbols, cw, queries, abandon, N0: 
 def plan_mixed(codes, params: Params, desc, symbols, cw, queries, abandon, N0: float = 1.0) -> Plan:
     import torch
 
+    F, n_sym = _check_mixed(desc, symbols)
+    _need(cw, "cw", _dtypes("int32", "uint32"), 0)
+    _need(queries, "queries", _dtypes("int32", "uint32"), F)
+    _need(abandon, "abandon", _dtypes("uint8"), F)
     _require_cuda(desc, symbols, cw, queries, abandon)
-    F = desc.numel() // FRAME_DESC_DTYPE.itemsize
     sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
-    n_sym = symbols.numel() if symbols.is_complex() else symbols.numel() // 2
     arr = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
     h = ctypes.c_void_p()
     rc = lib().grand_plan_mixed(arr, len(codes), ctypes.byref(params), _ptr(desc), F, _ptr(sym), n_sym, float(N0),
@@ -417,6 +523,7 @@ def autotune(code: Code, params: Params, symbols, N0: float = 1.0, cache_path: s
     """grand_autotune: picks params.tiles on a sample batch (in place)."""
     import torch
 
+    _check_symbols(symbols, _params_M(params), _symbols_per_frame(code.N, _params_M(params)))
     _require_cuda(symbols)
     sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
     r = TuneResult()
@@ -430,10 +537,9 @@ def autotune_mixed(codes, params: Params, desc, symbols, n_cw_words: int, N0: fl
                    cache_path: str | None = None, stream=None):
     import torch
 
+    F, n_sym = _check_mixed(desc, symbols)
     _require_cuda(desc, symbols)
-    F = desc.numel() // FRAME_DESC_DTYPE.itemsize
     sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
-    n_sym = symbols.numel() if symbols.is_complex() else symbols.numel() // 2
     arr = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
     r = TuneResult()
     rc = lib().grand_autotune_mixed(arr, len(codes), ctypes.byref(params), _ptr(desc), F, _ptr(sym), n_sym, float(N0),

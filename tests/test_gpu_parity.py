@@ -154,15 +154,25 @@ def test_demod_bpsk(g):
 
 
 def test_demod_rejects_bad_arguments(g):
+    import ctypes
+
     import torch
 
     s = torch.zeros((2, 32), dtype=torch.complex64, device="cuda")
     with pytest.raises(g.GrandError):
         g.demod(s, 16, 128, N0=0.0)
-    with pytest.raises(g.GrandError):
+    with pytest.raises(g.GrandArgumentError):  # the binding's own checks
         g.demod(s, 8, 128)
-    with pytest.raises(g.GrandError):
+    with pytest.raises(g.GrandArgumentError):
         g.demod(s, 64, 128)  # L must be ceil(128/6) = 22
+    # the library's checks, called directly (as a C caller would)
+    y = torch.zeros((2, 4), dtype=torch.int32, device="cuda")
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    L = g.lib()
+    assert L.grand_demod(P(s), 2, 32, 8, 1.0, 0, None, None, None, None, P(y), 128, None) == -1  # M = 8
+    assert L.grand_demod(P(s), 2, 32, 64, 1.0, 0, None, None, None, None, P(y), 128, None) == -1  # L != 22
+    assert L.grand_demod(P(s), 2, 32, 16, float("nan"), 0, None, None, None, None, P(y), 128, None) == -1
+    assert L.grand_demod(P(s), 2, 32, 16, 1.0, 2, None, None, None, None, P(y), 128, None) == -1  # lik variant
 
 
 # ---------------------------------------------------------------------------
