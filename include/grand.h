@@ -467,6 +467,27 @@ int grand_decode_symbols_noalloc(const grand_code* code, const grand_params* par
                                  int64_t n_frames, float N0, uint32_t* cw, uint32_t* queries, uint8_t* abandon,
                                  void* stream);
 
+/* Decode frames held in host memory (the decode of grand_decode_symbols with
+ * the transfers included and overlapped). The batch is cut into chunks of
+ * chunk_frames frames (0: a quarter of the batch, at least 65,536) that
+ * alternate between two internal streams with their own device buffers; on
+ * each, a chunk's symbols are copied to the device, decoded and its results
+ * copied back, so that the copies of one chunk run while another is decoded.
+ *   h_symbols  host, as `symbols` of grand_decode_symbols (complex64 [n][L],
+ *              or float32 [n][N] for the HAMMING order).
+ *   h_cw, h_queries, h_abandon  host outputs, as for grand_decode_symbols.
+ *   Host buffers should be page-locked (cudaHostAlloc / cudaHostRegister):
+ *   copies from pageable memory are staged by the driver and overlap less.
+ *   stream     the work starts after what is queued on it; on return every
+ *              result is in host memory and `stream` is ordered after the
+ *              pipeline (the call is synchronous).
+ * Each chunk is one decode call: a deadline (params->deadline_ns) applies per
+ * chunk. Errors: as grand_decode_symbols (arguments checked before any device
+ * work), GRAND_E_NOMEM, GRAND_E_CUDA. */
+int grand_decode_symbols_host(const grand_code* code, const grand_params* params, const void* h_symbols,
+                              int64_t n_frames, float N0, uint32_t* h_cw, uint32_t* h_queries, uint8_t* h_abandon,
+                              int64_t chunk_frames, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

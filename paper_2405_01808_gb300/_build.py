@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libgrand.so")
-SOURCES = ["code.cu", "decode.cu", "per_tep.cu", "autotune.cu", "server.cu"]
+SOURCES = ["code.cu", "decode.cu", "per_tep.cu", "autotune.cu", "server.cu", "host_pipeline.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -84,3 +84,10 @@ def test_mixed_batch_records():
     expect("cw", g.decode_mixed, [CODE], g.Params.make(M=0, S=10), desc, sym, 8,
            cw=torch.zeros(7, dtype=torch.int32))
     expect("CUDA device", g.decode_mixed, [CODE], g.Params.make(M=0, S=10), desc, sym, 8)
+
+
+def test_host_memory_call():
+    p = g.Params.make(M=16, S=10)
+    expect("exactly 128", g.decode_symbols_host, CODE, p, torch.zeros((4, 31), dtype=torch.complex64))
+    expect("queries: dtype", g.decode_symbols_host, CODE, p, torch.zeros((4, 32), dtype=torch.complex64),
+           queries=torch.zeros(4, dtype=torch.int64))
