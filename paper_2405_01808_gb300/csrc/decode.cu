@@ -508,8 +508,12 @@ __device__ __forceinline__ bool prep_frame(const PrepArgs& a, const int64_t f, c
   return false;
 }
 
+// Resident CTAs per SM: 12 for syndromes of at most two words (the register
+// bound then costs a few spilled words but the latency-bound preparation
+// gains warps); 8 for the longer syndromes, whose per-lane arrays would spill
+// heavily at 40 registers.
 template <int WM>
-__global__ void __launch_bounds__(128, 12) k_prep(PrepArgs a) {
+__global__ void __launch_bounds__(128, WM <= 2 ? 12 : 8) k_prep(PrepArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp_in_block = threadIdx.x >> 5;
