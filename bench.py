@@ -797,21 +797,25 @@ def main():
                              "not a per-TEP test, so not counted as checks"}
 
     # ---- e2e: the same decode from pinned host buffers, copies in the timed
-    #      region. Uniform batches go through the library's host-memory call
-    #      (grand_decode_symbols_host: chunks on two streams, copies overlapped
-    #      with decoding); the uneven mix copies around its device call.
+    #      region, through the library's host-memory calls
+    #      (grand_decode_symbols_host / grand_decode_mixed_host: chunks on two
+    #      streams, copies overlapped with decoding).
     h_cw = torch.empty(n_cw, dtype=torch.int32).pin_memory()
     h_q = torch.empty(n_frames, dtype=torch.int32).pin_memory()
     h_ab = torch.empty(n_frames, dtype=torch.uint8).pin_memory()
     d_sym2 = torch.empty_like(d_sym)
-    host_api = cfg["kind"] in ("qam", "ab")
+    host_api = cfg["kind"] in ("qam", "ab", "mixed")
+    if cfg["kind"] == "mixed":  # the descriptors are host input too, page-locked like the symbols
+        h_desc = torch.from_numpy(desc.view(np.uint8)).pin_memory()
     e2e_ms = []
     for _ in range(max(2, min(args.steps, 5))):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        if host_api:
+        if host_api and cfg["kind"] == "mixed":
+            g.decode_mixed_host(codes, p, h_desc, h_sym, n_cw, cw=h_cw, queries=h_q, abandon=h_ab, stream=stream)
+        elif host_api:
             g.decode_symbols_host(codes[0], p, h_sym, cw=h_cw, queries=h_q, abandon=h_ab, stream=stream)
         else:
             d_sym2.copy_(h_sym, non_blocking=True)
@@ -913,8 +917,8 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "checks/s", "h2d_bytes_per_step": int(h_sym.numel() * h_sym.element_size()),
                     "d2h_bytes_per_step": int(n_cw * 4 + n_frames * 5), "ms_per_step": statistics.mean(e2e_ms),
-                    "api": ("grand_decode_symbols_host (chunks on two streams, copies overlapped with decoding)"
-                            if host_api else "copies around grand_decode_mixed on one stream"),
+                    "api": ("grand_decode_mixed_host" if cfg["kind"] == "mixed" else "grand_decode_symbols_host")
+                           + " (chunks on two streams, copies overlapped with decoding)",
                     "outputs_equal_device": e2e_equal},
             "gpu_launches": 2 * args.steps if cfg["kind"] != "ab" else args.steps,
             "graph": bool(graph_steps),

@@ -488,6 +488,27 @@ int grand_decode_symbols_host(const grand_code* code, const grand_params* params
                               int64_t n_frames, float N0, uint32_t* h_cw, uint32_t* h_queries, uint8_t* h_abandon,
                               int64_t chunk_frames, void* stream);
 
+/* Decode an uneven batch held in host memory (grand_decode_mixed with the
+ * transfers included and overlapped the same way).
+ *   h_desc     host array of n_frames descriptors (offsets into h_symbols and
+ *              h_cw, as for grand_decode_mixed).
+ *   h_symbols  host complex64, n_symbols entries; h_cw host, n_cw_words words;
+ *              h_queries, h_abandon host, n_frames entries. Every host buffer,
+ *              the descriptors included, should be page-locked: a copy from
+ *              pageable memory holds the calling thread until it is staged.
+ * Chunks are runs of consecutive frames; they need the frames packed in
+ * increasing order (each frame's symbols and output words after the previous
+ * frame's, inside the arrays). Any other layout is decoded as one chunk over
+ * the whole arrays (no overlap). A chunk's descriptors are made relative to
+ * its own ranges on the device; a descriptor that is invalid there is
+ * reported as by grand_decode_mixed (abandon 3). Arguments are checked first
+ * (by a call of grand_decode_mixed without frames). Errors: as
+ * grand_decode_mixed, GRAND_E_NOMEM, GRAND_E_CUDA. */
+int grand_decode_mixed_host(const grand_code* const* codes, int n_codes, const grand_params* params,
+                            const grand_frame_desc* h_desc, int64_t n_frames, const void* h_symbols, int64_t n_symbols,
+                            float N0, uint32_t* h_cw, int64_t n_cw_words, uint32_t* h_queries, uint8_t* h_abandon,
+                            int64_t chunk_frames, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,7 @@ from . import _build
 
 __all__ = [
     "GrandError", "GrandArgumentError", "lib", "build", "polar_H", "Code", "Params", "demod", "decode_batch",
-    "decode_symbols", "decode_symbols_host", "decode_mixed", "frame_desc", "ORDER_HAMMING", "ORDER_QAM_NNE",
+    "decode_symbols", "decode_symbols_host", "decode_mixed", "decode_mixed_host", "frame_desc", "ORDER_HAMMING", "ORDER_QAM_NNE",
     "ORDER_QAM_NEARER", "ORDER_QAM_NNE5", "MEMBERSHIP_AUTO", "MEMBERSHIP_DELTA", "MEMBERSHIP_ROW_PARITY", "MEMBERSHIP_HASH",
     "LIK_THRESHOLD", "LIK_LITERAL", "stream_status", "E_TIMEOUT", "ABANDON_DEADLINE",
 ]
@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
             L.grand_decode_mixed.argtypes = [P, i32, P, P, i64, P, i64, ctypes.c_float, P, i64, P, P, P, P]
             L.grand_decode_symbols_noalloc.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, P]
             L.grand_decode_symbols_host.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, i64, P]
+            L.grand_decode_mixed_host.argtypes = [P, i32, P, P, i64, P, i64, ctypes.c_float, P, i64, P, P, i64, P]
             L.grand_plan_symbols.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, ctypes.POINTER(P)]
             L.grand_plan_mixed.argtypes = [P, i32, P, P, i64, P, i64, ctypes.c_float, P, i64, P, P, ctypes.POINTER(P)]
             L.grand_plan_launch.argtypes = [P, P]
@@ -128,7 +129,8 @@ def lib() -> ctypes.CDLL:
             for name in ("grand_polar_H", "grand_code_create", "grand_code_destroy", "grand_code_info",
                          "grand_stream_status",
                          "grand_demod", "grand_decode_batch", "grand_decode_symbols", "grand_decode_mixed",
-                         "grand_decode_symbols_noalloc", "grand_decode_symbols_host", "grand_plan_symbols", "grand_plan_mixed",
+                         "grand_decode_symbols_noalloc", "grand_decode_symbols_host", "grand_decode_mixed_host",
+                         "grand_plan_symbols", "grand_plan_mixed",
                          "grand_plan_launch", "grand_plan_destroy", "grand_autotune", "grand_autotune_mixed",
                          "grand_server_create", "grand_server_submit", "grand_server_poll", "grand_server_drain",
                          "grand_server_get_stats", "grand_server_destroy"):
@@ -429,6 +431,38 @@ def decode_mixed(codes, params: Params, desc, symbols, n_cw_words: int, N0: floa
                                   ctypes.byref(st) if stats else None, _stream(stream))
     _check(rc, "grand_decode_mixed")
     return _result(cw, queries, abandon, st, stats)
+
+
+def decode_mixed_host(codes, params: Params, desc, symbols, n_cw_words: int, N0: float = 1.0, cw=None, queries=None,
+                      abandon=None, chunk_frames: int = 0, stream=None):
+    """grand_decode_mixed_host: an uneven batch in host memory. desc: a
+    FRAME_DESC_DTYPE numpy array (or its bytes as a CPU uint8 tensor);
+    symbols: CPU complex64 tensor (best page-locked); returns host tensors."""
+    import torch
+
+    if isinstance(desc, np.ndarray):
+        desc = torch.from_numpy(np.ascontiguousarray(desc).view(np.uint8))
+    F, n_sym = _check_mixed(desc, symbols)
+    _need(cw, "cw", _dtypes("int32", "uint32"), n_cw_words)
+    _need(queries, "queries", _dtypes("int32", "uint32"), F)
+    _need(abandon, "abandon", _dtypes("uint8"), F)
+    for t in (desc, symbols, cw, queries, abandon):
+        if t is not None and (t.is_cuda or not t.is_contiguous()):
+            raise GrandArgumentError("host tensors (contiguous, on the CPU) expected")
+    pin = torch.cuda.is_available()
+    if cw is None:
+        cw = torch.zeros(n_cw_words, dtype=torch.int32, pin_memory=pin)
+    if queries is None:
+        queries = torch.empty(F, dtype=torch.int32, pin_memory=pin)
+    if abandon is None:
+        abandon = torch.empty(F, dtype=torch.uint8, pin_memory=pin)
+    sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
+    arr = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
+    rc = lib().grand_decode_mixed_host(arr, len(codes), ctypes.byref(params), _ptr(desc), F, _ptr(sym), n_sym,
+                                       float(N0), _ptr(cw), n_cw_words, _ptr(queries), _ptr(abandon),
+                                       int(chunk_frames), _stream(stream))
+    _check(rc, "grand_decode_mixed_host")
+    return {"cw": cw, "queries": queries, "abandon": abandon}
 
 
 NOALLOC_MAX_FRAMES = 16384

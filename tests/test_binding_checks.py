@@ -91,3 +91,13 @@ def test_host_memory_call():
     expect("exactly 128", g.decode_symbols_host, CODE, p, torch.zeros((4, 31), dtype=torch.complex64))
     expect("queries: dtype", g.decode_symbols_host, CODE, p, torch.zeros((4, 32), dtype=torch.complex64),
            queries=torch.zeros(4, dtype=torch.int64))
+
+
+def test_mixed_host_memory_call():
+    desc = g.frame_desc([0, 0], [16, 16], [0, 32], [0, 4])
+    p = g.Params.make(M=0, S=10)
+    expect("whole number", g.decode_mixed_host, [CODE], p, torch.from_numpy(desc.view(np.uint8))[:-1].contiguous(),
+           torch.zeros(64, dtype=torch.complex64), 8)
+    expect("dtype", g.decode_mixed_host, [CODE], p, desc, torch.zeros(64, dtype=torch.complex128), 8)
+    expect("cw", g.decode_mixed_host, [CODE], p, desc, torch.zeros(64, dtype=torch.complex64), 8,
+           cw=torch.zeros(7, dtype=torch.int32))

@@ -111,3 +111,79 @@ def test_arguments(g):
     with pytest.raises(g.GrandError):
         g.decode_symbols_host(code, p, torch.zeros((4, 32), dtype=torch.complex64), chunk_frames=-1)
     code.close()
+
+
+def mixed_codes(g, oracle_lib, Ns):
+    return [g.Code.polar(n, n // 2) for n in Ns]
+
+
+def device_mixed(g, codes, p, desc, sym, n_cw):
+    import torch
+
+    r = g.decode_mixed(codes, p, torch.from_numpy(desc.view(np.uint8)).cuda(), sym.cuda(), n_cw)
+    torch.cuda.synchronize()
+    return {k: r[k].cpu() for k in ("cw", "queries", "abandon")}
+
+
+@pytest.mark.parametrize("chunk", [7000, 0])
+def test_mixed_equals_device_call(g, oracle_lib, chunk):
+    """A packed uneven batch (every N and M) in chunks: same outputs as the
+    device call."""
+    import torch
+
+    Ns = wl.MIXED_N
+    codes = mixed_codes(g, oracle_lib, Ns)
+    info = {n: oracle_lib.info_set(n, n // 2) for n in Ns}
+    mx = wl.mixed_frames(9, 2, 30000, info)
+    desc = g.frame_desc(np.searchsorted(np.array(Ns), mx["N"]), mx["M"], mx["sym_offset"], mx["cw_offset"])
+    sym = torch.from_numpy(mx["symbols"]).pin_memory()
+    p = g.Params.make(M=0, S=10, query_cap=1 << 20)
+    want = device_mixed(g, codes, p, desc, sym, mx["n_cw_words"])
+    got = g.decode_mixed_host(codes, p, desc, sym, mx["n_cw_words"], chunk_frames=chunk)
+    for k in ("cw", "queries", "abandon"):
+        assert torch.equal(got[k], want[k]), k
+    for c in codes:
+        c.close()
+
+
+def test_mixed_unpacked_layout_and_bad_descriptor(g, oracle_lib):
+    """Frames stored out of order with gaps between their output words: one
+    chunk over the whole arrays; words no frame owns keep their values; a
+    descriptor naming a missing code is reported with abandon 3."""
+    import torch
+
+    Ns = (64, 256)
+    codes = mixed_codes(g, oracle_lib, Ns)
+    rng = np.random.default_rng(3)
+    parts, desc_rows, off = [], [], 0
+    blocks = []
+    for i, n in enumerate(Ns):
+        d = wl.qam_frames(10, i, 200, n, oracle_lib.info_set(n, n // 2), 16, 6.0)
+        blocks += [(i, 16, row) for row in d["symbols"]]
+    order = rng.permutation(len(blocks))
+    sym_parts, cw_off = [], 0
+    for j, b in enumerate(order):
+        ci, M, row = blocks[b]
+        desc_rows.append((ci, M, off, cw_off))
+        sym_parts.append(row)
+        off += len(row)
+        cw_off += Ns[ci] // 32 + 1  # one spare word after every frame
+    desc_rows = desc_rows[::-1]  # descriptors in reverse storage order: not packed
+    desc_rows[5] = (7, 16, desc_rows[5][2], desc_rows[5][3])  # no code 7
+    desc = g.frame_desc(*map(np.array, zip(*desc_rows)))
+    sym = torch.from_numpy(np.concatenate(sym_parts).astype(np.complex64)).pin_memory()
+    p = g.Params.make(M=0, S=8, query_cap=1 << 16)
+    cw = torch.full((cw_off,), 0x5A5A5A5A, dtype=torch.int32).pin_memory()
+    got = g.decode_mixed_host(codes, p, desc, sym, cw_off, cw=cw, chunk_frames=50)
+    want = device_mixed(g, codes, p, desc, sym, cw_off)
+    assert torch.equal(got["queries"], want["queries"]) and torch.equal(got["abandon"], want["abandon"])
+    assert int(got["abandon"][5]) == 3
+    owned = np.zeros(cw_off, bool)
+    for f, (ci, _, _, co) in enumerate(desc_rows):
+        if f != 5:
+            owned[co:co + Ns[ci] // 32] = True
+    c = got["cw"].numpy()
+    assert np.array_equal(c[owned], want["cw"].numpy()[owned])
+    assert np.all(c[~owned] == 0x5A5A5A5A)
+    for cd in codes:
+        cd.close()
