@@ -39,6 +39,10 @@
  *     word j >> 5, bit position j & 31 (LSB first).
  *   - A code object is immutable after creation; decodes on different streams
  *     may share it. Destroying it while work on it is in flight is undefined.
+ *   - The library keeps per-device state for the life of the process (the
+ *     pool threshold, the no-alloc scratch address, the host-memory calls'
+ *     two streams per host thread): a cudaDeviceReset while the library is in
+ *     use invalidates it.
  */
 #ifndef GRAND_H
 #define GRAND_H
