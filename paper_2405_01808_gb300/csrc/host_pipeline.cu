@@ -113,6 +113,7 @@ extern "C" int grand_decode_symbols_host(const grand_code* c, const grand_params
   // without frames validates and returns)
   int rc = grand_decode_symbols(c, p, nullptr, 0, N0, nullptr, nullptr, nullptr, nullptr, stream);
   if (rc != GRAND_OK || n_frames == 0) return rc;
+  grand::NvtxRange range("grand.host_pipeline");
   const size_t NW = (size_t)c->N / 32;
   const int64_t chunk = default_chunk(n_frames, chunk_frames);
   const size_t sym_b = round_up(in_bytes * (size_t)chunk), cw_b = round_up(4 * NW * (size_t)chunk),
@@ -213,6 +214,7 @@ extern "C" int grand_decode_mixed_host(const grand_code* const* codes, int n_cod
   int rc = grand_decode_mixed(codes, n_codes, p, nullptr, 0, nullptr, 0, N0, nullptr, 0, nullptr, nullptr, nullptr,
                               stream);
   if (rc != GRAND_OK || n_frames == 0) return rc;
+  grand::NvtxRange range("grand.host_pipeline.mixed");
   // symbols and output words of a frame, per (code, m); 0 for an invalid
   // descriptor (the device reports such a frame with abandon = 3)
   std::vector<int64_t> tabL((size_t)n_codes * 7, 0), tabNW((size_t)n_codes, 0);

@@ -495,8 +495,10 @@ extern "C" int grand_server_drain(grand_server* s, int64_t timeout_ns) {
   const int64_t deadline = now_ns() + timeout_ns;
   for (;;) {
     {
+      // live slots count every admitted request until its batch is reclaimed,
+      // including a batch the launcher is issuing (then in neither queue)
       std::unique_lock<std::mutex> lk(s->mu);
-      if (s->pending.empty() && s->inflight.empty()) return GRAND_OK;
+      if (s->live_slots == 0 && s->pending.empty() && s->inflight.empty()) return GRAND_OK;
     }
     if (now_ns() >= deadline) return GRAND_E_TIMEOUT;
     std::this_thread::sleep_for(std::chrono::microseconds(50));

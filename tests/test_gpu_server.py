@@ -67,7 +67,11 @@ def run_all(srv, reqs, timeout_s=30.0):
         got.append(srv.poll())
         assert time.time() - t0 < timeout_s
     srv.drain(timeout_s)
-    got.append(srv.poll())
+    while True:  # a poll returns a bounded number of results
+        more = srv.poll()
+        if not len(more):
+            break
+        got.append(more)
     return np.concatenate(got)
 
 
@@ -159,3 +163,53 @@ def test_concurrent_submitters(env):
     srv.close()
     assert not errors
     assert sorted(res["tag"].tolist()) == list(range(4000))
+
+
+def test_batch_deadline(env):
+    """params.deadline_ns bounds each batch: with a budget that has already run
+    out when the search starts, every frame the preparation hands on comes back
+    unsearched (abandon 5, the hard word, the preparation's query count) and
+    the others as decoded alone; the codes' status words report the cuts."""
+    g, codes, info = env
+    code_of_N = {n: i for i, n in enumerate(NS)}
+    mx = wl.mixed_frames(64, 0, 1500, info, ebn0_range=(4.0, 8.0))
+    p = g.Params.make(M=0, S=10, query_cap=1 << 20, deadline_ns=1)
+    srv = g.Server(codes, p, max_slots=4096, max_device_bytes=64 << 20, max_batch=512, n_streams=2)
+    reqs = make_requests(g, mx, code_of_N)
+    res = run_all(srv, reqs)
+    st = srv.stats()
+    srv.close()
+    assert len(res) == 1500 and st["errors"] == 0
+    cut = res["abandon"] == 5
+    assert cut.sum() > 50
+    p0 = g.Params.make(M=0, S=10, query_cap=1 << 20)
+    for r in res[:: 7]:
+        f = int(r["tag"])
+        cw, q, ab = alone(g, codes, code_of_N, mx, f, p0)
+        nw = int(mx["N"][f]) // 32
+        if int(r["abandon"]) == 5:
+            assert q > int(r["queries"])  # decoded alone it needs more than the preparation's queries
+            assert ab != 5
+        else:
+            assert (int(r["queries"]), int(r["abandon"])) == (q, ab), f
+            assert np.array_equal(r["cw"][:nw], cw), f
+    cut_codes = {code_of_N[int(mx["N"][int(t)])] for t in res["tag"][cut]}
+    for i, c in enumerate(codes):
+        assert g.stream_status(c) == (g.E_TIMEOUT if i in cut_codes else 0), i
+
+
+def test_drain_covers_batches_being_issued(env):
+    """After drain returns, every admitted request's result is ready: one poll
+    returns all of them (a batch the launcher is still issuing is counted)."""
+    g, codes, info = env
+    code_of_N = {n: i for i, n in enumerate(NS)}
+    mx = wl.mixed_frames(65, 0, 2000, info, ebn0_range=(10.0, 14.0))
+    p = g.Params.make(M=0, S=8, query_cap=1 << 16)
+    for trial in range(5):
+        srv = g.Server(codes, p, max_slots=4096, max_device_bytes=64 << 20, max_batch=256, n_streams=2)
+        reqs = make_requests(g, mx, code_of_N)
+        assert srv.submit(reqs) == 2000
+        srv.drain(30.0)
+        res = srv.poll()
+        srv.close()
+        assert len(res) == 2000, trial
