@@ -653,6 +653,7 @@ class Server:
         h = ctypes.c_void_p()
         _check(lib().grand_server_create(ctypes.byref(cfg), ctypes.byref(h)), "grand_server_create")
         self._h = h
+        self._poll_lock = threading.Lock()  # the result buffer below is shared by pollers
 
     def submit(self, reqs: np.ndarray) -> int:
         """Submit a REQUEST_DTYPE array (symbols = host addresses); returns how
@@ -665,13 +666,16 @@ class Server:
         return n.value
 
     def poll(self, max_results: int = 65536) -> np.ndarray:
-        """Completed results (RESULT_DTYPE), at most max_results per call."""
-        buf = getattr(self, "_buf", None)
-        if buf is None or len(buf) < max_results:
-            buf = self._buf = np.zeros(max_results, dtype=RESULT_DTYPE)
-        n = ctypes.c_int(0)
-        _check(lib().grand_server_poll(self._h, buf.ctypes.data, max_results, ctypes.byref(n)), "grand_server_poll")
-        return buf[: n.value].copy()
+        """Completed results (RESULT_DTYPE), at most max_results per call.
+        Thread-safe: concurrent pollers take disjoint results."""
+        with self._poll_lock:
+            buf = getattr(self, "_buf", None)
+            if buf is None or len(buf) < max_results:
+                buf = self._buf = np.zeros(max_results, dtype=RESULT_DTYPE)
+            n = ctypes.c_int(0)
+            _check(lib().grand_server_poll(self._h, buf.ctypes.data, max_results, ctypes.byref(n)),
+                   "grand_server_poll")
+            return buf[: n.value].copy()
 
     def drain(self, timeout_s: float = 10.0):
         _check(lib().grand_server_drain(self._h, int(timeout_s * 1e9)), "grand_server_drain")
