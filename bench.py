@@ -294,9 +294,9 @@ def run_serving(args, cfg, g, inputs):
         reqs["arrival_ns"] = arrival
         i = 0
         got = []
-        submit_ns = np.zeros(F, dtype=np.int64)  # when the driver handed each request over
+        submit_ns = np.zeros(F, dtype=np.int64)  # when the load generator handed each request over
         t_start = time.perf_counter()
-        gc.disable()  # the driver loop stands in for a native client: no collector pauses inside it
+        gc.disable()  # the load-generator loop stands in for a native client: no collector pauses inside it
         while i < F:
             now = g.clock_ns()
             j = int(np.searchsorted(arrival, now, side="right"))
@@ -333,8 +333,8 @@ def run_serving(args, cfg, g, inputs):
                      "launch_us": {"mean": st["launch_ns"] / max(1, st["batches"]) / 1e3,
                                    "max": st["max_launch_ns"] / 1e3},
                      "latency_us_hist": np.percentile(lat_us, [10, 25, 50, 75, 90, 95, 99, 99.9]).round(1).tolist(),
-                     # the two parts: the driver's delay in handing requests over, and the server's time
-                     "driver_lag_us": {"p50": float(np.percentile(lag_us, 50)), "p99": float(np.percentile(lag_us, 99)),
+                     # the two parts: the load generator's delay in handing requests over, and the server's time
+                     "client_lag_us": {"p50": float(np.percentile(lag_us, 50)), "p99": float(np.percentile(lag_us, 99)),
                                        "max": float(lag_us.max())},
                      "server_latency_us": {"p50": float(np.percentile(srv_us, 50)),
                                            "p99": float(np.percentile(srv_us, 99)), "max": float(srv_us.max())},

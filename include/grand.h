@@ -481,7 +481,7 @@ int grand_decode_symbols_noalloc(const grand_code* code, const grand_params* par
  *              or float32 [n][N] for the HAMMING order).
  *   h_cw, h_queries, h_abandon  host outputs, as for grand_decode_symbols.
  *   Host buffers should be page-locked (cudaHostAlloc / cudaHostRegister):
- *   copies from pageable memory are staged by the driver and overlap less.
+ *   copies from pageable memory are staged by the CUDA driver and overlap less.
  *   stream     the work starts after what is queued on it; on return every
  *              result is in host memory and `stream` is ordered after the
  *              pipeline (the call is synchronous).
