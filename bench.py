@@ -78,8 +78,8 @@ SMS, ALU_LANES, MAX_CLOCK_GHZ = 152, 64, 2.07
 ALU_PEAK_TOPS = SMS * ALU_LANES * MAX_CLOCK_GHZ / 1000.0
 # Counters of the search kernel from one ncu capture (profiles/k_search_warp_c2_small.md),
 # valid only while csrc/decode.cu is the captured source (sha256 prefix).
-NCU_SEARCH = {"sha": "9772aa1240ad19c4", "dram_bytes_per_hard_frame": 1552384 / 9596,
-              "alu_pipe_active": 0.735, "alu_ops_per_check": 0.75}
+NCU_SEARCH = {"sha": "85688c959b892ed8", "dram_bytes_per_hard_frame": 1554432 / 9596,
+              "alu_pipe_active": 0.735, "alu_ops_per_check": 0.76}
 
 
 def hbm_peak():

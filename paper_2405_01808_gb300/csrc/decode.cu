@@ -1510,51 +1510,85 @@ __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
     // B side: one lookup per entry
     if constexpr (kSide == kWarpSideMax) warp_fill_side(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, 0u, sl.Bz);
     uint32_t lr = 0xFFFFFFFFu, lc = 0;
-    for (unsigned col = lane; col < nB; col += 32) {
-      uint32_t z, bcode = 0;
-      bool have_b = false;
-      if constexpr (kSide == kWarpSideMax) {
-        z = sl.Bz[col];
-      } else {
-        warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, z, bcode);
+    // A slot whose top key bits equal the B projection's (the slot index came
+    // from the whole key): a candidate pair, confirmed on every syndrome word
+    // and ranked in closed form.
+    auto confirm = [&](uint32_t slot, unsigned col, bool& have_b, uint32_t& bcode) {
+      const uint32_t row = (slot & HD::kLow) - 1u;
+      if (!have_b) {
+        uint32_t bq;
+        warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, bq, bcode);
         have_b = true;
       }
-      uint32_t h = hash_slot<kSide>(z);
-      const uint32_t zhi = z & ~HD::kLow;
-      for (int probe = 0; probe < HD::kSlots; ++probe) {
-        const uint32_t slot = hslot[h];
-        if (slot == kHashEmpty) break;
-        if ((slot & ~HD::kLow) == zhi) {
-          // top bits equal (the slot index came from the whole key): a candidate;
-          // confirm on every syndrome word, rank in closed form
-          const uint32_t row = (slot & HD::kLow) - 1u;
-          if (!have_b) {
-            uint32_t bq;
-            warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, bq, bcode);
-            have_b = true;
-          }
-          uint32_t aq, acode;
-          warp_side_entry(sl, 0, nAr, sl.startA, sl.ordA, f0, row, aq, acode);
-          const uint32_t cc = acode | (bcode << (2 * nAr));
-          uint32_t orr = 0;
-          for (int w = 0; w < W; ++w) {
-            uint32_t zz = sl.s0[w];
-            for (int r = 0; r < Sp; ++r) {
-              const uint32_t d = (cc >> (2 * r)) & 3u;
-              if (d) zz ^= sl.delta[((size_t)r * 3 + (d - 1)) * W + w];
-            }
-            orr |= zz;
-          }
-          ++my_eval;
-          if (orr == 0) {
-            const uint32_t rk = tep_rank(sl.E, Sp, sl.ex, cc);
-            if (rk < lr) {
-              lr = rk;
-              lc = cc;
-            }
-          }
+      uint32_t aq, acode;
+      warp_side_entry(sl, 0, nAr, sl.startA, sl.ordA, f0, row, aq, acode);
+      const uint32_t cc = acode | (bcode << (2 * nAr));
+      uint32_t orr = 0;
+      for (int w = 0; w < W; ++w) {
+        uint32_t zz = sl.s0[w];
+        for (int r = 0; r < Sp; ++r) {
+          const uint32_t d = (cc >> (2 * r)) & 3u;
+          if (d) zz ^= sl.delta[((size_t)r * 3 + (d - 1)) * W + w];
         }
-        h = (h + 1) & (HD::kSlots - 1);
+        orr |= zz;
+      }
+      ++my_eval;
+      if (orr == 0) {
+        const uint32_t rk = tep_rank(sl.E, Sp, sl.ex, cc);
+        if (rk < lr) {
+          lr = rk;
+          lc = cc;
+        }
+      }
+    };
+    if constexpr (kSide == kWarpSideMax) {
+      // One probe per lane and step: a lane whose probe sequence ends (an
+      // empty slot) starts its next entry at once (a read of the scalar B
+      // table), so lanes with short sequences do not wait for the longest
+      // one of the warp before moving on.
+      unsigned col = lane;
+      bool live = false, have_b = false;
+      uint32_t zhi = 0, h = 0, bcode = 0;
+      int probes = 0;
+      for (;;) {
+        if (!live && col < nB) {
+          const uint32_t z = sl.Bz[col];
+          have_b = false;
+          bcode = 0;
+          h = hash_slot<kSide>(z);
+          zhi = z & ~HD::kLow;
+          probes = 0;
+          live = true;
+        }
+        if (!__any_sync(kFull, live)) break;
+        if (live) {
+          const uint32_t slot = hslot[h];
+          // the table is at most half full, so every sequence meets an empty
+          // slot; the probe count bounds it regardless
+          if (slot == kHashEmpty || ++probes > HD::kSlots) {
+            live = false;
+            col += 32;
+            continue;
+          }
+          if ((slot & ~HD::kLow) == zhi) confirm(slot, col, have_b, bcode);
+          h = (h + 1) & (HD::kSlots - 1);
+        }
+      }
+    } else {
+      // sides of 6 ranks: an entry's projection comes from the table layout
+      // (a search), so the warp starts its entries together
+      for (unsigned col = lane; col < nB; col += 32) {
+        uint32_t z, bcode = 0;
+        warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, z, bcode);
+        bool have_b = true;
+        uint32_t h = hash_slot<kSide>(z);
+        const uint32_t zhi = z & ~HD::kLow;
+        for (int probe = 0; probe < HD::kSlots; ++probe) {
+          const uint32_t slot = hslot[h];
+          if (slot == kHashEmpty) break;
+          if ((slot & ~HD::kLow) == zhi) confirm(slot, col, have_b, bcode);
+          h = (h + 1) & (HD::kSlots - 1);
+        }
       }
     }
     const uint32_t best_rank = __reduce_min_sync(kFull, lr);
