@@ -113,3 +113,59 @@ def test_params_layout_matches_header(glib):
                         ("GRAND_MEMBERSHIP_ROW_PARITY", glib.MEMBERSHIP_ROW_PARITY),
                         ("GRAND_MEMBERSHIP_HASH", glib.MEMBERSHIP_HASH)):
         assert re.search(rf"{name}\s*=\s*{value}\b", text), name
+
+
+# Every struct of the ABI as a C compiler lays it out (gcc on include/grand.h,
+# host only) against the binding's ctypes structures and numpy record types.
+_LAYOUT_C = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "grand.h"
+#define F(T, f) printf("%s %s %zu\n", #T, #f, offsetof(T, f));
+#define Z(T) printf("%s sizeof %zu\n", #T, sizeof(T));
+int main(void) {
+  Z(grand_params) F(grand_params, order) F(grand_params, M) F(grand_params, S) F(grand_params, max_weight)
+  F(grand_params, query_cap) F(grand_params, lik_variant) F(grand_params, tiles) F(grand_params, membership)
+  F(grand_params, deadline_ns)
+  Z(grand_frame_desc) F(grand_frame_desc, code) F(grand_frame_desc, M) F(grand_frame_desc, sym_offset)
+  F(grand_frame_desc, cw_offset)
+  Z(grand_stats) F(grand_stats, evaluated_checks) F(grand_stats, hard_frames) F(grand_stats, search_useful)
+  F(grand_stats, prep_ms) F(grand_stats, search_ms)
+  Z(grand_tune_result) F(grand_tune_result, best_ms) F(grand_tune_result, candidates) F(grand_tune_result, from_cache)
+  Z(grand_server_cfg) F(grand_server_cfg, codes) F(grand_server_cfg, n_codes) F(grand_server_cfg, params)
+  F(grand_server_cfg, N0) F(grand_server_cfg, max_slots) F(grand_server_cfg, max_device_bytes)
+  F(grand_server_cfg, max_batch) F(grand_server_cfg, n_streams)
+  Z(grand_request) F(grand_request, code) F(grand_request, M) F(grand_request, symbols) F(grand_request, tag)
+  F(grand_request, arrival_ns)
+  Z(grand_result) F(grand_result, tag) F(grand_result, arrival_ns) F(grand_result, done_ns) F(grand_result, queries)
+  F(grand_result, abandon) F(grand_result, pad) F(grand_result, cw)
+  Z(grand_server_stats) F(grand_server_stats, admitted) F(grand_server_stats, max_launch_ns)
+  return 0;
+}
+"""
+
+
+def test_struct_layouts_match_the_compiler(glib, tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(_LAYOUT_C)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    c = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        t, f, v = line.split()
+        c[(t, f)] = int(v)
+    g = glib
+    ctypes_structs = {"grand_params": g.Params, "grand_stats": g.Stats, "grand_tune_result": g.TuneResult,
+                      "grand_server_cfg": g.ServerCfg, "grand_server_stats": g.ServerStats}
+    for t, S in ctypes_structs.items():
+        assert ctypes.sizeof(S) == c[(t, "sizeof")], t
+        for name, _ in S._fields_:
+            if (t, name) in c:
+                assert getattr(S, name).offset == c[(t, name)], (t, name)
+    records = {"grand_frame_desc": g.FRAME_DESC_DTYPE, "grand_request": g.REQUEST_DTYPE, "grand_result": g.RESULT_DTYPE}
+    for t, dt in records.items():
+        assert dt.itemsize == c[(t, "sizeof")], t
+        for name in dt.names:
+            key = (t, name)
+            assert key in c, key
+            assert dt.fields[name][1] == c[key], key

@@ -39,3 +39,25 @@ def test_torch_frames_noise_and_codewords(oracle_lib):
     # the seed fixes the batch
     again = wl.torch_qam_frames(7, 20000, N, info, M, snr, "cpu")
     assert torch.equal(again["symbols"], d["symbols"])
+
+
+def test_uneven_batch_is_packed_in_frame_order(oracle_lib):
+    """The uneven-mix generator lays frames out back to back in frame order
+    (each frame's symbols and output words right after the previous frame's),
+    the layout the host-memory call cuts into chunks; the sent codewords sit at
+    the output offsets and satisfy H c = 0."""
+    info = {n: oracle_lib.info_set(n, n // 2) for n in wl.MIXED_N}
+    mx = wl.mixed_frames(5, 3, 3000, info)
+    L = np.array([wl.symbols_per_frame(int(n), int(m)) for n, m in zip(mx["N"], mx["M"])])
+    assert np.array_equal(mx["L"], L)
+    assert mx["sym_offset"][0] == 0 and mx["cw_offset"][0] == 0
+    assert np.array_equal(np.diff(mx["sym_offset"]), L[:-1])
+    assert np.array_equal(np.diff(mx["cw_offset"]), mx["N"][:-1] // 32)
+    assert mx["n_sym"] == mx["sym_offset"][-1] + L[-1] == len(mx["symbols"])
+    assert mx["n_cw_words"] == mx["cw_offset"][-1] + mx["N"][-1] // 32
+    for f in range(0, 3000, 97):
+        n, o = int(mx["N"][f]), int(mx["cw_offset"][f])
+        words = mx["codewords_packed"][o:o + n // 32]
+        bits = ((words[:, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(-1).astype(np.int64)
+        H = oracle_lib.parity_H(n, n // 2).astype(np.int64)
+        assert not (H @ bits % 2).any()
