@@ -135,6 +135,18 @@ class ClockSampler:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
+            return
+        # nvidia-smi's first query initialises NVML, which is slow and goes
+        # through the driver: let it finish (its first sample written, at most
+        # 3 s) before the measured work starts, so the two do not overlap
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.proc.poll() is None:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
