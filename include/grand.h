@@ -115,7 +115,8 @@ typedef enum grand_membership {
 /* Readings of Def. III.1 for a received value beyond the outermost level. */
 typedef enum grand_lik {
   GRAND_LIK_THRESHOLD = 0, /* d = distance to the nearest decision threshold (1 + |A - a|) */
-  GRAND_LIK_LITERAL = 1,   /* d = 1 - |A - a| as printed, clamped at 0 */
+  GRAND_LIK_LITERAL = 1,   /* d = 1 - |A - a| as printed: the ordering key clamps it at 0,
+                            * the reported likelihood (rel) uses it unclamped */
 } grand_lik;
 
 /* Built limits. */

@@ -85,6 +85,38 @@ MUTANTS = {
         "walk_teps(Sp, order == ORDER_NNE5 ? 4 : 3, exists, qam_visit, &c);",
         "walk_teps(Sp, order == ORDER_NNE5 ? 3 : 3, exists, qam_visit, &c);",
         ["test_five_point_away_error", "test_order_variants_match_codebook_bruteforce"]),
+    "level_not_clamped_to_the_top": (
+        "  if (l > sqrtM - 1) l = sqrtM - 1;\n",
+        "  if (0) l = sqrtM - 1;\n",
+        ["test_demod_hard_point_is_nearest_point"]),
+    "q_label_before_i_label": (
+        "  int label = (gI << m) | gQ;\n  int nb = 2 * m;",
+        "  int label = (gQ << m) | gI;\n  int nb = 2 * m;",
+        ["test_demod_packs_gray_labels", "test_decode_noise_free"]),
+    "literal_distance_not_clamped_at_zero": (
+        "  if (d < 0) d = 0;\n",
+        "  if (0) d = 0;\n",
+        ["test_demod_hand_vectors"]),
+    "nonfinite_not_read_as_zero": (
+        "  if (s.nonfinite) { a = 0.0f; b = 0.0f; }",
+        "  if (0) { a = 0.0f; b = 0.0f; }",
+        ["test_nonfinite_coordinate_reads_as_zero"]),
+    "neighbour_direction_flipped": (
+        "  if (delta > 0) dir = -1;\n  else if (delta < 0) dir = +1;",
+        "  if (delta > 0) dir = +1;\n  else if (delta < 0) dir = -1;",
+        ["test_demod_hand_vectors", "test_injected_error_at_least_reliable_symbol"]),
+    "diagonal_with_either_neighbour": (
+        "((ex_h && ex_v) ? 4 : 0)",
+        "((ex_h || ex_v) ? 4 : 0)",
+        ["test_symbol_level_matches_codebook_bruteforce"]),
+    "key_sum_of_distances": (
+        "  s.key = (uint32_t)s.I.dq * (uint32_t)s.I.dq + (uint32_t)s.Q.dq * (uint32_t)s.Q.dq;",
+        "  s.key = (uint32_t)s.I.dq + (uint32_t)s.Q.dq;",
+        ["test_demod_hand_vectors"]),
+    "bit_level_zero_is_one": (
+        "    ybits[j] = (uint8_t)(v < 0.0f);",
+        "    ybits[j] = (uint8_t)(v <= 0.0f);",
+        ["test_bit_level_hard_decision_of_zero"]),
 }
 
 

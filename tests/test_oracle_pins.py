@@ -629,6 +629,38 @@ def test_nonfinite_frame_is_not_searched(oracle_lib):
     assert (ra["abandon"][0], ra["queries"][0]) == (2, 0)
 
 
+def test_nonfinite_coordinate_reads_as_zero(oracle_lib):
+    """A non-finite received coordinate is read as 0 for the hard word (R11).
+    In 16-QAM, 0 lies exactly on the threshold between levels 1 and 2 and goes
+    up to level 2 (amplitude +1, Gray label 11), so the I label of symbol 7 in
+    the returned word is 1, 1 whatever was sent; every other symbol keeps its
+    own hard decision."""
+    N, M = 128, 16
+    H = oracle_lib.parity_H(N, 64)
+    d = wl.qam_frames(6, 1, 1, N, oracle_lib.info_set(N, 64), M, 30.0)
+    s = d["symbols"].copy()
+    s[0, 7] = np.complex64(complex(np.nan, s[0, 7].imag))
+    r = oracle_lib.decode_qam(H, s, M, 8, 1 << 16)
+    assert (r["abandon"][0], r["queries"][0]) == (2, 0)
+    bits = ((r["cw"][0][:, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(-1)
+    assert (bits[28], bits[29]) == (1, 1)  # symbol 7: bits 4*7 .. 4*7+3, I label first, MSB first
+    zeroed = s.copy()
+    zeroed[0, 7] = np.complex64(complex(0.0, s[0, 7].imag))
+    assert np.array_equal(r["cw"][0], oracle_lib.demod(zeroed, M, N)["y"][0])
+
+
+def test_bit_level_hard_decision_of_zero(oracle_lib):
+    """Bit-level hard decision y = [r < 0]: samples of exactly +0.0 and -0.0 are
+    bit 0. The all-zero codeword sent as +1 everywhere and received with two
+    zero samples is its own hard word: decoded at query 1."""
+    H = oracle_lib.parity_H(32, 16)
+    r = np.ones((1, 32), np.float32)
+    r[0, 3] = 0.0
+    r[0, 9] = -0.0
+    ra = oracle_lib.decode_ab(H, r, 3, 5489)
+    assert (ra["abandon"][0], ra["queries"][0]) == (0, 1) and not ra["cw"][0].any()
+
+
 def test_selection_ties_break_by_index(oracle_lib):
     """All 32 symbols of a 16-QAM frame sit 0.25 units from their point toward
     the centre (equal keys, exact in Q8.8, all k = 3); symbol 3 is received at
