@@ -116,6 +116,32 @@ def test_demod_parity(g, oracle_lib, M, lik):
     assert err.max() <= 1e-5
 
 
+@pytest.mark.parametrize("lik", [0, 1])
+def test_demod_hand_vectors(g, lik):
+    """The hand-worked vectors of Def. III.1 / III.2 (tests/golden, derived on
+    paper, independent of the oracle) through the device demodulator: hard
+    point, key, neighbour mask and likelihood of the frame's first symbol."""
+    import torch
+
+    from tests.test_oracle_pins import _read_hand_vectors
+
+    for t in _read_hand_vectors():
+        M, rI, rQ = int(t[0]), float(t[1]), float(t[2])
+        key = int(t[14]) if lik else int(t[8])
+        Lx = float(t[15]) if lik else float(t[7])
+        nmask = int(t[9]) | 32 * int(t[17] if lik else t[16])
+        d = math.sqrt(3 * (math.log2(M) / 2) / (M - 1))
+        N = 32
+        frame = np.full((1, wl.symbols_per_frame(N, M)), complex(rI * d, rQ * d), dtype=np.complex64)
+        r = g.demod(to_dev(frame), M, N, N0=1.0, lik_variant=lik)
+        torch.cuda.synchronize()
+        assert int(r["hard_idx"].cpu().numpy().view(np.uint16)[0, 0]) == int(t[10]), t
+        assert int(u32(r["key"])[0, 0]) == key, t
+        assert int(r["nmask"].cpu().numpy()[0, 0]) == nmask, t
+        rel = float(r["rel"].cpu().numpy()[0, 0])
+        assert abs(rel - Lx) <= 1e-5 * max(1.0, abs(Lx)), t
+
+
 @pytest.mark.parametrize("M", [64, 4096])
 def test_demod_unaligned_symbols(g, oracle_lib, M):
     """Symbols starting 8 bytes past a 16-byte boundary take the one-symbol-
