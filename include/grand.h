@@ -27,20 +27,22 @@
  *   - "device" pointers are CUDA global memory owned by the caller; the
  *     library never frees them. "host" pointers are ordinary CPU memory.
  *     With n_frames == 0 the data pointers may be NULL (nothing is launched).
- *   - The first decode call on a device raises the release threshold of that
- *     device's default stream-ordered memory pool (cudaMemPoolAttrRelease-
- *     Threshold = UINT64_MAX), so scratch stays cached between calls instead
- *     of being returned to the system at each synchronisation.
+ *   - Internal scratch comes from a stream-ordered memory pool that the
+ *     library creates on each device at its first allocation there and keeps
+ *     until the process exits. Its release threshold is UINT64_MAX, so
+ *     scratch stays cached between calls instead of being returned to the
+ *     system at each synchronisation. The device's default pool (used by
+ *     cudaMallocAsync elsewhere in the process) is not touched.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream). Calls that
  *     take a stream enqueue asynchronous work on it and return; the caller
  *     synchronises the stream before reading outputs and keeps every buffer
- *     alive until then. Internal scratch is stream-ordered (cudaMallocAsync).
+ *     alive until then. Internal scratch is stream-ordered (the pool above).
  *   - Bit packing: a word of N bits is stored in N/32 uint32 words, bit j at
  *     word j >> 5, bit position j & 31 (LSB first).
  *   - A code object is immutable after creation; decodes on different streams
  *     may share it. Destroying it while work on it is in flight is undefined.
- *   - The library keeps per-device state for the life of the process (the
- *     pool threshold, the no-alloc scratch address, the host-memory calls'
+ *   - The library keeps per-device state for the life of the process (its
+ *     memory pool, the SM count, the no-alloc scratch address, the host-memory calls'
  *     two streams per host thread): a cudaDeviceReset while the library is in
  *     use invalidates it.
  */
@@ -301,6 +303,11 @@ int grand_decode_symbols(const grand_code* code, const grand_params* params, con
 
 /* Decode an uneven batch: frames of different codes and constellations in
  * one launch sequence (persistent search kernel with a per-frame work queue).
+ * The paper decodes one frame of one (N, M) at a time (Alg. 2) and treats
+ * frames as independent (Sec. IV, no interleaving across codewords); batching
+ * frames of every N in {32..1024} and M of its set (Sec. I, Fig. 4 setup) into
+ * one launch is this library's own pattern for filling a GPU, with per-frame
+ * results equal to Alg. 2's for that frame alone.
  *   codes      host array of n_codes code pointers.
  *   desc       device array of n_frames grand_frame_desc.
  *   symbols    device complex64, flat, n_symbols entries; frame f starts at
@@ -318,7 +325,9 @@ int grand_decode_mixed(const grand_code* const* codes, int n_codes, const grand_
                        float N0, uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon,
                        grand_stats* stats, void* stream);
 
-/* Plans: one decode call captured into a CUDA graph, replayed by
+/* Plans (no counterpart in the paper, whose Prop. III.1 counts circuit clock
+ * cycles: on a GPU the fixed cost per call is the launch sequence, and a graph
+ * replays it with one launch): one decode call captured into a CUDA graph, replayed by
  * grand_plan_launch on any stream with the buffers given at creation (the
  * caller refills the inputs between launches; outputs are overwritten). The
  * captured sequence is the same as the direct call's (counter reset,
@@ -341,7 +350,9 @@ int grand_plan_mixed(const grand_code* const* codes, int n_codes, const grand_pa
 int grand_plan_launch(grand_plan* plan, void* stream);
 int grand_plan_destroy(grand_plan* plan);
 
-/* Launch-shape autotuner. Times every candidate `tiles` setting (preparation
+/* Launch-shape autotuner (no counterpart in the paper: its parallel design
+ * fixes 4^S instances, Prop. III.1, where a GPU must choose how many frames,
+ * TEPs and table slices share an SM). Times every candidate `tiles` setting (preparation
  * weights, search register budget, and for S' > 10 the warps per CTA) on the
  * given sample with CUDA events (median of 3 runs after one untimed run) and
  * writes the fastest into params->tiles. Results never depend on the tiles.
@@ -363,7 +374,12 @@ int grand_autotune_mixed(const grand_code* const* codes, int n_codes, grand_para
                          const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
                          float N0, int64_t n_cw_words, const char* cache_path, void* stream, grand_tune_result* out);
 
-/* Serving loop (continuous batching of decode requests). A request is one
+/* Serving loop (continuous batching of decode requests). The paper's target
+ * is per-frame latency for 5G and beyond (Sec. I: over-the-air latency under
+ * 1 ms); it decodes one frame per invocation of its parallel circuit. This
+ * loop is the library's way to meet a latency bound while frames arrive at
+ * millions per second: requests join the next batch on a free stream instead
+ * of waiting for a whole batch. A request is one
  * frame of any of the server's codes and any constellation. Submit admits
  * requests while a slot is free and the device memory budget allows (bytes
  * per request: 8 L received symbols + 144 hand-off record + N/8 + 5

@@ -2036,6 +2036,45 @@ int preload_qam_kernels() {
     if ((x) != cudaSuccess) return GRAND_E_CUDA; \
   } while (0)
 
+// The search stage of a symbol-level decode (Alg. 2 Step 5 for the frames
+// the preparation handed on): the kernel and its launch shape follow from the
+// params and the call's largest S' and syndrome length. Every symbol-level
+// call (direct, mixed, plans, the fixed-scratch variant) launches it here, so
+// they run the same kernel for the same params.
+static int launch_qam_search(const grand_params* p, int Smax, int w0, int Wmax, const CodeDev* d_codes,
+                             const FrameRec* recs, Scratch* scr, uint32_t* cw, uint32_t* queries, uint8_t* abandon,
+                             cudaStream_t st) {
+  if (Smax <= w0) return GRAND_OK;  // the preparation finished every frame
+  SearchArgs s{};
+  s.recs = recs;
+  s.codes = d_codes;
+  s.scr = scr;
+  s.cap = p->query_cap;
+  s.split = p->tiles[1];
+  // table capacities for the largest split the call can produce
+  s.tabA = kTableMax;
+  s.tabB = kTableMax;
+  if (s.split <= 0) {
+    s.tabA = 1 << (2 * (Smax / 2));
+    s.tabB = 1 << (2 * (Smax - Smax / 2));
+  }
+  s.max_tiles = ((s.tabA + kTileRows - 1) / kTileRows) * ((s.tabB + kTileCols - 1) / kTileCols);
+  s.Wmax = Wmax;
+  // warp-per-frame bit-sliced search with 5- or 6-rank sides; an explicit
+  // split selects the CTA kernel
+  s.warp_kernel = s.split > 0 ? 0 : (Smax <= 2 * kWarpSideMax ? 1 : 2);
+  if (p->membership == GRAND_MEMBERSHIP_HASH && s.split <= 0) s.warp_kernel = Smax <= 2 * kWarpSideMax ? 3 : 4;
+  s.warps = p->tiles[0] > 0 ? (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 0;
+  s.cw = cw;
+  s.queries = queries;
+  s.abandon = abandon;
+  s.deadline = p->deadline_ns;
+  const int threads = p->tiles[0] > 0 ? 32 * (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 256;
+  const size_t smem = search_smem_bytes(s.tabA, s.tabB, s.max_tiles, Wmax);
+  NvtxRange r_search("grand.search");
+  return launch_search(s, threads, smem, p->tiles[3], st);
+}
+
 // Common body of the symbol-level decode calls.
 static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, const grand_params* p,
                    const PrepArgs& proto, int64_t n_frames, grand_stats* stats, cudaStream_t st) {
@@ -2043,14 +2082,13 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     if (stats) *stats = grand_stats{};
     return GRAND_OK;
   }
-  keep_pool_cached();
   NvtxRange range("grand.decode");
   const int w0 = p->tiles[2] > 0 ? (p->tiles[2] > 3 ? 3 : p->tiles[2]) : 2;
   const int Smax = p->S < Lmax ? p->S : Lmax;
   // scratch: header + one record per frame (worst case: every frame hard)
   const size_t rec_bytes = sizeof(FrameRec) * (size_t)n_frames;
   char* scratch = nullptr;
-  if (cudaMallocAsync((void**)&scratch, 256 + rec_bytes, st) != cudaSuccess) return GRAND_E_NOMEM;
+  if (scratch_alloc((void**)&scratch, 256 + rec_bytes, st) != cudaSuccess) return GRAND_E_NOMEM;
   Scratch* scr = reinterpret_cast<Scratch*>(scratch);
   FrameRec* recs = reinterpret_cast<FrameRec*>(scratch + 256);
   int rc = GRAND_OK;
@@ -2088,38 +2126,10 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     if (stats) cudaEventRecord(ev[1], st);
     if (cudaGetLastError() != cudaSuccess) { rc = GRAND_E_CUDA; break; }
 
-    if (Smax > a.w0) {
-      SearchArgs s{};
-      s.recs = recs;
-      s.codes = d_codes;
-      s.scr = scr;
-      s.cap = p->query_cap;
-      s.split = p->tiles[1];
-      // table capacities for the largest split the call can produce
-      s.tabA = kTableMax;
-      s.tabB = kTableMax;
-      if (s.split <= 0) {
-        s.tabA = 1 << (2 * (Smax / 2));
-        s.tabB = 1 << (2 * (Smax - Smax / 2));
-      }
-      s.max_tiles = ((s.tabA + kTileRows - 1) / kTileRows) * ((s.tabB + kTileCols - 1) / kTileCols);
-      s.Wmax = Wmax;
-      // warp-per-frame bit-sliced search with 5- or 6-rank sides; an explicit
-      // split selects the CTA kernel
-      s.warp_kernel = s.split > 0 ? 0 : (Smax <= 2 * kWarpSideMax ? 1 : 2);
-      if (p->membership == GRAND_MEMBERSHIP_HASH && s.split <= 0) s.warp_kernel = Smax <= 2 * kWarpSideMax ? 3 : 4;
-      s.warps = p->tiles[0] > 0 ? (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 0;
-      s.cw = proto.cw;
-      s.queries = proto.queries;
-      s.abandon = proto.abandon;
-      s.deadline = p->deadline_ns;
-      const int threads = p->tiles[0] > 0 ? 32 * (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 256;
-      const size_t smem = search_smem_bytes(s.tabA, s.tabB, s.max_tiles, Wmax);
-      NvtxRange r_search("grand.search");
-      if (launch_search(s, threads, smem, p->tiles[3], st) != GRAND_OK) {
-        rc = GRAND_E_CUDA;
-        break;
-      }
+    if (launch_qam_search(p, Smax, a.w0, Wmax, d_codes, recs, scr, proto.cw, proto.queries, proto.abandon, st) !=
+        GRAND_OK) {
+      rc = GRAND_E_CUDA;
+      break;
     }
     if (stats) {
       cudaEventRecord(ev[2], st);
@@ -2178,7 +2188,7 @@ static int run_ab(const grand_code* c, const grand_params* p, const float* sampl
     return GRAND_OK;
   }
   Scratch* scr = nullptr;
-  if (cudaMallocAsync((void**)&scr, sizeof(Scratch), st) != cudaSuccess) return GRAND_E_NOMEM;
+  if (scratch_alloc((void**)&scr, sizeof(Scratch), st) != cudaSuccess) return GRAND_E_NOMEM;
   int rc = GRAND_OK;
   do {
     if (cudaMemsetAsync(scr, 0, sizeof(Scratch), st) != cudaSuccess) { rc = GRAND_E_CUDA; break; }
@@ -2418,7 +2428,7 @@ extern "C" int grand_decode_mixed(const grand_code* const* codes, int n_codes, c
   rc = code_table(codes, n_codes, table, Lmax, Wmax);
   if (rc) return rc;
   CodeDev* d_table = nullptr;
-  if (cudaMallocAsync((void**)&d_table, sizeof(CodeDev) * n_codes, st) != cudaSuccess) return GRAND_E_NOMEM;
+  if (scratch_alloc((void**)&d_table, sizeof(CodeDev) * n_codes, st) != cudaSuccess) return GRAND_E_NOMEM;
   // pageable source: the copy is staged before the call returns
   if (cudaMemcpyAsync(d_table, table.data(), sizeof(CodeDev) * n_codes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
     cudaFreeAsync(d_table, st);
@@ -2549,7 +2559,8 @@ extern "C" int grand_plan_destroy(grand_plan* plan) {
 // Allocation-free variant of grand_decode_symbols.
 //
 // The regular call takes its scratch (a header plus one hand-off record per
-// frame between the preparation and the search kernel) from cudaMallocAsync.
+// frame between the preparation and the search kernel) from the library's
+// stream-ordered pool.
 // This variant takes it from one fixed array in device memory instead, so a
 // caller that must not allocate after start-up can still decode. The array is
 // part of the library's device code: every GPU that loads the library holds
@@ -2637,29 +2648,7 @@ extern "C" int grand_decode_symbols_noalloc(const grand_code* c, const grand_par
   kp<<<grid, 32 * warps, prep_smem, st>>>(a);
   if (cudaGetLastError() != cudaSuccess) return GRAND_E_CUDA;
   const int Smax = p->S < L ? p->S : L;
-  if (Smax > a.w0) {
-    SearchArgs s{};
-    s.recs = recs;
-    s.codes = c->d_dev;
-    s.scr = scr;
-    s.cap = p->query_cap;
-    s.split = p->tiles[1];
-    s.tabA = kTableMax;
-    s.tabB = kTableMax;
-    if (s.split <= 0) {
-      s.tabA = 1 << (2 * (Smax / 2));
-      s.tabB = 1 << (2 * (Smax - Smax / 2));
-    }
-    s.max_tiles = ((s.tabA + kTileRows - 1) / kTileRows) * ((s.tabB + kTileCols - 1) / kTileCols);
-    s.Wmax = c->W;
-    s.warp_kernel = (Smax <= 2 * kWarpSideMax && s.split <= 0) ? 1 : 0;
-    s.cw = cw;
-    s.queries = queries;
-    s.abandon = abandon;
-    s.deadline = p->deadline_ns;
-    const int threads = p->tiles[0] > 0 ? 32 * (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 256;
-    const size_t smem = search_smem_bytes(s.tabA, s.tabB, s.max_tiles, c->W);
-    if (launch_search(s, threads, smem, p->tiles[3], st) != GRAND_OK) return GRAND_E_CUDA;
-  }
+  if (launch_qam_search(p, Smax, a.w0, c->W, c->d_dev, recs, scr, cw, queries, abandon, st) != GRAND_OK)
+    return GRAND_E_CUDA;
   return GRAND_OK;
 }

@@ -63,7 +63,7 @@ struct Pipe {
       if (!ts && cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) return GRAND_E_CUDA;
       s[i] = ts;
       if (cudaStreamWaitEvent(s[i], ev[kPipeStreams], 0) != cudaSuccess) return GRAND_E_CUDA;
-      if (bytes_per_stream && cudaMallocAsync((void**)&dbuf[i], bytes_per_stream, s[i]) != cudaSuccess)
+      if (bytes_per_stream && grand::scratch_alloc((void**)&dbuf[i], bytes_per_stream, s[i]) != cudaSuccess)
         return GRAND_E_NOMEM;
     }
     return GRAND_OK;
@@ -162,7 +162,7 @@ int issue_mixed_chunk(const grand_code* const* codes, int n_codes, const grand_p
   const size_t desc_b = round_up(sizeof(grand_frame_desc) * (size_t)nk), sym_b = round_up(8 * (size_t)n_sym),
                cw_b = round_up(4 * (size_t)n_cw), q_b = round_up(4 * (size_t)nk), ab_b = round_up((size_t)nk);
   char* buf = nullptr;
-  if (cudaMallocAsync((void**)&buf, desc_b + sym_b + cw_b + q_b + ab_b, st) != cudaSuccess) return GRAND_E_NOMEM;
+  if (grand::scratch_alloc((void**)&buf, desc_b + sym_b + cw_b + q_b + ab_b, st) != cudaSuccess) return GRAND_E_NOMEM;
   grand_frame_desc* d_desc = reinterpret_cast<grand_frame_desc*>(buf);
   float2* d_sym = reinterpret_cast<float2*>(buf + desc_b);
   uint32_t* d_cw = reinterpret_cast<uint32_t*>(buf + desc_b + sym_b);

@@ -1,10 +1,11 @@
 // Host-side helpers shared by the decoder translation units: constellation
-// constants, the device's SM count and the stream-ordered pool setting.
+// constants, the device's SM count and the library's stream-ordered pool.
 #pragma once
 
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
 
 #include <cuda_runtime.h>
@@ -43,32 +44,59 @@ inline QamConst make_qam_const() {
   return c;
 }
 
-// Keep the scratch of repeated calls cached: the default stream-ordered pool
-// of the device otherwise returns its memory to the system at every
-// synchronisation and the next call maps it again. Once per device.
-inline void keep_pool_cached() {
+constexpr int kMaxDevices = 64;
+
+// Stream-ordered scratch comes from a memory pool owned by the library, one
+// per device, created at the first allocation on that device and kept for the
+// life of the process. Its release threshold is raised so that scratch stays
+// cached between calls (a pool otherwise returns its memory to the system at
+// every synchronisation and the next call maps it again); the device's
+// default pool, which other code in the process may use, keeps its settings.
+inline cudaMemPool_t lib_pool(int dev) {
   static std::mutex mu;
-  static bool done[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  static cudaMemPool_t pools[kMaxDevices] = {};
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
   std::lock_guard<std::mutex> lock(mu);
-  if (done[dev]) return;
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
   }
-  done[dev] = true;
+  return pools[dev];
 }
 
+// Stream-ordered allocation from the library's pool of the current device
+// (freed with cudaFreeAsync). Inside a stream capture it becomes a graph
+// memory node like cudaMallocAsync.
+inline cudaError_t scratch_alloc(void** ptr, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool = lib_pool(dev);
+  if (!pool) return cudaErrorMemoryAllocation;
+  return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
+}
+
+// SM count of the current device, cached per device index (threads may race
+// to fill an entry; they store the same value).
 inline int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
+  static std::atomic<int> cached[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  if (dev >= 0 && dev < kMaxDevices) {
+    const int n = cached[dev].load(std::memory_order_relaxed);
+    if (n > 0) return n;
   }
+  int n = 0;
+  if (dev < 0 || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  if (dev >= 0 && dev < kMaxDevices && n > 1) cached[dev].store(n, std::memory_order_relaxed);
   return n;
 }
 

@@ -415,7 +415,6 @@ int run_per_tep(const grand_code* c, const grand_params* p, const void* symbols,
     if (stats) *stats = grand_stats{};
     return GRAND_OK;
   }
-  keep_pool_cached();
   NvtxRange range("grand.per_tep");
   const int m = m_of(p->M);
   TepArgs a{};
@@ -435,7 +434,7 @@ int run_per_tep(const grand_code* c, const grand_params* p, const void* symbols,
   a.queries = queries;
   a.abandon = abandon;
   char* scratch = nullptr;
-  if (cudaMallocAsync((void**)&scratch, 64, st) != cudaSuccess) return GRAND_E_NOMEM;
+  if (scratch_alloc((void**)&scratch, 64, st) != cudaSuccess) return GRAND_E_NOMEM;
   a.next = reinterpret_cast<unsigned int*>(scratch);
   a.counters = reinterpret_cast<unsigned long long*>(scratch + 8);
   a.t0 = reinterpret_cast<unsigned long long*>(scratch + 32);

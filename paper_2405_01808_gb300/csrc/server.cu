@@ -359,14 +359,13 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
       return GRAND_E_NOMEM;
     }
   }
-  // Grow the device's stream-ordered pool to the decode scratch of n_streams
+  // Grow the library's stream-ordered pool to the decode scratch of n_streams
   // full batches now, so that no batch waits on the pool growing later (the
-  // library keeps freed pool memory cached).
+  // pool keeps freed memory cached).
   {
-    grand::keep_pool_cached();
     const size_t per_batch = 256 + sizeof(grand::FrameRec) * mb + 4096;
     void* warm = nullptr;
-    if (cudaMallocAsync(&warm, per_batch * s->sb.size(), s->sb[0].stream) == cudaSuccess)
+    if (grand::scratch_alloc(&warm, per_batch * s->sb.size(), s->sb[0].stream) == cudaSuccess)
       cudaFreeAsync(warm, s->sb[0].stream);
     cudaStreamSynchronize(s->sb[0].stream);
   }

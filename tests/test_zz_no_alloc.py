@@ -36,11 +36,11 @@ def env():
     code.close()
 
 
-def _call_noalloc(g, code, p, sym, F):
+def _call_noalloc(g, code, p, sym, F, words=4):
     """Call the entry point directly through ctypes (the C ABI)."""
     import torch
 
-    cw = torch.full((F, 4), -1, dtype=torch.int32, device="cuda")
+    cw = torch.full((F, words), -1, dtype=torch.int32, device="cuda")
     q = torch.full((F,), -1, dtype=torch.int32, device="cuda")
     ab = torch.full((F,), 255, dtype=torch.uint8, device="cuda")
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -71,6 +71,36 @@ def test_noalloc_matches_allocating_call_twice(env):
         assert torch.equal(q, ref["queries"])
         assert torch.equal(ab, ref["abandon"])
         assert int((ab == 1).sum()) > 0 and int((ab == 0).sum()) > 0
+
+
+def test_noalloc_matches_allocating_call_s12(env):
+    """S' = 12 (N=512, 64-QAM, cap 2^24): the search stage with 6-rank sides,
+    launched by the same helper as grand_decode_symbols; two calls in a row."""
+    import torch
+
+    g, _, _ = env
+    N, K, M = 512, 256, 64
+    code = g.Code.polar(N, K)
+    try:
+        _, frozen = g.polar_H(N, K)
+        info = np.setdiff1d(np.arange(N), frozen)
+        p = g.Params.make(M=M, S=12, query_cap=1 << 24)
+        batches = [wl.qam_frames(78, 0, 1500, N, info, M, 14.0), wl.qam_frames(78, 1, 700, N, info, M, 15.0)]
+        for d in batches:
+            F = len(d["symbols"])
+            sym = torch.from_numpy(d["symbols"]).cuda()
+            ref = g.decode_symbols(code, p, sym)
+            torch.cuda.synchronize()
+            cw, q, ab = _call_noalloc(g, code, p, sym, F, N // 32)
+            assert torch.equal(cw, ref["cw"])
+            assert torch.equal(q, ref["queries"])
+            assert torch.equal(ab, ref["abandon"])
+            # frames decoded by the search stage (beyond the 631 TEPs of at most two
+            # altered symbols that the preparation tests at S' = 12) are present
+            assert int(((ab == 0) & (q.to(torch.int64) > 631)).sum()) > 0
+    finally:
+        torch.cuda.synchronize()
+        code.close()
 
 
 def test_noalloc_rejects_oversized_batch(env):
