@@ -69,17 +69,83 @@ CONFIGS = {
     "c5": dict(kind="serve", frames=1000000, S=10, cap=1 << 20, rates=(0.5e6, 1e6, 2e6, 5e6),
                desc="serving: Poisson arrivals at 0.5/1/2/5 M frames/s of the uneven mix (N 32..1024, "
                     "M 4..256, Eb/N0 U(4,14) dB), 1000000 requests per rate, S=min(L,10), cap 2^20"),
+    "c5adv": dict(kind="serve", frames=400000, S=10, cap=1 << 20, rates=(1e6,), adversarial=0.25,
+                  desc="serving, adversarial mix: the uneven mix with a quarter of the requests replaced by "
+                       "N=1024 frames at Eb/N0 4 dB (most search their whole 2^20 queries), Poisson 1 M frames/s, "
+                       "400000 requests; long frames whole in their batch vs carried as device-resident cursors"),
 }
 METRIC = "TEP syndrome checks/s & frames/s per GB300; p50/p99 decode latency"
-CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5, "c5": 6, "bler": 7, "orders": 2, "membership": 2}
+CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5, "c5": 6, "c5adv": 8, "bler": 7, "orders": 2,
+              "membership": 2}
 # ALU roofline: 152 SMs x 64 integer-ALU lanes per clock (LOP3/ISETP class)
 # x 2.07 GHz maximum SM clock.
 SMS, ALU_LANES, MAX_CLOCK_GHZ = 152, 64, 2.07
 ALU_PEAK_TOPS = SMS * ALU_LANES * MAX_CLOCK_GHZ / 1000.0
-# Counters of the search kernel from one ncu capture (profiles/k_search_warp_c2_small.md),
-# valid only while csrc/decode.cu is the captured source (sha256 prefix).
-NCU_SEARCH = {"sha": "85688c959b892ed8", "dram_bytes_per_hard_frame": 1554432 / 9596,
-              "alu_pipe_active": 0.735, "alu_ops_per_check": 0.76}
+# Counters of each search kernel from one ncu capture of a small case (the
+# profiles/ file named), taken on the decode.cu source with the given sha256
+# prefix. alu_lane_ops_per_check = ALU pipe busy fraction x elapsed cycles x
+# SMs x 64 lanes / TEP checks the kernel evaluated in that launch: what one
+# evaluated check costs the ALU pipe, everything in the kernel included.
+NCU_SEARCH = {
+    "k_search_warp<5>": {"sha": "85688c959b892ed8", "profile": "profiles/k_search_warp_c2_small.md",
+                         "alu_lane_ops_per_check": 0.76, "alu_pipe_active": 0.735,
+                         "dram_bytes_per_hard_frame": 1554432 / 9596},
+    "k_search_warp<6>": {"sha": "85688c959b892ed8", "profile": "profiles/k_search_warp6_c3a_small.md",
+                         "alu_lane_ops_per_check": 0.65, "alu_pipe_active": 0.765,
+                         "dram_bytes_per_hard_frame": 164.0},
+}
+
+
+def decode_source_sha():
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_2405_01808_gb300", "csrc", "decode.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def search_kernel(cfg):
+    """The kernel that runs the TEP search of a workload with automatic tiles."""
+    if cfg["kind"] == "ab":
+        return "k_ab_split<1,16>" if cfg["N"] == 32 else "k_ab"
+    return "k_search_warp<6>" if cfg["S"] > 10 else "k_search_warp<5>"
+
+
+def search_roofline(cfg, evaluated, useful, hard, kernel_ms, alg_words):
+    """Roofline of the TEP search kernel against the integer-ALU peak.
+
+    frac = ALU lane-ops executed per second / peak lane-ops per second, with
+    the lane-ops = TEP checks the kernel evaluated in this run (counted on the
+    device) x the ALU lane-ops one evaluated check costs (ncu, same kernel).
+    It stays below 1 by construction. The survey's model (N-K)/32 three-input
+    ops per useful check is kept beside it as model_ops: it can exceed the
+    peak, because the bit-sliced compare tests 32 TEPs per logic op on a 16-bit
+    projection and confirms only matches on the full syndrome."""
+    kern = search_kernel(cfg)
+    prof = NCU_SEARCH.get(kern)
+    t_s = kernel_ms / 1e3
+    rec = {"bound": "alu", "peak": ALU_PEAK_TOPS, "unit": "Tops/s", "kernel": kern, "kernel_ms": kernel_ms,
+           "evaluated_checks": evaluated, "useful_checks": useful,
+           "peak_source": f"derived: {SMS} SMs x {ALU_LANES} ALU lanes/clk x {MAX_CLOCK_GHZ} GHz (a LOP3 "
+                          "microbenchmark on this GPU measured 64 per clock per SM)"}
+    if prof is not None:
+        ops = evaluated * prof["alu_lane_ops_per_check"]
+        ach = ops / t_s / 1e12
+        same = decode_source_sha() == prof["sha"]
+        rec.update({"achieved": ach, "frac": ach / ALU_PEAK_TOPS,
+                    "traffic": prof["dram_bytes_per_hard_frame"] * hard if same and hard else None,
+                    "alu_lane_ops_per_evaluated_check": prof["alu_lane_ops_per_check"],
+                    "derivation": "evaluated checks of this run x ALU lane-ops per evaluated check (ncu) / "
+                                  "event-timed kernel time / ALU peak",
+                    "profile": prof["profile"], "profile_source_sha": prof["sha"], "profile_matches_source": same,
+                    "ncu_alu_pipe_active": prof["alu_pipe_active"]})
+    else:
+        rec.update({"achieved": None, "frac": None, "traffic": None})
+    if alg_words is not None:
+        m = useful * alg_words / t_s / 1e12
+        rec["model_ops"] = {"ops_per_useful_check": alg_words, "achieved": m, "frac": m / ALU_PEAK_TOPS,
+                            "note": "(N-K)/32 three-input ops per useful check; can exceed 1 (the split compare "
+                                    "tests 32 TEPs per op on a projection)"}
+    return rec
 
 
 def hbm_peak():
@@ -100,7 +166,10 @@ def make_inputs(cfg, rank, info_by_N):
         return None
     cid = CONFIG_IDS[cfg["name"]]
     if cfg["kind"] in ("mixed", "serve"):
-        return wl.mixed_frames(cid, 1000 + rank, cfg["frames"], info_by_N)
+        mx = wl.mixed_frames(cid, 1000 + rank, cfg["frames"], info_by_N)
+        if cfg.get("adversarial"):
+            mx = with_hard_share(mx, cid, rank, cfg["adversarial"], info_by_N)
+        return mx
     parts = []
     for i, snr in enumerate(cfg["snrs"]):
         if cfg["kind"] == "ab":
@@ -111,6 +180,39 @@ def make_inputs(cfg, rank, info_by_N):
     return {"symbols": np.concatenate([p["symbols"] for p in parts]),
             "codewords_packed": np.concatenate([p["codewords_packed"] for p in parts]),
             "snr": np.concatenate([np.full(len(p["symbols"]), p["ebn0_db"]) for p in parts])}
+
+
+def with_hard_share(mx, cid, rank, share, info_by_N):
+    """Replace a share of the frames of an uneven batch (seeded positions) by
+    N=1024 frames at Eb/N0 4 dB over the same constellation mix."""
+    F = len(mx["N"])
+    g = wl.rng(cid, 5000 + rank)
+    hard = np.sort(g.choice(F, size=int(F * share), replace=False))
+    hx = wl.mixed_frames(cid, 6000 + rank, len(hard), info_by_N, ebn0_range=(4.0, 4.0), n_choices=(1024,))
+    N, M, snr = mx["N"].copy(), mx["M"].copy(), mx["ebn0_db"].copy()
+    N[hard], M[hard], snr[hard] = hx["N"], hx["M"], hx["ebn0_db"]
+    L = np.array([wl.symbols_per_frame(int(n), int(m)) for n, m in zip(N, M)], dtype=np.int64)
+    sym_off = np.zeros(F + 1, dtype=np.int64)
+    np.cumsum(L, out=sym_off[1:])
+    cw_off = np.zeros(F + 1, dtype=np.int64)
+    np.cumsum(N // 32, out=cw_off[1:])
+    symbols = np.empty(int(sym_off[-1]), dtype=np.complex64)
+    cw = np.empty(int(cw_off[-1]), dtype=np.uint32)
+    is_hard = np.zeros(F, dtype=bool)
+    is_hard[hard] = True
+    easy = np.nonzero(~is_hard)[0]
+
+    def gather(src, src_off, dst, dst_off, lengths):
+        rel = np.arange(int(lengths.sum())) - np.repeat(np.cumsum(lengths) - lengths, lengths)
+        dst[np.repeat(dst_off, lengths) + rel] = src[np.repeat(src_off, lengths) + rel]
+
+    gather(mx["symbols"], mx["sym_offset"][easy], symbols, sym_off[easy], L[easy])
+    gather(hx["symbols"], hx["sym_offset"], symbols, sym_off[hard], L[hard])
+    gather(mx["codewords_packed"], mx["cw_offset"][easy], cw, cw_off[easy], (N[easy] // 32).astype(np.int64))
+    gather(hx["codewords_packed"], hx["cw_offset"], cw, cw_off[hard], (N[hard] // 32).astype(np.int64))
+    return {"hard": is_hard,"symbols": symbols, "N": N.astype(np.int32), "M": M.astype(np.int32), "L": L.astype(np.int32),
+            "sym_offset": sym_off[:-1].copy(), "cw_offset": cw_off[:-1].copy(), "ebn0_db": snr,
+            "codewords_packed": cw, "n_sym": int(sym_off[-1]), "n_cw_words": int(cw_off[-1])}
 
 
 # -------------------------------------------------------------------------
@@ -274,8 +376,10 @@ def run_reference(args, cfg):
 # -------------------------------------------------------------------------
 # serving (continuous batching server, Poisson arrivals)
 # -------------------------------------------------------------------------
-def run_serving(args, cfg, g, inputs):
-    """Offer the requests at each Poisson rate; latency = completion - arrival."""
+def run_serving(args, cfg, g, inputs, resume_step=0):
+    """Offer the requests at each Poisson rate; latency = completion - arrival.
+    resume_step > 0: long frames leave their batch as device-resident cursors
+    (grand_server_cfg.resume_weight_step)."""
     import torch
 
     codes = [g.Code.polar(n, n // 2) for n in wl.MIXED_N]
@@ -291,7 +395,8 @@ def run_serving(args, cfg, g, inputs):
     rows = []
     g_rng = np.random.default_rng(CONFIG_IDS["c5"])
     for rate in cfg["rates"]:
-        srv = g.Server(codes, p, max_slots=1 << 18, max_device_bytes=1 << 30, max_batch=args.serve_batch, n_streams=args.serve_streams)
+        srv = g.Server(codes, p, max_slots=1 << 18, max_device_bytes=1 << 30, max_batch=args.serve_batch,
+                       n_streams=args.serve_streams, resume_weight_step=resume_step)
         # warm-up: a short burst (module load, pools)
         w = srv.submit(reqs[:20000])
         srv.drain(60.0)
@@ -329,11 +434,19 @@ def run_serving(args, cfg, g, inputs):
         st = srv.stats()
         srv.close()
         res = np.concatenate(got)
-        res = res[res["tag"] >= 50000]  # the first 50,000 requests warm the server at this rate
+        warm = min(50000, F // 8)
+        res = res[res["tag"] >= warm]  # the first requests warm the server at this rate
         lat_us = (res["done_ns"] - res["arrival_ns"]) / 1e3
         lag_us = (submit_ns[res["tag"].astype(np.int64)] - res["arrival_ns"]) / 1e3
         srv_us = lat_us - lag_us
-        span = (res["done_ns"].max() - arrival[50000]) / 1e9
+        by_class = {}
+        if "hard" in inputs:  # latency of the injected long frames and of the rest, separately
+            hmask = inputs["hard"][res["tag"].astype(np.int64)]
+            for name, m in (("regular", ~hmask), ("hard", hmask)):
+                if m.any():
+                    by_class[name] = {"requests": int(m.sum()), "p50": float(np.percentile(lat_us[m], 50)),
+                                      "p99": float(np.percentile(lat_us[m], 99)), "max": float(lat_us[m].max())}
+        span = (res["done_ns"].max() - arrival[warm]) / 1e9
         rows.append({"offered_frames_per_s": rate, "completed": int(len(res)),
                      "frames_per_s": len(res) / span, "checks_per_s": float(res["queries"].sum()) / span,
                      "latency_us": {"p50": float(np.percentile(lat_us, 50)), "p99": float(np.percentile(lat_us, 99)),
@@ -350,14 +463,15 @@ def run_serving(args, cfg, g, inputs):
                                        "max": float(lag_us.max())},
                      "server_latency_us": {"p50": float(np.percentile(srv_us, 50)),
                                            "p99": float(np.percentile(srv_us, 99)), "max": float(srv_us.max())},
-                     "errors": st["errors"]})
+                     "errors": st["errors"], "resume_weight_step": resume_step, "latency_us_by_class": by_class,
+                     "long_frames": st["long_frames"], "resume_launches": st["resume_launches"]})
     last = res
     # the plain one-frame-per-launch GPU path on a sample of the same requests:
     # per request the host->device copy of its symbols, one decode call and the
     # read-back of its result, one request after another (no batching); its
     # outputs must equal the server's for the same requests (same BLER)
     n_one = min(2000, F)
-    pick = np.linspace(min(50000, F - 1), F - 1, n_one).astype(np.int64)
+    pick = np.linspace(min(min(50000, F // 8), F - 1), F - 1, n_one).astype(np.int64)
     pos = np.full(F, -1, dtype=np.int64)
     pos[last["tag"].astype(np.int64)] = np.arange(len(last))
     params_of_M = {}
@@ -551,98 +665,21 @@ def run_membership(args, cfg, g):
 # -------------------------------------------------------------------------
 # GPU arm
 # -------------------------------------------------------------------------
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gpu", choices=("gpu", "reference"))
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--frames", type=int, default=0, help="override frames per SNR (for quick runs)")
-    ap.add_argument("--tiles", default="0,0,0,0", help="launch shape (grand_params.tiles), 0 = automatic")
-    ap.add_argument("--membership", default="auto", choices=("auto", "hash"),
-                    help="membership test of the search (the headline uses the TEP-by-TEP search)")
-    ap.add_argument("--serve-batch", type=int, default=65536, help="serving: frames per launch")
-    ap.add_argument("--serve-streams", type=int, default=4, help="serving: batches in flight")
-    args = ap.parse_args()
-    cfg = dict(CONFIGS[args.config])
-    cfg["name"] = args.config
-    if args.frames:
-        cfg["frames"] = args.frames
-    tiles = tuple(int(t) for t in args.tiles.split(","))
-    membership = {"auto": 0, "hash": 3}[args.membership]
-    if args.impl == "reference":
-        return run_reference(args, cfg)
-
+def run_config(args, cfg, g, ctx):
+    """One workload as the bench line's record: device-timed decode steps
+    (inputs resident, L2 flushed), the kernel split and roofline, the hash
+    join on the same batch, the public demodulation, the host-memory (e2e)
+    call, the one-frame-per-launch path and the oracle on a bounded sample.
+    Returns the record on rank 0 (None elsewhere)."""
     import torch
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    import paper_2405_01808_gb300 as g
-
-    if rank == 0:
-        g.build()
-    if dist:
-        dist.barrier()
-    g.lib()
-
+    rank, world, dist, local = ctx["rank"], ctx["world"], ctx["dist"], ctx["local"]
+    tiles = tuple(int(t) for t in args.tiles.split(","))
+    membership = {"auto": 0, "hash": 3}[args.membership]
     info = info_sets(cfg, "library")
     inputs = make_inputs(cfg, rank, info)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    if cfg["kind"] == "bler":
-        rows, fps = run_bler(args, cfg, g)
-        if rank == 0:
-            print(json.dumps({"metric": "BLER vs Eb/N0 (own curves; the paper's Fig. 4 values are not in its text)",
-                              "value": fps, "unit": "frames/s (decode calls of the sweep)", "n_gpus": world,
-                              "steps": len(rows), "warmup": 0, "higher_is_better": True, "dtype": "u32",
-                              "data": "synthetic (seeded random polar codewords over AWGN)",
-                              "config": {"workload": cfg["desc"], "frames_per_point": cfg["frames"]},
-                              "bler": rows}), flush=True)
-        return 0
-    if cfg["kind"] in ("orders", "membership"):
-        clocks = ClockSampler(local)
-        clocks.start()
-        rows = run_orders(args, cfg, g) if cfg["kind"] == "orders" else run_membership(args, cfg, g)
-        clk = clocks.stop()
-        if rank == 0:
-            print(json.dumps({"metric": "TEP order comparison (queries, BLER)" if cfg["kind"] == "orders"
-                              else "membership-test ablation (checks/s)",
-                              "value": rows[0]["useful_checks_per_s"], "unit": "checks/s (first row)",
-                              "n_gpus": world, "steps": 1, "warmup": 1, "higher_is_better": True, "dtype": "u32",
-                              "data": "synthetic (seeded random polar codewords over AWGN)",
-                              "config": {"workload": cfg["desc"]}, "clocks": clk, "rows": rows}), flush=True)
-        return 0
-    if cfg["kind"] == "serve":
-        clocks = ClockSampler(local)
-        clocks.start()
-        rows, one = run_serving(args, cfg, g, inputs)
-        clk = clocks.stop()
-        if rank == 0:
-            head = rows[-1]
-            line = {"metric": METRIC, "value": head["frames_per_s"], "unit": "frames/s", "n_gpus": world,
-                    "steps": len(rows), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
-                    "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-                    "data": "synthetic (seeded random polar codewords over AWGN)",
-                    "config": {"workload": cfg["desc"],
-                               "server": f"max_slots 262144, budget 1 GiB, max_batch {args.serve_batch}, "
-                                         f"{args.serve_streams} streams"},
-                    "latency_us": head["latency_us"], "rates": rows, "one_frame_per_launch": one, "clocks": clk,
-                    "e2e": {"value": head["frames_per_s"], "unit": "frames/s",
-                            "h2d_bytes_per_step": int(inputs["symbols"].nbytes),
-                            "d2h_bytes_per_step": int(len(inputs["N"]) * 160)},
-                    "gpu_launches": int(sum(r["batches"] for r in rows) * 2)}
-            print(json.dumps(line), flush=True)
-        return 0
-
     # ---- code objects and device buffers
     if cfg["kind"] == "mixed":
         codes = [g.Code.polar(n, n // 2) for n in wl.MIXED_N]
@@ -703,13 +740,14 @@ def main():
     evaluated = 0
     hard = 0
     graph_steps = cfg["kind"] == "mixed"
+    split_after = graph_steps or cfg["kind"] == "ab"  # counters from one extra call after the timed steps
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        # GRAND-AB reports no per-kernel split: no statistics, so the step stays asynchronous
-        r = step(d_sym, stats=not graph_steps and cfg["kind"] != "ab")
+        # the graph replay and the one-kernel GRAND-AB step run without statistics (asynchronous)
+        r = step(d_sym, stats=not split_after)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -720,11 +758,14 @@ def main():
             evaluated += r["evaluated_checks"]
             hard += r["hard_frames"]
         useful_total += int(d_q.to(torch.int64).sum().item())  # outside the events
-    if graph_steps:  # kernel split and counters from one direct call of the same batch
+    if split_after:  # kernel split and counters from one direct call of the same batch
+        flush.zero_()
         r = step(d_sym, stats=True)
         search_ms, prep_ms = [r["search_ms"]], [r["prep_ms"]]
         search_useful, evaluated, hard = (r["search_useful"] * args.steps, r["evaluated_checks"] * args.steps,
                                           r["hard_frames"] * args.steps)
+        if cfg["kind"] == "ab":  # one kernel answers every query
+            search_useful = useful_total
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = sum(step_ms)
@@ -820,7 +861,7 @@ def main():
     if cfg["kind"] == "mixed":  # the descriptors are host input too, page-locked like the symbols
         h_desc = torch.from_numpy(desc.view(np.uint8)).pin_memory()
     e2e_ms = []
-    for _ in range(max(2, min(args.steps, 5))):
+    for it in range(1 + max(2, min(args.steps, 5))):  # the first call is untimed (pool growth, streams)
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -837,14 +878,16 @@ def main():
             h_ab.copy_(d_ab, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
+        if it:
+            e2e_ms.append(e0.elapsed_time(e1))
     e2e_value = (useful_total / args.steps) / (statistics.mean(e2e_ms) / 1e3)
     e2e_equal = bool(torch.equal(h_cw, d_cw.cpu()) and torch.equal(h_q, d_q.cpu()) and torch.equal(h_ab, d_ab.cpu()))
 
     # ---- the plain one-frame-per-launch GPU path on a sample (same frames, same results)
     one = None
     if cfg["kind"] in ("qam", "mixed"):
-        n_one = min(2000, n_frames)
+        # S' = 12 frames that abandon run 2^24 queries each in one warp: a smaller sample
+        n_one = min(2000 if cfg.get("S", 10) <= 10 else 200, n_frames)
         idx = np.linspace(0, n_frames - 1, n_one).astype(np.int64)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -866,42 +909,33 @@ def main():
 
     # ---- roofline of the dominant kernel (the TEP search)
     roofline = None
-    if alg_words is not None and sum(search_ms) > 0 and args.membership == "auto":  # TEPs tested one by one
-        import hashlib
-
-        ops = search_useful / args.steps * alg_words
-        achieved = ops / (statistics.mean(search_ms) / 1e3) / 1e12
-        src = os.path.join(ROOT, "paper_2405_01808_gb300", "csrc", "decode.cu")
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        fresh = sha == NCU_SEARCH["sha"] and cfg["name"] == "c2"
-        kernel = "k_search_warp" if cfg["S"] <= 10 else "k_search"
-        roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                    "frac": achieved / ALU_PEAK_TOPS,
-                    "traffic": NCU_SEARCH["dram_bytes_per_hard_frame"] * hard / args.steps if fresh else None,
-                    "kernel": kernel, "ops_per_check": alg_words,
-                    "ops_per_check_note": "model: (N-K)/32 LOP3 per useful check (one per syndrome word); the kernel compares a "
-                                          "16-bit projection bit-sliced (16 ops per 32 checks), 4 more bits on a "
-                                          "match, and verifies matches on the full syndrome",
-                    "ncu_alu_pipe_active": NCU_SEARCH["alu_pipe_active"] if fresh else None,
-                    "ncu_alu_ops_per_evaluated_check": NCU_SEARCH["alu_ops_per_check"] if fresh else None,
-                    "peak_source": f"derived: {SMS} SMs x {ALU_LANES} ALU lanes/clk x {MAX_CLOCK_GHZ} GHz"}
+    if sum(search_ms) > 0 and args.membership == "auto":  # TEPs tested one by one
+        roofline = search_roofline(cfg, evaluated / args.steps, search_useful / args.steps, hard / args.steps,
+                                   statistics.mean(search_ms), alg_words)
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per = {"ab": 3000, "qam": 48, "mixed": 40}[cfg["kind"]]
+        # frames per SNR point (a 2^24-query abandon of the S=12 workloads costs
+        # the oracle 15-25 s of one core, so those take one frame per point
+        # and no single-core leg)
+        per, per1 = {"ab": (3000, 750), "qam": (48, 12), "mixed": (40, 10)}[cfg["kind"]]
+        if cfg["kind"] == "qam" and cfg["S"] > 10:
+            per, per1 = 1, 0
         idx = oracle_sample(cfg, inputs, per)
         threads = os.cpu_count() or 1
         u, f, s = oracle_run(cfg, inputs, idx, threads)
-        cpu = {"value": u / s, "unit": "checks/s", "cores": threads, "kind": "oracle",
+        cpu = {"value": u / s, "unit": "checks/s", "cores": min(threads, f), "kind": "oracle",
                "sample": f"{f} frames ({per} per SNR point) of the same workload", "frames_per_s": f / s,
                "seconds": s}
         # the same oracle on one core, on a quarter of that sample
-        idx1 = oracle_sample(cfg, inputs, max(1, per // 4))
-        u1, f1, s1 = oracle_run(cfg, inputs, idx1, 1)
-        cpu["single_core"] = {"value": u1 / s1, "unit": "checks/s", "frames": f1, "seconds": s1,
-                              "frames_per_s": f1 / s1}
+        if per1:
+            idx1 = oracle_sample(cfg, inputs, per1)
+            u1, f1, s1 = oracle_run(cfg, inputs, idx1, 1)
+            cpu["single_core"] = {"value": u1 / s1, "unit": "checks/s", "frames": f1, "seconds": s1,
+                                  "frames_per_s": f1 / s1}
 
+    line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "checks/s", "n_gpus": world, "steps": args.steps,
@@ -936,6 +970,147 @@ def main():
             "graph": bool(graph_steps),
             "clocks": clk,
         }
+    return line
+
+
+def run_serve_config(args, cfg, g, ctx):
+    """The serving workload as a bench record: Poisson arrivals at each rate
+    through the continuous-batching server (frames/s, p50/p99 latency), and
+    the plain one-frame-per-launch path on a sample of the same requests. The
+    adversarial mix runs twice: long frames whole inside their batch, then
+    carried as device-resident cursors (resume_weight_step)."""
+    rank, world, local = ctx["rank"], ctx["world"], ctx["local"]
+    inputs = make_inputs(cfg, rank, info_sets(cfg, "library"))
+    clocks = ClockSampler(local)
+    clocks.start()
+    rows, one = run_serving(args, cfg, g, inputs, resume_step=0 if cfg.get("adversarial") else args.serve_resume_step)
+    carried = None
+    if cfg.get("adversarial"):
+        carried, _ = run_serving(args, cfg, g, inputs, resume_step=max(1, args.serve_resume_step))
+    clk = clocks.stop()
+    if rank != 0:
+        return None
+    head = (carried or rows)[-1]
+    line = {"metric": METRIC, "value": head["frames_per_s"], "unit": "frames/s", "n_gpus": world,
+            "steps": len(rows), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded random polar codewords over AWGN)",
+            "config": {"workload": cfg["desc"], "requests_per_rate": len(inputs["N"]),
+                       "server": f"max_slots 262144, budget 1 GiB, max_batch {args.serve_batch}, "
+                                 f"{args.serve_streams} streams"},
+            "latency_us": head["latency_us"], "rates": rows, "one_frame_per_launch": one, "clocks": clk,
+            "e2e": {"value": head["frames_per_s"], "unit": "frames/s",
+                    "h2d_bytes_per_step": int(inputs["symbols"].nbytes),
+                    "d2h_bytes_per_step": int(len(inputs["N"]) * 160)},
+            "gpu_launches": int(sum(r["batches"] for r in rows + (carried or [])) * 2)}
+    if carried is not None:
+        line["rates_long_frames_carried"] = carried
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=("gpu", "reference"))
+    ap.add_argument("--config", default=None, choices=sorted(CONFIGS),
+                    help="one workload alone (default: the N=128 16-QAM headline with the other throughput "
+                         "workloads as sub-records)")
+    ap.add_argument("--subconfigs", default="c1,c3a,c3b,c4,c5",
+                    help="workloads measured after the headline in the default run")
+    ap.add_argument("--no-subconfigs", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=0, help="override frames per SNR (for quick runs)")
+    ap.add_argument("--tiles", default="0,0,0,0", help="launch shape (grand_params.tiles), 0 = automatic")
+    ap.add_argument("--membership", default="auto", choices=("auto", "hash"),
+                    help="membership test of the search (the headline uses the TEP-by-TEP search)")
+    ap.add_argument("--serve-batch", type=int, default=65536, help="serving: frames per launch")
+    ap.add_argument("--serve-streams", type=int, default=4, help="serving: batches in flight")
+    ap.add_argument("--serve-resume-step", type=int, default=0,
+                    help="serving: TEP weights per window of a long frame (0: frames searched whole in their batch)")
+    args = ap.parse_args()
+    cfg = dict(CONFIGS[args.config or "c2"])
+    cfg["name"] = args.config or "c2"
+    if args.frames:
+        cfg["frames"] = args.frames
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import paper_2405_01808_gb300 as g
+
+    if rank == 0:
+        g.build()
+    if dist:
+        dist.barrier()
+    g.lib()
+
+    if cfg["kind"] == "bler":
+        rows, fps = run_bler(args, cfg, g)
+        if rank == 0:
+            print(json.dumps({"metric": "BLER vs Eb/N0 (own curves; the paper's Fig. 4 values are not in its text)",
+                              "value": fps, "unit": "frames/s (decode calls of the sweep)", "n_gpus": world,
+                              "steps": len(rows), "warmup": 0, "higher_is_better": True, "dtype": "u32",
+                              "data": "synthetic (seeded random polar codewords over AWGN)",
+                              "config": {"workload": cfg["desc"], "frames_per_point": cfg["frames"]},
+                              "bler": rows}), flush=True)
+        return 0
+    if cfg["kind"] in ("orders", "membership"):
+        clocks = ClockSampler(local)
+        clocks.start()
+        rows = run_orders(args, cfg, g) if cfg["kind"] == "orders" else run_membership(args, cfg, g)
+        clk = clocks.stop()
+        if rank == 0:
+            print(json.dumps({"metric": "TEP order comparison (queries, BLER)" if cfg["kind"] == "orders"
+                              else "membership-test ablation (checks/s)",
+                              "value": rows[0]["useful_checks_per_s"], "unit": "checks/s (first row)",
+                              "n_gpus": world, "steps": 1, "warmup": 1, "higher_is_better": True, "dtype": "u32",
+                              "data": "synthetic (seeded random polar codewords over AWGN)",
+                              "config": {"workload": cfg["desc"]}, "clocks": clk, "rows": rows}), flush=True)
+        return 0
+    ctx = {"rank": rank, "world": world, "dist": dist, "local": local}
+    if cfg["kind"] == "serve":
+        line = run_serve_config(args, cfg, g, ctx)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return 0
+
+    line = run_config(args, cfg, g, ctx)
+    if args.config is None and not args.no_subconfigs:
+        # the other throughput workloads, each measured the same way, as
+        # sub-records of the headline line
+        subs = {}
+        for name in [c for c in args.subconfigs.split(",") if c]:
+            sub = dict(CONFIGS[name])
+            sub["name"] = name
+            gc.collect()
+            torch.cuda.empty_cache()
+            if sub["kind"] == "serve":  # one rate and fewer requests inside the default run
+                if name == "c5":
+                    sub.update(rates=(2e6,), frames=300000,
+                               desc=sub["desc"].replace("0.5/1/2/5 M frames/s", "2 M frames/s").replace(
+                                   "1000000 requests per rate", "300000 requests"))
+                rec = run_serve_config(args, sub, g, ctx)
+            else:
+                rec = run_config(args, sub, g, ctx)
+            if rec is not None:
+                rec.pop("metric", None)
+                rec.pop("n_gpus", None)
+                subs[name] = rec
+        if line is not None:
+            line["configs"] = subs
+    if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -193,7 +193,9 @@ typedef struct grand_frame_desc {
  *   search_useful     valid TEP queries (positions <= the reported query
  *                     count) that fell to the search stage.
  *   prep_ms, search_ms  device time of the preparation and search kernels,
- *                     from CUDA events recorded on the call's stream. */
+ *                     from CUDA events recorded on the call's stream
+ *                     (HAMMING order: prep_ms = 0 and search_ms = the one
+ *                     bit-level kernel). */
 typedef struct grand_stats {
   uint64_t evaluated_checks;
   uint64_t hard_frames;
@@ -301,6 +303,52 @@ int grand_decode_symbols(const grand_code* code, const grand_params* params, con
                          int64_t n_frames, float N0, uint32_t* cw, uint32_t* queries, uint8_t* abandon,
                          grand_stats* stats, void* stream);
 
+/* Resumable decoding: a frame's TEP search in windows of TEP weights, with
+ * the search state (a cursor) kept in device memory between calls.
+ *
+ * Alg. 2 Step 5 queries the TEPs until the first codeword or the cap. In the
+ * canonical order the TEPs come by weight w (altered symbols), so a search
+ * that has tested every valid TEP of weight <= w without a hit can continue
+ * at weight w + 1 and reach exactly the result of an uninterrupted search:
+ * the first hit of the rest of the order is the first hit overall. A cursor
+ * holds what the continuation needs: the frame's base syndrome, its S' least
+ * reliable symbols (flip positions, existing alternatives) and the weight
+ * w_done already tested; GRAND_CURSOR_BYTES bytes, opaque.
+ *
+ * grand_decode_symbols_resumable: as grand_decode_symbols (orders QAM_NNE and
+ * QAM_NEARER, membership AUTO or HASH, automatic split: tiles[1] = 0), but
+ * the search of each frame stops after weight_step (>= 1) weight classes
+ * beyond those the preparation tested (weights <= 2 with default tiles). A
+ * frame with no codeword there, and weights left below the query cap, is
+ * suspended: abandon = GRAND_ABANDON_SUSPENDED (6), queries = the valid TEPs
+ * tested so far (all of weight <= w_done), cw = its hard word, and its cursor
+ * is written to cursors + frame * GRAND_CURSOR_BYTES.
+ *   cursors  device, n_frames * GRAND_CURSOR_BYTES bytes, caller-owned; only
+ *            the entries of suspended frames are written.
+ *   Other frames get their final outputs (decoded, abandoned, 2, 5).
+ *
+ * grand_decode_resume: the next weight_step weight classes (0: all that are
+ * left) of every cursor i in [0, n) whose abandon[i] is 6; cursors whose flag
+ * is anything else are skipped, so the same arrays can be passed again until
+ * no flag is 6. Cursor i writes queries[i], abandon[i] and, on a hit, flips
+ * the decoded bits in cw + i * cw_stride_words (which must hold the frame's
+ * hard word, as the first call left it), and its cursor is updated in place
+ * when it stays suspended. With the arrays of grand_decode_symbols_resumable
+ * (cw_stride_words = N/32) the final outputs equal grand_decode_symbols's
+ * for every frame, whatever the steps. params must equal the first call's
+ * (S, cap, order); a cursor naming another code, or not describing a search
+ * of this code, is marked abandon 3 and not read further.
+ * Errors: GRAND_E_INVALID, GRAND_E_UNSUPPORTED (another order or membership
+ * test, an explicit split), GRAND_E_NOMEM, GRAND_E_CUDA. Asynchronous. */
+#define GRAND_CURSOR_BYTES 144
+#define GRAND_ABANDON_SUSPENDED 6
+int grand_decode_symbols_resumable(const grand_code* code, const grand_params* params, const void* symbols,
+                                   int64_t n_frames, float N0, int32_t weight_step, void* cursors, uint32_t* cw,
+                                   uint32_t* queries, uint8_t* abandon, void* stream);
+int grand_decode_resume(const grand_code* code, const grand_params* params, void* cursors, int64_t n,
+                        int32_t weight_step, uint32_t* cw, int64_t cw_stride_words, uint32_t* queries,
+                        uint8_t* abandon, void* stream);
+
 /* Decode an uneven batch: frames of different codes and constellations in
  * one launch sequence (persistent search kernel with a per-frame work queue).
  * The paper decodes one frame of one (N, M) at a time (Alg. 2) and treats
@@ -400,7 +448,19 @@ int grand_autotune_mixed(const grand_code* const* codes, int n_codes, grand_para
  *                     symbol ring holds max_device_bytes / 8 symbols.
  *   max_batch         frames per launch (0: max_slots).
  *   n_streams         batches in flight at once (1..16).
- *   params.deadline_ns, when nonzero, is the budget of each batch launch. */
+ *   resume_weight_step  0: each frame is searched whole inside its batch.
+ *                     k > 0: a batch searches each frame's TEPs only up to k
+ *                     weight classes beyond the preparation's (the weight
+ *                     windows of grand_decode_symbols_resumable, tiles[1] = 0);
+ *                     a frame with no codeword there leaves the batch as a
+ *                     device-resident cursor in the server's long-frame pool,
+ *                     whose next k weight classes run on a stream of their own
+ *                     as often as the previous window has finished, until the
+ *                     frame is decoded or abandoned. The batch completes without
+ *                     waiting for its long frames; every result equals the
+ *                     uninterrupted search's. The pool holds max_slots cursors.
+ *   params.deadline_ns, when nonzero, is the budget of each batch launch (and
+ *   of each pool window). */
 typedef struct grand_server_cfg {
   const grand_code* const* codes;
   int32_t n_codes;
@@ -410,6 +470,7 @@ typedef struct grand_server_cfg {
   int64_t max_device_bytes;
   int32_t max_batch;
   int32_t n_streams;
+  int32_t resume_weight_step;
 } grand_server_cfg;
 
 /* One decode request. symbols: host complex64 [L], L = ceil(N / log2 M) of the
@@ -437,11 +498,13 @@ typedef struct grand_result {
 
 /* Counters of a server. batch_service_ns: sum over batches of (completion seen
  * - launch start); launch_ns: host time spent issuing batches (copies, decode
- * call, event). */
+ * call, event). long_frames: frames moved to the long-frame pool;
+ * resume_launches: pool windows launched; long_live: frames in the pool now. */
 typedef struct grand_server_stats {
   int64_t admitted, rejected, completed, batches, batched_frames, max_inflight_batches, errors;
   int64_t live_slots, live_bytes, pending, inflight_batches;
   int64_t batch_service_ns, max_batch_service_ns, launch_ns, max_launch_ns;
+  int64_t long_frames, resume_launches, long_live;
 } grand_server_stats;
 
 typedef struct grand_server grand_server;

@@ -34,6 +34,8 @@ LIK_THRESHOLD = 0
 LIK_LITERAL = 1
 E_TIMEOUT = -5         # grand_status GRAND_E_TIMEOUT
 ABANDON_DEADLINE = 5   # abandon flag of a frame cut at grand_params.deadline_ns
+ABANDON_SUSPENDED = 6  # abandon flag of a frame whose resumable search is suspended (GRAND_ABANDON_SUSPENDED)
+CURSOR_BYTES = 144     # GRAND_CURSOR_BYTES: the search state of one suspended frame
 
 _lock = threading.Lock()
 _lib = None
@@ -111,6 +113,8 @@ def lib() -> ctypes.CDLL:
             L.grand_decode_symbols.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, P, P]
             L.grand_decode_mixed.argtypes = [P, i32, P, P, i64, P, i64, ctypes.c_float, P, i64, P, P, P, P]
             L.grand_decode_symbols_noalloc.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, P]
+            L.grand_decode_symbols_resumable.argtypes = [P, P, P, i64, ctypes.c_float, i32, P, P, P, P, P]
+            L.grand_decode_resume.argtypes = [P, P, P, i64, i32, P, i64, P, P, P]
             L.grand_decode_symbols_host.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, i64, P]
             L.grand_decode_mixed_host.argtypes = [P, i32, P, P, i64, P, i64, ctypes.c_float, P, i64, P, P, i64, P]
             L.grand_plan_symbols.argtypes = [P, P, P, i64, ctypes.c_float, P, P, P, ctypes.POINTER(P)]
@@ -382,6 +386,45 @@ def decode_symbols(code: Code, params: Params, symbols, N0: float = 1.0, cw=None
     return _result(cw, queries, abandon, st, stats)
 
 
+def decode_symbols_resumable(code: Code, params: Params, symbols, weight_step: int, cursors=None, N0: float = 1.0,
+                             cw=None, queries=None, abandon=None, stream=None):
+    """grand_decode_symbols_resumable: the decode of `decode_symbols` with each
+    frame's search limited to `weight_step` TEP weights beyond the
+    preparation's. Frames left without a codeword and below the cap come back
+    with abandon ABANDON_SUSPENDED and their cursor in `cursors` (uint8 device
+    tensor of F * CURSOR_BYTES bytes; allocated when None). Returns the outputs
+    and the cursors."""
+    import torch
+
+    F = _check_symbols(symbols, _params_M(params), _symbols_per_frame(code.N, _params_M(params)))
+    _check_outputs(F, code.N, cw, queries, abandon)
+    if cursors is None:
+        cursors = torch.empty(max(1, F) * CURSOR_BYTES, dtype=torch.uint8, device=symbols.device)
+    _need(cursors, "cursors", _dtypes("uint8"), F * CURSOR_BYTES)
+    _require_cuda(symbols, cw, queries, abandon, cursors)
+    sym = torch.view_as_real(symbols) if symbols.is_complex() else symbols
+    cw, queries, abandon = _outputs(F, code.N, symbols.device, cw, queries, abandon)
+    rc = lib().grand_decode_symbols_resumable(code.handle, ctypes.byref(params), _ptr(sym), F, float(N0),
+                                              int(weight_step), _ptr(cursors), _ptr(cw), _ptr(queries),
+                                              _ptr(abandon), _stream(stream))
+    _check(rc, "grand_decode_symbols_resumable")
+    return {"cw": cw, "queries": queries, "abandon": abandon, "cursors": cursors}
+
+
+def decode_resume(code: Code, params: Params, cursors, cw, queries, abandon, weight_step: int = 0, stream=None):
+    """grand_decode_resume: the next `weight_step` TEP weights (0: all left) of
+    every frame whose abandon flag is ABANDON_SUSPENDED, on the arrays of a
+    decode_symbols_resumable call (cw of shape (F, N/32))."""
+    F = queries.numel()
+    _check_outputs(F, code.N, cw, queries, abandon)
+    _need(cursors, "cursors", _dtypes("uint8"), F * CURSOR_BYTES)
+    _require_cuda(cursors, cw, queries, abandon)
+    rc = lib().grand_decode_resume(code.handle, ctypes.byref(params), _ptr(cursors), F, int(weight_step), _ptr(cw),
+                                   code.N // 32, _ptr(queries), _ptr(abandon), _stream(stream))
+    _check(rc, "grand_decode_resume")
+    return {"cw": cw, "queries": queries, "abandon": abandon, "cursors": cursors}
+
+
 def frame_desc(code_idx, M, sym_offset, cw_offset) -> np.ndarray:
     d = np.zeros(len(code_idx), dtype=FRAME_DESC_DTYPE)
     d["code"], d["M"], d["sym_offset"], d["cw_offset"] = code_idx, M, sym_offset, cw_offset
@@ -622,14 +665,15 @@ RESULT_DTYPE = np.dtype([("tag", "<u8"), ("arrival_ns", "<i8"), ("done_ns", "<i8
 class ServerCfg(ctypes.Structure):
     _fields_ = [("codes", ctypes.c_void_p), ("n_codes", ctypes.c_int32), ("params", Params), ("N0", ctypes.c_float),
                 ("max_slots", ctypes.c_int32), ("max_device_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32),
-                ("n_streams", ctypes.c_int32)]
+                ("n_streams", ctypes.c_int32), ("resume_weight_step", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("admitted", "rejected", "completed", "batches", "batched_frames",
                                               "max_inflight_batches", "errors", "live_slots", "live_bytes",
                                               "pending", "inflight_batches", "batch_service_ns",
-                                              "max_batch_service_ns", "launch_ns", "max_launch_ns")]
+                                              "max_batch_service_ns", "launch_ns", "max_launch_ns",
+                                              "long_frames", "resume_launches", "long_live")]
 
 
 def clock_ns() -> int:
@@ -640,7 +684,7 @@ class Server:
     """grand_server_*: continuous-batching decode server on the current device."""
 
     def __init__(self, codes, params: Params, max_slots=65536, max_device_bytes=256 << 20, max_batch=0,
-                 n_streams=4, N0=1.0):
+                 n_streams=4, N0=1.0, resume_weight_step=0):
         self._codes = list(codes)
         self._arr = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
         cfg = ServerCfg()
@@ -650,6 +694,7 @@ class Server:
         cfg.N0 = float(N0)
         cfg.max_slots, cfg.max_device_bytes = int(max_slots), int(max_device_bytes)
         cfg.max_batch, cfg.n_streams = int(max_batch), int(n_streams)
+        cfg.resume_weight_step = int(resume_weight_step)
         h = ctypes.c_void_p()
         _check(lib().grand_server_create(ctypes.byref(cfg), ctypes.byref(h)), "grand_server_create")
         self._h = h

@@ -86,14 +86,105 @@ struct SearchArgs {
   uint32_t* queries;
   uint8_t* abandon;
   long long deadline;  // grand_params.deadline_ns (0: none)
+  // Resumable search (weight windows). w_step > 0: a frame's search covers the
+  // TEP weights w_done + 1 .. w_done + w_step only; a frame with no hit there
+  // and weights left below the cap is suspended (abandon 6, queries = the
+  // valid TEPs tested so far) and its record, with w_done advanced, is written
+  // to cur_out[frame]. cur_in != NULL: the work queue runs over the n_cur
+  // records of cur_in instead of the preparation's (record i writes its
+  // outputs at index i, cw at i * cw_stride) and skips those whose abandon
+  // flag is not 6; cur_out may equal cur_in.
+  int w_step;
+  FrameRec* cur_out;
+  const FrameRec* cur_in;
+  int64_t n_cur;
+  int64_t cw_stride;
+  int n_codes;  // entries of `codes` (a cursor naming another code is rejected)
+  int sp_max;   // largest S' the launched kernel's tables hold
 };
+
+// Output slot of queue entry fi: the batch frame of a preparation record, or
+// the cursor's own index when resuming (computed where needed, so that none of
+// it stays live in registers during the search).
+__device__ __forceinline__ uint32_t out_frame(const SearchArgs& a, unsigned fi, const FrameRec* rec) {
+  return a.cur_in ? fi : rec->frame;
+}
+__device__ __forceinline__ int64_t out_cw_off(const SearchArgs& a, unsigned fi, const FrameRec* rec) {
+  return a.cur_in ? (int64_t)fi * a.cw_stride : rec->cw_off;
+}
+
+// Cursor validation of the resume queue (outlined: it is not on the path of
+// an ordinary decode): a cursor is read only if it describes a search the
+// kernel can run -- a known code, 1 <= S' <= the kernel's bound, w_done < S',
+// existing-alternative masks and flip positions inside the code; otherwise
+// the entry gets abandon 3. Returns whether to search it.
+__device__ __noinline__ bool resume_entry_ok(const SearchArgs& a, unsigned fi) {
+  const FrameRec* rec = a.cur_in + fi;
+  if (a.abandon[fi] != GRAND_ABANDON_SUSPENDED) return false;
+  const int lane = threadIdx.x & 31;
+  bool ok = rec->code < (unsigned)a.n_codes;
+  const int sp = rec->sp;
+  ok = ok && sp >= 1 && sp <= a.sp_max && rec->w_done < sp;
+  if (ok) {
+    const CodeDev& c = a.codes[rec->code];
+    bool mine = true;
+    if (lane < sp) {
+      const uint16_t p0 = rec->pos[lane][0], p1 = rec->pos[lane][1];
+      mine = (p0 == kNoPos || p0 < c.N) && (p1 == kNoPos || p1 < c.N) && (rec->ex[lane] & ~7u) == 0;
+    }
+    ok = __all_sync(kFull, mine);
+  }
+  if (!ok) {
+    __syncwarp();
+    if (lane == 0) {
+      a.abandon[fi] = 3;
+      a.queries[fi] = 0;
+    }
+  }
+  return ok;
+}
+
+// The record of queue entry fi, or NULL when there is nothing to search.
+__device__ __forceinline__ const FrameRec* queue_entry(const SearchArgs& a, unsigned fi) {
+  if (a.cur_in) return resume_entry_ok(a, fi) ? a.cur_in + fi : nullptr;
+  return a.recs + fi;
+}
+
+// Suspend a frame (one warp): its record with w_done advanced to w_hi goes to
+// its cursor slot; outputs say abandon 6 with the valid TEPs tested so far.
+// The hard word stays in cw (the preparation wrote it).
+__device__ __noinline__ void suspend_frame(const SearchArgs& a, unsigned fi, const FrameRec* rec, int w_hi,
+                                           uint32_t tested) {
+  const int lane = threadIdx.x & 31;
+  static_assert(sizeof(FrameRec) % 4 == 0, "FrameRec words");
+  constexpr int kWords = (int)(sizeof(FrameRec) / 4);
+  const uint32_t frame = out_frame(a, fi, rec);
+  FrameRec* cursor = a.cur_out ? a.cur_out + frame : nullptr;
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(rec);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(cursor);
+  uint32_t v[(kWords + 31) / 32];
+#pragma unroll
+  for (int k = 0; k < (kWords + 31) / 32; ++k) v[k] = (lane + 32 * k < kWords) ? src[lane + 32 * k] : 0u;
+  __syncwarp();  // every lane read the record before any lane writes (the cursor may be the record)
+  if (dst) {
+#pragma unroll
+    for (int k = 0; k < (kWords + 31) / 32; ++k)
+      if (lane + 32 * k < kWords) dst[lane + 32 * k] = v[k];
+    __syncwarp();
+    if (lane == 0) cursor->w_done = (uint8_t)w_hi;
+  }
+  if (lane == 0) {
+    a.queries[frame] = tested;
+    a.abandon[frame] = GRAND_ABANDON_SUSPENDED;
+  }
+}
 
 // A hard frame fetched after the call's deadline (lane 0): it keeps what the
 // preparation wrote (cw = the hard word, queries = the valid TEPs it tested
 // without a hit) and is marked abandon 5; the code's status word records it.
-__device__ __forceinline__ bool cut_at_deadline(const SearchArgs& a, const FrameRec* rec) {
+__device__ __forceinline__ bool cut_at_deadline(const SearchArgs& a, const FrameRec* rec, uint32_t frame) {
   if (!past_deadline(&a.scr->t0, a.deadline)) return false;
-  a.abandon[rec->frame] = 5;
+  a.abandon[frame] = 5;
   atomicOr(a.codes[rec->code].status, 1u);
   return true;
 }
@@ -723,7 +814,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_search(SearchArgs a) {
     if (threadIdx.x == 0) {
       const unsigned f = atomicAdd(&a.scr->next, 1u);
       s_frame = f;
-      s_cut = a.deadline > 0 && f < (unsigned)n_hard && cut_at_deadline(a, a.recs + f);
+      s_cut = a.deadline > 0 && f < (unsigned)n_hard && cut_at_deadline(a, a.recs + f, a.recs[f].frame);
     }
     __syncthreads();
     const unsigned fi = s_frame;
@@ -1175,9 +1266,10 @@ __device__ __forceinline__ uint32_t group_acc_part(const uint32_t* planes, int g
 
 // The search of one frame from its hand-off record (one warp; `rec` may live in
 // global or shared memory). Lane 0 accumulates the evaluated and useful checks.
-template <int kSide>
-__device__ __forceinline__ void search_frame(const SearchArgs& a, const FrameRec* rec, const WarpSlice& sl,
-                                             unsigned long long& my_eval, unsigned long long& my_useful) {
+template <int kSide, bool kResume>
+__device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, const FrameRec* rec,
+                                             const WarpSlice& sl, unsigned long long& my_eval,
+                                             unsigned long long& my_useful) {
   using D = WarpDims<kSide>;
   const int lane = threadIdx.x & 31;
   {
@@ -1260,7 +1352,10 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, const FrameRec
     uint32_t best_rank = 0xFFFFFFFFu, best_code = 0;
     int best_w = 127;
     const int nCh = (int)((nB + 31) / 32);
-    const int w_lim = w_cap;  // no TEP heavier than the cap's class matters
+    // weight window of this call: w_done + 1 .. w_hi (all weights without a
+    // step); no TEP heavier than the cap's class matters
+    const int w_hi = kResume && a.w_step > 0 ? min(Sp, w_done + a.w_step) : Sp;
+    const int w_lim = min(w_cap, w_hi);
     for (int ch = 0; ch < nCh; ++ch) {
       const int wb = side_entry_weight(sl.cumB, nBr, 32u * ch);
       const int budget = min(best_w, w_lim) - wb;  // heaviest A weight still worth testing
@@ -1282,7 +1377,12 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, const FrameRec
       // chunk max weight: if it cannot exceed w_done with the heaviest group, skip
       const int wb_hi = side_entry_weight(sl.cumB, nBr, min(nB, 32u * ch + 32u) - 1u);
       if (wb_hi + nAr <= w_done) continue;
-      int g0 = 0;
+      // A groups whose entries all weigh <= w_done - wb_hi pair with this
+      // chunk into TEPs of weight <= w_done only (tested before): skip them
+      int g_start = 0;
+      if (kResume && w_done >= wb_hi)
+        g_start = (int)(sl.cumA[min(w_done - wb_hi, nAr)] / 32) / kGroupUnroll * kGroupUnroll;
+      int g0 = g_start;
       for (; g0 < g_end; g0 += kGroupUnroll) {
         // first level: kPlanesL1 projection bits of kGroupUnroll groups
         uint32_t acc[kGroupUnroll];
@@ -1342,14 +1442,25 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, const FrameRec
         }
       }
       if (lane == 0)
-        my_eval += (unsigned long long)min(nA, 32u * (unsigned)g0) * (unsigned long long)min(32u, nB - 32u * ch);
+        my_eval += (unsigned long long)(min(nA, 32u * (unsigned)g0) - min(nA, 32u * (unsigned)g_start)) *
+                   (unsigned long long)min(32u, nB - 32u * ch);
     }
     // --- result -------------------------------------------------------------
+    const bool hit = best_rank != 0xFFFFFFFFu && (uint64_t)best_rank <= (uint64_t)a.cap;
+    if (kResume && !hit && w_hi < w_cap) {  // no codeword up to w_hi, weights left below the cap
+      uint32_t tested = 0, done = 0;
+      for (int v = 0; v <= w_hi; ++v) tested += sl.E[Sp * kEStride + v];
+      for (int v = 0; v <= w_done; ++v) done += sl.E[Sp * kEStride + v];
+      suspend_frame(a, fi, rec, w_hi, tested);
+      if (lane == 0) my_useful += tested - done;
+      __syncwarp();
+      return;
+    }
     if (lane == 0) {
-      const unsigned f = rec->frame;
+      const unsigned f = out_frame(a, fi, rec);
       uint32_t q_out;
-      if (best_rank != 0xFFFFFFFFu && (uint64_t)best_rank <= (uint64_t)a.cap) {
-        uint32_t* cw = a.cw + rec->cw_off;
+      if (hit) {
+        uint32_t* cw = a.cw + out_cw_off(a, fi, rec);
         for (int r = 0; r < Sp; ++r) {
           const uint32_t d = (best_code >> (2 * r)) & 3u;
           if (d & 1u) { const uint16_t p = sl.pos[2 * r]; if (p != kNoPos) cw[p >> 5] ^= 1u << (p & 31); }
@@ -1370,25 +1481,27 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, const FrameRec
   }
 }
 
-template <int kMinBlocks, int kSide>
+template <int kMinBlocks, int kSide, bool kResume>
 __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31;
   const WarpSlice sl =
       warp_slice<kSide>(smem_raw + (threadIdx.x >> 5) * warp_slice_bytes<kSide>(a.Wmax), a.Wmax);
-  const unsigned n_hard = *(volatile unsigned*)&a.scr->n_hard;
+  const unsigned n_hard = kResume && a.cur_in ? (unsigned)a.n_cur : *(volatile unsigned*)&a.scr->n_hard;
   unsigned long long my_eval = 0, my_useful = 0;
   for (;;) {
     unsigned fi = 0;
     if (lane == 0) fi = atomicAdd(&a.scr->next, 1u);
     fi = __shfl_sync(kFull, fi, 0);
     if (fi >= n_hard) break;
+    const FrameRec* rec = kResume ? queue_entry(a, fi) : a.recs + fi;
+    if (!rec) continue;
     if (a.deadline > 0) {
       int cut = 0;
-      if (lane == 0) cut = cut_at_deadline(a, a.recs + fi);
+      if (lane == 0) cut = cut_at_deadline(a, rec, out_frame(a, fi, rec));
       if (__shfl_sync(kFull, cut, 0)) continue;
     }
-    search_frame<kSide>(a, a.recs + fi, sl, my_eval, my_useful);
+    search_frame<kSide, kResume>(a, fi, rec, sl, my_eval, my_useful);
   }
   if (lane == 0) {
     if (my_eval) atomicAdd(&a.scr->evaluated, my_eval);
@@ -1433,7 +1546,7 @@ __host__ __device__ inline size_t hash_slice_bytes(int Wmax) {
   return warp_slice_bytes<kSide, false>(Wmax) + 4 * (size_t)HashDims<kSide>::kSlots;
 }
 
-template <int kSide>
+template <int kSide, bool kResume>
 __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
   using HD = HashDims<kSide>;
   extern __shared__ __align__(16) char smem_raw[];
@@ -1441,7 +1554,7 @@ __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
   char* base = smem_raw + (threadIdx.x >> 5) * hash_slice_bytes<kSide>(a.Wmax);
   const WarpSlice sl = warp_slice<kSide, false>(base, a.Wmax);
   uint32_t* hslot = reinterpret_cast<uint32_t*>(base + warp_slice_bytes<kSide, false>(a.Wmax));
-  const unsigned n_hard = *(volatile unsigned*)&a.scr->n_hard;
+  const unsigned n_hard = kResume && a.cur_in ? (unsigned)a.n_cur : *(volatile unsigned*)&a.scr->n_hard;
   unsigned long long my_eval = 0, my_useful = 0;
 
   for (;;) {
@@ -1449,12 +1562,13 @@ __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
     if (lane == 0) fi = atomicAdd(&a.scr->next, 1u);
     fi = __shfl_sync(kFull, fi, 0);
     if (fi >= n_hard) break;
+    const FrameRec* rec = kResume ? queue_entry(a, fi) : a.recs + fi;
+    if (!rec) continue;
     if (a.deadline > 0) {
       int cut = 0;
-      if (lane == 0) cut = cut_at_deadline(a, a.recs + fi);
+      if (lane == 0) cut = cut_at_deadline(a, rec, out_frame(a, fi, rec));
       if (__shfl_sync(kFull, cut, 0)) continue;
     }
-    const FrameRec* rec = a.recs + fi;
     const int Sp = rec->sp;
     const int w_done = rec->w_done;
     const CodeDev code = a.codes[rec->code];
@@ -1486,8 +1600,22 @@ __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
     __syncwarp();
     const uint32_t total = esp_total(sl.E, Sp);
     const int nAr = Sp >> 1, nBr = Sp - nAr;
-    const unsigned nA = warp_side_layout(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, sl.cumA);
-    const unsigned nB = warp_side_layout(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, sl.cumB);
+    const unsigned nA_all = warp_side_layout(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, sl.cumA);
+    const unsigned nB_all = warp_side_layout(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, sl.cumB);
+    // weight window: w_done + 1 .. w_hi. With a step, only entries of weight
+    // <= w_hi take part and a pair heavier than w_hi is not a hit; the cap's
+    // weight class w_cap decides whether an empty window suspends the frame.
+    int w_cap = Sp;
+    if (kResume) {
+      uint64_t acc = 0;
+      for (int v = 0; v <= Sp; ++v) {
+        acc += sl.E[Sp * kEStride + v];
+        if (acc >= (uint64_t)a.cap) { w_cap = v; break; }
+      }
+    }
+    const int w_hi = kResume && a.w_step > 0 ? min(Sp, w_done + a.w_step) : Sp;
+    const unsigned nA = (!kResume || w_hi >= nAr) ? nA_all : sl.cumA[w_hi];
+    const unsigned nB = (!kResume || w_hi >= nBr) ? nB_all : sl.cumB[w_hi];
     // A side: projections (with s0's) into the hash table -- by doubling into
     // the scalar buffer for 5-rank sides, from the table layout otherwise
     if constexpr (kSide == kWarpSideMax) warp_fill_side(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, f0, sl.Bz);
@@ -1533,7 +1661,7 @@ __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
         orr |= zz;
       }
       ++my_eval;
-      if (orr == 0) {
+      if (orr == 0 && (!kResume || code_weight(cc) <= w_hi)) {
         const uint32_t rk = tep_rank(sl.E, Sp, sl.ex, cc);
         if (rk < lr) {
           lr = rk;
@@ -1595,11 +1723,21 @@ __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
     const unsigned who = __ballot_sync(kFull, lr == best_rank);
     const uint32_t best_code = __shfl_sync(kFull, lc, __ffs(who) - 1);
     // --- result -------------------------------------------------------------
+    const bool hit = best_rank != 0xFFFFFFFFu && (uint64_t)best_rank <= (uint64_t)a.cap;
+    if (kResume && !hit && w_hi < w_cap) {  // no codeword up to w_hi, weights left below the cap
+      uint32_t tested = 0, done = 0;
+      for (int v = 0; v <= w_hi; ++v) tested += sl.E[Sp * kEStride + v];
+      for (int v = 0; v <= w_done; ++v) done += sl.E[Sp * kEStride + v];
+      suspend_frame(a, fi, rec, w_hi, tested);
+      if (lane == 0) my_useful += tested - done;
+      __syncwarp();
+      continue;
+    }
     if (lane == 0) {
-      const unsigned f = rec->frame;
+      const unsigned f = out_frame(a, fi, rec);
       uint32_t q_out;
-      if (best_rank != 0xFFFFFFFFu && (uint64_t)best_rank <= (uint64_t)a.cap) {
-        uint32_t* cw = a.cw + rec->cw_off;
+      if (hit) {
+        uint32_t* cw = a.cw + out_cw_off(a, fi, rec);
         for (int r = 0; r < Sp; ++r) {
           const uint32_t d = (best_code >> (2 * r)) & 3u;
           if (d & 1u) { const uint16_t p = sl.pos[2 * r]; if (p != kNoPos) cw[p >> 5] ^= 1u << (p & 31); }
@@ -1772,6 +1910,218 @@ __global__ void __launch_bounds__(128) k_ab(AbArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Bit-level GRAND-AB on a code whose syndrome fits one word (N - K <= 32) and
+// N <= 64, weights <= 3: the TEPs split into a pair and a single.
+//
+// A TEP of weight 3, positions p1 < p2 < p3, is a codeword iff
+//     s0 ^ h_p1 ^ h_p2 == h_p3          (h_j = column j of H, s0 = H y).
+// Its colex rank is C(p3,3) + c with c = C(p2,2) + p1 the colex rank of the
+// pair, so the first hit in canonical order is the hit of smallest p3 and,
+// among those, of smallest c. Each lane takes one pair per step (pairs in
+// colex order) and compares its target s0 ^ h_p1 ^ h_p2 with 32 columns at
+// once: the columns of a 32-position group are held as R bit-planes
+// (plane[b] bit i = bit b of h_{32 g + i}), and OR_b(plane[b] ^ -(t_b)) has a
+// zero at every column equal to t -- 3 logic ops per syndrome bit for 32
+// TEPs. Weights 1 and 2 use the same compare (a single against s0, a column
+// p2 against s0 ^ h_p2). A step whose pairs all have p2 >= the best p3 so far
+// cannot improve it, which ends the weight-3 walk of a decoded frame early.
+// The planes depend only on the code: a CTA builds them once and keeps them
+// in registers for all its frames. Ranks fit 32 bits for N <= 1024.
+// ---------------------------------------------------------------------------
+// Columns of group g equal to t (bit i: column 32 g + i). g must be a
+// compile-time constant after unrolling (the planes stay in registers).
+template <int kNG, int kR>
+__device__ __forceinline__ uint32_t ab_match(const uint32_t (&plane)[kNG][kR], int g, uint32_t t) {
+  uint32_t acc = 0;
+#pragma unroll
+  for (int b = 0; b < kR; ++b) acc |= plane[g][b] ^ (0u - ((t >> b) & 1u));
+  return ~acc;
+}
+
+// Word w of a frame's words held uniformly by every lane, picked without
+// dynamic register indexing.
+template <int kNG>
+__device__ __forceinline__ uint32_t pick_word(const uint32_t (&v)[kNG], int w) {
+  uint32_t r = v[0];
+#pragma unroll
+  for (int i = 1; i < kNG; ++i)
+    if (w == i) r = v[i];
+  return r;
+}
+
+template <int kNG, int kR>
+__global__ void __launch_bounds__(128) k_ab_split(AbArgs a) {
+  __shared__ uint32_t s_h[4][32 * kNG];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  constexpr int N = 32 * kNG;
+  uint32_t* h = s_h[wib];
+  // columns and their bit-planes (code constants; syndrome bits >= kR are 0)
+  uint32_t plane[kNG][kR];
+#pragma unroll
+  for (int g = 0; g < kNG; ++g) {
+    const uint32_t col = __ldg(a.code.hcol + 32 * g + lane);
+    h[32 * g + lane] = col;
+#pragma unroll
+    for (int b = 0; b < kR; ++b) plane[g][b] = __ballot_sync(kFull, (col >> b) & 1u);
+  }
+  __syncwarp();
+  const uint32_t c2N = (uint32_t)(N * (N - 1) / 2);
+  uint64_t total = 0;
+  for (int w = 0; w <= a.max_weight; ++w) total += binom_big(N, w);
+  const uint64_t cap = (uint64_t)a.cap;
+  unsigned long long evaluated = 0;
+  for (int64_t f = gwarp; f < a.n_frames; f += nwarps) {
+    bool nonfinite = false;
+    uint32_t ywords[kNG];
+    if (a.samples) {
+#pragma unroll
+      for (int w = 0; w < kNG; ++w) {
+        float v = a.samples[f * N + 32 * w + lane];
+        const bool nf = !isfinite(v);
+        nonfinite |= nf;
+        if (nf) v = 0.0f;
+        ywords[w] = __ballot_sync(kFull, v < 0.0f);
+      }
+    } else {
+#pragma unroll
+      for (int w = 0; w < kNG; ++w) ywords[w] = __ldg(a.y_in + f * kNG + w);
+      if (a.nmask)
+        for (int j = lane; j < N; j += 32) nonfinite |= (a.nmask[f * N + j] & 128u) != 0;
+    }
+    nonfinite = __any_sync(kFull, nonfinite);
+    if (nonfinite) {
+      if (lane < kNG) a.cw[f * kNG + lane] = pick_word<kNG>(ywords, lane);
+      if (lane == 0) { a.queries[f] = 0; a.abandon[f] = 2; }
+      continue;
+    }
+    if (a.deadline > 0) {
+      int cut = 0;
+      if (lane == 0) cut = past_deadline(&a.scr->t0, a.deadline);
+      if (__shfl_sync(kFull, cut, 0)) {  // not searched: the hard word, marked 5
+        if (lane < kNG) a.cw[f * kNG + lane] = pick_word<kNG>(ywords, lane);
+        if (lane == 0) { a.queries[f] = 0; a.abandon[f] = 5; atomicOr(a.code.status, 1u); }
+        continue;
+      }
+    }
+    // base syndrome s0 = H y: XOR of the columns at the one-bits of y
+    uint32_t part = 0;
+#pragma unroll
+    for (int w = 0; w < kNG; ++w)
+      if ((ywords[w] >> lane) & 1u) part ^= h[32 * w + lane];
+    const uint32_t s0 = __reduce_xor_sync(kFull, part);
+    // first hit: weight and colex rank within the weight (positions p[0..w-1])
+    int hit_w = -1;
+    uint32_t hit_rank = 0;
+    if (s0 == 0) {
+      hit_w = 0;
+      evaluated += (lane == 0);
+    }
+    if (hit_w < 0 && a.max_weight >= 1 && cap > 1) {
+      uint32_t best = 0xFFFFFFFFu;
+#pragma unroll
+      for (int g = 0; g < kNG; ++g) {
+        const uint32_t m = ab_match<kNG, kR>(plane, g, s0);
+        if (m) best = min(best, (uint32_t)(32 * g + __ffs(m) - 1));
+      }
+      evaluated += (lane == 0) ? N : 0;
+      if (best != 0xFFFFFFFFu) { hit_w = 1; hit_rank = best; }
+    }
+    if (hit_w < 0 && a.max_weight >= 2 && cap > 1 + (uint64_t)N) {
+      // lane = p2 (per group step), matches p1 < p2
+      uint32_t best = 0xFFFFFFFFu;
+#pragma unroll
+      for (int s = 0; s < kNG; ++s) {
+        const int p2 = 32 * s + lane;
+        const uint32_t t = s0 ^ h[p2];
+#pragma unroll
+        for (int g = 0; g <= s; ++g) {
+          uint32_t m = ab_match<kNG, kR>(plane, g, t);
+          if (g == s) m &= (1u << lane) - 1u;  // p1 < p2
+          if (m) best = min(best, (uint32_t)(p2 * (p2 - 1) / 2 + 32 * g + __ffs(m) - 1));
+        }
+        evaluated += (uint32_t)p2;
+      }
+      best = __reduce_min_sync(kFull, best);
+      if (best != 0xFFFFFFFFu) { hit_w = 2; hit_rank = best; }
+    }
+    if (hit_w < 0 && a.max_weight >= 3 && cap > 1 + (uint64_t)N + c2N) {
+      // kPairs pairs per lane and step (independent compares in flight: the
+      // step count, which sets an abandoned frame's latency, drops by kPairs)
+      constexpr int kPairs = 4;
+      uint32_t best = 0xFFFFFFFFu;  // colex rank of the best triple so far
+      int best_p3 = N;
+      for (uint32_t base = 0; base < c2N; base += 32 * kPairs) {
+        // smallest p2 of this step's pairs: pairs are in colex order
+        int p2 = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)base)) * 0.5f);
+        while ((uint32_t)(p2 * (p2 - 1) / 2) > base) --p2;
+        while ((uint32_t)((p2 + 1) * p2 / 2) <= base) ++p2;
+        if (p2 >= best_p3 - 1) break;  // every later pair needs p3 > p2 >= best_p3 - 1
+#pragma unroll
+        for (int k = 0; k < kPairs; ++k) {
+          const uint32_t c = base + 32 * k + lane;
+          if (c < c2N) {
+            int q2 = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)c)) * 0.5f);
+            while ((uint32_t)(q2 * (q2 - 1) / 2) > c) --q2;
+            while ((uint32_t)((q2 + 1) * q2 / 2) <= c) ++q2;
+            const int q1 = (int)(c - (uint32_t)(q2 * (q2 - 1) / 2));
+            const uint32_t t = s0 ^ h[q1] ^ h[q2];
+#pragma unroll
+            for (int g = 0; g < kNG; ++g) {
+              if (32 * g + 31 <= q2) continue;  // every p3 of the group is <= p2
+              uint32_t m = ab_match<kNG, kR>(plane, g, t);
+              if (32 * g <= q2) m &= ~((2u << (q2 - 32 * g)) - 1u);  // p3 > p2
+              if (m) {
+                const uint32_t p3 = 32 * g + __ffs(m) - 1;
+                best = min(best, (uint32_t)(p3 * (p3 - 1) * (p3 - 2) / 6) + c);
+                break;
+              }
+            }
+            evaluated += (uint32_t)(N - 1 - q2);
+          }
+        }
+        best = __reduce_min_sync(kFull, best);
+        if (best != 0xFFFFFFFFu) {
+          int p3 = 2;
+          while ((uint32_t)((p3 + 1) * p3 * (p3 - 1) / 6) <= best) ++p3;
+          best_p3 = p3;
+        }
+      }
+      if (best != 0xFFFFFFFFu) { hit_w = 3; hit_rank = best; }
+    }
+    // query position of the hit (1-based) and the decoded word
+    uint64_t q = 0;
+    if (hit_w >= 0) {
+      uint64_t start = 0;
+      for (int w = 0; w < hit_w; ++w) start += binom_big(N, w);
+      q = start + hit_rank + 1;
+    }
+    const bool decoded = hit_w >= 0 && q <= cap;
+    if (lane < kNG) {
+      uint32_t word = pick_word<kNG>(ywords, lane);
+      if (decoded) {
+        // unrank the hit's positions (colex, largest first)
+        uint32_t rem = hit_rank;
+        for (int j = hit_w; j >= 1; --j) {
+          int pj = j - 1;
+          while (binom_big(pj + 1, j) <= rem) ++pj;
+          rem -= (uint32_t)binom_big(pj, j);
+          if ((pj >> 5) == lane) word ^= 1u << (pj & 31);
+        }
+      }
+      a.cw[f * kNG + lane] = word;
+    }
+    if (lane == 0) {
+      a.queries[f] = (uint32_t)(decoded ? q : min(total, cap));
+      a.abandon[f] = decoded ? 0 : 1;
+    }
+  }
+  for (int o = 16; o; o >>= 1) evaluated += __shfl_xor_sync(kFull, evaluated, o);
+  if (lane == 0 && evaluated && a.scr) atomicAdd(&a.scr->evaluated, evaluated);
+}
+
+// ---------------------------------------------------------------------------
 // Public demodulation: one thread per symbol
 // ---------------------------------------------------------------------------
 struct DemodArgs {
@@ -1791,20 +2141,28 @@ struct DemodArgs {
 // skipped); rl = the symbol's Gray label bits in transmission order (bit k =
 // label bit 2m-1-k), for the hard word. kM = log2(sqrt(M)) is a template
 // argument so that the level arithmetic folds into constants.
-template <int kM>
+// Square root by the SFU's approximate instruction (relative error about
+// 2^-22, far inside the 1e-5 tolerance of the reported likelihood).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+template <int kM, int kLit>
 __device__ __forceinline__ void demod_one(const DemodArgs& a, float2 v, uint16_t& hidx, uint32_t& key, uint8_t& nmask,
                                           float& rel, uint32_t& rl) {
   const bool nf = !(isfinite(v.x) && isfinite(v.y));
   if (nf) v = make_float2(0.0f, 0.0f);
-  const AxisDemod I = demod_axis_q(v.x, a.q, 1 << kM, a.lik);
-  const AxisDemod Q = demod_axis_q(v.y, a.q, 1 << kM, a.lik);
+  const AxisDemod I = demod_axis_q(v.x, a.q, 1 << kM, kLit);
+  const AxisDemod Q = demod_axis_q(v.y, a.q, 1 << kM, kLit);
   hidx = (uint16_t)((I.level << 8) | Q.level);
   key = (uint32_t)I.dq * (uint32_t)I.dq + (uint32_t)Q.dq * (uint32_t)Q.dq;
   nmask = (uint8_t)make_nmask(I, Q, nf);
   if (a.rel) {
-    const float dI = axis_dist_f32(v.x, a.inv_d, I.amp, I.outside, a.lik);
-    const float dQ = axis_dist_f32(v.y, a.inv_d, Q.amp, Q.outside, a.lik);
-    rel = sqrtf(dI * dI + dQ * dQ);
+    const float dI = axis_dist_f32(v.x, a.inv_d, I.amp, I.outside, kLit);
+    const float dQ = axis_dist_f32(v.y, a.inv_d, Q.amp, Q.outside, kLit);
+    rel = sqrt_approx(dI * dI + dQ * dQ);
   }
   const uint32_t label = ((uint32_t)gray_code(I.level) << kM) | (uint32_t)gray_code(Q.level);
   rl = __brev(label) >> (32 - 2 * kM);
@@ -1821,19 +2179,22 @@ __device__ __forceinline__ void or_bits(uint32_t* yf, int NW, int p0, uint32_t b
 
 // Two symbols per thread: 16-byte loads, paired stores (every pointer aligned
 // for its pair type, checked by the host); otherwise one symbol per thread.
-// The frame of a symbol is found once per pair; the pair's label bits go into
-// the hard word with one OR when both symbols belong to the same frame.
-template <bool kPaired, int kM>
-__global__ void __launch_bounds__(256) k_demod(DemodArgs a) {
+// The frame of a symbol is found once per thread and then advanced by the
+// grid stride (a quotient and remainder of the stride by L, no division per
+// step); the pair's label bits go into the hard word with one OR when both
+// symbols belong to the same frame. kLit: the likelihood reading (selects
+// fold into constants).
+template <bool kPaired, int kM, int kLit>
+__global__ void __launch_bounds__(256, 8) k_demod(DemodArgs a) {
   constexpr int b2 = 2 * kM;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   if constexpr (!kPaired) {
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_sym;
-         s += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_sym; s += gstride) {
       uint16_t h0;
       uint32_t k0, rl0;
       uint8_t m0;
       float r0 = 0.0f;
-      demod_one<kM>(a, a.symbols[s], h0, k0, m0, r0, rl0);
+      demod_one<kM, kLit>(a, a.symbols[s], h0, k0, m0, r0, rl0);
       if (a.hard_idx) a.hard_idx[s] = h0;
       if (a.key) a.key[s] = k0;
       if (a.nmask) a.nmask[s] = m0;
@@ -1848,7 +2209,14 @@ __global__ void __launch_bounds__(256) k_demod(DemodArgs a) {
   }
   const int64_t n_pairs = a.n_sym >> 1;
   const float4* sym4 = reinterpret_cast<const float4*>(a.symbols);
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= n_pairs; t += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // frame f and symbol i of this thread's first pair, and the symbol stride
+  // 2 * gstride = dq frames + dr symbols
+  int64_t f = (int64_t)__umul64hi((uint64_t)(2 * t0), a.Lmagic);
+  int i = (int)(2 * t0 - f * a.L);
+  const int64_t dq = (int64_t)__umul64hi((uint64_t)(2 * gstride), a.Lmagic);
+  const int dr = (int)(2 * gstride - dq * a.L);
+  for (int64_t t = t0; t <= n_pairs; t += gstride) {
     const int64_t s = 2 * t;
     if (t < n_pairs) {
       const float4 v = sym4[t];
@@ -1856,15 +2224,13 @@ __global__ void __launch_bounds__(256) k_demod(DemodArgs a) {
       uint32_t k0, k1, rl0, rl1;
       uint8_t m0, m1;
       float r0 = 0.0f, r1 = 0.0f;
-      demod_one<kM>(a, make_float2(v.x, v.y), h0, k0, m0, r0, rl0);
-      demod_one<kM>(a, make_float2(v.z, v.w), h1, k1, m1, r1, rl1);
+      demod_one<kM, kLit>(a, make_float2(v.x, v.y), h0, k0, m0, r0, rl0);
+      demod_one<kM, kLit>(a, make_float2(v.z, v.w), h1, k1, m1, r1, rl1);
       if (a.hard_idx) reinterpret_cast<ushort2*>(a.hard_idx)[t] = make_ushort2(h0, h1);
       if (a.key) reinterpret_cast<uint2*>(a.key)[t] = make_uint2(k0, k1);
       if (a.nmask) reinterpret_cast<uchar2*>(a.nmask)[t] = make_uchar2(m0, m1);
       if (a.rel) reinterpret_cast<float2*>(a.rel)[t] = make_float2(r0, r1);
       if (a.y) {
-        const int64_t f = (int64_t)__umul64hi((uint64_t)s, a.Lmagic);
-        const int i = (int)(s - f * a.L);
         uint32_t* yf = a.y + f * a.NW;
         if (i + 1 < a.L) {
           or_bits(yf, a.NW, b2 * i, rl0 | (rl1 << b2));
@@ -1878,16 +2244,19 @@ __global__ void __launch_bounds__(256) k_demod(DemodArgs a) {
       uint32_t k0, rl0;
       uint8_t m0;
       float r0 = 0.0f;
-      demod_one<kM>(a, a.symbols[s], h0, k0, m0, r0, rl0);
+      demod_one<kM, kLit>(a, a.symbols[s], h0, k0, m0, r0, rl0);
       if (a.hard_idx) a.hard_idx[s] = h0;
       if (a.key) a.key[s] = k0;
       if (a.nmask) a.nmask[s] = m0;
       if (a.rel) a.rel[s] = r0;
-      if (a.y) {
-        const int64_t f = (int64_t)__umul64hi((uint64_t)s, a.Lmagic);
-        const int i = (int)(s - f * a.L);
-        or_bits(a.y + f * a.NW, a.NW, b2 * i, rl0);
-      }
+      if (a.y) or_bits(a.y + f * a.NW, a.NW, b2 * i, rl0);
+    }
+    // advance to the next pair of this thread
+    f += dq;
+    i += dr;
+    if (i >= a.L) {
+      i -= a.L;
+      f += 1;
     }
   }
 }
@@ -1912,10 +2281,17 @@ __global__ void __launch_bounds__(256) k_demod_bpsk(const float* r, int64_t n_wo
 
 template <int kM>
 static void launch_demod_m(const DemodArgs& a, bool paired, int grid, cudaStream_t st) {
-  if (paired)
-    k_demod<true, kM><<<grid, 256, 0, st>>>(a);
-  else
-    k_demod<false, kM><<<grid, 256, 0, st>>>(a);
+  if (a.lik == GRAND_LIK_LITERAL) {
+    if (paired)
+      k_demod<true, kM, 1><<<grid, 256, 0, st>>>(a);
+    else
+      k_demod<false, kM, 1><<<grid, 256, 0, st>>>(a);
+  } else {
+    if (paired)
+      k_demod<true, kM, 0><<<grid, 256, 0, st>>>(a);
+    else
+      k_demod<false, kM, 0><<<grid, 256, 0, st>>>(a);
+  }
 }
 
 // m = log2(sqrt(M)) in 1..6 (validated by the caller).
@@ -1942,16 +2318,50 @@ static PrepKernel prep_kernel_for(int Wmax) {
 
 
 
+// Resident CTAs per SM of a kernel for one launch shape on the current
+// device, with its dynamic shared-memory limit raised to the request: both
+// runtime queries are made once per (kernel, device, shape) and cached, so a
+// launch costs no attribute or occupancy call after the first.
+static int resident_ctas(const void* kern, int threads, size_t smem) {
+  struct Entry {
+    const void* kern;
+    int dev, threads;
+    size_t smem;
+    int per_sm;
+  };
+  // a fixed table (no heap allocation on any launch path); when it is full
+  // the queries are simply made every time
+  constexpr int kEntries = 512;
+  static std::mutex mu;
+  static Entry cache[kEntries];
+  static int used = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t most = smem;  // the attribute is a per-kernel maximum: never lower it
+  for (int i = 0; i < used; ++i) {
+    const Entry& e = cache[i];
+    if (e.kern != kern || e.dev != dev) continue;
+    if (e.threads == threads && e.smem == smem) return e.per_sm;
+    if (e.smem > most) most = e.smem;
+  }
+  if (most > 48 * 1024 &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) != cudaSuccess)
+    return -1;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess) return -1;
+  if (per_sm < 1) per_sm = 1;
+  if (used < kEntries) cache[used++] = Entry{kern, dev, threads, smem, per_sm};
+  return per_sm;
+}
+
 // Persistent launch of the search kernel: one wave of CTAs (as many as fit
 // on every SM) pulling frames from the work queue. variant: register budget
 // (4, 6 or 8 CTAs of 256 threads per SM; 0 = 4).
 template <int B>
 static int launch_search_t(const SearchArgs& s, int threads, size_t smem, cudaStream_t st) {
-  if (cudaFuncSetAttribute(k_search<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return GRAND_E_CUDA;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search<B>, threads, smem);
-  if (per_sm < 1) per_sm = 1;
+  const int per_sm = resident_ctas((const void*)k_search<B>, threads, smem);
+  if (per_sm < 0) return GRAND_E_CUDA;
   k_search<B><<<sm_count() * per_sm, threads, smem, st>>>(s);
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
@@ -1960,12 +2370,9 @@ template <int B, int Side>
 static int launch_search_warp_t(const SearchArgs& s, int warps, cudaStream_t st) {
   constexpr int kSide = Side;
   const size_t smem = warp_slice_bytes<kSide>(s.Wmax) * warps;
-  auto kern = k_search_warp<B, kSide>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return GRAND_E_CUDA;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem);
-  if (per_sm < 1) per_sm = 1;
+  auto kern = (s.w_step > 0 || s.cur_in) ? k_search_warp<B, kSide, true> : k_search_warp<B, kSide, false>;
+  const int per_sm = resident_ctas((const void*)kern, 32 * warps, smem);
+  if (per_sm < 0) return GRAND_E_CUDA;
   kern<<<sm_count() * per_sm, 32 * warps, smem, st>>>(s);
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
@@ -1973,12 +2380,9 @@ static int launch_search_warp_t(const SearchArgs& s, int warps, cudaStream_t st)
 template <int kSide>
 static int launch_search_hash_t(const SearchArgs& s, int warps, cudaStream_t st) {
   const size_t hsmem = hash_slice_bytes<kSide>(s.Wmax) * warps;
-  auto kern = k_search_hash<kSide>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem) != cudaSuccess)
-    return GRAND_E_CUDA;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, hsmem);
-  if (per_sm < 1) per_sm = 1;
+  auto kern = (s.w_step > 0 || s.cur_in) ? k_search_hash<kSide, true> : k_search_hash<kSide, false>;
+  const int per_sm = resident_ctas((const void*)kern, 32 * warps, hsmem);
+  if (per_sm < 0) return GRAND_E_CUDA;
   kern<<<sm_count() * per_sm, 32 * warps, hsmem, st>>>(s);
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
@@ -2019,10 +2423,14 @@ int preload_qam_kernels() {
   const void* kernels[] = {
       (const void*)k_prep<1>, (const void*)k_prep<2>, (const void*)k_prep<4>, (const void*)k_prep<8>,
       (const void*)k_prep<16>,
-      (const void*)k_search_warp<4, kWarpSideMax>, (const void*)k_search_warp<6, kWarpSideMax>,
-      (const void*)k_search_warp<8, kWarpSideMax>, (const void*)k_search_warp<4, kWarpSideMax + 1>,
-      (const void*)k_search_warp<6, kWarpSideMax + 1>, (const void*)k_search_warp<8, kWarpSideMax + 1>,
-      (const void*)k_search_hash<kWarpSideMax>, (const void*)k_search_hash<kWarpSideMax + 1>,
+      (const void*)k_search_warp<4, kWarpSideMax, false>, (const void*)k_search_warp<6, kWarpSideMax, false>,
+      (const void*)k_search_warp<8, kWarpSideMax, false>, (const void*)k_search_warp<4, kWarpSideMax + 1, false>,
+      (const void*)k_search_warp<6, kWarpSideMax + 1, false>, (const void*)k_search_warp<8, kWarpSideMax + 1, false>,
+      (const void*)k_search_warp<4, kWarpSideMax, true>, (const void*)k_search_warp<6, kWarpSideMax, true>,
+      (const void*)k_search_warp<8, kWarpSideMax, true>, (const void*)k_search_warp<4, kWarpSideMax + 1, true>,
+      (const void*)k_search_warp<6, kWarpSideMax + 1, true>, (const void*)k_search_warp<8, kWarpSideMax + 1, true>,
+      (const void*)k_search_hash<kWarpSideMax, false>, (const void*)k_search_hash<kWarpSideMax + 1, false>,
+      (const void*)k_search_hash<kWarpSideMax, true>, (const void*)k_search_hash<kWarpSideMax + 1, true>,
       (const void*)k_search<4>, (const void*)k_search<6>, (const void*)k_search<8>};
   for (const void* k : kernels) {
     cudaFuncAttributes attr;
@@ -2041,11 +2449,28 @@ int preload_qam_kernels() {
 // params and the call's largest S' and syndrome length. Every symbol-level
 // call (direct, mixed, plans, the fixed-scratch variant) launches it here, so
 // they run the same kernel for the same params.
+// Options of a resumable search (weight windows and cursors; see SearchArgs).
+struct ResumeOpt {
+  int w_step = 0;
+  FrameRec* cur_out = nullptr;
+  const FrameRec* cur_in = nullptr;
+  int64_t n_cur = 0;
+  int64_t cw_stride = 0;
+  int n_codes = 1;
+};
+
 static int launch_qam_search(const grand_params* p, int Smax, int w0, int Wmax, const CodeDev* d_codes,
                              const FrameRec* recs, Scratch* scr, uint32_t* cw, uint32_t* queries, uint8_t* abandon,
-                             cudaStream_t st) {
+                             cudaStream_t st, const ResumeOpt& ro = ResumeOpt()) {
   if (Smax <= w0) return GRAND_OK;  // the preparation finished every frame
   SearchArgs s{};
+  s.w_step = ro.w_step;
+  s.cur_out = ro.cur_out;
+  s.cur_in = ro.cur_in;
+  s.n_cur = ro.n_cur;
+  s.cw_stride = ro.cw_stride;
+  s.n_codes = ro.n_codes;
+  s.sp_max = Smax;
   s.recs = recs;
   s.codes = d_codes;
   s.scr = scr;
@@ -2077,7 +2502,8 @@ static int launch_qam_search(const grand_params* p, int Smax, int w0, int Wmax, 
 
 // Common body of the symbol-level decode calls.
 static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, const grand_params* p,
-                   const PrepArgs& proto, int64_t n_frames, grand_stats* stats, cudaStream_t st) {
+                   const PrepArgs& proto, int64_t n_frames, grand_stats* stats, cudaStream_t st,
+                   const ResumeOpt& ro = ResumeOpt()) {
   if (n_frames == 0) {
     if (stats) *stats = grand_stats{};
     return GRAND_OK;
@@ -2108,8 +2534,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     const int64_t want = (n_frames + warps - 1) / warps;
     const int grid = (int)(want < (int64_t)sm_count() * 64 ? want : (int64_t)sm_count() * 64);
     auto kp = prep_kernel_for(Wmax);
-    if (prep_smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem) != cudaSuccess) {
+    if (prep_smem > 48 * 1024 && resident_ctas((const void*)kp, 32 * warps, prep_smem) < 0) {  // raises the limit
       rc = GRAND_E_CUDA;
       break;
     }
@@ -2126,7 +2551,9 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     if (stats) cudaEventRecord(ev[1], st);
     if (cudaGetLastError() != cudaSuccess) { rc = GRAND_E_CUDA; break; }
 
-    if (launch_qam_search(p, Smax, a.w0, Wmax, d_codes, recs, scr, proto.cw, proto.queries, proto.abandon, st) !=
+    ResumeOpt ro2 = ro;
+    ro2.n_codes = n_codes;
+    if (launch_qam_search(p, Smax, a.w0, Wmax, d_codes, recs, scr, proto.cw, proto.queries, proto.abandon, st, ro2) !=
         GRAND_OK) {
       rc = GRAND_E_CUDA;
       break;
@@ -2190,8 +2617,13 @@ static int run_ab(const grand_code* c, const grand_params* p, const float* sampl
   Scratch* scr = nullptr;
   if (scratch_alloc((void**)&scr, sizeof(Scratch), st) != cudaSuccess) return GRAND_E_NOMEM;
   int rc = GRAND_OK;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
   do {
     if (cudaMemsetAsync(scr, 0, sizeof(Scratch), st) != cudaSuccess) { rc = GRAND_E_CUDA; break; }
+    if (stats) {
+      if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) { rc = GRAND_E_CUDA; break; }
+      cudaEventRecord(ev[0], st);
+    }
     AbArgs a{};
     a.samples = samples;
     a.y_in = y;
@@ -2206,10 +2638,23 @@ static int run_ab(const grand_code* c, const grand_params* p, const float* sampl
     a.scr = scr;
     a.deadline = p->deadline_ns;
     const int64_t want = (n_frames + 3) / 4;
-    const int grid = (int)(want < (int64_t)sm_count() * 64 ? want : (int64_t)sm_count() * 64);
-    k_ab<<<grid, 128, 0, st>>>(a);
+    if (p->max_weight <= 3 && c->W == 1 && (c->N == 32 || c->N == 64)) {
+      // pair x single split with the columns as bit-planes in registers
+      const int grid = (int)(want < (int64_t)sm_count() * 16 ? want : (int64_t)sm_count() * 16);
+      if (c->N == 32) {
+        if (c->R <= 16) k_ab_split<1, 16><<<grid, 128, 0, st>>>(a);
+        else k_ab_split<1, 32><<<grid, 128, 0, st>>>(a);
+      } else {
+        if (c->R <= 16) k_ab_split<2, 16><<<grid, 128, 0, st>>>(a);
+        else k_ab_split<2, 32><<<grid, 128, 0, st>>>(a);
+      }
+    } else {
+      const int grid = (int)(want < (int64_t)sm_count() * 64 ? want : (int64_t)sm_count() * 64);
+      k_ab<<<grid, 128, 0, st>>>(a);
+    }
     if (cudaGetLastError() != cudaSuccess) { rc = GRAND_E_CUDA; break; }
     if (stats) {
+      cudaEventRecord(ev[1], st);
       Scratch h{};
       if (cudaMemcpyAsync(&h, scr, sizeof(Scratch), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
           cudaStreamSynchronize(st) != cudaSuccess) {
@@ -2219,9 +2664,12 @@ static int run_ab(const grand_code* c, const grand_params* p, const float* sampl
       stats->evaluated_checks = h.evaluated;
       stats->hard_frames = 0;
       stats->search_useful = 0;
-      stats->prep_ms = stats->search_ms = 0.0f;
+      stats->prep_ms = 0.0f;
+      cudaEventElapsedTime(&stats->search_ms, ev[0], ev[1]);  // the one search kernel
     }
   } while (0);
+  for (int i = 0; i < 2; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
   cudaFreeAsync(scr, st);
   return rc;
 }
@@ -2351,6 +2799,67 @@ extern "C" int grand_decode_symbols(const grand_code* c, const grand_params* p, 
 
 namespace grand {
 
+// Checks shared by the resumable calls: the split search (automatic split) of
+// the symbol-level orders, with a membership test that supports weight windows.
+static int check_resumable(const grand_params* p) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p->order != GRAND_ORDER_QAM_NNE && p->order != GRAND_ORDER_QAM_NEARER) return GRAND_E_UNSUPPORTED;
+  if (p->membership != GRAND_MEMBERSHIP_AUTO && p->membership != GRAND_MEMBERSHIP_HASH) return GRAND_E_UNSUPPORTED;
+  if (p->tiles[1] > 0) return GRAND_E_UNSUPPORTED;  // the CTA-per-frame search has no weight windows
+  return GRAND_OK;
+}
+
+}  // namespace grand
+
+extern "C" int grand_decode_symbols_resumable(const grand_code* c, const grand_params* p, const void* symbols,
+                                              int64_t n_frames, float N0, int32_t weight_step, void* cursors,
+                                              uint32_t* cw, uint32_t* queries, uint8_t* abandon, void* stream) {
+  using namespace grand;
+  static_assert(sizeof(FrameRec) == GRAND_CURSOR_BYTES, "cursor size");
+  if (!c || n_frames < 0 || (n_frames > 0 && (!symbols || !cw || !queries || !abandon || !cursors)))
+    return GRAND_E_INVALID;
+  if (!(N0 > 0.0f) || !isfinite(N0) || weight_step < 1) return GRAND_E_INVALID;
+  int rc = check_resumable(p);
+  if (rc) return rc;
+  const int m = m_of(p->M);
+  if (!m) return GRAND_E_INVALID;
+  if (n_frames > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
+  const int L = (c->N + 2 * m - 1) / (2 * m);
+  PrepArgs a{};
+  a.symbols = (const float2*)symbols;
+  a.codes = c->d_dev;
+  a.n_codes = 1;
+  a.n_frames = n_frames;
+  a.M = p->M;
+  a.S = p->S;
+  a.lik = p->lik_variant;
+  a.cap = p->query_cap;
+  a.qc = make_qam_const();
+  a.cw = cw;
+  a.queries = queries;
+  a.abandon = abandon;
+  ResumeOpt ro;
+  ro.w_step = weight_step;
+  ro.cur_out = static_cast<FrameRec*>(cursors);
+  return run_qam(c->d_dev, 1, L, c->W, p, a, n_frames, nullptr, (cudaStream_t)stream, ro);
+}
+
+extern "C" int grand_decode_resume(const grand_code* c, const grand_params* p, void* cursors, int64_t n,
+                                   int32_t weight_step, uint32_t* cw, int64_t cw_stride_words, uint32_t* queries,
+                                   uint8_t* abandon, void* stream) {
+  using namespace grand;
+  if (!c || n < 0 || (n > 0 && (!cursors || !cw || !queries || !abandon))) return GRAND_E_INVALID;
+  if (weight_step < 0 || cw_stride_words < c->N / 32) return GRAND_E_INVALID;
+  int rc = check_resumable(p);
+  if (rc) return rc;
+  if (n > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
+  return resume_resident(c->d_dev, 1, c->W, p, static_cast<FrameRec*>(cursors), n, weight_step, cw,
+                         cw_stride_words, queries, abandon, (cudaStream_t)stream);
+}
+
+namespace grand {
+
 // Code table of an uneven batch: device views plus the batch-wide bounds.
 static int code_table(const grand_code* const* codes, int n_codes, std::vector<CodeDev>& table, int& Lmax, int& Wmax) {
   Wmax = 1;
@@ -2386,7 +2895,7 @@ static int check_mixed_args(const grand_code* const* codes, int n_codes, const g
 static int mixed_impl(const CodeDev* d_table, int n_codes, int Lmax, int Wmax, const grand_params* p,
                       const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
                       uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon, grand_stats* stats,
-                      cudaStream_t st) {
+                      cudaStream_t st, const ResumeOpt& ro = ResumeOpt()) {
   PrepArgs a{};
   a.symbols = (const float2*)symbols;
   a.desc = desc;
@@ -2403,14 +2912,46 @@ static int mixed_impl(const CodeDev* d_table, int n_codes, int Lmax, int Wmax, c
   a.cw = cw;
   a.queries = queries;
   a.abandon = abandon;
-  return run_qam(d_table, n_codes, Lmax, Wmax, p, a, n_frames, stats, st);
+  return run_qam(d_table, n_codes, Lmax, Wmax, p, a, n_frames, stats, st, ro);
 }
 
 int decode_mixed_resident(const CodeDev* d_table, int n_codes, int Lmax, int Wmax, const grand_params* p,
                           const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
-                          uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon, cudaStream_t st) {
+                          uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon, cudaStream_t st,
+                          int w_step, FrameRec* cursors) {
+  ResumeOpt ro;
+  ro.w_step = w_step;
+  ro.cur_out = cursors;
   return mixed_impl(d_table, n_codes, Lmax, Wmax, p, desc, n_frames, symbols, n_symbols, cw, n_cw_words, queries,
-                    abandon, nullptr, st);
+                    abandon, nullptr, st, ro);
+}
+
+// The search over suspended cursors (grand_decode_resume, the serving loop's
+// long frames): one search launch with cursor i's outputs at index i.
+int resume_resident(const CodeDev* d_table, int n_codes, int Wmax, const grand_params* p, FrameRec* cursors,
+                    int64_t n, int w_step, uint32_t* cw, int64_t cw_stride, uint32_t* queries, uint8_t* abandon,
+                    cudaStream_t st) {
+  if (n == 0) return GRAND_OK;
+  Scratch* scr = nullptr;
+  if (scratch_alloc((void**)&scr, sizeof(Scratch), st) != cudaSuccess) return GRAND_E_NOMEM;
+  int rc = GRAND_OK;
+  if (cudaMemsetAsync(scr, 0, sizeof(Scratch), st) != cudaSuccess) rc = GRAND_E_CUDA;
+  if (rc == GRAND_OK) {
+    ResumeOpt ro;
+    ro.w_step = w_step;
+    ro.cur_out = cursors;
+    ro.cur_in = cursors;
+    ro.n_cur = n;
+    ro.cw_stride = cw_stride;
+    ro.n_codes = n_codes;
+    const int Smax = p->S < kSMax ? p->S : kSMax;
+    // w0 = 0: every cursor goes to the search (the preparation is not run)
+    NvtxRange range("grand.resume");
+    if (launch_qam_search(p, Smax, 0, Wmax, d_table, nullptr, scr, cw, queries, abandon, st, ro) != GRAND_OK)
+      rc = GRAND_E_CUDA;
+  }
+  cudaFreeAsync(scr, st);
+  return rc;
 }
 
 }  // namespace grand
@@ -2640,9 +3181,7 @@ extern "C" int grand_decode_symbols_noalloc(const grand_code* c, const grand_par
   const int warps = 4;
   const size_t prep_smem = prep_warp_bytes(L, c->W) * warps;
   auto kp = prep_kernel_for(c->W);
-  if (prep_smem > 48 * 1024 &&
-      cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem) != cudaSuccess)
-    return GRAND_E_CUDA;
+  if (prep_smem > 48 * 1024 && resident_ctas((const void*)kp, 32 * warps, prep_smem) < 0) return GRAND_E_CUDA;
   const int64_t want = (n_frames + warps - 1) / warps;
   const int grid = (int)(want < (int64_t)sm_count() * 64 ? want : (int64_t)sm_count() * 64);
   kp<<<grid, 32 * warps, prep_smem, st>>>(a);

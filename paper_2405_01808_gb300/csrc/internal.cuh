@@ -78,10 +78,22 @@ int preload_qam_kernels();
 
 // grand_decode_mixed on a code table already resident on the device (the
 // serving loop keeps one for its lifetime). The caller has validated params
-// (QAM order, membership AUTO); Lmax / Wmax bound L and W over the table.
+// (QAM order, membership AUTO or HASH); Lmax / Wmax bound L and W over the
+// table. w_step > 0 with cursors: the resumable search (frames with no hit in
+// the first w_step weights beyond the preparation's get abandon 6 and their
+// cursor at cursors[frame]).
 int decode_mixed_resident(const CodeDev* d_table, int n_codes, int Lmax, int Wmax, const grand_params* p,
                           const grand_frame_desc* desc, int64_t n_frames, const void* symbols, int64_t n_symbols,
-                          uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon, cudaStream_t st);
+                          uint32_t* cw, int64_t n_cw_words, uint32_t* queries, uint8_t* abandon, cudaStream_t st,
+                          int w_step = 0, FrameRec* cursors = nullptr);
+
+// The next weight window of every suspended cursor (abandon 6) of
+// cursors[0..n): cursor i writes its outputs at queries[i], abandon[i] and
+// cw + i * cw_stride, and stays suspended (with its w_done advanced) when the
+// window holds no codeword and weights below the cap remain.
+int resume_resident(const CodeDev* d_table, int n_codes, int Wmax, const grand_params* p, FrameRec* cursors,
+                    int64_t n, int w_step, uint32_t* cw, int64_t cw_stride, uint32_t* queries, uint8_t* abandon,
+                    cudaStream_t st);
 
 }  // namespace grand
 

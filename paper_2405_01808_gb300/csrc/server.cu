@@ -17,6 +17,18 @@
 // lock and hands the stream back. Results carry the arrival and completion
 // times (CLOCK_MONOTONIC). Ring space is reclaimed in launch order; results
 // are delivered in completion order. Every wait is bounded.
+//
+// Long frames (resume_weight_step > 0): a batch searches each frame only up
+// to resume_weight_step TEP weights beyond the preparation's; a frame with no
+// codeword there is suspended and its cursor (the search state, see
+// grand_decode_symbols_resumable) moves into a device-resident pool of long
+// frames, so the batch completes and its other frames are reported at once.
+// The launcher runs the pool's next weight window on a stream of its own
+// whenever no pool launch is in flight; a frame leaves the pool when its
+// search ends (decoded or abandoned), with the outputs an uninterrupted
+// search gives. The carry (records, hard words, counters) is a device-side
+// gather on the pool's stream; the batch's stream waits for it before its
+// buffers are reused.
 #include <errno.h>
 #include <stdlib.h>
 #include <string.h>
@@ -57,6 +69,11 @@ struct Req {
 
 struct StreamBuf {
   cudaStream_t stream = nullptr;
+  grand::FrameRec* d_cur = nullptr;   // per-frame cursors of the batch (long frames)
+  int2* h_pairs = nullptr;            // (frame, pool slot) of the frames to carry
+  int2* d_pairs = nullptr;
+  cudaEvent_t carried = nullptr;      // the carry out of this stream's buffers is done
+  bool wait_carry = false;            // the next batch waits for `carried`
   grand_frame_desc* d_desc = nullptr;
   grand_frame_desc* h_desc = nullptr;
   uint32_t* d_cw = nullptr;
@@ -77,6 +94,8 @@ struct Batch {
   cudaEvent_t ev;
   bool done;
   int status;
+  int64_t carried_bytes = 0;  // budget and slots of frames moved to the long-frame pool
+  int32_t carried = 0;
 };
 
 // Completed results waiting for poll, in completion order.
@@ -113,6 +132,28 @@ struct grand_server {
   std::thread launcher, harvester;
   std::atomic<bool> stop{false};
   grand_server_stats st{};
+  // long-frame pool (resume_weight_step > 0): cursor, hard word / decoded word,
+  // queries and abandon flag per slot on the device, host mirrors, requests
+  int32_t step = 0;
+  int32_t pool_cap = 0;
+  grand::FrameRec* d_pcur = nullptr;
+  uint32_t* d_pcw = nullptr;
+  uint32_t* d_pq = nullptr;
+  uint8_t* d_pab = nullptr;
+  uint32_t* h_pcw = nullptr;
+  uint32_t* h_pq = nullptr;
+  uint8_t* h_pab = nullptr;
+  cudaStream_t pstream = nullptr;
+  cudaEvent_t pev = nullptr;
+  std::vector<Req> preq;          // request of each live slot
+  std::vector<char> plive;
+  std::vector<int32_t> pfree;     // free slots
+  int32_t plive_n = 0;
+  bool presume = false;           // a pool launch is in flight
+  bool pissued = false;           // ... and its event is recorded (the harvester may look)
+  bool pfailed = false;           // ... and it could not be issued
+  std::vector<int32_t> psnap;     // live slots when it was launched
+  int64_t presume_ns = 0;
 };
 
 namespace {
@@ -120,8 +161,13 @@ namespace {
 int64_t request_bytes(int L, int N) { return 8ll * L + (int64_t)sizeof(grand::FrameRec) + 4ll * (N / 32) + 5; }
 
 void free_server(grand_server* s) {
+  if (s->pstream) cudaStreamSynchronize(s->pstream);
   for (StreamBuf& b : s->sb) {
     if (b.stream) cudaStreamSynchronize(b.stream);
+    cudaFree(b.d_cur);
+    cudaFree(b.d_pairs);
+    cudaFreeHost(b.h_pairs);
+    if (b.carried) cudaEventDestroy(b.carried);
     cudaFree(b.d_desc);
     cudaFree(b.d_cw);
     cudaFree(b.d_q);
@@ -133,10 +179,38 @@ void free_server(grand_server* s) {
     if (b.stream) cudaStreamDestroy(b.stream);
   }
   for (Batch& b : s->inflight) cudaEventDestroy(b.ev);
+  cudaFree(s->d_pcur);
+  cudaFree(s->d_pcw);
+  cudaFree(s->d_pq);
+  cudaFree(s->d_pab);
+  cudaFreeHost(s->h_pcw);
+  cudaFreeHost(s->h_pq);
+  cudaFreeHost(s->h_pab);
+  if (s->pev) cudaEventDestroy(s->pev);
+  if (s->pstream) cudaStreamDestroy(s->pstream);
   cudaFree(s->d_table);
   cudaFree(s->d_ring);
   cudaFreeHost(s->h_ring);
   delete s;
+}
+
+// Move suspended frames of a finished batch into the long-frame pool: warp k
+// copies pair k's cursor, hard word, query count and flag.
+__global__ void k_carry(const int2* pairs, int n, const grand::FrameRec* cur, const uint32_t* cw, const uint32_t* q,
+                        const uint8_t* ab, grand::FrameRec* pcur, uint32_t* pcw, uint32_t* pq, uint8_t* pab) {
+  const int lane = threadIdx.x & 31;
+  const int k = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (k >= n) return;
+  const int f = pairs[k].x, slot = pairs[k].y;
+  constexpr int kWords = (int)(sizeof(grand::FrameRec) / 4);
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(cur + f);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(pcur + slot);
+  for (int w = lane; w < kWords; w += 32) dst[w] = src[w];
+  pcw[(size_t)slot * kResultWords + lane] = cw[(size_t)f * kResultWords + lane];
+  if (lane == 0) {
+    pq[slot] = q[f];
+    pab[slot] = ab[f];
+  }
 }
 
 // Issue batch b on stream si (no lock held; b.reqs was taken under it).
@@ -144,6 +218,8 @@ int launch_batch(grand_server* s, int si, Batch& b) {
   grand::NvtxRange range("grand.server.batch");
   StreamBuf& buf = s->sb[si];
   const int n = (int)b.reqs.size();
+  // the previous batch's long frames must have left this stream's buffers
+  if (buf.wait_carry && cudaStreamWaitEvent(buf.stream, buf.carried, 0) != cudaSuccess) return GRAND_E_CUDA;
   for (int i = 0; i < n; ++i) {
     const Req& r = b.reqs[i];
     buf.h_desc[i].code = r.code;
@@ -169,7 +245,7 @@ int launch_batch(grand_server* s, int si, Batch& b) {
     return GRAND_E_CUDA;
   int rc = grand::decode_mixed_resident(s->d_table, (int)s->codes.size(), s->Lmax, s->Wmax, &s->cfg.params,
                                         buf.d_desc, n, s->d_ring, s->ring_cap, buf.d_cw, (int64_t)n * kResultWords,
-                                        buf.d_q, buf.d_ab, buf.stream);
+                                        buf.d_q, buf.d_ab, buf.stream, s->step, s->step > 0 ? buf.d_cur : nullptr);
   if (rc != GRAND_OK) return rc;
   if (cudaMemcpyAsync(buf.h_cw, buf.d_cw, sizeof(uint32_t) * n * kResultWords, cudaMemcpyDeviceToHost, buf.stream) !=
           cudaSuccess ||
@@ -180,6 +256,21 @@ int launch_batch(grand_server* s, int si, Batch& b) {
   return GRAND_OK;
 }
 
+// The next weight window of the long-frame pool's live slots [0, hi), on the
+// pool's stream, and the read-back of their outputs (no lock held).
+int launch_pool(grand_server* s, int32_t hi) {
+  grand::NvtxRange range("grand.server.resume");
+  int rc = grand::resume_resident(s->d_table, (int)s->codes.size(), s->Wmax, &s->cfg.params, s->d_pcur, hi, s->step,
+                                  s->d_pcw, kResultWords, s->d_pq, s->d_pab, s->pstream);
+  if (rc != GRAND_OK) return rc;
+  if (cudaMemcpyAsync(s->h_pcw, s->d_pcw, sizeof(uint32_t) * hi * kResultWords, cudaMemcpyDeviceToHost, s->pstream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(s->h_pq, s->d_pq, sizeof(uint32_t) * hi, cudaMemcpyDeviceToHost, s->pstream) != cudaSuccess ||
+      cudaMemcpyAsync(s->h_pab, s->d_pab, hi, cudaMemcpyDeviceToHost, s->pstream) != cudaSuccess)
+    return GRAND_E_CUDA;
+  return cudaEventRecord(s->pev, s->pstream) == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
+}
+
 void launcher_main(grand_server* s) {
   cudaSetDevice(s->device);
   for (;;) {
@@ -187,13 +278,39 @@ void launcher_main(grand_server* s) {
     int si = -1;
     {
       std::unique_lock<std::mutex> lk(s->mu);
+      int32_t pool_hi = -1;
       while (!s->stop.load(std::memory_order_acquire)) {
+        if (s->step > 0 && !s->presume && s->plive_n > 0) {  // the long frames' next window
+          s->psnap.clear();
+          for (int32_t k = 0; k < s->pool_cap; ++k)
+            if (s->plive[k]) {
+              s->psnap.push_back(k);
+              pool_hi = k + 1;
+            }
+          s->presume = true;
+          s->presume_ns = now_ns();
+          s->st.resume_launches += 1;
+          break;
+        }
         if (!s->pending.empty() && s->pending.front().ready) {
           for (int i = 0; i < (int)s->sb.size(); ++i)
             if (!s->sb[i].busy) { si = i; break; }
           if (si >= 0) break;
         }
         s->cv_launch.wait_for(lk, std::chrono::milliseconds(1));  // bounded: re-check
+      }
+      if (pool_hi > 0) {
+        lk.unlock();
+        const int rc = launch_pool(s, pool_hi);
+        if (rc != GRAND_OK) cudaEventRecord(s->pev, s->pstream);  // the harvester sees the failure
+        {
+          std::unique_lock<std::mutex> lk2(s->mu);
+          s->running += 1;
+          s->pfailed = rc != GRAND_OK;
+          s->pissued = true;
+        }
+        s->cv_harvest.notify_one();
+        continue;
       }
       if (si < 0) return;  // stop
       const int maxb = s->cfg.max_batch;
@@ -230,6 +347,59 @@ void launcher_main(grand_server* s) {
   }
 }
 
+// A finished pool launch: report the slots of its snapshot whose search
+// ended, free them; the others stay for the next window. Returns whether a
+// launch was harvested.
+bool harvest_pool(grand_server* s) {
+  std::vector<int32_t> snap;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (!s->presume || !s->pissued) return false;
+    snap = s->psnap;
+  }
+  const cudaError_t q = cudaEventQuery(s->pev);
+  if (q == cudaErrorNotReady) return false;
+  const int64_t t = now_ns();
+  Chunk c;
+  std::vector<int32_t> freed;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);  // preq of live slots is read under the lock
+    const bool failed = q != cudaSuccess || s->pfailed;
+    for (int32_t k : snap) {
+      if (!failed && s->h_pab[k] == GRAND_ABANDON_SUSPENDED) continue;
+      c.v.emplace_back();
+      grand_result& r = c.v.back();
+      memset(&r, 0, sizeof r);
+      r.tag = s->preq[k].tag;
+      r.arrival_ns = s->preq[k].arrival_ns;
+      r.done_ns = t;
+      if (!failed) {
+        r.queries = s->h_pq[k];
+        r.abandon = s->h_pab[k];
+        memcpy(r.cw, s->h_pcw + (size_t)k * kResultWords, sizeof(uint32_t) * s->preq[k].nw);
+      } else {
+        r.abandon = 4;
+      }
+      freed.push_back(k);
+    }
+    for (int32_t k : freed) {
+      s->plive[k] = 0;
+      s->plive_n -= 1;
+      s->pfree.push_back(k);
+      s->live_slots -= 1;
+      s->live_bytes -= s->preq[k].bytes;
+    }
+    s->st.completed += (int64_t)freed.size();
+    if (failed) s->st.errors += 1;
+    if (!c.v.empty()) s->done.push_back(std::move(c));
+    s->presume = false;
+    s->pissued = false;
+    s->running -= 1;
+  }
+  s->cv_launch.notify_one();
+  return true;
+}
+
 void harvester_main(grand_server* s) {
   cudaSetDevice(s->device);
   std::vector<Batch*> running;
@@ -251,11 +421,22 @@ void harvester_main(grand_server* s) {
       any = true;
       const int64_t t = now_ns();
       const int status = q == cudaSuccess ? b->status : GRAND_E_CUDA;
-      const StreamBuf& buf = s->sb[b->stream];
+      StreamBuf& buf = s->sb[b->stream];
+      // frames the batch's weight window suspended go to the long-frame pool
+      std::vector<int> carry;
+      if (status == GRAND_OK && s->step > 0)
+        for (size_t i = 0; i < b->reqs.size(); ++i)
+          if (buf.h_ab[i] == GRAND_ABANDON_SUSPENDED) carry.push_back((int)i);
       Chunk c;
-      c.v.resize(b->reqs.size());
+      c.v.reserve(b->reqs.size() - carry.size());
+      size_t ci = 0;
       for (size_t i = 0; i < b->reqs.size(); ++i) {
-        grand_result& r = c.v[i];
+        if (ci < carry.size() && carry[ci] == (int)i) {
+          ++ci;
+          continue;
+        }
+        c.v.emplace_back();
+        grand_result& r = c.v.back();
         memset(&r, 0, sizeof r);
         r.tag = b->reqs[i].tag;
         r.arrival_ns = b->reqs[i].arrival_ns;
@@ -268,13 +449,43 @@ void harvester_main(grand_server* s) {
           r.abandon = 4;  // the batch failed on the device
         }
       }
+      std::vector<int32_t> slots;
+      if (!carry.empty()) {
+        {
+          std::unique_lock<std::mutex> lk(s->mu);
+          for (size_t k = 0; k < carry.size(); ++k) {  // a carried request keeps its admission slot: never empty
+            slots.push_back(s->pfree.back());
+            s->pfree.pop_back();
+          }
+        }
+        const int nc = (int)carry.size();
+        for (int k = 0; k < nc; ++k) buf.h_pairs[k] = make_int2(carry[k], slots[k]);
+        // on the pool's stream (ordered before any later pool launch); the
+        // batch's stream waits for it before its buffers are reused
+        cudaMemcpyAsync(buf.d_pairs, buf.h_pairs, sizeof(int2) * nc, cudaMemcpyHostToDevice, s->pstream);
+        k_carry<<<(nc * 32 + 127) / 128, 128, 0, s->pstream>>>(buf.d_pairs, nc, buf.d_cur, buf.d_cw, buf.d_q, buf.d_ab,
+                                                             s->d_pcur, s->d_pcw, s->d_pq, s->d_pab);
+        cudaEventRecord(buf.carried, s->pstream);
+      }
       {
         std::unique_lock<std::mutex> lk(s->mu);
+        for (size_t k = 0; k < carry.size(); ++k) {
+          const Req& r = b->reqs[carry[k]];
+          s->preq[slots[k]] = r;
+          s->plive[slots[k]] = 1;
+          s->plive_n += 1;
+          b->carried += 1;
+          b->carried_bytes += r.bytes;
+        }
+        if (!carry.empty()) {
+          buf.wait_carry = true;
+          s->st.long_frames += (int64_t)carry.size();
+        }
         s->done.push_back(std::move(c));
         b->done = true;
         b->status = status;
         s->running -= 1;
-        s->st.completed += b->reqs.size();
+        s->st.completed += b->reqs.size() - carry.size();
         s->st.batch_service_ns += t - b->launch_ns;
         if (t - b->launch_ns > s->st.max_batch_service_ns) s->st.max_batch_service_ns = t - b->launch_ns;
         if (status != GRAND_OK) s->st.errors += 1;
@@ -283,14 +494,15 @@ void harvester_main(grand_server* s) {
         while (!s->inflight.empty() && s->inflight.front().done) {
           Batch& f = s->inflight.front();
           s->vtail = f.vend;
-          s->live_bytes -= f.bytes;
-          s->live_slots -= (int)f.reqs.size();
+          s->live_bytes -= f.bytes - f.carried_bytes;
+          s->live_slots -= (int)f.reqs.size() - f.carried;
           cudaEventDestroy(f.ev);
           s->inflight.pop_front();
         }
       }
       s->cv_launch.notify_one();
     }
+    if (s->step > 0 && harvest_pool(s)) any = true;
     if (!any) std::this_thread::sleep_for(std::chrono::microseconds(5));
   }
 }
@@ -306,8 +518,9 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
   if ((cfg->params.order != GRAND_ORDER_QAM_NNE && cfg->params.order != GRAND_ORDER_QAM_NEARER) ||
       (cfg->params.membership != GRAND_MEMBERSHIP_AUTO && cfg->params.membership != GRAND_MEMBERSHIP_HASH) ||
       cfg->params.query_cap < 1 || cfg->params.deadline_ns < 0 || cfg->params.S < 0 ||
-      cfg->params.S > GRAND_S_MAX)
+      cfg->params.S > GRAND_S_MAX || cfg->resume_weight_step < 0)
     return GRAND_E_INVALID;
+  if (cfg->resume_weight_step > 0 && cfg->params.tiles[1] > 0) return GRAND_E_UNSUPPORTED;
   for (int i = 0; i < cfg->n_codes; ++i)
     if (!cfg->codes[i]) return GRAND_E_INVALID;
   *out = nullptr;
@@ -345,7 +558,38 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
   }
   s->sb.resize(cfg->n_streams);
   const size_t mb = (size_t)s->cfg.max_batch;
+  s->step = cfg->resume_weight_step;
+  if (s->step > 0) {
+    // one pool slot per admission slot: a carried request keeps its slot
+    s->pool_cap = s->cfg.max_slots;
+    const size_t pc = (size_t)s->pool_cap;
+    if (cudaStreamCreateWithFlags(&s->pstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->pev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc((void**)&s->d_pcur, sizeof(grand::FrameRec) * pc) != cudaSuccess ||
+        cudaMalloc((void**)&s->d_pcw, sizeof(uint32_t) * pc * kResultWords) != cudaSuccess ||
+        cudaMalloc((void**)&s->d_pq, sizeof(uint32_t) * pc) != cudaSuccess ||
+        cudaMalloc((void**)&s->d_pab, pc) != cudaSuccess ||
+        cudaMallocHost((void**)&s->h_pcw, sizeof(uint32_t) * pc * kResultWords) != cudaSuccess ||
+        cudaMallocHost((void**)&s->h_pq, sizeof(uint32_t) * pc) != cudaSuccess ||
+        cudaMallocHost((void**)&s->h_pab, pc) != cudaSuccess ||
+        cudaMemset(s->d_pab, 0, pc) != cudaSuccess) {
+      free_server(s);
+      return GRAND_E_NOMEM;
+    }
+    s->preq.resize(pc);
+    s->plive.assign(pc, 0);
+    s->pfree.reserve(pc);
+    for (int32_t k = s->pool_cap - 1; k >= 0; --k) s->pfree.push_back(k);
+  }
   for (StreamBuf& b : s->sb) {
+    if (s->step > 0 &&
+        (cudaMalloc((void**)&b.d_cur, sizeof(grand::FrameRec) * mb) != cudaSuccess ||
+         cudaMalloc((void**)&b.d_pairs, sizeof(int2) * mb) != cudaSuccess ||
+         cudaMallocHost((void**)&b.h_pairs, sizeof(int2) * mb) != cudaSuccess ||
+         cudaEventCreateWithFlags(&b.carried, cudaEventDisableTiming) != cudaSuccess)) {
+      free_server(s);
+      return GRAND_E_NOMEM;
+    }
     if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc((void**)&b.d_desc, sizeof(grand_frame_desc) * mb) != cudaSuccess ||
         cudaMalloc((void**)&b.d_cw, sizeof(uint32_t) * mb * kResultWords) != cudaSuccess ||
@@ -512,6 +756,7 @@ extern "C" int grand_server_get_stats(grand_server* s, grand_server_stats* out) 
   out->live_bytes = s->live_bytes;
   out->pending = (int64_t)s->pending.size();
   out->inflight_batches = (int64_t)s->inflight.size();
+  out->long_live = s->plive_n;
   return GRAND_OK;
 }
 

@@ -345,6 +345,31 @@ def test_grand_ab_other_sizes(g, oracle_lib, N, w, cap):
     assert_same(got, want, f"AB N={N}")
 
 
+@pytest.mark.parametrize("N,K,w,cap,snr", [
+    (32, 16, 3, 1000, 3.0),      # cap inside the weight-3 class
+    (32, 16, 2, 529, 3.0),       # weights <= 2 only, the whole space
+    (32, 16, 1, 20, 6.0),        # cap inside the weight-1 class
+    (32, 8, 3, 5489, 2.0),       # 24 parity bits (the 32-plane compare)
+    (32, 12, 3, 5489, 1.0),      # 20 parity bits, low SNR: many weight-3 hits and abandons
+    (64, 32, 3, 10 ** 6, 4.0),   # two 32-position groups, 32 parity bits
+    (64, 48, 3, 45000, 5.0),     # two groups, 16 parity bits
+])
+def test_grand_ab_split_kernel(g, oracle_lib, N, K, w, cap, snr):
+    """The pair x single split of the bit-level search (N <= 64, N - K <= 32,
+    weights <= 3) against the oracle's sequential walk, including caps that
+    cut a weight class and codes with few and many parity bits."""
+    import torch
+
+    code, H, info = code_pair(g, oracle_lib, N, K)
+    d = wl.bpsk_frames(9, N * 100 + K, 3000, N, info, snr)
+    want = oracle_lib.decode_ab(H, d["symbols"], w, cap, threads=THREADS)
+    p = g.Params.make(order=g.ORDER_HAMMING, M=2, max_weight=w, query_cap=cap)
+    r = g.decode_symbols(code, p, to_dev(d["symbols"]))
+    torch.cuda.synchronize()
+    got = {"cw": u32(r["cw"]), "queries": u32(r["queries"]).astype(np.int64), "abandon": r["abandon"].cpu().numpy()}
+    assert_same(got, want, f"AB split N={N} K={K} w={w} cap={cap}")
+
+
 # ---------------------------------------------------------------------------
 # uneven batch
 # ---------------------------------------------------------------------------

@@ -99,6 +99,39 @@ def test_results_equal_alone(env, membership):
         assert np.array_equal(r["cw"][:nw], cw), f
 
 
+@pytest.mark.parametrize("membership,step", [(0, 1), (3, 1), (0, 2)])
+def test_long_frames_carried_equal_alone(env, membership, step):
+    """resume_weight_step > 0: frames whose search outlasts the batch's weight
+    window move to the long-frame pool as device-resident cursors and finish
+    in later pool windows; every result equals the frame decoded alone, the
+    batches complete without them, and the pool drains to empty."""
+    g, codes, info = env
+    code_of_N = {n: i for i, n in enumerate(NS)}
+    mx = wl.mixed_frames(62, step, 2000, info, ebn0_range=(4.0, 10.0))
+    p = g.Params.make(M=0, S=10, query_cap=1 << 20, membership=membership)
+    srv = g.Server(codes, p, max_slots=4096, max_device_bytes=64 << 20, max_batch=256, n_streams=4,
+                   resume_weight_step=step)
+    reqs = make_requests(g, mx, code_of_N)
+    res = run_all(srv, reqs, timeout_s=60.0)
+    st = srv.stats()
+    srv.close()
+    assert len(res) == 2000 and sorted(res["tag"].tolist()) == list(range(2000))
+    assert st["completed"] == 2000 and st["errors"] == 0
+    assert st["long_frames"] > 0 and st["resume_launches"] > 0
+    assert st["long_live"] == 0 and st["live_slots"] == 0 and st["live_bytes"] == 0
+    assert not (res["abandon"] == g.ABANDON_SUSPENDED).any()
+    by_tag = {int(r["tag"]): r for r in res}
+    # frames answered by the search stage (the carried ones among them) and a spread of the rest
+    long_tags = res["tag"][res["queries"] > 631][:150].astype(np.int64)
+    pick = np.unique(np.concatenate([long_tags, np.linspace(0, 1999, 150).astype(np.int64)]))
+    for f in pick.tolist():
+        cw, q, ab = alone(g, codes, code_of_N, mx, f, p)
+        r = by_tag[f]
+        nw = int(mx["N"][f]) // 32
+        assert (int(r["queries"]), int(r["abandon"])) == (q, ab), f
+        assert np.array_equal(r["cw"][:nw], cw), f
+
+
 def test_admission_by_slots(env):
     g, codes, info = env
     code_of_N = {n: i for i, n in enumerate(NS)}
