@@ -69,13 +69,19 @@ CONFIGS = {
     "c5": dict(kind="serve", frames=1000000, S=10, cap=1 << 20, rates=(0.5e6, 1e6, 2e6, 5e6),
                desc="serving: Poisson arrivals at 0.5/1/2/5 M frames/s of the uneven mix (N 32..1024, "
                     "M 4..256, Eb/N0 U(4,14) dB), 1000000 requests per rate, S=min(L,10), cap 2^20"),
+    "c5long": dict(kind="serve", frames=200000, S=12, cap=1 << 24, rates=(0.5e6,), adversarial=0.02,
+                   ebn0=(8.0, 14.0),
+                   desc="serving, long frames: the uneven mix at Eb/N0 U(8,14) dB with 2 % of the requests "
+                        "replaced by N=1024 frames at 4 dB, S=min(L,12), cap 2^24 (a long frame searches up to "
+                        "16.8 M TEPs), Poisson 0.5 M frames/s, 200000 requests; long frames whole in their batch "
+                        "vs continued from device-resident cursors after their batch is reported"),
     "c5adv": dict(kind="serve", frames=400000, S=10, cap=1 << 20, rates=(1e6,), adversarial=0.25,
                   desc="serving, adversarial mix: the uneven mix with a quarter of the requests replaced by "
                        "N=1024 frames at Eb/N0 4 dB (most search their whole 2^20 queries), Poisson 1 M frames/s, "
                        "400000 requests; long frames whole in their batch vs carried as device-resident cursors"),
 }
 METRIC = "TEP syndrome checks/s & frames/s per GB300; p50/p99 decode latency"
-CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5, "c5": 6, "c5adv": 8, "bler": 7, "orders": 2,
+CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5, "c5": 6, "c5adv": 8, "c5long": 9, "bler": 7, "orders": 2,
               "membership": 2}
 # ALU roofline: 152 SMs x 64 integer-ALU lanes per clock (LOP3/ISETP class)
 # x 2.07 GHz maximum SM clock.
@@ -93,6 +99,10 @@ NCU_SEARCH = {
     "k_search_warp<6>": {"sha": "85688c959b892ed8", "profile": "profiles/k_search_warp6_c3a_small.md",
                          "alu_lane_ops_per_check": 0.65, "alu_pipe_active": 0.765,
                          "dram_bytes_per_hard_frame": 164.0},
+    # the bit-level kernel reads every frame (no hand-off records): bytes per frame
+    "k_ab_split<1,16>": {"sha": "23898721c5d0be10", "profile": "profiles/k_ab_split_c1_n32_bpsk.md",
+                         "alu_lane_ops_per_check": 171.0, "alu_pipe_active": 0.360,
+                         "dram_bytes_per_frame": 1308672 / 10000},
 }
 
 
@@ -110,7 +120,7 @@ def search_kernel(cfg):
     return "k_search_warp<6>" if cfg["S"] > 10 else "k_search_warp<5>"
 
 
-def search_roofline(cfg, evaluated, useful, hard, kernel_ms, alg_words):
+def search_roofline(cfg, evaluated, useful, hard, kernel_ms, alg_words, frames=0):
     """Roofline of the TEP search kernel against the integer-ALU peak.
 
     frac = ALU lane-ops executed per second / peak lane-ops per second, with
@@ -131,8 +141,11 @@ def search_roofline(cfg, evaluated, useful, hard, kernel_ms, alg_words):
         ops = evaluated * prof["alu_lane_ops_per_check"]
         ach = ops / t_s / 1e12
         same = decode_source_sha() == prof["sha"]
-        rec.update({"achieved": ach, "frac": ach / ALU_PEAK_TOPS,
-                    "traffic": prof["dram_bytes_per_hard_frame"] * hard if same and hard else None,
+        if "dram_bytes_per_frame" in prof:
+            traffic = prof["dram_bytes_per_frame"] * frames if same and frames else None
+        else:
+            traffic = prof["dram_bytes_per_hard_frame"] * hard if same and hard else None
+        rec.update({"achieved": ach, "frac": ach / ALU_PEAK_TOPS, "traffic": traffic,
                     "alu_lane_ops_per_evaluated_check": prof["alu_lane_ops_per_check"],
                     "derivation": "evaluated checks of this run x ALU lane-ops per evaluated check (ncu) / "
                                   "event-timed kernel time / ALU peak",
@@ -146,6 +159,19 @@ def search_roofline(cfg, evaluated, useful, hard, kernel_ms, alg_words):
                             "note": "(N-K)/32 three-input ops per useful check; can exceed 1 (the split compare "
                                     "tests 32 TEPs per op on a projection)"}
     return rec
+
+
+def gpu_busy_us(us):
+    """Keep the current stream busy for about `us` microseconds (a spin kernel),
+    so that a kernel-level measurement whose events are recorded next does not
+    include the host's time to issue the call (the GPU would sit idle between
+    the first event and the launch)."""
+    import torch
+
+    try:
+        torch.cuda._sleep(int(us * MAX_CLOCK_GHZ * 1000))
+    except (AttributeError, RuntimeError):
+        pass
 
 
 def hbm_peak():
@@ -166,7 +192,7 @@ def make_inputs(cfg, rank, info_by_N):
         return None
     cid = CONFIG_IDS[cfg["name"]]
     if cfg["kind"] in ("mixed", "serve"):
-        mx = wl.mixed_frames(cid, 1000 + rank, cfg["frames"], info_by_N)
+        mx = wl.mixed_frames(cid, 1000 + rank, cfg["frames"], info_by_N, ebn0_range=cfg.get("ebn0", (4.0, 14.0)))
         if cfg.get("adversarial"):
             mx = with_hard_share(mx, cid, rank, cfg["adversarial"], info_by_N)
         return mx
@@ -802,6 +828,7 @@ def run_config(args, cfg, g, ctx):
         dm_ms = []
         for _ in range(args.steps):
             flush.zero_()
+            gpu_busy_us(100)  # the binding's host time before the launch falls outside the events
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -815,39 +842,55 @@ def run_config(args, cfg, g, ctx):
         ach = dm_bytes / (statistics.mean(dm_ms) / 1e3) / 1e9
         demod = {"kernel": "k_demod", "bound": "hbm", "ms": statistics.mean(dm_ms), "bytes": dm_bytes,
                  "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": src,
-                 "note": "about 159 instructions per symbol keep the ALU pipe 82% busy (ncu): the "
-                         "demodulation is issue-bound before it is HBM-bound"}
+                 "timing": "CUDA events around the call, the GPU kept busy while the host issues it (a spin "
+                           "kernel before the first event), L2 flushed before each call"}
 
-    # ---- the same batch decided by the hash join of the split (same outputs,
-    #      membership not tested TEP by TEP): reported beside the headline
-    hash_join = None
+    # ---- the fastest exact decode of the same batch: the autotuner chooses
+    #      between the TEP-by-TEP split search and the hash join of the split
+    #      (GRAND_MEMBERSHIP_FASTEST; identical outputs) and their launch
+    #      shapes; frames/s and latency on the chosen path (a CUDA-graph plan
+    #      for the uneven batch), reported beside the checks/s headline
+    fastest = None
     if cfg["kind"] in ("qam", "mixed") and args.membership == "auto":
         ref_out = (d_cw.clone(), d_q.clone(), d_ab.clone())
-        ph = g.Params.make(order=p.order, M=p.M, S=p.S, query_cap=p.query_cap, tiles=tiles,
-                           membership=g.MEMBERSHIP_HASH)
+        pf = g.Params.make(order=p.order, M=p.M, S=p.S, query_cap=p.query_cap, membership=g.MEMBERSHIP_FASTEST)
+        n_tune = min(n_frames, 100000)
+        if cfg["kind"] == "mixed":
+            ftune = g.autotune_mixed(codes, pf, d_desc[: n_tune * g.FRAME_DESC_DTYPE.itemsize], d_sym, n_cw)
+            fplan = g.plan_mixed(codes, pf, d_desc, d_sym, d_cw, d_q, d_ab)
+            fstep = fplan.launch
+        else:
+            # the tuning sample: frames spread over the batch (every SNR point)
+            pick = torch.from_numpy(np.linspace(0, n_frames - 1, n_tune).astype(np.int64)).to(dev)
+            ftune = g.autotune(codes[0], pf, d_sym.index_select(0, pick))
+            fplan = None
 
-        def hstep():
-            if cfg["kind"] == "mixed":
-                return g.decode_mixed(codes, ph, d_desc, d_sym, n_cw, cw=d_cw, queries=d_q, abandon=d_ab)
-            return g.decode_symbols(codes[0], ph, d_sym, cw=d_cw.view(n_frames, -1), queries=d_q, abandon=d_ab)
+            def fstep():
+                g.decode_symbols(codes[0], pf, d_sym, cw=d_cw.view(n_frames, -1), queries=d_q, abandon=d_ab)
 
         for _ in range(args.warmup):
-            hstep()
-        h_ms = []
+            fstep()
+        f_ms = []
         for _ in range(args.steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            hstep()
+            fstep()
             e1.record(stream)
             e1.synchronize()
-            h_ms.append(e0.elapsed_time(e1))
+            f_ms.append(e0.elapsed_time(e1))
         same = all(torch.equal(x, y) for x, y in zip((d_cw, d_q, d_ab), ref_out))
-        hash_join = {"ms_per_step": statistics.mean(h_ms), "frames_per_s": n_frames / (statistics.mean(h_ms) / 1e3),
-                     "outputs_equal": bool(same),
-                     "what": "membership decided by a hash join of the split (GRAND_MEMBERSHIP_HASH): same outputs, "
-                             "not a per-TEP test, so not counted as checks"}
+        if fplan is not None:
+            fplan.close()
+        fastest = {"membership": {0: "split search (TEP by TEP)", 3: "hash join"}.get(ftune["membership"]),
+                   "tiles": list(ftune["tiles"]), "ms_per_step": statistics.mean(f_ms),
+                   "frames_per_s": n_frames / (statistics.mean(f_ms) / 1e3),
+                   "latency_ms": {"p50": float(np.percentile(f_ms, 50)), "p99": float(np.percentile(f_ms, 99))},
+                   "outputs_equal": bool(same), "graph": cfg["kind"] == "mixed",
+                   "what": "the autotuner's fastest exact membership test (GRAND_MEMBERSHIP_FASTEST) on the same "
+                           "batch: same outputs; a hash join decides the queries without testing them one by "
+                           "one, so this line reports frames/s, not checks"}
 
     # ---- e2e: the same decode from pinned host buffers, copies in the timed
     #      region, through the library's host-memory calls
@@ -911,7 +954,7 @@ def run_config(args, cfg, g, ctx):
     roofline = None
     if sum(search_ms) > 0 and args.membership == "auto":  # TEPs tested one by one
         roofline = search_roofline(cfg, evaluated / args.steps, search_useful / args.steps, hard / args.steps,
-                                   statistics.mean(search_ms), alg_words)
+                                   statistics.mean(search_ms), alg_words, frames=n_frames)
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
     cpu = None
@@ -956,7 +999,7 @@ def run_config(args, cfg, g, ctx):
             "kernel_ms": ({"prep": statistics.mean(prep_ms), "search": statistics.mean(search_ms)} if search_ms
                           else None),
             "roofline": roofline,
-            "hash_join": hash_join,
+            "fastest_exact": fastest,
             "demod": demod,
             "one_frame_per_launch": one,
             "autotune": tune,

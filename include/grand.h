@@ -106,12 +106,17 @@ typedef enum grand_order {
  *               Same outputs as the TEP-by-TEP search (every codeword of the
  *               space is found), O(|A| + |B|) work per frame; stats count only
  *               the confirmed pairs as checks. QAM_NNE / QAM_NEARER, S' <= 12;
- *               not for QAM_NNE5. */
+ *               not for QAM_NNE5.
+ *   FASTEST     grand_autotune / grand_autotune_mixed only: time both
+ *               exact choices for the split (AUTO and HASH, identical
+ *               outputs) with their launch shapes and write the faster into
+ *               params->membership; the decode calls reject it. */
 typedef enum grand_membership {
   GRAND_MEMBERSHIP_AUTO = 0,
   GRAND_MEMBERSHIP_DELTA = 1,
   GRAND_MEMBERSHIP_ROW_PARITY = 2,
   GRAND_MEMBERSHIP_HASH = 3,
+  GRAND_MEMBERSHIP_FASTEST = 4,
 } grand_membership;
 
 /* Readings of Def. III.1 for a received value beyond the outermost level. */
@@ -403,18 +408,25 @@ int grand_plan_destroy(grand_plan* plan);
  * TEPs and table slices share an SM). Times every candidate `tiles` setting (preparation
  * weights, search register budget, and for S' > 10 the warps per CTA) on the
  * given sample with CUDA events (median of 3 runs after one untimed run) and
- * writes the fastest into params->tiles. Results never depend on the tiles.
+ * writes the fastest into params->tiles. With params->membership =
+ * GRAND_MEMBERSHIP_FASTEST the candidates also span the membership test (the
+ * TEP-by-TEP split search and the hash join, with the hash join's own launch
+ * shapes) and the chosen one is written into params->membership. Results
+ * never depend on the choice.
  *   cache_path  host path of a text cache (NULL: no cache). Lines are
- *               "key t0 t1 t2 t3 ms"; the key holds the GPU name and the
- *               workload (N, K, M, S, cap, likelihood variant; the codes of a
- *               mixed batch). A cached key is used without timing.
- *   out         host, may be NULL: best time, candidates tried, cache hit.
+ *               "key t0 t1 t2 t3 ms membership"; the key holds the GPU name
+ *               and the workload (N, K, M, S, cap, likelihood variant, the
+ *               membership asked for; the codes of a mixed batch). A cached
+ *               key is used without timing.
+ *   out         host, may be NULL: best time, candidates tried, cache hit,
+ *               the membership test chosen.
  * The sample buffers are device memory; the tuner allocates its own outputs
  * (cudaMalloc) and synchronises `stream`. Errors: as the decode calls. */
 typedef struct grand_tune_result {
   float best_ms;
   int32_t candidates;
   int32_t from_cache;
+  int32_t membership;
 } grand_tune_result;
 int grand_autotune(const grand_code* code, grand_params* params, const void* symbols, int64_t n_frames, float N0,
                    const char* cache_path, void* stream, grand_tune_result* out);
@@ -451,16 +463,17 @@ int grand_autotune_mixed(const grand_code* const* codes, int n_codes, grand_para
  *   resume_weight_step  0: each frame is searched whole inside its batch.
  *                     k > 0: a batch searches each frame's TEPs only up to k
  *                     weight classes beyond the preparation's (the weight
- *                     windows of grand_decode_symbols_resumable, tiles[1] = 0);
- *                     a frame with no codeword there leaves the batch as a
- *                     device-resident cursor in the server's long-frame pool,
- *                     whose next k weight classes run on a stream of their own
- *                     as often as the previous window has finished, until the
- *                     frame is decoded or abandoned. The batch completes without
- *                     waiting for its long frames; every result equals the
- *                     uninterrupted search's. The pool holds max_slots cursors.
+ *                     windows of grand_decode_symbols_resumable, tiles[1] = 0).
+ *                     The batch's other frames are reported as soon as that
+ *                     launch ends and its stream takes the next batch; the
+ *                     frames left without a codeword continue -- every
+ *                     remaining weight -- from their device-resident cursors
+ *                     on a separate stream, and are reported when done. Every
+ *                     result equals the uninterrupted search's. The server
+ *                     then holds twice n_streams buffer sets (a batch keeps
+ *                     its set until its last frame is reported).
  *   params.deadline_ns, when nonzero, is the budget of each batch launch (and
- *   of each pool window). */
+ *   of each continuation). */
 typedef struct grand_server_cfg {
   const grand_code* const* codes;
   int32_t n_codes;
@@ -498,8 +511,9 @@ typedef struct grand_result {
 
 /* Counters of a server. batch_service_ns: sum over batches of (completion seen
  * - launch start); launch_ns: host time spent issuing batches (copies, decode
- * call, event). long_frames: frames moved to the long-frame pool;
- * resume_launches: pool windows launched; long_live: frames in the pool now. */
+ * call, event). long_frames: frames continued after their batch's first
+ * launch (resume_weight_step > 0); resume_launches: continuation launches;
+ * long_live: frames being continued now. */
 typedef struct grand_server_stats {
   int64_t admitted, rejected, completed, batches, batched_frames, max_inflight_batches, errors;
   int64_t live_slots, live_bytes, pending, inflight_batches;

@@ -18,8 +18,9 @@ from . import _build
 __all__ = [
     "GrandError", "GrandArgumentError", "lib", "build", "polar_H", "Code", "Params", "demod", "decode_batch",
     "decode_symbols", "decode_symbols_host", "decode_mixed", "decode_mixed_host", "frame_desc", "ORDER_HAMMING", "ORDER_QAM_NNE",
-    "ORDER_QAM_NEARER", "ORDER_QAM_NNE5", "MEMBERSHIP_AUTO", "MEMBERSHIP_DELTA", "MEMBERSHIP_ROW_PARITY", "MEMBERSHIP_HASH",
-    "LIK_THRESHOLD", "LIK_LITERAL", "stream_status", "E_TIMEOUT", "ABANDON_DEADLINE",
+    "ORDER_QAM_NEARER", "ORDER_QAM_NNE5", "MEMBERSHIP_AUTO", "MEMBERSHIP_DELTA", "MEMBERSHIP_ROW_PARITY", "MEMBERSHIP_HASH", "MEMBERSHIP_FASTEST",
+    "LIK_THRESHOLD", "LIK_LITERAL", "stream_status", "E_TIMEOUT", "ABANDON_DEADLINE", "ABANDON_SUSPENDED",
+    "CURSOR_BYTES", "decode_symbols_resumable", "decode_resume",
 ]
 
 ORDER_HAMMING = 0
@@ -30,6 +31,7 @@ MEMBERSHIP_AUTO = 0
 MEMBERSHIP_DELTA = 1
 MEMBERSHIP_ROW_PARITY = 2
 MEMBERSHIP_HASH = 3
+MEMBERSHIP_FASTEST = 4  # autotuner only: choose between the split search and the hash join
 LIK_THRESHOLD = 0
 LIK_LITERAL = 1
 E_TIMEOUT = -5         # grand_status GRAND_E_TIMEOUT
@@ -616,12 +618,13 @@ def plan_mixed(codes, params: Params, desc, symbols, cw, queries, abandon, N0: f
 
 
 class TuneResult(ctypes.Structure):
-    _fields_ = [("best_ms", ctypes.c_float), ("candidates", ctypes.c_int32), ("from_cache", ctypes.c_int32)]
+    _fields_ = [("best_ms", ctypes.c_float), ("candidates", ctypes.c_int32), ("from_cache", ctypes.c_int32),
+                ("membership", ctypes.c_int32)]
 
 
 def _tune_dict(p, r):
     return {"tiles": tuple(p.tiles), "best_ms": float(r.best_ms), "candidates": int(r.candidates),
-            "from_cache": bool(r.from_cache)}
+            "from_cache": bool(r.from_cache), "membership": int(p.membership)}
 
 
 def autotune(code: Code, params: Params, symbols, N0: float = 1.0, cache_path: str | None = None, stream=None):

@@ -1,12 +1,14 @@
-// Launch-shape autotuner: times candidate `grand_params.tiles` on a sample
-// batch with CUDA events and keeps the fastest; results do not depend on the
-// tiles, only the time does. Choices are cached in a text file keyed by the
+// Launch-shape autotuner: times candidate `grand_params.tiles` (and, with
+// GRAND_MEMBERSHIP_FASTEST, the two exact membership tests) on a sample batch
+// with CUDA events and keeps the fastest; results do not depend on the
+// choice, only the time does. Choices are cached in a text file keyed by the
 // GPU name and the workload (code sizes, constellation, cut-off, cap).
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <functional>
 #include <string>
 #include <vector>
@@ -17,20 +19,38 @@ namespace {
 
 struct Candidate {
   int32_t tiles[4];
+  int32_t membership;
 };
 
-std::vector<Candidate> candidates(int S) {
-  std::vector<Candidate> out;
-  if (S <= 10) {
+// Launch shapes of one membership test.
+void shapes(int S, int membership, std::vector<Candidate>& out) {
+  if (membership == GRAND_MEMBERSHIP_HASH) {
+    // hash join: warps per CTA (its shared-memory tables bound residency) x prep weights
+    for (int warps : S <= 10 ? std::initializer_list<int>{2, 4} : std::initializer_list<int>{1, 2})
+      for (int w0 : {1, 2, 3}) out.push_back({{warps, 0, w0, 0}, membership});
+  } else if (S <= 10) {
     // warp-per-frame search: prep weights x register budget
     for (int w0 : {1, 2, 3})
-      for (int regs : {4, 6, 8}) out.push_back({{0, 0, w0, regs}});
+      for (int regs : {4, 6, 8}) out.push_back({{0, 0, w0, regs}, membership});
   } else {
     // warp-per-frame search with 6-rank sides: warps per CTA x prep weights x
     // register budget
     for (int warps : {1, 2, 4})
       for (int w0 : {2, 3})
-        for (int regs : {4, 6}) out.push_back({{warps, 0, w0, regs}});
+        for (int regs : {4, 6}) out.push_back({{warps, 0, w0, regs}, membership});
+  }
+}
+
+// The candidates: the launch shapes of the params' membership test, or with
+// GRAND_MEMBERSHIP_FASTEST those of both exact tests (the TEP-by-TEP split
+// search and the hash join), whose outputs are identical.
+std::vector<Candidate> candidates(int S, int membership) {
+  std::vector<Candidate> out;
+  if (membership == GRAND_MEMBERSHIP_FASTEST) {
+    shapes(S, GRAND_MEMBERSHIP_AUTO, out);
+    shapes(S, GRAND_MEMBERSHIP_HASH, out);
+  } else {
+    shapes(S, membership, out);
   }
   return out;
 }
@@ -45,7 +65,9 @@ std::string device_name() {
   return n;
 }
 
-bool cache_lookup(const char* path, const std::string& key, int32_t tiles[4]) {
+// Cache lines: "key t0 t1 t2 t3 ms membership" (lines without the membership
+// field keep the params' membership).
+bool cache_lookup(const char* path, const std::string& key, int32_t tiles[4], int32_t* membership) {
   if (!path) return false;
   FILE* f = fopen(path, "r");
   if (!f) return false;
@@ -53,10 +75,12 @@ bool cache_lookup(const char* path, const std::string& key, int32_t tiles[4]) {
   bool found = false;
   while (fgets(line, sizeof line, f)) {
     char k[384];
-    int t[4];
+    int t[4], mem = -1;
     float ms;
-    if (sscanf(line, "%383s %d %d %d %d %f", k, &t[0], &t[1], &t[2], &t[3], &ms) == 6 && key == k) {
+    const int n = sscanf(line, "%383s %d %d %d %d %f %d", k, &t[0], &t[1], &t[2], &t[3], &ms, &mem);
+    if (n >= 6 && key == k) {
       for (int i = 0; i < 4; ++i) tiles[i] = t[i];
+      if (n == 7 && (mem == GRAND_MEMBERSHIP_AUTO || mem == GRAND_MEMBERSHIP_HASH)) *membership = mem;
       found = true;  // the last entry for a key wins
     }
   }
@@ -64,11 +88,11 @@ bool cache_lookup(const char* path, const std::string& key, int32_t tiles[4]) {
   return found;
 }
 
-void cache_store(const char* path, const std::string& key, const int32_t tiles[4], float ms) {
+void cache_store(const char* path, const std::string& key, const int32_t tiles[4], float ms, int32_t membership) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d %d %.4f\n", key.c_str(), tiles[0], tiles[1], tiles[2], tiles[3], ms);
+  fprintf(f, "%s %d %d %d %d %.4f %d\n", key.c_str(), tiles[0], tiles[1], tiles[2], tiles[3], ms, membership);
   fclose(f);
 }
 
@@ -102,20 +126,24 @@ int time_runs(const std::function<int(cudaStream_t)>& run, cudaStream_t st, int 
 int tune(const std::string& key, grand_params* p, const char* cache_path, cudaStream_t st,
          const std::function<int(const grand_params*, cudaStream_t)>& run, grand_tune_result* res) {
   int32_t cached[4];
-  if (cache_lookup(cache_path, key, cached)) {
+  int32_t cached_mem = p->membership == GRAND_MEMBERSHIP_FASTEST ? GRAND_MEMBERSHIP_AUTO : p->membership;
+  if (cache_lookup(cache_path, key, cached, &cached_mem)) {
     for (int i = 0; i < 4; ++i) p->tiles[i] = cached[i];
+    p->membership = cached_mem;
     if (res) {
       memset(res, 0, sizeof *res);
       res->from_cache = 1;
+      res->membership = cached_mem;
     }
     return GRAND_OK;
   }
   float best = 1e30f;
-  Candidate best_c{{0, 0, 0, 0}};
+  Candidate best_c{{0, 0, 0, 0}, p->membership};
   int tried = 0;
-  for (const Candidate& c : candidates(p->S)) {
+  for (const Candidate& c : candidates(p->S, p->membership)) {
     grand_params q = *p;
     for (int i = 0; i < 4; ++i) q.tiles[i] = c.tiles[i];
+    q.membership = c.membership;
     q.deadline_ns = 0;  // time every candidate in full
     float ms = 0;
     const int rc = time_runs([&](cudaStream_t s) { return run(&q, s); }, st, 3, &ms);
@@ -127,11 +155,13 @@ int tune(const std::string& key, grand_params* p, const char* cache_path, cudaSt
     }
   }
   for (int i = 0; i < 4; ++i) p->tiles[i] = best_c.tiles[i];
-  cache_store(cache_path, key, p->tiles, best);
+  p->membership = best_c.membership;
+  cache_store(cache_path, key, p->tiles, best, p->membership);
   if (res) {
     res->best_ms = best;
     res->candidates = tried;
     res->from_cache = 0;
+    res->membership = p->membership;
   }
   return GRAND_OK;
 }
@@ -142,7 +172,8 @@ extern "C" int grand_autotune(const grand_code* c, grand_params* p, const void* 
                               const char* cache_path, void* stream, grand_tune_result* res) {
   if (!c || !p || !symbols || n_frames < 1 ||
       (p->order != GRAND_ORDER_QAM_NNE && p->order != GRAND_ORDER_QAM_NEARER) ||
-      (p->membership != GRAND_MEMBERSHIP_AUTO && p->membership != GRAND_MEMBERSHIP_HASH))
+      (p->membership != GRAND_MEMBERSHIP_AUTO && p->membership != GRAND_MEMBERSHIP_HASH &&
+       p->membership != GRAND_MEMBERSHIP_FASTEST))
     return GRAND_E_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   const int N = c->N, W = c->N / 32;
@@ -175,6 +206,9 @@ extern "C" int grand_autotune_mixed(const grand_code* const* codes, int n_codes,
                                     int64_t n_symbols, float N0, int64_t n_cw_words, const char* cache_path,
                                     void* stream, grand_tune_result* res) {
   if (!codes || n_codes < 1 || !p || !desc || !symbols || n_frames < 1 || n_cw_words < 1) return GRAND_E_INVALID;
+  if (p->membership != GRAND_MEMBERSHIP_AUTO && p->membership != GRAND_MEMBERSHIP_HASH &&
+      p->membership != GRAND_MEMBERSHIP_FASTEST)
+    return GRAND_E_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   uint32_t* cw = nullptr;
   uint32_t* q = nullptr;

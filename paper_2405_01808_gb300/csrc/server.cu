@@ -18,17 +18,16 @@
 // times (CLOCK_MONOTONIC). Ring space is reclaimed in launch order; results
 // are delivered in completion order. Every wait is bounded.
 //
-// Long frames (resume_weight_step > 0): a batch searches each frame only up
-// to resume_weight_step TEP weights beyond the preparation's; a frame with no
-// codeword there is suspended and its cursor (the search state, see
-// grand_decode_symbols_resumable) moves into a device-resident pool of long
-// frames, so the batch completes and its other frames are reported at once.
-// The launcher runs the pool's next weight window on a stream of its own
-// whenever no pool launch is in flight; a frame leaves the pool when its
-// search ends (decoded or abandoned), with the outputs an uninterrupted
-// search gives. The carry (records, hard words, counters) is a device-side
-// gather on the pool's stream; the batch's stream waits for it before its
-// buffers are reused.
+// Long frames (resume_weight_step > 0): a batch's search covers only the
+// first resume_weight_step TEP weights beyond the preparation's. Frames left
+// without a codeword there are suspended with their search state (a cursor,
+// see grand_decode_symbols_resumable) in the batch's buffer set on the
+// device; the harvester reports the batch's other frames at once, hands its
+// stream back, and continues the suspended ones -- every remaining weight --
+// on one of the server's continuation streams, from those cursors. The
+// buffer set stays with the batch until its last frame is reported, so
+// buffer sets outnumber streams (twice as many). Results are those of the
+// uninterrupted search.
 #include <errno.h>
 #include <stdlib.h>
 #include <string.h>
@@ -67,13 +66,10 @@ struct Req {
   bool ready;     // symbols copied into the ring
 };
 
-struct StreamBuf {
-  cudaStream_t stream = nullptr;
-  grand::FrameRec* d_cur = nullptr;   // per-frame cursors of the batch (long frames)
-  int2* h_pairs = nullptr;            // (frame, pool slot) of the frames to carry
-  int2* d_pairs = nullptr;
-  cudaEvent_t carried = nullptr;      // the carry out of this stream's buffers is done
-  bool wait_carry = false;            // the next batch waits for `carried`
+// Device and pinned host buffers of one batch (a batch holds its set until
+// every frame of it is reported; its stream is freed earlier).
+struct BufSet {
+  grand::FrameRec* d_cur = nullptr;  // per-frame cursors (resume_weight_step > 0)
   grand_frame_desc* d_desc = nullptr;
   grand_frame_desc* h_desc = nullptr;
   uint32_t* d_cw = nullptr;
@@ -87,15 +83,20 @@ struct StreamBuf {
 
 struct Batch {
   int stream;
+  int set;        // buffer set
   int64_t launch_ns;
   std::vector<Req> reqs;
-  int64_t vend;   // ring released up to here once this and all earlier batches are done
+  int64_t vend;   // ring released up to here once this and all earlier batches have left the ring
   int64_t bytes;
   cudaEvent_t ev;
-  bool done;
+  bool done;       // every frame reported
+  bool ring_done;  // the symbols are no longer read (the first launch finished)
   int status;
-  int64_t carried_bytes = 0;  // budget and slots of frames moved to the long-frame pool
-  int32_t carried = 0;
+  // continuation of the suspended frames (resume_weight_step > 0)
+  bool cont = false;               // the continuation is in flight (ev re-recorded on cstream)
+  int cstream = -1;
+  std::vector<int32_t> suspended;  // frames of the batch it continues
+  int64_t left_bytes = 0;          // budget still held by them
 };
 
 // Completed results waiting for poll, in completion order.
@@ -122,7 +123,12 @@ struct grand_server {
   int32_t live_slots = 0;
   uint64_t next_seq = 0;
   int running = 0;        // launched batches not yet harvested
-  std::vector<StreamBuf> sb;
+  std::vector<cudaStream_t> streams;
+  std::vector<char> stream_busy;
+  std::vector<BufSet> sets;
+  int32_t step = 0;                    // resume_weight_step
+  std::vector<cudaStream_t> cstreams;  // continuation streams of long frames
+  int next_cstream = 0;
   std::deque<Req> pending;     // admitted, not launched (ring order)
   std::deque<Batch> inflight;  // launch order
   std::deque<Chunk> done;
@@ -132,28 +138,6 @@ struct grand_server {
   std::thread launcher, harvester;
   std::atomic<bool> stop{false};
   grand_server_stats st{};
-  // long-frame pool (resume_weight_step > 0): cursor, hard word / decoded word,
-  // queries and abandon flag per slot on the device, host mirrors, requests
-  int32_t step = 0;
-  int32_t pool_cap = 0;
-  grand::FrameRec* d_pcur = nullptr;
-  uint32_t* d_pcw = nullptr;
-  uint32_t* d_pq = nullptr;
-  uint8_t* d_pab = nullptr;
-  uint32_t* h_pcw = nullptr;
-  uint32_t* h_pq = nullptr;
-  uint8_t* h_pab = nullptr;
-  cudaStream_t pstream = nullptr;
-  cudaEvent_t pev = nullptr;
-  std::vector<Req> preq;          // request of each live slot
-  std::vector<char> plive;
-  std::vector<int32_t> pfree;     // free slots
-  int32_t plive_n = 0;
-  bool presume = false;           // a pool launch is in flight
-  bool pissued = false;           // ... and its event is recorded (the harvester may look)
-  bool pfailed = false;           // ... and it could not be issued
-  std::vector<int32_t> psnap;     // live slots when it was launched
-  int64_t presume_ns = 0;
 };
 
 namespace {
@@ -161,13 +145,12 @@ namespace {
 int64_t request_bytes(int L, int N) { return 8ll * L + (int64_t)sizeof(grand::FrameRec) + 4ll * (N / 32) + 5; }
 
 void free_server(grand_server* s) {
-  if (s->pstream) cudaStreamSynchronize(s->pstream);
-  for (StreamBuf& b : s->sb) {
-    if (b.stream) cudaStreamSynchronize(b.stream);
+  for (cudaStream_t st : s->streams)
+    if (st) cudaStreamSynchronize(st);
+  for (cudaStream_t st : s->cstreams)
+    if (st) cudaStreamSynchronize(st);
+  for (BufSet& b : s->sets) {
     cudaFree(b.d_cur);
-    cudaFree(b.d_pairs);
-    cudaFreeHost(b.h_pairs);
-    if (b.carried) cudaEventDestroy(b.carried);
     cudaFree(b.d_desc);
     cudaFree(b.d_cw);
     cudaFree(b.d_q);
@@ -176,50 +159,25 @@ void free_server(grand_server* s) {
     cudaFreeHost(b.h_cw);
     cudaFreeHost(b.h_q);
     cudaFreeHost(b.h_ab);
-    if (b.stream) cudaStreamDestroy(b.stream);
   }
+  for (cudaStream_t st : s->streams)
+    if (st) cudaStreamDestroy(st);
+  for (cudaStream_t st : s->cstreams)
+    if (st) cudaStreamDestroy(st);
   for (Batch& b : s->inflight) cudaEventDestroy(b.ev);
-  cudaFree(s->d_pcur);
-  cudaFree(s->d_pcw);
-  cudaFree(s->d_pq);
-  cudaFree(s->d_pab);
-  cudaFreeHost(s->h_pcw);
-  cudaFreeHost(s->h_pq);
-  cudaFreeHost(s->h_pab);
-  if (s->pev) cudaEventDestroy(s->pev);
-  if (s->pstream) cudaStreamDestroy(s->pstream);
   cudaFree(s->d_table);
   cudaFree(s->d_ring);
   cudaFreeHost(s->h_ring);
   delete s;
 }
 
-// Move suspended frames of a finished batch into the long-frame pool: warp k
-// copies pair k's cursor, hard word, query count and flag.
-__global__ void k_carry(const int2* pairs, int n, const grand::FrameRec* cur, const uint32_t* cw, const uint32_t* q,
-                        const uint8_t* ab, grand::FrameRec* pcur, uint32_t* pcw, uint32_t* pq, uint8_t* pab) {
-  const int lane = threadIdx.x & 31;
-  const int k = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  if (k >= n) return;
-  const int f = pairs[k].x, slot = pairs[k].y;
-  constexpr int kWords = (int)(sizeof(grand::FrameRec) / 4);
-  const uint32_t* src = reinterpret_cast<const uint32_t*>(cur + f);
-  uint32_t* dst = reinterpret_cast<uint32_t*>(pcur + slot);
-  for (int w = lane; w < kWords; w += 32) dst[w] = src[w];
-  pcw[(size_t)slot * kResultWords + lane] = cw[(size_t)f * kResultWords + lane];
-  if (lane == 0) {
-    pq[slot] = q[f];
-    pab[slot] = ab[f];
-  }
-}
-
-// Issue batch b on stream si (no lock held; b.reqs was taken under it).
-int launch_batch(grand_server* s, int si, Batch& b) {
+// Issue batch b on its stream with its buffer set (no lock held; b.reqs was
+// taken under it).
+int launch_batch(grand_server* s, Batch& b) {
   grand::NvtxRange range("grand.server.batch");
-  StreamBuf& buf = s->sb[si];
+  BufSet& buf = s->sets[b.set];
+  const cudaStream_t stream = s->streams[b.stream];
   const int n = (int)b.reqs.size();
-  // the previous batch's long frames must have left this stream's buffers
-  if (buf.wait_carry && cudaStreamWaitEvent(buf.stream, buf.carried, 0) != cudaSuccess) return GRAND_E_CUDA;
   for (int i = 0; i < n; ++i) {
     const Req& r = b.reqs[i];
     buf.h_desc[i].code = r.code;
@@ -235,40 +193,45 @@ int launch_batch(grand_server* s, int si, Batch& b) {
   while (v < v1) {
     const int64_t p = v % s->ring_cap;
     const int64_t len = std::min(v1 - v, s->ring_cap - p);
-    if (cudaMemcpyAsync(s->d_ring + p, s->h_ring + p, sizeof(float2) * len, cudaMemcpyHostToDevice, buf.stream) !=
+    if (cudaMemcpyAsync(s->d_ring + p, s->h_ring + p, sizeof(float2) * len, cudaMemcpyHostToDevice, stream) !=
         cudaSuccess)
       return GRAND_E_CUDA;
     v += len;
   }
-  if (cudaMemcpyAsync(buf.d_desc, buf.h_desc, sizeof(grand_frame_desc) * n, cudaMemcpyHostToDevice, buf.stream) !=
+  if (cudaMemcpyAsync(buf.d_desc, buf.h_desc, sizeof(grand_frame_desc) * n, cudaMemcpyHostToDevice, stream) !=
       cudaSuccess)
     return GRAND_E_CUDA;
   int rc = grand::decode_mixed_resident(s->d_table, (int)s->codes.size(), s->Lmax, s->Wmax, &s->cfg.params,
                                         buf.d_desc, n, s->d_ring, s->ring_cap, buf.d_cw, (int64_t)n * kResultWords,
-                                        buf.d_q, buf.d_ab, buf.stream, s->step, s->step > 0 ? buf.d_cur : nullptr);
+                                        buf.d_q, buf.d_ab, stream, s->step, s->step > 0 ? buf.d_cur : nullptr);
   if (rc != GRAND_OK) return rc;
-  if (cudaMemcpyAsync(buf.h_cw, buf.d_cw, sizeof(uint32_t) * n * kResultWords, cudaMemcpyDeviceToHost, buf.stream) !=
+  if (cudaMemcpyAsync(buf.h_cw, buf.d_cw, sizeof(uint32_t) * n * kResultWords, cudaMemcpyDeviceToHost, stream) !=
           cudaSuccess ||
-      cudaMemcpyAsync(buf.h_q, buf.d_q, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, buf.stream) != cudaSuccess ||
-      cudaMemcpyAsync(buf.h_ab, buf.d_ab, n, cudaMemcpyDeviceToHost, buf.stream) != cudaSuccess)
+      cudaMemcpyAsync(buf.h_q, buf.d_q, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaMemcpyAsync(buf.h_ab, buf.d_ab, n, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
     return GRAND_E_CUDA;
-  if (cudaEventRecord(b.ev, buf.stream) != cudaSuccess) return GRAND_E_CUDA;
+  if (cudaEventRecord(b.ev, stream) != cudaSuccess) return GRAND_E_CUDA;
   return GRAND_OK;
 }
 
-// The next weight window of the long-frame pool's live slots [0, hi), on the
-// pool's stream, and the read-back of their outputs (no lock held).
-int launch_pool(grand_server* s, int32_t hi) {
+// The rest of batch b's suspended frames (every remaining weight) on a
+// continuation stream, from the cursors in its buffer set, and the read-back
+// of their outputs; b.ev is recorded again behind it. Called by the harvester
+// once the batch's first launch has finished (no lock held).
+int launch_continuation(grand_server* s, Batch& b) {
   grand::NvtxRange range("grand.server.resume");
-  int rc = grand::resume_resident(s->d_table, (int)s->codes.size(), s->Wmax, &s->cfg.params, s->d_pcur, hi, s->step,
-                                  s->d_pcw, kResultWords, s->d_pq, s->d_pab, s->pstream);
+  BufSet& buf = s->sets[b.set];
+  const cudaStream_t cs = s->cstreams[b.cstream];
+  const int n = (int)b.reqs.size();
+  int rc = grand::resume_resident(s->d_table, (int)s->codes.size(), s->Wmax, &s->cfg.params, buf.d_cur, n, 0,
+                                  buf.d_cw, kResultWords, buf.d_q, buf.d_ab, cs);
   if (rc != GRAND_OK) return rc;
-  if (cudaMemcpyAsync(s->h_pcw, s->d_pcw, sizeof(uint32_t) * hi * kResultWords, cudaMemcpyDeviceToHost, s->pstream) !=
+  if (cudaMemcpyAsync(buf.h_cw, buf.d_cw, sizeof(uint32_t) * n * kResultWords, cudaMemcpyDeviceToHost, cs) !=
           cudaSuccess ||
-      cudaMemcpyAsync(s->h_pq, s->d_pq, sizeof(uint32_t) * hi, cudaMemcpyDeviceToHost, s->pstream) != cudaSuccess ||
-      cudaMemcpyAsync(s->h_pab, s->d_pab, hi, cudaMemcpyDeviceToHost, s->pstream) != cudaSuccess)
+      cudaMemcpyAsync(buf.h_q, buf.d_q, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaMemcpyAsync(buf.h_ab, buf.d_ab, n, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
     return GRAND_E_CUDA;
-  return cudaEventRecord(s->pev, s->pstream) == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
+  return cudaEventRecord(b.ev, cs) == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
 void launcher_main(grand_server* s) {
@@ -278,39 +241,20 @@ void launcher_main(grand_server* s) {
     int si = -1;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      int32_t pool_hi = -1;
       while (!s->stop.load(std::memory_order_acquire)) {
-        if (s->step > 0 && !s->presume && s->plive_n > 0) {  // the long frames' next window
-          s->psnap.clear();
-          for (int32_t k = 0; k < s->pool_cap; ++k)
-            if (s->plive[k]) {
-              s->psnap.push_back(k);
-              pool_hi = k + 1;
-            }
-          s->presume = true;
-          s->presume_ns = now_ns();
-          s->st.resume_launches += 1;
-          break;
-        }
         if (!s->pending.empty() && s->pending.front().ready) {
-          for (int i = 0; i < (int)s->sb.size(); ++i)
-            if (!s->sb[i].busy) { si = i; break; }
-          if (si >= 0) break;
+          int set = -1;
+          for (int i = 0; i < (int)s->streams.size(); ++i)
+            if (!s->stream_busy[i]) { si = i; break; }
+          for (int i = 0; i < (int)s->sets.size(); ++i)
+            if (!s->sets[i].busy) { set = i; break; }
+          if (si >= 0 && set >= 0) {
+            b.set = set;
+            break;
+          }
+          si = -1;
         }
         s->cv_launch.wait_for(lk, std::chrono::milliseconds(1));  // bounded: re-check
-      }
-      if (pool_hi > 0) {
-        lk.unlock();
-        const int rc = launch_pool(s, pool_hi);
-        if (rc != GRAND_OK) cudaEventRecord(s->pev, s->pstream);  // the harvester sees the failure
-        {
-          std::unique_lock<std::mutex> lk2(s->mu);
-          s->running += 1;
-          s->pfailed = rc != GRAND_OK;
-          s->pissued = true;
-        }
-        s->cv_harvest.notify_one();
-        continue;
       }
       if (si < 0) return;  // stop
       const int maxb = s->cfg.max_batch;
@@ -324,16 +268,18 @@ void launcher_main(grand_server* s) {
       b.vend = b.reqs.back().vpos + b.reqs.back().L;
       b.bytes = bytes;
       b.done = false;
+      b.ring_done = false;
       b.status = GRAND_OK;
-      s->sb[si].busy = true;
+      s->stream_busy[si] = 1;
+      s->sets[b.set].busy = true;
       s->st.batches += 1;
       s->st.batched_frames += b.reqs.size();
     }
     cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
     b.launch_ns = now_ns();
-    b.status = launch_batch(s, si, b);
+    b.status = launch_batch(s, b);
     const int64_t issued = now_ns() - b.launch_ns;
-    if (b.status != GRAND_OK) cudaEventRecord(b.ev, s->sb[si].stream);
+    if (b.status != GRAND_OK) cudaEventRecord(b.ev, s->streams[si]);
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->st.launch_ns += issued;
@@ -345,59 +291,6 @@ void launcher_main(grand_server* s) {
     }
     s->cv_harvest.notify_one();
   }
-}
-
-// A finished pool launch: report the slots of its snapshot whose search
-// ended, free them; the others stay for the next window. Returns whether a
-// launch was harvested.
-bool harvest_pool(grand_server* s) {
-  std::vector<int32_t> snap;
-  {
-    std::unique_lock<std::mutex> lk(s->mu);
-    if (!s->presume || !s->pissued) return false;
-    snap = s->psnap;
-  }
-  const cudaError_t q = cudaEventQuery(s->pev);
-  if (q == cudaErrorNotReady) return false;
-  const int64_t t = now_ns();
-  Chunk c;
-  std::vector<int32_t> freed;
-  {
-    std::unique_lock<std::mutex> lk(s->mu);  // preq of live slots is read under the lock
-    const bool failed = q != cudaSuccess || s->pfailed;
-    for (int32_t k : snap) {
-      if (!failed && s->h_pab[k] == GRAND_ABANDON_SUSPENDED) continue;
-      c.v.emplace_back();
-      grand_result& r = c.v.back();
-      memset(&r, 0, sizeof r);
-      r.tag = s->preq[k].tag;
-      r.arrival_ns = s->preq[k].arrival_ns;
-      r.done_ns = t;
-      if (!failed) {
-        r.queries = s->h_pq[k];
-        r.abandon = s->h_pab[k];
-        memcpy(r.cw, s->h_pcw + (size_t)k * kResultWords, sizeof(uint32_t) * s->preq[k].nw);
-      } else {
-        r.abandon = 4;
-      }
-      freed.push_back(k);
-    }
-    for (int32_t k : freed) {
-      s->plive[k] = 0;
-      s->plive_n -= 1;
-      s->pfree.push_back(k);
-      s->live_slots -= 1;
-      s->live_bytes -= s->preq[k].bytes;
-    }
-    s->st.completed += (int64_t)freed.size();
-    if (failed) s->st.errors += 1;
-    if (!c.v.empty()) s->done.push_back(std::move(c));
-    s->presume = false;
-    s->pissued = false;
-    s->running -= 1;
-  }
-  s->cv_launch.notify_one();
-  return true;
 }
 
 void harvester_main(grand_server* s) {
@@ -421,88 +314,96 @@ void harvester_main(grand_server* s) {
       any = true;
       const int64_t t = now_ns();
       const int status = q == cudaSuccess ? b->status : GRAND_E_CUDA;
-      StreamBuf& buf = s->sb[b->stream];
-      // frames the batch's weight window suspended go to the long-frame pool
-      std::vector<int> carry;
-      if (status == GRAND_OK && s->step > 0)
-        for (size_t i = 0; i < b->reqs.size(); ++i)
-          if (buf.h_ab[i] == GRAND_ABANDON_SUSPENDED) carry.push_back((int)i);
+      const BufSet& buf = s->sets[b->set];
+      const bool first = !b->cont;  // the batch's first launch finished (else its continuation)
+      const int n = (int)b->reqs.size();
+      // frames suspended by the first launch's weight window continue
+      std::vector<int32_t> susp;
+      if (first && status == GRAND_OK && s->step > 0)
+        for (int i = 0; i < n; ++i)
+          if (buf.h_ab[i] == GRAND_ABANDON_SUSPENDED) susp.push_back(i);
       Chunk c;
-      c.v.reserve(b->reqs.size() - carry.size());
-      size_t ci = 0;
-      for (size_t i = 0; i < b->reqs.size(); ++i) {
-        if (ci < carry.size() && carry[ci] == (int)i) {
-          ++ci;
-          continue;
-        }
+      auto emit = [&](int i, bool failed) {
         c.v.emplace_back();
         grand_result& r = c.v.back();
         memset(&r, 0, sizeof r);
         r.tag = b->reqs[i].tag;
         r.arrival_ns = b->reqs[i].arrival_ns;
         r.done_ns = t;
-        if (status == GRAND_OK) {
+        if (!failed) {
           r.queries = buf.h_q[i];
           r.abandon = buf.h_ab[i];
-          memcpy(r.cw, buf.h_cw + i * kResultWords, sizeof(uint32_t) * b->reqs[i].nw);
+          memcpy(r.cw, buf.h_cw + (size_t)i * kResultWords, sizeof(uint32_t) * b->reqs[i].nw);
         } else {
           r.abandon = 4;  // the batch failed on the device
         }
-      }
-      std::vector<int32_t> slots;
-      if (!carry.empty()) {
-        {
-          std::unique_lock<std::mutex> lk(s->mu);
-          for (size_t k = 0; k < carry.size(); ++k) {  // a carried request keeps its admission slot: never empty
-            slots.push_back(s->pfree.back());
-            s->pfree.pop_back();
+      };
+      if (first) {
+        c.v.reserve(n - susp.size());
+        size_t k = 0;
+        for (int i = 0; i < n; ++i) {
+          if (k < susp.size() && susp[k] == i) {
+            ++k;
+            continue;
           }
+          emit(i, status != GRAND_OK);
         }
-        const int nc = (int)carry.size();
-        for (int k = 0; k < nc; ++k) buf.h_pairs[k] = make_int2(carry[k], slots[k]);
-        // on the pool's stream (ordered before any later pool launch); the
-        // batch's stream waits for it before its buffers are reused
-        cudaMemcpyAsync(buf.d_pairs, buf.h_pairs, sizeof(int2) * nc, cudaMemcpyHostToDevice, s->pstream);
-        k_carry<<<(nc * 32 + 127) / 128, 128, 0, s->pstream>>>(buf.d_pairs, nc, buf.d_cur, buf.d_cw, buf.d_q, buf.d_ab,
-                                                             s->d_pcur, s->d_pcw, s->d_pq, s->d_pab);
-        cudaEventRecord(buf.carried, s->pstream);
+      } else {
+        for (int32_t i : b->suspended) emit(i, status != GRAND_OK);
+      }
+      bool continues = false;
+      if (!susp.empty()) {
+        b->suspended = susp;
+        b->left_bytes = 0;
+        for (int32_t i : susp) b->left_bytes += b->reqs[i].bytes;
+        b->cstream = s->next_cstream;
+        s->next_cstream = (s->next_cstream + 1) % (int)s->cstreams.size();
+        b->cont = true;
+        continues = launch_continuation(s, *b) == GRAND_OK;
+        if (!continues) {  // report them as failed now
+          b->cont = false;
+          for (int32_t i : susp) emit(i, true);
+        }
       }
       {
         std::unique_lock<std::mutex> lk(s->mu);
-        for (size_t k = 0; k < carry.size(); ++k) {
-          const Req& r = b->reqs[carry[k]];
-          s->preq[slots[k]] = r;
-          s->plive[slots[k]] = 1;
-          s->plive_n += 1;
-          b->carried += 1;
-          b->carried_bytes += r.bytes;
+        if (!c.v.empty()) s->done.push_back(std::move(c));
+        if (first) {
+          b->ring_done = true;
+          s->stream_busy[b->stream] = 0;
+          s->st.batch_service_ns += t - b->launch_ns;
+          if (t - b->launch_ns > s->st.max_batch_service_ns) s->st.max_batch_service_ns = t - b->launch_ns;
         }
-        if (!carry.empty()) {
-          buf.wait_carry = true;
-          s->st.long_frames += (int64_t)carry.size();
+        if (status != GRAND_OK || (!susp.empty() && !continues)) s->st.errors += 1;
+        if (continues) {  // the frames reported now release their budget; the batch keeps its buffer set
+          s->st.long_frames += (int64_t)susp.size();
+          s->st.resume_launches += 1;
+          s->st.completed += n - (int64_t)susp.size();
+          s->live_bytes -= b->bytes - b->left_bytes;
+          s->live_slots -= n - (int)susp.size();
+        } else {
+          const int64_t nrep = first ? n : (int64_t)b->suspended.size();
+          s->st.completed += nrep;
+          s->live_bytes -= first ? b->bytes : b->left_bytes;
+          s->live_slots -= (int)nrep;
+          b->done = true;
+          b->status = status;
+          s->running -= 1;
+          s->sets[b->set].busy = false;
         }
-        s->done.push_back(std::move(c));
-        b->done = true;
-        b->status = status;
-        s->running -= 1;
-        s->st.completed += b->reqs.size() - carry.size();
-        s->st.batch_service_ns += t - b->launch_ns;
-        if (t - b->launch_ns > s->st.max_batch_service_ns) s->st.max_batch_service_ns = t - b->launch_ns;
-        if (status != GRAND_OK) s->st.errors += 1;
-        s->sb[b->stream].busy = false;
-        // reclaim ring space and budget in launch order
-        while (!s->inflight.empty() && s->inflight.front().done) {
-          Batch& f = s->inflight.front();
+        // ring space goes back in launch order, as soon as a batch's symbols
+        // are no longer read; batches leave the queue once fully reported
+        for (Batch& f : s->inflight) {
+          if (!f.ring_done) break;
           s->vtail = f.vend;
-          s->live_bytes -= f.bytes - f.carried_bytes;
-          s->live_slots -= (int)f.reqs.size() - f.carried;
-          cudaEventDestroy(f.ev);
+        }
+        while (!s->inflight.empty() && s->inflight.front().done) {
+          cudaEventDestroy(s->inflight.front().ev);
           s->inflight.pop_front();
         }
       }
       s->cv_launch.notify_one();
     }
-    if (s->step > 0 && harvest_pool(s)) any = true;
     if (!any) std::this_thread::sleep_for(std::chrono::microseconds(5));
   }
 }
@@ -556,41 +457,27 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
     free_server(s);
     return GRAND_E_NOMEM;
   }
-  s->sb.resize(cfg->n_streams);
-  const size_t mb = (size_t)s->cfg.max_batch;
   s->step = cfg->resume_weight_step;
+  const size_t mb = (size_t)s->cfg.max_batch;
+  s->streams.assign(cfg->n_streams, nullptr);
+  s->stream_busy.assign(cfg->n_streams, 0);
+  for (cudaStream_t& st : s->streams)
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      free_server(s);
+      return GRAND_E_CUDA;
+    }
   if (s->step > 0) {
-    // one pool slot per admission slot: a carried request keeps its slot
-    s->pool_cap = s->cfg.max_slots;
-    const size_t pc = (size_t)s->pool_cap;
-    if (cudaStreamCreateWithFlags(&s->pstream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->pev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMalloc((void**)&s->d_pcur, sizeof(grand::FrameRec) * pc) != cudaSuccess ||
-        cudaMalloc((void**)&s->d_pcw, sizeof(uint32_t) * pc * kResultWords) != cudaSuccess ||
-        cudaMalloc((void**)&s->d_pq, sizeof(uint32_t) * pc) != cudaSuccess ||
-        cudaMalloc((void**)&s->d_pab, pc) != cudaSuccess ||
-        cudaMallocHost((void**)&s->h_pcw, sizeof(uint32_t) * pc * kResultWords) != cudaSuccess ||
-        cudaMallocHost((void**)&s->h_pq, sizeof(uint32_t) * pc) != cudaSuccess ||
-        cudaMallocHost((void**)&s->h_pab, pc) != cudaSuccess ||
-        cudaMemset(s->d_pab, 0, pc) != cudaSuccess) {
-      free_server(s);
-      return GRAND_E_NOMEM;
-    }
-    s->preq.resize(pc);
-    s->plive.assign(pc, 0);
-    s->pfree.reserve(pc);
-    for (int32_t k = s->pool_cap - 1; k >= 0; --k) s->pfree.push_back(k);
+    s->cstreams.assign(cfg->n_streams, nullptr);
+    for (cudaStream_t& st : s->cstreams)
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        free_server(s);
+        return GRAND_E_CUDA;
+      }
   }
-  for (StreamBuf& b : s->sb) {
-    if (s->step > 0 &&
-        (cudaMalloc((void**)&b.d_cur, sizeof(grand::FrameRec) * mb) != cudaSuccess ||
-         cudaMalloc((void**)&b.d_pairs, sizeof(int2) * mb) != cudaSuccess ||
-         cudaMallocHost((void**)&b.h_pairs, sizeof(int2) * mb) != cudaSuccess ||
-         cudaEventCreateWithFlags(&b.carried, cudaEventDisableTiming) != cudaSuccess)) {
-      free_server(s);
-      return GRAND_E_NOMEM;
-    }
-    if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess ||
+  // a batch with long frames keeps its buffers after its stream is free again
+  s->sets.resize(s->step > 0 ? 2 * cfg->n_streams : cfg->n_streams);
+  for (BufSet& b : s->sets) {
+    if ((s->step > 0 && cudaMalloc((void**)&b.d_cur, sizeof(grand::FrameRec) * mb) != cudaSuccess) ||
         cudaMalloc((void**)&b.d_desc, sizeof(grand_frame_desc) * mb) != cudaSuccess ||
         cudaMalloc((void**)&b.d_cw, sizeof(uint32_t) * mb * kResultWords) != cudaSuccess ||
         cudaMalloc((void**)&b.d_q, sizeof(uint32_t) * mb) != cudaSuccess ||
@@ -609,9 +496,9 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
   {
     const size_t per_batch = 256 + sizeof(grand::FrameRec) * mb + 4096;
     void* warm = nullptr;
-    if (grand::scratch_alloc(&warm, per_batch * s->sb.size(), s->sb[0].stream) == cudaSuccess)
-      cudaFreeAsync(warm, s->sb[0].stream);
-    cudaStreamSynchronize(s->sb[0].stream);
+    if (grand::scratch_alloc(&warm, per_batch * s->sets.size(), s->streams[0]) == cudaSuccess)
+      cudaFreeAsync(warm, s->streams[0]);
+    cudaStreamSynchronize(s->streams[0]);
   }
   if (grand::preload_qam_kernels() != GRAND_OK) {
     free_server(s);
@@ -756,7 +643,9 @@ extern "C" int grand_server_get_stats(grand_server* s, grand_server_stats* out) 
   out->live_bytes = s->live_bytes;
   out->pending = (int64_t)s->pending.size();
   out->inflight_batches = (int64_t)s->inflight.size();
-  out->long_live = s->plive_n;
+  out->long_live = 0;
+  for (const Batch& b : s->inflight)
+    if (b.cont && !b.done) out->long_live += (int64_t)b.suspended.size();
   return GRAND_OK;
 }
 

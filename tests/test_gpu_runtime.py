@@ -110,3 +110,32 @@ def test_autotune_mixed(g):
     b = g.decode_mixed(codes, g.Params.make(M=0, S=10, query_cap=1 << 20), desc, sym, mx["n_cw_words"])
     torch.cuda.synchronize()
     assert torch.equal(a["cw"], b["cw"]) and torch.equal(a["queries"], b["queries"])
+
+
+@pytest.mark.parametrize("S,N,M,snr", [(10, 128, 16, 7.0), (12, 512, 64, 14.0)])
+def test_autotune_chooses_membership(g, tmp_path, S, N, M, snr):
+    """GRAND_MEMBERSHIP_FASTEST: the tuner times both exact membership tests
+    with their launch shapes, writes the faster into params.membership, records
+    it in the cache, and the tuned decode equals the TEP-by-TEP one."""
+    import torch
+
+    code = g.Code.polar(N, N // 2)
+    d = wl.qam_frames(54, S, 3000, N, info_of(g, N), M, snr)
+    sym = torch.from_numpy(d["symbols"]).cuda()
+    p = g.Params.make(M=M, S=S, query_cap=1 << 20, membership=g.MEMBERSHIP_FASTEST)
+    cache = str(tmp_path / "tiles.txt")
+    r = g.autotune(code, p, sym, cache_path=cache)
+    assert p.membership in (g.MEMBERSHIP_AUTO, g.MEMBERSHIP_HASH) and r["membership"] == p.membership
+    assert r["candidates"] > len({0, 3})  # shapes of both tests
+    with open(cache) as fh:
+        fields = fh.read().split()
+    assert int(fields[-1]) == p.membership
+    p2 = g.Params.make(M=M, S=S, query_cap=1 << 20, membership=g.MEMBERSHIP_FASTEST)
+    r2 = g.autotune(code, p2, sym, cache_path=cache)
+    assert r2["from_cache"] and p2.membership == p.membership and tuple(p2.tiles) == tuple(p.tiles)
+    a = g.decode_symbols(code, p, sym)
+    b = g.decode_symbols(code, g.Params.make(M=M, S=S, query_cap=1 << 20), sym)
+    torch.cuda.synchronize()
+    assert torch.equal(a["cw"], b["cw"]) and torch.equal(a["queries"], b["queries"])
+    assert torch.equal(a["abandon"], b["abandon"])
+    code.close()

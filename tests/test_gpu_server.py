@@ -102,9 +102,9 @@ def test_results_equal_alone(env, membership):
 @pytest.mark.parametrize("membership,step", [(0, 1), (3, 1), (0, 2)])
 def test_long_frames_carried_equal_alone(env, membership, step):
     """resume_weight_step > 0: frames whose search outlasts the batch's weight
-    window move to the long-frame pool as device-resident cursors and finish
-    in later pool windows; every result equals the frame decoded alone, the
-    batches complete without them, and the pool drains to empty."""
+    window are continued from their device-resident cursors on a separate
+    stream after the rest of their batch is reported; every result equals the
+    frame decoded alone, and nothing is left in flight after the drain."""
     g, codes, info = env
     code_of_N = {n: i for i, n in enumerate(NS)}
     mx = wl.mixed_frames(62, step, 2000, info, ebn0_range=(4.0, 10.0))
