@@ -470,7 +470,7 @@ int grand_autotune_mixed(const grand_code* const* codes, int n_codes, grand_para
  *                     remaining weight -- from their device-resident cursors
  *                     on a separate stream, and are reported when done. Every
  *                     result equals the uninterrupted search's. The server
- *                     then holds twice n_streams buffer sets (a batch keeps
+ *                     then holds 4 x n_streams buffer sets (a batch keeps
  *                     its set until its last frame is reported).
  *   params.deadline_ns, when nonzero, is the budget of each batch launch (and
  *   of each continuation). */
@@ -498,14 +498,17 @@ typedef struct grand_request {
 } grand_request;
 
 /* One completed request: decoded word (first N/32 words of cw), query count,
- * abandon flag (as grand_decode_batch; 4 = the batch failed on the device). */
+ * abandon flag (as grand_decode_batch; 4 = the batch failed on the device),
+ * continued = 1 when the frame's search went on after its batch was reported
+ * (resume_weight_step > 0), else 0. */
 typedef struct grand_result {
   uint64_t tag;
   int64_t arrival_ns;
   int64_t done_ns;
   uint32_t queries;
   uint8_t abandon;
-  uint8_t pad[3];
+  uint8_t continued;
+  uint8_t pad[2];
   uint32_t cw[GRAND_N_MAX / 32];
 } grand_result;
 

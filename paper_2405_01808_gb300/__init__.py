@@ -662,7 +662,7 @@ def autotune_mixed(codes, params: Params, desc, symbols, n_cw_words: int, N0: fl
 # --------------------------------------------------------------------------
 REQUEST_DTYPE = np.dtype([("code", "<i4"), ("M", "<i4"), ("symbols", "<u8"), ("tag", "<u8"), ("arrival_ns", "<i8")])
 RESULT_DTYPE = np.dtype([("tag", "<u8"), ("arrival_ns", "<i8"), ("done_ns", "<i8"), ("queries", "<u4"),
-                         ("abandon", "u1"), ("pad", "u1", (3,)), ("cw", "<u4", (32,))])
+                         ("abandon", "u1"), ("continued", "u1"), ("pad", "u1", (2,)), ("cw", "<u4", (32,))])
 
 
 class ServerCfg(ctypes.Structure):

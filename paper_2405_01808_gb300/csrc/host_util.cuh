@@ -67,6 +67,12 @@ inline cudaMemPool_t lib_pool(int dev) {
     if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    // Never reuse a block whose free is still pending on another stream by
+    // making the allocating stream wait for that stream: concurrent decodes
+    // (the serving loop's streams, a long frame's continuation) would then
+    // serialise behind one another. The pool grows instead, and keeps it.
+    int no = 0;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
     pools[dev] = pool;
   }
   return pools[dev];

@@ -24,10 +24,14 @@
 // see grand_decode_symbols_resumable) in the batch's buffer set on the
 // device; the harvester reports the batch's other frames at once, hands its
 // stream back, and continues the suspended ones -- every remaining weight --
-// on one of the server's continuation streams, from those cursors. The
-// buffer set stays with the batch until its last frame is reported, so
-// buffer sets outnumber streams (twice as many). Results are those of the
-// uninterrupted search.
+// on one of the server's continuation streams, from those cursors: a small
+// gather on the batch's stream first moves the suspended frames' cursors and
+// hard words into compact device memory of their own (stream-ordered pool),
+// so the batch's buffer set is free again at once, and their results come
+// back through one of the server's pinned result blocks. When every block is
+// in use, the continuation runs in place instead and the batch keeps its
+// buffer set until its last frame is reported (buffer sets outnumber streams:
+// four per stream). Results are those of the uninterrupted search.
 #include <errno.h>
 #include <stdlib.h>
 #include <string.h>
@@ -70,6 +74,9 @@ struct Req {
 // every frame of it is reported; its stream is freed earlier).
 struct BufSet {
   grand::FrameRec* d_cur = nullptr;  // per-frame cursors (resume_weight_step > 0)
+  int32_t* h_idx = nullptr;          // pinned: frames to gather into a continuation
+  cudaEvent_t free_after = nullptr;  // the gather out of this set is done
+  bool wait_free = false;            // the next batch on this set waits for free_after
   grand_frame_desc* d_desc = nullptr;
   grand_frame_desc* h_desc = nullptr;
   uint32_t* d_cw = nullptr;
@@ -97,6 +104,24 @@ struct Batch {
   int cstream = -1;
   std::vector<int32_t> suspended;  // frames of the batch it continues
   int64_t left_bytes = 0;          // budget still held by them
+};
+
+// Pinned host buffers receiving one continuation's results.
+struct ResultBlock {
+  uint32_t* h_cw = nullptr;
+  uint32_t* h_q = nullptr;
+  uint8_t* h_ab = nullptr;
+  bool busy = false;
+};
+
+// Suspended frames of one batch continued from compact device copies of
+// their cursors (the batch itself is done); request i is compact entry i.
+struct LongJob {
+  std::vector<Req> reqs;
+  int block;
+  int64_t bytes;
+  cudaEvent_t ev;
+  int status;
 };
 
 // Completed results waiting for poll, in completion order.
@@ -129,6 +154,9 @@ struct grand_server {
   int32_t step = 0;                    // resume_weight_step
   std::vector<cudaStream_t> cstreams;  // continuation streams of long frames
   int next_cstream = 0;
+  std::vector<ResultBlock> blocks;     // result blocks of continuations
+  std::deque<LongJob> jobs;            // continuations in flight (the harvester's)
+  int64_t long_live = 0;               // frames being continued
   std::deque<Req> pending;     // admitted, not launched (ring order)
   std::deque<Batch> inflight;  // launch order
   std::deque<Chunk> done;
@@ -149,8 +177,16 @@ void free_server(grand_server* s) {
     if (st) cudaStreamSynchronize(st);
   for (cudaStream_t st : s->cstreams)
     if (st) cudaStreamSynchronize(st);
+  for (ResultBlock& r : s->blocks) {
+    cudaFreeHost(r.h_cw);
+    cudaFreeHost(r.h_q);
+    cudaFreeHost(r.h_ab);
+  }
+  for (LongJob& j : s->jobs) cudaEventDestroy(j.ev);
   for (BufSet& b : s->sets) {
     cudaFree(b.d_cur);
+    cudaFreeHost(b.h_idx);
+    if (b.free_after) cudaEventDestroy(b.free_after);
     cudaFree(b.d_desc);
     cudaFree(b.d_cw);
     cudaFree(b.d_q);
@@ -178,6 +214,8 @@ int launch_batch(grand_server* s, Batch& b) {
   BufSet& buf = s->sets[b.set];
   const cudaStream_t stream = s->streams[b.stream];
   const int n = (int)b.reqs.size();
+  // the previous batch's long frames must have been gathered out of this set
+  if (buf.wait_free && cudaStreamWaitEvent(stream, buf.free_after, 0) != cudaSuccess) return GRAND_E_CUDA;
   for (int i = 0; i < n; ++i) {
     const Req& r = b.reqs[i];
     buf.h_desc[i].code = r.code;
@@ -212,6 +250,66 @@ int launch_batch(grand_server* s, Batch& b) {
     return GRAND_E_CUDA;
   if (cudaEventRecord(b.ev, stream) != cudaSuccess) return GRAND_E_CUDA;
   return GRAND_OK;
+}
+
+// Gather k suspended frames (indices idx) of a buffer set into compact arrays.
+__global__ void k_gather_long(const int32_t* idx, int k, const grand::FrameRec* cur, const uint32_t* cw,
+                              const uint32_t* q, const uint8_t* ab, grand::FrameRec* ccur, uint32_t* ccw,
+                              uint32_t* cq, uint8_t* cab) {
+  const int lane = threadIdx.x & 31;
+  const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (i >= k) return;
+  const int f = idx[i];
+  constexpr int kWords = (int)(sizeof(grand::FrameRec) / 4);
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(cur + f);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(ccur + i);
+  for (int w = lane; w < kWords; w += 32) dst[w] = src[w];
+  ccw[(size_t)i * kResultWords + lane] = cw[(size_t)f * kResultWords + lane];
+  if (lane == 0) {
+    cq[i] = q[f];
+    cab[i] = ab[f];
+  }
+}
+
+// The suspended frames `susp` of batch b (its first launch finished) as a
+// continuation job: gather their cursors and hard words out of the batch's
+// set on the batch's stream (the set is reusable after that), then every
+// remaining weight on a continuation stream, results into result block
+// `block`. No lock held; returns a CUDA status.
+int launch_job(grand_server* s, const Batch& b, const std::vector<int32_t>& susp, int block, int cstream,
+               cudaEvent_t ev) {
+  grand::NvtxRange range("grand.server.resume");
+  BufSet& buf = s->sets[b.set];
+  const cudaStream_t st = s->streams[b.stream];
+  const cudaStream_t cs = s->cstreams[cstream];
+  const int k = (int)susp.size();
+  const size_t cur_b = sizeof(grand::FrameRec) * k, cw_b = sizeof(uint32_t) * kResultWords * k;
+  const size_t q_b = sizeof(uint32_t) * k, idx_b = sizeof(int32_t) * k;
+  const size_t total = ((cur_b + cw_b + q_b + idx_b + k) + 255) & ~(size_t)255;
+  char* mem = nullptr;
+  if (grand::scratch_alloc((void**)&mem, total, st) != cudaSuccess) return GRAND_E_NOMEM;
+  grand::FrameRec* ccur = reinterpret_cast<grand::FrameRec*>(mem);
+  uint32_t* ccw = reinterpret_cast<uint32_t*>(mem + cur_b);
+  uint32_t* cq = reinterpret_cast<uint32_t*>(mem + cur_b + cw_b);
+  int32_t* cidx = reinterpret_cast<int32_t*>(mem + cur_b + cw_b + q_b);
+  uint8_t* cab = reinterpret_cast<uint8_t*>(mem + cur_b + cw_b + q_b + idx_b);
+  for (int i = 0; i < k; ++i) buf.h_idx[i] = susp[i];
+  if (cudaMemcpyAsync(cidx, buf.h_idx, idx_b, cudaMemcpyHostToDevice, st) != cudaSuccess) return GRAND_E_CUDA;
+  k_gather_long<<<(k * 32 + 127) / 128, 128, 0, st>>>(cidx, k, buf.d_cur, buf.d_cw, buf.d_q, buf.d_ab, ccur, ccw, cq,
+                                                      cab);
+  if (cudaGetLastError() != cudaSuccess || cudaEventRecord(buf.free_after, st) != cudaSuccess ||
+      cudaStreamWaitEvent(cs, buf.free_after, 0) != cudaSuccess)
+    return GRAND_E_CUDA;
+  int rc = grand::resume_resident(s->d_table, (int)s->codes.size(), s->Wmax, &s->cfg.params, ccur, k, 0, ccw,
+                                  kResultWords, cq, cab, cs);
+  if (rc != GRAND_OK) return rc;
+  const ResultBlock& rb = s->blocks[block];
+  if (cudaMemcpyAsync(rb.h_cw, ccw, cw_b, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaMemcpyAsync(rb.h_q, cq, q_b, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaMemcpyAsync(rb.h_ab, cab, k, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+    return GRAND_E_CUDA;
+  cudaFreeAsync(mem, cs);
+  return cudaEventRecord(ev, cs) == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
 // The rest of batch b's suspended frames (every remaining weight) on a
@@ -293,6 +391,56 @@ void launcher_main(grand_server* s) {
   }
 }
 
+// Finished continuation jobs: report their frames, free their result blocks.
+// Harvester thread only (it alone adds and removes jobs). Returns whether one
+// was harvested.
+bool harvest_jobs(grand_server* s) {
+  bool any = false;
+  for (auto it = s->jobs.begin(); it != s->jobs.end();) {
+    const cudaError_t q = cudaEventQuery(it->ev);
+    if (q == cudaErrorNotReady) {
+      ++it;
+      continue;
+    }
+    any = true;
+    const int64_t t = now_ns();
+    const ResultBlock& rb = s->blocks[it->block];
+    Chunk c;
+    c.v.resize(it->reqs.size());
+    for (size_t i = 0; i < it->reqs.size(); ++i) {
+      grand_result& r = c.v[i];
+      memset(&r, 0, sizeof r);
+      r.tag = it->reqs[i].tag;
+      r.arrival_ns = it->reqs[i].arrival_ns;
+      r.done_ns = t;
+      r.continued = 1;
+      if (q == cudaSuccess) {
+        r.queries = rb.h_q[i];
+        r.abandon = rb.h_ab[i];
+        memcpy(r.cw, rb.h_cw + i * kResultWords, sizeof(uint32_t) * it->reqs[i].nw);
+      } else {
+        r.abandon = 4;
+      }
+    }
+    cudaEventDestroy(it->ev);
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->done.push_back(std::move(c));
+      s->blocks[it->block].busy = false;
+      const int k = (int)it->reqs.size();
+      s->live_slots -= k;
+      s->live_bytes -= it->bytes;
+      s->long_live -= k;
+      s->st.completed += k;
+      if (q != cudaSuccess) s->st.errors += 1;
+      s->running -= 1;
+    }
+    it = s->jobs.erase(it);
+    s->cv_launch.notify_one();
+  }
+  return any;
+}
+
 void harvester_main(grand_server* s) {
   cudaSetDevice(s->device);
   std::vector<Batch*> running;
@@ -330,6 +478,7 @@ void harvester_main(grand_server* s) {
         r.tag = b->reqs[i].tag;
         r.arrival_ns = b->reqs[i].arrival_ns;
         r.done_ns = t;
+        r.continued = first ? 0 : 1;
         if (!failed) {
           r.queries = buf.h_q[i];
           r.abandon = buf.h_ab[i];
@@ -351,18 +500,45 @@ void harvester_main(grand_server* s) {
       } else {
         for (int32_t i : b->suspended) emit(i, status != GRAND_OK);
       }
-      bool continues = false;
+      bool continues = false;  // in place: the batch keeps its set
+      bool job = false;        // as a continuation job: the batch is done
+      LongJob lj;
       if (!susp.empty()) {
         b->suspended = susp;
         b->left_bytes = 0;
         for (int32_t i : susp) b->left_bytes += b->reqs[i].bytes;
-        b->cstream = s->next_cstream;
+        const int cstream = s->next_cstream;
         s->next_cstream = (s->next_cstream + 1) % (int)s->cstreams.size();
-        b->cont = true;
-        continues = launch_continuation(s, *b) == GRAND_OK;
-        if (!continues) {  // report them as failed now
-          b->cont = false;
-          for (int32_t i : susp) emit(i, true);
+        int block = -1;
+        {
+          std::unique_lock<std::mutex> lk(s->mu);
+          for (int i = 0; i < (int)s->blocks.size(); ++i)
+            if (!s->blocks[i].busy) {
+              block = i;
+              s->blocks[i].busy = true;
+              break;
+            }
+        }
+        if (block >= 0 && cudaEventCreateWithFlags(&lj.ev, cudaEventDisableTiming) == cudaSuccess) {
+          lj.block = block;
+          lj.bytes = b->left_bytes;
+          lj.status = GRAND_OK;
+          for (int32_t i : susp) lj.reqs.push_back(b->reqs[i]);
+          job = launch_job(s, *b, susp, block, cstream, lj.ev) == GRAND_OK;
+          if (!job) cudaEventDestroy(lj.ev);
+        }
+        if (!job) {
+          if (block >= 0) {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->blocks[block].busy = false;
+          }
+          b->cstream = cstream;
+          b->cont = true;
+          continues = launch_continuation(s, *b) == GRAND_OK;
+          if (!continues) {  // report them as failed now
+            b->cont = false;
+            for (int32_t i : susp) emit(i, true);
+          }
         }
       }
       {
@@ -374,15 +550,31 @@ void harvester_main(grand_server* s) {
           s->st.batch_service_ns += t - b->launch_ns;
           if (t - b->launch_ns > s->st.max_batch_service_ns) s->st.max_batch_service_ns = t - b->launch_ns;
         }
-        if (status != GRAND_OK || (!susp.empty() && !continues)) s->st.errors += 1;
-        if (continues) {  // the frames reported now release their budget; the batch keeps its buffer set
+        if (status != GRAND_OK || (!susp.empty() && !continues && !job)) s->st.errors += 1;
+        if (job) {  // the suspended frames left with the job: the batch is done, its set free after the gather
           s->st.long_frames += (int64_t)susp.size();
           s->st.resume_launches += 1;
           s->st.completed += n - (int64_t)susp.size();
           s->live_bytes -= b->bytes - b->left_bytes;
           s->live_slots -= n - (int)susp.size();
+          s->long_live += (int64_t)susp.size();
+          b->done = true;
+          b->status = status;
+          s->running -= 1;
+          s->sets[b->set].wait_free = true;
+          s->sets[b->set].busy = false;
+          s->jobs.push_back(std::move(lj));
+          s->running += 1;  // the job is harvested like a batch
+        } else if (continues) {  // the frames reported now release their budget; the batch keeps its buffer set
+          s->st.long_frames += (int64_t)susp.size();
+          s->st.resume_launches += 1;
+          s->long_live += (int64_t)susp.size();
+          s->st.completed += n - (int64_t)susp.size();
+          s->live_bytes -= b->bytes - b->left_bytes;
+          s->live_slots -= n - (int)susp.size();
         } else {
           const int64_t nrep = first ? n : (int64_t)b->suspended.size();
+          if (!first) s->long_live -= nrep;
           s->st.completed += nrep;
           s->live_bytes -= first ? b->bytes : b->left_bytes;
           s->live_slots -= (int)nrep;
@@ -404,6 +596,7 @@ void harvester_main(grand_server* s) {
       }
       s->cv_launch.notify_one();
     }
+    if (!s->jobs.empty() && harvest_jobs(s)) any = true;
     if (!any) std::this_thread::sleep_for(std::chrono::microseconds(5));
   }
 }
@@ -475,8 +668,25 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
       }
   }
   // a batch with long frames keeps its buffers after its stream is free again
-  s->sets.resize(s->step > 0 ? 2 * cfg->n_streams : cfg->n_streams);
+  // (until its last frame is reported): with a long frame in most batches,
+  // every set can be waiting on one, so there are four per stream
+  s->sets.resize(s->step > 0 ? 4 * cfg->n_streams : cfg->n_streams);
+  if (s->step > 0) {
+    s->blocks.resize(4 * cfg->n_streams);
+    for (ResultBlock& r : s->blocks)
+      if (cudaMallocHost((void**)&r.h_cw, sizeof(uint32_t) * mb * kResultWords) != cudaSuccess ||
+          cudaMallocHost((void**)&r.h_q, sizeof(uint32_t) * mb) != cudaSuccess ||
+          cudaMallocHost((void**)&r.h_ab, mb) != cudaSuccess) {
+        free_server(s);
+        return GRAND_E_NOMEM;
+      }
+  }
   for (BufSet& b : s->sets) {
+    if (s->step > 0 && (cudaMallocHost((void**)&b.h_idx, sizeof(int32_t) * mb) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&b.free_after, cudaEventDisableTiming) != cudaSuccess)) {
+      free_server(s);
+      return GRAND_E_NOMEM;
+    }
     if ((s->step > 0 && cudaMalloc((void**)&b.d_cur, sizeof(grand::FrameRec) * mb) != cudaSuccess) ||
         cudaMalloc((void**)&b.d_desc, sizeof(grand_frame_desc) * mb) != cudaSuccess ||
         cudaMalloc((void**)&b.d_cw, sizeof(uint32_t) * mb * kResultWords) != cudaSuccess ||
@@ -643,9 +853,7 @@ extern "C" int grand_server_get_stats(grand_server* s, grand_server_stats* out) 
   out->live_bytes = s->live_bytes;
   out->pending = (int64_t)s->pending.size();
   out->inflight_batches = (int64_t)s->inflight.size();
-  out->long_live = 0;
-  for (const Batch& b : s->inflight)
-    if (b.cont && !b.done) out->long_live += (int64_t)b.suspended.size();
+  out->long_live = s->long_live;
   return GRAND_OK;
 }
 
