@@ -111,8 +111,11 @@ def test_params_layout_matches_header(glib):
     for name, value in (("GRAND_ORDER_QAM_NEARER", glib.ORDER_QAM_NEARER), ("GRAND_ORDER_QAM_NNE5", glib.ORDER_QAM_NNE5),
                         ("GRAND_MEMBERSHIP_DELTA", glib.MEMBERSHIP_DELTA),
                         ("GRAND_MEMBERSHIP_ROW_PARITY", glib.MEMBERSHIP_ROW_PARITY),
-                        ("GRAND_MEMBERSHIP_HASH", glib.MEMBERSHIP_HASH)):
-        assert re.search(rf"{name}\s*=\s*{value}\b", text), name
+                        ("GRAND_MEMBERSHIP_HASH", glib.MEMBERSHIP_HASH),
+                        ("GRAND_MEMBERSHIP_FASTEST", glib.MEMBERSHIP_FASTEST),
+                        ("GRAND_ABANDON_SUSPENDED", glib.ABANDON_SUSPENDED),
+                        ("GRAND_CURSOR_BYTES", glib.CURSOR_BYTES)):
+        assert re.search(rf"{name}(\s*=\s*|\s+){value}\b", text), name
 
 
 # Every struct of the ABI as a C compiler lays it out (gcc on include/grand.h,
@@ -132,14 +135,16 @@ int main(void) {
   Z(grand_stats) F(grand_stats, evaluated_checks) F(grand_stats, hard_frames) F(grand_stats, search_useful)
   F(grand_stats, prep_ms) F(grand_stats, search_ms)
   Z(grand_tune_result) F(grand_tune_result, best_ms) F(grand_tune_result, candidates) F(grand_tune_result, from_cache)
+  F(grand_tune_result, membership)
   Z(grand_server_cfg) F(grand_server_cfg, codes) F(grand_server_cfg, n_codes) F(grand_server_cfg, params)
   F(grand_server_cfg, N0) F(grand_server_cfg, max_slots) F(grand_server_cfg, max_device_bytes)
-  F(grand_server_cfg, max_batch) F(grand_server_cfg, n_streams)
+  F(grand_server_cfg, max_batch) F(grand_server_cfg, n_streams) F(grand_server_cfg, resume_weight_step)
   Z(grand_request) F(grand_request, code) F(grand_request, M) F(grand_request, symbols) F(grand_request, tag)
   F(grand_request, arrival_ns)
   Z(grand_result) F(grand_result, tag) F(grand_result, arrival_ns) F(grand_result, done_ns) F(grand_result, queries)
-  F(grand_result, abandon) F(grand_result, pad) F(grand_result, cw)
+  F(grand_result, abandon) F(grand_result, continued) F(grand_result, pad) F(grand_result, cw)
   Z(grand_server_stats) F(grand_server_stats, admitted) F(grand_server_stats, max_launch_ns)
+  F(grand_server_stats, long_frames) F(grand_server_stats, resume_launches) F(grand_server_stats, long_live)
   return 0;
 }
 """
