@@ -101,7 +101,17 @@ struct SearchArgs {
   int64_t cw_stride;
   int n_codes;  // entries of `codes` (a cursor naming another code is rejected)
   int sp_max;   // largest S' the launched kernel's tables hold
+  int64_t max_entries;  // bound on the queue's length (the grid needs no more warps)
 };
+
+// CTAs of a persistent search launch: one wave (every SM full), or fewer when
+// the queue cannot have more entries than that many CTAs' warps (a small
+// batch then dispatches no CTAs that would only find the queue empty).
+static inline int search_grid(int per_sm, int warps_per_cta, int64_t max_entries) {
+  const int64_t full = (int64_t)sm_count() * per_sm;
+  const int64_t need = max_entries > 0 ? (max_entries + warps_per_cta - 1) / warps_per_cta : full;
+  return (int)(need < full ? (need > 0 ? need : 1) : full);
+}
 
 // Output slot of queue entry fi: the batch frame of a preparation record, or
 // the cursor's own index when resuming (computed where needed, so that none of
@@ -1314,6 +1324,13 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
     const unsigned nA = warp_side_layout(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, sl.cumA);
     const unsigned nB = warp_side_layout(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, sl.cumB);
     const int nG = (int)((nA + 31) / 32);
+    // weight window of this call: w_done + 1 .. w_hi (all weights without a
+    // step); no TEP heavier than the cap's class matters
+    const int w_hi = kResume && a.w_step > 0 ? min(Sp, w_done + a.w_step) : Sp;
+    const int w_lim = min(w_cap, w_hi);
+    // A groups a window can reach (entries of weight <= w_lim): the planes of
+    // later groups are never read, so a windowed search does not build them
+    const int nG_use = kResume ? (int)((sl.cumA[min(w_lim, nAr)] + 31) / 32) : nG;
     // the bit-plane pattern of a padding entry (never a candidate in practice;
     // candidates beyond nA are skipped at verification)
     const uint32_t pad_plane = (kPadA >> (lane < kPlanes ? lane : 0)) & 1u ? 0xFFFFFFFFu : 0u;
@@ -1321,7 +1338,9 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
       // A side: scalar projections into the B buffer (doubling), then
       // bit-planes (one group of 32 entries per warp transpose)
       warp_fill_side(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, f0, sl.Bz);
-      for (int g = 0; g < D::kGroups; ++g) {
+      const int g_build = kResume ? min(D::kGroups, (nG_use + kGroupUnroll - 1) / kGroupUnroll * kGroupUnroll)
+                                  : D::kGroups;
+      for (int g = 0; g < g_build; ++g) {
         if (g < nG) {
           const unsigned e = 32u * g + lane;
           const uint32_t q = e < nA ? sl.Bz[e] : kPadA;
@@ -1337,7 +1356,7 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
     } else {
       // large sides: no scalar tables; each lane derives its A entry from the
       // table layout, one group of 32 per warp transpose
-      const int nG8 = (nG + kGroupUnroll - 1) / kGroupUnroll * kGroupUnroll;
+      const int nG8 = (nG_use + kGroupUnroll - 1) / kGroupUnroll * kGroupUnroll;
       for (int g = 0; g < nG8; ++g) {
         const unsigned e = 32u * g + lane;
         uint32_t q = kPadA, acode;
@@ -1352,10 +1371,7 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
     uint32_t best_rank = 0xFFFFFFFFu, best_code = 0;
     int best_w = 127;
     const int nCh = (int)((nB + 31) / 32);
-    // weight window of this call: w_done + 1 .. w_hi (all weights without a
-    // step); no TEP heavier than the cap's class matters
-    const int w_hi = kResume && a.w_step > 0 ? min(Sp, w_done + a.w_step) : Sp;
-    const int w_lim = min(w_cap, w_hi);
+
     for (int ch = 0; ch < nCh; ++ch) {
       const int wb = side_entry_weight(sl.cumB, nBr, 32u * ch);
       const int budget = min(best_w, w_lim) - wb;  // heaviest A weight still worth testing
@@ -2362,7 +2378,7 @@ template <int B>
 static int launch_search_t(const SearchArgs& s, int threads, size_t smem, cudaStream_t st) {
   const int per_sm = resident_ctas((const void*)k_search<B>, threads, smem);
   if (per_sm < 0) return GRAND_E_CUDA;
-  k_search<B><<<sm_count() * per_sm, threads, smem, st>>>(s);
+  k_search<B><<<search_grid(per_sm, 1, s.max_entries), threads, smem, st>>>(s);
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
@@ -2373,7 +2389,7 @@ static int launch_search_warp_t(const SearchArgs& s, int warps, cudaStream_t st)
   auto kern = (s.w_step > 0 || s.cur_in) ? k_search_warp<B, kSide, true> : k_search_warp<B, kSide, false>;
   const int per_sm = resident_ctas((const void*)kern, 32 * warps, smem);
   if (per_sm < 0) return GRAND_E_CUDA;
-  kern<<<sm_count() * per_sm, 32 * warps, smem, st>>>(s);
+  kern<<<search_grid(per_sm, warps, s.max_entries), 32 * warps, smem, st>>>(s);
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
@@ -2383,7 +2399,7 @@ static int launch_search_hash_t(const SearchArgs& s, int warps, cudaStream_t st)
   auto kern = (s.w_step > 0 || s.cur_in) ? k_search_hash<kSide, true> : k_search_hash<kSide, false>;
   const int per_sm = resident_ctas((const void*)kern, 32 * warps, hsmem);
   if (per_sm < 0) return GRAND_E_CUDA;
-  kern<<<sm_count() * per_sm, 32 * warps, hsmem, st>>>(s);
+  kern<<<search_grid(per_sm, warps, s.max_entries), 32 * warps, hsmem, st>>>(s);
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
@@ -2457,6 +2473,7 @@ struct ResumeOpt {
   int64_t n_cur = 0;
   int64_t cw_stride = 0;
   int n_codes = 1;
+  int64_t max_entries = 0;  // bound on the search queue (0: unknown)
 };
 
 static int launch_qam_search(const grand_params* p, int Smax, int w0, int Wmax, const CodeDev* d_codes,
@@ -2471,6 +2488,7 @@ static int launch_qam_search(const grand_params* p, int Smax, int w0, int Wmax, 
   s.cw_stride = ro.cw_stride;
   s.n_codes = ro.n_codes;
   s.sp_max = Smax;
+  s.max_entries = ro.cur_in ? ro.n_cur : ro.max_entries;
   s.recs = recs;
   s.codes = d_codes;
   s.scr = scr;
@@ -2553,6 +2571,7 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
 
     ResumeOpt ro2 = ro;
     ro2.n_codes = n_codes;
+    ro2.max_entries = n_frames;  // at most every frame is handed on
     if (launch_qam_search(p, Smax, a.w0, Wmax, d_codes, recs, scr, proto.cw, proto.queries, proto.abandon, st, ro2) !=
         GRAND_OK) {
       rc = GRAND_E_CUDA;
@@ -2614,12 +2633,15 @@ static int run_ab(const grand_code* c, const grand_params* p, const float* sampl
     if (stats) *stats = grand_stats{};
     return GRAND_OK;
   }
+  // the counters (statistics) and the deadline's clock stamp are the only
+  // scratch of the bit-level search: without either, none is allocated
   Scratch* scr = nullptr;
-  if (scratch_alloc((void**)&scr, sizeof(Scratch), st) != cudaSuccess) return GRAND_E_NOMEM;
+  const bool need_scr = stats != nullptr || p->deadline_ns > 0;
+  if (need_scr && scratch_alloc((void**)&scr, sizeof(Scratch), st) != cudaSuccess) return GRAND_E_NOMEM;
   int rc = GRAND_OK;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   do {
-    if (cudaMemsetAsync(scr, 0, sizeof(Scratch), st) != cudaSuccess) { rc = GRAND_E_CUDA; break; }
+    if (need_scr && cudaMemsetAsync(scr, 0, sizeof(Scratch), st) != cudaSuccess) { rc = GRAND_E_CUDA; break; }
     if (stats) {
       if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) { rc = GRAND_E_CUDA; break; }
       cudaEventRecord(ev[0], st);
@@ -2670,7 +2692,7 @@ static int run_ab(const grand_code* c, const grand_params* p, const float* sampl
   } while (0);
   for (int i = 0; i < 2; ++i)
     if (ev[i]) cudaEventDestroy(ev[i]);
-  cudaFreeAsync(scr, st);
+  if (scr) cudaFreeAsync(scr, st);
   return rc;
 }
 

@@ -26,10 +26,10 @@
 // stream back, and continues the suspended ones -- every remaining weight --
 // on one of the server's continuation streams, from those cursors: a small
 // gather on the batch's stream first moves the suspended frames' cursors and
-// hard words into compact device memory of their own (stream-ordered pool),
-// so the batch's buffer set is free again at once, and their results come
-// back through one of the server's pinned result blocks. When every block is
-// in use, the continuation runs in place instead and the batch keeps its
+// hard words into one of the server's continuation blocks (compact device
+// arrays and pinned result buffers, preallocated), so the batch's buffer set
+// is free again at once. When every block is in use (or a batch has more
+// long frames than a block holds), the continuation runs in place instead and the batch keeps its
 // buffer set until its last frame is reported (buffer sets outnumber streams:
 // four per stream). Results are those of the uninterrupted search.
 #include <errno.h>
@@ -106,8 +106,17 @@ struct Batch {
   int64_t left_bytes = 0;          // budget still held by them
 };
 
-// Pinned host buffers receiving one continuation's results.
+// Buffers of one continuation job (capacity kBlockFrames frames): compact
+// device copies of the suspended frames' cursors, words and counters, and the
+// pinned host buffers receiving their results. Preallocated: a job allocates
+// nothing (growing a memory pool under a running server stalls it).
+constexpr int kBlockFrames = 4096;
 struct ResultBlock {
+  grand::FrameRec* d_cur = nullptr;
+  uint32_t* d_cw = nullptr;
+  uint32_t* d_q = nullptr;
+  uint8_t* d_ab = nullptr;
+  int32_t* d_idx = nullptr;
   uint32_t* h_cw = nullptr;
   uint32_t* h_q = nullptr;
   uint8_t* h_ab = nullptr;
@@ -178,6 +187,11 @@ void free_server(grand_server* s) {
   for (cudaStream_t st : s->cstreams)
     if (st) cudaStreamSynchronize(st);
   for (ResultBlock& r : s->blocks) {
+    cudaFree(r.d_cur);
+    cudaFree(r.d_cw);
+    cudaFree(r.d_q);
+    cudaFree(r.d_ab);
+    cudaFree(r.d_idx);
     cudaFreeHost(r.h_cw);
     cudaFreeHost(r.h_q);
     cudaFreeHost(r.h_ab);
@@ -283,16 +297,13 @@ int launch_job(grand_server* s, const Batch& b, const std::vector<int32_t>& susp
   const cudaStream_t st = s->streams[b.stream];
   const cudaStream_t cs = s->cstreams[cstream];
   const int k = (int)susp.size();
-  const size_t cur_b = sizeof(grand::FrameRec) * k, cw_b = sizeof(uint32_t) * kResultWords * k;
-  const size_t q_b = sizeof(uint32_t) * k, idx_b = sizeof(int32_t) * k;
-  const size_t total = ((cur_b + cw_b + q_b + idx_b + k) + 255) & ~(size_t)255;
-  char* mem = nullptr;
-  if (grand::scratch_alloc((void**)&mem, total, st) != cudaSuccess) return GRAND_E_NOMEM;
-  grand::FrameRec* ccur = reinterpret_cast<grand::FrameRec*>(mem);
-  uint32_t* ccw = reinterpret_cast<uint32_t*>(mem + cur_b);
-  uint32_t* cq = reinterpret_cast<uint32_t*>(mem + cur_b + cw_b);
-  int32_t* cidx = reinterpret_cast<int32_t*>(mem + cur_b + cw_b + q_b);
-  uint8_t* cab = reinterpret_cast<uint8_t*>(mem + cur_b + cw_b + q_b + idx_b);
+  const ResultBlock& rb = s->blocks[block];
+  const size_t cw_b = sizeof(uint32_t) * kResultWords * k, q_b = sizeof(uint32_t) * k, idx_b = sizeof(int32_t) * k;
+  grand::FrameRec* ccur = rb.d_cur;
+  uint32_t* ccw = rb.d_cw;
+  uint32_t* cq = rb.d_q;
+  int32_t* cidx = rb.d_idx;
+  uint8_t* cab = rb.d_ab;
   for (int i = 0; i < k; ++i) buf.h_idx[i] = susp[i];
   if (cudaMemcpyAsync(cidx, buf.h_idx, idx_b, cudaMemcpyHostToDevice, st) != cudaSuccess) return GRAND_E_CUDA;
   k_gather_long<<<(k * 32 + 127) / 128, 128, 0, st>>>(cidx, k, buf.d_cur, buf.d_cw, buf.d_q, buf.d_ab, ccur, ccw, cq,
@@ -303,12 +314,10 @@ int launch_job(grand_server* s, const Batch& b, const std::vector<int32_t>& susp
   int rc = grand::resume_resident(s->d_table, (int)s->codes.size(), s->Wmax, &s->cfg.params, ccur, k, 0, ccw,
                                   kResultWords, cq, cab, cs);
   if (rc != GRAND_OK) return rc;
-  const ResultBlock& rb = s->blocks[block];
   if (cudaMemcpyAsync(rb.h_cw, ccw, cw_b, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
       cudaMemcpyAsync(rb.h_q, cq, q_b, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
       cudaMemcpyAsync(rb.h_ab, cab, k, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
     return GRAND_E_CUDA;
-  cudaFreeAsync(mem, cs);
   return cudaEventRecord(ev, cs) == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
@@ -510,7 +519,7 @@ void harvester_main(grand_server* s) {
         const int cstream = s->next_cstream;
         s->next_cstream = (s->next_cstream + 1) % (int)s->cstreams.size();
         int block = -1;
-        {
+        if ((int)susp.size() <= kBlockFrames) {
           std::unique_lock<std::mutex> lk(s->mu);
           for (int i = 0; i < (int)s->blocks.size(); ++i)
             if (!s->blocks[i].busy) {
@@ -673,10 +682,16 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
   s->sets.resize(s->step > 0 ? 4 * cfg->n_streams : cfg->n_streams);
   if (s->step > 0) {
     s->blocks.resize(4 * cfg->n_streams);
+    const size_t bf = kBlockFrames;
     for (ResultBlock& r : s->blocks)
-      if (cudaMallocHost((void**)&r.h_cw, sizeof(uint32_t) * mb * kResultWords) != cudaSuccess ||
-          cudaMallocHost((void**)&r.h_q, sizeof(uint32_t) * mb) != cudaSuccess ||
-          cudaMallocHost((void**)&r.h_ab, mb) != cudaSuccess) {
+      if (cudaMalloc((void**)&r.d_cur, sizeof(grand::FrameRec) * bf) != cudaSuccess ||
+          cudaMalloc((void**)&r.d_cw, sizeof(uint32_t) * bf * kResultWords) != cudaSuccess ||
+          cudaMalloc((void**)&r.d_q, sizeof(uint32_t) * bf) != cudaSuccess ||
+          cudaMalloc((void**)&r.d_ab, bf) != cudaSuccess ||
+          cudaMalloc((void**)&r.d_idx, sizeof(int32_t) * bf) != cudaSuccess ||
+          cudaMallocHost((void**)&r.h_cw, sizeof(uint32_t) * bf * kResultWords) != cudaSuccess ||
+          cudaMallocHost((void**)&r.h_q, sizeof(uint32_t) * bf) != cudaSuccess ||
+          cudaMallocHost((void**)&r.h_ab, bf) != cudaSuccess) {
         free_server(s);
         return GRAND_E_NOMEM;
       }
