@@ -93,12 +93,12 @@ ALU_PEAK_TOPS = SMS * ALU_LANES * MAX_CLOCK_GHZ / 1000.0
 # SMs x 64 lanes / TEP checks the kernel evaluated in that launch: what one
 # evaluated check costs the ALU pipe, everything in the kernel included.
 NCU_SEARCH = {
-    "k_search_warp<5>": {"sha": "85688c959b892ed8", "profile": "profiles/k_search_warp_c2_small.md",
-                         "alu_lane_ops_per_check": 0.76, "alu_pipe_active": 0.735,
-                         "dram_bytes_per_hard_frame": 1554432 / 9596},
-    "k_search_warp<6>": {"sha": "85688c959b892ed8", "profile": "profiles/k_search_warp6_c3a_small.md",
-                         "alu_lane_ops_per_check": 0.65, "alu_pipe_active": 0.765,
-                         "dram_bytes_per_hard_frame": 164.0},
+    "k_search_warp<5>": {"sha": "b1d00947d52a7877", "profile": "profiles/k_search_warp_c2_small.md",
+                         "alu_lane_ops_per_check": 0.779, "alu_pipe_active": 0.737,
+                         "dram_bytes_per_hard_frame": 1551872 / 9596},
+    "k_search_warp<6>": {"sha": "b1d00947d52a7877", "profile": "profiles/k_search_warp6_c3a_small.md",
+                         "alu_lane_ops_per_check": 0.650, "alu_pipe_active": 0.753,
+                         "dram_bytes_per_hard_frame": 772864 / 4706},
     # the bit-level kernel reads every frame (no hand-off records): bytes per frame
     "k_ab_split<1,16>": {"sha": "23898721c5d0be10", "profile": "profiles/k_ab_split_c1_n32_bpsk.md",
                          "alu_lane_ops_per_check": 171.0, "alu_pipe_active": 0.360,
