@@ -100,9 +100,9 @@ NCU_SEARCH = {
                          "alu_lane_ops_per_check": 0.650, "alu_pipe_active": 0.753,
                          "dram_bytes_per_hard_frame": 772864 / 4706},
     # the bit-level kernel reads every frame (no hand-off records): bytes per frame
-    "k_ab_split<1,16>": {"sha": "23898721c5d0be10", "profile": "profiles/k_ab_split_c1_n32_bpsk.md",
-                         "alu_lane_ops_per_check": 171.0, "alu_pipe_active": 0.360,
-                         "dram_bytes_per_frame": 1308672 / 10000},
+    "k_ab_split<1,16>": {"sha": "b1d00947d52a7877", "profile": "profiles/k_ab_split_c1_n32_bpsk.md",
+                         "alu_lane_ops_per_check": 166.0, "alu_pipe_active": 0.360,
+                         "dram_bytes_per_frame": 1308160 / 10000},
 }
 
 
