@@ -87,20 +87,28 @@ CONFIG_IDS = {"c1": 1, "c2": 2, "c3a": 3, "c3b": 4, "c4": 5, "c5": 6, "c5adv": 8
 # x 2.07 GHz maximum SM clock.
 SMS, ALU_LANES, MAX_CLOCK_GHZ = 152, 64, 2.07
 ALU_PEAK_TOPS = SMS * ALU_LANES * MAX_CLOCK_GHZ / 1000.0
+# Shared-memory roofline: one 128-byte wavefront per clock per SM (32 banks x
+# 4 B; ncu's l1tex data-pipe peak), 152 SMs x 2.07 GHz.
+SMEM_PEAK_GBS = SMS * 128 * MAX_CLOCK_GHZ
 # Counters of each search kernel from one ncu capture of a small case (the
 # profiles/ file named), taken on the decode.cu source with the given sha256
-# prefix. alu_lane_ops_per_check = ALU pipe busy fraction x elapsed cycles x
-# SMs x 64 lanes / TEP checks the kernel evaluated in that launch: what one
-# evaluated check costs the ALU pipe, everything in the kernel included.
+# prefix. Per TEP check the kernel evaluated in that launch:
+#   smem_bytes_per_check = shared-memory wavefronts x 128 B / checks (the
+#     nibble-table search reads four table words per 32 TEPs per lane: it is
+#     bound by shared-memory bandwidth);
+#   alu_lane_ops_per_check = ALU pipe busy fraction x elapsed cycles x SMs x
+#     64 lanes / checks (the bit-plane search is bound by the integer pipe).
+# Everything in the kernel is included in both.
 NCU_SEARCH = {
-    "k_search_warp<5>": {"sha": "b1d00947d52a7877", "profile": "profiles/k_search_warp_c2_small.md",
-                         "alu_lane_ops_per_check": 0.779, "alu_pipe_active": 0.737,
-                         "dram_bytes_per_hard_frame": 1551872 / 9596},
-    "k_search_warp<6>": {"sha": "b1d00947d52a7877", "profile": "profiles/k_search_warp6_c3a_small.md",
+    "k_search_warp<5>": {"sha": "31af198c6f0e2acf", "profile": "profiles/k_search_warp_c2_small.md", "bound": "smem",
+                         "smem_bytes_per_check": 0.5763, "smem_wavefronts_frac": 0.838, "lsu_pipe_active": 0.910,
+                         "alu_lane_ops_per_check": 0.151, "alu_pipe_active": 0.439,
+                         "dram_bytes_per_hard_frame": 1872640 / 11181},
+    "k_search_warp<6>": {"sha": "b1d00947d52a7877", "profile": "profiles/k_search_warp6_c3a_small.md", "bound": "alu",
                          "alu_lane_ops_per_check": 0.650, "alu_pipe_active": 0.753,
                          "dram_bytes_per_hard_frame": 772864 / 4706},
     # the bit-level kernel reads every frame (no hand-off records): bytes per frame
-    "k_ab_split<1,16>": {"sha": "b1d00947d52a7877", "profile": "profiles/k_ab_split_c1_n32_bpsk.md",
+    "k_ab_split<1,16>": {"sha": "b1d00947d52a7877", "profile": "profiles/k_ab_split_c1_n32_bpsk.md", "bound": "alu",
                          "alu_lane_ops_per_check": 166.0, "alu_pipe_active": 0.360,
                          "dram_bytes_per_frame": 1308160 / 10000},
 }
@@ -121,43 +129,63 @@ def search_kernel(cfg):
 
 
 def search_roofline(cfg, evaluated, useful, hard, kernel_ms, alg_words, frames=0):
-    """Roofline of the TEP search kernel against the integer-ALU peak.
+    """Roofline of the TEP search kernel against the peak of the unit that
+    bounds it: shared-memory bandwidth for the nibble-table search (S' <= 10),
+    the integer ALU for the bit-plane searches (S' = 11, 12; GRAND-AB).
 
-    frac = ALU lane-ops executed per second / peak lane-ops per second, with
-    the lane-ops = TEP checks the kernel evaluated in this run (counted on the
-    device) x the ALU lane-ops one evaluated check costs (ncu, same kernel).
-    It stays below 1 by construction. The survey's model (N-K)/32 three-input
-    ops per useful check is kept beside it as model_ops: it can exceed the
-    peak, because the bit-sliced compare tests 32 TEPs per logic op on a 16-bit
-    projection and confirms only matches on the full syndrome."""
+    frac = the kernel's use of that unit per second / its peak, with the use =
+    TEP checks the kernel evaluated in this run (counted on the device) x what
+    one evaluated check costs the unit (ncu, same kernel: shared-memory bytes
+    or ALU lane-ops). It stays below 1 by construction. The survey's model
+    (N-K)/32 three-input ops per useful check is kept beside it as model_ops:
+    it can exceed the ALU peak, because the split compare tests 32 TEPs per
+    table word or logic op on a projection and confirms only matches on the
+    full syndrome."""
     kern = search_kernel(cfg)
     prof = NCU_SEARCH.get(kern)
     t_s = kernel_ms / 1e3
-    rec = {"bound": "alu", "peak": ALU_PEAK_TOPS, "unit": "Tops/s", "kernel": kern, "kernel_ms": kernel_ms,
-           "evaluated_checks": evaluated, "useful_checks": useful,
-           "peak_source": f"derived: {SMS} SMs x {ALU_LANES} ALU lanes/clk x {MAX_CLOCK_GHZ} GHz (a LOP3 "
-                          "microbenchmark on this GPU measured 64 per clock per SM)"}
+    alu_src = (f"derived: {SMS} SMs x {ALU_LANES} ALU lanes/clk x {MAX_CLOCK_GHZ} GHz (a LOP3 microbenchmark on "
+               "this GPU measured 64 per clock per SM)")
+    smem_src = f"derived: {SMS} SMs x 128 B/clk (one shared-memory wavefront) x {MAX_CLOCK_GHZ} GHz"
+    bound = prof.get("bound", "alu") if prof else "alu"
+    rec = {"bound": bound, "kernel": kern, "kernel_ms": kernel_ms, "evaluated_checks": evaluated,
+           "useful_checks": useful}
+    if bound == "smem":
+        rec.update({"peak": SMEM_PEAK_GBS, "unit": "GB/s", "peak_source": smem_src})
+    else:
+        rec.update({"peak": ALU_PEAK_TOPS, "unit": "Tops/s", "peak_source": alu_src})
     if prof is not None:
-        ops = evaluated * prof["alu_lane_ops_per_check"]
-        ach = ops / t_s / 1e12
         same = decode_source_sha() == prof["sha"]
         if "dram_bytes_per_frame" in prof:
             traffic = prof["dram_bytes_per_frame"] * frames if same and frames else None
         else:
             traffic = prof["dram_bytes_per_hard_frame"] * hard if same and hard else None
-        rec.update({"achieved": ach, "frac": ach / ALU_PEAK_TOPS, "traffic": traffic,
-                    "alu_lane_ops_per_evaluated_check": prof["alu_lane_ops_per_check"],
-                    "derivation": "evaluated checks of this run x ALU lane-ops per evaluated check (ncu) / "
-                                  "event-timed kernel time / ALU peak",
-                    "profile": prof["profile"], "profile_source_sha": prof["sha"], "profile_matches_source": same,
-                    "ncu_alu_pipe_active": prof["alu_pipe_active"]})
+        alu_ach = evaluated * prof["alu_lane_ops_per_check"] / t_s / 1e12
+        if bound == "smem":
+            ach = evaluated * prof["smem_bytes_per_check"] / t_s / 1e9
+            rec.update({"achieved": ach, "frac": ach / SMEM_PEAK_GBS,
+                        "smem_bytes_per_evaluated_check": prof["smem_bytes_per_check"],
+                        "derivation": "evaluated checks of this run x shared-memory bytes per evaluated check "
+                                      "(ncu wavefronts x 128 B) / event-timed kernel time / shared-memory peak",
+                        "ncu_smem_wavefronts_frac": prof["smem_wavefronts_frac"],
+                        "ncu_lsu_pipe_active": prof["lsu_pipe_active"],
+                        "alu": {"achieved": alu_ach, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                                "frac": alu_ach / ALU_PEAK_TOPS,
+                                "alu_lane_ops_per_evaluated_check": prof["alu_lane_ops_per_check"]}})
+        else:
+            rec.update({"achieved": alu_ach, "frac": alu_ach / ALU_PEAK_TOPS,
+                        "alu_lane_ops_per_evaluated_check": prof["alu_lane_ops_per_check"],
+                        "derivation": "evaluated checks of this run x ALU lane-ops per evaluated check (ncu) / "
+                                      "event-timed kernel time / ALU peak"})
+        rec.update({"traffic": traffic, "profile": prof["profile"], "profile_source_sha": prof["sha"],
+                    "profile_matches_source": same, "ncu_alu_pipe_active": prof["alu_pipe_active"]})
     else:
         rec.update({"achieved": None, "frac": None, "traffic": None})
     if alg_words is not None:
         m = useful * alg_words / t_s / 1e12
         rec["model_ops"] = {"ops_per_useful_check": alg_words, "achieved": m, "frac": m / ALU_PEAK_TOPS,
-                            "note": "(N-K)/32 three-input ops per useful check; can exceed 1 (the split compare "
-                                    "tests 32 TEPs per op on a projection)"}
+                            "note": "(N-K)/32 three-input ops per useful check against the ALU peak; can exceed 1 "
+                                    "(the split compare tests 32 TEPs per table word or logic op on a projection)"}
     return rec
 
 

@@ -27,6 +27,7 @@
 #include <stdio.h>
 
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "device_common.cuh"
@@ -140,7 +141,10 @@ __device__ __noinline__ bool resume_entry_ok(const SearchArgs& a, unsigned fi) {
     bool mine = true;
     if (lane < sp) {
       const uint16_t p0 = rec->pos[lane][0], p1 = rec->pos[lane][1];
-      mine = (p0 == kNoPos || p0 < c.N) && (p1 == kNoPos || p1 < c.N) && (rec->ex[lane] & ~7u) == 0;
+      // the diagonal alternative exists exactly when both single-axis ones do
+      const uint32_t e = rec->ex[lane];
+      mine = (p0 == kNoPos || p0 < c.N) && (p1 == kNoPos || p1 < c.N) && (e & ~7u) == 0 &&
+             ((e >> 2) & 1u) == (e & (e >> 1) & 1u);
     }
     ok = __all_sync(kFull, mine);
   }
@@ -1008,11 +1012,23 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_search(SearchArgs a) {
 // z's: kPlanes 3-input logic ops test 32 TEPs (0.66 integer ops per TEP with
 // the candidate fold). Candidates (false rate 2^-kPlanes) are verified on every
 // syndrome word.
+//
+// With 5-rank sides (S' <= 10) the masks are folded into the tables instead:
+// every A group keeps, per nibble k of the projection (planes 4k..4k+3), the
+// 16 words T[k][v] = OR_{j<4} (plane_{4k+j} XOR (bit j of v ? ~0 : 0)), so a
+// lane with B projection z gets the same acc from one table word per nibble,
+//     acc = T[0][z & 15] | T[1][(z >> 4) & 15] | T[2][...] | T[3][...],
+// four shared-memory reads and two logic ops for 32 TEPs x 16 bits. The 16
+// words of a nibble sit in 16 distinct banks, so any pattern of lane reads is
+// conflict-free; the kernel is then bound by shared-memory bandwidth (0.5 B
+// per TEP) instead of the integer pipe.
 // ---------------------------------------------------------------------------
 constexpr int kWarpSideMax = 5;                      // the small-table variant (S' <= 10)
 constexpr int kPlanes = 20;                          // projection bits compared per TEP
 constexpr int kGroupUnroll = 8;                      // groups per candidate check
 constexpr int kPlanesL1 = 16;                        // first-level planes (the rest only on a match)
+constexpr int kLutSets = kPlanes / 4;                // nibble tables per group (5-rank sides)
+constexpr int kLutStride = kLutSets * 16 + 1;        // words per group (odd: conflict-free per-lane stores)
 
 // Table sizes of one side for the kSide variant.
 template <int kSide>
@@ -1042,11 +1058,17 @@ struct WarpSlice {
   uint16_t* pos;     // [kRanks][2]
 };
 
+// words of the bit-planes of one warp's A side
+template <int kSide>
+__host__ __device__ constexpr int warp_table_words() {
+  return WarpDims<kSide>::kGroups * kPlanes;
+}
+
 template <int kSide, bool kWithPlanes = true>
 __host__ __device__ inline size_t warp_slice_bytes(int Wmax) {
   using D = WarpDims<kSide>;
   const size_t bz = kSide == kWarpSideMax ? D::kTab : 0;
-  size_t words = (kWithPlanes ? (size_t)D::kGroups * kPlanes : 0) + bz + 3 * D::kRanks * (size_t)Wmax + 3 * D::kRanks +
+  size_t words = (kWithPlanes ? (size_t)warp_table_words<kSide>() : 0) + bz + 3 * D::kRanks * (size_t)Wmax + 3 * D::kRanks +
                  kEStride * kEStride + Wmax + 2 * (D::kSub + 1) + 8 + 8 + D::kSub + 4 + D::kRanks;
   return (words * 4 + 15) & ~(size_t)15;
 }
@@ -1057,7 +1079,7 @@ __device__ inline WarpSlice warp_slice(char* base, int Wmax) {
   WarpSlice w;
   uint32_t* p = reinterpret_cast<uint32_t*>(base);
   w.planes = kWithPlanes ? p : nullptr;
-  p += kWithPlanes ? D::kGroups * kPlanes : 0;
+  p += kWithPlanes ? warp_table_words<kSide>() : 0;
   w.Bz = p; p += kSide == kWarpSideMax ? D::kTab : 0;
   w.delta = p; p += 3 * D::kRanks * Wmax;
   w.dflt = p; p += 3 * D::kRanks;
@@ -1079,26 +1101,31 @@ __device__ inline WarpSlice warp_slice(char* base, int Wmax) {
 // Layout of one side's table, computed by one warp. Subsets of the side's n
 // ranks are laid out by (size, colex order), i.e. by TEP weight; the k-th
 // subset's entries start at start[k]; cum[v] = entries of weight <= v.
-// Returns the number of entries.
+// Returns the number of entries. The subset order (ord, inv) depends on n
+// only: ord_ready says it is already in place from an earlier frame.
 __device__ inline unsigned warp_side_layout(const WarpSlice& sl, int r0, int n, uint32_t* start, uint8_t* ord,
-                                            uint8_t* inv, uint32_t* cum) {
+                                            uint8_t* inv, uint32_t* cum, bool ord_ready = false) {
   const int lane = threadIdx.x & 31;
   const int nsub = 1 << n;  // <= 64: two subsets per lane
-  for (int sb = lane; sb < nsub; sb += 32) {
-    int w = 0, colex = 0;
-    for (int j = 0; j < n; ++j)
-      if ((sb >> j) & 1) {
-        ++w;
-        colex += (int)binom16(j, w);
-      }
-    int before = 0;
-    for (int v = 0; v < w; ++v) before += (int)binom16(n, v);
-    const int posk = before + colex;
-    ord[posk] = (uint8_t)sb;
-    inv[sb] = (uint8_t)posk;
+  if (!ord_ready) {
+    for (int sb = lane; sb < nsub; sb += 32) {
+      int w = 0, colex = 0;
+      for (int j = 0; j < n; ++j)
+        if ((sb >> j) & 1) {
+          ++w;
+          colex += (int)binom16(j, w);
+        }
+      int before = 0;
+      for (int v = 0; v < w; ++v) before += (int)binom16(n, v);
+      const int posk = before + colex;
+      ord[posk] = (uint8_t)sb;
+      inv[sb] = (uint8_t)posk;
+    }
+    __syncwarp();
   }
-  __syncwarp();
   // entries of the subset at table position k, then an exclusive scan
+  uint32_t kk = 0;  // 2 bits per rank of the side: its number of alternatives (1 or 3; 0 = none)
+  for (int j = 0; j < n; ++j) kk |= (uint32_t)__popc(sl.ex[r0 + j] & 7u) << (2 * j);
   unsigned carry = 0;
   for (int k0 = 0; k0 < nsub; k0 += 32) {
     const int k = k0 + lane;
@@ -1107,7 +1134,7 @@ __device__ inline unsigned warp_side_layout(const WarpSlice& sl, int r0, int n, 
       const int sb = ord[k];
       size_k = 1;
       for (int j = 0; j < n; ++j)
-        if ((sb >> j) & 1) size_k *= (unsigned)__popc(sl.ex[r0 + j] & 7u);
+        if ((sb >> j) & 1) size_k *= (kk >> (2 * j)) & 3u;
     }
     unsigned incl = size_k;
     for (int o = 1; o < 32; o <<= 1) {
@@ -1120,10 +1147,14 @@ __device__ inline unsigned warp_side_layout(const WarpSlice& sl, int r0, int n, 
   const unsigned total = carry;
   if (lane == 0) start[nsub] = total;
   __syncwarp();
-  // cumulative count per weight: subsets of weight <= v end at position sum_{u<=v} C(n,u)
+  // cumulative count per weight: subsets of weight <= v end at position
+  // sum_{u<=v} C(n,u) (C(n,u+1) = C(n,u) (n-u) / (u+1))
   if (lane <= n) {
-    int endk = 0;
-    for (int u = 0; u <= lane; ++u) endk += (int)binom16(n, u);
+    int endk = 0, c = 1;
+    for (int u = 0; u <= lane; ++u) {
+      endk += c;
+      c = c * (n - u) / (u + 1);
+    }
     cum[lane] = start[endk];
   }
   for (int v = n + 1 + lane; v < 8; v += 32) cum[v] = total;
@@ -1274,13 +1305,90 @@ __device__ __forceinline__ uint32_t group_acc_part(const uint32_t* planes, int g
   return acc;
 }
 
-// The search of one frame from its hand-off record (one warp; `rec` may live in
-// global or shared memory). Lane 0 accumulates the evaluated and useful checks.
+// The compare of one lane's B entry against A groups: 6-rank sides XOR the
+// group's bit-planes with the entry's bit masks; 5-rank sides read the
+// group's nibble tables at the entry's nibbles. first(g): OR over planes
+// 0..15 (zero bits: entries equal on those bits); second(g): planes 16..19.
+// block(g0) fixes the first group of a block of kGroupUnroll groups;
+// first<U>() / second<U>() then address group g0 + U (U a compile-time
+// constant, so the table reads of a block take immediate offsets);
+// first_at / second_at address any group (the candidate path).
+struct PlaneCmp {
+  const uint32_t* planes;
+  uint32_t m[kPlanes];
+  int g0;
+  __device__ __forceinline__ void load(const uint32_t* tab, uint32_t z) {
+    planes = tab;
+#pragma unroll
+    for (int b = 0; b < kPlanes; ++b) m[b] = 0u - ((z >> b) & 1u);
+  }
+  __device__ __forceinline__ void block(int g) { g0 = g; }
+  template <int U>
+  __device__ __forceinline__ uint32_t first() const { return first_at(g0 + U); }
+  template <int U>
+  __device__ __forceinline__ uint32_t second() const { return second_at(g0 + U); }
+  __device__ __forceinline__ uint32_t first_at(int g) const { return group_acc_part<0, kPlanesL1>(planes, g, m); }
+  __device__ __forceinline__ uint32_t second_at(int g) const {
+    return group_acc_part<kPlanesL1, kPlanes>(planes, g, m);
+  }
+};
+
+// 32-bit shared-memory read at a shared-window address plus an immediate.
+template <int kOff>
+__device__ __forceinline__ uint32_t lds_imm(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(kOff) : "memory");
+  return v;
+}
+
+struct LutCmp {
+  uint32_t t[kLutSets];  // shared-window address of the word of nibble k of z in group 0
+  uint32_t b[kLutSets];  // the same in group g0 of the current block
+  __device__ __forceinline__ void load(const uint32_t* tab, uint32_t z) {
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(tab);
+#pragma unroll
+    for (int k = 0; k < kLutSets; ++k) t[k] = base + 4u * (16u * k + ((z >> (4 * k)) & 15u));
+  }
+  __device__ __forceinline__ void block(int g) {
+#pragma unroll
+    for (int k = 0; k < kLutSets; ++k) b[k] = t[k] + 4u * kLutStride * (uint32_t)g;
+  }
+  template <int U>
+  __device__ __forceinline__ uint32_t first() const {
+    constexpr int o = 4 * kLutStride * U;
+    return lds_imm<o>(b[0]) | lds_imm<o>(b[1]) | lds_imm<o>(b[2]) | lds_imm<o>(b[3]);
+  }
+  template <int U>
+  __device__ __forceinline__ uint32_t second() const {
+    return lds_imm<4 * kLutStride * U>(b[4]);
+  }
+  __device__ __forceinline__ uint32_t first_at(int g) const {
+    const uint32_t o = 4u * kLutStride * (uint32_t)g;
+    return lds_imm<0>(t[0] + o) | lds_imm<0>(t[1] + o) | lds_imm<0>(t[2] + o) | lds_imm<0>(t[3] + o);
+  }
+  __device__ __forceinline__ uint32_t second_at(int g) const {
+    return lds_imm<0>(t[4] + 4u * kLutStride * (uint32_t)g);
+  }
+};
+
+// f(std::integral_constant<int, U>) for U = I .. N-1, unrolled at compile time.
+template <int I, int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+// The search of one frame from its hand-off record with sides of 6 ranks
+// (S' = 11, 12; one warp; `rec` may live in global or shared memory). Lane 0
+// accumulates the evaluated and useful checks. lay_key: the side sizes whose
+// subset order the slice already holds.
 template <int kSide, bool kResume>
 __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, const FrameRec* rec,
                                              const WarpSlice& sl, unsigned long long& my_eval,
-                                             unsigned long long& my_useful) {
-  using D = WarpDims<kSide>;
+                                             unsigned long long& my_useful, uint32_t& lay_key) {
+  static_assert(kSide != kWarpSideMax, "5-rank sides use search_frame5");
   const int lane = threadIdx.x & 31;
   {
     const int Sp = rec->sp;
@@ -1295,34 +1403,35 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
     if (lane < W) sl.s0[lane] = rec->s0[lane];
     const uint32_t f0 = rec->f0;
     __syncwarp();
-    for (int t = lane; t < Sp * 3 * W; t += 32) {
-      const int r = t / (3 * W), rem = t % (3 * W), alt = rem / W, w = rem % W;
-      const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
-      const uint32_t h = (alt != 1 && pI != kNoPos) ? __ldg(code.hcol + (size_t)pI * W + w) : 0u;
-      const uint32_t v = (alt != 0 && pQ != kNoPos) ? __ldg(code.hcol + (size_t)pQ * W + w) : 0u;
-      sl.delta[t] = h ^ v;
-    }
+    // deltas of rank r's alternatives (h, v, diag) on every syndrome word and
+    // their projections: lane t = 3 r + alt
     for (int t = lane; t < 3 * Sp; t += 32) {
-      const int r = t / 3, alt = t % 3;
+      const int r = t / 3, alt = t - 3 * (t / 3);
       const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
-      const uint32_t h = (alt != 1 && pI != kNoPos) ? __ldg(code.hf + pI) : 0u;
-      const uint32_t v = (alt != 0 && pQ != kNoPos) ? __ldg(code.hf + pQ) : 0u;
-      sl.dflt[t] = h ^ v;
+      const bool useI = alt != 1 && pI != kNoPos, useQ = alt != 0 && pQ != kNoPos;
+      sl.dflt[t] = (useI ? __ldg(code.hf + pI) : 0u) ^ (useQ ? __ldg(code.hf + pQ) : 0u);
+      for (int w = 0; w < W; ++w)
+        sl.delta[t * W + w] = (useI ? __ldg(code.hcol + (size_t)pI * W + w) : 0u) ^
+                              (useQ ? __ldg(code.hcol + (size_t)pQ * W + w) : 0u);
     }
     esp_table_warp(sl.ex, Sp, sl.E);
     __syncwarp();
-    const uint32_t total = esp_total(sl.E, Sp);
-    int w_cap = Sp;
-    {
-      uint64_t acc = 0;
-      for (int v = 0; v <= Sp; ++v) {
-        acc += sl.E[Sp * kEStride + v];
-        if (acc >= (uint64_t)a.cap) { w_cap = v; break; }
-      }
+    // valid TEPs of weight <= v (lane v, a warp scan); the cap's weight class
+    uint32_t cnt = lane <= Sp ? sl.E[Sp * kEStride + lane] : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, cnt, o);
+      if (lane >= o) cnt += t;
     }
+    const uint32_t total = __shfl_sync(kFull, cnt, Sp);
+    const unsigned over = __ballot_sync(kFull, lane <= Sp && (uint64_t)cnt >= (uint64_t)a.cap);
+    const int w_cap = over ? __ffs(over) - 1 : Sp;
     const int nAr = Sp >> 1, nBr = Sp - nAr;
-    const unsigned nA = warp_side_layout(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, sl.cumA);
-    const unsigned nB = warp_side_layout(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, sl.cumB);
+    // the subset orders of the previous frame's sides are still in place when
+    // the side sizes are the same
+    const unsigned nA = warp_side_layout(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, sl.cumA, (lay_key & 0xFu) == (unsigned)nAr);
+    const unsigned nB =
+        warp_side_layout(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, sl.cumB, (lay_key >> 4) == (unsigned)nBr);
+    lay_key = (uint32_t)nAr | ((uint32_t)nBr << 4);
     const int nG = (int)((nA + 31) / 32);
     // weight window of this call: w_done + 1 .. w_hi (all weights without a
     // step); no TEP heavier than the cap's class matters
@@ -1331,31 +1440,12 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
     // A groups a window can reach (entries of weight <= w_lim): the planes of
     // later groups are never read, so a windowed search does not build them
     const int nG_use = kResume ? (int)((sl.cumA[min(w_lim, nAr)] + 31) / 32) : nG;
-    // the bit-plane pattern of a padding entry (never a candidate in practice;
-    // candidates beyond nA are skipped at verification)
-    const uint32_t pad_plane = (kPadA >> (lane < kPlanes ? lane : 0)) & 1u ? 0xFFFFFFFFu : 0u;
-    if constexpr (kSide == kWarpSideMax) {
-      // A side: scalar projections into the B buffer (doubling), then
-      // bit-planes (one group of 32 entries per warp transpose)
-      warp_fill_side(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, f0, sl.Bz);
-      const int g_build = kResume ? min(D::kGroups, (nG_use + kGroupUnroll - 1) / kGroupUnroll * kGroupUnroll)
-                                  : D::kGroups;
-      for (int g = 0; g < g_build; ++g) {
-        if (g < nG) {
-          const unsigned e = 32u * g + lane;
-          const uint32_t q = e < nA ? sl.Bz[e] : kPadA;
-          const uint32_t mine = warp_transpose32(q);  // lane b: bit-plane b of the group
-          if (lane < kPlanes) sl.planes[g * kPlanes + lane] = mine;
-        } else if (lane < kPlanes) {
-          sl.planes[g * kPlanes + lane] = pad_plane;
-        }
-      }
-      __syncwarp();
-      // B side, scalar projections
-      warp_fill_side(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, 0u, sl.Bz);
-    } else {
-      // large sides: no scalar tables; each lane derives its A entry from the
-      // table layout, one group of 32 per warp transpose
+    // no scalar tables: each lane derives its A entry from the table layout,
+    // one group of 32 per warp transpose. The bit-plane pattern of a padding
+    // entry is never a candidate in practice (candidates beyond nA are skipped
+    // at verification).
+    {
+      const uint32_t pad_plane = (kPadA >> (lane < kPlanes ? lane : 0)) & 1u ? 0xFFFFFFFFu : 0u;
       const int nG8 = (nG_use + kGroupUnroll - 1) / kGroupUnroll * kGroupUnroll;
       for (int g = 0; g < nG8; ++g) {
         const unsigned e = 32u * g + lane;
@@ -1371,22 +1461,15 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
     uint32_t best_rank = 0xFFFFFFFFu, best_code = 0;
     int best_w = 127;
     const int nCh = (int)((nB + 31) / 32);
-
     for (int ch = 0; ch < nCh; ++ch) {
       const int wb = side_entry_weight(sl.cumB, nBr, 32u * ch);
       const int budget = min(best_w, w_lim) - wb;  // heaviest A weight still worth testing
       if (budget < 0) break;
       const unsigned col = 32u * ch + lane;
-      uint32_t z = kPadB;
-      if constexpr (kSide == kWarpSideMax) {
-        if (col < nB) z = sl.Bz[col];
-      } else {
-        uint32_t bcode0;
-        if (col < nB) warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, z, bcode0);
-      }
-      uint32_t m[kPlanes];
-#pragma unroll
-      for (int b = 0; b < kPlanes; ++b) m[b] = 0u - ((z >> b) & 1u);
+      uint32_t z = kPadB, bcode0;
+      if (col < nB) warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, z, bcode0);
+      PlaneCmp cmp;
+      cmp.load(sl.planes, z);
       // groups holding an A entry of weight <= budget; skip what the
       // preparation already tested (every TEP of weight <= w_done)
       int g_end = (int)((sl.cumA[min(budget, nAr)] + 31) / 32);
@@ -1403,17 +1486,19 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
         // first level: kPlanesL1 projection bits of kGroupUnroll groups
         uint32_t acc[kGroupUnroll];
         uint32_t all = 0xFFFFFFFFu;
-#pragma unroll
-        for (int u = 0; u < kGroupUnroll; ++u) {
-          acc[u] = group_acc_part<0, kPlanesL1>(sl.planes, g0 + u, m);
+        cmp.block(g0);
+        static_for<0, kGroupUnroll>([&](auto uc) {
+          constexpr int u = decltype(uc)::value;
+          acc[u] = cmp.template first<u>();
           all &= acc[u];
-        }
+        });
         if (!__any_sync(kFull, all != 0xFFFFFFFFu)) continue;
         // a first-level match somewhere in the warp: the remaining planes
         uint32_t cand = 0;
-#pragma unroll
-        for (int u = 0; u < kGroupUnroll; ++u)
-          cand |= ~(acc[u] | group_acc_part<kPlanesL1, kPlanes>(sl.planes, g0 + u, m));
+        static_for<0, kGroupUnroll>([&](auto uc) {
+          constexpr int u = decltype(uc)::value;
+          cand |= ~(acc[u] | cmp.template second<u>());
+        });
         if (__any_sync(kFull, cand)) {
           // rare: locate candidates of this lane and verify every syndrome word
           uint32_t lr = 0xFFFFFFFFu, lc = 0;
@@ -1421,7 +1506,7 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
             uint32_t bcode, bq;
             warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, bq, bcode);
             for (int u = 0; u < kGroupUnroll; ++u) {
-              uint32_t c = ~group_acc(sl.planes, g0 + u, m);
+              uint32_t c = ~(cmp.first_at(g0 + u) | cmp.second_at(g0 + u));
               while (c) {
                 const int i = __ffs(c) - 1;
                 c &= c - 1;
@@ -1430,6 +1515,7 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
                 uint32_t aq, acode;
                 warp_side_entry(sl, 0, nAr, sl.startA, sl.ordA, f0, row, aq, acode);
                 const uint32_t cc = acode | (bcode << (2 * nAr));
+                if (kResume && code_weight(cc) > w_hi) continue;  // beyond this call's window
                 uint32_t orr = 0;
                 for (int w = 0; w < W; ++w) {
                   uint32_t zz = sl.s0[w];
@@ -1464,14 +1550,13 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
     // --- result -------------------------------------------------------------
     const bool hit = best_rank != 0xFFFFFFFFu && (uint64_t)best_rank <= (uint64_t)a.cap;
     if (kResume && !hit && w_hi < w_cap) {  // no codeword up to w_hi, weights left below the cap
-      uint32_t tested = 0, done = 0;
-      for (int v = 0; v <= w_hi; ++v) tested += sl.E[Sp * kEStride + v];
-      for (int v = 0; v <= w_done; ++v) done += sl.E[Sp * kEStride + v];
+      const uint32_t tested = __shfl_sync(kFull, cnt, w_hi), done = __shfl_sync(kFull, cnt, w_done);
       suspend_frame(a, fi, rec, w_hi, tested);
       if (lane == 0) my_useful += tested - done;
       __syncwarp();
       return;
     }
+    const uint32_t done = __shfl_sync(kFull, cnt, w_done);
     if (lane == 0) {
       const unsigned f = out_frame(a, fi, rec);
       uint32_t q_out;
@@ -1489,22 +1574,342 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
         a.abandon[f] = 1;
       }
       a.queries[f] = q_out;
-      uint32_t done = 0;
-      for (int v = 0; v <= w_done; ++v) done += sl.E[Sp * kEStride + v];
       my_useful += q_out - done;
     }
     __syncwarp();
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp search with sides of at most 5 ranks (S' <= 10): flip-bit tables.
+//
+// A TEP restricted to one side is a vector x of 2n flip bits: bit 2r selects
+// the I-slot alternative of the side's r-th rank, bit 2r+1 the Q-slot one, and
+// both together the diagonal one (which exists exactly when both single-axis
+// ones do). x is then also the TEP's code in the canonical 2-bits-per-rank
+// form, and its syndrome projection is linear in x:
+//     proj(x) = seed ^ XOR_{b in x} H_b.
+// A side's vectors are cut as x = 32 g + i: i (bits 0..4) within a group, g
+// (bits 5..9) the group. Within group g the projections are C_g ^ P_i, with
+// P_i = XOR_{b < 5, b in i} H_b the same for every group, so the bit-planes
+// of every group are those of P (one set of 20 warp ballots) with plane b
+// inverted where bit b of C_g is set, and the nibble tables of a group follow
+// from the planes and C_g without a per-group transpose or any table of
+// projections. Vectors naming an alternative that does not exist are masked:
+// existence is a per-bit property (within part and group part separately).
+// Groups of both sides are visited in order of their lightest TEP weight
+// (A groups as table rows, B groups two per chunk, one entry per lane each),
+// which keeps the weight cut-offs of the canonical order.
+// ---------------------------------------------------------------------------
+struct Slice5 {
+  uint32_t* lut;    // [32][kLutStride] nibble tables of the A groups in visiting order
+  uint32_t* delta;  // [10][3][Wmax] full syndrome deltas
+  uint32_t* dflt;   // [10][3] projections of the deltas
+  uint32_t* E;      // [kEStride^2]
+  uint32_t* s0;     // [Wmax]
+  uint8_t* ordA;    // [32] A group at visiting position t
+  uint8_t* ordB;    // [32] B group at visiting position s
+  uint8_t* ex;      // [16]
+  uint16_t* pos;    // [10][2]
+};
+
+__host__ __device__ inline size_t slice5_bytes(int Wmax) {
+  const size_t words = 32 * kLutStride + 30 * (size_t)Wmax + 30 + kEStride * kEStride + Wmax + 8 + 8 + 4 + 10;
+  return (words * 4 + 15) & ~(size_t)15;
+}
+
+__device__ inline Slice5 slice5(char* base, int Wmax) {
+  Slice5 w;
+  uint32_t* p = reinterpret_cast<uint32_t*>(base);
+  w.lut = p; p += 32 * kLutStride;
+  w.delta = p; p += 30 * Wmax;
+  w.dflt = p; p += 30;
+  w.E = p; p += kEStride * kEStride;
+  w.s0 = p; p += Wmax;
+  w.ordA = reinterpret_cast<uint8_t*>(p); p += 8;
+  w.ordB = reinterpret_cast<uint8_t*>(p); p += 8;
+  w.ex = reinterpret_cast<uint8_t*>(p); p += 4;
+  w.pos = reinterpret_cast<uint16_t*>(p);
+  return w;
+}
+
+// Lightest TEP weight of flip-bit group g (its group bits shifted into place).
+__device__ __forceinline__ int group_min_weight(uint32_t g) { return code_weight(g << 5); }
+
+// Visiting order of the valid groups of one side (group existence bits ehi):
+// by lightest weight, then by index. Writes ord[0..n) and returns n; lane w
+// (w <= 5) gets in *cum the number of groups of lightest weight <= w.
+__device__ __forceinline__ int order_groups(uint32_t ehi, uint8_t* ord, uint32_t* cum) {
+  const int lane = threadIdx.x & 31;
+  const bool valid = ((uint32_t)lane & ~ehi) == 0u;
+  const int mw = group_min_weight((uint32_t)lane);
+  int n = 0, my = 0;
+  uint32_t c = 0;
+  for (int w = 0; w <= 3; ++w) {
+    const unsigned m = __ballot_sync(kFull, valid && mw == w);
+    if (valid && mw == w) my = n + __popc(m & ((1u << lane) - 1u));
+    n += __popc(m);
+    if (lane == w) c = (uint32_t)n;
+  }
+  if (lane > 3) c = (uint32_t)n;
+  if (valid) ord[my] = (uint8_t)lane;
+  *cum = c;
+  __syncwarp();
+  return n;
+}
+
+// XOR of h[b] over the bits b of x (x < 32).
+__device__ __forceinline__ uint32_t xor_bits5(uint32_t x, const uint32_t (&h)[5]) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int b = 0; b < 5; ++b) r ^= ((x >> b) & 1u) ? h[b] : 0u;
+  return r;
+}
+
+template <bool kResume>
+__device__ __forceinline__ void search_frame5(const SearchArgs& a, unsigned fi, const FrameRec* rec, const Slice5& sl,
+                                              unsigned long long& my_eval, unsigned long long& my_useful) {
+  const int lane = threadIdx.x & 31;
+  const int Sp = rec->sp;
+  const int w_done = rec->w_done;
+  const CodeDev code = a.codes[rec->code];
+  const int W = code.W;
+  uint32_t my_ex = 0;
+  if (lane < Sp) {
+    my_ex = rec->ex[lane];
+    sl.ex[lane] = (uint8_t)my_ex;
+    sl.pos[2 * lane] = rec->pos[lane][0];
+    sl.pos[2 * lane + 1] = rec->pos[lane][1];
+  }
+  if (lane < W) sl.s0[lane] = rec->s0[lane];
+  const uint32_t f0 = rec->f0;
+  __syncwarp();
+  // deltas of rank r's alternatives (h, v, diag) on every syndrome word and
+  // their projections: lane t = 3 r + alt
+  for (int t = lane; t < 3 * Sp; t += 32) {
+    const int r = t / 3, alt = t - 3 * (t / 3);
+    const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
+    const bool useI = alt != 1 && pI != kNoPos, useQ = alt != 0 && pQ != kNoPos;
+    sl.dflt[t] = (useI ? __ldg(code.hf + pI) : 0u) ^ (useQ ? __ldg(code.hf + pQ) : 0u);
+    for (int w = 0; w < W; ++w)
+      sl.delta[t * W + w] = (useI ? __ldg(code.hcol + (size_t)pI * W + w) : 0u) ^
+                            (useQ ? __ldg(code.hcol + (size_t)pQ * W + w) : 0u);
+  }
+  esp_table_warp(sl.ex, Sp, sl.E);
+  __syncwarp();
+  // valid TEPs of weight <= v (lane v, a warp scan); the cap's weight class
+  uint32_t cnt = lane <= Sp ? sl.E[Sp * kEStride + lane] : 0u;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, cnt, o);
+    if (lane >= o) cnt += t;
+  }
+  const uint32_t total = __shfl_sync(kFull, cnt, Sp);
+  const unsigned over = __ballot_sync(kFull, lane <= Sp && (uint64_t)cnt >= (uint64_t)a.cap);
+  const int w_cap = over ? __ffs(over) - 1 : Sp;
+  const int w_hi = kResume && a.w_step > 0 ? min(Sp, w_done + a.w_step) : Sp;
+  const int w_lim = min(w_cap, w_hi);
+  const int nAr = Sp >> 1;
+  // existence bits of both sides' flip vectors (bit 2r: I slot, 2r+1: Q slot)
+  const unsigned exh = __ballot_sync(kFull, lane < Sp && (my_ex & 1u)), exv = __ballot_sync(kFull, lane < Sp && (my_ex & 2u));
+  uint32_t EA = 0, EB = 0;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    EA |= (((exh >> r) & 1u) << (2 * r)) | (((exv >> r) & 1u) << (2 * r + 1));
+    EB |= (((exh >> (nAr + r)) & 1u) << (2 * r)) | (((exv >> (nAr + r)) & 1u) << (2 * r + 1));
+  }
+  EA &= (1u << (2 * nAr)) - 1u;
+  EB &= (1u << (2 * (Sp - nAr))) - 1u;
+  // flip projections H_b of both sides (b = 2r + slot)
+  uint32_t HAlo[5], HAhi[5], HBlo[5], HBhi[5];
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    HAlo[b] = ((EA >> b) & 1u) ? sl.dflt[(b >> 1) * 3 + (b & 1)] : 0u;
+    HAhi[b] = ((EA >> (b + 5)) & 1u) ? sl.dflt[((b + 5) >> 1) * 3 + ((b + 5) & 1)] : 0u;
+    HBlo[b] = ((EB >> b) & 1u) ? sl.dflt[(nAr + (b >> 1)) * 3 + (b & 1)] : 0u;
+    HBhi[b] = ((EB >> (b + 5)) & 1u) ? sl.dflt[(nAr + ((b + 5) >> 1)) * 3 + ((b + 5) & 1)] : 0u;
+  }
+  // visiting orders of the groups
+  uint32_t cumA_v, cumB_v;
+  const int nGA = order_groups(EA >> 5, sl.ordA, &cumA_v);
+  const int nGB = order_groups(EB >> 5, sl.ordB, &cumB_v);
+  (void)cumB_v;
+  const uint32_t WA = __ballot_sync(kFull, ((uint32_t)lane & ~EA & 31u) == 0u);  // valid within-group A bits
+  const uint32_t WB = __ballot_sync(kFull, ((uint32_t)lane & ~EB & 31u) == 0u);
+  const bool lane_b_ok = (WB >> lane) & 1u;
+  const int maxwA = code_weight(EA);
+  // bit-planes of the within-group A projections: plane b bit i = bit b of P_i
+  const uint32_t PA = xor_bits5((uint32_t)lane, HAlo);
+  uint32_t pl[kPlanes];
+#pragma unroll
+  for (int b = 0; b < kPlanes; ++b) pl[b] = __ballot_sync(kFull, (PA >> b) & 1u);
+  // table row t (lane t): A group g = ordA[t], planes inverted at the bits of
+  // C_g = f0 ^ XOR_{b in g} H_{5+b}; rows past the valid groups never match
+  {
+    const int t = lane;
+    uint32_t* row = sl.lut + t * kLutStride;
+    if (t < nGA) {
+      const uint32_t g = sl.ordA[t];
+      const uint32_t cg = f0 ^ xor_bits5(g, HAhi);
+      const uint32_t nwa = ~WA;
+#pragma unroll
+      for (int k = 0; k < kLutSets; ++k) {
+        const uint32_t q0 = pl[4 * k + 0] ^ (0u - ((cg >> (4 * k + 0)) & 1u));
+        const uint32_t q1 = pl[4 * k + 1] ^ (0u - ((cg >> (4 * k + 1)) & 1u));
+        const uint32_t q2 = pl[4 * k + 2] ^ (0u - ((cg >> (4 * k + 2)) & 1u));
+        const uint32_t q3 = pl[4 * k + 3] ^ (0u - ((cg >> (4 * k + 3)) & 1u));
+#pragma unroll
+        for (int v = 0; v < 16; ++v)
+          row[16 * k + v] = ((q0 ^ ((v & 1) ? 0xFFFFFFFFu : 0u)) | (q1 ^ ((v & 2) ? 0xFFFFFFFFu : 0u)) |
+                             (q2 ^ ((v & 4) ? 0xFFFFFFFFu : 0u))) |
+                            ((q3 ^ ((v & 8) ? 0xFFFFFFFFu : 0u)) | nwa);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < kLutSets * 16; ++c) row[c] = 0xFFFFFFFFu;
+    }
+  }
+  // B side: lane pattern P'_lane and, lane s, the group at visiting position s
+  const uint32_t PB = xor_bits5((uint32_t)lane, HBlo);
+  uint32_t cb_s = 0, bw_s = 0;  // C'_h of B group h = ordB[s]; (lightest | heaviest weight << 8)
+  if (lane < nGB) {
+    const uint32_t h = sl.ordB[lane];
+    cb_s = xor_bits5(h, HBhi);
+    bw_s = (uint32_t)group_min_weight(h) | ((uint32_t)code_weight((h << 5) | (EB & 31u)) << 8);
+  }
+  __syncwarp();
+
+  // --- chunks of two B groups in visiting order, A rows in visiting order ----
+  constexpr int kB = 2;
+  uint32_t best_rank = 0xFFFFFFFFu, best_code = 0;
+  int best_w = 127;
+  const int nCh = (nGB + 1) / 2;
+  const unsigned wa_cnt = (unsigned)__popc(WA), wb_cnt = (unsigned)__popc(WB);
+  for (int ch = 0; ch < nCh; ++ch) {
+    const bool two = 2 * ch + 1 < nGB;
+    const uint32_t bw0 = __shfl_sync(kFull, bw_s, 2 * ch), bw1 = __shfl_sync(kFull, bw_s, min(2 * ch + 1, 31));
+    const uint32_t cb0 = __shfl_sync(kFull, cb_s, 2 * ch), cb1 = __shfl_sync(kFull, cb_s, min(2 * ch + 1, 31));
+    const int wb = (int)(bw0 & 0xFFu);
+    const int wb_hi = (int)max(bw0 >> 8, two ? bw1 >> 8 : 0u);
+    const int budget = min(best_w, w_lim) - wb;  // heaviest A weight still worth testing
+    if (budget < 0) break;                      // later chunks are no lighter
+    if (wb_hi + maxwA <= w_done) continue;      // every TEP here was tested before
+    LutCmp cmp[kB];
+    cmp[0].load(sl.lut, PB ^ cb0);
+    cmp[1].load(sl.lut, PB ^ cb1);
+    // A rows whose lightest weight is <= budget
+    int g_end = (int)__shfl_sync(kFull, cumA_v, min(budget, 5));
+    int g0 = 0;
+    for (; g0 < g_end; g0 += kGroupUnroll) {
+      uint32_t acc[kB][kGroupUnroll];
+      uint32_t all = 0xFFFFFFFFu;
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        cmp[b].block(g0);
+        static_for<0, kGroupUnroll>([&](auto uc) {
+          constexpr int u = decltype(uc)::value;
+          acc[b][u] = cmp[b].template first<u>();
+          all &= acc[b][u];
+        });
+      }
+      if (!__any_sync(kFull, all != 0xFFFFFFFFu)) continue;
+      uint32_t cand[kB];
+      uint32_t any_cand = 0;
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        cand[b] = 0;
+        static_for<0, kGroupUnroll>([&](auto uc) {
+          constexpr int u = decltype(uc)::value;
+          cand[b] |= ~(acc[b][u] | cmp[b].template second<u>());
+        });
+        any_cand |= cand[b];
+      }
+      if (__any_sync(kFull, any_cand)) {
+        // rare: verify this lane's candidates on every syndrome word
+        uint32_t lr = 0xFFFFFFFFu, lc = 0;
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+          if (!cand[b] || !lane_b_ok || (b == 1 && !two)) continue;
+          const uint32_t y = ((uint32_t)sl.ordB[2 * ch + b] << 5) | (uint32_t)lane;
+          for (int u = 0; u < kGroupUnroll; ++u) {
+            uint32_t c = ~(cmp[b].first_at(g0 + u) | cmp[b].second_at(g0 + u));
+            if (c == 0u || g0 + u >= nGA) continue;
+            const uint32_t xg = (uint32_t)sl.ordA[g0 + u] << 5;
+            while (c) {
+              const int i = __ffs(c) - 1;
+              c &= c - 1;
+              const uint32_t cc = (xg | (uint32_t)i) | (y << (2 * nAr));
+              if (kResume && code_weight(cc) > w_hi) continue;  // beyond this call's window
+              uint32_t orr = 0;
+              for (int w = 0; w < W; ++w) {
+                uint32_t zz = sl.s0[w];
+                for (int r = 0; r < Sp; ++r) {
+                  const uint32_t d = (cc >> (2 * r)) & 3u;
+                  if (d) zz ^= sl.delta[((size_t)r * 3 + (d - 1)) * W + w];
+                }
+                orr |= zz;
+              }
+              if (orr == 0) {
+                const uint32_t rk = tep_rank(sl.E, Sp, sl.ex, cc);
+                if (rk < lr) { lr = rk; lc = cc; }
+              }
+            }
+          }
+        }
+        const uint32_t wr = __reduce_min_sync(kFull, lr);
+        if (wr < best_rank) {
+          const unsigned who = __ballot_sync(kFull, lr == wr);
+          best_code = __shfl_sync(kFull, lc, __ffs(who) - 1);
+          best_rank = wr;
+          best_w = code_weight(best_code);
+          const int nb = min(best_w, w_lim) - wb;
+          g_end = nb < 0 ? 0 : min(g_end, (int)__shfl_sync(kFull, cumA_v, min(nb, 5)));
+        }
+      }
+    }
+    if (lane == 0)
+      my_eval += (unsigned long long)min(g0, nGA) * wa_cnt * (unsigned long long)(wb_cnt * (two ? 2u : 1u));
+  }
+  // --- result ---------------------------------------------------------------
+  const bool hit = best_rank != 0xFFFFFFFFu && (uint64_t)best_rank <= (uint64_t)a.cap;
+  if (kResume && !hit && w_hi < w_cap) {  // no codeword up to w_hi, weights left below the cap
+    uint32_t tested = __shfl_sync(kFull, cnt, w_hi), done = __shfl_sync(kFull, cnt, w_done);
+    suspend_frame(a, fi, rec, w_hi, tested);
+    if (lane == 0) my_useful += tested - done;
+    __syncwarp();
+    return;
+  }
+  const uint32_t done = __shfl_sync(kFull, cnt, w_done);
+  if (lane == 0) {
+    const unsigned f = out_frame(a, fi, rec);
+    uint32_t q_out;
+    if (hit) {
+      uint32_t* cw = a.cw + out_cw_off(a, fi, rec);
+      for (int r = 0; r < Sp; ++r) {
+        const uint32_t d = (best_code >> (2 * r)) & 3u;
+        if (d & 1u) { const uint16_t p = sl.pos[2 * r]; if (p != kNoPos) cw[p >> 5] ^= 1u << (p & 31); }
+        if (d & 2u) { const uint16_t p = sl.pos[2 * r + 1]; if (p != kNoPos) cw[p >> 5] ^= 1u << (p & 31); }
+      }
+      q_out = best_rank;
+      a.abandon[f] = 0;
+    } else {
+      q_out = (uint32_t)((uint64_t)total < (uint64_t)a.cap ? total : (uint64_t)a.cap);
+      a.abandon[f] = 1;
+    }
+    a.queries[f] = q_out;
+    my_useful += q_out - done;
+  }
+  __syncwarp();
+}
+
 template <int kMinBlocks, int kSide, bool kResume>
 __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31;
-  const WarpSlice sl =
-      warp_slice<kSide>(smem_raw + (threadIdx.x >> 5) * warp_slice_bytes<kSide>(a.Wmax), a.Wmax);
+  char* my_slice = smem_raw + (threadIdx.x >> 5) * (kSide == kWarpSideMax ? slice5_bytes(a.Wmax)
+                                                                          : warp_slice_bytes<kSide>(a.Wmax));
   const unsigned n_hard = kResume && a.cur_in ? (unsigned)a.n_cur : *(volatile unsigned*)&a.scr->n_hard;
   unsigned long long my_eval = 0, my_useful = 0;
+  uint32_t lay_key = 0xFFu;  // side sizes whose subset order the slice holds (none yet)
   for (;;) {
     unsigned fi = 0;
     if (lane == 0) fi = atomicAdd(&a.scr->next, 1u);
@@ -1517,7 +1922,10 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
       if (lane == 0) cut = cut_at_deadline(a, rec, out_frame(a, fi, rec));
       if (__shfl_sync(kFull, cut, 0)) continue;
     }
-    search_frame<kSide, kResume>(a, fi, rec, sl, my_eval, my_useful);
+    if constexpr (kSide == kWarpSideMax)
+      search_frame5<kResume>(a, fi, rec, slice5(my_slice, a.Wmax), my_eval, my_useful);
+    else
+      search_frame<kSide, kResume>(a, fi, rec, warp_slice<kSide>(my_slice, a.Wmax), my_eval, my_useful, lay_key);
   }
   if (lane == 0) {
     if (my_eval) atomicAdd(&a.scr->evaluated, my_eval);
@@ -2385,7 +2793,7 @@ static int launch_search_t(const SearchArgs& s, int threads, size_t smem, cudaSt
 template <int B, int Side>
 static int launch_search_warp_t(const SearchArgs& s, int warps, cudaStream_t st) {
   constexpr int kSide = Side;
-  const size_t smem = warp_slice_bytes<kSide>(s.Wmax) * warps;
+  const size_t smem = (kSide == kWarpSideMax ? slice5_bytes(s.Wmax) : warp_slice_bytes<kSide>(s.Wmax)) * warps;
   auto kern = (s.w_step > 0 || s.cur_in) ? k_search_warp<B, kSide, true> : k_search_warp<B, kSide, false>;
   const int per_sm = resident_ctas((const void*)kern, 32 * warps, smem);
   if (per_sm < 0) return GRAND_E_CUDA;
@@ -2404,15 +2812,16 @@ static int launch_search_hash_t(const SearchArgs& s, int warps, cudaStream_t st)
 }
 
 static int launch_search(const SearchArgs& s, int threads, size_t smem, int variant, cudaStream_t st) {
-  if (s.warp_kernel == 1) {
-    switch (variant) {
-      case 4: return launch_search_warp_t<4, kWarpSideMax>(s, 4, st);
-      case 8: return launch_search_warp_t<8, kWarpSideMax>(s, 4, st);
-      default: return launch_search_warp_t<6, kWarpSideMax>(s, 4, st);
-    }
-  }
   // the warp-per-frame kernels are compiled for CTAs of at most 4 warps
   const int req_warps = s.warps > 4 ? 4 : s.warps;
+  if (s.warp_kernel == 1) {  // sides of 5 ranks; warps per CTA from the tiles (default 4)
+    const int warps = req_warps > 0 ? req_warps : 4;
+    switch (variant) {
+      case 4: return launch_search_warp_t<4, kWarpSideMax>(s, warps, st);
+      case 8: return launch_search_warp_t<8, kWarpSideMax>(s, warps, st);
+      default: return launch_search_warp_t<6, kWarpSideMax>(s, warps, st);
+    }
+  }
   if (s.warp_kernel == 3 || s.warp_kernel == 4) {  // hash join; warps per CTA from the tiles
     return s.warp_kernel == 3 ? launch_search_hash_t<kWarpSideMax>(s, req_warps > 0 ? req_warps : 4, st)
                               : launch_search_hash_t<kWarpSideMax + 1>(s, req_warps > 0 ? req_warps : 1, st);

@@ -103,22 +103,26 @@ def test_reference_arm_under_torchrun_two_ranks():
 
 
 def test_roofline_fraction_is_bounded_and_reproducible():
-    """The bench line's roofline.frac comes from executed ALU operations: for
-    the profiled launch itself (its evaluated checks over its own duration)
-    it reproduces the ALU-pipe busy fraction the profile measured, and it is
-    below 1; the survey-model figure is kept apart (model_ops)."""
+    """The bench line's roofline.frac comes from the work the kernel executed
+    on the unit that bounds it: for the profiled launch itself (its evaluated
+    checks over its own duration) it reproduces the busy fraction the profile
+    measured (shared-memory wavefronts for the nibble-table search, the ALU
+    pipe for the bit-plane search) and it is below 1; the survey-model figure
+    is kept apart (model_ops)."""
     bench = load_bench()
     cfg = dict(bench.CONFIGS["c2"], name="c2")
     prof = bench.NCU_SEARCH["k_search_warp<5>"]
-    # the profiled small case: 8.96e9 evaluated checks in 462.7 us at 2.07 GHz
-    r = bench.search_roofline(cfg, 8960902651.0, 8800799405.0, 9596, 0.4627, 2.0)
-    assert r["kernel"] == "k_search_warp<5>" and r["bound"] == "alu"
+    # the profiled small case: 9.69e9 evaluated checks in 164.1 us at 2.07 GHz
+    r = bench.search_roofline(cfg, 9688332411.0, 8800799405.0, 11181, 0.164128, 2.0)
+    assert r["kernel"] == "k_search_warp<5>" and r["bound"] == "smem" and r["unit"] == "GB/s"
     assert 0.5 < r["frac"] < 1.0
-    assert abs(r["frac"] - prof["alu_pipe_active"]) < 0.02
-    assert r["model_ops"]["frac"] > 1.0  # the survey's per-useful-check model is not a fraction of the pipe
+    assert abs(r["frac"] - prof["smem_wavefronts_frac"]) < 0.02
+    assert 0.0 < r["alu"]["frac"] < 1.0
+    assert r["model_ops"]["frac"] > 1.0  # the survey's per-useful-check model is not a fraction of a pipe
     cfg3 = dict(bench.CONFIGS["c3a"], name="c3a")
     assert bench.search_kernel(cfg3) == "k_search_warp<6>"
     r3 = bench.search_roofline(cfg3, 77756186838.0, 77714307970.0, 4706, 3.364384, 8.0)
+    assert r3["bound"] == "alu"
     assert abs(r3["frac"] - bench.NCU_SEARCH["k_search_warp<6>"]["alu_pipe_active"]) < 0.02
 
 
