@@ -100,13 +100,14 @@ SMEM_PEAK_GBS = SMS * 128 * MAX_CLOCK_GHZ
 #     64 lanes / checks (the bit-plane search is bound by the integer pipe).
 # Everything in the kernel is included in both.
 NCU_SEARCH = {
-    "k_search_warp<5>": {"sha": "31af198c6f0e2acf", "profile": "profiles/k_search_warp_c2_small.md", "bound": "smem",
-                         "smem_bytes_per_check": 0.5763, "smem_wavefronts_frac": 0.838, "lsu_pipe_active": 0.910,
-                         "alu_lane_ops_per_check": 0.151, "alu_pipe_active": 0.439,
-                         "dram_bytes_per_hard_frame": 1872640 / 11181},
-    "k_search_warp<6>": {"sha": "b1d00947d52a7877", "profile": "profiles/k_search_warp6_c3a_small.md", "bound": "alu",
-                         "alu_lane_ops_per_check": 0.650, "alu_pipe_active": 0.753,
-                         "dram_bytes_per_hard_frame": 772864 / 4706},
+    "k_search_warp S'<=10": {"sha": "ab8dcb515250d93f", "profile": "profiles/k_search_warp_c2_small.md",
+                             "bound": "smem", "smem_bytes_per_check": 0.5731, "smem_wavefronts_frac": 0.809,
+                             "lsu_pipe_active": 0.877, "alu_lane_ops_per_check": 0.162, "alu_pipe_active": 0.459,
+                             "dram_bytes_per_hard_frame": 1879552 / 11181},
+    "k_search_warp S'=12": {"sha": "ab8dcb515250d93f", "profile": "profiles/k_search_warp_c3a_small.md",
+                            "bound": "smem", "smem_bytes_per_check": 0.5531, "smem_wavefronts_frac": 0.782,
+                            "lsu_pipe_active": 0.833, "alu_lane_ops_per_check": 0.141, "alu_pipe_active": 0.399,
+                            "dram_bytes_per_hard_frame": 776704 / 4706},
     # the bit-level kernel reads every frame (no hand-off records): bytes per frame
     "k_ab_split<1,16>": {"sha": "b1d00947d52a7877", "profile": "profiles/k_ab_split_c1_n32_bpsk.md", "bound": "alu",
                          "alu_lane_ops_per_check": 166.0, "alu_pipe_active": 0.360,
@@ -122,10 +123,13 @@ def decode_source_sha():
 
 
 def search_kernel(cfg):
-    """The kernel that runs the TEP search of a workload with automatic tiles."""
+    """The kernel that runs the TEP search of a workload with automatic tiles,
+    and the key of its profile (the flip-bit search is profiled at S' <= 10
+    and at S' = 12, whose B side is 16 times larger)."""
     if cfg["kind"] == "ab":
-        return "k_ab_split<1,16>" if cfg["N"] == 32 else "k_ab"
-    return "k_search_warp<6>" if cfg["S"] > 10 else "k_search_warp<5>"
+        k = "k_ab_split<1,16>" if cfg["N"] == 32 else "k_ab"
+        return k, k
+    return "k_search_warp", ("k_search_warp S'=12" if cfg["S"] > 10 else "k_search_warp S'<=10")
 
 
 def search_roofline(cfg, evaluated, useful, hard, kernel_ms, alg_words, frames=0):
@@ -141,8 +145,8 @@ def search_roofline(cfg, evaluated, useful, hard, kernel_ms, alg_words, frames=0
     it can exceed the ALU peak, because the split compare tests 32 TEPs per
     table word or logic op on a projection and confirms only matches on the
     full syndrome."""
-    kern = search_kernel(cfg)
-    prof = NCU_SEARCH.get(kern)
+    kern, prof_key = search_kernel(cfg)
+    prof = NCU_SEARCH.get(prof_key)
     t_s = kernel_ms / 1e3
     alu_src = (f"derived: {SMS} SMs x {ALU_LANES} ALU lanes/clk x {MAX_CLOCK_GHZ} GHz (a LOP3 microbenchmark on "
                "this GPU measured 64 per clock per SM)")

@@ -80,9 +80,9 @@ struct SearchArgs {
   int tabA, tabB;  // table capacities
   int max_tiles;
   int Wmax;
-  int warp_kernel;  // 1 / 2: warp-per-frame kernel with 5- / 6-rank sides (automatic split); 0: CTA kernel;
+  int warp_kernel;  // 1 / 2: warp-per-frame flip-bit search, S' <= 10 / 12 (automatic split); 0: CTA kernel;
                     // 3 / 4: hash join (membership HASH) with 5- / 6-rank sides
-  int warps;        // warps per CTA of the 6-rank warp kernel (0: 2)
+  int warps;        // warps per CTA of the warp-per-frame kernels (0: their default)
   uint32_t* cw;
   uint32_t* queries;
   uint8_t* abandon;
@@ -994,40 +994,29 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_search(SearchArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Warp-per-frame, bit-sliced search: sides of at most kSide ranks, 4^kSide
-// table entries per side (kSide = 5: S' <= 10; kSide = 6: S' <= 12).
+// Meet-in-the-middle split of the TEP space: A x B sides. The warp search
+// (k_search_warp, every S' <= 12) and the hash join (k_search_hash) own one
+// frame per warp, with its tables in the warp's own slice of shared memory and
+// a set-up that runs on warp shuffles and ballots, so no block-wide barrier
+// exists and the set-up of one warp overlaps the compares of the others.
 //
-// Every warp owns one frame at a time; its tables live in the warp's own slice
-// of shared memory and the whole set-up runs on warp shuffles, so no
-// block-wide barrier exists and the set-up of one warp overlaps the compares of
-// the others.
-//
-// The compare is bit-sliced. The A side (s0 ^ D_A, weight-sorted) is cut into
-// groups of 32 entries and each group is stored as kPlanes bit-planes: plane b
-// holds bit b of the projections of the group's 32 entries. A lane holds one B
-// entry and expands its projection z into kPlanes masks (all-ones where the bit
-// is 1). For one group,
-//     acc = OR_b (plane_b XOR mask_b)
-// has a zero bit exactly at the entries whose low kPlanes projection bits equal
-// z's: kPlanes 3-input logic ops test 32 TEPs (0.66 integer ops per TEP with
-// the candidate fold). Candidates (false rate 2^-kPlanes) are verified on every
-// syndrome word.
-//
-// With 5-rank sides (S' <= 10) the masks are folded into the tables instead:
-// every A group keeps, per nibble k of the projection (planes 4k..4k+3), the
-// 16 words T[k][v] = OR_{j<4} (plane_{4k+j} XOR (bit j of v ? ~0 : 0)), so a
-// lane with B projection z gets the same acc from one table word per nibble,
+// The warp search compares a B entry with 32 A entries at once on a 20-bit
+// projection of the syndrome (false matches 2^-20; candidates are verified on
+// every syndrome word). Each A group of 32 entries keeps, per nibble k of the
+// projection (bit-planes 4k..4k+3), the 16 words
+//     T[k][v] = OR_{j<4} (plane_{4k+j} XOR (bit j of v ? ~0 : 0)),
+// so a lane with B projection z gets
 //     acc = T[0][z & 15] | T[1][(z >> 4) & 15] | T[2][...] | T[3][...],
-// four shared-memory reads and two logic ops for 32 TEPs x 16 bits. The 16
-// words of a nibble sit in 16 distinct banks, so any pattern of lane reads is
-// conflict-free; the kernel is then bound by shared-memory bandwidth (0.5 B
-// per TEP) instead of the integer pipe.
+// zero exactly at the A entries equal to z on 16 bits: four shared-memory
+// reads and two logic ops test 32 TEPs (the last nibble only after a match).
+// The 16 words of a nibble sit in 16 distinct banks, so any pattern of lane
+// reads is conflict-free; the kernel is bound by shared-memory bandwidth
+// (0.5 B per TEP).
 // ---------------------------------------------------------------------------
-constexpr int kWarpSideMax = 5;                      // the small-table variant (S' <= 10)
+constexpr int kWarpSideMax = 5;                      // hash join: the small-table variant (S' <= 10)
 constexpr int kPlanes = 20;                          // projection bits compared per TEP
 constexpr int kGroupUnroll = 8;                      // groups per candidate check
-constexpr int kPlanesL1 = 16;                        // first-level planes (the rest only on a match)
-constexpr int kLutSets = kPlanes / 4;                // nibble tables per group (5-rank sides)
+constexpr int kLutSets = kPlanes / 4;                // nibble tables per group
 constexpr int kLutStride = kLutSets * 16 + 1;        // words per group (odd: conflict-free per-lane stores)
 
 // Table sizes of one side for the kSide variant.
@@ -1039,8 +1028,8 @@ struct WarpDims {
   static constexpr int kRanks = 2 * kSide;       // S' bound
 };
 
+// The hash join's per-warp slice (sides of kSide ranks, weight-sorted tables).
 struct WarpSlice {
-  uint32_t* planes;  // [kGroups][kPlanes] bit-planes of the A side
   uint32_t* Bz;      // [kTab] projection of D_A, then of D_B, weight-sorted (kSide = 5 only)
   uint32_t* delta;   // [kRanks][3][Wmax] full syndrome deltas
   uint32_t* dflt;    // [kRanks][3] projections of the deltas
@@ -1058,28 +1047,20 @@ struct WarpSlice {
   uint16_t* pos;     // [kRanks][2]
 };
 
-// words of the bit-planes of one warp's A side
 template <int kSide>
-__host__ __device__ constexpr int warp_table_words() {
-  return WarpDims<kSide>::kGroups * kPlanes;
-}
-
-template <int kSide, bool kWithPlanes = true>
 __host__ __device__ inline size_t warp_slice_bytes(int Wmax) {
   using D = WarpDims<kSide>;
   const size_t bz = kSide == kWarpSideMax ? D::kTab : 0;
-  size_t words = (kWithPlanes ? (size_t)warp_table_words<kSide>() : 0) + bz + 3 * D::kRanks * (size_t)Wmax + 3 * D::kRanks +
+  size_t words = bz + 3 * D::kRanks * (size_t)Wmax + 3 * D::kRanks +
                  kEStride * kEStride + Wmax + 2 * (D::kSub + 1) + 8 + 8 + D::kSub + 4 + D::kRanks;
   return (words * 4 + 15) & ~(size_t)15;
 }
 
-template <int kSide, bool kWithPlanes = true>
+template <int kSide>
 __device__ inline WarpSlice warp_slice(char* base, int Wmax) {
   using D = WarpDims<kSide>;
   WarpSlice w;
   uint32_t* p = reinterpret_cast<uint32_t*>(base);
-  w.planes = kWithPlanes ? p : nullptr;
-  p += kWithPlanes ? warp_table_words<kSide>() : 0;
   w.Bz = p; p += kSide == kWarpSideMax ? D::kTab : 0;
   w.delta = p; p += 3 * D::kRanks * Wmax;
   w.dflt = p; p += 3 * D::kRanks;
@@ -1253,86 +1234,11 @@ __device__ inline void warp_fill_side(const WarpSlice& sl, int r0, int n, const 
   __syncwarp();
 }
 
-// 32 x 32 bit transpose across the warp: on return lane b holds the word whose
-// bit i is bit b of lane i's input (five butterfly exchange stages).
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const uint32_t m = s == 16 ? 0x0000FFFFu : (s == 8 ? 0x00FF00FFu : (s == 4 ? 0x0F0F0F0Fu : (s == 2 ? 0x33333333u
-                                                                                                      : 0x55555555u)));
-    const uint32_t y = __shfl_xor_sync(kFull, x, s);
-    x = (lane & s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y << s) & ~m));
-  }
-  return x;
-}
-
-// weight of entry e: the number of weights whose cumulative count is <= e
-__device__ __forceinline__ int side_entry_weight(const uint32_t* cum, int n, unsigned e) {
-  int w = 0;
-  while (w < n && cum[w] <= e) ++w;
-  return w;
-}
-
-// OR over the planes of group g of (plane XOR mask): zero bits mark candidates.
-__device__ __forceinline__ uint32_t group_acc(const uint32_t* planes, int g, const uint32_t (&m)[kPlanes]) {
-  const uint4* pl = reinterpret_cast<const uint4*>(planes + g * kPlanes);
-  uint32_t acc = 0;
-#pragma unroll
-  for (int j = 0; j < kPlanes / 4; ++j) {
-    const uint4 p = pl[j];
-    acc |= p.x ^ m[4 * j + 0];
-    acc |= p.y ^ m[4 * j + 1];
-    acc |= p.z ^ m[4 * j + 2];
-    acc |= p.w ^ m[4 * j + 3];
-  }
-  return acc;
-}
-
-// The same OR over a range of planes [B0, B1) (multiples of 4).
-template <int B0, int B1>
-__device__ __forceinline__ uint32_t group_acc_part(const uint32_t* planes, int g, const uint32_t (&m)[kPlanes]) {
-  const uint4* pl = reinterpret_cast<const uint4*>(planes + g * kPlanes);
-  uint32_t acc = 0;
-#pragma unroll
-  for (int j = B0 / 4; j < B1 / 4; ++j) {
-    const uint4 p = pl[j];
-    acc |= p.x ^ m[4 * j + 0];
-    acc |= p.y ^ m[4 * j + 1];
-    acc |= p.z ^ m[4 * j + 2];
-    acc |= p.w ^ m[4 * j + 3];
-  }
-  return acc;
-}
-
-// The compare of one lane's B entry against A groups: 6-rank sides XOR the
-// group's bit-planes with the entry's bit masks; 5-rank sides read the
-// group's nibble tables at the entry's nibbles. first(g): OR over planes
-// 0..15 (zero bits: entries equal on those bits); second(g): planes 16..19.
+// The compare of one lane's B entry z against the A groups' nibble tables:
 // block(g0) fixes the first group of a block of kGroupUnroll groups;
-// first<U>() / second<U>() then address group g0 + U (U a compile-time
-// constant, so the table reads of a block take immediate offsets);
-// first_at / second_at address any group (the candidate path).
-struct PlaneCmp {
-  const uint32_t* planes;
-  uint32_t m[kPlanes];
-  int g0;
-  __device__ __forceinline__ void load(const uint32_t* tab, uint32_t z) {
-    planes = tab;
-#pragma unroll
-    for (int b = 0; b < kPlanes; ++b) m[b] = 0u - ((z >> b) & 1u);
-  }
-  __device__ __forceinline__ void block(int g) { g0 = g; }
-  template <int U>
-  __device__ __forceinline__ uint32_t first() const { return first_at(g0 + U); }
-  template <int U>
-  __device__ __forceinline__ uint32_t second() const { return second_at(g0 + U); }
-  __device__ __forceinline__ uint32_t first_at(int g) const { return group_acc_part<0, kPlanesL1>(planes, g, m); }
-  __device__ __forceinline__ uint32_t second_at(int g) const {
-    return group_acc_part<kPlanesL1, kPlanes>(planes, g, m);
-  }
-};
-
+// first<U>() (nibbles 0..3) and second<U>() (nibble 4) then read group g0 + U
+// with immediate offsets; first_at / second_at read any group (candidates).
+//
 // 32-bit shared-memory read at a shared-window address plus an immediate.
 template <int kOff>
 __device__ __forceinline__ uint32_t lds_imm(uint32_t addr) {
@@ -1380,208 +1286,8 @@ __device__ __forceinline__ void static_for(F&& f) {
   }
 }
 
-// The search of one frame from its hand-off record with sides of 6 ranks
-// (S' = 11, 12; one warp; `rec` may live in global or shared memory). Lane 0
-// accumulates the evaluated and useful checks. lay_key: the side sizes whose
-// subset order the slice already holds.
-template <int kSide, bool kResume>
-__device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, const FrameRec* rec,
-                                             const WarpSlice& sl, unsigned long long& my_eval,
-                                             unsigned long long& my_useful, uint32_t& lay_key) {
-  static_assert(kSide != kWarpSideMax, "5-rank sides use search_frame5");
-  const int lane = threadIdx.x & 31;
-  {
-    const int Sp = rec->sp;
-    const int w_done = rec->w_done;
-    const CodeDev code = a.codes[rec->code];
-    const int W = code.W;
-    if (lane < Sp) {
-      sl.ex[lane] = rec->ex[lane];
-      sl.pos[2 * lane] = rec->pos[lane][0];
-      sl.pos[2 * lane + 1] = rec->pos[lane][1];
-    }
-    if (lane < W) sl.s0[lane] = rec->s0[lane];
-    const uint32_t f0 = rec->f0;
-    __syncwarp();
-    // deltas of rank r's alternatives (h, v, diag) on every syndrome word and
-    // their projections: lane t = 3 r + alt
-    for (int t = lane; t < 3 * Sp; t += 32) {
-      const int r = t / 3, alt = t - 3 * (t / 3);
-      const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
-      const bool useI = alt != 1 && pI != kNoPos, useQ = alt != 0 && pQ != kNoPos;
-      sl.dflt[t] = (useI ? __ldg(code.hf + pI) : 0u) ^ (useQ ? __ldg(code.hf + pQ) : 0u);
-      for (int w = 0; w < W; ++w)
-        sl.delta[t * W + w] = (useI ? __ldg(code.hcol + (size_t)pI * W + w) : 0u) ^
-                              (useQ ? __ldg(code.hcol + (size_t)pQ * W + w) : 0u);
-    }
-    esp_table_warp(sl.ex, Sp, sl.E);
-    __syncwarp();
-    // valid TEPs of weight <= v (lane v, a warp scan); the cap's weight class
-    uint32_t cnt = lane <= Sp ? sl.E[Sp * kEStride + lane] : 0u;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(kFull, cnt, o);
-      if (lane >= o) cnt += t;
-    }
-    const uint32_t total = __shfl_sync(kFull, cnt, Sp);
-    const unsigned over = __ballot_sync(kFull, lane <= Sp && (uint64_t)cnt >= (uint64_t)a.cap);
-    const int w_cap = over ? __ffs(over) - 1 : Sp;
-    const int nAr = Sp >> 1, nBr = Sp - nAr;
-    // the subset orders of the previous frame's sides are still in place when
-    // the side sizes are the same
-    const unsigned nA = warp_side_layout(sl, 0, nAr, sl.startA, sl.ordA, sl.invA, sl.cumA, (lay_key & 0xFu) == (unsigned)nAr);
-    const unsigned nB =
-        warp_side_layout(sl, nAr, nBr, sl.startB, sl.ordB, sl.invB, sl.cumB, (lay_key >> 4) == (unsigned)nBr);
-    lay_key = (uint32_t)nAr | ((uint32_t)nBr << 4);
-    const int nG = (int)((nA + 31) / 32);
-    // weight window of this call: w_done + 1 .. w_hi (all weights without a
-    // step); no TEP heavier than the cap's class matters
-    const int w_hi = kResume && a.w_step > 0 ? min(Sp, w_done + a.w_step) : Sp;
-    const int w_lim = min(w_cap, w_hi);
-    // A groups a window can reach (entries of weight <= w_lim): the planes of
-    // later groups are never read, so a windowed search does not build them
-    const int nG_use = kResume ? (int)((sl.cumA[min(w_lim, nAr)] + 31) / 32) : nG;
-    // no scalar tables: each lane derives its A entry from the table layout,
-    // one group of 32 per warp transpose. The bit-plane pattern of a padding
-    // entry is never a candidate in practice (candidates beyond nA are skipped
-    // at verification).
-    {
-      const uint32_t pad_plane = (kPadA >> (lane < kPlanes ? lane : 0)) & 1u ? 0xFFFFFFFFu : 0u;
-      const int nG8 = (nG_use + kGroupUnroll - 1) / kGroupUnroll * kGroupUnroll;
-      for (int g = 0; g < nG8; ++g) {
-        const unsigned e = 32u * g + lane;
-        uint32_t q = kPadA, acode;
-        if (e < nA) warp_side_entry(sl, 0, nAr, sl.startA, sl.ordA, f0, e, q, acode);
-        const uint32_t mine = warp_transpose32(q);
-        if (lane < kPlanes) sl.planes[g * kPlanes + lane] = g < nG ? mine : pad_plane;
-      }
-      __syncwarp();
-    }
-
-    // --- chunks of 32 B entries in weight order, A groups in weight order ----
-    uint32_t best_rank = 0xFFFFFFFFu, best_code = 0;
-    int best_w = 127;
-    const int nCh = (int)((nB + 31) / 32);
-    for (int ch = 0; ch < nCh; ++ch) {
-      const int wb = side_entry_weight(sl.cumB, nBr, 32u * ch);
-      const int budget = min(best_w, w_lim) - wb;  // heaviest A weight still worth testing
-      if (budget < 0) break;
-      const unsigned col = 32u * ch + lane;
-      uint32_t z = kPadB, bcode0;
-      if (col < nB) warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, z, bcode0);
-      PlaneCmp cmp;
-      cmp.load(sl.planes, z);
-      // groups holding an A entry of weight <= budget; skip what the
-      // preparation already tested (every TEP of weight <= w_done)
-      int g_end = (int)((sl.cumA[min(budget, nAr)] + 31) / 32);
-      // chunk max weight: if it cannot exceed w_done with the heaviest group, skip
-      const int wb_hi = side_entry_weight(sl.cumB, nBr, min(nB, 32u * ch + 32u) - 1u);
-      if (wb_hi + nAr <= w_done) continue;
-      // A groups whose entries all weigh <= w_done - wb_hi pair with this
-      // chunk into TEPs of weight <= w_done only (tested before): skip them
-      int g_start = 0;
-      if (kResume && w_done >= wb_hi)
-        g_start = (int)(sl.cumA[min(w_done - wb_hi, nAr)] / 32) / kGroupUnroll * kGroupUnroll;
-      int g0 = g_start;
-      for (; g0 < g_end; g0 += kGroupUnroll) {
-        // first level: kPlanesL1 projection bits of kGroupUnroll groups
-        uint32_t acc[kGroupUnroll];
-        uint32_t all = 0xFFFFFFFFu;
-        cmp.block(g0);
-        static_for<0, kGroupUnroll>([&](auto uc) {
-          constexpr int u = decltype(uc)::value;
-          acc[u] = cmp.template first<u>();
-          all &= acc[u];
-        });
-        if (!__any_sync(kFull, all != 0xFFFFFFFFu)) continue;
-        // a first-level match somewhere in the warp: the remaining planes
-        uint32_t cand = 0;
-        static_for<0, kGroupUnroll>([&](auto uc) {
-          constexpr int u = decltype(uc)::value;
-          cand |= ~(acc[u] | cmp.template second<u>());
-        });
-        if (__any_sync(kFull, cand)) {
-          // rare: locate candidates of this lane and verify every syndrome word
-          uint32_t lr = 0xFFFFFFFFu, lc = 0;
-          if (cand && col < nB) {
-            uint32_t bcode, bq;
-            warp_side_entry(sl, nAr, nBr, sl.startB, sl.ordB, 0u, col, bq, bcode);
-            for (int u = 0; u < kGroupUnroll; ++u) {
-              uint32_t c = ~(cmp.first_at(g0 + u) | cmp.second_at(g0 + u));
-              while (c) {
-                const int i = __ffs(c) - 1;
-                c &= c - 1;
-                const unsigned row = 32u * (g0 + u) + i;
-                if (row >= nA) continue;
-                uint32_t aq, acode;
-                warp_side_entry(sl, 0, nAr, sl.startA, sl.ordA, f0, row, aq, acode);
-                const uint32_t cc = acode | (bcode << (2 * nAr));
-                if (kResume && code_weight(cc) > w_hi) continue;  // beyond this call's window
-                uint32_t orr = 0;
-                for (int w = 0; w < W; ++w) {
-                  uint32_t zz = sl.s0[w];
-                  for (int r = 0; r < Sp; ++r) {
-                    const uint32_t d = (cc >> (2 * r)) & 3u;
-                    if (d) zz ^= sl.delta[((size_t)r * 3 + (d - 1)) * W + w];
-                  }
-                  orr |= zz;
-                }
-                if (orr == 0) {
-                  const uint32_t rk = tep_rank(sl.E, Sp, sl.ex, cc);
-                  if (rk < lr) { lr = rk; lc = cc; }
-                }
-              }
-            }
-          }
-          const uint32_t wr = __reduce_min_sync(kFull, lr);
-          if (wr < best_rank) {
-            const unsigned who = __ballot_sync(kFull, lr == wr);
-            best_code = __shfl_sync(kFull, lc, __ffs(who) - 1);
-            best_rank = wr;
-            best_w = code_weight(best_code);
-            const int nb = min(best_w, w_lim) - wb;
-            g_end = nb < 0 ? 0 : min(g_end, (int)((sl.cumA[min(nb, nAr)] + 31) / 32));
-          }
-        }
-      }
-      if (lane == 0)
-        my_eval += (unsigned long long)(min(nA, 32u * (unsigned)g0) - min(nA, 32u * (unsigned)g_start)) *
-                   (unsigned long long)min(32u, nB - 32u * ch);
-    }
-    // --- result -------------------------------------------------------------
-    const bool hit = best_rank != 0xFFFFFFFFu && (uint64_t)best_rank <= (uint64_t)a.cap;
-    if (kResume && !hit && w_hi < w_cap) {  // no codeword up to w_hi, weights left below the cap
-      const uint32_t tested = __shfl_sync(kFull, cnt, w_hi), done = __shfl_sync(kFull, cnt, w_done);
-      suspend_frame(a, fi, rec, w_hi, tested);
-      if (lane == 0) my_useful += tested - done;
-      __syncwarp();
-      return;
-    }
-    const uint32_t done = __shfl_sync(kFull, cnt, w_done);
-    if (lane == 0) {
-      const unsigned f = out_frame(a, fi, rec);
-      uint32_t q_out;
-      if (hit) {
-        uint32_t* cw = a.cw + out_cw_off(a, fi, rec);
-        for (int r = 0; r < Sp; ++r) {
-          const uint32_t d = (best_code >> (2 * r)) & 3u;
-          if (d & 1u) { const uint16_t p = sl.pos[2 * r]; if (p != kNoPos) cw[p >> 5] ^= 1u << (p & 31); }
-          if (d & 2u) { const uint16_t p = sl.pos[2 * r + 1]; if (p != kNoPos) cw[p >> 5] ^= 1u << (p & 31); }
-        }
-        q_out = best_rank;
-        a.abandon[f] = 0;
-      } else {
-        q_out = (uint32_t)((uint64_t)total < (uint64_t)a.cap ? total : (uint64_t)a.cap);
-        a.abandon[f] = 1;
-      }
-      a.queries[f] = q_out;
-      my_useful += q_out - done;
-    }
-    __syncwarp();
-  }
-}
-
 // ---------------------------------------------------------------------------
-// Warp search with sides of at most 5 ranks (S' <= 10): flip-bit tables.
+// Warp search on flip-bit tables (every S' <= 12).
 //
 // A TEP restricted to one side is a vector x of 2n flip bits: bit 2r selects
 // the I-slot alternative of the side's r-th rank, bit 2r+1 the Q-slot one, and
@@ -1590,56 +1296,80 @@ __device__ __forceinline__ void search_frame(const SearchArgs& a, unsigned fi, c
 // form, and its syndrome projection is linear in x:
 //     proj(x) = seed ^ XOR_{b in x} H_b.
 // A side's vectors are cut as x = 32 g + i: i (bits 0..4) within a group, g
-// (bits 5..9) the group. Within group g the projections are C_g ^ P_i, with
-// P_i = XOR_{b < 5, b in i} H_b the same for every group, so the bit-planes
-// of every group are those of P (one set of 20 warp ballots) with plane b
-// inverted where bit b of C_g is set, and the nibble tables of a group follow
-// from the planes and C_g without a per-group transpose or any table of
-// projections. Vectors naming an alternative that does not exist are masked:
-// existence is a per-bit property (within part and group part separately).
-// Groups of both sides are visited in order of their lightest TEP weight
-// (A groups as table rows, B groups two per chunk, one entry per lane each),
-// which keeps the weight cut-offs of the canonical order.
+// (the higher bits) the group. Within group g the projections are C_g ^ P_i,
+// with P_i = XOR_{b < 5, b in i} H_b the same for every group, so
+//   * the A side (at most 5 ranks: 32 groups) keeps one row of nibble tables
+//     per group, derived from the 20 bit-planes of P (one set of warp ballots)
+//     inverted at the bits of C_g -- no per-group transposes and no table of
+//     projections;
+//   * the B side (at most 7 ranks: up to 512 groups) needs no table at all: the
+//     lane holding within-group vector i of group h compares C'_h ^ P'_i.
+// Vectors naming an alternative that does not exist are masked (existence is
+// a per-bit property, within part and group part separately). Groups of both
+// sides are visited in order of their lightest TEP weight (A groups as table
+// rows, B groups two per chunk, one entry per lane each), which keeps the
+// weight cut-offs of the canonical order.
 // ---------------------------------------------------------------------------
-struct Slice5 {
+constexpr int kFlipSideA = 5;   // ranks of the A side (table rows: 2^(2*5-5) = 32 groups)
+constexpr int kFlipSideB = 7;   // ranks of the B side at most (S' <= 12)
+
+// B groups of the largest split a launch handles (the size of its B-group list).
+__host__ __device__ inline int flip_b_groups(int sp_max) {
+  const int nA = sp_max >> 1 < kFlipSideA ? sp_max >> 1 : kFlipSideA;
+  const int bits = 2 * (sp_max - nA) - 5;
+  return bits > 0 ? 1 << bits : 1;
+}
+
+struct FlipSlice {
   uint32_t* lut;    // [32][kLutStride] nibble tables of the A groups in visiting order
-  uint32_t* delta;  // [10][3][Wmax] full syndrome deltas
-  uint32_t* dflt;   // [10][3] projections of the deltas
+  uint2* bgrp;      // [flip_b_groups] B groups in visiting order: (C'_h, h << 16 | heaviest << 8 | lightest)
+  uint32_t* delta;  // [kSMax][3][Wmax] full syndrome deltas
+  uint32_t* dflt;   // [kSMax][3] projections of the deltas
   uint32_t* E;      // [kEStride^2]
   uint32_t* s0;     // [Wmax]
   uint8_t* ordA;    // [32] A group at visiting position t
-  uint8_t* ordB;    // [32] B group at visiting position s
   uint8_t* ex;      // [16]
-  uint16_t* pos;    // [10][2]
+  uint16_t* pos;    // [kSMax][2]
 };
 
-__host__ __device__ inline size_t slice5_bytes(int Wmax) {
-  const size_t words = 32 * kLutStride + 30 * (size_t)Wmax + 30 + kEStride * kEStride + Wmax + 8 + 8 + 4 + 10;
+__host__ __device__ inline size_t flip_slice_bytes(int Wmax, int sp_max) {
+  const size_t words = 32 * kLutStride + 2 * (size_t)flip_b_groups(sp_max) + 3 * kSMax * (size_t)Wmax + 3 * kSMax +
+                       kEStride * kEStride + Wmax + 8 + 4 + kSMax;
   return (words * 4 + 15) & ~(size_t)15;
 }
 
-__device__ inline Slice5 slice5(char* base, int Wmax) {
-  Slice5 w;
+__device__ inline FlipSlice flip_slice(char* base, int Wmax, int sp_max) {
+  FlipSlice w;
   uint32_t* p = reinterpret_cast<uint32_t*>(base);
-  w.lut = p; p += 32 * kLutStride;
-  w.delta = p; p += 30 * Wmax;
-  w.dflt = p; p += 30;
+  w.lut = p; p += 32 * kLutStride;  // even: the B-group list is 8-byte aligned
+  w.bgrp = reinterpret_cast<uint2*>(p); p += 2 * flip_b_groups(sp_max);
+  w.delta = p; p += 3 * kSMax * Wmax;
+  w.dflt = p; p += 3 * kSMax;
   w.E = p; p += kEStride * kEStride;
   w.s0 = p; p += Wmax;
   w.ordA = reinterpret_cast<uint8_t*>(p); p += 8;
-  w.ordB = reinterpret_cast<uint8_t*>(p); p += 8;
   w.ex = reinterpret_cast<uint8_t*>(p); p += 4;
   w.pos = reinterpret_cast<uint16_t*>(p);
   return w;
 }
 
-// Lightest TEP weight of flip-bit group g (its group bits shifted into place).
+// Lightest TEP weight of the flip-bit group g (group bits start at bit 5).
 __device__ __forceinline__ int group_min_weight(uint32_t g) { return code_weight(g << 5); }
 
-// Visiting order of the valid groups of one side (group existence bits ehi):
-// by lightest weight, then by index. Writes ord[0..n) and returns n; lane w
-// (w <= 5) gets in *cum the number of groups of lightest weight <= w.
-__device__ __forceinline__ int order_groups(uint32_t ehi, uint8_t* ord, uint32_t* cum) {
+// XOR of h[b] over the bits b of x (b < N).
+template <int N>
+__device__ __forceinline__ uint32_t xor_bits(uint32_t x, const uint32_t (&h)[N]) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int b = 0; b < N; ++b) r ^= ((x >> b) & 1u) ? h[b] : 0u;
+  return r;
+}
+
+// Visiting order of the A side's valid groups (group existence bits ehi, at
+// most 32 groups): by lightest weight, then by index. Writes ord[0..n) and
+// returns n; lane w (w <= 5) gets in *cum the number of groups of lightest
+// weight <= w.
+__device__ __forceinline__ int order_groups_a(uint32_t ehi, uint8_t* ord, uint32_t* cum) {
   const int lane = threadIdx.x & 31;
   const bool valid = ((uint32_t)lane & ~ehi) == 0u;
   const int mw = group_min_weight((uint32_t)lane);
@@ -1658,17 +1388,36 @@ __device__ __forceinline__ int order_groups(uint32_t ehi, uint8_t* ord, uint32_t
   return n;
 }
 
-// XOR of h[b] over the bits b of x (x < 32).
-__device__ __forceinline__ uint32_t xor_bits5(uint32_t x, const uint32_t (&h)[5]) {
-  uint32_t r = 0;
-#pragma unroll
-  for (int b = 0; b < 5; ++b) r ^= ((x >> b) & 1u) ? h[b] : 0u;
-  return r;
+// Visiting order of the B side's valid groups (group bits nbits <= 9,
+// existence bits ehi): by lightest weight, then by index; each entry carries
+// the group constant C'_h and the group's lightest and heaviest TEP weights
+// (ewithin: the existence bits of the within-group part). Returns the count.
+__device__ inline int order_groups_b(uint32_t ehi, int nbits, uint32_t ewithin, const uint32_t (&hhi)[9],
+                                     uint2* out) {
+  const int lane = threadIdx.x & 31;
+  const int ng = 1 << nbits;
+  int n = 0;
+  for (int w = 0; w <= kFlipSideB - 2; ++w) {
+    for (int h0 = 0; h0 < ng; h0 += 32) {
+      const uint32_t h = (uint32_t)(h0 + lane);
+      const bool take = (int)h < ng && (h & ~ehi) == 0u && group_min_weight(h) == w;
+      const unsigned m = __ballot_sync(kFull, take);
+      if (take) {
+        const int at = n + __popc(m & ((1u << lane) - 1u));
+        const uint32_t heavy = (uint32_t)code_weight((h << 5) | ewithin);
+        out[at] = make_uint2(xor_bits<9>(h, hhi), (h << 16) | (heavy << 8) | (uint32_t)w);
+      }
+      n += __popc(m);
+    }
+  }
+  __syncwarp();
+  return n;
 }
 
 template <bool kResume>
-__device__ __forceinline__ void search_frame5(const SearchArgs& a, unsigned fi, const FrameRec* rec, const Slice5& sl,
-                                              unsigned long long& my_eval, unsigned long long& my_useful) {
+__device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned fi, const FrameRec* rec,
+                                                  const FlipSlice& sl, unsigned long long& my_eval,
+                                                  unsigned long long& my_useful) {
   const int lane = threadIdx.x & 31;
   const int Sp = rec->sp;
   const int w_done = rec->w_done;
@@ -1708,37 +1457,39 @@ __device__ __forceinline__ void search_frame5(const SearchArgs& a, unsigned fi, 
   const int w_cap = over ? __ffs(over) - 1 : Sp;
   const int w_hi = kResume && a.w_step > 0 ? min(Sp, w_done + a.w_step) : Sp;
   const int w_lim = min(w_cap, w_hi);
-  const int nAr = Sp >> 1;
+  const int nAr = min(Sp >> 1, kFlipSideA), nBr = Sp - nAr;
   // existence bits of both sides' flip vectors (bit 2r: I slot, 2r+1: Q slot)
-  const unsigned exh = __ballot_sync(kFull, lane < Sp && (my_ex & 1u)), exv = __ballot_sync(kFull, lane < Sp && (my_ex & 2u));
+  const unsigned exh = __ballot_sync(kFull, lane < Sp && (my_ex & 1u));
+  const unsigned exv = __ballot_sync(kFull, lane < Sp && (my_ex & 2u));
   uint32_t EA = 0, EB = 0;
 #pragma unroll
-  for (int r = 0; r < 5; ++r) {
-    EA |= (((exh >> r) & 1u) << (2 * r)) | (((exv >> r) & 1u) << (2 * r + 1));
+  for (int r = 0; r < kFlipSideB; ++r) {
+    if (r < kFlipSideA) EA |= (((exh >> r) & 1u) << (2 * r)) | (((exv >> r) & 1u) << (2 * r + 1));
     EB |= (((exh >> (nAr + r)) & 1u) << (2 * r)) | (((exv >> (nAr + r)) & 1u) << (2 * r + 1));
   }
   EA &= (1u << (2 * nAr)) - 1u;
-  EB &= (1u << (2 * (Sp - nAr))) - 1u;
-  // flip projections H_b of both sides (b = 2r + slot)
-  uint32_t HAlo[5], HAhi[5], HBlo[5], HBhi[5];
+  EB &= (1u << (2 * nBr)) - 1u;
+  // flip projections H_b of both sides (b = 2r + slot; 0 where the flip does not exist)
+  uint32_t HAlo[5], HAhi[5], HBlo[5], HBhi[9];
 #pragma unroll
   for (int b = 0; b < 5; ++b) {
     HAlo[b] = ((EA >> b) & 1u) ? sl.dflt[(b >> 1) * 3 + (b & 1)] : 0u;
     HAhi[b] = ((EA >> (b + 5)) & 1u) ? sl.dflt[((b + 5) >> 1) * 3 + ((b + 5) & 1)] : 0u;
     HBlo[b] = ((EB >> b) & 1u) ? sl.dflt[(nAr + (b >> 1)) * 3 + (b & 1)] : 0u;
-    HBhi[b] = ((EB >> (b + 5)) & 1u) ? sl.dflt[(nAr + ((b + 5) >> 1)) * 3 + ((b + 5) & 1)] : 0u;
   }
+#pragma unroll
+  for (int b = 0; b < 9; ++b)
+    HBhi[b] = ((EB >> (b + 5)) & 1u) ? sl.dflt[(nAr + ((b + 5) >> 1)) * 3 + ((b + 5) & 1)] : 0u;
   // visiting orders of the groups
-  uint32_t cumA_v, cumB_v;
-  const int nGA = order_groups(EA >> 5, sl.ordA, &cumA_v);
-  const int nGB = order_groups(EB >> 5, sl.ordB, &cumB_v);
-  (void)cumB_v;
+  uint32_t cumA_v;
+  const int nGA = order_groups_a(EA >> 5, sl.ordA, &cumA_v);
+  const int nGB = order_groups_b(EB >> 5, max(0, 2 * nBr - 5), EB & 31u, HBhi, sl.bgrp);
   const uint32_t WA = __ballot_sync(kFull, ((uint32_t)lane & ~EA & 31u) == 0u);  // valid within-group A bits
   const uint32_t WB = __ballot_sync(kFull, ((uint32_t)lane & ~EB & 31u) == 0u);
   const bool lane_b_ok = (WB >> lane) & 1u;
   const int maxwA = code_weight(EA);
   // bit-planes of the within-group A projections: plane b bit i = bit b of P_i
-  const uint32_t PA = xor_bits5((uint32_t)lane, HAlo);
+  const uint32_t PA = xor_bits<5>((uint32_t)lane, HAlo);
   uint32_t pl[kPlanes];
 #pragma unroll
   for (int b = 0; b < kPlanes; ++b) pl[b] = __ballot_sync(kFull, (PA >> b) & 1u);
@@ -1749,7 +1500,7 @@ __device__ __forceinline__ void search_frame5(const SearchArgs& a, unsigned fi, 
     uint32_t* row = sl.lut + t * kLutStride;
     if (t < nGA) {
       const uint32_t g = sl.ordA[t];
-      const uint32_t cg = f0 ^ xor_bits5(g, HAhi);
+      const uint32_t cg = f0 ^ xor_bits<5>(g, HAhi);
       const uint32_t nwa = ~WA;
 #pragma unroll
       for (int k = 0; k < kLutSets; ++k) {
@@ -1768,14 +1519,8 @@ __device__ __forceinline__ void search_frame5(const SearchArgs& a, unsigned fi, 
       for (int c = 0; c < kLutSets * 16; ++c) row[c] = 0xFFFFFFFFu;
     }
   }
-  // B side: lane pattern P'_lane and, lane s, the group at visiting position s
-  const uint32_t PB = xor_bits5((uint32_t)lane, HBlo);
-  uint32_t cb_s = 0, bw_s = 0;  // C'_h of B group h = ordB[s]; (lightest | heaviest weight << 8)
-  if (lane < nGB) {
-    const uint32_t h = sl.ordB[lane];
-    cb_s = xor_bits5(h, HBhi);
-    bw_s = (uint32_t)group_min_weight(h) | ((uint32_t)code_weight((h << 5) | (EB & 31u)) << 8);
-  }
+  // B side: this lane's within-group vector and its projection P'_lane
+  const uint32_t PB = xor_bits<5>((uint32_t)lane, HBlo);
   __syncwarp();
 
   // --- chunks of two B groups in visiting order, A rows in visiting order ----
@@ -1786,16 +1531,16 @@ __device__ __forceinline__ void search_frame5(const SearchArgs& a, unsigned fi, 
   const unsigned wa_cnt = (unsigned)__popc(WA), wb_cnt = (unsigned)__popc(WB);
   for (int ch = 0; ch < nCh; ++ch) {
     const bool two = 2 * ch + 1 < nGB;
-    const uint32_t bw0 = __shfl_sync(kFull, bw_s, 2 * ch), bw1 = __shfl_sync(kFull, bw_s, min(2 * ch + 1, 31));
-    const uint32_t cb0 = __shfl_sync(kFull, cb_s, 2 * ch), cb1 = __shfl_sync(kFull, cb_s, min(2 * ch + 1, 31));
-    const int wb = (int)(bw0 & 0xFFu);
-    const int wb_hi = (int)max(bw0 >> 8, two ? bw1 >> 8 : 0u);
+    const uint2 b0 = sl.bgrp[2 * ch];
+    const uint2 b1 = two ? sl.bgrp[2 * ch + 1] : b0;
+    const int wb = (int)(b0.y & 0xFFu);
+    const int wb_hi = (int)max((b0.y >> 8) & 0xFFu, (b1.y >> 8) & 0xFFu);
     const int budget = min(best_w, w_lim) - wb;  // heaviest A weight still worth testing
     if (budget < 0) break;                      // later chunks are no lighter
     if (wb_hi + maxwA <= w_done) continue;      // every TEP here was tested before
     LutCmp cmp[kB];
-    cmp[0].load(sl.lut, PB ^ cb0);
-    cmp[1].load(sl.lut, PB ^ cb1);
+    cmp[0].load(sl.lut, PB ^ b0.x);
+    cmp[1].load(sl.lut, PB ^ b1.x);
     // A rows whose lightest weight is <= budget
     int g_end = (int)__shfl_sync(kFull, cumA_v, min(budget, 5));
     int g0 = 0;
@@ -1829,7 +1574,7 @@ __device__ __forceinline__ void search_frame5(const SearchArgs& a, unsigned fi, 
 #pragma unroll
         for (int b = 0; b < kB; ++b) {
           if (!cand[b] || !lane_b_ok || (b == 1 && !two)) continue;
-          const uint32_t y = ((uint32_t)sl.ordB[2 * ch + b] << 5) | (uint32_t)lane;
+          const uint32_t y = (((b == 0 ? b0.y : b1.y) >> 16) << 5) | (uint32_t)lane;
           for (int u = 0; u < kGroupUnroll; ++u) {
             uint32_t c = ~(cmp[b].first_at(g0 + u) | cmp[b].second_at(g0 + u));
             if (c == 0u || g0 + u >= nGA) continue;
@@ -1872,7 +1617,7 @@ __device__ __forceinline__ void search_frame5(const SearchArgs& a, unsigned fi, 
   // --- result ---------------------------------------------------------------
   const bool hit = best_rank != 0xFFFFFFFFu && (uint64_t)best_rank <= (uint64_t)a.cap;
   if (kResume && !hit && w_hi < w_cap) {  // no codeword up to w_hi, weights left below the cap
-    uint32_t tested = __shfl_sync(kFull, cnt, w_hi), done = __shfl_sync(kFull, cnt, w_done);
+    const uint32_t tested = __shfl_sync(kFull, cnt, w_hi), done = __shfl_sync(kFull, cnt, w_done);
     suspend_frame(a, fi, rec, w_hi, tested);
     if (lane == 0) my_useful += tested - done;
     __syncwarp();
@@ -1901,15 +1646,16 @@ __device__ __forceinline__ void search_frame5(const SearchArgs& a, unsigned fi, 
   __syncwarp();
 }
 
-template <int kMinBlocks, int kSide, bool kResume>
+// Persistent warp search: every warp pulls frames from the work queue and
+// searches each in its own slice of shared memory (no block-wide barrier).
+template <int kMinBlocks, bool kResume>
 __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31;
-  char* my_slice = smem_raw + (threadIdx.x >> 5) * (kSide == kWarpSideMax ? slice5_bytes(a.Wmax)
-                                                                          : warp_slice_bytes<kSide>(a.Wmax));
+  const FlipSlice sl =
+      flip_slice(smem_raw + (threadIdx.x >> 5) * flip_slice_bytes(a.Wmax, a.sp_max), a.Wmax, a.sp_max);
   const unsigned n_hard = kResume && a.cur_in ? (unsigned)a.n_cur : *(volatile unsigned*)&a.scr->n_hard;
   unsigned long long my_eval = 0, my_useful = 0;
-  uint32_t lay_key = 0xFFu;  // side sizes whose subset order the slice holds (none yet)
   for (;;) {
     unsigned fi = 0;
     if (lane == 0) fi = atomicAdd(&a.scr->next, 1u);
@@ -1922,10 +1668,7 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
       if (lane == 0) cut = cut_at_deadline(a, rec, out_frame(a, fi, rec));
       if (__shfl_sync(kFull, cut, 0)) continue;
     }
-    if constexpr (kSide == kWarpSideMax)
-      search_frame5<kResume>(a, fi, rec, slice5(my_slice, a.Wmax), my_eval, my_useful);
-    else
-      search_frame<kSide, kResume>(a, fi, rec, warp_slice<kSide>(my_slice, a.Wmax), my_eval, my_useful, lay_key);
+    search_frame_flip<kResume>(a, fi, rec, sl, my_eval, my_useful);
   }
   if (lane == 0) {
     if (my_eval) atomicAdd(&a.scr->evaluated, my_eval);
@@ -1967,7 +1710,7 @@ __device__ __forceinline__ uint32_t hash_slot(uint32_t key) {
 
 template <int kSide>
 __host__ __device__ inline size_t hash_slice_bytes(int Wmax) {
-  return warp_slice_bytes<kSide, false>(Wmax) + 4 * (size_t)HashDims<kSide>::kSlots;
+  return warp_slice_bytes<kSide>(Wmax) + 4 * (size_t)HashDims<kSide>::kSlots;
 }
 
 template <int kSide, bool kResume>
@@ -1976,8 +1719,8 @@ __global__ void __launch_bounds__(128) k_search_hash(SearchArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31;
   char* base = smem_raw + (threadIdx.x >> 5) * hash_slice_bytes<kSide>(a.Wmax);
-  const WarpSlice sl = warp_slice<kSide, false>(base, a.Wmax);
-  uint32_t* hslot = reinterpret_cast<uint32_t*>(base + warp_slice_bytes<kSide, false>(a.Wmax));
+  const WarpSlice sl = warp_slice<kSide>(base, a.Wmax);
+  uint32_t* hslot = reinterpret_cast<uint32_t*>(base + warp_slice_bytes<kSide>(a.Wmax));
   const unsigned n_hard = kResume && a.cur_in ? (unsigned)a.n_cur : *(volatile unsigned*)&a.scr->n_hard;
   unsigned long long my_eval = 0, my_useful = 0;
 
@@ -2790,11 +2533,10 @@ static int launch_search_t(const SearchArgs& s, int threads, size_t smem, cudaSt
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
-template <int B, int Side>
+template <int B>
 static int launch_search_warp_t(const SearchArgs& s, int warps, cudaStream_t st) {
-  constexpr int kSide = Side;
-  const size_t smem = (kSide == kWarpSideMax ? slice5_bytes(s.Wmax) : warp_slice_bytes<kSide>(s.Wmax)) * warps;
-  auto kern = (s.w_step > 0 || s.cur_in) ? k_search_warp<B, kSide, true> : k_search_warp<B, kSide, false>;
+  const size_t smem = flip_slice_bytes(s.Wmax, s.sp_max) * warps;
+  auto kern = (s.w_step > 0 || s.cur_in) ? k_search_warp<B, true> : k_search_warp<B, false>;
   const int per_sm = resident_ctas((const void*)kern, 32 * warps, smem);
   if (per_sm < 0) return GRAND_E_CUDA;
   kern<<<search_grid(per_sm, warps, s.max_entries), 32 * warps, smem, st>>>(s);
@@ -2814,25 +2556,17 @@ static int launch_search_hash_t(const SearchArgs& s, int warps, cudaStream_t st)
 static int launch_search(const SearchArgs& s, int threads, size_t smem, int variant, cudaStream_t st) {
   // the warp-per-frame kernels are compiled for CTAs of at most 4 warps
   const int req_warps = s.warps > 4 ? 4 : s.warps;
-  if (s.warp_kernel == 1) {  // sides of 5 ranks; warps per CTA from the tiles (default 4)
+  if (s.warp_kernel == 1 || s.warp_kernel == 2) {  // flip-bit warp search; warps per CTA from the tiles (default 4)
     const int warps = req_warps > 0 ? req_warps : 4;
-    switch (variant) {
-      case 4: return launch_search_warp_t<4, kWarpSideMax>(s, warps, st);
-      case 8: return launch_search_warp_t<8, kWarpSideMax>(s, warps, st);
-      default: return launch_search_warp_t<6, kWarpSideMax>(s, warps, st);
+    switch (variant) {  // default: 128 registers (shared memory already bounds residency)
+      case 6: return launch_search_warp_t<6>(s, warps, st);
+      case 8: return launch_search_warp_t<8>(s, warps, st);
+      default: return launch_search_warp_t<4>(s, warps, st);
     }
   }
   if (s.warp_kernel == 3 || s.warp_kernel == 4) {  // hash join; warps per CTA from the tiles
     return s.warp_kernel == 3 ? launch_search_hash_t<kWarpSideMax>(s, req_warps > 0 ? req_warps : 4, st)
                               : launch_search_hash_t<kWarpSideMax + 1>(s, req_warps > 0 ? req_warps : 1, st);
-  }
-  if (s.warp_kernel == 2) {  // sides of 6 ranks; warps per CTA from the tiles (default 2)
-    const int warps = req_warps > 0 ? req_warps : 2;
-    switch (variant) {
-      case 6: return launch_search_warp_t<6, kWarpSideMax + 1>(s, warps, st);
-      case 8: return launch_search_warp_t<8, kWarpSideMax + 1>(s, warps, st);
-      default: return launch_search_warp_t<4, kWarpSideMax + 1>(s, warps, st);
-    }
   }
   switch (variant) {
     case 6: return launch_search_t<6>(s, threads, smem, st);
@@ -2848,12 +2582,8 @@ int preload_qam_kernels() {
   const void* kernels[] = {
       (const void*)k_prep<1>, (const void*)k_prep<2>, (const void*)k_prep<4>, (const void*)k_prep<8>,
       (const void*)k_prep<16>,
-      (const void*)k_search_warp<4, kWarpSideMax, false>, (const void*)k_search_warp<6, kWarpSideMax, false>,
-      (const void*)k_search_warp<8, kWarpSideMax, false>, (const void*)k_search_warp<4, kWarpSideMax + 1, false>,
-      (const void*)k_search_warp<6, kWarpSideMax + 1, false>, (const void*)k_search_warp<8, kWarpSideMax + 1, false>,
-      (const void*)k_search_warp<4, kWarpSideMax, true>, (const void*)k_search_warp<6, kWarpSideMax, true>,
-      (const void*)k_search_warp<8, kWarpSideMax, true>, (const void*)k_search_warp<4, kWarpSideMax + 1, true>,
-      (const void*)k_search_warp<6, kWarpSideMax + 1, true>, (const void*)k_search_warp<8, kWarpSideMax + 1, true>,
+      (const void*)k_search_warp<4, false>, (const void*)k_search_warp<6, false>, (const void*)k_search_warp<8, false>,
+      (const void*)k_search_warp<4, true>, (const void*)k_search_warp<6, true>, (const void*)k_search_warp<8, true>,
       (const void*)k_search_hash<kWarpSideMax, false>, (const void*)k_search_hash<kWarpSideMax + 1, false>,
       (const void*)k_search_hash<kWarpSideMax, true>, (const void*)k_search_hash<kWarpSideMax + 1, true>,
       (const void*)k_search<4>, (const void*)k_search<6>, (const void*)k_search<8>};
@@ -2912,8 +2642,8 @@ static int launch_qam_search(const grand_params* p, int Smax, int w0, int Wmax, 
   }
   s.max_tiles = ((s.tabA + kTileRows - 1) / kTileRows) * ((s.tabB + kTileCols - 1) / kTileCols);
   s.Wmax = Wmax;
-  // warp-per-frame bit-sliced search with 5- or 6-rank sides; an explicit
-  // split selects the CTA kernel
+  // warp-per-frame flip-bit search (or the hash join with 5- or 6-rank
+  // sides); an explicit split selects the CTA kernel
   s.warp_kernel = s.split > 0 ? 0 : (Smax <= 2 * kWarpSideMax ? 1 : 2);
   if (p->membership == GRAND_MEMBERSHIP_HASH && s.split <= 0) s.warp_kernel = Smax <= 2 * kWarpSideMax ? 3 : 4;
   s.warps = p->tiles[0] > 0 ? (p->tiles[0] > 8 ? 8 : p->tiles[0]) : 0;

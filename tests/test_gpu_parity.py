@@ -262,9 +262,9 @@ def test_tiles_do_not_change_results(g, oracle_lib, tiles):
 
 @pytest.mark.parametrize("tiles", [(4, 6, 2, 0), (1, 0, 3, 6), (4, 0, 2, 8), (8, 5, 2, 0), (8, 0, 2, 0)])
 def test_tiles_do_not_change_results_s12(g, oracle_lib, tiles):
-    """S' = 12: the warp-per-frame search with 6-rank sides (automatic split,
-    any warps per CTA and register budget) and the CTA search (explicit
-    split) decide identically."""
+    """S' = 12: the warp-per-frame search (5 + 7 ranks, automatic split, any
+    warps per CTA and register budget) and the CTA search (explicit split)
+    decide identically."""
     N, M, S = 512, 64, 12
     code, H, info = code_pair(g, oracle_lib, N)
     d = wl.qam_frames(35, 0, 200, N, info, M, 12.0)
@@ -403,7 +403,7 @@ def test_mixed_batch_parity(g, oracle_lib):
 @pytest.mark.parametrize("membership", [0, 3])
 def test_mixed_batch_s12(g, oracle_lib, membership):
     """S = 12 over an uneven batch: frames of every S' from 3 to 12 go through
-    the search for 6-rank sides (or its hash join) in one launch."""
+    the warp search (or the hash join with 6-rank sides) in one launch."""
     import torch
 
     Ns = (32, 64, 128, 256)

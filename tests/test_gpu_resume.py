@@ -32,7 +32,7 @@ CASES = [
     (128, 16, 10, 1 << 20, 3000, 6.5, 1),
     (128, 16, 10, 1 << 20, 3000, 6.5, 3),
     (128, 16, 10, 5000, 3000, 6.5, 1),      # the cap falls inside weight class 4
-    (512, 64, 12, 1 << 24, 1200, 13.0, 2),  # 6-rank sides
+    (512, 64, 12, 1 << 24, 1200, 13.0, 2),  # 5 + 7 ranks
     (1024, 256, 12, 1 << 20, 600, 16.0, 4),
 ]
 

@@ -74,7 +74,7 @@ def test_noalloc_matches_allocating_call_twice(env):
 
 
 def test_noalloc_matches_allocating_call_s12(env):
-    """S' = 12 (N=512, 64-QAM, cap 2^24): the search stage with 6-rank sides,
+    """S' = 12 (N=512, 64-QAM, cap 2^24): the search stage with a 7-rank B side,
     launched by the same helper as grand_decode_symbols; two calls in a row."""
     import torch
 
