@@ -97,21 +97,22 @@ SMEM_PEAK_GBS = SMS * 128 * MAX_CLOCK_GHZ
 #     nibble-table search reads four table words per 32 TEPs per lane: it is
 #     bound by shared-memory bandwidth);
 #   alu_lane_ops_per_check = ALU pipe busy fraction x elapsed cycles x SMs x
-#     64 lanes / checks (the bit-plane search is bound by the integer pipe).
+#     64 lanes / checks (the bit-level GRAND-AB kernel is bound by the integer
+#     pipe).
 # Everything in the kernel is included in both.
 NCU_SEARCH = {
     "k_search_warp S'<=10": {"sha": "ab8dcb515250d93f", "profile": "profiles/k_search_warp_c2_small.md",
-                             "bound": "smem", "smem_bytes_per_check": 0.5731, "smem_wavefronts_frac": 0.809,
-                             "lsu_pipe_active": 0.877, "alu_lane_ops_per_check": 0.162, "alu_pipe_active": 0.459,
-                             "dram_bytes_per_hard_frame": 1879552 / 11181},
+                             "bound": "smem", "smem_bytes_per_check": 0.5724, "smem_wavefronts_frac": 0.837,
+                             "lsu_pipe_active": 0.900, "alu_lane_ops_per_check": 0.160, "alu_pipe_active": 0.468,
+                             "dram_bytes_per_hard_frame": 1878528 / 11181},
     "k_search_warp S'=12": {"sha": "ab8dcb515250d93f", "profile": "profiles/k_search_warp_c3a_small.md",
-                            "bound": "smem", "smem_bytes_per_check": 0.5531, "smem_wavefronts_frac": 0.782,
-                            "lsu_pipe_active": 0.833, "alu_lane_ops_per_check": 0.141, "alu_pipe_active": 0.399,
-                            "dram_bytes_per_hard_frame": 776704 / 4706},
+                            "bound": "smem", "smem_bytes_per_check": 0.5531, "smem_wavefronts_frac": 0.814,
+                            "lsu_pipe_active": 0.878, "alu_lane_ops_per_check": 0.142, "alu_pipe_active": 0.418,
+                            "dram_bytes_per_hard_frame": 772352 / 4706},
     # the bit-level kernel reads every frame (no hand-off records): bytes per frame
-    "k_ab_split<1,16>": {"sha": "b1d00947d52a7877", "profile": "profiles/k_ab_split_c1_n32_bpsk.md", "bound": "alu",
-                         "alu_lane_ops_per_check": 166.0, "alu_pipe_active": 0.360,
-                         "dram_bytes_per_frame": 1308160 / 10000},
+    "k_ab_split<1,16>": {"sha": "ab8dcb515250d93f", "profile": "profiles/k_ab_split_c1_n32_bpsk.md", "bound": "alu",
+                         "alu_lane_ops_per_check": 165.6, "alu_pipe_active": 0.358,
+                         "dram_bytes_per_frame": 1308416 / 10000},
 }
 
 
