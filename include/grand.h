@@ -142,14 +142,15 @@ typedef enum grand_lik {
  *   query_cap   abandonment threshold, >= 1 valid queries.
  *   lik_variant GRAND_LIK_*.
  *   tiles       launch shape, 0 = automatic: [0] warps per search CTA (1..8
- *               for explicit splits, 1..4 for the warp-per-frame kernels of
- *               S' = 11, 12 and the hash join), [1] A-side ranks of the
- *               search split (1..6; a nonzero value selects the CTA-per-frame
- *               search, 0 the warp-per-frame search with S'/2 ranks on the A
- *               side), [2] number of TEP weights tested by the per-frame
- *               preparation (0..3), [3] register budget of the search kernel
- *               as resident CTAs per SM (4, 6 or 8). Results do not depend on
- *               tiles.
+ *               for explicit splits, 1..4 for the warp-per-frame search and
+ *               the hash join), [1] A-side ranks of the search split (1..6; a
+ *               nonzero value selects the CTA-per-frame search, 0 the
+ *               warp-per-frame search with min(S'/2, 5) ranks on the A side),
+ *               [2] number of TEP weights tested by the per-frame preparation
+ *               (1..3; automatic: 2), [3] register budget of the search kernel as resident
+ *               CTAs of 128 threads per SM (4, 6 or 8; automatic: 4 for the
+ *               warp-per-frame search, whose residency shared memory bounds).
+ *               Results do not depend on tiles.
  *   membership  GRAND_MEMBERSHIP_*.
  *   deadline_ns device-time budget of the call in nanoseconds, 0 = none
  *               (the watchdog). The budget runs from the first look at the
