@@ -94,25 +94,25 @@ SMEM_PEAK_GBS = SMS * 128 * MAX_CLOCK_GHZ
 # profiles/ file named), taken on the decode.cu source with the given sha256
 # prefix. Per TEP check the kernel evaluated in that launch:
 #   smem_bytes_per_check = shared-memory wavefronts x 128 B / checks (the
-#     nibble-table search reads four table words per 32 TEPs per lane: it is
-#     bound by shared-memory bandwidth);
+#     warp search reads three table words per 32 TEPs per lane: it is bound
+#     by shared-memory bandwidth);
 #   alu_lane_ops_per_check = ALU pipe busy fraction x elapsed cycles x SMs x
 #     64 lanes / checks (the bit-level GRAND-AB kernel is bound by the integer
 #     pipe).
 # Everything in the kernel is included in both.
 NCU_SEARCH = {
-    "k_search_warp S'<=10": {"sha": "ab8dcb515250d93f", "profile": "profiles/k_search_warp_c2_small.md",
-                             "bound": "smem", "smem_bytes_per_check": 0.5724, "smem_wavefronts_frac": 0.837,
-                             "lsu_pipe_active": 0.900, "alu_lane_ops_per_check": 0.160, "alu_pipe_active": 0.468,
-                             "dram_bytes_per_hard_frame": 1878528 / 11181},
-    "k_search_warp S'=12": {"sha": "ab8dcb515250d93f", "profile": "profiles/k_search_warp_c3a_small.md",
-                            "bound": "smem", "smem_bytes_per_check": 0.5531, "smem_wavefronts_frac": 0.814,
-                            "lsu_pipe_active": 0.878, "alu_lane_ops_per_check": 0.142, "alu_pipe_active": 0.418,
-                            "dram_bytes_per_hard_frame": 772352 / 4706},
+    "k_search_warp S'<=10": {"sha": "6f9bb098bca101ef", "profile": "profiles/k_search_warp_c2_small.md",
+                             "bound": "smem", "smem_bytes_per_check": 0.4730, "smem_wavefronts_frac": 0.758,
+                             "lsu_pipe_active": 0.807, "alu_lane_ops_per_check": 0.137, "alu_pipe_active": 0.438,
+                             "dram_bytes_per_hard_frame": 1892096 / 11181},
+    "k_search_warp S'=12": {"sha": "6f9bb098bca101ef", "profile": "profiles/k_search_warp_c3a_small.md",
+                            "bound": "smem", "smem_bytes_per_check": 0.4367, "smem_wavefronts_frac": 0.786,
+                            "lsu_pipe_active": 0.805, "alu_lane_ops_per_check": 0.098, "alu_pipe_active": 0.354,
+                            "dram_bytes_per_hard_frame": 776704 / 4706},
     # the bit-level kernel reads every frame (no hand-off records): bytes per frame
-    "k_ab_split<1,16>": {"sha": "ab8dcb515250d93f", "profile": "profiles/k_ab_split_c1_n32_bpsk.md", "bound": "alu",
-                         "alu_lane_ops_per_check": 165.6, "alu_pipe_active": 0.358,
-                         "dram_bytes_per_frame": 1308416 / 10000},
+    "k_ab_split<1,16>": {"sha": "6f9bb098bca101ef", "profile": "profiles/k_ab_split_c1_n32_bpsk.md", "bound": "alu",
+                         "alu_lane_ops_per_check": 166.8, "alu_pipe_active": 0.359,
+                         "dram_bytes_per_frame": 1308160 / 10000},
 }
 
 

@@ -1016,8 +1016,10 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_search(SearchArgs a) {
 constexpr int kWarpSideMax = 5;                      // hash join: the small-table variant (S' <= 10)
 constexpr int kPlanes = 20;                          // projection bits compared per TEP
 constexpr int kGroupUnroll = 8;                      // groups per candidate check
-constexpr int kLutSets = kPlanes / 4;                // nibble tables per group
-constexpr int kLutStride = kLutSets * 16 + 1;        // words per group (odd: conflict-free per-lane stores)
+constexpr int kLutBits = 5;                          // projection bits per table (32 words)
+constexpr int kLutSets = kPlanes / kLutBits;         // tables per group (the last one: second level)
+constexpr int kLutWords = 1 << kLutBits;
+constexpr int kLutStride = kLutSets * kLutWords + 1; // words per group (odd: conflict-free per-lane stores)
 
 // Table sizes of one side for the kSide variant.
 template <int kSide>
@@ -1253,7 +1255,8 @@ struct LutCmp {
   __device__ __forceinline__ void load(const uint32_t* tab, uint32_t z) {
     const uint32_t base = (uint32_t)__cvta_generic_to_shared(tab);
 #pragma unroll
-    for (int k = 0; k < kLutSets; ++k) t[k] = base + 4u * (16u * k + ((z >> (4 * k)) & 15u));
+    for (int k = 0; k < kLutSets; ++k)
+      t[k] = base + 4u * (kLutWords * k + ((z >> (kLutBits * k)) & (kLutWords - 1u)));
   }
   __device__ __forceinline__ void block(int g) {
 #pragma unroll
@@ -1262,18 +1265,18 @@ struct LutCmp {
   template <int U>
   __device__ __forceinline__ uint32_t first() const {
     constexpr int o = 4 * kLutStride * U;
-    return lds_imm<o>(b[0]) | lds_imm<o>(b[1]) | lds_imm<o>(b[2]) | lds_imm<o>(b[3]);
+    return lds_imm<o>(b[0]) | lds_imm<o>(b[1]) | lds_imm<o>(b[2]);
   }
   template <int U>
   __device__ __forceinline__ uint32_t second() const {
-    return lds_imm<4 * kLutStride * U>(b[4]);
+    return lds_imm<4 * kLutStride * U>(b[3]);
   }
   __device__ __forceinline__ uint32_t first_at(int g) const {
     const uint32_t o = 4u * kLutStride * (uint32_t)g;
-    return lds_imm<0>(t[0] + o) | lds_imm<0>(t[1] + o) | lds_imm<0>(t[2] + o) | lds_imm<0>(t[3] + o);
+    return lds_imm<0>(t[0] + o) | lds_imm<0>(t[1] + o) | lds_imm<0>(t[2] + o);
   }
   __device__ __forceinline__ uint32_t second_at(int g) const {
-    return lds_imm<0>(t[4] + 4u * kLutStride * (uint32_t)g);
+    return lds_imm<0>(t[3] + 4u * kLutStride * (uint32_t)g);
   }
 };
 
@@ -1321,10 +1324,10 @@ __host__ __device__ inline int flip_b_groups(int sp_max) {
 }
 
 struct FlipSlice {
-  uint32_t* lut;    // [32][kLutStride] nibble tables of the A groups in visiting order
+  uint32_t* lut;    // [32][kLutStride] tables of the A groups in visiting order
   uint2* bgrp;      // [flip_b_groups] B groups in visiting order: (C'_h, h << 16 | heaviest << 8 | lightest)
-  uint32_t* delta;  // [kSMax][3][Wmax] full syndrome deltas
   uint32_t* dflt;   // [kSMax][3] projections of the deltas
+  uint32_t* d0;     // [kSMax][3] first syndrome word of the deltas
   uint32_t* E;      // [kEStride^2]
   uint32_t* s0;     // [Wmax]
   uint8_t* ordA;    // [32] A group at visiting position t
@@ -1332,8 +1335,11 @@ struct FlipSlice {
   uint16_t* pos;    // [kSMax][2]
 };
 
+// (Of the full syndrome deltas only the first word is kept: the rare
+// candidates of the projection compare are rejected on it, and a candidate
+// that passes reads the code's columns for the other words.)
 __host__ __device__ inline size_t flip_slice_bytes(int Wmax, int sp_max) {
-  const size_t words = 32 * kLutStride + 2 * (size_t)flip_b_groups(sp_max) + 3 * kSMax * (size_t)Wmax + 3 * kSMax +
+  const size_t words = 32 * kLutStride + 2 * (size_t)flip_b_groups(sp_max) + 3 * kSMax + 3 * kSMax +
                        kEStride * kEStride + Wmax + 8 + 4 + kSMax;
   return (words * 4 + 15) & ~(size_t)15;
 }
@@ -1343,8 +1349,8 @@ __device__ inline FlipSlice flip_slice(char* base, int Wmax, int sp_max) {
   uint32_t* p = reinterpret_cast<uint32_t*>(base);
   w.lut = p; p += 32 * kLutStride;  // even: the B-group list is 8-byte aligned
   w.bgrp = reinterpret_cast<uint2*>(p); p += 2 * flip_b_groups(sp_max);
-  w.delta = p; p += 3 * kSMax * Wmax;
   w.dflt = p; p += 3 * kSMax;
+  w.d0 = p; p += 3 * kSMax;
   w.E = p; p += kEStride * kEStride;
   w.s0 = p; p += Wmax;
   w.ordA = reinterpret_cast<uint8_t*>(p); p += 8;
@@ -1433,16 +1439,14 @@ __device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned 
   if (lane < W) sl.s0[lane] = rec->s0[lane];
   const uint32_t f0 = rec->f0;
   __syncwarp();
-  // deltas of rank r's alternatives (h, v, diag) on every syndrome word and
-  // their projections: lane t = 3 r + alt
+  // projections and first syndrome words of rank r's alternatives (h, v,
+  // diag): lane t = 3 r + alt
   for (int t = lane; t < 3 * Sp; t += 32) {
     const int r = t / 3, alt = t - 3 * (t / 3);
     const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
     const bool useI = alt != 1 && pI != kNoPos, useQ = alt != 0 && pQ != kNoPos;
     sl.dflt[t] = (useI ? __ldg(code.hf + pI) : 0u) ^ (useQ ? __ldg(code.hf + pQ) : 0u);
-    for (int w = 0; w < W; ++w)
-      sl.delta[t * W + w] = (useI ? __ldg(code.hcol + (size_t)pI * W + w) : 0u) ^
-                            (useQ ? __ldg(code.hcol + (size_t)pQ * W + w) : 0u);
+    sl.d0[t] = (useI ? __ldg(code.hcol + (size_t)pI * W) : 0u) ^ (useQ ? __ldg(code.hcol + (size_t)pQ * W) : 0u);
   }
   esp_table_warp(sl.ex, Sp, sl.E);
   __syncwarp();
@@ -1504,19 +1508,20 @@ __device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned 
       const uint32_t nwa = ~WA;
 #pragma unroll
       for (int k = 0; k < kLutSets; ++k) {
-        const uint32_t q0 = pl[4 * k + 0] ^ (0u - ((cg >> (4 * k + 0)) & 1u));
-        const uint32_t q1 = pl[4 * k + 1] ^ (0u - ((cg >> (4 * k + 1)) & 1u));
-        const uint32_t q2 = pl[4 * k + 2] ^ (0u - ((cg >> (4 * k + 2)) & 1u));
-        const uint32_t q3 = pl[4 * k + 3] ^ (0u - ((cg >> (4 * k + 3)) & 1u));
+        uint32_t q[kLutBits];
 #pragma unroll
-        for (int v = 0; v < 16; ++v)
-          row[16 * k + v] = ((q0 ^ ((v & 1) ? 0xFFFFFFFFu : 0u)) | (q1 ^ ((v & 2) ? 0xFFFFFFFFu : 0u)) |
-                             (q2 ^ ((v & 4) ? 0xFFFFFFFFu : 0u))) |
-                            ((q3 ^ ((v & 8) ? 0xFFFFFFFFu : 0u)) | nwa);
+        for (int j = 0; j < kLutBits; ++j) q[j] = pl[kLutBits * k + j] ^ (0u - ((cg >> (kLutBits * k + j)) & 1u));
+#pragma unroll
+        for (int v = 0; v < kLutWords; ++v) {
+          uint32_t w = nwa;
+#pragma unroll
+          for (int j = 0; j < kLutBits; ++j) w |= q[j] ^ (((v >> j) & 1) ? 0xFFFFFFFFu : 0u);
+          row[kLutWords * k + v] = w;
+        }
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < kLutSets * 16; ++c) row[c] = 0xFFFFFFFFu;
+      for (int c = 0; c < kLutSets * kLutWords; ++c) row[c] = 0xFFFFFFFFu;
     }
   }
   // B side: this lane's within-group vector and its projection P'_lane
@@ -1584,12 +1589,21 @@ __device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned 
               c &= c - 1;
               const uint32_t cc = (xg | (uint32_t)i) | (y << (2 * nAr));
               if (kResume && code_weight(cc) > w_hi) continue;  // beyond this call's window
-              uint32_t orr = 0;
-              for (int w = 0; w < W; ++w) {
+              // the full syndrome s0 ^ (the H columns the TEP flips), word by
+              // word: the first from the kept deltas (a false match of the
+              // projection fails there), the others from the code's columns
+              uint32_t orr = sl.s0[0];
+              for (int r = 0; r < Sp; ++r) {
+                const uint32_t d = (cc >> (2 * r)) & 3u;
+                if (d) orr ^= sl.d0[r * 3 + (d - 1)];
+              }
+              for (int w = 1; w < W && orr == 0; ++w) {
                 uint32_t zz = sl.s0[w];
                 for (int r = 0; r < Sp; ++r) {
                   const uint32_t d = (cc >> (2 * r)) & 3u;
-                  if (d) zz ^= sl.delta[((size_t)r * 3 + (d - 1)) * W + w];
+                  const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
+                  if ((d & 1u) && pI != kNoPos) zz ^= __ldg(code.hcol + (size_t)pI * W + w);
+                  if ((d & 2u) && pQ != kNoPos) zz ^= __ldg(code.hcol + (size_t)pQ * W + w);
                 }
                 orr |= zz;
               }
