@@ -1002,16 +1002,16 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_search(SearchArgs a) {
 //
 // The warp search compares a B entry with 32 A entries at once on a 20-bit
 // projection of the syndrome (false matches 2^-20; candidates are verified on
-// every syndrome word). Each A group of 32 entries keeps, per nibble k of the
-// projection (bit-planes 4k..4k+3), the 16 words
-//     T[k][v] = OR_{j<4} (plane_{4k+j} XOR (bit j of v ? ~0 : 0)),
+// every syndrome word). Each A group of 32 entries keeps, per 5-bit slice k
+// of the projection (bit-planes 5k..5k+4), the 32 words
+//     T[k][v] = OR_{j<5} (plane_{5k+j} XOR (bit j of v ? ~0 : 0)),
 // so a lane with B projection z gets
-//     acc = T[0][z & 15] | T[1][(z >> 4) & 15] | T[2][...] | T[3][...],
-// zero exactly at the A entries equal to z on 16 bits: four shared-memory
-// reads and two logic ops test 32 TEPs (the last nibble only after a match).
-// The 16 words of a nibble sit in 16 distinct banks, so any pattern of lane
+//     acc = T[0][z & 31] | T[1][(z >> 5) & 31] | T[2][(z >> 10) & 31],
+// zero exactly at the A entries equal to z on 15 bits: three shared-memory
+// reads and one logic op test 32 TEPs (the fourth slice only after a match).
+// The 32 words of a slice sit in 32 distinct banks, so any pattern of lane
 // reads is conflict-free; the kernel is bound by shared-memory bandwidth
-// (0.5 B per TEP).
+// (0.375 B per TEP).
 // ---------------------------------------------------------------------------
 constexpr int kWarpSideMax = 5;                      // hash join: the small-table variant (S' <= 10)
 constexpr int kPlanes = 20;                          // projection bits compared per TEP
@@ -1236,9 +1236,9 @@ __device__ inline void warp_fill_side(const WarpSlice& sl, int r0, int n, const 
   __syncwarp();
 }
 
-// The compare of one lane's B entry z against the A groups' nibble tables:
+// The compare of one lane's B entry z against the A groups' tables:
 // block(g0) fixes the first group of a block of kGroupUnroll groups;
-// first<U>() (nibbles 0..3) and second<U>() (nibble 4) then read group g0 + U
+// first<U>() (slices 0..2) and second<U>() (slice 3) then read group g0 + U
 // with immediate offsets; first_at / second_at read any group (candidates).
 //
 // 32-bit shared-memory read at a shared-window address plus an immediate.
@@ -1250,7 +1250,7 @@ __device__ __forceinline__ uint32_t lds_imm(uint32_t addr) {
 }
 
 struct LutCmp {
-  uint32_t t[kLutSets];  // shared-window address of the word of nibble k of z in group 0
+  uint32_t t[kLutSets];  // shared-window address of the word of slice k of z in group 0
   uint32_t b[kLutSets];  // the same in group g0 of the current block
   __device__ __forceinline__ void load(const uint32_t* tab, uint32_t z) {
     const uint32_t base = (uint32_t)__cvta_generic_to_shared(tab);
@@ -1301,7 +1301,7 @@ __device__ __forceinline__ void static_for(F&& f) {
 // A side's vectors are cut as x = 32 g + i: i (bits 0..4) within a group, g
 // (the higher bits) the group. Within group g the projections are C_g ^ P_i,
 // with P_i = XOR_{b < 5, b in i} H_b the same for every group, so
-//   * the A side (at most 5 ranks: 32 groups) keeps one row of nibble tables
+//   * the A side (at most 5 ranks: 32 groups) keeps one row of slice tables
 //     per group, derived from the 20 bit-planes of P (one set of warp ballots)
 //     inverted at the bits of C_g -- no per-group transposes and no table of
 //     projections;
