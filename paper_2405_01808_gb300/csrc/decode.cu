@@ -268,6 +268,15 @@ __device__ __forceinline__ uint32_t projection(uint32_t f0, const uint32_t* dflt
 
 constexpr int kPrepMaxW0 = 3;  // TEP weights the preparation can test in canonical order
 
+// C(n, k) for 0 <= k <= 3 by integer arithmetic (0 when n < k): the lanes of
+// the preparation's unranking hold different n, where a table read would be
+// serialised.
+__device__ __forceinline__ uint32_t binom_le3(int n, int k) {
+  if (n < k) return 0u;
+  const uint32_t m = (uint32_t)n;
+  return k == 0 ? 1u : (k == 1 ? m : (k == 2 ? m * (m - 1) / 2u : m * (m - 1) * (m - 2) / 6u));
+}
+
 // One frame of the preparation (one warp). Returns true when the frame needs
 // the search stage; its hand-off record then went to a fresh slot of the
 // batch's record array. WM: compile-time bound on the syndrome words
@@ -499,9 +508,9 @@ __device__ __forceinline__ bool prep_frame(const PrepArgs& a, const int64_t f, c
 #pragma unroll
             for (int jj = kPrepMaxW0; jj >= 1; --jj) {
               if (jj > w) continue;
-              while (binom16(p, jj) > rem) --p;
+              while (binom_le3(p, jj) > rem) --p;
               P[jj - 1] = p;
-              rem -= binom16(p, jj);
+              rem -= binom_le3(p, jj);
               --p;
             }
             // alternatives in base-3 order, least significant digit first
