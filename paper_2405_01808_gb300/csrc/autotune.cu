@@ -29,13 +29,13 @@ void shapes(int S, int membership, std::vector<Candidate>& out) {
     for (int warps : S <= 10 ? std::initializer_list<int>{2, 4} : std::initializer_list<int>{1, 2})
       for (int w0 : {1, 2, 3}) out.push_back({{warps, 0, w0, 0}, membership});
   } else if (S <= 10) {
-    // warp-per-frame search: prep weights x register budget
+    // warp search (warp pairs sharing a frame): prep weights x register budget
     for (int w0 : {1, 2, 3})
       for (int regs : {4, 6, 8}) out.push_back({{0, 0, w0, regs}, membership});
   } else {
-    // warp-per-frame search with 6-rank sides: warps per CTA x prep weights x
-    // register budget
-    for (int warps : {1, 2, 4})
+    // warp search with a 7-rank B side: warp pairs or one warp per frame
+    // (CTAs of 1, 2, 4 warps) x prep weights x register budget
+    for (int warps : {0, 1, 2, 4})
       for (int w0 : {2, 3})
         for (int regs : {4, 6}) out.push_back({{warps, 0, w0, regs}, membership});
   }

@@ -1384,7 +1384,7 @@ __device__ __forceinline__ uint32_t xor_bits(uint32_t x, const uint32_t (&h)[N])
 // most 32 groups): by lightest weight, then by index. Writes ord[0..n) and
 // returns n; lane w (w <= 5) gets in *cum the number of groups of lightest
 // weight <= w.
-__device__ __forceinline__ int order_groups_a(uint32_t ehi, uint8_t* ord, uint32_t* cum) {
+__device__ __forceinline__ int order_groups_a(uint32_t ehi, uint8_t* ord, uint32_t* cum, bool write = true) {
   const int lane = threadIdx.x & 31;
   const bool valid = ((uint32_t)lane & ~ehi) == 0u;
   const int mw = group_min_weight((uint32_t)lane);
@@ -1397,7 +1397,7 @@ __device__ __forceinline__ int order_groups_a(uint32_t ehi, uint8_t* ord, uint32
     if (lane == w) c = (uint32_t)n;
   }
   if (lane > 3) c = (uint32_t)n;
-  if (valid) ord[my] = (uint8_t)lane;
+  if (valid && write) ord[my] = (uint8_t)lane;
   *cum = c;
   __syncwarp();
   return n;
@@ -1429,36 +1429,63 @@ __device__ inline int order_groups_b(uint32_t ehi, int nbits, uint32_t ewithin, 
   return n;
 }
 
-template <bool kResume>
+// State of the warp pair that shares one frame (pair mode: a CTA of two
+// warps, one slice of shared memory).
+struct PairShared {
+  unsigned fi;            // the frame the pair works on
+  int flag;               // a per-frame decision of warp 0 (cursor valid, deadline cut)
+  int best_w;             // lightest hit weight found by either warp
+  int nGB;                // valid B groups (ordered by warp 1)
+  uint32_t best_rank[2];  // each warp's first hit
+  uint32_t best_code[2];
+};
+
+// Block-wide barrier in pair mode, warp barrier otherwise.
+template <bool kPair>
+__device__ __forceinline__ void pair_sync() {
+  if constexpr (kPair) __syncthreads(); else __syncwarp();
+}
+
+// The search of one frame. kPair: two warps of a CTA share the frame and its
+// tables -- warp 0 writes the per-frame arrays and the A rows while warp 1
+// orders the B groups, and the chunks then alternate between the warps (the
+// lightest hit weight is shared, so either warp's hit tightens the other's
+// cut-off); warp 0 reports the lower of the two first hits. Every barrier is
+// reached by both warps.
+template <bool kResume, bool kPair>
 __device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned fi, const FrameRec* rec,
                                                   const FlipSlice& sl, unsigned long long& my_eval,
-                                                  unsigned long long& my_useful) {
+                                                  unsigned long long& my_useful, PairShared* ps) {
   const int lane = threadIdx.x & 31;
+  const int wid = kPair ? (int)((threadIdx.x >> 5) & 1) : 0;
   const int Sp = rec->sp;
   const int w_done = rec->w_done;
   const CodeDev code = a.codes[rec->code];
   const int W = code.W;
-  uint32_t my_ex = 0;
-  if (lane < Sp) {
-    my_ex = rec->ex[lane];
-    sl.ex[lane] = (uint8_t)my_ex;
-    sl.pos[2 * lane] = rec->pos[lane][0];
-    sl.pos[2 * lane + 1] = rec->pos[lane][1];
+  const uint32_t my_ex = lane < Sp ? (uint32_t)rec->ex[lane] : 0u;
+  if (wid == 0) {
+    if (lane < Sp) {
+      sl.ex[lane] = (uint8_t)my_ex;
+      sl.pos[2 * lane] = rec->pos[lane][0];
+      sl.pos[2 * lane + 1] = rec->pos[lane][1];
+    }
+    if (lane < W) sl.s0[lane] = rec->s0[lane];
   }
-  if (lane < W) sl.s0[lane] = rec->s0[lane];
   const uint32_t f0 = rec->f0;
-  __syncwarp();
-  // projections and first syndrome words of rank r's alternatives (h, v,
-  // diag): lane t = 3 r + alt
-  for (int t = lane; t < 3 * Sp; t += 32) {
-    const int r = t / 3, alt = t - 3 * (t / 3);
-    const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
-    const bool useI = alt != 1 && pI != kNoPos, useQ = alt != 0 && pQ != kNoPos;
-    sl.dflt[t] = (useI ? __ldg(code.hf + pI) : 0u) ^ (useQ ? __ldg(code.hf + pQ) : 0u);
-    sl.d0[t] = (useI ? __ldg(code.hcol + (size_t)pI * W) : 0u) ^ (useQ ? __ldg(code.hcol + (size_t)pQ * W) : 0u);
+  pair_sync<kPair>();
+  if (wid == 0) {
+    // projections and first syndrome words of rank r's alternatives (h, v,
+    // diag): lane t = 3 r + alt
+    for (int t = lane; t < 3 * Sp; t += 32) {
+      const int r = t / 3, alt = t - 3 * (t / 3);
+      const uint16_t pI = sl.pos[2 * r], pQ = sl.pos[2 * r + 1];
+      const bool useI = alt != 1 && pI != kNoPos, useQ = alt != 0 && pQ != kNoPos;
+      sl.dflt[t] = (useI ? __ldg(code.hf + pI) : 0u) ^ (useQ ? __ldg(code.hf + pQ) : 0u);
+      sl.d0[t] = (useI ? __ldg(code.hcol + (size_t)pI * W) : 0u) ^ (useQ ? __ldg(code.hcol + (size_t)pQ * W) : 0u);
+    }
+    esp_table_warp(sl.ex, Sp, sl.E);
   }
-  esp_table_warp(sl.ex, Sp, sl.E);
-  __syncwarp();
+  pair_sync<kPair>();
   // valid TEPs of weight <= v (lane v, a warp scan); the cap's weight class
   uint32_t cnt = lane <= Sp ? sl.E[Sp * kEStride + lane] : 0u;
   for (int o = 1; o < 32; o <<= 1) {
@@ -1493,10 +1520,12 @@ __device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned 
 #pragma unroll
   for (int b = 0; b < 9; ++b)
     HBhi[b] = ((EB >> (b + 5)) & 1u) ? sl.dflt[(nAr + ((b + 5) >> 1)) * 3 + ((b + 5) & 1)] : 0u;
-  // visiting orders of the groups
+  // visiting orders of the groups (pair mode: warp 0 writes the A order,
+  // warp 1 the B list)
   uint32_t cumA_v;
-  const int nGA = order_groups_a(EA >> 5, sl.ordA, &cumA_v);
-  const int nGB = order_groups_b(EB >> 5, max(0, 2 * nBr - 5), EB & 31u, HBhi, sl.bgrp);
+  const int nGA = order_groups_a(EA >> 5, sl.ordA, &cumA_v, wid == 0);
+  int nGB = 0;
+  if (!kPair || wid == 1) nGB = order_groups_b(EB >> 5, max(0, 2 * nBr - 5), EB & 31u, HBhi, sl.bgrp);
   const uint32_t WA = __ballot_sync(kFull, ((uint32_t)lane & ~EA & 31u) == 0u);  // valid within-group A bits
   const uint32_t WB = __ballot_sync(kFull, ((uint32_t)lane & ~EB & 31u) == 0u);
   const bool lane_b_ok = (WB >> lane) & 1u;
@@ -1508,7 +1537,7 @@ __device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned 
   for (int b = 0; b < kPlanes; ++b) pl[b] = __ballot_sync(kFull, (PA >> b) & 1u);
   // table row t (lane t): A group g = ordA[t], planes inverted at the bits of
   // C_g = f0 ^ XOR_{b in g} H_{5+b}; rows past the valid groups never match
-  {
+  if (wid == 0) {
     const int t = lane;
     uint32_t* row = sl.lut + t * kLutStride;
     if (t < nGA) {
@@ -1535,7 +1564,12 @@ __device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned 
   }
   // B side: this lane's within-group vector and its projection P'_lane
   const uint32_t PB = xor_bits<5>((uint32_t)lane, HBlo);
-  __syncwarp();
+  if constexpr (kPair) {
+    if (wid == 1 && lane == 0) ps->nGB = nGB;
+    if (wid == 0 && lane == 0) ps->best_w = 127;
+  }
+  pair_sync<kPair>();
+  if constexpr (kPair) nGB = ps->nGB;
 
   // --- chunks of two B groups in visiting order, A rows in visiting order ----
   constexpr int kB = 2;
@@ -1543,12 +1577,13 @@ __device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned 
   int best_w = 127;
   const int nCh = (nGB + 1) / 2;
   const unsigned wa_cnt = (unsigned)__popc(WA), wb_cnt = (unsigned)__popc(WB);
-  for (int ch = 0; ch < nCh; ++ch) {
+  for (int ch = wid; ch < nCh; ch += kPair ? 2 : 1) {
     const bool two = 2 * ch + 1 < nGB;
     const uint2 b0 = sl.bgrp[2 * ch];
     const uint2 b1 = two ? sl.bgrp[2 * ch + 1] : b0;
     const int wb = (int)(b0.y & 0xFFu);
     const int wb_hi = (int)max((b0.y >> 8) & 0xFFu, (b1.y >> 8) & 0xFFu);
+    if constexpr (kPair) best_w = min(best_w, *(volatile int*)&ps->best_w);
     const int budget = min(best_w, w_lim) - wb;  // heaviest A weight still worth testing
     if (budget < 0) break;                      // later chunks are no lighter
     if (wb_hi + maxwA <= w_done) continue;      // every TEP here was tested before
@@ -1628,7 +1663,8 @@ __device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned 
           const unsigned who = __ballot_sync(kFull, lr == wr);
           best_code = __shfl_sync(kFull, lc, __ffs(who) - 1);
           best_rank = wr;
-          best_w = code_weight(best_code);
+          best_w = min(best_w, code_weight(best_code));
+          if (kPair && lane == 0) atomicMin(&ps->best_w, best_w);
           const int nb = min(best_w, w_lim) - wb;
           g_end = nb < 0 ? 0 : min(g_end, (int)__shfl_sync(kFull, cumA_v, min(nb, 5)));
         }
@@ -1636,6 +1672,18 @@ __device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned 
     }
     if (lane == 0)
       my_eval += (unsigned long long)min(g0, nGA) * wa_cnt * (unsigned long long)(wb_cnt * (two ? 2u : 1u));
+  }
+  if constexpr (kPair) {  // the lower of the two warps' first hits
+    if (lane == 0) {
+      ps->best_rank[wid] = best_rank;
+      ps->best_code[wid] = best_code;
+    }
+    __syncthreads();
+    if (wid == 1) return;
+    if (ps->best_rank[1] < best_rank) {
+      best_rank = ps->best_rank[1];
+      best_code = ps->best_code[1];
+    }
   }
   // --- result ---------------------------------------------------------------
   const bool hit = best_rank != 0xFFFFFFFFu && (uint64_t)best_rank <= (uint64_t)a.cap;
@@ -1669,29 +1717,62 @@ __device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned 
   __syncwarp();
 }
 
-// Persistent warp search: every warp pulls frames from the work queue and
-// searches each in its own slice of shared memory (no block-wide barrier).
-template <int kMinBlocks, bool kResume>
+// Persistent warp search: every warp (kPair: every pair of warps, one per
+// CTA) pulls frames from the work queue and searches each in its own slice of
+// shared memory. In pair mode the per-frame decisions are taken by thread 0 /
+// warp 0 and read by both warps after a block barrier, so both reach every
+// barrier.
+template <int kMinBlocks, bool kResume, bool kPair>
 __global__ void __launch_bounds__(128, kMinBlocks) k_search_warp(SearchArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
+  __shared__ PairShared ps;
   const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
   const FlipSlice sl =
-      flip_slice(smem_raw + (threadIdx.x >> 5) * flip_slice_bytes(a.Wmax, a.sp_max), a.Wmax, a.sp_max);
+      flip_slice(smem_raw + (kPair ? 0 : wid) * flip_slice_bytes(a.Wmax, a.sp_max), a.Wmax, a.sp_max);
   const unsigned n_hard = kResume && a.cur_in ? (unsigned)a.n_cur : *(volatile unsigned*)&a.scr->n_hard;
   unsigned long long my_eval = 0, my_useful = 0;
   for (;;) {
     unsigned fi = 0;
-    if (lane == 0) fi = atomicAdd(&a.scr->next, 1u);
-    fi = __shfl_sync(kFull, fi, 0);
-    if (fi >= n_hard) break;
-    const FrameRec* rec = kResume ? queue_entry(a, fi) : a.recs + fi;
-    if (!rec) continue;
-    if (a.deadline > 0) {
-      int cut = 0;
-      if (lane == 0) cut = cut_at_deadline(a, rec, out_frame(a, fi, rec));
-      if (__shfl_sync(kFull, cut, 0)) continue;
+    const FrameRec* rec = nullptr;
+    if constexpr (kPair) {
+      if (threadIdx.x == 0) ps.fi = atomicAdd(&a.scr->next, 1u);
+      __syncthreads();
+      fi = ps.fi;
+      __syncthreads();
+      if (fi >= n_hard) break;
+      if (kResume && a.cur_in) {  // cursor validation by warp 0
+        int ok = 0;
+        if (wid == 0) ok = queue_entry(a, fi) != nullptr;
+        if (threadIdx.x == 0) ps.flag = ok;
+        __syncthreads();
+        ok = ps.flag;
+        __syncthreads();
+        if (!ok) continue;
+        rec = a.cur_in + fi;
+      } else {
+        rec = a.recs + fi;
+      }
+      if (a.deadline > 0) {
+        if (threadIdx.x == 0) ps.flag = cut_at_deadline(a, rec, out_frame(a, fi, rec)) ? 1 : 0;
+        __syncthreads();
+        const int cut = ps.flag;
+        __syncthreads();
+        if (cut) continue;
+      }
+    } else {
+      if (lane == 0) fi = atomicAdd(&a.scr->next, 1u);
+      fi = __shfl_sync(kFull, fi, 0);
+      if (fi >= n_hard) break;
+      rec = kResume ? queue_entry(a, fi) : a.recs + fi;
+      if (!rec) continue;
+      if (a.deadline > 0) {
+        int cut = 0;
+        if (lane == 0) cut = cut_at_deadline(a, rec, out_frame(a, fi, rec));
+        if (__shfl_sync(kFull, cut, 0)) continue;
+      }
     }
-    search_frame_flip<kResume>(a, fi, rec, sl, my_eval, my_useful);
+    search_frame_flip<kResume, kPair>(a, fi, rec, sl, my_eval, my_useful, &ps);
   }
   if (lane == 0) {
     if (my_eval) atomicAdd(&a.scr->evaluated, my_eval);
@@ -2556,13 +2637,19 @@ static int launch_search_t(const SearchArgs& s, int threads, size_t smem, cudaSt
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
+// warps = 0: pair mode (CTAs of two warps sharing each frame); else CTAs of
+// `warps` warps, one frame per warp.
 template <int B>
 static int launch_search_warp_t(const SearchArgs& s, int warps, cudaStream_t st) {
-  const size_t smem = flip_slice_bytes(s.Wmax, s.sp_max) * warps;
-  auto kern = (s.w_step > 0 || s.cur_in) ? k_search_warp<B, true> : k_search_warp<B, false>;
-  const int per_sm = resident_ctas((const void*)kern, 32 * warps, smem);
+  const bool res = s.w_step > 0 || s.cur_in;
+  const bool pair = warps == 0;
+  const size_t smem = flip_slice_bytes(s.Wmax, s.sp_max) * (pair ? 1 : warps);
+  auto kern = pair ? (res ? k_search_warp<B, true, true> : k_search_warp<B, false, true>)
+                   : (res ? k_search_warp<B, true, false> : k_search_warp<B, false, false>);
+  const int threads = pair ? 64 : 32 * warps;
+  const int per_sm = resident_ctas((const void*)kern, threads, smem);
   if (per_sm < 0) return GRAND_E_CUDA;
-  kern<<<search_grid(per_sm, warps, s.max_entries), 32 * warps, smem, st>>>(s);
+  kern<<<search_grid(per_sm, pair ? 1 : warps, s.max_entries), threads, smem, st>>>(s);
   return cudaGetLastError() == cudaSuccess ? GRAND_OK : GRAND_E_CUDA;
 }
 
@@ -2579,9 +2666,9 @@ static int launch_search_hash_t(const SearchArgs& s, int warps, cudaStream_t st)
 static int launch_search(const SearchArgs& s, int threads, size_t smem, int variant, cudaStream_t st) {
   // the warp-per-frame kernels are compiled for CTAs of at most 4 warps
   const int req_warps = s.warps > 4 ? 4 : s.warps;
-  if (s.warp_kernel == 1 || s.warp_kernel == 2) {  // flip-bit warp search; warps per CTA from the tiles (default 4)
-    const int warps = req_warps > 0 ? req_warps : 4;
-    switch (variant) {  // default: 128 registers (shared memory already bounds residency)
+  if (s.warp_kernel == 1 || s.warp_kernel == 2) {  // flip-bit warp search; warps per CTA from the tiles
+    const int warps = req_warps > 0 ? req_warps : 0;   // automatic: warp pairs sharing a frame
+    switch (variant) {  // default: 128 registers
       case 6: return launch_search_warp_t<6>(s, warps, st);
       case 8: return launch_search_warp_t<8>(s, warps, st);
       default: return launch_search_warp_t<4>(s, warps, st);
@@ -2605,8 +2692,12 @@ int preload_qam_kernels() {
   const void* kernels[] = {
       (const void*)k_prep<1>, (const void*)k_prep<2>, (const void*)k_prep<4>, (const void*)k_prep<8>,
       (const void*)k_prep<16>,
-      (const void*)k_search_warp<4, false>, (const void*)k_search_warp<6, false>, (const void*)k_search_warp<8, false>,
-      (const void*)k_search_warp<4, true>, (const void*)k_search_warp<6, true>, (const void*)k_search_warp<8, true>,
+      (const void*)k_search_warp<4, false, false>, (const void*)k_search_warp<6, false, false>,
+      (const void*)k_search_warp<8, false, false>, (const void*)k_search_warp<4, true, false>,
+      (const void*)k_search_warp<6, true, false>, (const void*)k_search_warp<8, true, false>,
+      (const void*)k_search_warp<4, false, true>, (const void*)k_search_warp<6, false, true>,
+      (const void*)k_search_warp<8, false, true>, (const void*)k_search_warp<4, true, true>,
+      (const void*)k_search_warp<6, true, true>, (const void*)k_search_warp<8, true, true>,
       (const void*)k_search_hash<kWarpSideMax, false>, (const void*)k_search_hash<kWarpSideMax + 1, false>,
       (const void*)k_search_hash<kWarpSideMax, true>, (const void*)k_search_hash<kWarpSideMax + 1, true>,
       (const void*)k_search<4>, (const void*)k_search<6>, (const void*)k_search<8>};
