@@ -1093,28 +1093,25 @@ __device__ inline WarpSlice warp_slice(char* base, int Wmax) {
 // Layout of one side's table, computed by one warp. Subsets of the side's n
 // ranks are laid out by (size, colex order), i.e. by TEP weight; the k-th
 // subset's entries start at start[k]; cum[v] = entries of weight <= v.
-// Returns the number of entries. The subset order (ord, inv) depends on n
-// only: ord_ready says it is already in place from an earlier frame.
+// Returns the number of entries.
 __device__ inline unsigned warp_side_layout(const WarpSlice& sl, int r0, int n, uint32_t* start, uint8_t* ord,
-                                            uint8_t* inv, uint32_t* cum, bool ord_ready = false) {
+                                            uint8_t* inv, uint32_t* cum) {
   const int lane = threadIdx.x & 31;
   const int nsub = 1 << n;  // <= 64: two subsets per lane
-  if (!ord_ready) {
-    for (int sb = lane; sb < nsub; sb += 32) {
-      int w = 0, colex = 0;
-      for (int j = 0; j < n; ++j)
-        if ((sb >> j) & 1) {
-          ++w;
-          colex += (int)binom16(j, w);
-        }
-      int before = 0;
-      for (int v = 0; v < w; ++v) before += (int)binom16(n, v);
-      const int posk = before + colex;
-      ord[posk] = (uint8_t)sb;
-      inv[sb] = (uint8_t)posk;
-    }
-    __syncwarp();
+  for (int sb = lane; sb < nsub; sb += 32) {
+    int w = 0, colex = 0;
+    for (int j = 0; j < n; ++j)
+      if ((sb >> j) & 1) {
+        ++w;
+        colex += (int)binom16(j, w);
+      }
+    int before = 0;
+    for (int v = 0; v < w; ++v) before += (int)binom16(n, v);
+    const int posk = before + colex;
+    ord[posk] = (uint8_t)sb;
+    inv[sb] = (uint8_t)posk;
   }
+  __syncwarp();
   // entries of the subset at table position k, then an exclusive scan
   uint32_t kk = 0;  // 2 bits per rank of the side: its number of alternatives (1 or 3; 0 = none)
   for (int j = 0; j < n; ++j) kk |= (uint32_t)__popc(sl.ex[r0 + j] & 7u) << (2 * j);
