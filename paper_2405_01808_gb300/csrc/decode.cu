@@ -215,13 +215,12 @@ struct PrepSmem {
   uint32_t* E;      // [kEStride^2]
   uint32_t* s0;     // [Wmax] base syndrome
   uint8_t* ex;      // [kSMax]
-  uint8_t* sel;     // [kSMax] symbol of each reliability rank (L <= 32)
   uint16_t* pos;    // [kSMax][2]
 };
 
 __host__ __device__ inline size_t prep_warp_bytes(int Lmax, int Wmax) {
   size_t words = 2 * (size_t)Lmax + 32 + (size_t)kSMax * 3 * Wmax + kSMax * 3 + kEStride * kEStride + Wmax +
-                 kSMax / 4 + 1 + kSMax / 4 + 1 + kSMax;
+                 kSMax / 4 + 1 + kSMax;
   return ((words * 4) + 15) & ~(size_t)15;
 }
 
@@ -236,8 +235,7 @@ __device__ inline PrepSmem prep_smem(char* base, int Lmax, int Wmax) {
   s.E = p; p += kEStride * kEStride;
   s.s0 = p; p += Wmax;
   s.pos = reinterpret_cast<uint16_t*>(p); p += kSMax;
-  s.ex = reinterpret_cast<uint8_t*>(p); p += kSMax / 4 + 1;
-  s.sel = reinterpret_cast<uint8_t*>(p);
+  s.ex = reinterpret_cast<uint8_t*>(p);
   return s;
 }
 
@@ -425,17 +423,15 @@ __device__ __forceinline__ bool prep_frame(const PrepArgs& a, const int64_t f, c
     // --- Steps 2-3: the S' least reliable symbols, by (key, index) ---------
     int my_sel = -1;
     if (L <= 32) {
-      // one symbol per lane: its rank is the number of (key, index) pairs below it
-      const uint32_t k_i = lane < L ? sm.key[lane] : 0xFFFFFFFFu;
-      int rank = 0;
-#pragma unroll 8
-      for (int j = 0; j < 32; ++j) {
-        const uint32_t k_j = __shfl_sync(kFull, k_i, j);
-        rank += (k_j < k_i || (k_j == k_i && j < lane)) ? 1 : 0;
+      // one symbol per lane: S' rounds of the warp minimum of the keys; ties
+      // go to the lowest index (the lowest lane of the ballot)
+      uint32_t k_i = lane < L ? sm.key[lane] : 0xFFFFFFFFu;  // keys are < 2^31
+      for (int r = 0; r < Sp; ++r) {
+        const uint32_t kmin = __reduce_min_sync(kFull, k_i);
+        const int win = __ffs(__ballot_sync(kFull, k_i == kmin)) - 1;
+        if (lane == r) my_sel = win;
+        if (lane == win) k_i = 0xFFFFFFFFu;
       }
-      if (lane < L && rank < Sp) sm.sel[rank] = (uint8_t)lane;
-      __syncwarp();
-      if (lane < Sp) my_sel = sm.sel[lane];
     } else
     for (int r = 0; r < Sp; ++r) {
       uint32_t best_k = 0xFFFFFFFFu, best_i = 0xFFFFFFFFu;
@@ -502,16 +498,19 @@ __device__ __forceinline__ bool prep_frame(const PrepArgs& a, const int64_t f, c
           bool hit = false;
           if (cidx < nsets) {
             // colex unranking of the altered rank set P[0] < ... < P[w-1]
-            int P[kPrepMaxW0] = {0, 0, 0};
-            uint32_t rem = cidx;
-            int p = Sp - 1;
+            // (a single rank is its own index)
+            int P[kPrepMaxW0] = {(int)cidx, 0, 0};
+            if (w >= 2) {
+              uint32_t rem = cidx;
+              int p = Sp - 1;
 #pragma unroll
-            for (int jj = kPrepMaxW0; jj >= 1; --jj) {
-              if (jj > w) continue;
-              while (binom_le3(p, jj) > rem) --p;
-              P[jj - 1] = p;
-              rem -= binom_le3(p, jj);
-              --p;
+              for (int jj = kPrepMaxW0; jj >= 1; --jj) {
+                if (jj > w) continue;
+                while (binom_le3(p, jj) > rem) --p;
+                P[jj - 1] = p;
+                rem -= binom_le3(p, jj);
+                --p;
+              }
             }
             // alternatives in base-3 order, least significant digit first
             int dig[kPrepMaxW0] = {0, 0, 0};
@@ -579,12 +578,10 @@ __device__ __forceinline__ bool prep_frame(const PrepArgs& a, const int64_t f, c
         q = (uint32_t)((uint64_t)total < (uint64_t)a.cap ? total : a.cap);
         ab = 1;
       }
-      if (flip && lane == 0) {
-        for (int r = 0; r < Sp; ++r) {
-          const uint32_t c = (best_code >> (2 * r)) & 3u;
-          if (c & 1u) { const uint16_t p = sm.pos[2 * r]; if (p != kNoPos) sm.y[p >> 5] ^= 1u << (p & 31); }
-          if (c & 2u) { const uint16_t p = sm.pos[2 * r + 1]; if (p != kNoPos) sm.y[p >> 5] ^= 1u << (p & 31); }
-        }
+      if (flip && lane < Sp) {  // lane r flips the bits of rank r's alternative
+        const uint32_t c = (best_code >> (2 * lane)) & 3u;
+        if (c & 1u) { const uint16_t p = sm.pos[2 * lane]; if (p != kNoPos) atomicXor(&sm.y[p >> 5], 1u << (p & 31)); }
+        if (c & 2u) { const uint16_t p = sm.pos[2 * lane + 1]; if (p != kNoPos) atomicXor(&sm.y[p >> 5], 1u << (p & 31)); }
       }
       __syncwarp();
       if (lane < NW) a.cw[cw_off + lane] = sm.y[lane];
