@@ -1022,6 +1022,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_search(SearchArgs a) {
 constexpr int kWarpSideMax = 5;                      // hash join: the small-table variant (S' <= 10)
 constexpr int kPlanes = 20;                          // projection bits compared per TEP
 constexpr int kGroupUnroll = 8;                      // groups per candidate check
+constexpr int kQuarter = 4;                          // groups per fourth-slice decision
 constexpr int kLutBits = 5;                          // projection bits per table (32 words)
 constexpr int kLutSets = kPlanes / kLutBits;         // tables per group (the last one: second level)
 constexpr int kLutWords = 1 << kLutBits;
@@ -1589,25 +1590,38 @@ __device__ __forceinline__ void search_frame_flip(const SearchArgs& a, unsigned 
     int g0 = 0;
     for (; g0 < g_end; g0 += kGroupUnroll) {
       uint32_t acc[kB][kGroupUnroll];
-      uint32_t all = 0xFFFFFFFFu;
+      uint32_t part[kB][kGroupUnroll / kQuarter];  // AND of the words of each quarter block
 #pragma unroll
       for (int b = 0; b < kB; ++b) {
         cmp[b].block(g0);
         static_for<0, kGroupUnroll>([&](auto uc) {
           constexpr int u = decltype(uc)::value;
           acc[b][u] = cmp[b].template first<u>();
-          all &= acc[b][u];
+          if constexpr (u % kQuarter == 0) part[b][u / kQuarter] = acc[b][u];
+          else part[b][u / kQuarter] &= acc[b][u];
         });
       }
+      uint32_t all = 0xFFFFFFFFu;
+#pragma unroll
+      for (int b = 0; b < kB; ++b)
+#pragma unroll
+        for (int h = 0; h < kGroupUnroll / kQuarter; ++h) all &= part[b][h];
       if (!__any_sync(kFull, all != 0xFFFFFFFFu)) continue;
+      // rare: a 15-bit match somewhere in the block; only the quarters with
+      // a match in some lane read the fourth slice
       uint32_t cand[kB];
       uint32_t any_cand = 0;
 #pragma unroll
       for (int b = 0; b < kB; ++b) {
         cand[b] = 0;
-        static_for<0, kGroupUnroll>([&](auto uc) {
-          constexpr int u = decltype(uc)::value;
-          cand[b] |= ~(acc[b][u] | cmp[b].template second<u>());
+        static_for<0, kGroupUnroll / kQuarter>([&](auto hc) {
+          constexpr int h = decltype(hc)::value;
+          if (__any_sync(kFull, part[b][h] != 0xFFFFFFFFu)) {
+            static_for<h * kQuarter, (h + 1) * kQuarter>([&](auto uc) {
+              constexpr int u = decltype(uc)::value;
+              cand[b] |= ~(acc[b][u] | cmp[b].template second<u>());
+            });
+          }
         });
         any_cand |= cand[b];
       }
