@@ -952,6 +952,49 @@ def run_config(args, cfg, g, ctx):
                            "batch: same outputs; a hash join decides the queries without testing them one by "
                            "one, so this line reports frames/s, not checks"}
 
+    # ---- the same batch through GRAND_MEMBERSHIP_SOLVE: the first hit by
+    #      Gaussian elimination over each frame's TEP coordinates (the TEP
+    #      space of S' ranks with at most 4 alternatives is a GF(2) coordinate
+    #      space, so its codewords are the solutions of a linear system), one
+    #      CUDA-graph replay per step like the headline; identical outputs.
+    #      It tests no TEP one by one, so it reports frames/s, not checks.
+    solve = None
+    if cfg["kind"] in ("qam", "mixed") and args.membership == "auto":
+        ref_out = (d_cw.clone(), d_q.clone(), d_ab.clone())
+        ps = g.Params.make(order=p.order, M=p.M, S=p.S, query_cap=p.query_cap, membership=g.MEMBERSHIP_SOLVE)
+        if cfg["kind"] == "mixed":
+            splan = g.plan_mixed(codes, ps, d_desc, d_sym, d_cw, d_q, d_ab)
+            rs = g.decode_mixed(codes, ps, d_desc, d_sym, n_cw, cw=d_cw, queries=d_q, abandon=d_ab, stats=True)
+        else:
+            splan = g.plan_symbols(codes[0], ps, d_sym, d_cw.view(n_frames, -1), d_q, d_ab)
+            rs = g.decode_symbols(codes[0], ps, d_sym, cw=d_cw.view(n_frames, -1), queries=d_q, abandon=d_ab,
+                                  stats=True)
+        for _ in range(args.warmup):
+            splan.launch()
+        s_ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            splan.launch()
+            e1.record(stream)
+            e1.synchronize()
+            s_ms.append(e0.elapsed_time(e1))
+        same = all(torch.equal(x, y) for x, y in zip((d_cw, d_q, d_ab), ref_out))
+        splan.close()
+        s_mean = statistics.mean(s_ms)
+        solve = {"membership": "linear solve (GRAND_MEMBERSHIP_SOLVE)", "ms_per_step": s_mean,
+                 "frames_per_s": n_frames / (s_mean / 1e3),
+                 "latency_ms": {"p50": float(np.percentile(s_ms, 50)), "p99": float(np.percentile(s_ms, 99))},
+                 "kernel_ms": {"prep": rs["prep_ms"], "search": rs["search_ms"]},
+                 "frames_to_tep_search": int(rs["hard_frames"]), "ranked_solutions": int(rs["evaluated_checks"]),
+                 "outputs_equal": bool(same), "graph": True,
+                 "what": "the same batch with the first hit found by Gaussian elimination over each frame's TEP "
+                         "coordinates (the codewords of the TEP space are the solutions of a GF(2) linear "
+                         "system; the first hit is the one of smallest canonical rank): same outputs, no TEP "
+                         "tested one by one, so this line reports frames/s, not checks"}
+
     # ---- e2e: the same decode from pinned host buffers, copies in the timed
     #      region, through the library's host-memory calls
     #      (grand_decode_symbols_host / grand_decode_mixed_host: chunks on two
@@ -1062,6 +1105,7 @@ def run_config(args, cfg, g, ctx):
                           else None),
             "roofline": roofline,
             "fastest_exact": fastest,
+            "solve": solve,
             "demod": demod,
             "one_frame_per_launch": one,
             "autotune": tune,

@@ -110,13 +110,31 @@ typedef enum grand_order {
  *   FASTEST     grand_autotune / grand_autotune_mixed only: time both
  *               exact choices for the split (AUTO and HASH, identical
  *               outputs) with their launch shapes and write the faster into
- *               params->membership; the decode calls reject it. */
+ *               params->membership; the decode calls reject it.
+ *   SOLVE       no test per TEP: the valid TEPs of a frame (Alg. 2 Step 5
+ *               over the S' ranks, at most 4 alternatives each, Def. III.2)
+ *               are the flip vectors x over the existing I / Q slots (the
+ *               diagonal alternative flips both), and y xor e is a codeword
+ *               iff the XOR of the slots' syndrome deltas over x equals s(y):
+ *               a linear system over GF(2) with at most 2 S' unknowns. The
+ *               preparation solves it by Gaussian elimination; its solutions
+ *               are the frame's codewords within the TEP space, and the one of
+ *               smallest canonical rank is the first hit (no solution: the
+ *               frame abandons with min(valid TEPs, query_cap) queries).
+ *               Outputs are those of AUTO (decoded word, query count = the
+ *               hit's position in the canonical order, abandon flag); stats
+ *               count the ranked solutions as checks. Frames whose solution
+ *               set has more than 2^8 members go to the TEP search.
+ *               QAM_NNE / QAM_NEARER (uniform and uneven batches); not for
+ *               QAM_NNE5, HAMMING, the resumable search, the autotuner or
+ *               the no-allocation entry point. */
 typedef enum grand_membership {
   GRAND_MEMBERSHIP_AUTO = 0,
   GRAND_MEMBERSHIP_DELTA = 1,
   GRAND_MEMBERSHIP_ROW_PARITY = 2,
   GRAND_MEMBERSHIP_HASH = 3,
   GRAND_MEMBERSHIP_FASTEST = 4,
+  GRAND_MEMBERSHIP_SOLVE = 5,
 } grand_membership;
 
 /* Readings of Def. III.1 for a received value beyond the outermost level. */
@@ -369,7 +387,7 @@ int grand_decode_resume(const grand_code* code, const grand_params* params, void
  *   cw         device uint32, flat, n_cw_words entries; frame f starts at
  *              desc[f].cw_offset.
  *   params     order GRAND_ORDER_QAM_NNE or QAM_NEARER with membership
- *              AUTO or HASH; params->M is ignored (each frame has its own);
+ *              AUTO, HASH or SOLVE; params->M is ignored (each frame has its own);
  *              S' = min(params->S, L) per frame.
  * Errors as for grand_decode_batch. A descriptor with an unknown code, an
  * unsupported M or a range outside the arrays is not decoded: its abandon
@@ -455,7 +473,8 @@ int grand_autotune_mixed(const grand_code* const* codes, int n_codes, grand_para
  *   codes             host array of n_codes code pointers (borrowed; they must
  *                     outlive the server).
  *   params            order GRAND_ORDER_QAM_NNE or QAM_NEARER, membership
- *                     AUTO or HASH; M comes with each request.
+ *                     AUTO, HASH or SOLVE (SOLVE without resume_weight_step);
+ *                     M comes with each request.
  *   max_slots         admitted requests resident at once.
  *   max_device_bytes  memory budget of the resident request state; the
  *                     symbol ring holds max_device_bytes / 8 symbols.

@@ -18,7 +18,7 @@ from . import _build
 __all__ = [
     "GrandError", "GrandArgumentError", "lib", "build", "polar_H", "Code", "Params", "demod", "decode_batch",
     "decode_symbols", "decode_symbols_host", "decode_mixed", "decode_mixed_host", "frame_desc", "ORDER_HAMMING", "ORDER_QAM_NNE",
-    "ORDER_QAM_NEARER", "ORDER_QAM_NNE5", "MEMBERSHIP_AUTO", "MEMBERSHIP_DELTA", "MEMBERSHIP_ROW_PARITY", "MEMBERSHIP_HASH", "MEMBERSHIP_FASTEST",
+    "ORDER_QAM_NEARER", "ORDER_QAM_NNE5", "MEMBERSHIP_AUTO", "MEMBERSHIP_DELTA", "MEMBERSHIP_ROW_PARITY", "MEMBERSHIP_HASH", "MEMBERSHIP_FASTEST", "MEMBERSHIP_SOLVE", "E_UNSUPPORTED",
     "LIK_THRESHOLD", "LIK_LITERAL", "stream_status", "E_TIMEOUT", "ABANDON_DEADLINE", "ABANDON_SUSPENDED",
     "CURSOR_BYTES", "decode_symbols_resumable", "decode_resume",
 ]
@@ -32,9 +32,11 @@ MEMBERSHIP_DELTA = 1
 MEMBERSHIP_ROW_PARITY = 2
 MEMBERSHIP_HASH = 3
 MEMBERSHIP_FASTEST = 4  # autotuner only: choose between the split search and the hash join
+MEMBERSHIP_SOLVE = 5  # the first hit by Gaussian elimination over the frame's TEP coordinates
 LIK_THRESHOLD = 0
 LIK_LITERAL = 1
 E_TIMEOUT = -5         # grand_status GRAND_E_TIMEOUT
+E_UNSUPPORTED = -7     # grand_status GRAND_E_UNSUPPORTED
 ABANDON_DEADLINE = 5   # abandon flag of a frame cut at grand_params.deadline_ns
 ABANDON_SUSPENDED = 6  # abandon flag of a frame whose resumable search is suspended (GRAND_ABANDON_SUSPENDED)
 CURSOR_BYTES = 144     # GRAND_CURSOR_BYTES: the search state of one suspended frame

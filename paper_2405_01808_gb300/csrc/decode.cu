@@ -275,11 +275,180 @@ __device__ __forceinline__ uint32_t binom_le3(int n, int k) {
   return k == 0 ? 1u : (k == 1 ? m : (k == 2 ? m * (m - 1) / 2u : m * (m - 1) * (m - 2) / 6u));
 }
 
+// Largest kernel dimension solve_frame ranks exhaustively (2^8 solutions).
+constexpr int kSolveKerMax = 8;
+// Resident CTAs per SM of the preparation with the elimination (syndromes of
+// at most two words; the longer ones run 8 like the plain preparation).
+constexpr int kPrepSolveBlocks = 10;
+
+// Column b of the slot system (see solve_frame): the syndrome delta of slot b
+// (slot b & 1 of rank b >> 1) in the preparation's delta array.
+__device__ __forceinline__ const uint32_t* slot_column(const PrepSmem& sm, int b, int W) {
+  return sm.delta + ((b >> 1) * 3 + (b & 1)) * W;
+}
+
+// XOR of the slot columns over x (and s0 when with_s0) is zero on every
+// syndrome word (lanes = words; x is the same in every lane).
+__device__ __forceinline__ bool slot_sum_zero(const PrepSmem& sm, int W, uint32_t x, bool with_s0) {
+  const int lane = threadIdx.x & 31;
+  uint32_t acc = 0;
+  if (lane < W) {
+    acc = with_s0 ? sm.s0[lane] : 0u;
+    for (uint32_t m = x; m; m &= m - 1u) acc ^= slot_column(sm, __ffs(m) - 1, W)[lane];
+  }
+  return !__any_sync(kFull, acc != 0u);
+}
+
+// The first hit among the solutions x0 + span(km[0..d)): every one is a
+// valid TEP (only existing slots take part) and is ranked by its canonical
+// position.
+__device__ __forceinline__ void rank_solutions(const PrepSmem& sm, int Sp, uint32_t x0, const uint32_t (&km)[kSolveKerMax],
+                                               int d, uint32_t& best_rank, uint32_t& best_code,
+                                               unsigned long long& evaluated) {
+  const int lane = threadIdx.x & 31;
+  if (d == 0) {  // the usual case: one solution, ranked by every lane alike
+    best_rank = tep_rank(sm.E, Sp, sm.ex, x0);
+    best_code = x0;
+    if (lane == 0) evaluated += 1;
+    return;
+  }
+  uint32_t lr = 0xFFFFFFFFu, lc = 0;
+  for (uint32_t c = (uint32_t)lane; c < (1u << d); c += 32) {
+    uint32_t x = x0;
+#pragma unroll
+    for (int t = 0; t < kSolveKerMax; ++t)
+      if ((c >> t) & 1u) x ^= km[t];
+    const uint32_t rk = tep_rank(sm.E, Sp, sm.ex, x);
+    if (rk < lr) { lr = rk; lc = x; }
+  }
+  if (lane == 0) evaluated += 1ull << d;
+  const uint32_t br = __reduce_min_sync(kFull, lr);
+  const unsigned who = __ballot_sync(kFull, lr == br);
+  best_code = __shfl_sync(kFull, lc, __ffs(who) - 1);
+  best_rank = br;
+}
+
+// GRAND_MEMBERSHIP_SOLVE: the frame's first codeword in canonical order by
+// Gaussian elimination over GF(2) instead of a test per TEP. A valid TEP is a
+// flip vector x over the existing slots (bit 2r: the first single-axis slot
+// of rank r, bit 2r+1: the second; the diagonal is both), and H (y xor e) = 0
+// reads XOR_{b in x} c_b = s0 with c_b the syndrome delta of slot b (zero for
+// a flip beyond N): the codewords of the TEP space are the solutions x0 +
+// ker of this system, and the first hit is the solution of smallest
+// canonical rank.
+//   Fast path: the same elimination on one 32-bit word per column and for s0
+// (lane b < 2 S' holds slot b, lane 31 s0; pivots in lane order at a
+// column's lowest set bit; each lane carries the set of original slots its
+// word now sums): the syndrome itself when it has one word (exact), else the
+// 32-bit projections of the columns and of s0. The projection is linear, so
+// no projected solution means no solution. Otherwise the projected kernel vectors and x0 are checked on
+// the full syndrome: when every kernel vector passes, the two kernels agree,
+// and then x0 either passes (the solutions are x0 + that kernel) or no
+// solution exists. A kernel vector that fails (the projection lost rank on
+// the columns' span, about 2^(2S'-32) of frames) sends the frame to the
+// exact path: the elimination on the full columns in shared memory.
+// Returns 1 (best_rank and best_code set), 0 (no valid TEP gives a
+// codeword: the frame abandons) or -1 (more than 2^kSolveKerMax solutions:
+// the frame goes to the TEP search).
+__device__ __forceinline__ int solve_frame(const PrepSmem& sm, int Sp, int W, uint32_t f0, uint32_t& best_rank,
+                                           uint32_t& best_code, unsigned long long& evaluated) {
+  const int lane = threadIdx.x & 31;
+  const int nb = 2 * Sp;  // <= 24 < 31
+  const bool on = lane < nb && ((sm.ex[lane >> 1] >> (lane & 1)) & 1u);
+  uint32_t km[kSolveKerMax];
+  {
+    const bool one_word = W == 1;
+    uint32_t val = on ? (one_word ? slot_column(sm, lane, 1)[0] : sm.dflt[(lane >> 1) * 3 + (lane & 1)])
+                      : (lane == 31 ? (one_word ? sm.s0[0] : f0) : 0u);
+    uint32_t msk = on ? 1u << lane : 0u;
+    bool pivot = false;
+    for (int j = 0; j < nb; ++j) {
+      int p = -1;
+      if (lane == j && on && val) p = __ffs(val) - 1;
+      if (lane == j) pivot = p >= 0;
+      p = __shfl_sync(kFull, p, j);
+      if (p < 0) continue;
+      const uint32_t pv = __shfl_sync(kFull, val, j);
+      const uint32_t pm = __shfl_sync(kFull, msk, j);
+      if (lane > j && ((val >> p) & 1u)) {
+        val ^= pv;
+        msk ^= pm;
+      }
+    }
+    if (__shfl_sync(kFull, val, 31) != 0u) return 0;  // not even the projection of s0 is reached
+    const uint32_t x0 = __shfl_sync(kFull, msk, 31);
+    uint32_t dep = __ballot_sync(kFull, on && !pivot);
+    const int d = __popc(dep);
+    bool kernels_agree = d <= kSolveKerMax;
+#pragma unroll
+    for (int t = 0; t < kSolveKerMax; ++t) {
+      km[t] = 0;
+      if (t < d) {
+        km[t] = __shfl_sync(kFull, msk, __ffs(dep) - 1);
+        dep &= dep - 1;
+        if (!one_word) kernels_agree = kernels_agree && slot_sum_zero(sm, W, km[t], false);
+      }
+    }
+    if (kernels_agree) {
+      if (!one_word && !slot_sum_zero(sm, W, x0, true)) return 0;
+      rank_solutions(sm, Sp, x0, km, d, best_rank, best_code, evaluated);
+      return 1;
+    }
+    if (one_word) return -1;  // exact already: the solution set is too large to rank
+  }
+  // exact path: lane b reduces column b in place (the delta slots), lane 31
+  // reduces s0 (copied to the unused diagonal slot of rank 0)
+  uint32_t* s0c = sm.delta + 2 * W;
+  for (int w = lane; w < W; w += 32) s0c[w] = sm.s0[w];
+  __syncwarp();
+  const bool act = on || lane == 31;
+  uint32_t* col = lane == 31 ? s0c : sm.delta + ((lane >> 1) * 3 + (lane & 1)) * W;
+  uint32_t msk = on ? 1u << lane : 0u;
+  bool pivot = false;
+  for (int j = 0; j < nb; ++j) {
+    int p = -1;
+    if (lane == j && on) {
+      for (int w = 0; w < W; ++w) {
+        const uint32_t x = col[w];
+        if (x) { p = 32 * w + __ffs(x) - 1; break; }
+      }
+      pivot = p >= 0;
+    }
+    p = __shfl_sync(kFull, p, j);
+    if (p < 0) continue;  // slot j absent, or its column a sum of earlier ones
+    const uint32_t pm = __shfl_sync(kFull, msk, j);
+    const uint32_t* pc = slot_column(sm, j, W);
+    if (act && lane > j && ((col[p >> 5] >> (p & 31)) & 1u)) {
+      for (int w = 0; w < W; ++w) col[w] ^= pc[w];
+      msk ^= pm;
+    }
+    __syncwarp();
+  }
+  uint32_t rest = 0;
+  if (lane == 31)
+    for (int w = 0; w < W; ++w) rest |= col[w];
+  if (__shfl_sync(kFull, rest, 31) != 0u) return 0;  // s0 is not a sum of the slot columns
+  const uint32_t x0 = __shfl_sync(kFull, msk, 31);
+  uint32_t dep = __ballot_sync(kFull, on && !pivot);
+  const int d = __popc(dep);
+  if (d > kSolveKerMax) return -1;
+#pragma unroll
+  for (int t = 0; t < kSolveKerMax; ++t) {
+    km[t] = 0;
+    if (t < d) {
+      km[t] = __shfl_sync(kFull, msk, __ffs(dep) - 1);
+      dep &= dep - 1;
+    }
+  }
+  rank_solutions(sm, Sp, x0, km, d, best_rank, best_code, evaluated);
+  return 1;
+}
+
 // One frame of the preparation (one warp). Returns true when the frame needs
 // the search stage; its hand-off record then went to a fresh slot of the
 // batch's record array. WM: compile-time bound on the syndrome words
 // (registers of the base syndrome).
-template <int WM>
+template <int WM, bool kSolve>
 __device__ __forceinline__ bool prep_frame(const PrepArgs& a, const int64_t f, const PrepSmem& sm,
                                            unsigned long long& evaluated) {
   const int lane = threadIdx.x & 31;
@@ -565,7 +734,12 @@ __device__ __forceinline__ bool prep_frame(const PrepArgs& a, const int64_t f, c
     uint32_t done_count = 0;  // valid TEPs with at most w_done altered ranks
     for (int v = 0; v <= w_done; ++v) done_count += sm.E[Sp * kEStride + v];
 
-    const bool resolved = best_rank != 0xFFFFFFFFu || w_done >= Sp || (uint64_t)done_count >= (uint64_t)a.cap;
+    bool none = false;  // no valid TEP of the frame gives a codeword
+    if constexpr (kSolve) {
+      if (best_rank == 0xFFFFFFFFu && w_done < Sp && (uint64_t)done_count < (uint64_t)a.cap)
+        none = solve_frame(sm, Sp, W, f0, best_rank, best_code, evaluated) == 0;
+    }
+    const bool resolved = best_rank != 0xFFFFFFFFu || none || w_done >= Sp || (uint64_t)done_count >= (uint64_t)a.cap;
     if (resolved) {
       uint32_t q;
       uint8_t ab;
@@ -623,8 +797,8 @@ __device__ __forceinline__ bool prep_frame(const PrepArgs& a, const int64_t f, c
 // bound then costs a few spilled words but the latency-bound preparation
 // gains warps); 8 for the longer syndromes, whose per-lane arrays would spill
 // heavily at 40 registers.
-template <int WM>
-__global__ void __launch_bounds__(128, WM <= 2 ? 12 : 8) k_prep(PrepArgs a) {
+template <int WM, bool kSolve>
+__global__ void __launch_bounds__(128, WM <= 2 ? (kSolve ? kPrepSolveBlocks : 12) : 8) k_prep(PrepArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp_in_block = threadIdx.x >> 5;
@@ -634,7 +808,7 @@ __global__ void __launch_bounds__(128, WM <= 2 ? 12 : 8) k_prep(PrepArgs a) {
   const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
   unsigned long long evaluated = 0;
   if (a.deadline > 0 && lane == 0) past_deadline(&a.scr->t0, a.deadline);  // start the call's clock
-  for (int64_t f = gwarp; f < a.n_frames; f += nwarps) prep_frame<WM>(a, f, sm, evaluated);
+  for (int64_t f = gwarp; f < a.n_frames; f += nwarps) prep_frame<WM, kSolve>(a, f, sm, evaluated);
   // stats
   for (int o = 16; o; o >>= 1) evaluated += __shfl_xor_sync(kFull, evaluated, o);
   if (lane == 0 && evaluated) atomicAdd(&a.scr->evaluated, evaluated);
@@ -2586,12 +2760,19 @@ static void launch_demod(const DemodArgs& a, bool paired, int grid, cudaStream_t
 }
 
 typedef void (*PrepKernel)(PrepArgs);
-static PrepKernel prep_kernel_for(int Wmax) {
-  if (Wmax <= 1) return k_prep<1>;
-  if (Wmax <= 2) return k_prep<2>;
-  if (Wmax <= 4) return k_prep<4>;
-  if (Wmax <= 8) return k_prep<8>;
-  return k_prep<16>;
+static PrepKernel prep_kernel_for(int Wmax, bool solve = false) {
+  if (solve) {
+    if (Wmax <= 1) return k_prep<1, true>;
+    if (Wmax <= 2) return k_prep<2, true>;
+    if (Wmax <= 4) return k_prep<4, true>;
+    if (Wmax <= 8) return k_prep<8, true>;
+    return k_prep<16, true>;
+  }
+  if (Wmax <= 1) return k_prep<1, false>;
+  if (Wmax <= 2) return k_prep<2, false>;
+  if (Wmax <= 4) return k_prep<4, false>;
+  if (Wmax <= 8) return k_prep<8, false>;
+  return k_prep<16, false>;
 }
 
 
@@ -2698,8 +2879,10 @@ static int launch_search(const SearchArgs& s, int threads, size_t smem, int vari
 // one-time stall of milliseconds into the first batch that needs it).
 int preload_qam_kernels() {
   const void* kernels[] = {
-      (const void*)k_prep<1>, (const void*)k_prep<2>, (const void*)k_prep<4>, (const void*)k_prep<8>,
-      (const void*)k_prep<16>,
+      (const void*)k_prep<1, false>, (const void*)k_prep<2, false>, (const void*)k_prep<4, false>,
+      (const void*)k_prep<8, false>, (const void*)k_prep<16, false>, (const void*)k_prep<1, true>,
+      (const void*)k_prep<2, true>, (const void*)k_prep<4, true>, (const void*)k_prep<8, true>,
+      (const void*)k_prep<16, true>,
       (const void*)k_search_warp<4, false, false>, (const void*)k_search_warp<6, false, false>,
       (const void*)k_search_warp<8, false, false>, (const void*)k_search_warp<4, true, false>,
       (const void*)k_search_warp<6, true, false>, (const void*)k_search_warp<8, true, false>,
@@ -2807,12 +2990,13 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     a.deadline = p->deadline_ns;
     a.Lmax = Lmax;
     a.Wmax = Wmax;
-    a.w0 = w0;
+    const bool solve = p->membership == GRAND_MEMBERSHIP_SOLVE;
+    a.w0 = solve ? 1 : w0;  // weights <= 1 filter the frames the elimination then solves
     const int warps = 4;
     const size_t prep_smem = prep_warp_bytes(Lmax, Wmax) * warps;
     const int64_t want = (n_frames + warps - 1) / warps;
     const int grid = (int)(want < (int64_t)sm_count() * 64 ? want : (int64_t)sm_count() * 64);
-    auto kp = prep_kernel_for(Wmax);
+    auto kp = prep_kernel_for(Wmax, solve);
     if (prep_smem > 48 * 1024 && resident_ctas((const void*)kp, 32 * warps, prep_smem) < 0) {  // raises the limit
       rc = GRAND_E_CUDA;
       break;
@@ -2863,8 +3047,14 @@ static int check_params(const grand_params* p) {
   if (!p) return GRAND_E_INVALID;
   if (p->query_cap < 1 || p->deadline_ns < 0) return GRAND_E_INVALID;
   if (p->lik_variant != GRAND_LIK_THRESHOLD && p->lik_variant != GRAND_LIK_LITERAL) return GRAND_E_INVALID;
-  if (p->membership < GRAND_MEMBERSHIP_AUTO || p->membership > GRAND_MEMBERSHIP_HASH) return GRAND_E_INVALID;
-  if (p->order == GRAND_ORDER_QAM_NNE5 && p->membership == GRAND_MEMBERSHIP_HASH) return GRAND_E_UNSUPPORTED;
+  if (p->membership < GRAND_MEMBERSHIP_AUTO || p->membership > GRAND_MEMBERSHIP_SOLVE ||
+      p->membership == GRAND_MEMBERSHIP_FASTEST)
+    return GRAND_E_INVALID;
+  if (p->order == GRAND_ORDER_QAM_NNE5 &&
+      (p->membership == GRAND_MEMBERSHIP_HASH || p->membership == GRAND_MEMBERSHIP_SOLVE))
+    return GRAND_E_UNSUPPORTED;
+  // the bit-level TEP set (weights <= max_weight) is not a coordinate space
+  if (p->order == GRAND_ORDER_HAMMING && p->membership == GRAND_MEMBERSHIP_SOLVE) return GRAND_E_UNSUPPORTED;
   if (p->order == GRAND_ORDER_QAM_NNE || p->order == GRAND_ORDER_QAM_NEARER || p->order == GRAND_ORDER_QAM_NNE5) {
     if (p->S < 0) return GRAND_E_INVALID;
     if (p->S > (p->order == GRAND_ORDER_QAM_NNE5 ? GRAND_S_MAX_NNE5 : kSMax)) return GRAND_E_UNSUPPORTED;
@@ -3168,7 +3358,8 @@ static int check_mixed_args(const grand_code* const* codes, int n_codes, const g
   int rc = check_params(p);
   if (rc) return rc;
   if ((p->order != GRAND_ORDER_QAM_NNE && p->order != GRAND_ORDER_QAM_NEARER) ||
-      (p->membership != GRAND_MEMBERSHIP_AUTO && p->membership != GRAND_MEMBERSHIP_HASH))
+      (p->membership != GRAND_MEMBERSHIP_AUTO && p->membership != GRAND_MEMBERSHIP_HASH &&
+       p->membership != GRAND_MEMBERSHIP_SOLVE))
     return GRAND_E_INVALID;
   if (n_frames > 0xFFFFFFFFll) return GRAND_E_UNSUPPORTED;
   return GRAND_OK;

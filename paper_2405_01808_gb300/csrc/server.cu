@@ -619,11 +619,13 @@ extern "C" int grand_server_create(const grand_server_cfg* cfg, grand_server** o
       cfg->n_streams < 1 || cfg->n_streams > kMaxStreams || cfg->max_batch < 0 || !(cfg->N0 > 0.0f))
     return GRAND_E_INVALID;
   if ((cfg->params.order != GRAND_ORDER_QAM_NNE && cfg->params.order != GRAND_ORDER_QAM_NEARER) ||
-      (cfg->params.membership != GRAND_MEMBERSHIP_AUTO && cfg->params.membership != GRAND_MEMBERSHIP_HASH) ||
+      (cfg->params.membership != GRAND_MEMBERSHIP_AUTO && cfg->params.membership != GRAND_MEMBERSHIP_HASH &&
+       cfg->params.membership != GRAND_MEMBERSHIP_SOLVE) ||
       cfg->params.query_cap < 1 || cfg->params.deadline_ns < 0 || cfg->params.S < 0 ||
       cfg->params.S > GRAND_S_MAX || cfg->resume_weight_step < 0)
     return GRAND_E_INVALID;
-  if (cfg->resume_weight_step > 0 && cfg->params.tiles[1] > 0) return GRAND_E_UNSUPPORTED;
+  if (cfg->resume_weight_step > 0 && (cfg->params.tiles[1] > 0 || cfg->params.membership == GRAND_MEMBERSHIP_SOLVE))
+    return GRAND_E_UNSUPPORTED;
   for (int i = 0; i < cfg->n_codes; ++i)
     if (!cfg->codes[i]) return GRAND_E_INVALID;
   *out = nullptr;

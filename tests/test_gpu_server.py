@@ -75,7 +75,7 @@ def run_all(srv, reqs, timeout_s=30.0):
     return np.concatenate(got)
 
 
-@pytest.mark.parametrize("membership", [0, 3])  # TEP-by-TEP search; hash join
+@pytest.mark.parametrize("membership", [0, 3, 5])  # TEP-by-TEP search; hash join; elimination
 def test_results_equal_alone(env, membership):
     g, codes, info = env
     code_of_N = {n: i for i, n in enumerate(NS)}
