@@ -450,7 +450,8 @@ def run_serving(args, cfg, g, inputs, resume_step=0):
     reqs["M"] = inputs["M"]
     reqs["symbols"] = sym.ctypes.data + 8 * inputs["sym_offset"].astype(np.uint64)
     reqs["tag"] = np.arange(F, dtype=np.uint64)
-    p = g.Params.make(M=0, S=cfg["S"], query_cap=cfg["cap"], membership={"auto": 0, "hash": 3}[args.membership])
+    p = g.Params.make(M=0, S=cfg["S"], query_cap=cfg["cap"],
+                      membership={"auto": 0, "hash": 3, "solve": 5}[args.membership])
     rows = []
     g_rng = np.random.default_rng(CONFIG_IDS["c5"])
     for rate in cfg["rates"]:
@@ -1134,7 +1135,7 @@ def run_serve_config(args, cfg, g, ctx):
     clocks.start()
     rows, one = run_serving(args, cfg, g, inputs, resume_step=0 if cfg.get("adversarial") else args.serve_resume_step)
     carried = None
-    if cfg.get("adversarial"):
+    if cfg.get("adversarial") and args.membership != "solve":
         carried, _ = run_serving(args, cfg, g, inputs, resume_step=max(1, args.serve_resume_step))
     clk = clocks.stop()
     if rank != 0:
@@ -1146,7 +1147,9 @@ def run_serve_config(args, cfg, g, ctx):
             "data": "synthetic (seeded random polar codewords over AWGN)",
             "config": {"workload": cfg["desc"], "requests_per_rate": len(inputs["N"]),
                        "server": f"max_slots 262144, budget 1 GiB, max_batch {args.serve_batch}, "
-                                 f"{args.serve_streams} streams"},
+                                 f"{args.serve_streams} streams",
+                       "membership": {"auto": "split search (TEP by TEP)", "hash": "hash join",
+                                      "solve": "linear solve (GRAND_MEMBERSHIP_SOLVE)"}[args.membership]},
             "latency_us": head["latency_us"], "rates": rows, "one_frame_per_launch": one, "clocks": clk,
             "e2e": {"value": head["frames_per_s"], "unit": "frames/s",
                     "h2d_bytes_per_step": int(inputs["symbols"].nbytes),
@@ -1172,13 +1175,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=0, help="override frames per SNR (for quick runs)")
     ap.add_argument("--tiles", default="0,0,0,0", help="launch shape (grand_params.tiles), 0 = automatic")
-    ap.add_argument("--membership", default="auto", choices=("auto", "hash"),
-                    help="membership test of the search (the headline uses the TEP-by-TEP search)")
+    ap.add_argument("--membership", default="auto", choices=("auto", "hash", "solve"),
+                    help="membership test of the search (the headline uses the TEP-by-TEP search; "
+                         "solve: serving configs only -- the other records carry it under 'solve')")
     ap.add_argument("--serve-batch", type=int, default=65536, help="serving: frames per launch")
     ap.add_argument("--serve-streams", type=int, default=4, help="serving: batches in flight")
     ap.add_argument("--serve-resume-step", type=int, default=0,
                     help="serving: TEP weights per window of a long frame (0: frames searched whole in their batch)")
     args = ap.parse_args()
+    if args.membership == "solve" and not (args.config or "").startswith("c5"):
+        ap.error("--membership solve applies to the serving configs (c5, c5long, c5adv); the decode "
+                 "records report the solve path under their 'solve' key")
+    if args.membership == "solve" and args.serve_resume_step:
+        ap.error("--membership solve has no TEP search to continue (--serve-resume-step 0)")
     cfg = dict(CONFIGS[args.config or "c2"])
     cfg["name"] = args.config or "c2"
     if args.frames:

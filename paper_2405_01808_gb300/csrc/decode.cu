@@ -281,6 +281,21 @@ constexpr int kSolveKerMax = 8;
 // at most two words; the longer ones run 8 like the plain preparation).
 constexpr int kPrepSolveBlocks = 10;
 
+// 32 x 32 bit transpose across a warp: lane i holds row i on entry, lane j
+// holds column j on return (bit i of it = bit j of row i).
+__device__ __forceinline__ uint32_t warp_transpose_bits(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+  constexpr uint32_t kMask[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int k = 16 >> s;
+    const uint32_t m = kMask[s];
+    const uint32_t y = __shfl_xor_sync(kFull, x, k);
+    x = (lane & k) ? (((y >> k) & m) | (x & ~m)) : ((x & m) | ((y & m) << k));
+  }
+  return x;
+}
+
 // Column b of the slot system (see solve_frame): the syndrome delta of slot b
 // (slot b & 1 of rank b >> 1) in the preparation's delta array.
 __device__ __forceinline__ const uint32_t* slot_column(const PrepSmem& sm, int b, int W) {
@@ -336,15 +351,15 @@ __device__ __forceinline__ void rank_solutions(const PrepSmem& sm, int Sp, uint3
 // a flip beyond N): the codewords of the TEP space are the solutions x0 +
 // ker of this system, and the first hit is the solution of smallest
 // canonical rank.
-//   Fast path: the same elimination on one 32-bit word per column and for s0
-// (lane b < 2 S' holds slot b, lane 31 s0; pivots in lane order at a
-// column's lowest set bit; each lane carries the set of original slots its
-// word now sums): the syndrome itself when it has one word (exact), else the
-// 32-bit projections of the columns and of s0. The projection is linear, so
-// no projected solution means no solution. Otherwise the projected kernel vectors and x0 are checked on
-// the full syndrome: when every kernel vector passes, the two kernels agree,
-// and then x0 either passes (the solutions are x0 + that kernel) or no
-// solution exists. A kernel vector that fails (the projection lost rank on
+//   Fast path: the system on one 32-bit word per column and for s0 -- the
+// syndrome itself when it has one word (exact), else the 32-bit projections
+// of the columns and of s0 -- transposed across the warp (lane r holds bit r
+// of every column and of s0) and brought to reduced row echelon form, pivots
+// in slot order (one ballot and one shuffle per slot). The projection is
+// linear, so no projected solution means no solution. Otherwise the
+// projected kernel vectors and x0 are checked on the full syndrome: when
+// every kernel vector passes, the two kernels agree, and then x0 either
+// passes (the solutions are x0 + that kernel) or no solution exists. A kernel vector that fails (the projection lost rank on
 // the columns' span, about 2^(2S'-32) of frames) sends the frame to the
 // exact path: the elimination on the full columns in shared memory.
 // Returns 1 (best_rank and best_code set), 0 (no valid TEP gives a
@@ -358,34 +373,45 @@ __device__ __forceinline__ int solve_frame(const PrepSmem& sm, int Sp, int W, ui
   uint32_t km[kSolveKerMax];
   {
     const bool one_word = W == 1;
-    uint32_t val = on ? (one_word ? slot_column(sm, lane, 1)[0] : sm.dflt[(lane >> 1) * 3 + (lane & 1)])
+    // lane b: the word of slot b, lane 31: that of s0; transposed so that
+    // lane r holds bit r of every column (bit b: slot b, bit 31: s0)
+    uint32_t row = on ? (one_word ? slot_column(sm, lane, 1)[0] : sm.dflt[(lane >> 1) * 3 + (lane & 1)])
                       : (lane == 31 ? (one_word ? sm.s0[0] : f0) : 0u);
-    uint32_t msk = on ? 1u << lane : 0u;
-    bool pivot = false;
-    for (int j = 0; j < nb; ++j) {
-      int p = -1;
-      if (lane == j && on && val) p = __ffs(val) - 1;
-      if (lane == j) pivot = p >= 0;
-      p = __shfl_sync(kFull, p, j);
-      if (p < 0) continue;
-      const uint32_t pv = __shfl_sync(kFull, val, j);
-      const uint32_t pm = __shfl_sync(kFull, msk, j);
-      if (lane > j && ((val >> p) & 1u)) {
-        val ^= pv;
-        msk ^= pm;
+    row = warp_transpose_bits(row);
+    // reduced row echelon form over the existing slots, pivots in slot order
+    const unsigned on_mask = __ballot_sync(kFull, on);
+    bool used = false;  // this row holds a pivot
+    int pc = 0;         // its slot
+    uint32_t free_slots = 0;
+    for (int b = 0; b < nb; ++b) {
+      if (!((on_mask >> b) & 1u)) continue;  // an absent slot is no unknown
+      const unsigned cand = __ballot_sync(kFull, !used && ((row >> b) & 1u));
+      if (!cand) {
+        free_slots |= 1u << b;
+        continue;
+      }
+      const int pr = __ffs(cand) - 1;
+      const uint32_t prow = __shfl_sync(kFull, row, pr);
+      if (lane == pr) {
+        used = true;
+        pc = b;
+      } else if ((row >> b) & 1u) {
+        row ^= prow;
       }
     }
-    if (__shfl_sync(kFull, val, 31) != 0u) return 0;  // not even the projection of s0 is reached
-    const uint32_t x0 = __shfl_sync(kFull, msk, 31);
-    uint32_t dep = __ballot_sync(kFull, on && !pivot);
-    const int d = __popc(dep);
+    // a row without pivot that still needs s0's bit: not even the word of s0 is reached
+    if (__any_sync(kFull, !used && (row >> 31))) return 0;
+    const uint32_t x0 = __reduce_or_sync(kFull, used && (row >> 31) ? 1u << pc : 0u);
+    const int d = __popc(free_slots);
     bool kernels_agree = d <= kSolveKerMax;
+    uint32_t fs = free_slots;
 #pragma unroll
     for (int t = 0; t < kSolveKerMax; ++t) {
       km[t] = 0;
       if (t < d) {
-        km[t] = __shfl_sync(kFull, msk, __ffs(dep) - 1);
-        dep &= dep - 1;
+        const int f = __ffs(fs) - 1;
+        fs &= fs - 1u;
+        km[t] = (1u << f) | __reduce_or_sync(kFull, used && ((row >> f) & 1u) ? 1u << pc : 0u);
         if (!one_word) kernels_agree = kernels_agree && slot_sum_zero(sm, W, km[t], false);
       }
     }
@@ -3017,6 +3043,10 @@ static int run_qam(const CodeDev* d_codes, int n_codes, int Lmax, int Wmax, cons
     ResumeOpt ro2 = ro;
     ro2.n_codes = n_codes;
     ro2.max_entries = n_frames;  // at most every frame is handed on
+    // with the elimination, only frames whose solution set is too large to
+    // rank are handed on (none on the measured workloads): one CTA per SM
+    // keeps that launch short
+    if (solve) ro2.max_entries = n_frames < (int64_t)sm_count() ? n_frames : (int64_t)sm_count();
     if (launch_qam_search(p, Smax, a.w0, Wmax, d_codes, recs, scr, proto.cw, proto.queries, proto.abandon, st, ro2) !=
         GRAND_OK) {
       rc = GRAND_E_CUDA;
