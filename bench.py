@@ -101,18 +101,18 @@ SMEM_PEAK_GBS = SMS * 128 * MAX_CLOCK_GHZ
 #     pipe).
 # Everything in the kernel is included in both.
 NCU_SEARCH = {
-    "k_search_warp S'<=10": {"sha": "ea04ab8cce1c1ed7", "profile": "profiles/k_search_warp_c2_small.md",
-                             "bound": "smem", "smem_bytes_per_check": 0.4489, "smem_wavefronts_frac": 0.780,
-                             "lsu_pipe_active": 0.818, "alu_lane_ops_per_check": 0.147, "alu_pipe_active": 0.510,
-                             "dram_bytes_per_hard_frame": 1891840 / 11181},
-    "k_search_warp S'=12": {"sha": "ea04ab8cce1c1ed7", "profile": "profiles/k_search_warp_c3a_small.md",
-                            "bound": "smem", "smem_bytes_per_check": 0.4059, "smem_wavefronts_frac": 0.871,
-                            "lsu_pipe_active": 0.904, "alu_lane_ops_per_check": 0.103, "alu_pipe_active": 0.443,
+    "k_search_warp S'<=10": {"sha": "c0a370e5b6a95e2b", "profile": "profiles/k_search_warp_c2_small.md",
+                             "bound": "smem", "smem_bytes_per_check": 0.4489, "smem_wavefronts_frac": 0.778,
+                             "lsu_pipe_active": 0.820, "alu_lane_ops_per_check": 0.147, "alu_pipe_active": 0.511,
+                             "dram_bytes_per_hard_frame": 1894912 / 11181},
+    "k_search_warp S'=12": {"sha": "c0a370e5b6a95e2b", "profile": "profiles/k_search_warp_c3a_small.md",
+                            "bound": "smem", "smem_bytes_per_check": 0.4059, "smem_wavefronts_frac": 0.867,
+                            "lsu_pipe_active": 0.904, "alu_lane_ops_per_check": 0.104, "alu_pipe_active": 0.443,
                             "dram_bytes_per_hard_frame": 777216 / 4706},
     # the bit-level kernel reads every frame (no hand-off records): bytes per frame
-    "k_ab_split<1,16>": {"sha": "f8fb1514c5487c59", "profile": "profiles/k_ab_split_c1_n32_bpsk.md", "bound": "alu",
-                         "alu_lane_ops_per_check": 165.4, "alu_pipe_active": 0.359,
-                         "dram_bytes_per_frame": 1308160 / 10000},
+    "k_ab_split<1,16>": {"sha": "c0a370e5b6a95e2b", "profile": "profiles/k_ab_split_c1_n32_bpsk.md", "bound": "alu",
+                         "alu_lane_ops_per_check": 162.4, "alu_pipe_active": 0.349,
+                         "dram_bytes_per_frame": 1308416 / 10000},
 }
 
 

@@ -26,8 +26,12 @@ struct Candidate {
 void shapes(int S, int membership, std::vector<Candidate>& out) {
   if (membership == GRAND_MEMBERSHIP_HASH) {
     // hash join: warps per CTA (its shared-memory tables bound residency) x prep weights
-    for (int warps : S <= 10 ? std::initializer_list<int>{2, 4} : std::initializer_list<int>{1, 2})
-      for (int w0 : {1, 2, 3}) out.push_back({{warps, 0, w0, 0}, membership});
+    // (static arrays: the backing array of a braced list chosen by ?: would not
+    // outlive the range-for's initialisation)
+    static const int kWarpsS10[2] = {2, 4}, kWarpsS12[2] = {1, 2};
+    const int* warps = S <= 10 ? kWarpsS10 : kWarpsS12;
+    for (int i = 0; i < 2; ++i)
+      for (int w0 : {1, 2, 3}) out.push_back({{warps[i], 0, w0, 0}, membership});
   } else if (S <= 10) {
     // warp search (warp pairs sharing a frame): prep weights x register budget
     for (int w0 : {1, 2, 3})

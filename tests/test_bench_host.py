@@ -113,8 +113,8 @@ def test_roofline_fraction_is_bounded_and_reproducible():
     cfg = dict(bench.CONFIGS["c2"], name="c2")
     assert bench.search_kernel(cfg) == ("k_search_warp", "k_search_warp S'<=10")
     prof = bench.NCU_SEARCH["k_search_warp S'<=10"]
-    # the profiled small case: 1.00e10 evaluated checks in 146.4 us at 2.07 GHz
-    r = bench.search_roofline(cfg, 10027309179.0, 8800799405.0, 11181, 0.146432, 2.0)
+    # the profiled small case: 1.00e10 evaluated checks in 143.1 us at 2.07 GHz
+    r = bench.search_roofline(cfg, 10032515195.0, 8800799405.0, 11181, 0.143072, 2.0)
     assert r["kernel"] == "k_search_warp" and r["bound"] == "smem" and r["unit"] == "GB/s"
     assert 0.5 < r["frac"] < 1.0
     assert abs(r["frac"] - prof["smem_wavefronts_frac"]) < 0.02
@@ -122,7 +122,7 @@ def test_roofline_fraction_is_bounded_and_reproducible():
     assert r["model_ops"]["frac"] > 1.0  # the survey's per-useful-check model is not a fraction of a pipe
     cfg3 = dict(bench.CONFIGS["c3a"], name="c3a")
     assert bench.search_kernel(cfg3) == ("k_search_warp", "k_search_warp S'=12")
-    r3 = bench.search_roofline(cfg3, 78007509206.0, 77714307970.0, 4706, 0.901792, 8.0)
+    r3 = bench.search_roofline(cfg3, 78007607510.0, 77714307970.0, 4706, 0.901472, 8.0)
     assert r3["bound"] == "smem"
     assert abs(r3["frac"] - bench.NCU_SEARCH["k_search_warp S'=12"]["smem_wavefronts_frac"]) < 0.02
     cfg1 = dict(bench.CONFIGS["c1"], name="c1")
