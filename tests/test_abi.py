@@ -113,6 +113,8 @@ def test_params_layout_matches_header(glib):
                         ("GRAND_MEMBERSHIP_ROW_PARITY", glib.MEMBERSHIP_ROW_PARITY),
                         ("GRAND_MEMBERSHIP_HASH", glib.MEMBERSHIP_HASH),
                         ("GRAND_MEMBERSHIP_FASTEST", glib.MEMBERSHIP_FASTEST),
+                        ("GRAND_MEMBERSHIP_SOLVE", glib.MEMBERSHIP_SOLVE),
+                        ("GRAND_E_UNSUPPORTED", glib.E_UNSUPPORTED),
                         ("GRAND_ABANDON_SUSPENDED", glib.ABANDON_SUSPENDED),
                         ("GRAND_CURSOR_BYTES", glib.CURSOR_BYTES)):
         assert re.search(rf"{name}(\s*=\s*|\s+){value}\b", text), name
