@@ -139,3 +139,25 @@ def test_autotune_chooses_membership(g, tmp_path, S, N, M, snr):
     assert torch.equal(a["cw"], b["cw"]) and torch.equal(a["queries"], b["queries"])
     assert torch.equal(a["abandon"], b["abandon"])
     code.close()
+
+
+@pytest.mark.parametrize("S,N,M,snr,warps", [(10, 128, 16, 7.0, (2, 4)), (12, 512, 64, 14.0, (1, 2))])
+def test_autotune_hash_join_alone(g, S, N, M, snr, warps):
+    """With membership HASH the tuner times the hash join's own launch shapes
+    (warps per CTA x preparation weights, 6 candidates) and every candidate
+    is a valid shape; the tuned decode equals the TEP-by-TEP one."""
+    import torch
+
+    code = g.Code.polar(N, N // 2)
+    d = wl.qam_frames(55, S, 2000, N, info_of(g, N), M, snr)
+    sym = torch.from_numpy(d["symbols"]).cuda()
+    p = g.Params.make(M=M, S=S, query_cap=1 << 20, membership=g.MEMBERSHIP_HASH)
+    r = g.autotune(code, p, sym)
+    assert r["membership"] == g.MEMBERSHIP_HASH and r["candidates"] == 6 and not r["from_cache"]
+    assert p.tiles[0] in warps and p.tiles[1] == 0 and p.tiles[2] in (1, 2, 3)
+    a = g.decode_symbols(code, p, sym)
+    b = g.decode_symbols(code, g.Params.make(M=M, S=S, query_cap=1 << 20), sym)
+    torch.cuda.synchronize()
+    assert torch.equal(a["cw"], b["cw"]) and torch.equal(a["queries"], b["queries"])
+    assert torch.equal(a["abandon"], b["abandon"])
+    code.close()
