@@ -88,6 +88,36 @@ def test_solve_two_call_path_and_stats(g, oracle_lib):
     assert fused["evaluated_checks"] >= int((a["abandon"] == 0).sum())
 
 
+def test_solve_plan_host_memory_and_deadline(g, oracle_lib):
+    """SOLVE through a CUDA-graph plan, from host memory, and with a device-time
+    budget: the outputs equal the direct call's (the preparation decides every
+    frame, and frames the preparation decides are never cut)."""
+    import torch
+
+    N, M, S = 128, 16, 10
+    code, H, info = code_pair(g, oracle_lib, N)
+    d = wl.qam_frames(72, 5, 3000, N, info, M, 7.0)
+    sym = to_dev(d["symbols"])
+    p = g.Params.make(M=M, S=S, query_cap=1 << 20, membership=SOLVE)
+    ref = unpack(g.decode_symbols(code, p, sym))
+    cw = torch.empty((3000, N // 32), dtype=torch.int32, device="cuda")
+    q = torch.empty(3000, dtype=torch.int32, device="cuda")
+    ab = torch.empty(3000, dtype=torch.uint8, device="cuda")
+    plan = g.plan_symbols(code, p, sym, cw, q, ab)
+    for _ in range(2):
+        cw.zero_()
+        q.zero_()
+        ab.fill_(9)
+        plan.launch()
+        assert_same(unpack({"cw": cw, "queries": q, "abandon": ab}), ref, "solve plan")
+    plan.close()
+    h = g.decode_symbols_host(code, p, torch.from_numpy(d["symbols"]).pin_memory())
+    assert_same({"cw": h["cw"].numpy().view(np.uint32), "queries": h["queries"].numpy().view(np.uint32).astype(np.int64),
+                 "abandon": h["abandon"].numpy()}, ref, "solve host memory")
+    pd = g.Params.make(M=M, S=S, query_cap=1 << 20, membership=SOLVE, deadline_ns=1)
+    assert_same(unpack(g.decode_symbols(code, pd, sym)), ref, "solve with a deadline")
+
+
 @pytest.mark.parametrize("S", [10, 12])
 def test_solve_mixed_batch(g, oracle_lib, S):
     import torch
