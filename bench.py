@@ -990,7 +990,7 @@ def run_config(args, cfg, g, ctx):
                  "latency_ms": {"p50": float(np.percentile(s_ms, 50)), "p99": float(np.percentile(s_ms, 99))},
                  "kernel_ms": {"prep": rs["prep_ms"], "search": rs["search_ms"]},
                  "frames_to_tep_search": int(rs["hard_frames"]), "ranked_solutions": int(rs["evaluated_checks"]),
-                 "outputs_equal": bool(same), "graph": True,
+                 "outputs_equal": bool(same), "graph": True, "profile": "profiles/k_prep_solve_c2_small.md",
                  "what": "the same batch with the first hit found by Gaussian elimination over each frame's TEP "
                          "coordinates (the codewords of the TEP space are the solutions of a GF(2) linear "
                          "system; the first hit is the one of smallest canonical rank): same outputs, no TEP "
