@@ -141,8 +141,8 @@ def search_roofline(cfg, evaluated, useful, hard, kernel_ms, alg_words, frames=0
     frac = the kernel's use of that unit per second / its peak, with the use =
     TEP checks the kernel evaluated in this run (counted on the device) x what
     one evaluated check costs the unit (ncu, same kernel: shared-memory bytes
-    or ALU lane-ops). It stays below 1 by construction. The survey's model
-    (N-K)/32 three-input ops per useful check is kept beside it as model_ops:
+    or ALU lane-ops). It stays below 1 by construction. The per-check cost
+    model of (N-K)/32 three-input ops per useful check is kept beside it as model_ops:
     it can exceed the ALU peak, because the split compare tests 32 TEPs per
     table word or logic op on a projection and confirms only matches on the
     full syndrome."""

@@ -107,8 +107,8 @@ def test_roofline_fraction_is_bounded_and_reproducible():
     on the unit that bounds it: for the profiled launch itself (its evaluated
     checks over its own duration) it reproduces the busy fraction the profile
     measured (shared-memory wavefronts for the nibble-table search, the ALU
-    pipe for the bit-plane search) and it is below 1; the survey-model figure
-    is kept apart (model_ops)."""
+    pipe for the bit-plane search) and it is below 1; the (N-K)/32-ops-per-check
+    model figure is kept apart (model_ops)."""
     bench = load_bench()
     cfg = dict(bench.CONFIGS["c2"], name="c2")
     assert bench.search_kernel(cfg) == ("k_search_warp", "k_search_warp S'<=10")
@@ -119,7 +119,7 @@ def test_roofline_fraction_is_bounded_and_reproducible():
     assert 0.5 < r["frac"] < 1.0
     assert abs(r["frac"] - prof["smem_wavefronts_frac"]) < 0.02
     assert 0.0 < r["alu"]["frac"] < 1.0
-    assert r["model_ops"]["frac"] > 1.0  # the survey's per-useful-check model is not a fraction of a pipe
+    assert r["model_ops"]["frac"] > 1.0  # the per-useful-check cost model is not a fraction of a pipe
     cfg3 = dict(bench.CONFIGS["c3a"], name="c3a")
     assert bench.search_kernel(cfg3) == ("k_search_warp", "k_search_warp S'=12")
     r3 = bench.search_roofline(cfg3, 78007607510.0, 77714307970.0, 4706, 0.901472, 8.0)
