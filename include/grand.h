@@ -123,8 +123,9 @@ typedef enum grand_order {
  *               frame abandons with min(valid TEPs, query_cap) queries).
  *               Outputs are those of AUTO (decoded word, query count = the
  *               hit's position in the canonical order, abandon flag); stats
- *               count the ranked solutions as checks. Frames whose solution
- *               set has more than 2^8 members go to the TEP search.
+ *               count the ranked solutions as checks. The preparation tests
+ *               weights <= 1 first (tiles[2] is not used). Frames whose
+ *               solution set has more than 2^8 members go to the TEP search.
  *               QAM_NNE / QAM_NEARER (uniform and uneven batches); not for
  *               QAM_NNE5, HAMMING, the resumable search, the autotuner or
  *               the no-allocation entry point. */
